@@ -1,0 +1,359 @@
+"""FP64 CPU oracle for the joint 3DGS + pose + feature-track training step.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import this package.  It shares
+no code with the CUDA library (``paper_2603_04847_gb300``) and imports
+nothing from it.
+
+The arithmetic lives in ``gs_oracle.c`` (plain C, double precision), built
+here with gcc into ``liboracle.so`` and loaded through ctypes.  This module
+only marshals numpy arrays and adds the discrete tile stage, which is a
+plain lexicographic sort (a library primitive) over the oracle's own
+projected records.
+
+Passages restated (GloSplat, arXiv 2603.04847):
+  * Eq. 5 (L1 part of the photometric loss) and Algorithm 1 "Rasterize";
+  * Eq. 6 (Huber reprojection loss on track points, delta = 1 px);
+  * the projection pi(K, T, X) = proj(K (R X + t)) after Algorithm 1;
+  * T_i = T_i^(0) (+) dT_i (Algorithm 1), read as Exp(xi) T0.
+Every reading of a point the paper leaves open is listed in the design doc.
+
+Parity status: every function here is pinned by ``tests/test_oracle_*.py``
+(closed forms, invariants, library special cases and central finite
+differences).  The paper's own quality numbers (PSNR etc.) need its datasets
+and are not reproduced ("parity unpinned" for those only).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gs_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ALPHA_MIN = 1.0 / 255.0
+ALPHA_MAX = 0.99
+T_MIN = 1e-4
+
+PROJ_FIELDS = [
+    "visible", "depth", "mx", "my", "cov_xx", "cov_xy", "cov_yy",
+    "con_a", "con_b", "con_c", "opacity", "r", "g", "b",
+    "bound_x0", "bound_y0", "bound_x1", "bound_y1",
+    "px_x0", "px_y0", "px_x1", "px_y1", "xc", "yc",
+]
+P = {name: i for i, name in enumerate(PROJ_FIELDS)}
+
+KNIFE_ALPHA_MIN = 1
+KNIFE_T_MIN = 2
+KNIFE_ALPHA_MAX = 4
+KNIFE_DEPTH = 8
+
+
+def build(force: bool = False) -> str:
+    """Compile gs_oracle.c into liboracle.so with gcc (portable flags only)."""
+    with _lock:
+        if (not force and os.path.exists(_LIB_PATH)
+                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            return _LIB_PATH
+        tmp = _LIB_PATH + ".tmp.%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+               "-D_DEFAULT_SOURCE", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd, cwd=_HERE)
+        os.replace(tmp, _LIB_PATH)
+        return _LIB_PATH
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [
+        ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+        ("fx", ctypes.c_double), ("fy", ctypes.c_double),
+        ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+        ("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3),
+        ("near_plane", ctypes.c_double), ("far_plane", ctypes.c_double),
+    ]
+
+
+class _Scene(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32), ("sh_degree", ctypes.c_int32),
+        ("mean", ctypes.c_void_p), ("log_scale", ctypes.c_void_p),
+        ("quat", ctypes.c_void_p), ("opacity_logit", ctypes.c_void_p),
+        ("sh", ctypes.c_void_p),
+    ]
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        lib.orc_sh_eval.argtypes = [ctypes.c_int, vp, vp, vp]
+        lib.orc_project.argtypes = [vp, vp, vp]
+        lib.orc_render.argtypes = [vp, vp, vp, i64, vp, dbl, vp, vp, vp, vp, vp, vp]
+        lib.orc_render_tiled.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp]
+        lib.orc_render_bwd.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.orc_track.argtypes = [i32, vp, i64, vp, vp, vp, i32, vp, dbl, dbl, vp, vp, vp, vp]
+        lib.orc_se3_exp.argtypes = [vp, vp]
+        lib.orc_se3_log.argtypes = [vp, vp]
+        lib.orc_se3_left_jacobian.argtypes = [vp, vp]
+        lib.orc_adam.argtypes = [i64, vp, vp, vp, vp, dbl, dbl, dbl, dbl, ctypes.c_int]
+        lib.orc_pose_update.argtypes = [i32, vp, vp, vp, vp, vp, vp, ctypes.c_int,
+                                        dbl, dbl, dbl, dbl, ctypes.c_int, vp]
+        _lib = lib
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def make_camera(width, height, fx, fy, cx, cy, R, t, near=0.01, far=1e10) -> Camera:
+    c = Camera()
+    c.width, c.height = int(width), int(height)
+    c.fx, c.fy, c.cx, c.cy = float(fx), float(fy), float(cx), float(cy)
+    R = np.asarray(R, dtype=np.float64).reshape(9)
+    t = np.asarray(t, dtype=np.float64).reshape(3)
+    for i in range(9):
+        c.R[i] = R[i]
+    for i in range(3):
+        c.t[i] = t[i]
+    c.near_plane, c.far_plane = float(near), float(far)
+    return c
+
+
+def camera_from_rt(width, height, K, Rt, near=0.01, far=1e10) -> Camera:
+    """K = (fx, fy, cx, cy); Rt = 12 numbers, row-major R then t."""
+    Rt = np.asarray(Rt, dtype=np.float64).reshape(12)
+    return make_camera(width, height, K[0], K[1], K[2], K[3], Rt[:9], Rt[9:], near, far)
+
+
+class Scene:
+    """Raw Gaussian parameters in double precision (keeps the arrays alive)."""
+
+    def __init__(self, mean, log_scale, quat, opacity_logit, sh):
+        self.mean = _f64(mean).reshape(-1, 3)
+        self.log_scale = _f64(log_scale).reshape(-1, 3)
+        self.quat = _f64(quat).reshape(-1, 4)
+        self.opacity_logit = _f64(opacity_logit).reshape(-1)
+        sh = _f64(sh)
+        n = self.mean.shape[0]
+        self.sh = sh.reshape(n, -1, 3)
+        K = self.sh.shape[1]
+        deg = int(round(np.sqrt(K))) - 1
+        if (deg + 1) ** 2 != K or deg > 3:
+            raise ValueError("sh must have (deg+1)^2 <= 16 coefficients per channel")
+        self.sh_degree = deg
+        self.n = n
+        self._c = _Scene(n, deg, _ptr(self.mean), _ptr(self.log_scale), _ptr(self.quat),
+                         _ptr(self.opacity_logit), _ptr(self.sh))
+
+    @property
+    def c(self):
+        return ctypes.byref(self._c)
+
+    def copy(self):
+        return Scene(self.mean.copy(), self.log_scale.copy(), self.quat.copy(),
+                     self.opacity_logit.copy(), self.sh.copy())
+
+
+def sh_eval(degree, d):
+    K = (degree + 1) ** 2
+    Y = np.zeros(K)
+    dY = np.zeros((K, 3))
+    r = _L().orc_sh_eval(int(degree), _ptr(_f64(d)), _ptr(Y), _ptr(dY))
+    if r < 0:
+        raise ValueError("bad degree")
+    return Y, dY
+
+
+def project(scene: Scene, cam: Camera) -> np.ndarray:
+    out = np.zeros((scene.n, len(PROJ_FIELDS)))
+    _L().orc_project(scene.c, ctypes.byref(cam), _ptr(out))
+    return out
+
+
+def render(scene: Scene, cam: Camera, bg=(0.0, 0.0, 0.0), pixels=None, knife_eps=0.0):
+    """Brute-force render of one view.  Returns dict with image [H,W,3] (or
+    [npix,3]), T_final, last_id, n_added, knife flags and the pair count."""
+    bg = _f64(bg)
+    if pixels is None:
+        npix = cam.width * cam.height
+        pix = None
+        shape = (cam.height, cam.width)
+    else:
+        pix = _i32(pixels).reshape(-1, 2)
+        npix = pix.shape[0]
+        shape = (npix,)
+    image = np.zeros(shape + (3,))
+    T = np.zeros(shape)
+    last = np.zeros(shape, dtype=np.int32)
+    nadd = np.zeros(shape, dtype=np.int32)
+    knife = np.zeros(shape, dtype=np.int32)
+    pairs = ctypes.c_int64(0)
+    _L().orc_render(scene.c, ctypes.byref(cam), _ptr(bg), npix, _ptr(pix), float(knife_eps),
+                    _ptr(image), _ptr(T), _ptr(last), _ptr(nadd), _ptr(knife),
+                    ctypes.byref(pairs))
+    return dict(image=image, T_final=T, last_id=last, n_added=nadd, knife=knife,
+                n_pairs=pairs.value)
+
+
+def render_tiled(scene: Scene, cam: Camera, tile: int, bg=(0.0, 0.0, 0.0)):
+    bg = _f64(bg)
+    image = np.zeros((cam.height, cam.width, 3))
+    T = np.zeros((cam.height, cam.width))
+    r = _L().orc_render_tiled(scene.c, ctypes.byref(cam), _ptr(bg), int(tile), _ptr(image), _ptr(T))
+    if r != 0:
+        raise ValueError("bad tile")
+    return image, T
+
+
+def render_bwd(scene: Scene, cam: Camera, v_image, bg=(0.0, 0.0, 0.0), pixels=None):
+    """Gradients of sum(v_image * image) w.r.t. all raw parameters and the
+    camera's left-perturbation pose tangent (6)."""
+    bg = _f64(bg)
+    v = _f64(v_image)
+    if pixels is None:
+        npix, pix = cam.width * cam.height, None
+    else:
+        pix = _i32(pixels).reshape(-1, 2)
+        npix = pix.shape[0]
+    v = v.reshape(npix, 3)
+    n, K = scene.n, scene.sh.shape[1]
+    g = dict(mean=np.zeros((n, 3)), log_scale=np.zeros((n, 3)), quat=np.zeros((n, 4)),
+             opacity_logit=np.zeros(n), sh=np.zeros((n, K, 3)), tangent=np.zeros(6),
+             v2d=np.zeros((n, 9)))
+    _L().orc_render_bwd(scene.c, ctypes.byref(cam), _ptr(bg), npix, _ptr(pix), _ptr(v),
+                        _ptr(g["mean"]), _ptr(g["log_scale"]), _ptr(g["quat"]),
+                        _ptr(g["opacity_logit"]), _ptr(g["sh"]), _ptr(g["tangent"]),
+                        _ptr(g["v2d"]))
+    return g
+
+
+def l1_loss_grad(image, target, weight=1.0):
+    """L1 part of Eq. 5 for one view: weight * mean |image - target| over
+    pixels and channels, and its (sub)gradient with sign(0) = 0."""
+    image = _f64(image)
+    target = _f64(target)
+    n = image.size
+    d = image - target
+    return weight * np.abs(d).sum() / n, weight * np.sign(d) / n
+
+
+def track(X, obs_point, obs_cam, obs_xy, cams, delta=1.0, weight=1.0):
+    """Eq. 6 over the given observations.  Returns (sum rho, grad_X of
+    weight*sum rho, pose tangents [n_cams,6], n_masked)."""
+    X = _f64(X).reshape(-1, 3)
+    op, oc = _i32(obs_point), _i32(obs_cam)
+    xy = _f64(obs_xy).reshape(-1, 2)
+    arr = (Camera * len(cams))(*cams)
+    loss = ctypes.c_double(0.0)
+    masked = ctypes.c_int64(0)
+    gX = np.zeros_like(X)
+    tan = np.zeros((len(cams), 6))
+    r = _L().orc_track(X.shape[0], _ptr(X), op.shape[0], _ptr(op), _ptr(oc), _ptr(xy),
+                       len(cams), arr, float(delta), float(weight), ctypes.byref(loss),
+                       _ptr(gX), _ptr(tan), ctypes.byref(masked))
+    if r != 0:
+        raise ValueError("observation index out of range")
+    return loss.value, gX, tan, masked.value
+
+
+def project_points(X, cam: Camera):
+    """pi(K, T, X) for points X [n,3] (the projection after Algorithm 1);
+    returns uv [n,2] and camera depth [n].  Used to synthesise noiseless
+    track observations in tests."""
+    X = _f64(X).reshape(-1, 3)
+    R = np.array(cam.R[:]).reshape(3, 3)
+    t = np.array(cam.t[:])
+    Xc = X @ R.T + t
+    uv = np.stack([cam.fx * Xc[:, 0] / Xc[:, 2] + cam.cx,
+                   cam.fy * Xc[:, 1] / Xc[:, 2] + cam.cy], axis=1)
+    return uv, Xc[:, 2]
+
+
+def se3_exp(xi):
+    T = np.zeros(12)
+    _L().orc_se3_exp(_ptr(_f64(xi)), _ptr(T))
+    return T
+
+
+def se3_log(T):
+    xi = np.zeros(6)
+    _L().orc_se3_log(_ptr(_f64(T)), _ptr(xi))
+    return xi
+
+
+def se3_left_jacobian(xi):
+    J = np.zeros(36)
+    _L().orc_se3_left_jacobian(_ptr(_f64(xi)), _ptr(J))
+    return J.reshape(6, 6)
+
+
+def adam(p, g, m, v, lr, beta1=0.9, beta2=0.999, eps=1e-15, step=1):
+    """In-place Adam step on float64 arrays p, m, v."""
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = _f64(g)
+    _L().orc_adam(p.size, _ptr(p), _ptr(g), _ptr(m), _ptr(v), float(lr), float(beta1),
+                  float(beta2), float(eps), int(step))
+
+
+def pose_update(T0, xi, g_tangent, m=None, v=None, lr=1e-5, beta1=0.9, beta2=0.999,
+                eps=1e-15, step=1, use_adam=True):
+    """Returns (g_xi, Rt_out); xi, m, v are updated in place when use_adam."""
+    T0 = _f64(T0).reshape(-1, 12)
+    V = T0.shape[0]
+    for a in (xi,) + ((m, v) if use_adam else ()):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    gt = _f64(g_tangent).reshape(V, 6)
+    g_xi = np.zeros((V, 6))
+    Rt = np.zeros((V, 12))
+    if m is None:
+        m = np.zeros((V, 6))
+    if v is None:
+        v = np.zeros((V, 6))
+    _L().orc_pose_update(V, _ptr(T0), _ptr(xi), _ptr(gt), _ptr(g_xi), _ptr(m), _ptr(v),
+                         int(bool(use_adam)), float(lr), float(beta1), float(beta2),
+                         float(eps), int(step), _ptr(Rt))
+    return g_xi, Rt
+
+
+def tile_lists(proj: np.ndarray, width: int, height: int, tile: int):
+    """Discrete stage: every (tile, depth, index) instance of one view from
+    the oracle's own pixel rectangles, in the canonical order (tile, depth
+    ascending, index ascending).  Returns (tile_id, depth, gid) arrays."""
+    vis = proj[:, P["visible"]] > 0
+    idx = np.nonzero(vis)[0]
+    tiles_x = (width + tile - 1) // tile
+    tl, dl, gl = [], [], []
+    for j in idx:
+        x0 = int(proj[j, P["px_x0"]]) // tile
+        y0 = int(proj[j, P["px_y0"]]) // tile
+        x1 = int(proj[j, P["px_x1"]]) // tile
+        y1 = int(proj[j, P["px_y1"]]) // tile
+        for ty in range(y0, y1 + 1):
+            for tx in range(x0, x1 + 1):
+                tl.append(ty * tiles_x + tx)
+                dl.append(proj[j, P["depth"]])
+                gl.append(j)
+    t = np.array(tl, dtype=np.int64)
+    d = np.array(dl, dtype=np.float64)
+    g = np.array(gl, dtype=np.int64)
+    order = np.lexsort((g, d, t))
+    return t[order], d[order], g[order]
