@@ -1,0 +1,473 @@
+"""Benchmark of the joint pose-appearance training step (one iteration of
+Algorithm 1 over a batch of views: projection, tile sort, compositing,
+fused L1 + backward with pose gradient, Huber track term, Adam on
+Gaussians, track points and SE(3) pose deltas).
+
+Default workload: 8 cameras 1237x822 on a sphere looking at the scene,
+200k Gaussians with SH degree 3, 20k tracks with 2..12 observations, all 8
+views in every step, batched and captured in a CUDA graph.  Prints one JSON
+line (metric: Mpix*views/s of the joint fwd+bwd step).
+
+--impl reference times the FP64 CPU oracle (the only reference this build
+has) on a bounded pixel sample of the same workload.
+--gpus N under torchrun runs N independent replicas (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "joint fwd+bwd steps/s (Mpix·views/s) incl. pose+track grads; % HBM roofline"
+UNIT = "Mpix*views/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mid", choices=["mid", "train", "batched"])
+    ap.add_argument("--mode", default="batched", choices=["batched", "plain"])
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain one-view-per-launch timing")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="run this many eager steps and exit (for ncu launch lists)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_desc(name, w):
+    W = w["workload"]
+    return dict(workload="%s: %d views %s, %d Gaussians SH%d, %d tracks (%d-%d obs), batch %d" % (
+        name, W.n_views, "%dx%d" % (W.width[0], W.height[0]) if W.width[0] == W.width[1] else
+        "%d-%dx%d-%d" % (W.width[0], W.width[1], W.height[0], W.height[1]), W.n_gaussians, W.sh_degree,
+        W.n_tracks, W.obs_range[0], W.obs_range[1], W.batch))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg
+
+def oracle_sample_step(w, n_pix, rng):
+    """One bounded sample of the workload on the FP64 oracle: forward and
+    backward (random cotangent) of n_pix pixels of view 0 over all its
+    Gaussians, plus the track term of view 0's observations.  Returns
+    (seconds, pixels)."""
+    import oracle
+    sc = oracle.Scene(**w["scene"])
+    K, Rt, wh = w["K"], w["Rt"], w["wh"]
+    cam = oracle.camera_from_rt(int(wh[0][0]), int(wh[0][1]), K[0], Rt[0])
+    W, H = int(wh[0][0]), int(wh[0][1])
+    pix = np.stack([rng.integers(W // 4, 3 * W // 4, n_pix), rng.integers(H // 4, 3 * H // 4, n_pix)], 1)
+    v = rng.normal(size=(n_pix, 3))
+    tr = w["tracks"]
+    sel = tr["obs_view"] == 0
+    X = tr["X"]
+    xy = rng.uniform(0, W, (int(sel.sum()), 2))
+    t0 = time.perf_counter()
+    oracle.render(sc, cam, pixels=pix)
+    oracle.render_bwd(sc, cam, v, pixels=pix)
+    oracle.track(X, tr["obs_point"][sel], tr["obs_view"][sel] * 0, xy, [cam], 1.0, 0.1)
+    return time.perf_counter() - t0, n_pix
+
+
+def cpu_baseline(w, seconds):
+    rng = np.random.default_rng(123)
+    t, n = oracle_sample_step(w, 16, rng)
+    per_px = max(t / n, 1e-6)
+    n_pix = int(max(16, min(20000, seconds / per_px)))
+    t, n = oracle_sample_step(w, n_pix, rng)
+    return dict(value=n / 1e6 / t, unit=UNIT, cores=1, kind="oracle",
+                sample="fwd+bwd of %d random pixels of view 0 (%dx%d) over all %d Gaussians + view-0 "
+                       "track term, single-threaded FP64 C oracle, %.1f s" % (
+                           n, int(w["wh"][0][0]), int(w["wh"][0][1]), w["workload"].n_gaussians, t))
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(0)
+    t, n = oracle_sample_step(w, 16, rng)
+    per_px = max(t / n, 1e-6)
+    budget = 150.0 / max(args.steps + args.warmup, 1)   # whole run within a few minutes
+    n_pix = int(max(8, min(5000, budget / per_px)))
+    for _ in range(args.warmup):
+        oracle_sample_step(w, n_pix, rng)
+    times = []
+    for _ in range(args.steps):
+        t, n = oracle_sample_step(w, n_pix, rng)
+        times.append(t)
+    tot = sum(times)
+    value = n_pix * args.steps / 1e6 / tot
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * tot / args.steps,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload_desc(args.workload, w), sample="%d pixels of view 0 per step" % n_pix),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle",
+                                  sample="fwd+bwd of %d random pixels of view 0 over all Gaussians + "
+                                         "view-0 track term per step" % n_pix),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.dev = device_id
+        self.proc = None
+        self.lines = []
+        self.t_on = None
+        self.t_off = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark_on(self):
+        self.t_on = time.time()
+
+    def mark_off(self):
+        self.t_off = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [l for (t, l) in self.lines if self.t_on is None or (self.t_on <= t <= (self.t_off or t))]
+        if not rows:
+            rows = [l for _, l in self.lines]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            p = [x.strip() for x in r.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, p[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons), samples=len(sm))
+
+
+def gpu_inputs(name, device):
+    """Synthetic workload on the device.  Targets are renders of the
+    ground-truth scene at the ground-truth poses; track observations are the
+    projections of the track points at those poses plus the workload's pixel
+    noise (and outliers)."""
+    import torch
+    import synth
+    from paper_2603_04847_gb300 import Batch, Cameras, Gaussians, Renderer
+    w = synth.make_workload(name)
+    wh, K = w["wh"], w["K"]
+    V = len(wh)
+    cams_gt = Cameras.from_numpy(wh, K, w["Rt_gt"], device=device)
+    g_gt = Gaussians.from_numpy(w["gt"], device=device)
+    P = (wh[:, 0].astype(np.int64) * wh[:, 1])
+    off = np.concatenate([[0], np.cumsum(P)])
+    targets = torch.empty((int(off[-1]), 3), dtype=torch.float32, device=device)
+    for v0 in range(0, V, 16):
+        views = list(range(v0, min(V, v0 + 16)))
+        b = Batch(cams_gt, views, device=device)
+        r = Renderer(g_gt.n, cams_gt, b, device=device)
+        r.ensure_capacity(g_gt)
+        r.forward(g_gt)
+        targets[int(off[v0]):int(off[views[-1] + 1])].copy_(r.image)
+        del r
+    tr = w["tracks"]
+    X = torch.as_tensor(tr["X"], dtype=torch.float32, device=device)
+    Rt = torch.as_tensor(w["Rt_gt"], dtype=torch.float32, device=device)
+    Kt = torch.as_tensor(K, dtype=torch.float32, device=device)
+    op = torch.as_tensor(tr["obs_point"], dtype=torch.int64, device=device)
+    ov = torch.as_tensor(tr["obs_view"], dtype=torch.int64, device=device)
+    R = Rt[ov, :9].reshape(-1, 3, 3)
+    Xc = torch.einsum("nij,nj->ni", R, X[op]) + Rt[ov, 9:]
+    uv = torch.stack([Kt[ov, 0] * Xc[:, 0] / Xc[:, 2] + Kt[ov, 2], Kt[ov, 1] * Xc[:, 1] / Xc[:, 2] + Kt[ov, 3]], 1)
+    uv = uv + torch.as_tensor(tr["noise"], dtype=torch.float32, device=device)
+    out = torch.as_tensor(tr["outlier"], device=device)
+    whv = torch.as_tensor(wh, dtype=torch.float32, device=device)[ov]
+    uv = torch.where(out[:, None], torch.as_tensor(tr["outlier_uv01"], dtype=torch.float32, device=device) * whv, uv)
+    g = Gaussians.from_numpy(w["scene"], device=device)
+    cams = Cameras.from_numpy(wh, K, w["Rt"], device=device)
+    return dict(w=w, g=g, cams=cams, X=X.clone(), obs_point=op.to(torch.int32).contiguous(),
+                obs_xy=uv.contiguous(), view_obs_offset=torch.as_tensor(tr["view_obs_offset"], device=device),
+                targets=targets, off=off)
+
+
+def make_step(inp, views, mode, lambda_ba):
+    from paper_2603_04847_gb300 import Hyper, JointStep
+    js = JointStep(inp["g"], inp["cams"], inp["X"], inp["obs_point"], inp["obs_xy"], inp["view_obs_offset"],
+                   inp["targets"], inp["off"], views, Hyper(lambda_ba=lambda_ba), mode=mode)
+    js.ensure_capacity()
+    return js
+
+
+def time_graph(js, steps, flush, use_graph=True):
+    import torch
+    st = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        evs[i][0].record(st)
+        js.run() if use_graph else js.step()
+        evs[i][1].record(st)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def stage_times(js, reps, flush):
+    """Per-stage device times (ms, mean over reps) of the eager step, with
+    CUDA events recorded on the launching stream between stages."""
+    import torch
+    st = torch.cuda.current_stream()
+    acc = {}
+    for _ in range(reps):
+        flush.zero_()
+        marks = [("start", torch.cuda.Event(enable_timing=True))]
+        marks[0][1].record(st)
+
+        def mark(name):
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(st)
+            marks.append((name, e))
+        js.step(mark)
+        torch.cuda.synchronize()
+        for (n0, e0), (n1, e1) in zip(marks[:-1], marks[1:]):
+            acc[n1] = acc.get(n1, 0.0) + e0.elapsed_time(e1)
+    return {k: v / reps for k, v in acc.items()}
+
+
+def algorithmic_model(js):
+    """Algorithmic bytes per stage (each intermediate written once and read
+    once; the sort as one read + one write of its 12-byte pairs) and the
+    compositing pair counts, from this step's own device counters."""
+    import torch
+    r = js.renderers[0]
+    g = js.g
+    N = g.n
+    K = g.sh.shape[1]
+    B = js.batch.B
+    P = js.batch.n_pixels
+    I = sum(rr.n_instances() for rr in js.renderers)
+    vis = sum(int((rr.proj.n_tiles[:N * rr.batch.B] > 0).sum().item()) for rr in js.renderers)
+    pairs_bwd = sum(int(rr.n_contrib.to(torch.int64).sum().item()) for rr in js.renderers)
+    n_tiles_total = sum(rr.batch.n_tiles for rr in js.renderers)
+    pbytes = N * (44 + 12 * K)
+    M_b = int(sum(int(js.view_obs_offset[v + 1] - js.view_obs_offset[v]) for v in js.views))
+    model = {
+        "project": pbytes + vis * 60 + (B * N - vis) * 4,
+        "sort": B * N * 12 + vis * 20 + I * 24 + I * 8 + n_tiles_total * 8,
+        "render_fwd": I * 40 + P * 20,
+        "raster_bwd": I * 40 + P * 32 + vis * 36,
+        "project_bwd": pbytes + vis * 36 + B * N * 4 + 2 * pbytes,
+        "track": M_b * 24 + min(M_b, js.X.shape[0]) * 24,
+        "adam": (N * (7 + 4 + 3 * K) + js.X.shape[0] * 3) * 4 * 7,
+    }
+    return model, dict(instances=I, visible_records=vis, pairs_bwd=pairs_bwd, pixels=P, obs_in_batch=M_b)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = "cuda:%d" % local
+    from paper_2603_04847_gb300 import build as libbuild
+    libbuild.build()
+    import synth
+    inp = gpu_inputs(args.workload, dev)
+    w = inp["w"]
+    W = w["workload"]
+    views = list(range(min(W.batch, W.n_views)))
+    js = make_step(inp, views, args.mode, W.lambda_ba)
+    if args.profile_steps:
+        for _ in range(args.profile_steps):
+            js.step()
+        torch.cuda.synchronize()
+        return
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    use_graph = not args.no_graph
+    if use_graph:
+        js.capture(warmup=1)
+    for _ in range(args.warmup):
+        flush.zero_()
+        js.run() if use_graph else js.step()
+    torch.cuda.synchronize()
+    flags = js.status_flags()
+    if flags:
+        raise RuntimeError("device status flags %d after warm-up" % flags)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.5)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.mark_on()
+    times = time_graph(js, args.steps, flush, use_graph)
+    torch.cuda.synchronize()
+    clocks.mark_off()
+    tot = torch.tensor([sum(times)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.barrier()
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    clk = clocks.stop()
+    ms = tot.item() / args.steps
+    P = js.batch.n_pixels
+    value = ws * P / 1e6 / (ms / 1e3)
+
+    # per-stage event timing of the same step (eager), for the roofline
+    st_ms = stage_times(js, 5, flush)
+    model, counts = algorithmic_model(js)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    stages = {k: dict(ms=st_ms.get(k, 0.0)) for k in model}
+    for k in stages:
+        t = stages[k]["ms"]
+        stages[k]["GBps"] = model[k] / (t * 1e-3) / 1e9 if t > 0 else None
+        stages[k]["hbm_frac"] = stages[k]["GBps"] / hbm_peak if t > 0 else None
+    dominant = max(("project", "sort", "render_fwd", "raster_bwd", "project_bwd"), key=lambda k: st_ms.get(k, 0))
+    # the compositing kernels are bound by FP32/SFU issue, not HBM: report
+    # their pair throughput against the FP32 lane peak
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = sms * 128 * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12   # TFLOP/s, FMA = 2
+    FLOP_PER_PAIR = {"render_fwd": 26.0, "raster_bwd": 86.0}
+    if dominant in FLOP_PER_PAIR:
+        fl = counts["pairs_bwd"] * FLOP_PER_PAIR[dominant]
+        ach = fl / (st_ms[dominant] * 1e-3) / 1e12
+        roof = dict(kernel=dominant, bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
+                    traffic=None, peak_source="derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (
+                        sms, peaks.get("sm_max_mhz", 2070.0)),
+                    work="%d compositing pairs x %.0f flop" % (counts["pairs_bwd"], FLOP_PER_PAIR[dominant]))
+    else:
+        ach = model[dominant] / (st_ms[dominant] * 1e-3) / 1e9
+        roof = dict(kernel=dominant, bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak,
+                    traffic=None, peak_source=peak_src)
+    step_bytes = sum(model.values())
+    hbm_step = dict(algorithmic_bytes=step_bytes, GBps=step_bytes / (ms * 1e-3) / 1e9,
+                    frac=step_bytes / (ms * 1e-3) / 1e9 / hbm_peak)
+
+    # plain one-view-per-launch form on the same inputs (eager, no graph)
+    plain = None
+    if not args.no_plain and args.mode == "batched":
+        jp = make_step(inp, views, "plain", W.lambda_ba)
+        for _ in range(2):
+            flush.zero_()
+            jp.step()
+        pt = time_graph(jp, max(3, min(args.steps, 10)), flush, use_graph=False)
+        pms = sum(pt) / len(pt)
+        plain = dict(ms_per_step=pms, value=P / 1e6 / (pms / 1e3), launches_per_step=jp.kernels_per_step())
+        del jp
+
+    # end to end through the public API: targets H2D from pinned memory every
+    # step, graph replay, loss D2H
+    host_tgt = js.target_batch.cpu().pin_memory()
+    loss_host = torch.zeros(2, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        js.target_batch.copy_(host_tgt, non_blocking=True)
+        js.run() if use_graph else js.step()
+        loss_host.copy_(js.loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e_t)
+    e2e = dict(value=ws * P / 1e6 / e2e_s, unit=UNIT, h2d_bytes_per_step=int(host_tgt.numel() * 4),
+               d2h_bytes_per_step=16, ms_per_step=e2e_s * 1e3)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cpu = cpu_baseline(w, args.cpu_seconds)
+
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
+                    ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+                    data="synthetic",
+                    config=dict(workload_desc(args.workload, w), mode=args.mode,
+                                graph=use_graph, l2="flushed between steps (256 MB write)",
+                                parallelism="replicas" if ws > 1 else "single GPU"),
+                    steps_per_s=1e3 / ms, e2e=e2e, gpu_launches=js.kernels_per_step() * args.steps,
+                    roofline=roof, hbm_step=hbm_step, stages=stages, counts=counts, clocks=clk,
+                    cpu_baseline=cpu, plain=plain)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        import synth
+        w = synth.make_workload(args.workload)
+        run_reference(args, w)
+        return
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,309 @@
+/*
+ * libgs — C ABI of the joint pose-appearance training step of GloSplat
+ * (arXiv 2603.04847): differentiable 3D Gaussian splatting with camera poses
+ * as parameters, fused with the explicit feature-track reprojection term.
+ *
+ * The step (Algorithm 1, one iteration, for a batch of views B):
+ *   gs_project        EWA projection + SH colour + tile rectangle per
+ *                     (view, Gaussian)                       ("Rasterize")
+ *   gs_sort_tiles     scan, per-tile duplication, depth-key radix sort and
+ *                     per-tile ranges                        ("Rasterize")
+ *   gs_render_fwd     front-to-back alpha compositing        ("Rasterize")
+ *   gs_render_bwd     L1 gradient of Eq. 5 (fused) + compositing backward
+ *                     + projection backward with pose gradient
+ *                     (Algorithm 1 "Backpropagate"; Sec. 3.3: poses are
+ *                     optimised by both losses)
+ *   track_reproj_fwd_bwd   Eq. 6: Huber reprojection of the separate track
+ *                     points, loss and Jacobians w.r.t. points and poses
+ *   pose_se3_update   T_i = T_i^(0) (+) dT_i (Algorithm 1) with the SE(3)
+ *                     gradient map and the Adam step on the pose deltas
+ *   gs_adam_update    Adam on Gaussian / track-point parameter arrays
+ *                     (Algorithm 1 "Update Gaussians", "Update track
+ *                     points"; Sec. 3.3 learning rates)
+ *
+ * Conventions shared by every entry point
+ *   - All array arguments are DEVICE pointers owned by the caller, unless a
+ *     field says "host".  Arrays are dense, row-major, 4-byte floats unless
+ *     stated; float arrays read with 16-byte vector loads must be 16-byte
+ *     aligned (checked: GS_ERR_ARG).
+ *   - No entry point allocates memory.  Scratch comes from a caller buffer
+ *     `ws` whose size the matching *_workspace() query returns.
+ *   - Every entry point is asynchronous on `stream` (a cudaStream_t; NULL =
+ *     the legacy default stream), returns a gs_status and never throws.
+ *     On failure gs_last_error() (thread-local) describes the cause.
+ *   - Conditions found on the device (instance capacity overflow,
+ *     non-finite inputs) are OR-ed into the caller's device word `status`
+ *     (GS_FLAG_*), so a captured CUDA graph can be checked after a replay.
+ *   - Camera model: world-to-camera x_c = R x + t, pinhole intrinsics
+ *     (fx, fy, cx, cy), pi(X) = (fx X/Z + cx, fy Y/Z + cy) (Sec. 3.2, the
+ *     projection pi of Eq. 4; Appendix E "Projection function").  Pixel
+ *     (u, v) has its centre at (u + 0.5, v + 0.5).
+ *   - Pose tangent: g = (dL/d rho, dL/d phi) for T <- Exp((rho, phi)) T at
+ *     0 (left perturbation, translation first), accumulated in double.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int gs_status;
+enum {
+  GS_OK = 0,
+  GS_ERR_ARG = 1,         /* invalid argument (null, size, alignment)      */
+  GS_ERR_CAPACITY = 2,    /* host-detected capacity problem                */
+  GS_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed          */
+  GS_ERR_NONFINITE = 4,   /* host-detected non-finite scalar argument      */
+  GS_ERR_UNSUPPORTED = 5  /* valid but unsupported configuration           */
+};
+
+/* Bits OR-ed into the device status word. */
+enum {
+  GS_FLAG_CAPACITY = 1,   /* more tile instances than `capacity`: the sort
+                             and renders ran on a truncated list; re-run
+                             with a larger capacity                      */
+  GS_FLAG_NONFINITE = 2   /* a Gaussian had a non-finite parameter and was
+                             treated as invisible                         */
+};
+
+#define GS_ABI_VERSION 1
+#define GS_MAX_BATCH 64   /* views per call */
+
+typedef struct CUstream_st* gs_stream; /* = cudaStream_t */
+
+/* Gaussian parameters, raw (pre-activation): scale = exp(log_scale),
+ * opacity = sigmoid(opacity_logit), rotation = quat / |quat| with quat =
+ * (w, x, y, z).  SH colour of degree sh_degree (<= 3) in the real basis of
+ * the original 3DGS renderer, K = (sh_degree + 1)^2 coefficients per colour
+ * channel, colour = max(0, 0.5 + sum_k sh[k] Y_k(dir)) with dir from the
+ * camera centre to the mean (Sec. 3.3 "Implementation": SH up to degree 3). */
+typedef struct gs_gaussians {
+  int32_t n;                  /* number of Gaussians N                     */
+  int32_t sh_degree;          /* 0..3                                       */
+  const float* mean;          /* [N,3]                                      */
+  const float* log_scale;     /* [N,3]                                      */
+  const float* quat;          /* [N,4]   16-byte aligned                    */
+  const float* opacity_logit; /* [N]                                        */
+  const float* sh;            /* [N,K,3]                                    */
+} gs_gaussians;
+
+/* Gradients w.r.t. the raw parameters, same layouts; ACCUMULATED (+=). */
+typedef struct gs_gaussian_grads {
+  float* mean;
+  float* log_scale;
+  float* quat;
+  float* opacity_logit;
+  float* sh;
+} gs_gaussian_grads;
+
+/* All cameras of the scene (Algorithm 1 REQUIRE: intrinsics K_i, poses). */
+typedef struct gs_cameras {
+  int32_t n_cams;             /* V                                          */
+  const int32_t* wh;          /* [V,2] width, height in pixels              */
+  const float* K;             /* [V,4] fx, fy, cx, cy                       */
+  const float* Rt;            /* [V,12] world-to-camera R (row-major), t    */
+  float near_plane;           /* splats/points with z < near are culled     */
+  float far_plane;            /* splats with z > far are culled             */
+} gs_cameras;
+
+/* A batch of views rendered together (Algorithm 1 "Sample image indices").
+ * Slot b renders camera views[b].  Per-slot images are packed one after
+ * another: pixel (u, v) of slot b is element px_offset[b] + v * W + u of
+ * every per-pixel buffer; its tiles are global tiles tile_offset[b] ..
+ * tile_offset[b+1]-1, row-major within the view. */
+typedef struct gs_batch {
+  int32_t B;                  /* 1..GS_MAX_BATCH                            */
+  int32_t tile;               /* tile edge in pixels: 16                    */
+  const int32_t* views;       /* [B]   device                               */
+  const int64_t* px_offset;   /* [B+1] device                               */
+  const int32_t* tile_offset; /* [B+1] device                               */
+  int64_t n_pixels;           /* host copy of px_offset[B]                  */
+  int32_t n_tiles;            /* host copy of tile_offset[B]                */
+  int32_t _pad;
+} gs_batch;
+
+/* Per-(slot, Gaussian) screen-space records, index r = b * N + j. */
+typedef struct gs_projected {
+  float* splat;     /* [B*N,12]: mean2d x, y, opacity, depth | conic a, b,
+                       c, q_max | colour r, g, b, 0.  16-byte aligned.
+                       q = a dx^2 + 2 b dx dy + c dy^2; alpha >= 1/255 iff
+                       q <= q_max = 2 ln(255 opacity) (below the clamp)   */
+  uint16_t* rect;   /* [B*N,4] tile rectangle x0, y0, x1, y1 (inclusive,
+                       tile units, within the view)                      */
+  uint32_t* n_tiles;/* [B*N]   tiles touched; 0 = invisible in that view   */
+} gs_projected;
+
+/* Adam hyperparameters.  `step` points to a DEVICE int32 holding the
+ * 1-based step number t used for bias correction (advance it with
+ * gs_step_advance, so a captured graph stays valid across replays). */
+typedef struct gs_adam {
+  float lr, beta1, beta2, eps;
+  const int32_t* step;
+} gs_adam;
+
+/* ---------------------------------------------------------------------- */
+
+int gs_abi_version(void);
+const char* gs_last_error(void);
+/* sizeof of the ABI structs, for bindings to verify their layout:
+ * 0 gs_gaussians, 1 gs_gaussian_grads, 2 gs_cameras, 3 gs_batch,
+ * 4 gs_projected, 5 gs_adam.  Returns 0 for an unknown id. */
+size_t gs_struct_size(int which);
+/* Number of streaming multiprocessors of the current device (0 on error). */
+int gs_device_sm_count(void);
+
+/*
+ * gs_project — EWA splatting of every Gaussian into every view of the batch
+ * (the rasterizer of Sec. 3.3, "Implementation"; the mean follows pi of
+ * Sec. 3.2).  Per (slot b, Gaussian j): x_c = R mu + t, culled if z is
+ * outside [near, far]; 2-D covariance J R Sigma R^T J^T + 0.3 I with the
+ * Jacobian J of pi at x_c (x/z, y/z clamped to 1.3 half-fields of view);
+ * conic = its inverse; colour from SH; tile rectangle of the pixels whose
+ * alpha can reach 1/255 (one pixel of margin).  Writes out->splat, ->rect
+ * and ->n_tiles for all B*N records (n_tiles = 0 when culled).
+ * Non-finite parameters set GS_FLAG_NONFINITE and cull the Gaussian.
+ */
+gs_status gs_project(const gs_gaussians* g, const gs_cameras* cams,
+                     const gs_batch* batch, const gs_projected* out,
+                     int32_t* status, gs_stream stream);
+
+/*
+ * gs_sort_tiles — per-tile duplication and depth ordering.  Exclusive scan
+ * of n_tiles over r = b*N + j, then one instance per (record, covered tile)
+ * with key (global tile << 32 | float bits of depth) and value r, then a
+ * stable LSD radix sort over the significant key bits, so that every tile's
+ * list is ordered by (depth, j).  ranges[2*t], ranges[2*t+1] = [start, end)
+ * of global tile t in the sorted list (0, 0 when empty).  The full instance
+ * count (saturated at 2^32 - 1) is written to n_instances (device) and never
+ * read back by the library, so the call can be captured in a CUDA graph.  If
+ * it exceeds `capacity`, GS_FLAG_CAPACITY is set and only the first
+ * `capacity` instances (in record order) are sorted and rendered.
+ * keys/vals: [capacity]; ranges: [2 * batch->n_tiles]; ws: see query.
+ */
+gs_status gs_sort_tiles_workspace(int32_t n_gaussians, const gs_batch* batch,
+                                  size_t capacity, size_t* ws_bytes);
+gs_status gs_sort_tiles(int32_t n_gaussians, const gs_cameras* cams,
+                        const gs_batch* batch,
+                        const gs_projected* proj, uint64_t* keys,
+                        uint32_t* vals, size_t capacity, uint32_t* ranges,
+                        uint32_t* n_instances, void* ws, size_t ws_bytes,
+                        int32_t* status, gs_stream stream);
+
+/*
+ * gs_render_fwd — front-to-back alpha compositing (Algorithm 1,
+ * "Rasterize").  For each pixel, over its tile's list: alpha = min(0.99,
+ * o exp(-q/2)); splats with alpha < 1/255 are skipped; the pixel stops
+ * before the splat that would take its transmittance T below 1e-4;
+ * C = sum c alpha T + T_final bg.  Writes image [n_pixels,3],
+ * T_final [n_pixels] and n_contrib [n_pixels] (position in the tile list,
+ * plus one, of the last splat added; 0 if none).  bg: [3] device.
+ */
+gs_status gs_render_fwd(const gs_batch* batch, const gs_cameras* cams,
+                        const gs_projected* proj, const uint32_t* vals,
+                        const uint32_t* ranges, const float* bg, float* image,
+                        float* T_final, uint32_t* n_contrib, gs_stream stream);
+
+/*
+ * gs_render_bwd — backward of gs_project + gs_render_fwd.
+ * dL/dimage is either v_image [n_pixels,3] or, when v_image is NULL, the L1
+ * term of Eq. 5 computed in place: l1_weight * sign(image - target) /
+ * (3 W_b H_b) per slot (sign(0) = 0); then loss (device double, may be
+ * NULL) += l1_weight * sum |image - target| / (3 W_b H_b).
+ * Compositing is recomputed back to front from T_final (nothing else is
+ * stored per pixel); per-splat gradients are reduced inside each tile's
+ * thread block before one atomic add per splat; then the projection
+ * backward accumulates dL/d(raw parameters) into dg and the per-camera pose
+ * tangent into g_pose_tangent [V,6] (double, +=) for cameras views[b].
+ * ws: see query (holds the screen-space gradients and block partials).
+ */
+gs_status gs_render_bwd_workspace(int32_t n_gaussians, const gs_batch* batch,
+                                  size_t* ws_bytes);
+gs_status gs_render_bwd(const gs_gaussians* g, const gs_cameras* cams,
+                        const gs_batch* batch, const gs_projected* proj,
+                        const uint32_t* vals, const uint32_t* ranges,
+                        const float* bg, const float* image,
+                        const float* T_final, const uint32_t* n_contrib,
+                        const float* v_image, const float* target,
+                        float l1_weight, double* loss,
+                        const gs_gaussian_grads* dg, double* g_pose_tangent,
+                        void* ws, size_t ws_bytes, gs_stream stream);
+
+/*
+ * The two halves of gs_render_bwd, callable separately (same arguments and
+ * workspace; gs_render_bwd == gs_raster_bwd then gs_project_bwd):
+ *  gs_raster_bwd   zeroes the screen-space gradient records in ws, then runs
+ *                  the compositing backward (fused L1 when v_image is NULL)
+ *                  and accumulates per-record gradients of (mean2d, conic,
+ *                  opacity, colour) into ws;
+ *  gs_project_bwd  chains those records through the projection into dg and
+ *                  g_pose_tangent.
+ */
+gs_status gs_raster_bwd(const gs_gaussians* g, const gs_cameras* cams,
+                        const gs_batch* batch, const gs_projected* proj,
+                        const uint32_t* vals, const uint32_t* ranges,
+                        const float* bg, const float* image,
+                        const float* T_final, const uint32_t* n_contrib,
+                        const float* v_image, const float* target,
+                        float l1_weight, double* loss, void* ws,
+                        size_t ws_bytes, gs_stream stream);
+gs_status gs_project_bwd(const gs_gaussians* g, const gs_cameras* cams,
+                         const gs_batch* batch, const gs_projected* proj,
+                         const gs_gaussian_grads* dg, double* g_pose_tangent,
+                         void* ws, size_t ws_bytes, gs_stream stream);
+
+/*
+ * track_reproj_fwd_bwd — Eq. 6 for the observations of the batch's views
+ * (Algorithm 1, "Joint BA loss on track points").  Observations are
+ * bucketed by camera: those of camera i are obs [view_obs_offset[i],
+ * view_obs_offset[i+1]); observation o sees track point obs_point[o] at
+ * pixel obs_xy[o] (continuous coordinates, pixel centres at +0.5).
+ * For each: X_c = R_i X + t_i; masked (counted in n_masked) if Z_c <= near;
+ * r = pi_i(X) - x; rho = |r|^2 if |r| <= delta else 2 delta |r| - delta^2.
+ * loss (device double) += sum rho; grad_X [n_points,3] += weight * d rho/dX;
+ * g_pose_tangent [V,6] (double) += weight * d rho / d(pose tangent).
+ * n_masked (device uint32, may be NULL) += masked count.
+ */
+gs_status track_reproj_workspace(const gs_batch* batch, size_t* ws_bytes);
+gs_status track_reproj_fwd_bwd(const float* X, int32_t n_points,
+                               const int32_t* obs_point, const float* obs_xy,
+                               const int64_t* view_obs_offset,
+                               const gs_cameras* cams, const gs_batch* batch,
+                               float delta, float weight, double* loss,
+                               float* grad_X, double* g_pose_tangent,
+                               uint32_t* n_masked, void* ws, size_t ws_bytes,
+                               gs_stream stream);
+
+/*
+ * pose_se3_update — pose composition of Algorithm 1 (T_i = T_i^(0) (+)
+ * dT_i, read as T_i = Exp(xi_i) T_i^(0), xi = (rho, phi)) and the pose
+ * step ("Update poses"; Sec. 3.3: Adam, learning rate 1e-5).  For every
+ * camera: g_xi = Jl(xi)^T g_tangent with the closed-form SE(3) left
+ * Jacobian; if hp is not NULL, one Adam step on xi with g_xi (moments m,
+ * v); then Rt_out = Exp(xi) T0.  Computed in double per camera.
+ * T0, Rt_out: [V,12]; xi, g_xi (may be NULL), m, v: [V,6] float;
+ * g_tangent: [V,6] double.
+ */
+gs_status pose_se3_update(int32_t n_cams, const float* T0, float* xi,
+                          const double* g_tangent, float* g_xi, float* m,
+                          float* v, const gs_adam* hp, float* Rt_out,
+                          gs_stream stream);
+
+/* gs_adam_update — one Adam step on n floats p with gradient g and
+ * moments m, v (Kingma & Ba, bias-corrected with t = *hp->step). */
+gs_status gs_adam_update(float* p, const float* g, float* m, float* v,
+                         int64_t n, const gs_adam* hp, gs_stream stream);
+
+/* gs_step_advance — *step += 1 on the device. */
+gs_status gs_step_advance(int32_t* step, gs_stream stream);
+
+/* gs_zero — set `bytes` bytes at ptr to zero on the stream. */
+gs_status gs_zero(void* ptr, size_t bytes, gs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

@@ -99,8 +99,8 @@ def _L():
         lib.orc_project.argtypes = [vp, vp, vp]
         lib.orc_render.argtypes = [vp, vp, vp, i64, vp, dbl, vp, vp, vp, vp, vp, vp]
         lib.orc_render_tiled.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp]
-        lib.orc_render_bwd.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
-        lib.orc_track.argtypes = [i32, vp, i64, vp, vp, vp, i32, vp, dbl, dbl, vp, vp, vp, vp]
+        lib.orc_render_bwd.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.orc_track.argtypes = [i32, vp, i64, vp, vp, vp, i32, vp, dbl, dbl, vp, vp, vp, vp, vp]
         lib.orc_se3_exp.argtypes = [vp, vp]
         lib.orc_se3_log.argtypes = [vp, vp]
         lib.orc_se3_left_jacobian.argtypes = [vp, vp]
@@ -225,7 +225,8 @@ def render_tiled(scene: Scene, cam: Camera, tile: int, bg=(0.0, 0.0, 0.0)):
 
 def render_bwd(scene: Scene, cam: Camera, v_image, bg=(0.0, 0.0, 0.0), pixels=None):
     """Gradients of sum(v_image * image) w.r.t. all raw parameters and the
-    camera's left-perturbation pose tangent (6)."""
+    camera's left-perturbation pose tangent (6); tangent_abs is the sum of
+    the absolute per-Gaussian tangent contributions."""
     bg = _f64(bg)
     v = _f64(v_image)
     if pixels is None:
@@ -237,11 +238,11 @@ def render_bwd(scene: Scene, cam: Camera, v_image, bg=(0.0, 0.0, 0.0), pixels=No
     n, K = scene.n, scene.sh.shape[1]
     g = dict(mean=np.zeros((n, 3)), log_scale=np.zeros((n, 3)), quat=np.zeros((n, 4)),
              opacity_logit=np.zeros(n), sh=np.zeros((n, K, 3)), tangent=np.zeros(6),
-             v2d=np.zeros((n, 9)))
+             tangent_abs=np.zeros(6), v2d=np.zeros((n, 9)))
     _L().orc_render_bwd(scene.c, ctypes.byref(cam), _ptr(bg), npix, _ptr(pix), _ptr(v),
                         _ptr(g["mean"]), _ptr(g["log_scale"]), _ptr(g["quat"]),
                         _ptr(g["opacity_logit"]), _ptr(g["sh"]), _ptr(g["tangent"]),
-                        _ptr(g["v2d"]))
+                        _ptr(g["tangent_abs"]), _ptr(g["v2d"]))
     return g
 
 
@@ -255,9 +256,10 @@ def l1_loss_grad(image, target, weight=1.0):
     return weight * np.abs(d).sum() / n, weight * np.sign(d) / n
 
 
-def track(X, obs_point, obs_cam, obs_xy, cams, delta=1.0, weight=1.0):
+def track(X, obs_point, obs_cam, obs_xy, cams, delta=1.0, weight=1.0, with_abs=False):
     """Eq. 6 over the given observations.  Returns (sum rho, grad_X of
-    weight*sum rho, pose tangents [n_cams,6], n_masked)."""
+    weight*sum rho, pose tangents [n_cams,6], n_masked) and, with_abs, the
+    per-camera sums of absolute tangent contributions."""
     X = _f64(X).reshape(-1, 3)
     op, oc = _i32(obs_point), _i32(obs_cam)
     xy = _f64(obs_xy).reshape(-1, 2)
@@ -266,11 +268,14 @@ def track(X, obs_point, obs_cam, obs_xy, cams, delta=1.0, weight=1.0):
     masked = ctypes.c_int64(0)
     gX = np.zeros_like(X)
     tan = np.zeros((len(cams), 6))
+    tabs = np.zeros((len(cams), 6))
     r = _L().orc_track(X.shape[0], _ptr(X), op.shape[0], _ptr(op), _ptr(oc), _ptr(xy),
                        len(cams), arr, float(delta), float(weight), ctypes.byref(loss),
-                       _ptr(gX), _ptr(tan), ctypes.byref(masked))
+                       _ptr(gX), _ptr(tan), _ptr(tabs), ctypes.byref(masked))
     if r != 0:
         raise ValueError("observation index out of range")
+    if with_abs:
+        return loss.value, gX, tan, masked.value, tabs
     return loss.value, gX, tan, masked.value
 
 

@@ -661,13 +661,15 @@ static void tangent_from_GW(const orc_camera* cam, const double* GW,
  * S_k the colour composited behind k (incl. T_final bg); then through
  * alpha = o exp(-q/2) (zero above the 0.99 clamp) and project_bwd.
  * All outputs accumulate (+=).  v2d, if not NULL, receives the per-Gaussian
- * screen-space gradients [n][9] (accumulated).
+ * screen-space gradients [n][9] (accumulated); v_tangent_abs, if not NULL,
+ * the sum over Gaussians of the absolute value of each one's pose-tangent
+ * contribution (the scale of the cancelling pose sum).
  */
 int orc_render_bwd(const orc_scene* sc, const orc_camera* cam,
                    const double bg[3], int64_t npix, const int32_t* pix,
                    const double* v_image, double* v_mean, double* v_log_scale,
                    double* v_quat, double* v_opacity_logit, double* v_sh,
-                   double* v_tangent, double* v2d_out) {
+                   double* v_tangent, double* v_tangent_abs, double* v2d_out) {
   proj_state* st;
   int* order;
   const int nv = visible_order(sc, cam, &st, &order);
@@ -717,8 +719,16 @@ int orc_render_bwd(const orc_scene* sc, const orc_camera* cam,
     int nz = 0;
     for (int i = 0; i < 9; ++i) nz |= (g[i] != 0.0);
     if (!nz) continue;
+    double GWj[9] = {0}, vtj[3] = {0};
     project_bwd(sc, j, cam, &st[j], g, v_mean, v_log_scale, v_quat,
-                v_opacity_logit, v_sh, GW, vt);
+                v_opacity_logit, v_sh, GWj, vtj);
+    for (int i = 0; i < 9; ++i) GW[i] += GWj[i];
+    for (int i = 0; i < 3; ++i) vt[i] += vtj[i];
+    if (v_tangent_abs) {
+      double gj[6];
+      tangent_from_GW(cam, GWj, vtj, gj);
+      for (int i = 0; i < 6; ++i) v_tangent_abs[i] += fabs(gj[i]);
+    }
   }
   if (v_tangent) {
     double gt[6];
@@ -743,12 +753,15 @@ int orc_render_bwd(const orc_scene* sc, const orc_camera* cam,
  * s = |r|^2; rho(s) = s if s <= delta^2 else 2 delta sqrt(s) - delta^2.
  * loss += rho (unweighted, Eq. 6); gradients are those of weight * rho and
  * accumulate into grad_X [n_points][3] and the pose tangents [n_cams][6].
+ * tangent_abs (may be NULL) accumulates the absolute value of every
+ * observation's tangent contribution: the scale against which the
+ * cancelling pose sum is compared.
  */
 int orc_track(int32_t n_points, const double* X, int64_t n_obs,
               const int32_t* obs_point, const int32_t* obs_cam,
               const double* obs_xy, int32_t n_cams, const orc_camera* cams,
               double delta, double weight, double* loss, double* grad_X,
-              double* tangent, int64_t* n_masked) {
+              double* tangent, double* tangent_abs, int64_t* n_masked) {
   double L = 0.0;
   int64_t masked = 0;
   for (int64_t o = 0; o < n_obs; ++o) {
@@ -782,6 +795,10 @@ int orc_track(int32_t n_points, const double* X, int64_t n_obs,
     for (int a = 0; a < 3; ++a) {
       tangent[6 * i + a] += vXc[a];
       tangent[6 * i + 3 + a] += cr[a];
+      if (tangent_abs) {
+        tangent_abs[6 * i + a] += fabs(vXc[a]);
+        tangent_abs[6 * i + 3 + a] += fabs(cr[a]);
+      }
     }
   }
   if (loss) *loss += L;

@@ -86,12 +86,12 @@ int orc_render_bwd(const orc_scene* s, const orc_camera* cam,
                    const double bg[3], int64_t npix, const int32_t* pix,
                    const double* v_image, double* v_mean, double* v_log_scale,
                    double* v_quat, double* v_opacity_logit, double* v_sh,
-                   double* v_tangent, double* v2d);
+                   double* v_tangent, double* v_tangent_abs, double* v2d);
 int orc_track(int32_t n_points, const double* X, int64_t n_obs,
               const int32_t* obs_point, const int32_t* obs_cam,
               const double* obs_xy, int32_t n_cams, const orc_camera* cams,
               double delta, double weight, double* loss, double* grad_X,
-              double* tangent, int64_t* n_masked);
+              double* tangent, double* tangent_abs, int64_t* n_masked);
 void orc_se3_exp(const double xi[6], double T[12]);
 void orc_se3_log(const double T[12], double xi[6]);
 void orc_se3_left_jacobian(const double xi[6], double J[36]);

@@ -1,0 +1,302 @@
+"""Tensor containers and thin wrappers over the C ABI, one per entry point,
+with the entry points' names.  PyTorch supplies device memory and streams;
+every computation runs in libgs kernels."""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+
+TILE = 16
+
+
+def _p(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and (not t.is_cuda or not t.is_contiguous()):
+            raise ValueError("libgs arguments must be contiguous CUDA tensors")
+
+
+@dataclass
+class Gaussians:
+    """Raw Gaussian parameters (float32, CUDA): mean [N,3], log_scale [N,3],
+    quat [N,4] (w,x,y,z), opacity_logit [N], sh [N,K,3]."""
+    mean: torch.Tensor
+    log_scale: torch.Tensor
+    quat: torch.Tensor
+    opacity_logit: torch.Tensor
+    sh: torch.Tensor
+
+    @property
+    def n(self):
+        return self.mean.shape[0]
+
+    @property
+    def sh_degree(self):
+        return int(round(self.sh.shape[1] ** 0.5)) - 1
+
+    def tensors(self):
+        return [self.mean, self.log_scale, self.quat, self.opacity_logit, self.sh]
+
+    def c(self):
+        _need_cuda(*self.tensors())
+        return _lib.gs_gaussians(self.n, self.sh_degree, self.mean.data_ptr(), self.log_scale.data_ptr(),
+                                 self.quat.data_ptr(), self.opacity_logit.data_ptr(), self.sh.data_ptr())
+
+    def grads_c(self):
+        _need_cuda(*self.tensors())
+        return _lib.gs_gaussian_grads(self.mean.data_ptr(), self.log_scale.data_ptr(), self.quat.data_ptr(),
+                                      self.opacity_logit.data_ptr(), self.sh.data_ptr())
+
+    @staticmethod
+    def zeros_like(g: "Gaussians") -> "Gaussians":
+        return Gaussians(*[torch.zeros_like(t) for t in g.tensors()])
+
+    @staticmethod
+    def from_numpy(d: dict, device="cuda") -> "Gaussians":
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=device).contiguous()
+        return Gaussians(f(d["mean"]), f(d["log_scale"]), f(d["quat"]), f(d["opacity_logit"]).reshape(-1),
+                         f(d["sh"]))
+
+
+@dataclass
+class Cameras:
+    """All cameras: wh [V,2] int32, K [V,4] (fx,fy,cx,cy), Rt [V,12]
+    world-to-camera (R row-major, t)."""
+    wh: torch.Tensor
+    K: torch.Tensor
+    Rt: torch.Tensor
+    near: float = 0.01
+    far: float = 1e10
+    wh_host: np.ndarray = None
+
+    def __post_init__(self):
+        if self.wh_host is None:
+            self.wh_host = self.wh.detach().cpu().numpy().astype(np.int64)
+
+    @property
+    def V(self):
+        return self.wh.shape[0]
+
+    def c(self, Rt: torch.Tensor = None):
+        Rt = self.Rt if Rt is None else Rt
+        _need_cuda(self.wh, self.K, Rt)
+        return _lib.gs_cameras(self.V, self.wh.data_ptr(), self.K.data_ptr(), Rt.data_ptr(),
+                               float(self.near), float(self.far))
+
+    @staticmethod
+    def from_numpy(wh, K, Rt, near=0.01, far=1e10, device="cuda") -> "Cameras":
+        return Cameras(torch.as_tensor(np.asarray(wh), dtype=torch.int32, device=device).contiguous(),
+                       torch.as_tensor(np.asarray(K), dtype=torch.float32, device=device).contiguous(),
+                       torch.as_tensor(np.asarray(Rt), dtype=torch.float32, device=device).contiguous(),
+                       near, far, np.asarray(wh).astype(np.int64))
+
+
+class Batch:
+    """A batch of views rendered together; per-slot images packed in slot
+    order (pixel offsets) and tiles numbered globally (tile offsets)."""
+
+    def __init__(self, cams: Cameras, views, tile: int = TILE, device="cuda"):
+        views = np.asarray(views, dtype=np.int64).reshape(-1)
+        if not 1 <= len(views) <= _lib.GS_MAX_BATCH:
+            raise ValueError("batch size must be 1..%d" % _lib.GS_MAX_BATCH)
+        wh = cams.wh_host[views]
+        self.views_host = views
+        self.W = wh[:, 0].copy()
+        self.H = wh[:, 1].copy()
+        px = np.zeros(len(views) + 1, dtype=np.int64)
+        px[1:] = np.cumsum(self.W * self.H)
+        tx = (self.W + tile - 1) // tile
+        ty = (self.H + tile - 1) // tile
+        to = np.zeros(len(views) + 1, dtype=np.int64)
+        to[1:] = np.cumsum(tx * ty)
+        self.px_offset_host = px
+        self.tile_offset_host = to
+        self.tile = tile
+        self.B = len(views)
+        self.n_pixels = int(px[-1])
+        self.n_tiles = int(to[-1])
+        self.views = torch.as_tensor(views.astype(np.int32), device=device)
+        self.px_offset = torch.as_tensor(px, device=device)
+        self.tile_offset = torch.as_tensor(to.astype(np.int32), device=device)
+
+    def c(self):
+        return _lib.gs_batch(self.B, self.tile, self.views.data_ptr(), self.px_offset.data_ptr(),
+                             self.tile_offset.data_ptr(), self.n_pixels, self.n_tiles, 0)
+
+    def slot_image(self, buf: torch.Tensor, b: int) -> torch.Tensor:
+        """View of slot b of a packed per-pixel buffer as [H, W, ...]."""
+        a, e = int(self.px_offset_host[b]), int(self.px_offset_host[b + 1])
+        return buf[a:e].reshape(int(self.H[b]), int(self.W[b]), *buf.shape[1:])
+
+
+class Projected:
+    """Per-(slot, Gaussian) records: splat [B*N,12] f32, rect [B*N,4] u16,
+    n_tiles [B*N] u32 (int16/int32 storage)."""
+
+    def __init__(self, n: int, B: int, device="cuda"):
+        M = n * B
+        self.splat = torch.empty((max(M, 1), 12), dtype=torch.float32, device=device)
+        self.rect = torch.empty((max(M, 1), 4), dtype=torch.int16, device=device)
+        self.n_tiles = torch.zeros((max(M, 1),), dtype=torch.int32, device=device)
+
+    def c(self):
+        return _lib.gs_projected(self.splat.data_ptr(), self.rect.data_ptr(), self.n_tiles.data_ptr())
+
+
+class TileLists:
+    """Sorted tile instances: keys [cap] u64, vals [cap] u32, ranges
+    [2*n_tiles] u32, n_instances [1] u32, sort workspace."""
+
+    def __init__(self, n: int, batch: Batch, capacity: int, device="cuda"):
+        lib = _lib.load()
+        self.capacity = int(capacity)
+        self.keys = torch.empty(self.capacity, dtype=torch.int64, device=device)
+        self.vals = torch.empty(self.capacity, dtype=torch.int32, device=device)
+        self.ranges = torch.zeros(max(2 * batch.n_tiles, 2), dtype=torch.int32, device=device)
+        self.n_instances = torch.zeros(1, dtype=torch.int32, device=device)
+        ws = ctypes.c_size_t(0)
+        bc = batch.c()
+        check(lib.gs_sort_tiles_workspace(n, ctypes.byref(bc), self.capacity, ctypes.byref(ws)),
+              "gs_sort_tiles_workspace")
+        self.ws = torch.empty(max(ws.value, 256), dtype=torch.uint8, device=device)
+
+
+def new_status(device="cuda"):
+    return torch.zeros(1, dtype=torch.int32, device=device)
+
+
+# ---------------------------------------------------------------------------
+# thin wrappers, same names as the C entry points
+
+
+def gs_project(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, status: torch.Tensor,
+               Rt: torch.Tensor = None, stream=None):
+    lib = _lib.load()
+    gc, cc, bc, pc = g.c(), cams.c(Rt), batch.c(), proj.c()
+    check(lib.gs_project(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc),
+                         _p(status), _stream(stream)), "gs_project")
+
+
+def gs_sort_tiles(n: int, cams: Cameras, batch: Batch, proj: Projected, tl: TileLists, status: torch.Tensor,
+                  Rt: torch.Tensor = None, stream=None):
+    lib = _lib.load()
+    cc, bc, pc = cams.c(Rt), batch.c(), proj.c()
+    check(lib.gs_sort_tiles(n, ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc), _p(tl.keys), _p(tl.vals),
+                            tl.capacity, _p(tl.ranges), _p(tl.n_instances), _p(tl.ws), tl.ws.numel(),
+                            _p(status), _stream(stream)), "gs_sort_tiles")
+
+
+def gs_render_fwd(batch: Batch, cams: Cameras, proj: Projected, tl: TileLists, bg: torch.Tensor,
+                  image: torch.Tensor, T_final: torch.Tensor, n_contrib: torch.Tensor, Rt=None, stream=None):
+    lib = _lib.load()
+    _need_cuda(bg, image, T_final, n_contrib)
+    cc, bc, pc = cams.c(Rt), batch.c(), proj.c()
+    check(lib.gs_render_fwd(ctypes.byref(bc), ctypes.byref(cc), ctypes.byref(pc), _p(tl.vals), _p(tl.ranges),
+                            _p(bg), _p(image), _p(T_final), _p(n_contrib), _stream(stream)), "gs_render_fwd")
+
+
+def render_bwd_workspace_bytes(n: int, batch: Batch) -> int:
+    lib = _lib.load()
+    ws = ctypes.c_size_t(0)
+    bc = batch.c()
+    check(lib.gs_render_bwd_workspace(n, ctypes.byref(bc), ctypes.byref(ws)), "gs_render_bwd_workspace")
+    return ws.value
+
+
+def gs_render_bwd(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, tl: TileLists,
+                  bg: torch.Tensor, image, T_final, n_contrib, v_image, target, l1_weight: float,
+                  loss, dg: Gaussians, g_pose_tangent: torch.Tensor, ws: torch.Tensor, Rt=None, stream=None):
+    lib = _lib.load()
+    _need_cuda(bg, T_final, n_contrib, g_pose_tangent, ws, image, v_image, target, loss)
+    gc, cc, bc, pc, dgc = g.c(), cams.c(Rt), batch.c(), proj.c(), dg.grads_c()
+    check(lib.gs_render_bwd(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc),
+                            _p(tl.vals), _p(tl.ranges), _p(bg), _p(image), _p(T_final), _p(n_contrib),
+                            _p(v_image), _p(target), float(l1_weight), _p(loss), ctypes.byref(dgc),
+                            _p(g_pose_tangent), _p(ws), ws.numel(), _stream(stream)), "gs_render_bwd")
+
+
+def gs_raster_bwd(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, tl: TileLists, bg, image,
+                  T_final, n_contrib, v_image, target, l1_weight: float, loss, ws: torch.Tensor, Rt=None,
+                  stream=None):
+    lib = _lib.load()
+    _need_cuda(bg, T_final, n_contrib, ws, image, v_image, target, loss)
+    gc, cc, bc, pc = g.c(), cams.c(Rt), batch.c(), proj.c()
+    check(lib.gs_raster_bwd(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc),
+                            _p(tl.vals), _p(tl.ranges), _p(bg), _p(image), _p(T_final), _p(n_contrib),
+                            _p(v_image), _p(target), float(l1_weight), _p(loss), _p(ws), ws.numel(),
+                            _stream(stream)), "gs_raster_bwd")
+
+
+def gs_project_bwd(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, dg: Gaussians,
+                   g_pose_tangent: torch.Tensor, ws: torch.Tensor, Rt=None, stream=None):
+    lib = _lib.load()
+    _need_cuda(g_pose_tangent, ws)
+    gc, cc, bc, pc, dgc = g.c(), cams.c(Rt), batch.c(), proj.c(), dg.grads_c()
+    check(lib.gs_project_bwd(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc),
+                             ctypes.byref(dgc), _p(g_pose_tangent), _p(ws), ws.numel(), _stream(stream)),
+          "gs_project_bwd")
+
+
+def track_workspace_bytes(batch: Batch) -> int:
+    lib = _lib.load()
+    ws = ctypes.c_size_t(0)
+    bc = batch.c()
+    check(lib.track_reproj_workspace(ctypes.byref(bc), ctypes.byref(ws)), "track_reproj_workspace")
+    return ws.value
+
+
+def track_reproj_fwd_bwd(X, obs_point, obs_xy, view_obs_offset, cams: Cameras, batch: Batch, delta: float,
+                         weight: float, loss, grad_X, g_pose_tangent, n_masked, ws, Rt=None, stream=None):
+    lib = _lib.load()
+    _need_cuda(X, obs_point, obs_xy, view_obs_offset, loss, grad_X, g_pose_tangent, n_masked, ws)
+    cc, bc = cams.c(Rt), batch.c()
+    check(lib.track_reproj_fwd_bwd(_p(X), X.shape[0], _p(obs_point), _p(obs_xy), _p(view_obs_offset),
+                                   ctypes.byref(cc), ctypes.byref(bc), float(delta), float(weight), _p(loss),
+                                   _p(grad_X), _p(g_pose_tangent), _p(n_masked), _p(ws), ws.numel(),
+                                   _stream(stream)), "track_reproj_fwd_bwd")
+
+
+def adam_c(lr, beta1, beta2, eps, step: torch.Tensor):
+    return _lib.gs_adam(float(lr), float(beta1), float(beta2), float(eps), step.data_ptr())
+
+
+def pose_se3_update(T0, xi, g_tangent, g_xi, m, v, hp, Rt_out, stream=None):
+    """hp: gs_adam struct or None (gradient map and recomposition only)."""
+    lib = _lib.load()
+    _need_cuda(T0, xi, g_tangent, g_xi, m, v, Rt_out)
+    check(lib.pose_se3_update(T0.shape[0], _p(T0), _p(xi), _p(g_tangent), _p(g_xi), _p(m), _p(v),
+                              None if hp is None else ctypes.byref(hp), _p(Rt_out), _stream(stream)),
+          "pose_se3_update")
+
+
+def gs_adam_update(p, g, m, v, hp, stream=None):
+    lib = _lib.load()
+    _need_cuda(p, g, m, v)
+    check(lib.gs_adam_update(_p(p), _p(g), _p(m), _p(v), p.numel(), ctypes.byref(hp), _stream(stream)),
+          "gs_adam_update")
+
+
+def gs_step_advance(step, stream=None):
+    lib = _lib.load()
+    _need_cuda(step)
+    check(lib.gs_step_advance(_p(step), _stream(stream)), "gs_step_advance")
+
+
+def gs_zero(t: torch.Tensor, stream=None):
+    lib = _lib.load()
+    _need_cuda(t)
+    check(lib.gs_zero(_p(t), t.numel() * t.element_size(), _stream(stream)), "gs_zero")

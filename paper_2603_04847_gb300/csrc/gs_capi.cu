@@ -1,0 +1,316 @@
+// C ABI of libgs: argument validation, workspace carving and launches.
+// Nothing here allocates device memory and nothing throws across the ABI.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "gs_internal.h"
+
+namespace gs {
+
+namespace {
+thread_local char g_err[512] = "";
+
+gs_status fail(gs_status code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+gs_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(GS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+gs_status check_gaussians(const gs_gaussians* g) {
+  if (!g) return fail(GS_ERR_ARG, "gaussians: null");
+  if (g->n < 0) return fail(GS_ERR_ARG, "gaussians: n < 0");
+  if (g->sh_degree < 0 || g->sh_degree > 3) return fail(GS_ERR_ARG, "gaussians: sh_degree must be 0..3");
+  if (g->n > 0 && (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->sh))
+    return fail(GS_ERR_ARG, "gaussians: null array");
+  if (!aligned(g->quat, 16)) return fail(GS_ERR_ARG, "gaussians: quat must be 16-byte aligned");
+  return GS_OK;
+}
+
+gs_status check_cameras(const gs_cameras* c) {
+  if (!c) return fail(GS_ERR_ARG, "cameras: null");
+  if (c->n_cams < 1) return fail(GS_ERR_ARG, "cameras: n_cams < 1");
+  if (!c->wh || !c->K || !c->Rt) return fail(GS_ERR_ARG, "cameras: null array");
+  if (!std::isfinite(c->near_plane) || !std::isfinite(c->far_plane))
+    return fail(GS_ERR_NONFINITE, "cameras: non-finite near/far");
+  if (!(c->near_plane > 0.f) || !(c->far_plane > c->near_plane))
+    return fail(GS_ERR_ARG, "cameras: need 0 < near < far");
+  return GS_OK;
+}
+
+gs_status check_batch(const gs_batch* b) {
+  if (!b) return fail(GS_ERR_ARG, "batch: null");
+  if (b->B < 1 || b->B > GS_MAX_BATCH) return fail(GS_ERR_ARG, "batch: B must be 1..%d", GS_MAX_BATCH);
+  if (b->tile != 16) return fail(GS_ERR_UNSUPPORTED, "batch: tile %d unsupported (16)", b->tile);
+  if (!b->views || !b->px_offset || !b->tile_offset) return fail(GS_ERR_ARG, "batch: null array");
+  if (b->n_pixels < 0 || b->n_tiles < 0) return fail(GS_ERR_ARG, "batch: negative sizes");
+  return GS_OK;
+}
+
+gs_status check_projected(const gs_projected* p) {
+  if (!p) return fail(GS_ERR_ARG, "projected: null");
+  if (!p->splat || !p->rect || !p->n_tiles) return fail(GS_ERR_ARG, "projected: null array");
+  if (!aligned(p->splat, 16) || !aligned(p->rect, 8))
+    return fail(GS_ERR_ARG, "projected: splat must be 16-byte and rect 8-byte aligned");
+  return GS_OK;
+}
+
+inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t v2d_bytes(int N, const gs_batch& b) { return align_up((size_t)b.B * N * 12 * sizeof(float)); }
+size_t pose_partial_bytes(int N, const gs_batch& b) {
+  return align_up((size_t)project_bwd_blocks(N) * b.B * 6 * sizeof(double));
+}
+
+}  // namespace
+
+int device_sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 148;
+  if (dev < 64 && cache[dev] > 0) return cache[dev];
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+    sms = 148;
+  if (dev < 64) cache[dev] = sms;
+  return sms;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+int gs_abi_version(void) { return GS_ABI_VERSION; }
+
+const char* gs_last_error(void) { return g_err; }
+
+size_t gs_struct_size(int which) {
+  switch (which) {
+    case 0: return sizeof(gs_gaussians);
+    case 1: return sizeof(gs_gaussian_grads);
+    case 2: return sizeof(gs_cameras);
+    case 3: return sizeof(gs_batch);
+    case 4: return sizeof(gs_projected);
+    case 5: return sizeof(gs_adam);
+    default: return 0;
+  }
+}
+
+int gs_device_sm_count(void) { return device_sm_count(); }
+
+gs_status gs_project(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
+                     const gs_projected* out, int32_t* status, gs_stream stream) {
+  gs_status s;
+  if ((s = check_gaussians(g)) || (s = check_cameras(cams)) || (s = check_batch(batch)) ||
+      (s = check_projected(out)))
+    return s;
+  if ((unsigned long long)batch->B * (unsigned long long)g->n >= 0xffffffffull)
+    return fail(GS_ERR_ARG, "gs_project: B*N must be < 2^32");
+  cudaError_t e = launch_project_fwd(*g, *cams, *batch, *out, status, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_project");
+  return GS_OK;
+}
+
+gs_status gs_sort_tiles_workspace(int32_t n_gaussians, const gs_batch* batch, size_t capacity,
+                                  size_t* ws_bytes) {
+  gs_status s;
+  if ((s = check_batch(batch))) return s;
+  if (!ws_bytes || n_gaussians < 0) return fail(GS_ERR_ARG, "gs_sort_tiles_workspace: bad argument");
+  *ws_bytes = sort_workspace_bytes(n_gaussians, *batch, capacity);
+  return GS_OK;
+}
+
+gs_status gs_sort_tiles(int32_t n_gaussians, const gs_cameras* cams, const gs_batch* batch,
+                        const gs_projected* proj, uint64_t* keys, uint32_t* vals, size_t capacity,
+                        uint32_t* ranges, uint32_t* n_instances, void* ws, size_t ws_bytes,
+                        int32_t* status, gs_stream stream) {
+  gs_status s;
+  if ((s = check_cameras(cams)) || (s = check_batch(batch)) || (s = check_projected(proj))) return s;
+  if (n_gaussians < 0 || !keys || !vals || !ranges || !n_instances || !ws)
+    return fail(GS_ERR_ARG, "gs_sort_tiles: null argument");
+  if (capacity == 0 || capacity >= 0xffffffffull)
+    return fail(GS_ERR_CAPACITY, "gs_sort_tiles: capacity must be in [1, 2^32 - 1)");
+  if (!aligned(keys, 8) || !aligned(ws, 256)) return fail(GS_ERR_ARG, "gs_sort_tiles: misaligned buffer");
+  const size_t need = sort_workspace_bytes(n_gaussians, *batch, capacity);
+  if (ws_bytes < need) return fail(GS_ERR_ARG, "gs_sort_tiles: workspace %zu < %zu bytes", ws_bytes, need);
+  cudaError_t e = launch_sort_tiles(n_gaussians, *cams, *batch, *proj, keys, vals, capacity, ranges,
+                                    n_instances, ws, status, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_sort_tiles");
+  return GS_OK;
+}
+
+gs_status gs_render_fwd(const gs_batch* batch, const gs_cameras* cams, const gs_projected* proj,
+                        const uint32_t* vals, const uint32_t* ranges, const float* bg, float* image,
+                        float* T_final, uint32_t* n_contrib, gs_stream stream) {
+  gs_status s;
+  if ((s = check_batch(batch)) || (s = check_cameras(cams)) || (s = check_projected(proj))) return s;
+  if (!vals || !ranges || !bg || !image || !T_final || !n_contrib)
+    return fail(GS_ERR_ARG, "gs_render_fwd: null argument");
+  cudaError_t e = launch_render_fwd(*batch, *cams, *proj, vals, ranges, bg, image, T_final, n_contrib,
+                                    (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_render_fwd");
+  return GS_OK;
+}
+
+gs_status gs_render_bwd_workspace(int32_t n_gaussians, const gs_batch* batch, size_t* ws_bytes) {
+  gs_status s;
+  if ((s = check_batch(batch))) return s;
+  if (!ws_bytes || n_gaussians < 0) return fail(GS_ERR_ARG, "gs_render_bwd_workspace: bad argument");
+  *ws_bytes = v2d_bytes(n_gaussians, *batch) + pose_partial_bytes(n_gaussians, *batch);
+  return GS_OK;
+}
+
+namespace {
+gs_status check_bwd_common(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
+                           const gs_projected* proj, void* ws, size_t ws_bytes, const char* who) {
+  gs_status s;
+  if ((s = check_gaussians(g)) || (s = check_cameras(cams)) || (s = check_batch(batch)) ||
+      (s = check_projected(proj)))
+    return s;
+  if (!ws) return fail(GS_ERR_ARG, "%s: null workspace", who);
+  if (!aligned(ws, 256)) return fail(GS_ERR_ARG, "%s: ws must be 256-byte aligned", who);
+  const size_t need = v2d_bytes(g->n, *batch) + pose_partial_bytes(g->n, *batch);
+  if (ws_bytes < need) return fail(GS_ERR_ARG, "%s: workspace %zu < %zu bytes", who, ws_bytes, need);
+  return GS_OK;
+}
+}  // namespace
+
+gs_status gs_raster_bwd(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
+                        const gs_projected* proj, const uint32_t* vals, const uint32_t* ranges,
+                        const float* bg, const float* image, const float* T_final,
+                        const uint32_t* n_contrib, const float* v_image, const float* target,
+                        float l1_weight, double* loss, void* ws, size_t ws_bytes, gs_stream stream) {
+  gs_status s;
+  if ((s = check_bwd_common(g, cams, batch, proj, ws, ws_bytes, "gs_raster_bwd"))) return s;
+  if (!vals || !ranges || !bg || !T_final || !n_contrib)
+    return fail(GS_ERR_ARG, "gs_raster_bwd: null argument");
+  if (!v_image && (!target || !image))
+    return fail(GS_ERR_ARG, "gs_raster_bwd: need v_image, or image and target for the fused L1");
+  if (!v_image && !std::isfinite(l1_weight)) return fail(GS_ERR_NONFINITE, "gs_raster_bwd: l1_weight");
+  cudaStream_t st = (cudaStream_t)stream;
+  float* v2d = reinterpret_cast<float*>(ws);
+  cudaError_t e = cudaMemsetAsync(v2d, 0, (size_t)batch->B * g->n * 12 * sizeof(float), st);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_raster_bwd memset");
+  e = launch_render_bwd(*batch, *cams, *proj, vals, ranges, bg, image, T_final, n_contrib, v_image,
+                        target, l1_weight, loss, v2d, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_raster_bwd");
+  return GS_OK;
+}
+
+gs_status gs_project_bwd(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
+                         const gs_projected* proj, const gs_gaussian_grads* dg, double* g_pose_tangent,
+                         void* ws, size_t ws_bytes, gs_stream stream) {
+  gs_status s;
+  if ((s = check_bwd_common(g, cams, batch, proj, ws, ws_bytes, "gs_project_bwd"))) return s;
+  if (!dg || !g_pose_tangent) return fail(GS_ERR_ARG, "gs_project_bwd: null argument");
+  if (!dg->mean || !dg->log_scale || !dg->quat || !dg->opacity_logit || !dg->sh)
+    return fail(GS_ERR_ARG, "gs_project_bwd: null gradient array");
+  if (!aligned(dg->quat, 16)) return fail(GS_ERR_ARG, "gs_project_bwd: grad quat must be 16-byte aligned");
+  const size_t vb = v2d_bytes(g->n, *batch);
+  float* v2d = reinterpret_cast<float*>(ws);
+  double* partial = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + vb);
+  cudaError_t e = launch_project_bwd(*g, *cams, *batch, *proj, v2d, *dg, partial, g_pose_tangent,
+                                     (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_project_bwd");
+  return GS_OK;
+}
+
+gs_status gs_render_bwd(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
+                        const gs_projected* proj, const uint32_t* vals, const uint32_t* ranges,
+                        const float* bg, const float* image, const float* T_final,
+                        const uint32_t* n_contrib, const float* v_image, const float* target,
+                        float l1_weight, double* loss, const gs_gaussian_grads* dg,
+                        double* g_pose_tangent, void* ws, size_t ws_bytes, gs_stream stream) {
+  if (!dg || !g_pose_tangent) return fail(GS_ERR_ARG, "gs_render_bwd: null argument");
+  gs_status s = gs_raster_bwd(g, cams, batch, proj, vals, ranges, bg, image, T_final, n_contrib, v_image,
+                              target, l1_weight, loss, ws, ws_bytes, stream);
+  if (s != GS_OK) return s;
+  return gs_project_bwd(g, cams, batch, proj, dg, g_pose_tangent, ws, ws_bytes, stream);
+}
+
+gs_status track_reproj_workspace(const gs_batch* batch, size_t* ws_bytes) {
+  gs_status s;
+  if ((s = check_batch(batch))) return s;
+  if (!ws_bytes) return fail(GS_ERR_ARG, "track_reproj_workspace: null");
+  *ws_bytes = align_up(track_workspace_bytes(*batch));
+  return GS_OK;
+}
+
+gs_status track_reproj_fwd_bwd(const float* X, int32_t n_points, const int32_t* obs_point,
+                               const float* obs_xy, const int64_t* view_obs_offset,
+                               const gs_cameras* cams, const gs_batch* batch, float delta,
+                               float weight, double* loss, float* grad_X, double* g_pose_tangent,
+                               uint32_t* n_masked, void* ws, size_t ws_bytes, gs_stream stream) {
+  gs_status s;
+  if ((s = check_cameras(cams)) || (s = check_batch(batch))) return s;
+  if (n_points < 0 || !view_obs_offset || !grad_X || !g_pose_tangent || !ws)
+    return fail(GS_ERR_ARG, "track_reproj_fwd_bwd: null argument");
+  if (n_points > 0 && (!X || !obs_point || !obs_xy))
+    return fail(GS_ERR_ARG, "track_reproj_fwd_bwd: null array");
+  if (obs_xy && !aligned(obs_xy, 8)) return fail(GS_ERR_ARG, "track_reproj_fwd_bwd: obs_xy must be 8-byte aligned");
+  if (!std::isfinite(delta) || !std::isfinite(weight))
+    return fail(GS_ERR_NONFINITE, "track_reproj_fwd_bwd: non-finite delta/weight");
+  if (!(delta > 0.f)) return fail(GS_ERR_ARG, "track_reproj_fwd_bwd: delta must be > 0");
+  if (ws_bytes < track_workspace_bytes(*batch))
+    return fail(GS_ERR_ARG, "track_reproj_fwd_bwd: workspace too small");
+  cudaError_t e = launch_track(X, n_points, obs_point, obs_xy, view_obs_offset, *cams, *batch, delta,
+                               weight, loss, grad_X, g_pose_tangent, n_masked, ws, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "track_reproj_fwd_bwd");
+  return GS_OK;
+}
+
+gs_status pose_se3_update(int32_t n_cams, const float* T0, float* xi, const double* g_tangent,
+                          float* g_xi, float* m, float* v, const gs_adam* hp, float* Rt_out,
+                          gs_stream stream) {
+  if (n_cams < 0 || (n_cams > 0 && (!T0 || !xi || !g_tangent || !Rt_out)))
+    return fail(GS_ERR_ARG, "pose_se3_update: null argument");
+  if (hp) {
+    if (!m || !v || !hp->step) return fail(GS_ERR_ARG, "pose_se3_update: Adam needs m, v and step");
+    if (!std::isfinite(hp->lr) || !std::isfinite(hp->beta1) || !std::isfinite(hp->beta2) ||
+        !std::isfinite(hp->eps))
+      return fail(GS_ERR_NONFINITE, "pose_se3_update: non-finite hyperparameter");
+  }
+  cudaError_t e = launch_pose_update(n_cams, T0, xi, g_tangent, g_xi, m, v, hp, Rt_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pose_se3_update");
+  return GS_OK;
+}
+
+gs_status gs_adam_update(float* p, const float* g, float* m, float* v, int64_t n, const gs_adam* hp,
+                         gs_stream stream) {
+  if (n < 0 || !hp || (n > 0 && (!p || !g || !m || !v)) || !hp->step)
+    return fail(GS_ERR_ARG, "gs_adam_update: bad argument");
+  if (!std::isfinite(hp->lr) || !std::isfinite(hp->beta1) || !std::isfinite(hp->beta2) ||
+      !std::isfinite(hp->eps))
+    return fail(GS_ERR_NONFINITE, "gs_adam_update: non-finite hyperparameter");
+  cudaError_t e = launch_adam(p, g, m, v, n, *hp, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_adam_update");
+  return GS_OK;
+}
+
+gs_status gs_step_advance(int32_t* step, gs_stream stream) {
+  if (!step) return fail(GS_ERR_ARG, "gs_step_advance: null");
+  cudaError_t e = launch_step_advance(step, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_step_advance");
+  return GS_OK;
+}
+
+gs_status gs_zero(void* ptr, size_t bytes, gs_stream stream) {
+  if (bytes == 0) return GS_OK;
+  if (!ptr) return fail(GS_ERR_ARG, "gs_zero: null");
+  cudaError_t e = cudaMemsetAsync(ptr, 0, bytes, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_zero");
+  return GS_OK;
+}
+
+}  // extern "C"

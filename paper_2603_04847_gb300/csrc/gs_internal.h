@@ -1,0 +1,57 @@
+// Internal launch interface between the C ABI layer (gs_capi.cu) and the
+// kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <utility>
+
+#include "gs.h"
+#include "gs_common.cuh"
+
+namespace gs {
+
+int device_sm_count();
+
+cudaError_t launch_project_fwd(const gs_gaussians& g, const gs_cameras& cams, const gs_batch& batch,
+                               const gs_projected& out, int32_t* status, cudaStream_t st);
+int project_bwd_blocks(int n);
+cudaError_t launch_project_bwd(const gs_gaussians& g, const gs_cameras& cams, const gs_batch& batch,
+                               const gs_projected& proj, const float* v2d, const gs_gaussian_grads& dg,
+                               double* partial, double* g_pose_tangent, cudaStream_t st);
+
+int sort_key_bits(int n_tiles_total);
+size_t sort_workspace_bytes(int N, const gs_batch& batch, size_t capacity);
+int sort_launch_count(const gs_batch& batch);
+cudaError_t launch_sort_tiles(int N, const gs_cameras& cams, const gs_batch& batch,
+                              const gs_projected& proj, uint64_t* keys, uint32_t* vals,
+                              size_t capacity, uint32_t* ranges, uint32_t* n_instances, void* ws,
+                              int32_t* status, cudaStream_t st);
+
+cudaError_t launch_render_fwd(const gs_batch& batch, const gs_cameras& cams, const gs_projected& proj,
+                              const uint32_t* vals, const uint32_t* ranges, const float* bg,
+                              float* image, float* T_final, uint32_t* n_contrib, cudaStream_t st);
+cudaError_t launch_render_bwd(const gs_batch& batch, const gs_cameras& cams, const gs_projected& proj,
+                              const uint32_t* vals, const uint32_t* ranges, const float* bg,
+                              const float* image, const float* T_final, const uint32_t* n_contrib,
+                              const float* v_image, const float* target, float l1_weight,
+                              double* loss, float* v2d, cudaStream_t st);
+
+int track_blocks();
+size_t track_workspace_bytes(const gs_batch& batch);
+cudaError_t launch_track(const float* X, int n_points, const int32_t* obs_point, const float* obs_xy,
+                         const int64_t* view_obs_offset, const gs_cameras& cams, const gs_batch& batch,
+                         float delta, float weight, double* loss, float* grad_X,
+                         double* g_pose_tangent, uint32_t* n_masked, void* ws, cudaStream_t st);
+
+cudaError_t launch_pose_partials_finalize(const double* partial, int n_blocks, const gs_batch& batch,
+                                          int n_cams, double* g_pose_tangent, cudaStream_t st);
+cudaError_t launch_pose_update(int V, const float* T0, float* xi, const double* g_tangent, float* g_xi,
+                               float* m, float* v, const gs_adam* hp, float* Rt_out, cudaStream_t st);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, const gs_adam& hp,
+                        cudaStream_t st);
+cudaError_t launch_step_advance(int32_t* step, cudaStream_t st);
+
+}  // namespace gs

@@ -1,0 +1,212 @@
+// Pose composition and optimiser steps:
+//  - pose_se3_update: T_i = Exp(xi_i) T_i^(0) (Algorithm 1, "Apply pose
+//    adjustment"), the SE(3) gradient map g_xi = Jl(xi)^T g_tangent with the
+//    closed-form left Jacobian of SE(3) (Barfoot, State Estimation for
+//    Robotics), and an Adam step on xi (Sec. 3.3: Adam, lr 1e-5).  One
+//    thread per camera, double precision.
+//  - Adam on parameter arrays (Algorithm 1, "Update Gaussians" / "Update
+//    track points"), elementwise and HBM-bound.
+//  - the fixed-order sum of per-block pose partials used by the projection
+//    backward and the track term.
+#include "gs_internal.h"
+
+namespace gs {
+
+namespace {
+
+__device__ inline void skew(const double* w, double* S) {
+  S[0] = 0.0;   S[1] = -w[2]; S[2] = w[1];
+  S[3] = w[2];  S[4] = 0.0;   S[5] = -w[0];
+  S[6] = -w[1]; S[7] = w[0];  S[8] = 0.0;
+}
+
+__device__ inline void mm3(const double* A, const double* B, double* C) {
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      C[3 * r + c] = A[3 * r] * B[c] + A[3 * r + 1] * B[3 + c] + A[3 * r + 2] * B[6 + c];
+}
+
+// sin(th)/th, (1-cos th)/th^2, (th - sin th)/th^3 with series near 0.
+__device__ inline void so3_series(double th, double& A, double& B, double& C) {
+  if (th < 1e-4) {
+    const double t2 = th * th;
+    A = 1.0 - t2 / 6.0 + t2 * t2 / 120.0;
+    B = 0.5 - t2 / 24.0 + t2 * t2 / 720.0;
+    C = 1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0;
+  } else {
+    const double s = sin(th), c = cos(th);
+    A = s / th;
+    B = (1.0 - c) / (th * th);
+    C = (th - s) / (th * th * th);
+  }
+}
+
+__global__ void pose_update_kernel(int V, const float* __restrict__ T0, float* __restrict__ xi,
+                                   const double* __restrict__ g_tangent, float* __restrict__ g_xi,
+                                   float* __restrict__ m, float* __restrict__ v, int use_adam,
+                                   float lr, float beta1, float beta2, float eps,
+                                   const int32_t* __restrict__ step, float* __restrict__ Rt_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  double x[6];
+  for (int c = 0; c < 6; ++c) x[c] = (double)xi[6 * i + c];
+  const double* rho = x;
+  const double* phi = x + 3;
+  const double th = sqrt(phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2]);
+  double A, B, C;
+  so3_series(th, A, B, C);
+  // Q-block coefficients of the SE(3) left Jacobian
+  double c1, c2, c3;
+  if (th < 1e-3) {
+    const double t2 = th * th;
+    c1 = 1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0;
+    c2 = 1.0 / 24.0 - t2 / 720.0 + t2 * t2 / 40320.0;
+    c3 = 1.0 / 120.0 - t2 / 2520.0;
+  } else {
+    const double s = sin(th), c = cos(th), t2 = th * th;
+    c1 = (th - s) / (t2 * th);
+    c2 = (t2 + 2.0 * c - 2.0) / (2.0 * t2 * t2);
+    c3 = (2.0 * th - 3.0 * s + th * c) / (2.0 * t2 * t2 * th);
+  }
+  double P[9], Rh[9], P2[9];
+  skew(phi, P);
+  skew(rho, Rh);
+  mm3(P, P, P2);
+  double Jl[9];
+  for (int k = 0; k < 9; ++k) Jl[k] = ((k % 4) == 0 ? 1.0 : 0.0) + B * P[k] + C * P2[k];
+  double PR[9], RP[9], PRP[9], PPR[9], RPP[9], PRPP[9], PPRP[9], Q[9];
+  mm3(P, Rh, PR);
+  mm3(Rh, P, RP);
+  mm3(PR, P, PRP);
+  mm3(P, PR, PPR);
+  mm3(RP, P, RPP);
+  mm3(PRP, P, PRPP);
+  mm3(P, PRP, PPRP);
+  for (int k = 0; k < 9; ++k)
+    Q[k] = 0.5 * Rh[k] + c1 * (PR[k] + RP[k] + PRP[k]) + c2 * (PPR[k] + RPP[k] - 3.0 * PRP[k]) +
+           c3 * (PRPP[k] + PPRP[k]);
+  // g_xi = Jl^T g with Jl = [[Jl, Q], [0, Jl]]
+  const double* g = g_tangent + 6 * i;
+  double gx[6];
+  for (int c = 0; c < 3; ++c) {
+    gx[c] = Jl[c] * g[0] + Jl[3 + c] * g[1] + Jl[6 + c] * g[2];
+    gx[3 + c] = Q[c] * g[0] + Q[3 + c] * g[1] + Q[6 + c] * g[2] + Jl[c] * g[3] + Jl[3 + c] * g[4] +
+                Jl[6 + c] * g[5];
+  }
+  if (g_xi)
+    for (int c = 0; c < 6; ++c) g_xi[6 * i + c] = (float)gx[c];
+  if (use_adam) {
+    const int t = *step;
+    const double bc1 = 1.0 - pow((double)beta1, (double)t);
+    const double bc2 = 1.0 - pow((double)beta2, (double)t);
+    for (int c = 0; c < 6; ++c) {
+      const double mm = (double)beta1 * m[6 * i + c] + (1.0 - (double)beta1) * gx[c];
+      const double vv = (double)beta2 * v[6 * i + c] + (1.0 - (double)beta2) * gx[c] * gx[c];
+      m[6 * i + c] = (float)mm;
+      v[6 * i + c] = (float)vv;
+      const double upd = (double)lr * (mm / bc1) / (sqrt(vv / bc2) + (double)eps);
+      const float nx = (float)(x[c] - upd);
+      xi[6 * i + c] = nx;
+      x[c] = (double)nx;
+    }
+  }
+  // Rt_out = Exp(xi) T0
+  const double th2 = sqrt(x[3] * x[3] + x[4] * x[4] + x[5] * x[5]);
+  so3_series(th2, A, B, C);
+  skew(x + 3, P);
+  mm3(P, P, P2);
+  double ER[9], EV[9];
+  for (int k = 0; k < 9; ++k) {
+    const double I = (k % 4) == 0 ? 1.0 : 0.0;
+    ER[k] = I + A * P[k] + B * P2[k];
+    EV[k] = I + B * P[k] + C * P2[k];
+  }
+  double Et[3];
+  for (int r = 0; r < 3; ++r) Et[r] = EV[3 * r] * x[0] + EV[3 * r + 1] * x[1] + EV[3 * r + 2] * x[2];
+  const float* T = T0 + 12 * i;
+  double R0[9], t0[3];
+  for (int k = 0; k < 9; ++k) R0[k] = T[k];
+  for (int k = 0; k < 3; ++k) t0[k] = T[9 + k];
+  double R[9];
+  mm3(ER, R0, R);
+  float* out = Rt_out + 12 * i;
+  for (int k = 0; k < 9; ++k) out[k] = (float)R[k];
+  for (int r = 0; r < 3; ++r)
+    out[9 + r] = (float)(ER[3 * r] * t0[0] + ER[3 * r + 1] * t0[1] + ER[3 * r + 2] * t0[2] + Et[r]);
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int64_t n, float lr, float beta1, float beta2,
+                            float eps, const int32_t* __restrict__ step) {
+  const int t = *step;
+  const float bc1 = 1.f - powf(beta1, (float)t);
+  const float bc2 = 1.f - powf(beta2, (float)t);
+  const float a = lr / bc1;
+  const float rb2 = 1.f / bc2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = beta1 * m[i] + (1.f - beta1) * gi;
+    const float vi = beta2 * v[i] + (1.f - beta2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= a * mi / (sqrtf(vi * rb2) + eps);
+  }
+}
+
+__global__ void step_advance_kernel(int32_t* step) { *step += 1; }
+
+__global__ void pose_partial_finalize_kernel(const double* __restrict__ partial, int n_blocks,
+                                             gs_batch batch, int n_cams, double* g_pose_tangent) {
+  const int b = blockIdx.x / 6, i = blockIdx.x % 6;
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < n_blocks; k += blockDim.x)
+    s += partial[(size_t)k * batch.B * 6 + 6 * b + i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int v = batch.views[b];
+    if ((unsigned)v < (unsigned)n_cams) g_pose_tangent[6 * v + i] += red[0];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_pose_partials_finalize(const double* partial, int n_blocks, const gs_batch& batch,
+                                          int n_cams, double* g_pose_tangent, cudaStream_t st) {
+  pose_partial_finalize_kernel<<<batch.B * 6, 256, 0, st>>>(partial, n_blocks, batch, n_cams,
+                                                            g_pose_tangent);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pose_update(int V, const float* T0, float* xi, const double* g_tangent, float* g_xi,
+                               float* m, float* v, const gs_adam* hp, float* Rt_out, cudaStream_t st) {
+  if (V == 0) return cudaSuccess;
+  const int threads = 128;
+  pose_update_kernel<<<(V + threads - 1) / threads, threads, 0, st>>>(
+      V, T0, xi, g_tangent, g_xi, m, v, hp ? 1 : 0, hp ? hp->lr : 0.f, hp ? hp->beta1 : 0.f,
+      hp ? hp->beta2 : 0.f, hp ? hp->eps : 0.f, hp ? hp->step : nullptr, Rt_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, const gs_adam& hp,
+                        cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int threads = 256;
+  const int64_t want = (n + threads - 1) / threads;
+  const int blocks = (int)std::min<int64_t>(want, (int64_t)device_sm_count() * 8);
+  adam_kernel<<<blocks, threads, 0, st>>>(p, g, m, v, n, hp.lr, hp.beta1, hp.beta2, hp.eps, hp.step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_advance(int32_t* step, cudaStream_t st) {
+  step_advance_kernel<<<1, 1, 0, st>>>(step);
+  return cudaGetLastError();
+}
+
+}  // namespace gs

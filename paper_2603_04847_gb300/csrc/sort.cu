@@ -1,0 +1,420 @@
+// Per-tile duplication and depth ordering of projected splats.
+//
+//   scan       exclusive prefix sum of tiles-touched over records r = b*N+j
+//   duplicate  one (key, value) per covered tile: key = tile << 32 | depth
+//              bits, value = r
+//   radix      stable LSD radix sort, 8-bit digits, only over the bits a
+//              key can use (32 depth bits + bits of the largest tile id)
+//   ranges     [start, end) per global tile
+//
+// The instance count stays on the device: every kernel after the scan reads
+// it, and all grids are sized from host-known bounds (records, capacity,
+// SM count), so the whole stage can be captured in a CUDA graph.  The radix
+// pass is the classic three-kernel form (per-block digit histogram, per-digit
+// scan over blocks, stable scatter); it needs no inter-block waiting.
+#include "gs_internal.h"
+
+namespace gs {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;  // 2048 records per tile
+
+__device__ inline uint32_t block_exclusive_scan_u32(uint32_t v, uint32_t* total, uint32_t* sm) {
+  // sm: >= 32 words.  Returns exclusive prefix of v over the block.
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) sm[warp] = x;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  if (warp == 0) {
+    uint32_t w = lane < nw ? sm[lane] : 0u;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, off);
+      if (lane >= off) w += y;
+    }
+    if (lane < nw) sm[lane] = w;
+  }
+  __syncthreads();
+  const uint32_t warp_prefix = warp > 0 ? sm[warp - 1] : 0u;
+  if (total) *total = sm[nw - 1];
+  __syncthreads();
+  return warp_prefix + x - v;
+}
+
+// Sum of n_tiles per scan tile (64-bit to detect overflow of 32-bit offsets).
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ in,
+                                                                   size_t M,
+                                                                   unsigned long long* tile_sums) {
+  __shared__ unsigned long long red[kScanThreads / 32];
+  const size_t base = (size_t)blockIdx.x * kScanTile;
+  unsigned long long s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const size_t k = base + (size_t)i * kScanThreads + threadIdx.x;
+    if (k < M) s += in[k];
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) t += red[w];
+    tile_sums[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of the tile sums in one block; writes the instance count
+// and raises GS_FLAG_CAPACITY when it exceeds the capacity.
+__global__ void __launch_bounds__(1024) scan_tiles_kernel(unsigned long long* tile_sums, int n_tiles,
+                                                          size_t capacity, uint32_t* n_instances,
+                                                          int32_t* status) {
+  __shared__ unsigned long long sm[32];
+  const int per = (n_tiles + blockDim.x - 1) / blockDim.x;
+  const int lo = threadIdx.x * per;
+  const int hi = min(lo + per, n_tiles);
+  unsigned long long s = 0;
+  for (int k = lo; k < hi; ++k) s += tile_sums[k];
+  // block exclusive scan of s (64-bit)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long x = s;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) sm[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    unsigned long long w = lane < nw ? sm[lane] : 0ull;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, w, off);
+      if (lane >= off) w += y;
+    }
+    if (lane < nw) sm[lane] = w;
+  }
+  __syncthreads();
+  unsigned long long run = (warp > 0 ? sm[warp - 1] : 0ull) + x - s;
+  for (int k = lo; k < hi; ++k) {
+    const unsigned long long v = tile_sums[k];
+    tile_sums[k] = run;
+    run += v;
+  }
+  if (threadIdx.x == blockDim.x - 1) {
+    // the full count (saturated to 32 bits) tells the host how much capacity
+    // it needs; every consumer uses min(count, capacity)
+    const unsigned long long total = run;
+    if (total > (unsigned long long)capacity) set_flag(status, GS_FLAG_CAPACITY);
+    *n_instances = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t* __restrict__ in,
+                                                                  size_t M,
+                                                                  const unsigned long long* tile_offs,
+                                                                  uint32_t* __restrict__ out) {
+  __shared__ uint32_t sm[32];
+  const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const size_t k = base + i;
+    v[i] = k < M ? in[k] : 0u;
+    s += v[i];
+  }
+  const uint32_t ex = block_exclusive_scan_u32(s, nullptr, sm);
+  // offsets beyond 2^32 cannot be valid instances (capacity < 2^32): clamp
+  const unsigned long long t0 = tile_offs[blockIdx.x] + ex;
+  unsigned long long run = t0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const size_t k = base + i;
+    if (k < M) out[k] = run > 0xffffffffull ? 0xffffffffu : (uint32_t)run;
+    run += v[i];
+  }
+}
+
+struct SlotTiles {
+  int tiles_x;
+  int tile_offset;
+};
+
+__global__ void __launch_bounds__(256) duplicate_kernel(gs_projected proj, const uint32_t* __restrict__ offs,
+                                                        int N, gs_cameras cams, gs_batch batch,
+                                                        uint64_t* __restrict__ keys,
+                                                        uint32_t* __restrict__ vals, size_t capacity,
+                                                        int32_t* status) {
+  __shared__ SlotTiles st[GS_MAX_BATCH];
+  for (int b = threadIdx.x; b < batch.B; b += blockDim.x) {
+    const int v = slot_view(cams, batch, b);
+    st[b].tiles_x = (cams.wh[2 * v] + batch.tile - 1) / batch.tile;
+    st[b].tile_offset = batch.tile_offset[b];
+  }
+  __syncthreads();
+  const size_t M = (size_t)batch.B * N;
+  for (size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x; r < M;
+       r += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t n = proj.n_tiles[r];
+    if (n == 0) continue;
+    const int b = (int)(r / N);
+    const ushort4 rc = reinterpret_cast<const ushort4*>(proj.rect)[r];
+    const float depth = reinterpret_cast<const float4*>(proj.splat)[3 * r].w;
+    const uint64_t dbits = (uint64_t)__float_as_uint(depth);
+    size_t o = offs[r];
+    if (o + n > capacity) set_flag(status, GS_FLAG_CAPACITY);
+    const int tx_n = st[b].tiles_x, t0 = st[b].tile_offset;
+    for (int ty = rc.y; ty <= rc.w; ++ty)
+      for (int tx = rc.x; tx <= rc.z; ++tx) {
+        if (o < capacity) {
+          const uint64_t tile = (uint64_t)(t0 + ty * tx_n + tx);
+          keys[o] = (tile << 32) | dbits;
+          vals[o] = (uint32_t)r;
+        }
+        ++o;
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort over a device-side item count.
+
+constexpr int kRadixThreads = 512;
+constexpr int kRadixWarps = kRadixThreads / 32;
+
+__device__ inline void chunk_of(uint32_t n, int nb, int blk, uint32_t& lo, uint32_t& hi) {
+  uint32_t chunk = (n + nb - 1) / nb;
+  chunk = (chunk + kRadixThreads - 1) / kRadixThreads * kRadixThreads;
+  lo = min((uint32_t)blk * chunk, n);
+  hi = min(lo + chunk, n);
+}
+
+__global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const uint64_t* __restrict__ keys,
+                                                                   const uint32_t* n_dev, size_t capacity,
+                                                                   int shift, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[kRadixWarps][256];
+  for (int i = threadIdx.x; i < kRadixWarps * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t n = (uint32_t)min((size_t)*n_dev, capacity);
+  uint32_t lo, hi;
+  chunk_of(n, gridDim.x, blockIdx.x, lo, hi);
+  const int warp = threadIdx.x >> 5;
+  for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const uint32_t d = (uint32_t)(keys[i] >> shift) & 0xffu;
+    atomicAdd(&h[warp][d], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int w = 0; w < kRadixWarps; ++w) s += h[w][d];
+    hist[(size_t)d * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// Block d: exclusive scan over the NB block counts of digit d, in place;
+// digit total to totals[d].
+__global__ void __launch_bounds__(256) radix_scan_kernel(uint32_t* hist, int nb, uint32_t* totals) {
+  __shared__ uint32_t sm[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  uint32_t* row = hist + (size_t)blockIdx.x * nb;
+  for (int base = 0; base < nb; base += blockDim.x) {
+    const int k = base + threadIdx.x;
+    const uint32_t v = k < nb ? row[k] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan_u32(v, &tot, sm);
+    if (k < nb) row[k] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+}
+
+__global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
+    const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, const uint32_t* n_dev, size_t capacity, int shift,
+    const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals) {
+  __shared__ uint32_t run[256];
+  __shared__ uint32_t wcnt[kRadixWarps][256];
+  __shared__ uint32_t sm[32];
+  // digit base = exclusive scan of the digit totals
+  {
+    const uint32_t t = threadIdx.x < 256 ? totals[threadIdx.x] : 0u;
+    const uint32_t ex = block_exclusive_scan_u32(t, nullptr, sm);
+    if (threadIdx.x < 256) run[threadIdx.x] = ex + hist[(size_t)threadIdx.x * gridDim.x + blockIdx.x];
+  }
+  for (int i = threadIdx.x; i < kRadixWarps * 256; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t n = (uint32_t)min((size_t)*n_dev, capacity);
+  uint32_t lo, hi;
+  chunk_of(n, gridDim.x, blockIdx.x, lo, hi);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (uint32_t base = lo; base < hi; base += kRadixThreads) {
+    const uint32_t i = base + threadIdx.x;
+    const bool valid = i < hi;
+    uint64_t k = 0;
+    uint32_t v = 0;
+    uint32_t d = 256u + (uint32_t)lane;  // unique sentinel for invalid lanes
+    if (valid) {
+      k = kin[i];
+      v = vin[i];
+      d = (uint32_t)(k >> shift) & 0xffu;
+    }
+    __syncwarp();
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t rank = __popc(peers & lt_mask);
+    const bool leader = (peers & lt_mask) == 0;
+    if (valid && leader) wcnt[warp][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      uint32_t pre = 0;
+      for (int w = 0; w < warp; ++w) pre += wcnt[w][d];
+      const uint32_t pos = run[d] + pre + rank;
+      kout[pos] = k;
+      vout[pos] = v;
+    }
+    __syncthreads();
+    if (valid && leader) {
+      atomicAdd(&run[d], (uint32_t)__popc(peers));
+      wcnt[warp][d] = 0;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) tile_ranges_kernel(const uint64_t* __restrict__ keys,
+                                                          const uint32_t* n_dev, size_t capacity,
+                                                          uint32_t* __restrict__ ranges) {
+  const uint32_t n = (uint32_t)min((size_t)*n_dev, capacity);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t t = (uint32_t)(keys[i] >> 32);
+    if (i == 0) {
+      ranges[2 * t] = 0;
+    } else {
+      const uint32_t p = (uint32_t)(keys[i - 1] >> 32);
+      if (p != t) {
+        ranges[2 * p + 1] = i;
+        ranges[2 * t] = i;
+      }
+    }
+    if (i == n - 1) ranges[2 * t + 1] = n;
+  }
+}
+
+inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct SortWs {
+  uint32_t* offs;
+  unsigned long long* tile_sums;
+  uint64_t* keys_alt;
+  uint32_t* vals_alt;
+  uint32_t* hist;
+  uint32_t* totals;
+  size_t bytes;
+};
+
+SortWs sort_ws_layout(void* base, size_t M, size_t capacity, int nb) {
+  SortWs w;
+  char* p = (char*)base;
+  size_t o = 0;
+  const size_t n_scan_tiles = (M + kScanTile - 1) / kScanTile;
+  w.offs = (uint32_t*)(p + o);
+  o += align_up(M * 4);
+  w.tile_sums = (unsigned long long*)(p + o);
+  o += align_up(n_scan_tiles * 8 + 8);
+  w.keys_alt = (uint64_t*)(p + o);
+  o += align_up(capacity * 8);
+  w.vals_alt = (uint32_t*)(p + o);
+  o += align_up(capacity * 4);
+  w.hist = (uint32_t*)(p + o);
+  o += align_up((size_t)256 * nb * 4);
+  w.totals = (uint32_t*)(p + o);
+  o += align_up(256 * 4);
+  w.bytes = o;
+  return w;
+}
+
+int radix_blocks() {
+  static int nb = 0;
+  if (nb == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    nb = sms > 0 ? sms * 2 : 304;
+  }
+  return nb;
+}
+
+}  // namespace
+
+int sort_key_bits(int n_tiles_total) {
+  int tb = 0;
+  while ((1ll << tb) < (long long)n_tiles_total) ++tb;
+  return 32 + tb;
+}
+
+size_t sort_workspace_bytes(int N, const gs_batch& batch, size_t capacity) {
+  return sort_ws_layout(nullptr, (size_t)batch.B * N, capacity, radix_blocks()).bytes;
+}
+
+cudaError_t launch_sort_tiles(int N, const gs_cameras& cams, const gs_batch& batch,
+                              const gs_projected& proj, uint64_t* keys, uint32_t* vals,
+                              size_t capacity, uint32_t* ranges, uint32_t* n_instances, void* ws,
+                              int32_t* status, cudaStream_t st) {
+  const size_t M = (size_t)batch.B * N;
+  const int nb = radix_blocks();
+  SortWs w = sort_ws_layout(ws, M, capacity, nb);
+  cudaError_t e;
+  e = cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)batch.n_tiles, st);
+  if (e != cudaSuccess) return e;
+  const int n_scan_tiles = (int)((M + kScanTile - 1) / kScanTile);
+  if (n_scan_tiles == 0) return cudaMemsetAsync(n_instances, 0, 4, st);
+  scan_reduce_kernel<<<n_scan_tiles, kScanThreads, 0, st>>>(proj.n_tiles, M, w.tile_sums);
+  scan_tiles_kernel<<<1, 1024, 0, st>>>(w.tile_sums, n_scan_tiles, capacity, n_instances, status);
+  scan_apply_kernel<<<n_scan_tiles, kScanThreads, 0, st>>>(proj.n_tiles, M, w.tile_sums, w.offs);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+
+  const int bits = sort_key_bits(batch.n_tiles);
+  const int passes = (bits + 7) / 8;
+  // Duplicate into the buffer that leaves the sorted result in keys/vals.
+  uint64_t* kA = (passes & 1) ? w.keys_alt : keys;
+  uint32_t* vA = (passes & 1) ? w.vals_alt : vals;
+  uint64_t* kB = (passes & 1) ? keys : w.keys_alt;
+  uint32_t* vB = (passes & 1) ? vals : w.vals_alt;
+  const int dup_blocks = (int)std::min<size_t>((M + 255) / 256, (size_t)nb * 8);
+  duplicate_kernel<<<dup_blocks, 256, 0, st>>>(proj, w.offs, N, cams, batch, kA, vA, capacity, status);
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    radix_hist_kernel<<<nb, kRadixThreads, 0, st>>>(kA, n_instances, capacity, shift, w.hist);
+    radix_scan_kernel<<<256, 256, 0, st>>>(w.hist, nb, w.totals);
+    radix_scatter_kernel<<<nb, kRadixThreads, 0, st>>>(kA, vA, kB, vB, n_instances, capacity, shift,
+                                                       w.hist, w.totals);
+    std::swap(kA, kB);
+    std::swap(vA, vB);
+  }
+  tile_ranges_kernel<<<nb * 4, 256, 0, st>>>(keys, n_instances, capacity, ranges);
+  return cudaGetLastError();
+}
+
+int sort_launch_count(const gs_batch& batch) {
+  const int passes = (sort_key_bits(batch.n_tiles) + 7) / 8;
+  return 3 + 1 + 3 * passes + 1;
+}
+
+}  // namespace gs

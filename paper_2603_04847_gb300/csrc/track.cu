@@ -1,0 +1,185 @@
+// Feature-track reprojection term of Eq. 6 (Algorithm 1, "Joint BA loss on
+// track points"), forward and backward in one pass.
+//
+// Observations are bucketed by camera (view-CSR), so the batch's
+// observations are B contiguous ranges.  A fixed grid walks their
+// concatenation; each observation does its projection, Huber weight and
+// Jacobians in registers, adds weight * drho/dX to its track point (three
+// scalar atomics; a track has few observations, so they rarely collide),
+// and its pose-tangent share is reduced warp -> block (shared double) ->
+// per-block partial, summed in block order by a second kernel.
+#include "gs_internal.h"
+
+namespace gs {
+
+namespace {
+
+struct TrackSlot {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  long long start;  // first observation of the slot's camera
+  long long pref;   // observations of slots before this one
+};
+
+__global__ void __launch_bounds__(256) track_kernel(const float* __restrict__ X, int n_points,
+                                                    const int32_t* __restrict__ obs_point,
+                                                    const float2* __restrict__ obs_xy,
+                                                    const int64_t* __restrict__ view_obs_offset,
+                                                    gs_cameras cams, gs_batch batch, float delta,
+                                                    float weight, double* loss, float* grad_X,
+                                                    uint32_t* n_masked, double* partial) {
+  __shared__ TrackSlot ts[GS_MAX_BATCH];
+  __shared__ long long s_total;
+  __shared__ double s_tan[GS_MAX_BATCH * 6];
+  __shared__ double s_loss;
+  __shared__ uint32_t s_masked;
+  if (threadIdx.x == 0) {
+    long long acc = 0;
+    for (int b = 0; b < batch.B; ++b) {
+      const int v = slot_view(cams, batch, b);
+      const long long s = view_obs_offset[v], e = view_obs_offset[v + 1];
+      ts[b].start = s;
+      ts[b].pref = acc;
+      acc += e > s ? e - s : 0;
+    }
+    s_total = acc;
+    s_loss = 0.0;
+    s_masked = 0;
+  }
+  for (int b = threadIdx.x; b < batch.B; b += blockDim.x) {
+    const int v = slot_view(cams, batch, b);
+    const float* Rt = cams.Rt + 12 * v;
+    for (int i = 0; i < 9; ++i) ts[b].R[i] = Rt[i];
+    for (int i = 0; i < 3; ++i) ts[b].t[i] = Rt[9 + i];
+    ts[b].fx = cams.K[4 * v];
+    ts[b].fy = cams.K[4 * v + 1];
+    ts[b].cx = cams.K[4 * v + 2];
+    ts[b].cy = cams.K[4 * v + 3];
+  }
+  for (int i = threadIdx.x; i < batch.B * 6; i += blockDim.x) s_tan[i] = 0.0;
+  __syncthreads();
+  const long long total = s_total;
+  const int lane = threadIdx.x & 31;
+  const float d2 = delta * delta;
+  float lsum = 0.f;
+  uint32_t masked = 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  // every lane of a warp runs the same number of iterations (warp collectives)
+  const long long wbase0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  for (long long wbase = wbase0; wbase < total; wbase += stride) {
+    const long long i = wbase + lane;
+    const bool valid = i < total;
+    int b = 0;
+    float tan[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (valid) {
+      int lo = 0, hi = batch.B - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ts[mid].pref <= i) lo = mid;
+        else hi = mid - 1;
+      }
+      b = lo;
+      const TrackSlot& c = ts[b];
+      const long long o = c.start + (i - c.pref);
+      const int k = obs_point[o];
+      const float2 xy = obs_xy[o];
+      const bool in_range = (unsigned)k < (unsigned)n_points;
+      const size_t kk = in_range ? (size_t)k : 0;
+      const float Xw0 = X[3 * kk], Xw1 = X[3 * kk + 1], Xw2 = X[3 * kk + 2];
+      float Xc[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) Xc[r] = c.R[3 * r] * Xw0 + c.R[3 * r + 1] * Xw1 + c.R[3 * r + 2] * Xw2 + c.t[r];
+      if (!in_range) {
+        // observation of a point that does not exist: ignored
+      } else if (Xc[2] <= cams.near_plane) {
+        ++masked;
+      } else {
+        const float iz = 1.f / Xc[2];
+        const float rx = c.fx * Xc[0] * iz + c.cx - xy.x;
+        const float ry = c.fy * Xc[1] * iz + c.cy - xy.y;
+        const float s = rx * rx + ry * ry;
+        float rho, drho;
+        if (s <= d2) {
+          rho = s;
+          drho = 1.f;
+        } else {
+          const float rs = sqrtf(s);
+          rho = 2.f * delta * rs - d2;
+          drho = delta / rs;
+        }
+        lsum += rho;
+        const float vu = weight * 2.f * rx * drho;
+        const float vv = weight * 2.f * ry * drho;
+        float vX[3];
+        vX[0] = vu * c.fx * iz;
+        vX[1] = vv * c.fy * iz;
+        vX[2] = -(vu * c.fx * Xc[0] + vv * c.fy * Xc[1]) * iz * iz;
+        float* gX = grad_X + 3 * kk;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          atomicAdd(gX + a, c.R[a] * vX[0] + c.R[3 + a] * vX[1] + c.R[6 + a] * vX[2]);
+        tan[0] = vX[0];
+        tan[1] = vX[1];
+        tan[2] = vX[2];
+        tan[3] = Xc[1] * vX[2] - Xc[2] * vX[1];
+        tan[4] = Xc[2] * vX[0] - Xc[0] * vX[2];
+        tan[5] = Xc[0] * vX[1] - Xc[1] * vX[0];
+      }
+    }
+    // valid lanes form a prefix of the warp, so lane 0 is valid here
+    const int b0 = __shfl_sync(0xffffffffu, b, 0);
+    if (__all_sync(0xffffffffu, !valid || b == b0)) {
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        float x = tan[a];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if (lane == 0) atomicAdd(&s_tan[6 * b0 + a], (double)x);
+      }
+    } else if (valid) {
+#pragma unroll
+      for (int a = 0; a < 6; ++a) atomicAdd(&s_tan[6 * b + a], (double)tan[a]);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+    masked += __shfl_xor_sync(0xffffffffu, masked, off);
+  }
+  if (lane == 0) {
+    atomicAdd(&s_loss, (double)lsum);
+    atomicAdd(&s_masked, masked);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (loss && s_loss != 0.0) atomicAdd(loss, s_loss);
+    if (n_masked && s_masked) atomicAdd(n_masked, s_masked);
+  }
+  for (int i = threadIdx.x; i < batch.B * 6; i += blockDim.x)
+    partial[(size_t)blockIdx.x * batch.B * 6 + i] = s_tan[i];
+}
+
+}  // namespace
+
+int track_blocks() { return 2 * device_sm_count(); }
+
+size_t track_workspace_bytes(const gs_batch& batch) {
+  return (size_t)track_blocks() * batch.B * 6 * sizeof(double);
+}
+
+cudaError_t launch_track(const float* X, int n_points, const int32_t* obs_point, const float* obs_xy,
+                         const int64_t* view_obs_offset, const gs_cameras& cams, const gs_batch& batch,
+                         float delta, float weight, double* loss, float* grad_X,
+                         double* g_pose_tangent, uint32_t* n_masked, void* ws, cudaStream_t st) {
+  const int nb = track_blocks();
+  double* partial = reinterpret_cast<double*>(ws);
+  track_kernel<<<nb, 256, 0, st>>>(X, n_points, obs_point, reinterpret_cast<const float2*>(obs_xy),
+                                   view_obs_offset, cams, batch, delta, weight, loss, grad_X,
+                                   n_masked, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_pose_partials_finalize(partial, nb, batch, cams.n_cams, g_pose_tangent, st);
+}
+
+}  // namespace gs

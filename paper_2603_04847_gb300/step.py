@@ -1,0 +1,260 @@
+"""Joint pose-appearance training step (Algorithm 1, one iteration) driven
+through the C ABI: the batched form (every stage one launch over all views
+of the batch, capturable in a CUDA graph) and the plain form (one view per
+launch, for comparison)."""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _lib
+from .core import (Batch, Cameras, Gaussians, Projected, TileLists, adam_c, gs_adam_update, gs_project,
+                   gs_project_bwd, gs_raster_bwd, gs_render_fwd, gs_sort_tiles, gs_step_advance, gs_zero,
+                   new_status, pose_se3_update, render_bwd_workspace_bytes, track_reproj_fwd_bwd,
+                   track_workspace_bytes)
+
+
+def _nomark(name):
+    pass
+
+
+class Renderer:
+    """Buffers and launches for rendering one batch of views: projection,
+    tile sort, compositing, and the backward.  Launches never read anything
+    back; `ensure_capacity` is the only host synchronisation and grows the
+    instance buffers when the sort reported an overflow."""
+
+    def __init__(self, n: int, cams: Cameras, batch: Batch, capacity: int = 0, bg=(0.0, 0.0, 0.0),
+                 device="cuda"):
+        self.n, self.cams, self.batch = n, cams, batch
+        self.proj = Projected(n, batch.B, device)
+        cap = capacity if capacity > 0 else max(1 << 16, 4 * n * batch.B)
+        self.tl = TileLists(n, batch, cap, device)
+        P = max(batch.n_pixels, 1)
+        self.image = torch.zeros((P, 3), dtype=torch.float32, device=device)
+        self.T_final = torch.zeros(P, dtype=torch.float32, device=device)
+        self.n_contrib = torch.zeros(P, dtype=torch.int32, device=device)
+        self.bg = torch.tensor(bg, dtype=torch.float32, device=device)
+        self.ws_bwd = torch.empty(max(render_bwd_workspace_bytes(n, batch), 256), dtype=torch.uint8,
+                                  device=device)
+        self.status = new_status(device)
+
+    def forward(self, g: Gaussians, Rt: torch.Tensor = None, mark=_nomark):
+        gs_project(g, self.cams, self.batch, self.proj, self.status, Rt)
+        mark("project")
+        gs_sort_tiles(self.n, self.cams, self.batch, self.proj, self.tl, self.status, Rt)
+        mark("sort")
+        gs_render_fwd(self.batch, self.cams, self.proj, self.tl, self.bg, self.image, self.T_final,
+                      self.n_contrib, Rt)
+        mark("render_fwd")
+
+    def backward(self, g: Gaussians, dg: Gaussians, g_tangent: torch.Tensor, v_image=None, target=None,
+                 l1_weight: float = 1.0, loss=None, Rt: torch.Tensor = None, mark=_nomark):
+        # gs_render_bwd is exactly these two calls; issuing them separately
+        # lets a caller time each half
+        gs_raster_bwd(g, self.cams, self.batch, self.proj, self.tl, self.bg, self.image, self.T_final,
+                      self.n_contrib, v_image, target, l1_weight, loss, self.ws_bwd, Rt)
+        mark("raster_bwd")
+        gs_project_bwd(g, self.cams, self.batch, self.proj, dg, g_tangent, self.ws_bwd, Rt)
+        mark("project_bwd")
+
+    def n_instances(self) -> int:
+        return int(self.tl.n_instances.item()) & 0xffffffff
+
+    def ensure_capacity(self, g: Gaussians, Rt: torch.Tensor = None, headroom: float = 1.25) -> bool:
+        """Runs projection + sort once, reads the instance count and grows
+        the buffers if needed.  Returns True when they were resized."""
+        self.status.zero_()
+        gs_project(g, self.cams, self.batch, self.proj, self.status, Rt)
+        gs_sort_tiles(self.n, self.cams, self.batch, self.proj, self.tl, self.status, Rt)
+        need = self.n_instances()
+        if need > self.tl.capacity:
+            self.tl = TileLists(self.n, self.batch, int(need * headroom) + 1024, self.image.device)
+            self.status.zero_()
+            return True
+        self.status.zero_()
+        return False
+
+
+@dataclass
+class Hyper:
+    """Learning rates of Sec. 3.3 ("Implementation"; camera extrinsics: Adam
+    with lr 1e-5).  The paper gives no rate for the track points; they use
+    the position rate."""
+    lr_mean: float = 1.6e-4
+    lr_log_scale: float = 5e-3
+    lr_quat: float = 1e-3
+    lr_opacity: float = 5e-2
+    lr_sh: float = 2.5e-3
+    lr_track: float = 1.6e-4
+    lr_pose: float = 1e-5
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-15
+    scene_extent: float = 1.0
+    lambda_ba: float = 1e-4       # Sec. 3.3 total objective
+    huber_delta: float = 1.0      # Eq. 6
+    l1_weight: float = 1.0        # L1 part of Eq. 5 (SSIM term not in this step)
+
+
+class JointStep:
+    """State and launches of the joint training step.
+
+    Parameters: Gaussians G, track points X, per-camera pose deltas xi with
+    T = Exp(xi) T0 (Algorithm 1).  One call of `step()` performs, for the
+    current batch: projection, tile sort, compositing, fused L1 + backward
+    with pose gradient, the track term, and the Adam updates of G, X and xi
+    (which also recomposes the poses used by the next step).  Nothing is
+    read back to the host.  `mode="plain"` issues every stage once per view
+    (B = 1 launches); `mode="batched"` issues each stage once for the batch.
+    """
+
+    def __init__(self, gaussians: Gaussians, cams: Cameras, X: torch.Tensor, obs_point: torch.Tensor,
+                 obs_xy: torch.Tensor, view_obs_offset: torch.Tensor, targets: torch.Tensor,
+                 target_px_offset: np.ndarray, views, hyper: Hyper = None, mode: str = "batched",
+                 capacity: int = 0, device="cuda"):
+        self.h = hyper or Hyper()
+        self.mode = mode
+        self.g = gaussians
+        self.dg = Gaussians.zeros_like(gaussians)
+        self.m = Gaussians.zeros_like(gaussians)
+        self.v = Gaussians.zeros_like(gaussians)
+        self.cams = cams
+        self.T0 = cams.Rt.clone()
+        self.Rt = cams.Rt.clone()
+        V = cams.V
+        self.xi = torch.zeros((V, 6), dtype=torch.float32, device=device)
+        self.g_xi = torch.zeros_like(self.xi)
+        self.m_xi = torch.zeros_like(self.xi)
+        self.v_xi = torch.zeros_like(self.xi)
+        self.g_tan = torch.zeros((V, 6), dtype=torch.float64, device=device)
+        self.X = X
+        self.gX = torch.zeros_like(X)
+        self.mX = torch.zeros_like(X)
+        self.vX = torch.zeros_like(X)
+        self.obs_point, self.obs_xy, self.view_obs_offset = obs_point, obs_xy, view_obs_offset
+        self.targets = targets                  # all views, packed by target_px_offset
+        self.target_px_offset = np.asarray(target_px_offset, dtype=np.int64)
+        self.loss = torch.zeros(2, dtype=torch.float64, device=device)   # [L_photo, sum rho]
+        self.n_masked = torch.zeros(1, dtype=torch.int32, device=device)
+        self.step_no = torch.zeros(1, dtype=torch.int32, device=device)
+        self.device = device
+        self._capacity = capacity
+        self.graph = None
+        self.set_batch(views)
+
+    # -- batch management --------------------------------------------------
+    def set_batch(self, views):
+        views = np.asarray(views, dtype=np.int64)
+        self.views = views
+        self.batch = Batch(self.cams, views, device=self.device)
+        n = self.g.n
+        if self.mode == "batched":
+            self.renderers = [Renderer(n, self.cams, self.batch, self._capacity, device=self.device)]
+            self.slot_batches = [self.batch]
+        else:
+            self.slot_batches = [Batch(self.cams, [v], device=self.device) for v in views]
+            cap = self._capacity // max(len(views), 1)
+            self.renderers = [Renderer(n, self.cams, b, cap, device=self.device) for b in self.slot_batches]
+        self.track_ws = torch.empty(max(track_workspace_bytes(self.batch), 256), dtype=torch.uint8,
+                                    device=self.device)
+        self.target_batch = torch.empty((max(self.batch.n_pixels, 1), 3), dtype=torch.float32,
+                                        device=self.device)
+        self.load_targets()
+        self.graph = None
+
+    def load_targets(self):
+        """Gathers the batch's target images into slot order (one device
+        copy per view)."""
+        for b, v in enumerate(self.views):
+            a, e = int(self.target_px_offset[v]), int(self.target_px_offset[v + 1])
+            d = int(self.batch.px_offset_host[b])
+            self.target_batch[d:d + (e - a)].copy_(self.targets[a:e], non_blocking=True)
+
+    def ensure_capacity(self):
+        grew = False
+        for r in self.renderers:
+            grew |= r.ensure_capacity(self.g, self.Rt)
+        if grew:
+            self.graph = None
+        return grew
+
+    # -- the step ----------------------------------------------------------
+    def _adam(self, p, g, m, v, lr):
+        gs_adam_update(p, g, m, v, adam_c(lr, self.h.beta1, self.h.beta2, self.h.eps, self.step_no))
+
+    def step(self, mark=_nomark):
+        """One training iteration; `mark(name)` is called after each stage
+        (for event timing)."""
+        h = self.h
+        for t in self.dg.tensors() + [self.gX, self.g_tan, self.loss, self.n_masked]:
+            gs_zero(t)
+        mark("zero")
+        if self.mode == "batched":
+            r = self.renderers[0]
+            r.forward(self.g, self.Rt, mark)
+            r.backward(self.g, self.dg, self.g_tan, target=self.target_batch, l1_weight=h.l1_weight,
+                       loss=self.loss[0:1], Rt=self.Rt, mark=mark)
+        else:
+            for b, r in enumerate(self.renderers):
+                a, e = int(self.batch.px_offset_host[b]), int(self.batch.px_offset_host[b + 1])
+                r.forward(self.g, self.Rt, mark)
+                r.backward(self.g, self.dg, self.g_tan, target=self.target_batch[a:e], l1_weight=h.l1_weight,
+                           loss=self.loss[0:1], Rt=self.Rt, mark=mark)
+        track_reproj_fwd_bwd(self.X, self.obs_point, self.obs_xy, self.view_obs_offset, self.cams, self.batch,
+                             h.huber_delta, h.lambda_ba, self.loss[1:2], self.gX, self.g_tan, self.n_masked,
+                             self.track_ws, self.Rt)
+        mark("track")
+        gs_step_advance(self.step_no)
+        ext = h.scene_extent
+        self._adam(self.g.mean, self.dg.mean, self.m.mean, self.v.mean, h.lr_mean * ext)
+        self._adam(self.g.log_scale, self.dg.log_scale, self.m.log_scale, self.v.log_scale, h.lr_log_scale)
+        self._adam(self.g.quat, self.dg.quat, self.m.quat, self.v.quat, h.lr_quat)
+        self._adam(self.g.opacity_logit, self.dg.opacity_logit, self.m.opacity_logit, self.v.opacity_logit,
+                   h.lr_opacity)
+        self._adam(self.g.sh, self.dg.sh, self.m.sh, self.v.sh, h.lr_sh)
+        self._adam(self.X, self.gX, self.mX, self.vX, h.lr_track * ext)
+        mark("adam")
+        hp = adam_c(h.lr_pose, h.beta1, h.beta2, h.eps, self.step_no)
+        pose_se3_update(self.T0, self.xi, self.g_tan, self.g_xi, self.m_xi, self.v_xi, hp, self.Rt)
+        mark("pose")
+
+    def kernels_per_step(self) -> int:
+        """libgs kernel launches one step issues (memsets not counted)."""
+        per_render = 0
+        for b in self.slot_batches:
+            passes = (32 + max(int(math.ceil(math.log2(max(b.n_tiles, 1)))), 0) + 7) // 8
+            # project 1; sort: 3 scan + duplicate + 3 per pass + ranges;
+            # render fwd 1; raster bwd 1; project bwd + finalize 2
+            per_render += 1 + (3 + 1 + 3 * passes + 1) + 1 + 1 + 2
+        # track + finalize 2, step advance 1, Adam 6, pose 1
+        return per_render + 2 + 1 + 6 + 1
+
+    # -- CUDA graph ----------------------------------------------------------
+    def capture(self, warmup: int = 1):
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.step()
+        torch.cuda.synchronize()
+
+    def run(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.step()
+
+    def status_flags(self) -> int:
+        f = 0
+        for r in self.renderers:
+            f |= int(r.status.item())
+        return f

@@ -1,0 +1,166 @@
+"""Edge cases of the CUDA path: empty and fully culled scenes, ragged image
+sizes, capacity overflow, non-finite parameters, argument errors, and the
+CUDA-graph replay of the joint step against eager launches."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _gpu import f32, gpu_forward, knife_mask, oracle_cam, oracle_scene, rel_linf
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_04847_gb300 import build
+    build.build()
+
+
+def _cam_arrays(W, H, f=220.0):
+    Rt = np.zeros((1, 12))
+    Rt[0, [0, 4, 8]] = 1.0
+    return np.array([[W, H]]), np.array([[f, f, W / 2, H / 2]]), Rt
+
+
+def test_empty_scene_renders_background():
+    wh, K, Rt = _cam_arrays(40, 30)
+    sc = dict(mean=np.zeros((0, 3)), log_scale=np.zeros((0, 3)), quat=np.zeros((0, 4)),
+              opacity_logit=np.zeros(0), sh=np.zeros((0, 1, 3)))
+    r, *_ = gpu_forward(sc, wh, K, Rt, [0], bg=(0.1, 0.2, 0.3))
+    img = r.image.cpu().numpy()
+    bg32 = np.array([0.1, 0.2, 0.3], dtype=np.float32)
+    np.testing.assert_array_equal(img, np.tile(bg32, (1200, 1)))
+    assert (r.T_final.cpu().numpy() == 1.0).all() and (r.n_contrib.cpu().numpy() == 0).all()
+    assert r.n_instances() == 0
+
+
+def test_all_culled_scene():
+    wh, K, Rt = _cam_arrays(48, 32)
+    n = 50
+    rng = np.random.default_rng(0)
+    sc = dict(mean=np.stack([rng.uniform(-1, 1, n), rng.uniform(-1, 1, n), rng.uniform(-5, -1, n)], 1),
+              log_scale=np.full((n, 3), -2.0), quat=rng.normal(size=(n, 4)), opacity_logit=np.zeros(n),
+              sh=np.zeros((n, 1, 3)))
+    r, *_ = gpu_forward(sc, wh, K, Rt, [0])
+    assert r.n_instances() == 0
+    assert (r.image.cpu().numpy() == 0).all()
+
+
+@pytest.mark.parametrize("W,H", [(250, 190), (17, 33), (1, 1), (16, 16)])
+def test_ragged_sizes_match_oracle(W, H):
+    w = synth.make_workload("tiny", n_gaussians=500)
+    sc = w["scene"]
+    wh, K, Rt = _cam_arrays(W, H)
+    r, *_ = gpu_forward(sc, wh, K, Rt, [0])
+    ref = oracle.render(oracle_scene(sc), oracle_cam(wh, K, Rt, 0), knife_eps=1e-4)
+    img = r.image.cpu().numpy().reshape(H, W, 3)
+    ok = ~knife_mask(ref)
+    if ok.any() and np.abs(ref["image"][ok]).max() > 0:
+        assert rel_linf(img[ok], ref["image"][ok]) <= 1e-4
+    else:
+        assert np.abs(img[ok]).max() <= 1e-6
+
+
+def test_capacity_overflow_sets_flag_and_is_recoverable():
+    from paper_2603_04847_gb300 import Batch, Cameras, Gaussians, Renderer, _lib
+    w = synth.make_workload("tiny", n_gaussians=800)
+    g = Gaussians.from_numpy(w["scene"])
+    cams = Cameras.from_numpy(w["wh"], w["K"], w["Rt"])
+    r = Renderer(g.n, cams, Batch(cams, [0]), capacity=64)
+    r.forward(g)
+    torch.cuda.synchronize()
+    assert int(r.status.item()) & _lib.GS_FLAG_CAPACITY
+    need = r.n_instances()
+    assert need > 64
+    assert r.ensure_capacity(g)
+    r.forward(g)
+    torch.cuda.synchronize()
+    assert int(r.status.item()) == 0 and r.tl.capacity >= need
+    ref, *_ = gpu_forward(w["scene"], w["wh"], w["K"], w["Rt"], [0])
+    np.testing.assert_array_equal(r.image.cpu().numpy(), ref.image.cpu().numpy())
+
+
+def test_nonfinite_gaussian_is_flagged_and_culled():
+    from paper_2603_04847_gb300 import _lib
+    w = synth.make_workload("tiny", n_gaussians=300)
+    sc = {k: v.copy() for k, v in w["scene"].items()}
+    sc["mean"][5, 0] = np.nan
+    sc["sh"][9, 0, 1] = np.inf
+    r, *_ = gpu_forward(sc, w["wh"], w["K"], w["Rt"], [0])
+    assert int(r.status.item()) & _lib.GS_FLAG_NONFINITE
+    nt = r.proj.n_tiles.cpu().numpy()
+    assert nt[5] == 0 and nt[9] == 0
+    keep = np.ones(300, bool)
+    keep[[5, 9]] = False
+    sc2 = {k: v[keep] for k, v in w["scene"].items()}
+    r2, *_ = gpu_forward(sc2, w["wh"], w["K"], w["Rt"], [0])
+    np.testing.assert_array_equal(r.image.cpu().numpy(), r2.image.cpu().numpy())
+
+
+def test_argument_errors_are_reported():
+    from paper_2603_04847_gb300 import Batch, Cameras, Gaussians, GsError, Projected, gs_project
+    from paper_2603_04847_gb300.core import new_status
+    w = synth.make_workload("tiny", n_gaussians=10)
+    g = Gaussians.from_numpy(w["scene"])
+    cams = Cameras.from_numpy(w["wh"], w["K"], w["Rt"])
+    b = Batch(cams, [0])
+    b.tile = 8
+    with pytest.raises(GsError, match="UNSUPPORTED"):
+        gs_project(g, cams, b, Projected(g.n, 1), new_status())
+    cams_bad = Cameras.from_numpy(w["wh"], w["K"], w["Rt"], near=-1.0)
+    with pytest.raises(GsError, match="GS_ERR_ARG"):
+        gs_project(g, cams_bad, Batch(cams, [0]), Projected(g.n, 1), new_status())
+    g.quat = torch.empty(g.n * 4 + 1, device="cuda")[1:].view(g.n, 4)  # misaligned
+    with pytest.raises(GsError, match="aligned"):
+        gs_project(g, cams, Batch(cams, [0]), Projected(g.n, 1), new_status())
+
+
+def _joint(mode, seed=0):
+    from paper_2603_04847_gb300 import Cameras, Gaussians, Hyper, JointStep
+    w = synth.make_workload("batched", n_gaussians=3000, n_views=5, width=(80, 160), height=(64, 120),
+                            n_tracks=200, seed=seed)
+    wh, K, Rt = w["wh"], w["K"], w["Rt"]
+    cams = Cameras.from_numpy(wh, K, Rt)
+    g = Gaussians.from_numpy(w["scene"])
+    tr = w["tracks"]
+    rng = np.random.default_rng(1)
+    xy = rng.uniform(10, 60, (len(tr["obs_point"]), 2))
+    P = (wh[:, 0] * wh[:, 1]).astype(np.int64)
+    off = np.concatenate([[0], np.cumsum(P)])
+    targets = torch.as_tensor(rng.uniform(0, 1, (int(off[-1]), 3)), dtype=torch.float32, device="cuda")
+    dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    js = JointStep(g, cams, dev(tr["X"], torch.float32), dev(tr["obs_point"], torch.int32),
+                   dev(xy, torch.float32), dev(tr["view_obs_offset"], torch.int64), targets, off,
+                   [4, 1, 3], Hyper(lambda_ba=0.1, lr_pose=1e-3, eps=1e-6), mode=mode)
+    js.ensure_capacity()
+    return js
+
+
+def _state(js):
+    return [t.detach().cpu().numpy().copy() for t in js.g.tensors() + [js.X, js.xi, js.Rt]]
+
+
+def test_graph_replay_matches_eager_and_plain():
+    eager = _joint("batched")
+    for _ in range(3):
+        eager.step()
+    torch.cuda.synchronize()
+    graphed = _joint("batched")
+    graphed.capture(warmup=0)   # capturing does not run the step
+    for _ in range(3):
+        graphed.run()
+    torch.cuda.synchronize()
+    plain = _joint("plain")
+    for _ in range(3):
+        plain.step()
+    torch.cuda.synchronize()
+    a, b, c = _state(eager), _state(graphed), _state(plain)
+    for x, y, z in zip(a, b, c):
+        np.testing.assert_allclose(y, x, rtol=1e-4, atol=1e-6)
+        np.testing.assert_allclose(z, x, rtol=1e-4, atol=1e-6)
+    assert eager.status_flags() == 0
+    assert int(eager.step_no.item()) == 3 and int(graphed.step_no.item()) == 3

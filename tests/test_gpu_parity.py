@@ -1,0 +1,320 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
+same seeded inputs.  Bars: bit-exact tile sets, sort order and ranges away
+from knife edges; images within 1e-4 relative L-inf; gradients within 1e-3
+relative (per tensor, normwise)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _gpu import (f32, gpu_backward, gpu_forward, knife_mask, oracle_cam, oracle_scene, pose_rel_err, rel_linf,
+                  scene32)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KNIFE_EPS = 1e-4
+GRAD_TOL = 1e-3
+IMG_TOL = 1e-4
+P = oracle.P
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_04847_gb300 import build
+    build.build()
+
+
+def oracle_rect_knife(proj, W, H, tile, eps=2e-4):
+    """Tile rectangles from the oracle's pixel rectangles and a flag for
+    records whose rectangle or visibility sits within rounding of a
+    decision boundary (a knife edge: either answer is valid).  The FP32
+    bounds carry ~3e-5 px of rounding at these image sizes."""
+    vis = proj[:, P["visible"]] > 0
+    px = proj[:, [P["px_x0"], P["px_y0"], P["px_x1"], P["px_y1"]]].astype(np.int64)
+    b = proj[:, [P["bound_x0"], P["bound_y0"], P["bound_x1"], P["bound_y1"]]]
+    near_int = np.abs(b - np.round(b)) < eps
+    knife = near_int.any(1) | (np.abs(proj[:, P["opacity"]] - 1 / 255) < 1e-6)
+    return vis, px // tile, knife
+
+
+def tiny():
+    w = synth.make_workload("tiny")
+    return w, w["scene"], w["wh"], w["K"], w["Rt"]
+
+
+def test_tiny_forward_image_matches_oracle():
+    w, sc, wh, K, Rt = tiny()
+    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, [0])
+    cam = oracle_cam(wh, K, Rt, 0)
+    ref = oracle.render(oracle_scene(sc), cam, knife_eps=KNIFE_EPS)
+    img = r.image.cpu().numpy().reshape(192, 256, 3)
+    T = r.T_final.cpu().numpy().reshape(192, 256)
+    ok = ~knife_mask(ref)
+    assert (~ok).mean() < 2e-3, "too many knife-edge pixels: %d" % (~ok).sum()
+    assert rel_linf(img[ok], ref["image"][ok]) <= IMG_TOL
+    assert np.abs(T[ok] - ref["T_final"][ok]).max() <= IMG_TOL
+    assert T.min() >= 1e-4 and T.max() <= 1.0
+
+
+def test_tiny_discrete_stage_bit_exact():
+    """Tile sets, per-tile order (depth, index) and ranges equal the
+    oracle's discrete stage (plain lexicographic sort of its own FP64
+    rectangles), away from knife edges."""
+    w, sc, wh, K, Rt = tiny()
+    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, [0])
+    cam = oracle_cam(wh, K, Rt, 0)
+    osc = oracle_scene(sc)
+    proj = oracle.project(osc, cam)
+    vis, trect, knife = oracle_rect_knife(proj, 256, 192, 16)
+    N = g.n
+    n_tiles = r.proj.n_tiles.cpu().numpy()[:N].astype(np.int64)
+    rect = r.proj.rect.cpu().numpy()[:N].astype(np.int64) & 0xFFFF
+    kvis = n_tiles > 0
+    sure = ~knife
+    assert knife.sum() <= max(5, N // 200), "knife-edge records: %d" % knife.sum()
+    np.testing.assert_array_equal(kvis[sure], vis[sure])
+    both = sure & vis
+    np.testing.assert_array_equal(rect[both], trect[both])
+    np.testing.assert_array_equal(n_tiles[both], ((trect[both, 2] - trect[both, 0] + 1) *
+                                                  (trect[both, 3] - trect[both, 1] + 1)))
+    # order within every tile
+    t_o, d_o, g_o = oracle.tile_lists(proj, 256, 192, 16)
+    keep = ~knife[g_o]
+    t_o, d_o, g_o = t_o[keep], d_o[keep], g_o[keep]
+    n_inst = r.n_instances()
+    vals = r.tl.vals.cpu().numpy()[:n_inst].astype(np.int64)
+    keys = r.tl.keys.cpu().numpy()[:n_inst]
+    ranges = r.tl.ranges.cpu().numpy().reshape(-1, 2).astype(np.int64)
+    ktile = (keys.view(np.uint64) >> np.uint64(32)).astype(np.int64)
+    assert np.all(np.diff(ktile) >= 0)
+    kk = ~knife[vals]
+    kt, kv = ktile[kk], vals[kk]
+    assert len(kt) == len(t_o)
+    np.testing.assert_array_equal(kt, t_o)
+    # ties in depth (FP32 rounding) may permute; compare exactly elsewhere
+    same = kv == g_o
+    if not same.all():
+        bad = np.nonzero(~same)[0]
+        for i in bad:
+            j1, j2 = kv[i], g_o[i]
+            assert abs(proj[j1, P["depth"]] - proj[j2, P["depth"]]) <= 1e-6 * proj[j1, P["depth"]]
+    # ranges agree with the per-tile counts
+    for t in range(ranges.shape[0]):
+        s, e = ranges[t]
+        assert np.all(ktile[s:e] == t)
+    counts_k = np.bincount(ktile, minlength=ranges.shape[0])
+    np.testing.assert_array_equal(ranges[:, 1] - ranges[:, 0], counts_k)
+
+
+def test_tiny_n_contrib_matches_oracle_positions():
+    w, sc, wh, K, Rt = tiny()
+    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, [0])
+    cam = oracle_cam(wh, K, Rt, 0)
+    ref = oracle.render(oracle_scene(sc), cam, knife_eps=KNIFE_EPS)
+    nc = r.n_contrib.cpu().numpy().reshape(192, 256)
+    vals = r.tl.vals.cpu().numpy().astype(np.int64)
+    ranges = r.tl.ranges.cpu().numpy().reshape(-1, 2)
+    ok = ~knife_mask(ref)
+    last = ref["last_id"]
+    checked = 0
+    for v in range(0, 192, 7):
+        for u in range(0, 256, 5):
+            if not ok[v, u]:
+                continue
+            t = (v // 16) * 16 + u // 16
+            s, e = ranges[t]
+            if last[v, u] < 0:
+                assert nc[v, u] == 0
+            else:
+                pos = np.nonzero(vals[s:e] == last[v, u])[0]
+                assert len(pos) == 1 and nc[v, u] == pos[0] + 1
+            checked += 1
+    assert checked > 1000
+
+
+def _compare_grads(got, ref, view=0, tol=GRAD_TOL):
+    for name in ("mean", "log_scale", "quat", "opacity_logit", "sh"):
+        e = rel_linf(got[name], ref[name])
+        assert e <= tol, "%s: %.3g" % (name, e)
+    e = pose_rel_err(got["tangent"][view], ref["tangent"], ref["tangent_abs"])
+    assert e <= tol, "pose tangent: %.3g" % e
+
+
+def test_tiny_backward_random_cotangent():
+    """dL/dparams and the pose tangent for L = <w, image> with a seeded
+    random w (knife-edge pixels zeroed on both sides)."""
+    w, sc, wh, K, Rt = tiny()
+    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, [0])
+    cam = oracle_cam(wh, K, Rt, 0)
+    osc = oracle_scene(sc)
+    ref = oracle.render(osc, cam, knife_eps=KNIFE_EPS)
+    rng = np.random.default_rng(10)
+    wv = f32(rng.normal(size=(192, 256, 3)))
+    wv[knife_mask(ref)] = 0.0
+    got = gpu_backward(r, g, v_image=wv.reshape(-1, 3))
+    exp = oracle.render_bwd(osc, cam, wv)
+    _compare_grads(got, exp)
+
+
+def test_tiny_backward_fused_l1():
+    """Fused L1 of Eq. 5 against a target rendered (by the oracle) from the
+    un-jittered scene: loss and all gradients."""
+    w, sc, wh, K, Rt = tiny()
+    cam = oracle_cam(wh, K, Rt, 0)
+    target = oracle.render(oracle_scene(w["gt"]), cam)["image"]
+    target = f32(target)
+    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, [0])
+    got = gpu_backward(r, g, target=target.reshape(-1, 3), l1_weight=0.8)
+    osc = oracle_scene(sc)
+    ref = oracle.render(osc, cam, knife_eps=KNIFE_EPS)
+    loss, v = oracle.l1_loss_grad(ref["image"], target, weight=0.8)
+    assert got["loss"] == pytest.approx(loss, rel=1e-4)
+    exp = oracle.render_bwd(osc, cam, v)
+    _compare_grads(got, exp)
+
+
+def small_batched(n=4000, views=4, seed=None):
+    return synth.make_workload("batched", n_gaussians=n, n_views=views, width=(90, 200), height=(70, 150),
+                               n_tracks=300, seed=seed)
+
+
+def test_batched_uneven_views_forward_backward():
+    """Several views of uneven, ragged resolution in one launch per stage:
+    images and gradients against the oracle view by view."""
+    w = small_batched()
+    sc, wh, K, Rt = w["scene"], w["wh"], w["K"], w["Rt"]
+    views = [2, 0, 3, 1]
+    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, views)
+    osc = oracle_scene(sc)
+    img = r.image.cpu().numpy()
+    rng = np.random.default_rng(3)
+    vfull = np.zeros_like(img, dtype=np.float64)
+    exp = None
+    for b, v in enumerate(views):
+        cam = oracle_cam(wh, K, Rt, v)
+        ref = oracle.render(osc, cam, knife_eps=KNIFE_EPS)
+        Wb, Hb = int(wh[v][0]), int(wh[v][1])
+        a = int(batch.px_offset_host[b])
+        ib = img[a:a + Wb * Hb].reshape(Hb, Wb, 3)
+        ok = ~knife_mask(ref)
+        assert rel_linf(ib[ok], ref["image"][ok]) <= IMG_TOL
+        wv = f32(rng.normal(size=(Hb, Wb, 3)))
+        wv[~ok] = 0.0
+        vfull[a:a + Wb * Hb] = wv.reshape(-1, 3)
+        e = oracle.render_bwd(osc, cam, wv)
+        tan = np.zeros((len(wh), 6))
+        tan[v] = e["tangent"]
+        e["tangent"] = tan
+        tab = np.zeros((len(wh), 6))
+        tab[v] = e["tangent_abs"]
+        e["tangent_abs"] = tab
+        if exp is None:
+            exp = e
+        else:
+            for k in ("mean", "log_scale", "quat", "opacity_logit", "sh", "tangent", "tangent_abs"):
+                exp[k] = exp[k] + e[k]
+    got = gpu_backward(r, g, v_image=vfull)
+    for k in ("mean", "log_scale", "quat", "opacity_logit", "sh"):
+        assert rel_linf(got[k], exp[k]) <= GRAD_TOL, k
+    for v in views:
+        assert pose_rel_err(got["tangent"][v], exp["tangent"][v], exp["tangent_abs"][v]) <= GRAD_TOL
+
+
+def test_batched_equals_plain_per_view():
+    """The batched launch and one-view-per-launch give identical images and
+    tile lists (same records, same order)."""
+    w = small_batched(seed=7)
+    sc, wh, K, Rt = w["scene"], w["wh"], w["K"], w["Rt"]
+    views = [0, 1, 2, 3]
+    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, views)
+    img = r.image.cpu().numpy()
+    for b, v in enumerate(views):
+        rp, *_ = gpu_forward(sc, wh, K, Rt, [v])
+        a, e = int(batch.px_offset_host[b]), int(batch.px_offset_host[b + 1])
+        np.testing.assert_array_equal(img[a:e], rp.image.cpu().numpy())
+
+
+def test_track_term_matches_oracle():
+    w = synth.make_workload("train", n_gaussians=20000, n_views=12, n_tracks=2000)
+    wh, K, Rt = w["wh"], w["K"], w["Rt"]
+    tr = w["tracks"]
+    cams_o = [oracle_cam(wh, K, Rt, v) for v in range(len(wh))]
+    X = f32(tr["X"])
+    xy = np.zeros((len(tr["obs_point"]), 2))
+    for i, (k, v) in enumerate(zip(tr["obs_point"], tr["obs_view"])):
+        uv, _ = oracle.project_points(X[k:k + 1], cams_o[v])
+        xy[i] = uv[0] + tr["noise"][i]
+        if tr["outlier"][i]:
+            xy[i] = tr["outlier_uv01"][i] * wh[v]
+    xy = f32(xy)
+    views = [3, 7, 0, 11, 5]
+    sel = np.isin(tr["obs_view"], views)
+    lo, gX, tan, masked, tabs = oracle.track(X, tr["obs_point"][sel], tr["obs_view"][sel], xy[sel], cams_o,
+                                             delta=1.0, weight=0.1, with_abs=True)
+    from paper_2603_04847_gb300 import Batch, Cameras, track_reproj_fwd_bwd
+    from paper_2603_04847_gb300.core import track_workspace_bytes
+    cams = Cameras.from_numpy(wh, K, Rt)
+    batch = Batch(cams, views)
+    dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    Xt = dev(X, torch.float32)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    gXt = torch.zeros_like(Xt)
+    gt = torch.zeros((len(wh), 6), dtype=torch.float64, device="cuda")
+    nm = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(track_workspace_bytes(batch), dtype=torch.uint8, device="cuda")
+    track_reproj_fwd_bwd(Xt, dev(tr["obs_point"], torch.int32), dev(xy, torch.float32),
+                         dev(tr["view_obs_offset"], torch.int64), cams, batch, 1.0, 0.1, loss, gXt, gt, nm, ws)
+    torch.cuda.synchronize()
+    assert loss.item() == pytest.approx(lo, rel=1e-5)
+    assert rel_linf(gXt.cpu().numpy(), gX) <= GRAD_TOL
+    got_t = gt.cpu().numpy()
+    for v in views:
+        assert pose_rel_err(got_t[v], tan[v], tabs[v]) <= GRAD_TOL
+    assert int(nm.item()) == masked
+
+
+def test_pose_update_and_adam_match_oracle():
+    from paper_2603_04847_gb300.core import adam_c, gs_adam_update, pose_se3_update
+    rng = np.random.default_rng(4)
+    V = 37
+    from scipy.spatial.transform import Rotation
+    T0 = np.zeros((V, 12))
+    T0[:, :9] = Rotation.from_rotvec(rng.normal(0, 1, (V, 3))).as_matrix().reshape(V, 9)
+    T0[:, 9:] = rng.normal(0, 2, (V, 3))
+    T0 = f32(T0)
+    xi = f32(np.concatenate([rng.normal(0, 0.05, (V, 3)), rng.normal(0, 0.05, (V, 3))], 1))
+    xi[0] = 0.0
+    xi[1, 3:] = [1e-6, -2e-6, 5e-7]  # series branch
+    gtan = rng.normal(0, 1, (V, 6))
+    m = f32(rng.normal(0, 0.1, (V, 6)))
+    v = f32(np.abs(rng.normal(0, 0.1, (V, 6))))
+    step = 5
+    xo, mo, vo = xi.copy(), m.copy(), v.copy()
+    g_xi_o, Rt_o = oracle.pose_update(T0, xo, gtan, mo, vo, lr=1e-3, step=step)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+    T0t, xt, mt, vt = dev(T0), dev(xi), dev(m), dev(v)
+    gt = torch.as_tensor(gtan, dtype=torch.float64, device="cuda")
+    gx = torch.zeros_like(xt)
+    Rt = torch.zeros_like(T0t)
+    st = torch.tensor([step], dtype=torch.int32, device="cuda")
+    pose_se3_update(T0t, xt, gt, gx, mt, vt, adam_c(1e-3, 0.9, 0.999, 1e-15, st), Rt)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(gx.cpu().numpy(), g_xi_o, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(xt.cpu().numpy(), xo, rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(Rt.cpu().numpy(), Rt_o, rtol=1e-5, atol=2e-6)
+    # elementwise Adam
+    n = 100003
+    p, g, mm, vv = (f32(rng.normal(size=n)) for _ in range(4))
+    vv = np.abs(vv)
+    po, mo2, vo2 = p.copy(), mm.copy(), vv.copy()
+    oracle.adam(po, g, mo2, vo2, 5e-3, 0.9, 0.999, 1e-15, 3)
+    pt, mt2, vt2 = dev(p), dev(mm), dev(vv)
+    st[0] = 3
+    gs_adam_update(pt, dev(g), mt2, vt2, adam_c(5e-3, 0.9, 0.999, 1e-15, st))
+    torch.cuda.synchronize()
+    # inputs are O(1): FP32 rounding of the moment updates is ~1e-7 absolute
+    np.testing.assert_allclose(pt.cpu().numpy(), po, rtol=1e-5, atol=3e-7)
+    np.testing.assert_allclose(mt2.cpu().numpy(), mo2, rtol=1e-5, atol=3e-7)
