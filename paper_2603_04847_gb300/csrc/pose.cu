@@ -3,7 +3,7 @@
 //    adjustment"), the SE(3) gradient map g_xi = Jl(xi)^T g_tangent with the
 //    closed-form left Jacobian of SE(3) (Barfoot, State Estimation for
 //    Robotics), and an Adam step on xi (Sec. 3.3: Adam, lr 1e-5).  One
-//    thread per camera, double precision.
+//    thread per camera; FP32 except for the series coefficients.
 //  - Adam on parameter arrays (Algorithm 1, "Update Gaussians" / "Update
 //    track points"), elementwise and HBM-bound.
 //  - the fixed-order sum of per-block pose partials used by the projection
@@ -14,31 +14,49 @@ namespace gs {
 
 namespace {
 
-__device__ inline void skew(const double* w, double* S) {
-  S[0] = 0.0;   S[1] = -w[2]; S[2] = w[1];
-  S[3] = w[2];  S[4] = 0.0;   S[5] = -w[0];
-  S[6] = -w[1]; S[7] = w[0];  S[8] = 0.0;
+__device__ inline void skew(const float* w, float* S) {
+  S[0] = 0.f;   S[1] = -w[2]; S[2] = w[1];
+  S[3] = w[2];  S[4] = 0.f;   S[5] = -w[0];
+  S[6] = -w[1]; S[7] = w[0];  S[8] = 0.f;
 }
 
-__device__ inline void mm3(const double* A, const double* B, double* C) {
+__device__ inline void mm3(const float* A, const float* B, float* C) {
+#pragma unroll
   for (int r = 0; r < 3; ++r)
+#pragma unroll
     for (int c = 0; c < 3; ++c)
       C[3 * r + c] = A[3 * r] * B[c] + A[3 * r + 1] * B[3 + c] + A[3 * r + 2] * B[6 + c];
 }
 
-// sin(th)/th, (1-cos th)/th^2, (th - sin th)/th^3 with series near 0.
-__device__ inline void so3_series(double th, double& A, double& B, double& C) {
-  if (th < 1e-4) {
-    const double t2 = th * th;
-    A = 1.0 - t2 / 6.0 + t2 * t2 / 120.0;
-    B = 0.5 - t2 / 24.0 + t2 * t2 / 720.0;
-    C = 1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0;
+// Scalar coefficients of Exp and of the SE(3) left Jacobian for angle th:
+// A = sin th / th, B = (1 - cos th) / th^2, C = (th - sin th) / th^3 and the
+// Q-block coefficients c2 = (th^2 + 2 cos th - 2) / (2 th^4),
+// c3 = (2 th - 3 sin th + th cos th) / (2 th^5) (c1 = C).  They cancel badly
+// in single precision, so they alone are formed in double (one sincos);
+// Taylor series near 0.
+struct Se3Coef {
+  float A, B, C, c2, c3;
+};
+
+__device__ inline Se3Coef se3_coef(double th) {
+  Se3Coef k;
+  const double t2 = th * th;
+  if (th < 1e-3) {
+    k.A = (float)(1.0 - t2 / 6.0 + t2 * t2 / 120.0);
+    k.B = (float)(0.5 - t2 / 24.0 + t2 * t2 / 720.0);
+    k.C = (float)(1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0);
+    k.c2 = (float)(1.0 / 24.0 - t2 / 720.0 + t2 * t2 / 40320.0);
+    k.c3 = (float)(1.0 / 120.0 - t2 / 2520.0);
   } else {
-    const double s = sin(th), c = cos(th);
-    A = s / th;
-    B = (1.0 - c) / (th * th);
-    C = (th - s) / (th * th * th);
+    double s, c;
+    sincos(th, &s, &c);
+    k.A = (float)(s / th);
+    k.B = (float)((1.0 - c) / t2);
+    k.C = (float)((th - s) / (t2 * th));
+    k.c2 = (float)((t2 + 2.0 * c - 2.0) / (2.0 * t2 * t2));
+    k.c3 = (float)((2.0 * th - 3.0 * s + th * c) / (2.0 * t2 * t2 * th));
   }
+  return k;
 }
 
 __global__ void pose_update_kernel(int V, const float* __restrict__ T0, float* __restrict__ xi,
@@ -48,33 +66,21 @@ __global__ void pose_update_kernel(int V, const float* __restrict__ T0, float* _
                                    const int32_t* __restrict__ step, float* __restrict__ Rt_out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V) return;
-  double x[6];
-  for (int c = 0; c < 6; ++c) x[c] = (double)xi[6 * i + c];
-  const double* rho = x;
-  const double* phi = x + 3;
-  const double th = sqrt(phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2]);
-  double A, B, C;
-  so3_series(th, A, B, C);
-  // Q-block coefficients of the SE(3) left Jacobian
-  double c1, c2, c3;
-  if (th < 1e-3) {
-    const double t2 = th * th;
-    c1 = 1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0;
-    c2 = 1.0 / 24.0 - t2 / 720.0 + t2 * t2 / 40320.0;
-    c3 = 1.0 / 120.0 - t2 / 2520.0;
-  } else {
-    const double s = sin(th), c = cos(th), t2 = th * th;
-    c1 = (th - s) / (t2 * th);
-    c2 = (t2 + 2.0 * c - 2.0) / (2.0 * t2 * t2);
-    c3 = (2.0 * th - 3.0 * s + th * c) / (2.0 * t2 * t2 * th);
-  }
-  double P[9], Rh[9], P2[9];
+  float x[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) x[c] = xi[6 * i + c];
+  const float* rho = x;
+  const float* phi = x + 3;
+  const double th = sqrt((double)phi[0] * phi[0] + (double)phi[1] * phi[1] + (double)phi[2] * phi[2]);
+  Se3Coef k = se3_coef(th);
+  float P[9], Rh[9], P2[9];
   skew(phi, P);
   skew(rho, Rh);
   mm3(P, P, P2);
-  double Jl[9];
-  for (int k = 0; k < 9; ++k) Jl[k] = ((k % 4) == 0 ? 1.0 : 0.0) + B * P[k] + C * P2[k];
-  double PR[9], RP[9], PRP[9], PPR[9], RPP[9], PRPP[9], PPRP[9], Q[9];
+  float Jl[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) Jl[e] = ((e % 4) == 0 ? 1.f : 0.f) + k.B * P[e] + k.C * P2[e];
+  float PR[9], RP[9], PRP[9], PPR[9], RPP[9], PRPP[9], PPRP[9], Q[9];
   mm3(P, Rh, PR);
   mm3(Rh, P, RP);
   mm3(PR, P, PRP);
@@ -82,57 +88,67 @@ __global__ void pose_update_kernel(int V, const float* __restrict__ T0, float* _
   mm3(RP, P, RPP);
   mm3(PRP, P, PRPP);
   mm3(P, PRP, PPRP);
-  for (int k = 0; k < 9; ++k)
-    Q[k] = 0.5 * Rh[k] + c1 * (PR[k] + RP[k] + PRP[k]) + c2 * (PPR[k] + RPP[k] - 3.0 * PRP[k]) +
-           c3 * (PRPP[k] + PPRP[k]);
+#pragma unroll
+  for (int e = 0; e < 9; ++e)
+    Q[e] = 0.5f * Rh[e] + k.C * (PR[e] + RP[e] + PRP[e]) + k.c2 * (PPR[e] + RPP[e] - 3.f * PRP[e]) +
+           k.c3 * (PRPP[e] + PPRP[e]);
   // g_xi = Jl^T g with Jl = [[Jl, Q], [0, Jl]]
-  const double* g = g_tangent + 6 * i;
-  double gx[6];
+  const double* gd = g_tangent + 6 * i;
+  float g[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) g[c] = (float)gd[c];
+  float gx[6];
+#pragma unroll
   for (int c = 0; c < 3; ++c) {
     gx[c] = Jl[c] * g[0] + Jl[3 + c] * g[1] + Jl[6 + c] * g[2];
     gx[3 + c] = Q[c] * g[0] + Q[3 + c] * g[1] + Q[6 + c] * g[2] + Jl[c] * g[3] + Jl[3 + c] * g[4] +
                 Jl[6 + c] * g[5];
   }
   if (g_xi)
-    for (int c = 0; c < 6; ++c) g_xi[6 * i + c] = (float)gx[c];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) g_xi[6 * i + c] = gx[c];
   if (use_adam) {
-    const int t = *step;
-    const double bc1 = 1.0 - pow((double)beta1, (double)t);
-    const double bc2 = 1.0 - pow((double)beta2, (double)t);
+    const float t = (float)*step;
+    const float bc1 = 1.f - exp2f(t * log2f(beta1));
+    const float bc2 = 1.f - exp2f(t * log2f(beta2));
+#pragma unroll
     for (int c = 0; c < 6; ++c) {
-      const double mm = (double)beta1 * m[6 * i + c] + (1.0 - (double)beta1) * gx[c];
-      const double vv = (double)beta2 * v[6 * i + c] + (1.0 - (double)beta2) * gx[c] * gx[c];
-      m[6 * i + c] = (float)mm;
-      v[6 * i + c] = (float)vv;
-      const double upd = (double)lr * (mm / bc1) / (sqrt(vv / bc2) + (double)eps);
-      const float nx = (float)(x[c] - upd);
-      xi[6 * i + c] = nx;
-      x[c] = (double)nx;
+      const float mm = beta1 * m[6 * i + c] + (1.f - beta1) * gx[c];
+      const float vv = beta2 * v[6 * i + c] + (1.f - beta2) * gx[c] * gx[c];
+      m[6 * i + c] = mm;
+      v[6 * i + c] = vv;
+      x[c] -= lr * (mm / bc1) / (sqrtf(vv / bc2) + eps);
+      xi[6 * i + c] = x[c];
     }
+    const double th2 = sqrt((double)x[3] * x[3] + (double)x[4] * x[4] + (double)x[5] * x[5]);
+    k = se3_coef(th2);
+    skew(x + 3, P);
+    mm3(P, P, P2);
   }
   // Rt_out = Exp(xi) T0
-  const double th2 = sqrt(x[3] * x[3] + x[4] * x[4] + x[5] * x[5]);
-  so3_series(th2, A, B, C);
-  skew(x + 3, P);
-  mm3(P, P, P2);
-  double ER[9], EV[9];
-  for (int k = 0; k < 9; ++k) {
-    const double I = (k % 4) == 0 ? 1.0 : 0.0;
-    ER[k] = I + A * P[k] + B * P2[k];
-    EV[k] = I + B * P[k] + C * P2[k];
+  float ER[9], EV[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    const float I = (e % 4) == 0 ? 1.f : 0.f;
+    ER[e] = I + k.A * P[e] + k.B * P2[e];
+    EV[e] = I + k.B * P[e] + k.C * P2[e];
   }
-  double Et[3];
+  float Et[3];
+#pragma unroll
   for (int r = 0; r < 3; ++r) Et[r] = EV[3 * r] * x[0] + EV[3 * r + 1] * x[1] + EV[3 * r + 2] * x[2];
   const float* T = T0 + 12 * i;
-  double R0[9], t0[3];
-  for (int k = 0; k < 9; ++k) R0[k] = T[k];
-  for (int k = 0; k < 3; ++k) t0[k] = T[9 + k];
-  double R[9];
+  float R0[9], t0[3];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) R0[e] = T[e];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) t0[e] = T[9 + e];
+  float R[9];
   mm3(ER, R0, R);
   float* out = Rt_out + 12 * i;
-  for (int k = 0; k < 9; ++k) out[k] = (float)R[k];
-  for (int r = 0; r < 3; ++r)
-    out[9 + r] = (float)(ER[3 * r] * t0[0] + ER[3 * r + 1] * t0[1] + ER[3 * r + 2] * t0[2] + Et[r]);
+#pragma unroll
+  for (int e = 0; e < 9; ++e) out[e] = R[e];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) out[9 + r] = ER[3 * r] * t0[0] + ER[3 * r + 1] * t0[1] + ER[3 * r + 2] * t0[2] + Et[r];
 }
 
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,

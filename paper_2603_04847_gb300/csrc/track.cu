@@ -87,17 +87,25 @@ __global__ void __launch_bounds__(256) track_kernel(const float* __restrict__ X,
       const bool in_range = (unsigned)k < (unsigned)n_points;
       const size_t kk = in_range ? (size_t)k : 0;
       const float Xw0 = X[3 * kk], Xw1 = X[3 * kk + 1], Xw2 = X[3 * kk + 2];
-      float Xc[3];
+      // The projection and residual are formed in double: the residual is a
+      // difference of two pixel coordinates of order 1e3 whose FP32 rounding
+      // (~1e-4 px) would otherwise dominate the cancelling pose sum.  A few
+      // dozen FP64 operations per observation cost nothing here.
+      double Xd[3];
 #pragma unroll
-      for (int r = 0; r < 3; ++r) Xc[r] = c.R[3 * r] * Xw0 + c.R[3 * r + 1] * Xw1 + c.R[3 * r + 2] * Xw2 + c.t[r];
+      for (int r = 0; r < 3; ++r)
+        Xd[r] = (double)c.R[3 * r] * Xw0 + (double)c.R[3 * r + 1] * Xw1 + (double)c.R[3 * r + 2] * Xw2 +
+                (double)c.t[r];
+      float Xc[3] = {(float)Xd[0], (float)Xd[1], (float)Xd[2]};
       if (!in_range) {
         // observation of a point that does not exist: ignored
-      } else if (Xc[2] <= cams.near_plane) {
+      } else if (Xd[2] <= (double)cams.near_plane) {
         ++masked;
       } else {
-        const float iz = 1.f / Xc[2];
-        const float rx = c.fx * Xc[0] * iz + c.cx - xy.x;
-        const float ry = c.fy * Xc[1] * iz + c.cy - xy.y;
+        const double izd = 1.0 / Xd[2];
+        const float rx = (float)((double)c.fx * Xd[0] * izd + (double)c.cx - (double)xy.x);
+        const float ry = (float)((double)c.fy * Xd[1] * izd + (double)c.cy - (double)xy.y);
+        const float iz = (float)izd;
         const float s = rx * rx + ry * ry;
         float rho, drho;
         if (s <= d2) {
