@@ -278,6 +278,37 @@ gs_status track_reproj_fwd_bwd(const float* X, int32_t n_points,
                                gs_stream stream);
 
 /*
+ * track_reproj_fwd_bwd_static — the same computation as track_reproj_fwd_bwd
+ * with the same arguments except `ws`/`ws_bytes`: it allocates nothing and
+ * needs no workspace from the caller.  The paper has no counterpart; this
+ * entry point exists for callers that cannot allocate device memory when they
+ * run the track term: real-time loops that must not risk the implicit device
+ * synchronisation an allocation can cause, plug-ins that live inside a host
+ * framework's memory pool and may not allocate outside it, and processes that
+ * reserve all device memory up front.
+ * Its scratch (the per-block pose partials) is a 1 MiB array in device
+ * memory owned by the library; every GPU that loads the library keeps it
+ * until the process exits.  A batch whose partials need more than 1 MiB
+ * (2 x SM count x B x 48 bytes; never on GPUs with up to 170 SMs) is
+ * rejected with GS_ERR_CAPACITY.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current and
+ * caches it; make that first call before any stream capture.  All calls
+ * share the one array and it keeps the last call's contents (every call
+ * overwrites all the partials it reads, so nothing needs clearing): calls
+ * that overlap on the GPU, on different streams or devices sharing the
+ * process, race on it and must be serialised by the caller.
+ */
+gs_status track_reproj_fwd_bwd_static(const float* X, int32_t n_points,
+                                      const int32_t* obs_point,
+                                      const float* obs_xy,
+                                      const int64_t* view_obs_offset,
+                                      const gs_cameras* cams,
+                                      const gs_batch* batch, float delta,
+                                      float weight, double* loss,
+                                      float* grad_X, double* g_pose_tangent,
+                                      uint32_t* n_masked, gs_stream stream);
+
+/*
  * pose_se3_update — pose composition of Algorithm 1 (T_i = T_i^(0) (+)
  * dT_i, read as T_i = Exp(xi_i) T_i^(0), xi = (rho, phi)) and the pose
  * step ("Update poses"; Sec. 3.3: Adam, learning rate 1e-5).  For every

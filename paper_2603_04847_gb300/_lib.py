@@ -78,6 +78,9 @@ PROTOTYPES = {
     "track_reproj_fwd_bwd": (ctypes.c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                             c_void_p, c_float, c_float, c_void_p, c_void_p, c_void_p,
                                             c_void_p, c_void_p, c_size_t, c_void_p]),
+    "track_reproj_fwd_bwd_static": (ctypes.c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p,
+                                                   c_void_p, c_void_p, c_float, c_float, c_void_p, c_void_p,
+                                                   c_void_p, c_void_p, c_void_p]),
     "pose_se3_update": (ctypes.c_int, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                        c_void_p, c_void_p, c_void_p]),
     "gs_adam_update": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),

@@ -270,6 +270,20 @@ def track_reproj_fwd_bwd(X, obs_point, obs_xy, view_obs_offset, cams: Cameras, b
                                    _stream(stream)), "track_reproj_fwd_bwd")
 
 
+def track_reproj_fwd_bwd_static(X, obs_point, obs_xy, view_obs_offset, cams: Cameras, batch: Batch,
+                                delta: float, weight: float, loss, grad_X, g_pose_tangent, n_masked, Rt=None,
+                                stream=None):
+    """The track term with the library's own fixed scratch instead of a
+    caller workspace (for callers that cannot allocate device memory)."""
+    lib = _lib.load()
+    _need_cuda(X, obs_point, obs_xy, view_obs_offset, loss, grad_X, g_pose_tangent, n_masked)
+    cc, bc = cams.c(Rt), batch.c()
+    check(lib.track_reproj_fwd_bwd_static(_p(X), X.shape[0], _p(obs_point), _p(obs_xy), _p(view_obs_offset),
+                                          ctypes.byref(cc), ctypes.byref(bc), float(delta), float(weight),
+                                          _p(loss), _p(grad_X), _p(g_pose_tangent), _p(n_masked),
+                                          _stream(stream)), "track_reproj_fwd_bwd_static")
+
+
 def adam_c(lr, beta1, beta2, eps, step: torch.Tensor):
     return _lib.gs_adam(float(lr), float(beta1), float(beta2), float(eps), step.data_ptr())
 

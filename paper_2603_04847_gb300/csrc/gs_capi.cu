@@ -314,3 +314,32 @@ gs_status gs_zero(void* ptr, size_t bytes, gs_stream stream) {
 }
 
 }  // extern "C"
+
+namespace gs {
+
+// Shared helpers for entry points defined in other translation units.
+gs_status record_error(gs_status code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+gs_status check_track_call(const float* X, int32_t n_points, const int32_t* obs_point, const float* obs_xy,
+                           const int64_t* view_obs_offset, const gs_cameras* cams, const gs_batch* batch,
+                           float delta, float weight, const float* grad_X, const double* g_pose_tangent,
+                           const char* who) {
+  gs_status s;
+  if ((s = check_cameras(cams)) || (s = check_batch(batch))) return s;
+  if (n_points < 0 || !view_obs_offset || !grad_X || !g_pose_tangent)
+    return fail(GS_ERR_ARG, "%s: null argument", who);
+  if (n_points > 0 && (!X || !obs_point || !obs_xy)) return fail(GS_ERR_ARG, "%s: null array", who);
+  if (obs_xy && !aligned(obs_xy, 8)) return fail(GS_ERR_ARG, "%s: obs_xy must be 8-byte aligned", who);
+  if (!std::isfinite(delta) || !std::isfinite(weight))
+    return fail(GS_ERR_NONFINITE, "%s: non-finite delta/weight", who);
+  if (!(delta > 0.f)) return fail(GS_ERR_ARG, "%s: delta must be > 0", who);
+  return GS_OK;
+}
+
+}  // namespace gs

@@ -54,4 +54,12 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n,
                         cudaStream_t st);
 cudaError_t launch_step_advance(int32_t* step, cudaStream_t st);
 
+// Error reporting and argument checks shared with entry points outside
+// gs_capi.cu.
+gs_status record_error(gs_status code, const char* fmt, ...);
+gs_status check_track_call(const float* X, int32_t n_points, const int32_t* obs_point, const float* obs_xy,
+                           const int64_t* view_obs_offset, const gs_cameras* cams, const gs_batch* batch,
+                           float delta, float weight, const float* grad_X, const double* g_pose_tangent,
+                           const char* who);
+
 }  // namespace gs

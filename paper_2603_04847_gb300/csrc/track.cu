@@ -8,6 +8,8 @@
 // scalar atomics; a track has few observations, so they rarely collide),
 // and its pose-tangent share is reduced warp -> block (shared double) ->
 // per-block partial, summed in block order by a second kernel.
+#include <mutex>
+
 #include "gs_internal.h"
 
 namespace gs {
@@ -191,3 +193,75 @@ cudaError_t launch_track(const float* X, int n_points, const int32_t* obs_point,
 }
 
 }  // namespace gs
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of track_reproj_fwd_bwd.
+//
+// Some callers cannot call cudaMalloc when they run this term: real-time
+// loops that must not risk the implicit device synchronisation an allocation
+// can cause, plug-ins that live inside a host framework's memory pool and may
+// not allocate outside it, and processes that reserve all device memory up
+// front.  For them the per-block pose partials go to a fixed array in device
+// memory that belongs to this library.
+
+// 1 MiB of scratch: enough for the partials of 2 * SMs blocks x 64 views x 6
+// doubles on GPUs with up to 170 SMs.  Every GPU that loads the library
+// keeps this array until the process exits.
+#define GS_TRACK_STATIC_SCRATCH_BYTES (1u << 20)
+static __device__ __align__(256) double gs_track_static_scratch[GS_TRACK_STATIC_SCRATCH_BYTES / sizeof(double)];
+
+namespace gs {
+namespace {
+
+std::mutex g_track_scratch_mu;
+void* g_track_scratch_ptr[64] = {nullptr};
+
+// Device address of the scratch array on the current device.  Host code
+// cannot pass the symbol itself to a kernel (on the host it names a host-side
+// stand-in); the address is looked up once per device and cached.
+cudaError_t track_static_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_track_scratch_mu);
+  if (g_track_scratch_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, gs_track_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_track_scratch_ptr[dev] = p;
+  }
+  *out = g_track_scratch_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+}  // namespace gs
+
+extern "C" gs_status track_reproj_fwd_bwd_static(const float* X, int32_t n_points, const int32_t* obs_point,
+                                                 const float* obs_xy, const int64_t* view_obs_offset,
+                                                 const gs_cameras* cams, const gs_batch* batch, float delta,
+                                                 float weight, double* loss, float* grad_X,
+                                                 double* g_pose_tangent, uint32_t* n_masked,
+                                                 gs_stream stream) {
+  using namespace gs;
+  const char* who = "track_reproj_fwd_bwd_static";
+  gs_status s = check_track_call(X, n_points, obs_point, obs_xy, view_obs_offset, cams, batch, delta,
+                                 weight, grad_X, g_pose_tangent, who);
+  if (s != GS_OK) return s;
+  const size_t need = track_workspace_bytes(*batch);
+  if (need > GS_TRACK_STATIC_SCRATCH_BYTES)
+    return record_error(GS_ERR_CAPACITY,
+                        "%s: this batch needs %zu bytes of scratch, more than the %u-byte static array; "
+                        "use track_reproj_fwd_bwd with a caller workspace",
+                        who, need, (unsigned)GS_TRACK_STATIC_SCRATCH_BYTES);
+  void* ws = nullptr;
+  cudaError_t e = track_static_scratch(&ws);
+  if (e != cudaSuccess) return record_error(GS_ERR_CUDA, "%s: scratch address: %s", who, cudaGetErrorString(e));
+  e = launch_track(X, n_points, obs_point, obs_xy, view_obs_offset, *cams, *batch, delta, weight, loss, grad_X,
+                   g_pose_tangent, n_masked, ws, (cudaStream_t)stream);
+  if (e != cudaSuccess) return record_error(GS_ERR_CUDA, "%s: %s", who, cudaGetErrorString(e));
+  return GS_OK;
+}
+
