@@ -380,11 +380,12 @@ def run_ours(args):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    stages = {k: dict(ms=st_ms.get(k, 0.0)) for k in model}
+    stages = {k: dict(ms=st_ms.get(k, 0.0)) for k in list(model) + [k for k in st_ms if k not in model]}
     for k in stages:
         t = stages[k]["ms"]
-        stages[k]["GBps"] = model[k] / (t * 1e-3) / 1e9 if t > 0 else None
-        stages[k]["hbm_frac"] = stages[k]["GBps"] / hbm_peak if t > 0 else None
+        if k in model and t > 0:
+            stages[k]["GBps"] = model[k] / (t * 1e-3) / 1e9
+            stages[k]["hbm_frac"] = stages[k]["GBps"] / hbm_peak
     dominant = max(("project", "sort", "render_fwd", "raster_bwd", "project_bwd"), key=lambda k: st_ms.get(k, 0))
     # the compositing kernels are bound by FP32/SFU issue, not HBM: report
     # their pair throughput against the FP32 lane peak

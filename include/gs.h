@@ -172,23 +172,24 @@ gs_status gs_project(const gs_gaussians* g, const gs_cameras* cams,
                      int32_t* status, gs_stream stream);
 
 /*
- * gs_sort_tiles — per-tile duplication and depth ordering.  Exclusive scan
- * of n_tiles over r = b*N + j, then one instance per (record, covered tile)
- * with key (global tile << 32 | float bits of depth) and value r, then a
- * stable LSD radix sort over the significant key bits, so that every tile's
- * list is ordered by (depth, j).  ranges[2*t], ranges[2*t+1] = [start, end)
- * of global tile t in the sorted list (0, 0 when empty).  The full instance
- * count (saturated at 2^32 - 1) is written to n_instances (device) and never
- * read back by the library, so the call can be captured in a CUDA graph.  If
- * it exceeds `capacity`, GS_FLAG_CAPACITY is set and only the first
- * `capacity` instances (in record order) are sorted and rendered.
- * keys/vals: [capacity]; ranges: [2 * batch->n_tiles]; ws: see query.
+ * gs_sort_tiles — per-tile duplication and depth ordering.  A stable sort
+ * of the B*N records r = b*N + j by camera depth (ties in record order),
+ * an exclusive scan of n_tiles in that order, one instance (global tile, r)
+ * per covered tile, and a stable sort of the instances by tile id, so that
+ * every tile's list is ordered by (depth, j).  Outputs: tiles[i], vals[i] =
+ * tile id and record of sorted instance i; ranges[2*t], ranges[2*t+1] =
+ * [start, end) of global tile t (0, 0 when empty).  The full instance count
+ * (saturated at 2^32 - 1) is written to n_instances (device) and never read
+ * back by the library, so the call can be captured in a CUDA graph.  If it
+ * exceeds `capacity`, GS_FLAG_CAPACITY is set and only the first `capacity`
+ * instances (in depth order) are sorted and rendered; re-run with more.
+ * tiles/vals: [capacity] uint32; ranges: [2 * batch->n_tiles]; ws: see query.
  */
 gs_status gs_sort_tiles_workspace(int32_t n_gaussians, const gs_batch* batch,
                                   size_t capacity, size_t* ws_bytes);
 gs_status gs_sort_tiles(int32_t n_gaussians, const gs_cameras* cams,
                         const gs_batch* batch,
-                        const gs_projected* proj, uint64_t* keys,
+                        const gs_projected* proj, uint32_t* tiles,
                         uint32_t* vals, size_t capacity, uint32_t* ranges,
                         uint32_t* n_instances, void* ws, size_t ws_bytes,
                         int32_t* status, gs_stream stream);

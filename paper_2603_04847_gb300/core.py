@@ -158,13 +158,13 @@ class Projected:
 
 
 class TileLists:
-    """Sorted tile instances: keys [cap] u64, vals [cap] u32, ranges
-    [2*n_tiles] u32, n_instances [1] u32, sort workspace."""
+    """Sorted tile instances: tiles [cap] u32 (tile id), vals [cap] u32
+    (record), ranges [2*n_tiles] u32, n_instances [1] u32, sort workspace."""
 
     def __init__(self, n: int, batch: Batch, capacity: int, device="cuda"):
         lib = _lib.load()
         self.capacity = int(capacity)
-        self.keys = torch.empty(self.capacity, dtype=torch.int64, device=device)
+        self.tiles = torch.empty(self.capacity, dtype=torch.int32, device=device)
         self.vals = torch.empty(self.capacity, dtype=torch.int32, device=device)
         self.ranges = torch.zeros(max(2 * batch.n_tiles, 2), dtype=torch.int32, device=device)
         self.n_instances = torch.zeros(1, dtype=torch.int32, device=device)
@@ -195,7 +195,7 @@ def gs_sort_tiles(n: int, cams: Cameras, batch: Batch, proj: Projected, tl: Tile
                   Rt: torch.Tensor = None, stream=None):
     lib = _lib.load()
     cc, bc, pc = cams.c(Rt), batch.c(), proj.c()
-    check(lib.gs_sort_tiles(n, ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc), _p(tl.keys), _p(tl.vals),
+    check(lib.gs_sort_tiles(n, ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc), _p(tl.tiles), _p(tl.vals),
                             tl.capacity, _p(tl.ranges), _p(tl.n_instances), _p(tl.ws), tl.ws.numel(),
                             _p(status), _stream(stream)), "gs_sort_tiles")
 

@@ -132,19 +132,21 @@ gs_status gs_sort_tiles_workspace(int32_t n_gaussians, const gs_batch* batch, si
 }
 
 gs_status gs_sort_tiles(int32_t n_gaussians, const gs_cameras* cams, const gs_batch* batch,
-                        const gs_projected* proj, uint64_t* keys, uint32_t* vals, size_t capacity,
+                        const gs_projected* proj, uint32_t* tiles, uint32_t* vals, size_t capacity,
                         uint32_t* ranges, uint32_t* n_instances, void* ws, size_t ws_bytes,
                         int32_t* status, gs_stream stream) {
   gs_status s;
   if ((s = check_cameras(cams)) || (s = check_batch(batch)) || (s = check_projected(proj))) return s;
-  if (n_gaussians < 0 || !keys || !vals || !ranges || !n_instances || !ws)
+  if (n_gaussians < 0 || !tiles || !vals || !ranges || !n_instances || !ws)
     return fail(GS_ERR_ARG, "gs_sort_tiles: null argument");
+  if ((unsigned long long)batch->B * (unsigned long long)n_gaussians >= 0xffffffffull)
+    return fail(GS_ERR_ARG, "gs_sort_tiles: B*N must be < 2^32");
   if (capacity == 0 || capacity >= 0xffffffffull)
     return fail(GS_ERR_CAPACITY, "gs_sort_tiles: capacity must be in [1, 2^32 - 1)");
-  if (!aligned(keys, 8) || !aligned(ws, 256)) return fail(GS_ERR_ARG, "gs_sort_tiles: misaligned buffer");
+  if (!aligned(ws, 256)) return fail(GS_ERR_ARG, "gs_sort_tiles: ws must be 256-byte aligned");
   const size_t need = sort_workspace_bytes(n_gaussians, *batch, capacity);
   if (ws_bytes < need) return fail(GS_ERR_ARG, "gs_sort_tiles: workspace %zu < %zu bytes", ws_bytes, need);
-  cudaError_t e = launch_sort_tiles(n_gaussians, *cams, *batch, *proj, keys, vals, capacity, ranges,
+  cudaError_t e = launch_sort_tiles(n_gaussians, *cams, *batch, *proj, tiles, vals, capacity, ranges,
                                     n_instances, ws, status, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "gs_sort_tiles");
   return GS_OK;

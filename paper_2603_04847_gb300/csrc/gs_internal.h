@@ -22,11 +22,11 @@ cudaError_t launch_project_bwd(const gs_gaussians& g, const gs_cameras& cams, co
                                const gs_projected& proj, const float* v2d, const gs_gaussian_grads& dg,
                                double* partial, double* g_pose_tangent, cudaStream_t st);
 
-int sort_key_bits(int n_tiles_total);
+int sort_tile_bits(int n_tiles_total);
 size_t sort_workspace_bytes(int N, const gs_batch& batch, size_t capacity);
-int sort_launch_count(const gs_batch& batch);
+int sort_kernel_count(const gs_batch& batch);
 cudaError_t launch_sort_tiles(int N, const gs_cameras& cams, const gs_batch& batch,
-                              const gs_projected& proj, uint64_t* keys, uint32_t* vals,
+                              const gs_projected& proj, uint32_t* tiles, uint32_t* vals,
                               size_t capacity, uint32_t* ranges, uint32_t* n_instances, void* ws,
                               int32_t* status, cudaStream_t st);
 

@@ -3,10 +3,14 @@
 // fused in.
 //
 // One thread block per 16x16 tile of any view in the batch, one pixel per
-// thread.  Splat records (48 B) are staged in shared memory 256 at a time
-// with one cooperative load per thread; every thread then walks the staged
-// batch.  A pixel stops before the splat that would drop its transmittance
-// below 1e-4; the block leaves when all its pixels are done.
+// thread; each warp owns an 8x4 block of the tile.  Splat records (48 B) are
+// staged in shared memory 256 at a time with one cooperative load per
+// thread, which also computes an 8-bit mask of the warps whose pixels the
+// splat's alpha >= 1/255 support can reach (a conservative bounding box);
+// a warp skips every staged splat whose bit it lacks with one uniform
+// branch, before any per-pixel arithmetic.  A pixel stops before the splat
+// that would drop its transmittance below 1e-4; the block leaves when all
+// its pixels are done.
 //
 // The backward recomputes compositing back to front from T_final (only
 // T_final and n_contrib are stored per pixel).  All 256 pixels of a block
@@ -54,6 +58,35 @@ __device__ inline void find_tile(const gs_batch& batch, const gs_cameras& cams, 
   }
 }
 
+// Pixel of thread `tid` in its 16x16 tile: warp w covers the 8x4 block at
+// ((w & 1) * 8, (w >> 1) * 4), lane l the pixel (l & 7, l >> 3) in it.
+__device__ inline void tile_pixel(int tid, int& lx, int& ly) {
+  const int w = tid >> 5, l = tid & 31;
+  lx = (w & 1) * 8 + (l & 7);
+  ly = (w >> 1) * 4 + (l >> 3);
+}
+
+// Bit w set iff the bounding box of the splat's support {q <= q_max} can
+// reach a pixel centre of warp w's 8x4 block in the tile at pixel (x0, y0).
+// The box is widened by 2 % + 0.01 in q and 0.01 px: the FP32 evaluation of q
+// for strongly anisotropic conics carries relative errors of that order, so
+// no pixel that the exact alpha test would accept is ever skipped.
+__device__ inline uint32_t warp_mask(const float4 xyo, const float4 con, float x0, float y0) {
+  const float detc = con.x * con.z - con.y * con.y;
+  const float qc = (con.w + 1e-3f) * 1.02f + 0.01f;
+  const float rx = sqrtf(qc * con.z / detc) + 0.01f;
+  const float ry = sqrtf(qc * con.x / detc) + 0.01f;
+  uint32_t m = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    const float bx0 = x0 + (float)((w & 1) * 8) + 0.5f, by0 = y0 + (float)((w >> 1) * 4) + 0.5f;
+    const bool hit = (xyo.x + rx >= bx0) && (xyo.x - rx <= bx0 + 7.f) && (xyo.y + ry >= by0) &&
+                     (xyo.y - ry <= by0 + 3.f);
+    m |= hit ? (1u << w) : 0u;
+  }
+  return m;
+}
+
 // alpha of a staged splat at pixel centre (px, py); returns false when the
 // splat cannot contribute (alpha < 1/255).  Shared by forward and backward
 // so both take identical decisions.
@@ -78,13 +111,17 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
   __shared__ float4 s_xyo[kThreads];
   __shared__ float4 s_con[kThreads];
   __shared__ float4 s_col[kThreads];
+  __shared__ uint32_t s_mask[kThreads];
   const int gt = blockIdx.x;
   find_tile(batch, cams, gt, &ti);
   __syncthreads();
-  const int lx = threadIdx.x % kTile, ly = threadIdx.x / kTile;
+  int lx, ly;
+  tile_pixel(threadIdx.x, lx, ly);
+  const uint32_t wbit = 1u << (threadIdx.x >> 5);
   const int u = ti.tx * kTile + lx, v = ti.ty * kTile + ly;
   const bool inside = u < ti.W && v < ti.H;
   const float px = (float)u + 0.5f, py = (float)v + 0.5f;
+  const float x0 = (float)(ti.tx * kTile), y0 = (float)(ti.ty * kTile);
   const uint32_t start = ranges[2 * gt], end = ranges[2 * gt + 1];
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
   uint32_t last = 0;
@@ -94,13 +131,17 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
     const uint32_t idx = base + threadIdx.x;
     if (idx < end) {
       const uint32_t r = vals[idx];
-      s_xyo[threadIdx.x] = splat[3 * (size_t)r];
-      s_con[threadIdx.x] = splat[3 * (size_t)r + 1];
+      const float4 xyo = splat[3 * (size_t)r];
+      const float4 con = splat[3 * (size_t)r + 1];
+      s_xyo[threadIdx.x] = xyo;
+      s_con[threadIdx.x] = con;
       s_col[threadIdx.x] = splat[3 * (size_t)r + 2];
+      s_mask[threadIdx.x] = warp_mask(xyo, con, x0, y0);
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)kThreads, end - base);
     for (int k = 0; k < cnt && !done; ++k) {
+      if (!(s_mask[k] & wbit)) continue;  // uniform across the warp
       float dx, dy, G, alpha;
       if (!splat_alpha(s_xyo[k], s_con[k], px, py, dx, dy, G, alpha)) continue;
       const float Tn = T * (1.f - alpha);
@@ -162,6 +203,7 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
   __shared__ float4 s_con[kThreads];
   __shared__ float4 s_col[kThreads];
   __shared__ uint32_t s_rec[kThreads];
+  __shared__ uint32_t s_mask[kThreads];
   __shared__ float s_g[kThreads][9];
   __shared__ uint32_t s_max;
   __shared__ float s_loss[kThreads / 32];
@@ -170,10 +212,13 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
   find_tile(batch, cams, gt, &ti);
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int lx = threadIdx.x % kTile, ly = threadIdx.x / kTile;
+  int lx, ly;
+  tile_pixel(threadIdx.x, lx, ly);
+  const uint32_t wbit = 1u << (threadIdx.x >> 5);
   const int u = ti.tx * kTile + lx, v = ti.ty * kTile + ly;
   const bool inside = u < ti.W && v < ti.H;
   const float px = (float)u + 0.5f, py = (float)v + 0.5f;
+  const float x0 = (float)(ti.tx * kTile), y0 = (float)(ti.ty * kTile);
   const uint32_t start = ranges[2 * gt];
   float T = 1.f, S0 = 0.f, S1 = 0.f, S2 = 0.f, vC0 = 0.f, vC1 = 0.f, vC2 = 0.f;
   uint32_t nc = 0;
@@ -214,21 +259,28 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
     if (t != 0.0) atomicAdd(loss, t);
   }
   const uint32_t n_end = s_max;  // positions [0, n_end) of the tile list
+  const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, nc);
   for (int bend = (int)n_end; bend > 0; bend -= kThreads) {
     const int bstart = max(0, bend - kThreads);
     const int cnt = bend - bstart;
     if (threadIdx.x < cnt) {
       const uint32_t r = vals[start + bstart + threadIdx.x];
+      const float4 xyo = splat[3 * (size_t)r];
+      const float4 con = splat[3 * (size_t)r + 1];
       s_rec[threadIdx.x] = r;
-      s_xyo[threadIdx.x] = splat[3 * (size_t)r];
-      s_con[threadIdx.x] = splat[3 * (size_t)r + 1];
+      s_xyo[threadIdx.x] = xyo;
+      s_con[threadIdx.x] = con;
       s_col[threadIdx.x] = splat[3 * (size_t)r + 2];
+      s_mask[threadIdx.x] = warp_mask(xyo, con, x0, y0);
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) s_g[threadIdx.x][i] = 0.f;
     __syncthreads();
     for (int k = cnt - 1; k >= 0; --k) {
       const uint32_t pos = (uint32_t)(bstart + k);
+      // uniform across the warp: past all its pixels' last contributor, or
+      // the splat cannot reach its 8x4 block
+      if (pos >= warp_nc || !(s_mask[k] & wbit)) continue;
       float g[9];
       bool contrib = false;
       if (pos < nc) {
@@ -238,7 +290,7 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
         if (splat_alpha(xyo, con, px, py, dx, dy, G, alpha)) {
           contrib = true;
           const float4 c = s_col[k];
-          const float ra = 1.f / (1.f - alpha);
+          const float ra = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 0.01
           const float Tk = T * ra;
           const float w = alpha * Tk;
           g[6] = w * vC0;

@@ -1,17 +1,24 @@
 // Per-tile duplication and depth ordering of projected splats.
 //
-//   scan       exclusive prefix sum of tiles-touched over records r = b*N+j
-//   duplicate  one (key, value) per covered tile: key = tile << 32 | depth
-//              bits, value = r
-//   radix      stable LSD radix sort, 8-bit digits, only over the bits a
-//              key can use (32 depth bits + bits of the largest tile id)
-//   ranges     [start, end) per global tile
+//   depth sort  stable LSD radix sort of the B*N records r = b*N + j by the
+//               float bits of their camera depth (invisible records last);
+//               ties keep record order, i.e. index order within a view
+//   scan        exclusive prefix sum of tiles-touched in depth order
+//   duplicate   one (global tile, r) instance per covered tile, emitted in
+//               depth order
+//   tile sort   stable LSD radix sort of the instances by tile id, over the
+//               bits the largest tile id uses only
+//   ranges      [start, end) per global tile
+//
+// Sorting 8-byte records by depth once and then 8-byte instances by tile
+// moves far fewer bytes than sorting 12-byte instances by a 47-bit
+// (tile, depth) key, and gives the same order: (tile, depth, j).
 //
 // The instance count stays on the device: every kernel after the scan reads
-// it, and all grids are sized from host-known bounds (records, capacity,
-// SM count), so the whole stage can be captured in a CUDA graph.  The radix
-// pass is the classic three-kernel form (per-block digit histogram, per-digit
-// scan over blocks, stable scatter); it needs no inter-block waiting.
+// it, and all grids are sized from host-known bounds (records, capacity, SM
+// count), so the whole stage can be captured in a CUDA graph.  Each radix
+// pass is the classic three-kernel form (per-block digit histogram,
+// per-digit scan over blocks, stable scatter); no block waits on another.
 #include "gs_internal.h"
 
 namespace gs {
@@ -20,7 +27,7 @@ namespace {
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
-constexpr int kScanTile = kScanThreads * kScanItems;  // 2048 records per tile
+constexpr int kScanTile = kScanThreads * kScanItems;  // 2048 items per tile
 
 __device__ inline uint32_t block_exclusive_scan_u32(uint32_t v, uint32_t* total, uint32_t* sm) {
   // sm: >= 32 words.  Returns exclusive prefix of v over the block.
@@ -50,8 +57,22 @@ __device__ inline uint32_t block_exclusive_scan_u32(uint32_t v, uint32_t* total,
   return warp_prefix + x - v;
 }
 
-// Sum of n_tiles per scan tile (64-bit to detect overflow of 32-bit offsets).
+// Depth sort keys: float bits of the depth (positive, so the bits order like
+// the values) for visible records, all ones for invisible ones.
+__global__ void __launch_bounds__(256) depth_keys_kernel(gs_projected proj, uint32_t M,
+                                                         uint32_t* __restrict__ keys,
+                                                         uint32_t* __restrict__ vals) {
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < M; r += gridDim.x * blockDim.x) {
+    const bool vis = proj.n_tiles[r] != 0;
+    keys[r] = vis ? __float_as_uint(reinterpret_cast<const float4*>(proj.splat)[3 * (size_t)r].w)
+                  : 0xffffffffu;
+    vals[r] = r;
+  }
+}
+
+// Sum of n_tiles[order[k]] per scan tile (64-bit to detect overflow).
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ in,
+                                                                   const uint32_t* __restrict__ order,
                                                                    size_t M,
                                                                    unsigned long long* tile_sums) {
   __shared__ unsigned long long red[kScanThreads / 32];
@@ -60,7 +81,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const size_t k = base + (size_t)i * kScanThreads + threadIdx.x;
-    if (k < M) s += in[k];
+    if (k < M) s += in[order[k]];
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
@@ -84,7 +105,6 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(unsigned long long* ti
   const int hi = min(lo + per, n_tiles);
   unsigned long long s = 0;
   for (int k = lo; k < hi; ++k) s += tile_sums[k];
-  // block exclusive scan of s (64-bit)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long x = s;
 #pragma unroll
@@ -121,6 +141,7 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(unsigned long long* ti
 }
 
 __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t* __restrict__ in,
+                                                                  const uint32_t* __restrict__ order,
                                                                   size_t M,
                                                                   const unsigned long long* tile_offs,
                                                                   uint32_t* __restrict__ out) {
@@ -131,13 +152,12 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const size_t k = base + i;
-    v[i] = k < M ? in[k] : 0u;
+    v[i] = k < M ? in[order[k]] : 0u;
     s += v[i];
   }
   const uint32_t ex = block_exclusive_scan_u32(s, nullptr, sm);
   // offsets beyond 2^32 cannot be valid instances (capacity < 2^32): clamp
-  const unsigned long long t0 = tile_offs[blockIdx.x] + ex;
-  unsigned long long run = t0;
+  unsigned long long run = tile_offs[blockIdx.x] + ex;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const size_t k = base + i;
@@ -151,9 +171,11 @@ struct SlotTiles {
   int tile_offset;
 };
 
-__global__ void __launch_bounds__(256) duplicate_kernel(gs_projected proj, const uint32_t* __restrict__ offs,
-                                                        int N, gs_cameras cams, gs_batch batch,
-                                                        uint64_t* __restrict__ keys,
+// Instances in depth order: position k of the depth-sorted records emits
+// its tiles at offs[k] onwards.
+__global__ void __launch_bounds__(256) duplicate_kernel(gs_projected proj, const uint32_t* __restrict__ order,
+                                                        const uint32_t* __restrict__ offs, int N, gs_cameras cams,
+                                                        gs_batch batch, uint32_t* __restrict__ tiles,
                                                         uint32_t* __restrict__ vals, size_t capacity,
                                                         int32_t* status) {
   __shared__ SlotTiles st[GS_MAX_BATCH];
@@ -164,23 +186,21 @@ __global__ void __launch_bounds__(256) duplicate_kernel(gs_projected proj, const
   }
   __syncthreads();
   const size_t M = (size_t)batch.B * N;
-  for (size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x; r < M;
-       r += (size_t)gridDim.x * blockDim.x) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < M;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t r = order[k];
     const uint32_t n = proj.n_tiles[r];
     if (n == 0) continue;
-    const int b = (int)(r / N);
+    const int b = (int)(r / (uint32_t)N);
     const ushort4 rc = reinterpret_cast<const ushort4*>(proj.rect)[r];
-    const float depth = reinterpret_cast<const float4*>(proj.splat)[3 * r].w;
-    const uint64_t dbits = (uint64_t)__float_as_uint(depth);
-    size_t o = offs[r];
+    size_t o = offs[k];
     if (o + n > capacity) set_flag(status, GS_FLAG_CAPACITY);
     const int tx_n = st[b].tiles_x, t0 = st[b].tile_offset;
     for (int ty = rc.y; ty <= rc.w; ++ty)
       for (int tx = rc.x; tx <= rc.z; ++tx) {
         if (o < capacity) {
-          const uint64_t tile = (uint64_t)(t0 + ty * tx_n + tx);
-          keys[o] = (tile << 32) | dbits;
-          vals[o] = (uint32_t)r;
+          tiles[o] = (uint32_t)(t0 + ty * tx_n + tx);
+          vals[o] = r;
         }
         ++o;
       }
@@ -188,10 +208,16 @@ __global__ void __launch_bounds__(256) duplicate_kernel(gs_projected proj, const
 }
 
 // ---------------------------------------------------------------------------
-// LSD radix sort over a device-side item count.
+// Stable LSD radix sort of (uint32 key, uint32 value) pairs, 8-bit digits.
+// The item count is either host-known (n_dev == nullptr) or read on the
+// device, clamped to the buffer capacity.
 
 constexpr int kRadixThreads = 512;
 constexpr int kRadixWarps = kRadixThreads / 32;
+
+__device__ inline uint32_t radix_count(const uint32_t* n_dev, uint32_t n_host, size_t capacity) {
+  return n_dev ? (uint32_t)min((size_t)*n_dev, capacity) : n_host;
+}
 
 __device__ inline void chunk_of(uint32_t n, int nb, int blk, uint32_t& lo, uint32_t& hi) {
   uint32_t chunk = (n + nb - 1) / nb;
@@ -200,18 +226,19 @@ __device__ inline void chunk_of(uint32_t n, int nb, int blk, uint32_t& lo, uint3
   hi = min(lo + chunk, n);
 }
 
-__global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const uint64_t* __restrict__ keys,
-                                                                   const uint32_t* n_dev, size_t capacity,
-                                                                   int shift, uint32_t* __restrict__ hist) {
+__global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const uint32_t* __restrict__ keys,
+                                                                   const uint32_t* n_dev, uint32_t n_host,
+                                                                   size_t capacity, int shift,
+                                                                   uint32_t* __restrict__ hist) {
   __shared__ uint32_t h[kRadixWarps][256];
   for (int i = threadIdx.x; i < kRadixWarps * 256; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
-  const uint32_t n = (uint32_t)min((size_t)*n_dev, capacity);
+  const uint32_t n = radix_count(n_dev, n_host, capacity);
   uint32_t lo, hi;
   chunk_of(n, gridDim.x, blockIdx.x, lo, hi);
   const int warp = threadIdx.x >> 5;
   for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const uint32_t d = (uint32_t)(keys[i] >> shift) & 0xffu;
+    const uint32_t d = (keys[i] >> shift) & 0xffu;
     atomicAdd(&h[warp][d], 1u);
   }
   __syncthreads();
@@ -245,8 +272,8 @@ __global__ void __launch_bounds__(256) radix_scan_kernel(uint32_t* hist, int nb,
 }
 
 __global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
-    const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, const uint32_t* n_dev, size_t capacity, int shift,
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, const uint32_t* n_dev, uint32_t n_host, size_t capacity, int shift,
     const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals) {
   __shared__ uint32_t run[256];
   __shared__ uint32_t wcnt[kRadixWarps][256];
@@ -259,22 +286,27 @@ __global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
   }
   for (int i = threadIdx.x; i < kRadixWarps * 256; i += blockDim.x) (&wcnt[0][0])[i] = 0;
   __syncthreads();
-  const uint32_t n = (uint32_t)min((size_t)*n_dev, capacity);
+  const uint32_t n = radix_count(n_dev, n_host, capacity);
   uint32_t lo, hi;
   chunk_of(n, gridDim.x, blockIdx.x, lo, hi);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
+  // the next round's items are loaded while this round is ranked
+  uint32_t i = lo + threadIdx.x;
+  uint32_t k = 0, v = 0;
+  if (i < hi) {
+    k = kin[i];
+    v = vin[i];
+  }
   for (uint32_t base = lo; base < hi; base += kRadixThreads) {
-    const uint32_t i = base + threadIdx.x;
     const bool valid = i < hi;
-    uint64_t k = 0;
-    uint32_t v = 0;
-    uint32_t d = 256u + (uint32_t)lane;  // unique sentinel for invalid lanes
-    if (valid) {
-      k = kin[i];
-      v = vin[i];
-      d = (uint32_t)(k >> shift) & 0xffu;
+    const uint32_t inext = i + kRadixThreads;
+    uint32_t kn = 0, vn = 0;
+    if (inext < hi) {
+      kn = kin[inext];
+      vn = vin[inext];
     }
+    const uint32_t d = valid ? (k >> shift) & 0xffu : 256u + (uint32_t)lane;  // unique sentinel
     __syncwarp();
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const uint32_t rank = __popc(peers & lt_mask);
@@ -294,19 +326,22 @@ __global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
       wcnt[warp][d] = 0;
     }
     __syncthreads();
+    i = inext;
+    k = kn;
+    v = vn;
   }
 }
 
-__global__ void __launch_bounds__(256) tile_ranges_kernel(const uint64_t* __restrict__ keys,
+__global__ void __launch_bounds__(256) tile_ranges_kernel(const uint32_t* __restrict__ tiles,
                                                           const uint32_t* n_dev, size_t capacity,
                                                           uint32_t* __restrict__ ranges) {
   const uint32_t n = (uint32_t)min((size_t)*n_dev, capacity);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t t = (uint32_t)(keys[i] >> 32);
+    const uint32_t t = tiles[i];
     if (i == 0) {
       ranges[2 * t] = 0;
     } else {
-      const uint32_t p = (uint32_t)(keys[i - 1] >> 32);
+      const uint32_t p = tiles[i - 1];
       if (p != t) {
         ranges[2 * p + 1] = i;
         ranges[2 * t] = i;
@@ -319,10 +354,12 @@ __global__ void __launch_bounds__(256) tile_ranges_kernel(const uint64_t* __rest
 inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct SortWs {
-  uint32_t* offs;
+  uint32_t* dkeys[2];   // depth keys, double-buffered [M]
+  uint32_t* dvals[2];   // record ids [M]
+  uint32_t* offs;       // instance offset per depth-sorted record [M]
   unsigned long long* tile_sums;
-  uint64_t* keys_alt;
-  uint32_t* vals_alt;
+  uint32_t* tiles_alt;  // [capacity]
+  uint32_t* vals_alt;   // [capacity]
   uint32_t* hist;
   uint32_t* totals;
   size_t bytes;
@@ -332,40 +369,45 @@ SortWs sort_ws_layout(void* base, size_t M, size_t capacity, int nb) {
   SortWs w;
   char* p = (char*)base;
   size_t o = 0;
-  const size_t n_scan_tiles = (M + kScanTile - 1) / kScanTile;
-  w.offs = (uint32_t*)(p + o);
-  o += align_up(M * 4);
-  w.tile_sums = (unsigned long long*)(p + o);
-  o += align_up(n_scan_tiles * 8 + 8);
-  w.keys_alt = (uint64_t*)(p + o);
-  o += align_up(capacity * 8);
-  w.vals_alt = (uint32_t*)(p + o);
-  o += align_up(capacity * 4);
-  w.hist = (uint32_t*)(p + o);
-  o += align_up((size_t)256 * nb * 4);
-  w.totals = (uint32_t*)(p + o);
-  o += align_up(256 * 4);
+  auto take = [&](size_t bytes) {
+    char* q = p + o;
+    o += align_up(bytes);
+    return q;
+  };
+  for (int i = 0; i < 2; ++i) w.dkeys[i] = (uint32_t*)take(M * 4);
+  for (int i = 0; i < 2; ++i) w.dvals[i] = (uint32_t*)take(M * 4);
+  w.offs = (uint32_t*)take(M * 4);
+  w.tile_sums = (unsigned long long*)take(((M + kScanTile - 1) / kScanTile) * 8 + 8);
+  w.tiles_alt = (uint32_t*)take(capacity * 4);
+  w.vals_alt = (uint32_t*)take(capacity * 4);
+  w.hist = (uint32_t*)take((size_t)256 * nb * 4);
+  w.totals = (uint32_t*)take(256 * 4);
   w.bytes = o;
   return w;
 }
 
-int radix_blocks() {
-  static int nb = 0;
-  if (nb == 0) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    nb = sms > 0 ? sms * 2 : 304;
+int radix_blocks() { return 2 * device_sm_count(); }
+
+// Stable LSD passes over bits [0, bits) of (kA, vA); kA/vA point at the
+// sorted result afterwards.
+void radix_sort_u32(uint32_t*& kA, uint32_t*& vA, uint32_t*& kB, uint32_t*& vB, const uint32_t* n_dev,
+                    uint32_t n_host, size_t capacity, int bits, SortWs& w, int nb, cudaStream_t st) {
+  for (int shift = 0; shift < bits; shift += 8) {
+    radix_hist_kernel<<<nb, kRadixThreads, 0, st>>>(kA, n_dev, n_host, capacity, shift, w.hist);
+    radix_scan_kernel<<<256, 256, 0, st>>>(w.hist, nb, w.totals);
+    radix_scatter_kernel<<<nb, kRadixThreads, 0, st>>>(kA, vA, kB, vB, n_dev, n_host, capacity, shift, w.hist,
+                                                       w.totals);
+    std::swap(kA, kB);
+    std::swap(vA, vB);
   }
-  return nb;
 }
 
 }  // namespace
 
-int sort_key_bits(int n_tiles_total) {
+int sort_tile_bits(int n_tiles_total) {
   int tb = 0;
   while ((1ll << tb) < (long long)n_tiles_total) ++tb;
-  return 32 + tb;
+  return tb;
 }
 
 size_t sort_workspace_bytes(int N, const gs_batch& batch, size_t capacity) {
@@ -373,7 +415,7 @@ size_t sort_workspace_bytes(int N, const gs_batch& batch, size_t capacity) {
 }
 
 cudaError_t launch_sort_tiles(int N, const gs_cameras& cams, const gs_batch& batch,
-                              const gs_projected& proj, uint64_t* keys, uint32_t* vals,
+                              const gs_projected& proj, uint32_t* tiles, uint32_t* vals,
                               size_t capacity, uint32_t* ranges, uint32_t* n_instances, void* ws,
                               int32_t* status, cudaStream_t st) {
   const size_t M = (size_t)batch.B * N;
@@ -384,37 +426,39 @@ cudaError_t launch_sort_tiles(int N, const gs_cameras& cams, const gs_batch& bat
   if (e != cudaSuccess) return e;
   const int n_scan_tiles = (int)((M + kScanTile - 1) / kScanTile);
   if (n_scan_tiles == 0) return cudaMemsetAsync(n_instances, 0, 4, st);
-  scan_reduce_kernel<<<n_scan_tiles, kScanThreads, 0, st>>>(proj.n_tiles, M, w.tile_sums);
-  scan_tiles_kernel<<<1, 1024, 0, st>>>(w.tile_sums, n_scan_tiles, capacity, n_instances, status);
-  scan_apply_kernel<<<n_scan_tiles, kScanThreads, 0, st>>>(proj.n_tiles, M, w.tile_sums, w.offs);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
 
-  const int bits = sort_key_bits(batch.n_tiles);
-  const int passes = (bits + 7) / 8;
-  // Duplicate into the buffer that leaves the sorted result in keys/vals.
-  uint64_t* kA = (passes & 1) ? w.keys_alt : keys;
+  // 1. stable depth sort of the records (32-bit keys, host-known count)
+  const int grid = (int)std::min<size_t>((M + 255) / 256, (size_t)nb * 8);
+  depth_keys_kernel<<<grid, 256, 0, st>>>(proj, (uint32_t)M, w.dkeys[0], w.dvals[0]);
+  uint32_t *dkA = w.dkeys[0], *dvA = w.dvals[0], *dkB = w.dkeys[1], *dvB = w.dvals[1];
+  radix_sort_u32(dkA, dvA, dkB, dvB, nullptr, (uint32_t)M, M, 32, w, nb, st);
+  const uint32_t* order = dvA;
+
+  // 2. instance offsets in depth order
+  scan_reduce_kernel<<<n_scan_tiles, kScanThreads, 0, st>>>(proj.n_tiles, order, M, w.tile_sums);
+  scan_tiles_kernel<<<1, 1024, 0, st>>>(w.tile_sums, n_scan_tiles, capacity, n_instances, status);
+  scan_apply_kernel<<<n_scan_tiles, kScanThreads, 0, st>>>(proj.n_tiles, order, M, w.tile_sums, w.offs);
+
+  // 3. duplicate into whichever buffer leaves the tile-sorted result in
+  //    tiles/vals, then 4. stable sort by tile id
+  const int tbits = sort_tile_bits(batch.n_tiles);
+  const int passes = (tbits + 7) / 8;
+  uint32_t* kA = (passes & 1) ? w.tiles_alt : tiles;
   uint32_t* vA = (passes & 1) ? w.vals_alt : vals;
-  uint64_t* kB = (passes & 1) ? keys : w.keys_alt;
+  uint32_t* kB = (passes & 1) ? tiles : w.tiles_alt;
   uint32_t* vB = (passes & 1) ? vals : w.vals_alt;
-  const int dup_blocks = (int)std::min<size_t>((M + 255) / 256, (size_t)nb * 8);
-  duplicate_kernel<<<dup_blocks, 256, 0, st>>>(proj, w.offs, N, cams, batch, kA, vA, capacity, status);
-  for (int p = 0; p < passes; ++p) {
-    const int shift = 8 * p;
-    radix_hist_kernel<<<nb, kRadixThreads, 0, st>>>(kA, n_instances, capacity, shift, w.hist);
-    radix_scan_kernel<<<256, 256, 0, st>>>(w.hist, nb, w.totals);
-    radix_scatter_kernel<<<nb, kRadixThreads, 0, st>>>(kA, vA, kB, vB, n_instances, capacity, shift,
-                                                       w.hist, w.totals);
-    std::swap(kA, kB);
-    std::swap(vA, vB);
-  }
-  tile_ranges_kernel<<<nb * 4, 256, 0, st>>>(keys, n_instances, capacity, ranges);
+  duplicate_kernel<<<grid, 256, 0, st>>>(proj, order, w.offs, N, cams, batch, kA, vA, capacity, status);
+  radix_sort_u32(kA, vA, kB, vB, n_instances, 0, capacity, tbits, w, nb, st);
+
+  // 5. ranges
+  tile_ranges_kernel<<<nb * 4, 256, 0, st>>>(tiles, n_instances, capacity, ranges);
   return cudaGetLastError();
 }
 
-int sort_launch_count(const gs_batch& batch) {
-  const int passes = (sort_key_bits(batch.n_tiles) + 7) / 8;
-  return 3 + 1 + 3 * passes + 1;
+int sort_kernel_count(const gs_batch& batch) {
+  const int passes = (sort_tile_bits(batch.n_tiles) + 7) / 8;
+  // depth keys 1, depth sort 4 x 3, scan 3, duplicate 1, tile sort 3 / pass, ranges 1
+  return 1 + 4 * 3 + 3 + 1 + 3 * passes + 1;
 }
 
 }  // namespace gs

@@ -226,10 +226,11 @@ class JointStep:
         """libgs kernel launches one step issues (memsets not counted)."""
         per_render = 0
         for b in self.slot_batches:
-            passes = (32 + max(int(math.ceil(math.log2(max(b.n_tiles, 1)))), 0) + 7) // 8
-            # project 1; sort: 3 scan + duplicate + 3 per pass + ranges;
-            # render fwd 1; raster bwd 1; project bwd + finalize 2
-            per_render += 1 + (3 + 1 + 3 * passes + 1) + 1 + 1 + 2
+            tbits = int(math.ceil(math.log2(b.n_tiles))) if b.n_tiles > 1 else 0
+            # project 1; sort: depth keys 1, depth sort 4 x 3, scan 3,
+            # duplicate 1, tile sort 3 per pass, ranges 1; render fwd 1;
+            # raster bwd 1; project bwd + finalize 2
+            per_render += 1 + (1 + 12 + 3 + 1 + 3 * ((tbits + 7) // 8) + 1) + 1 + 1 + 2
         # track + finalize 2, step advance 1, Adam 6, pose 1
         return per_render + 2 + 1 + 6 + 1
 

@@ -86,9 +86,8 @@ def test_tiny_discrete_stage_bit_exact():
     t_o, d_o, g_o = t_o[keep], d_o[keep], g_o[keep]
     n_inst = r.n_instances()
     vals = r.tl.vals.cpu().numpy()[:n_inst].astype(np.int64)
-    keys = r.tl.keys.cpu().numpy()[:n_inst]
     ranges = r.tl.ranges.cpu().numpy().reshape(-1, 2).astype(np.int64)
-    ktile = (keys.view(np.uint64) >> np.uint64(32)).astype(np.int64)
+    ktile = r.tl.tiles.cpu().numpy()[:n_inst].astype(np.int64)
     assert np.all(np.diff(ktile) >= 0)
     kk = ~knife[vals]
     kt, kv = ktile[kk], vals[kk]
