@@ -2,22 +2,28 @@
 // (Algorithm 1 "Rasterize"), and its backward pass with the L1 term of Eq. 5
 // fused in.
 //
-// One thread block per 16x16 tile of any view in the batch, one pixel per
-// thread; each warp owns an 8x4 block of the tile.  Splat records (48 B) are
-// staged in shared memory 256 at a time with one cooperative load per
-// thread, which also computes an 8-bit mask of the warps whose pixels the
-// splat's alpha >= 1/255 support can reach (a conservative bounding box);
-// a warp skips every staged splat whose bit it lacks with one uniform
-// branch, before any per-pixel arithmetic.  A pixel stops before the splat
-// that would drop its transmittance below 1e-4; the block leaves when all
-// its pixels are done.
+// One thread block of 128 threads per 16x16 tile of any view in the batch.
+// Each warp owns an 8x8 block of the tile and each thread two pixels of it,
+// (x, y) and (x, y + 4): the per-splat shared-memory loads, the cull test
+// and the loop overhead are paid once per two pixels, and in the backward
+// one warp reduction covers 64 pixels.
+//
+// Splat records are staged in shared memory 256 at a time.  Staging turns
+// each record into the exponent form alpha_raw = 2^e with
+//   e = A dx^2 + B dx dy + C dy^2 + log2(opacity),
+//   A = -a/(2 ln 2), B = -b/ln 2, C = -c/(2 ln 2)  (conic a, b, c),
+// so that the alpha >= 1/255 test is one compare and one exp2 per pixel, and
+// computes a 4-bit mask of the warps whose 8x8 block the splat's support can
+// reach (a conservative bounding box): a warp skips splats without its bit
+// with one uniform branch.  Forward and backward evaluate alpha with the same
+// function on the same staged values, so they take identical decisions.
 //
 // The backward recomputes compositing back to front from T_final (only
-// T_final and n_contrib are stored per pixel).  All 256 pixels of a block
-// walk the same splat in lockstep, so its nine screen-space gradients are
-// reduced in registers: a transposing warp reduction (9 shuffles for 8
-// values + 5 for the ninth) followed by shared-memory adds from 9 lanes per
-// warp, and one vector atomic per splat per tile into global memory.
+// T_final and n_contrib are stored per pixel).  All lanes of a warp walk the
+// same splat in lockstep, so its nine screen-space gradients are reduced in
+// registers — a transposing warp reduction (9 shuffles for 8 values + 5 for
+// the ninth) — then added in shared memory by 9 lanes per warp, and written
+// with one vector atomic per splat per tile.
 #include "gs_internal.h"
 
 namespace gs {
@@ -25,7 +31,10 @@ namespace gs {
 namespace {
 
 constexpr int kTile = 16;
-constexpr int kThreads = kTile * kTile;
+constexpr int kThreads = 128;  // 2 pixels per thread
+constexpr int kBatch = 256;    // splats staged per round
+constexpr float kLn2 = 0.69314718055994531f;
+constexpr float kHalfLog2e = 0.72134752044448170f;  // 1 / (2 ln 2)
 
 struct TileInfo {
   int slot;
@@ -58,19 +67,20 @@ __device__ inline void find_tile(const gs_batch& batch, const gs_cameras& cams, 
   }
 }
 
-// Pixel of thread `tid` in its 16x16 tile: warp w covers the 8x4 block at
-// ((w & 1) * 8, (w >> 1) * 4), lane l the pixel (l & 7, l >> 3) in it.
-__device__ inline void tile_pixel(int tid, int& lx, int& ly) {
+// Pixels of thread `tid` in its 16x16 tile: warp w covers the 8x8 block at
+// ((w & 1) * 8, (w >> 1) * 8); lane l the pixels (l & 7, l >> 3) and
+// (l & 7, (l >> 3) + 4) in it.
+__device__ inline void tile_pixels(int tid, int& lx, int& ly) {
   const int w = tid >> 5, l = tid & 31;
   lx = (w & 1) * 8 + (l & 7);
-  ly = (w >> 1) * 4 + (l >> 3);
+  ly = (w >> 1) * 8 + (l >> 3);
 }
 
 // Bit w set iff the bounding box of the splat's support {q <= q_max} can
-// reach a pixel centre of warp w's 8x4 block in the tile at pixel (x0, y0).
-// The box is widened by 2 % + 0.01 in q and 0.01 px: the FP32 evaluation of q
-// for strongly anisotropic conics carries relative errors of that order, so
-// no pixel that the exact alpha test would accept is ever skipped.
+// reach a pixel centre of warp w's 8x8 block in the tile at pixel (x0, y0).
+// The box is widened by 2 % + 0.01 in q and 0.01 px: the FP32 evaluation of
+// alpha for strongly anisotropic conics carries relative errors of that
+// order, so no pixel whose alpha can pass the test is ever skipped.
 __device__ inline uint32_t warp_mask(const float4 xyo, const float4 con, float x0, float y0) {
   const float detc = con.x * con.z - con.y * con.y;
   const float qc = (con.w + 1e-3f) * 1.02f + 0.01f;
@@ -78,29 +88,46 @@ __device__ inline uint32_t warp_mask(const float4 xyo, const float4 con, float x
   const float ry = sqrtf(qc * con.x / detc) + 0.01f;
   uint32_t m = 0;
 #pragma unroll
-  for (int w = 0; w < 8; ++w) {
-    const float bx0 = x0 + (float)((w & 1) * 8) + 0.5f, by0 = y0 + (float)((w >> 1) * 4) + 0.5f;
+  for (int w = 0; w < 4; ++w) {
+    const float bx0 = x0 + (float)((w & 1) * 8) + 0.5f, by0 = y0 + (float)((w >> 1) * 8) + 0.5f;
     const bool hit = (xyo.x + rx >= bx0) && (xyo.x - rx <= bx0 + 7.f) && (xyo.y + ry >= by0) &&
-                     (xyo.y - ry <= by0 + 3.f);
+                     (xyo.y - ry <= by0 + 7.f);
     m |= hit ? (1u << w) : 0u;
   }
   return m;
 }
 
-// alpha of a staged splat at pixel centre (px, py); returns false when the
-// splat cannot contribute (alpha < 1/255).  Shared by forward and backward
-// so both take identical decisions.
-__device__ inline bool splat_alpha(const float4 xyo, const float4 con, float px, float py,
-                                   float& dx, float& dy, float& G, float& alpha) {
-  dx = px - xyo.x;
-  dy = py - xyo.y;
-  const float q = con.x * dx * dx + 2.f * con.y * dx * dy + con.z * dy * dy;
-  // q_max = 2 ln(255 o): beyond it (with margin far above FP32 error)
-  // alpha is certainly below 1/255
-  if (q > con.w + 1e-3f) return false;
-  G = __expf(-0.5f * q);
-  alpha = fminf(kAlphaMax, xyo.z * G);
-  return alpha >= kAlphaMin;
+__device__ inline float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ inline float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Stages record r into slot `s` of the shared arrays.
+__device__ inline void stage_splat(int s, uint32_t r, const float4* __restrict__ splat, float x0, float y0,
+                                   float2* s_m, float4* s_q, float4* s_c, uint32_t* s_mask) {
+  const float4 xyo = splat[3 * (size_t)r];
+  const float4 con = splat[3 * (size_t)r + 1];
+  const float4 col = splat[3 * (size_t)r + 2];
+  s_m[s] = make_float2(xyo.x, xyo.y);
+  s_q[s] = make_float4(-kHalfLog2e * con.x, -2.f * kHalfLog2e * con.y, -kHalfLog2e * con.z, lg2_approx(xyo.z));
+  s_c[s] = make_float4(col.x, col.y, col.z, 1.f / xyo.z);
+  s_mask[s] = warp_mask(xyo, con, x0, y0);
+}
+
+// Exponent e of alpha_raw = 2^e at offset (dx, dy), given Adx = A * dx.
+// Written with explicit roundings so that every kernel computes the same
+// value from the same staged inputs.
+__device__ inline float splat_exponent(const float4 q, float Adx, float dx, float dy) {
+  const float t = __fmaf_rn(q.y, dy, Adx);                  // A dx + B dy
+  const float s = __fmaf_rn(__fmul_rn(q.z, dy), dy, q.w);   // C dy^2 + log2 o
+  return __fmaf_rn(t, dx, s);
 }
 
 __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
@@ -108,63 +135,90 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
     const uint32_t* __restrict__ ranges, const float* __restrict__ bg, float* __restrict__ image,
     float* __restrict__ T_final, uint32_t* __restrict__ n_contrib) {
   __shared__ TileInfo ti;
-  __shared__ float4 s_xyo[kThreads];
-  __shared__ float4 s_con[kThreads];
-  __shared__ float4 s_col[kThreads];
-  __shared__ uint32_t s_mask[kThreads];
+  __shared__ float2 s_m[kBatch];
+  __shared__ float4 s_q[kBatch];
+  __shared__ float4 s_c[kBatch];
+  __shared__ uint32_t s_mask[kBatch];
   const int gt = blockIdx.x;
   find_tile(batch, cams, gt, &ti);
   __syncthreads();
   int lx, ly;
-  tile_pixel(threadIdx.x, lx, ly);
+  tile_pixels(threadIdx.x, lx, ly);
   const uint32_t wbit = 1u << (threadIdx.x >> 5);
-  const int u = ti.tx * kTile + lx, v = ti.ty * kTile + ly;
-  const bool inside = u < ti.W && v < ti.H;
-  const float px = (float)u + 0.5f, py = (float)v + 0.5f;
+  const int u = ti.tx * kTile + lx, v0 = ti.ty * kTile + ly, v1 = v0 + 4;
+  const bool in0 = u < ti.W && v0 < ti.H, in1 = u < ti.W && v1 < ti.H;
+  const float px = (float)u + 0.5f, py0 = (float)v0 + 0.5f, py1 = (float)v1 + 0.5f;
   const float x0 = (float)(ti.tx * kTile), y0 = (float)(ti.ty * kTile);
   const uint32_t start = ranges[2 * gt], end = ranges[2 * gt + 1];
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-  uint32_t last = 0;
-  bool done = !inside;
-  for (uint32_t base = start; base < end; base += kThreads) {
-    if (__syncthreads_count(done) == kThreads) break;
-    const uint32_t idx = base + threadIdx.x;
-    if (idx < end) {
-      const uint32_t r = vals[idx];
-      const float4 xyo = splat[3 * (size_t)r];
-      const float4 con = splat[3 * (size_t)r + 1];
-      s_xyo[threadIdx.x] = xyo;
-      s_con[threadIdx.x] = con;
-      s_col[threadIdx.x] = splat[3 * (size_t)r + 2];
-      s_mask[threadIdx.x] = warp_mask(xyo, con, x0, y0);
+  float T0 = 1.f, T1 = 1.f;
+  float C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
+  uint32_t last0 = 0, last1 = 0;
+  bool done0 = !in0, done1 = !in1;
+  for (uint32_t base = start; base < end; base += kBatch) {
+    if (__syncthreads_count(done0 && done1) == kThreads) break;
+    for (int s = threadIdx.x; s < kBatch; s += kThreads) {
+      const uint32_t idx = base + s;
+      if (idx < end) stage_splat(s, vals[idx], splat, x0, y0, s_m, s_q, s_c, s_mask);
     }
     __syncthreads();
-    const int cnt = (int)min((uint32_t)kThreads, end - base);
-    for (int k = 0; k < cnt && !done; ++k) {
+    const int cnt = (int)min((uint32_t)kBatch, end - base);
+    for (int k = 0; k < cnt; ++k) {
+      if (done0 && done1) break;
       if (!(s_mask[k] & wbit)) continue;  // uniform across the warp
-      float dx, dy, G, alpha;
-      if (!splat_alpha(s_xyo[k], s_con[k], px, py, dx, dy, G, alpha)) continue;
-      const float Tn = T * (1.f - alpha);
-      if (Tn < kTMin) {
-        done = true;
-        break;
+      const float2 m = s_m[k];
+      const float4 q = s_q[k];
+      const float dx = px - m.x;
+      const float Adx = __fmul_rn(q.x, dx);
+      const float a0 = fminf(kAlphaMax, ex2_approx(splat_exponent(q, Adx, dx, py0 - m.y)));
+      const float a1 = fminf(kAlphaMax, ex2_approx(splat_exponent(q, Adx, dx, py1 - m.y)));
+      const bool c0 = !done0 && a0 >= kAlphaMin;
+      const bool c1 = !done1 && a1 >= kAlphaMin;
+      if (!(c0 || c1)) continue;
+      const float4 c = s_c[k];
+      const uint32_t pos1 = base - start + (uint32_t)k + 1u;
+      if (c0) {
+        const float Tn = T0 * (1.f - a0);
+        if (Tn < kTMin) {
+          done0 = true;
+        } else {
+          const float w = a0 * T0;
+          C00 += c.x * w;
+          C01 += c.y * w;
+          C02 += c.z * w;
+          T0 = Tn;
+          last0 = pos1;
+        }
       }
-      const float4 c = s_col[k];
-      const float w = alpha * T;
-      C0 += c.x * w;
-      C1 += c.y * w;
-      C2 += c.z * w;
-      T = Tn;
-      last = base - start + (uint32_t)k + 1u;
+      if (c1) {
+        const float Tn = T1 * (1.f - a1);
+        if (Tn < kTMin) {
+          done1 = true;
+        } else {
+          const float w = a1 * T1;
+          C10 += c.x * w;
+          C11 += c.y * w;
+          C12 += c.z * w;
+          T1 = Tn;
+          last1 = pos1;
+        }
+      }
     }
   }
-  if (inside) {
-    const size_t p = (size_t)ti.px_offset + (size_t)v * ti.W + u;
-    image[3 * p + 0] = C0 + T * bg[0];
-    image[3 * p + 1] = C1 + T * bg[1];
-    image[3 * p + 2] = C2 + T * bg[2];
-    T_final[p] = T;
-    n_contrib[p] = last;
+  if (in0) {
+    const size_t p = (size_t)ti.px_offset + (size_t)v0 * ti.W + u;
+    image[3 * p + 0] = C00 + T0 * bg[0];
+    image[3 * p + 1] = C01 + T0 * bg[1];
+    image[3 * p + 2] = C02 + T0 * bg[2];
+    T_final[p] = T0;
+    n_contrib[p] = last0;
+  }
+  if (in1) {
+    const size_t p = (size_t)ti.px_offset + (size_t)v1 * ti.W + u;
+    image[3 * p + 0] = C10 + T1 * bg[0];
+    image[3 * p + 1] = C11 + T1 * bg[1];
+    image[3 * p + 2] = C12 + T1 * bg[2];
+    T_final[p] = T1;
+    n_contrib[p] = last1;
   }
 }
 
@@ -192,6 +246,74 @@ __device__ inline float warp_sum8_transposed(const float* v, int lane) {
   return c;
 }
 
+// Per-pixel backward state.
+struct PixBwd {
+  float T, S0, S1, S2, v0, v1, v2;
+  uint32_t nc;
+};
+
+// Backward of one accepted splat at one pixel (alpha_raw = 2^e, alpha its
+// clamp); adds this pixel's screen-space gradients into g:
+// 0 mean2d x, 1 mean2d y, 2 conic a, 3 conic b, 4 conic c, 5 opacity,
+// 6..8 colour.
+__device__ inline void bwd_pixel(PixBwd& P, const float4 q, const float4 c, float dx, float dy, float araw,
+                                 float alpha, float* g) {
+  const float ra = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 0.01
+  const float Tk = P.T * ra;                      // transmittance before this splat
+  const float w = alpha * Tk;
+  g[6] += w * P.v0;
+  g[7] += w * P.v1;
+  g[8] += w * P.v2;
+  const float va = P.v0 * (c.x * Tk - P.S0 * ra) + P.v1 * (c.y * Tk - P.S1 * ra) + P.v2 * (c.z * Tk - P.S2 * ra);
+  P.S0 += c.x * w;
+  P.S1 += c.y * w;
+  P.S2 += c.z * w;
+  P.T = Tk;
+  if (araw < kAlphaMax) {
+    // dalpha/dq = -alpha/2 with q = a dx^2 + 2 b dx dy + c dy^2, d = pixel - mean;
+    // a = -2 ln2 A, b = -ln2 B, c = -2 ln2 C
+    const float vq = -0.5f * alpha * va;
+    const float t = 2.f * kLn2 * vq;
+    g[0] += t * (2.f * q.x * dx + q.y * dy);
+    g[1] += t * (q.y * dx + 2.f * q.z * dy);
+    g[2] += vq * dx * dx;
+    g[3] += 2.f * vq * dx * dy;
+    g[4] += vq * dy * dy;
+    g[5] += va * araw * c.w;  // dalpha/do = exp(-q/2) = alpha_raw / o
+  }
+}
+
+__device__ inline void load_pixel(PixBwd& P, bool inside, size_t p, const TileInfo& ti, const float* bg,
+                                  const float* __restrict__ image, const float* __restrict__ T_final,
+                                  const uint32_t* __restrict__ n_contrib, const float* __restrict__ v_image,
+                                  const float* __restrict__ target, float l1_weight, float& lsum) {
+  P.T = 1.f;
+  P.S0 = P.S1 = P.S2 = 0.f;
+  P.v0 = P.v1 = P.v2 = 0.f;
+  P.nc = 0;
+  if (!inside) return;
+  P.T = T_final[p];
+  P.nc = n_contrib[p];
+  P.S0 = P.T * bg[0];
+  P.S1 = P.T * bg[1];
+  P.S2 = P.T * bg[2];
+  if (v_image) {
+    P.v0 = v_image[3 * p];
+    P.v1 = v_image[3 * p + 1];
+    P.v2 = v_image[3 * p + 2];
+  } else {
+    const float s = l1_weight * ti.inv_norm;
+    const float d0 = image[3 * p] - target[3 * p];
+    const float d1 = image[3 * p + 1] - target[3 * p + 1];
+    const float d2 = image[3 * p + 2] - target[3 * p + 2];
+    P.v0 = d0 > 0.f ? s : (d0 < 0.f ? -s : 0.f);
+    P.v1 = d1 > 0.f ? s : (d1 < 0.f ? -s : 0.f);
+    P.v2 = d2 > 0.f ? s : (d2 < 0.f ? -s : 0.f);
+    lsum += s * (fabsf(d0) + fabsf(d1) + fabsf(d2));
+  }
+  if (P.v0 == 0.f && P.v1 == 0.f && P.v2 == 0.f) P.nc = 0;
+}
+
 __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
     gs_batch batch, gs_cameras cams, const float4* __restrict__ splat, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ ranges, const float* __restrict__ bg, const float* __restrict__ image,
@@ -199,12 +321,12 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
     const float* __restrict__ v_image, const float* __restrict__ target, float l1_weight, double* loss,
     float* __restrict__ v2d) {
   __shared__ TileInfo ti;
-  __shared__ float4 s_xyo[kThreads];
-  __shared__ float4 s_con[kThreads];
-  __shared__ float4 s_col[kThreads];
-  __shared__ uint32_t s_rec[kThreads];
-  __shared__ uint32_t s_mask[kThreads];
-  __shared__ float s_g[kThreads][9];
+  __shared__ float2 s_m[kBatch];
+  __shared__ float4 s_q[kBatch];
+  __shared__ float4 s_c[kBatch];
+  __shared__ uint32_t s_mask[kBatch];
+  __shared__ uint32_t s_rec[kBatch];
+  __shared__ float s_g[kBatch][9];
   __shared__ uint32_t s_max;
   __shared__ float s_loss[kThreads / 32];
   const int gt = blockIdx.x;
@@ -213,40 +335,21 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
   __syncthreads();
   const int lane = threadIdx.x & 31;
   int lx, ly;
-  tile_pixel(threadIdx.x, lx, ly);
+  tile_pixels(threadIdx.x, lx, ly);
   const uint32_t wbit = 1u << (threadIdx.x >> 5);
-  const int u = ti.tx * kTile + lx, v = ti.ty * kTile + ly;
-  const bool inside = u < ti.W && v < ti.H;
-  const float px = (float)u + 0.5f, py = (float)v + 0.5f;
+  const int u = ti.tx * kTile + lx, v0 = ti.ty * kTile + ly, v1 = v0 + 4;
+  const bool in0 = u < ti.W && v0 < ti.H, in1 = u < ti.W && v1 < ti.H;
+  const float px = (float)u + 0.5f, py0 = (float)v0 + 0.5f, py1 = (float)v1 + 0.5f;
   const float x0 = (float)(ti.tx * kTile), y0 = (float)(ti.ty * kTile);
   const uint32_t start = ranges[2 * gt];
-  float T = 1.f, S0 = 0.f, S1 = 0.f, S2 = 0.f, vC0 = 0.f, vC1 = 0.f, vC2 = 0.f;
-  uint32_t nc = 0;
   float lsum = 0.f;
-  if (inside) {
-    const size_t p = (size_t)ti.px_offset + (size_t)v * ti.W + u;
-    T = T_final[p];
-    nc = n_contrib[p];
-    S0 = T * bg[0];
-    S1 = T * bg[1];
-    S2 = T * bg[2];
-    if (v_image) {
-      vC0 = v_image[3 * p];
-      vC1 = v_image[3 * p + 1];
-      vC2 = v_image[3 * p + 2];
-    } else {
-      const float s = l1_weight * ti.inv_norm;
-      const float d0 = image[3 * p] - target[3 * p];
-      const float d1 = image[3 * p + 1] - target[3 * p + 1];
-      const float d2 = image[3 * p + 2] - target[3 * p + 2];
-      vC0 = d0 > 0.f ? s : (d0 < 0.f ? -s : 0.f);
-      vC1 = d1 > 0.f ? s : (d1 < 0.f ? -s : 0.f);
-      vC2 = d2 > 0.f ? s : (d2 < 0.f ? -s : 0.f);
-      lsum = s * (fabsf(d0) + fabsf(d1) + fabsf(d2));
-    }
-    if (vC0 == 0.f && vC1 == 0.f && vC2 == 0.f) nc = 0;
-    atomicMax(&s_max, nc);
-  }
+  PixBwd P0, P1;
+  load_pixel(P0, in0, (size_t)ti.px_offset + (size_t)v0 * ti.W + u, ti, bg, image, T_final, n_contrib, v_image,
+             target, l1_weight, lsum);
+  load_pixel(P1, in1, (size_t)ti.px_offset + (size_t)v1 * ti.W + u, ti, bg, image, T_final, n_contrib, v_image,
+             target, l1_weight, lsum);
+  const uint32_t nc_max = max(P0.nc, P1.nc);
+  if (nc_max) atomicMax(&s_max, nc_max);
   if (loss != nullptr && v_image == nullptr) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
@@ -259,69 +362,52 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
     if (t != 0.0) atomicAdd(loss, t);
   }
   const uint32_t n_end = s_max;  // positions [0, n_end) of the tile list
-  const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, nc);
-  for (int bend = (int)n_end; bend > 0; bend -= kThreads) {
-    const int bstart = max(0, bend - kThreads);
+  const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, nc_max);
+  for (int bend = (int)n_end; bend > 0; bend -= kBatch) {
+    const int bstart = max(0, bend - kBatch);
     const int cnt = bend - bstart;
-    if (threadIdx.x < cnt) {
-      const uint32_t r = vals[start + bstart + threadIdx.x];
-      const float4 xyo = splat[3 * (size_t)r];
-      const float4 con = splat[3 * (size_t)r + 1];
-      s_rec[threadIdx.x] = r;
-      s_xyo[threadIdx.x] = xyo;
-      s_con[threadIdx.x] = con;
-      s_col[threadIdx.x] = splat[3 * (size_t)r + 2];
-      s_mask[threadIdx.x] = warp_mask(xyo, con, x0, y0);
-    }
+    for (int s = threadIdx.x; s < kBatch; s += kThreads) {
+      if (s < cnt) {
+        const uint32_t r = vals[start + bstart + s];
+        s_rec[s] = r;
+        stage_splat(s, r, splat, x0, y0, s_m, s_q, s_c, s_mask);
+      }
 #pragma unroll
-    for (int i = 0; i < 9; ++i) s_g[threadIdx.x][i] = 0.f;
+      for (int i = 0; i < 9; ++i) s_g[s][i] = 0.f;
+    }
     __syncthreads();
     for (int k = cnt - 1; k >= 0; --k) {
       const uint32_t pos = (uint32_t)(bstart + k);
       // uniform across the warp: past all its pixels' last contributor, or
-      // the splat cannot reach its 8x4 block
+      // the splat cannot reach its 8x8 block
       if (pos >= warp_nc || !(s_mask[k] & wbit)) continue;
+      const float2 m = s_m[k];
+      const float4 q = s_q[k];
+      const float dx = px - m.x;
+      const float Adx = __fmul_rn(q.x, dx);
       float g[9];
-      bool contrib = false;
-      if (pos < nc) {
-        float dx, dy, G, alpha;
-        const float4 xyo = s_xyo[k];
-        const float4 con = s_con[k];
-        if (splat_alpha(xyo, con, px, py, dx, dy, G, alpha)) {
-          contrib = true;
-          const float4 c = s_col[k];
-          const float ra = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 0.01
-          const float Tk = T * ra;
-          const float w = alpha * Tk;
-          g[6] = w * vC0;
-          g[7] = w * vC1;
-          g[8] = w * vC2;
-          const float va = vC0 * (c.x * Tk - S0 * ra) + vC1 * (c.y * Tk - S1 * ra) +
-                           vC2 * (c.z * Tk - S2 * ra);
-          S0 += c.x * w;
-          S1 += c.y * w;
-          S2 += c.z * w;
-          T = Tk;
-          if (xyo.z * G < kAlphaMax) {
-            const float vq = -0.5f * alpha * va;
-            g[5] = va * G;
-            g[0] = -2.f * vq * (con.x * dx + con.y * dy);
-            g[1] = -2.f * vq * (con.y * dx + con.z * dy);
-            g[2] = vq * dx * dx;
-            g[3] = 2.f * vq * dx * dy;
-            g[4] = vq * dy * dy;
-          } else {
 #pragma unroll
-            for (int i = 0; i < 6; ++i) g[i] = 0.f;
-          }
+      for (int i = 0; i < 9; ++i) g[i] = 0.f;
+      bool contrib = false;
+      if (pos < P0.nc) {
+        const float dy = py0 - m.y;
+        const float araw = ex2_approx(splat_exponent(q, Adx, dx, dy));
+        const float alpha = fminf(kAlphaMax, araw);
+        if (alpha >= kAlphaMin) {
+          contrib = true;
+          bwd_pixel(P0, q, s_c[k], dx, dy, araw, alpha, g);
         }
       }
-      if (!contrib) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = 0.f;
+      if (pos < P1.nc) {
+        const float dy = py1 - m.y;
+        const float araw = ex2_approx(splat_exponent(q, Adx, dx, dy));
+        const float alpha = fminf(kAlphaMax, araw);
+        if (alpha >= kAlphaMin) {
+          contrib = true;
+          bwd_pixel(P1, q, s_c[k], dx, dy, araw, alpha, g);
+        }
       }
       if (__ballot_sync(0xffffffffu, contrib)) {
-        // order: 0 mx, 1 my, 2 a, 3 b, 4 c, 5 opacity, 6 r, 7 g | 8 b
         const float s8 = warp_sum8_transposed(g, lane);
         float s9 = g[8];
 #pragma unroll
@@ -331,14 +417,14 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
       }
     }
     __syncthreads();
-    if (threadIdx.x < cnt) {
-      const float* sg = s_g[threadIdx.x];
+    for (int s = threadIdx.x; s < cnt; s += kThreads) {
+      const float* sg = s_g[s];
       const float4 a = make_float4(sg[0], sg[1], sg[2], sg[3]);
       const float4 b = make_float4(sg[4], sg[5], sg[6], sg[7]);
-      const bool nz = a.x != 0.f || a.y != 0.f || a.z != 0.f || a.w != 0.f || b.x != 0.f ||
-                      b.y != 0.f || b.z != 0.f || b.w != 0.f || sg[8] != 0.f;
+      const bool nz = a.x != 0.f || a.y != 0.f || a.z != 0.f || a.w != 0.f || b.x != 0.f || b.y != 0.f ||
+                      b.z != 0.f || b.w != 0.f || sg[8] != 0.f;
       if (nz) {
-        float4* dst = reinterpret_cast<float4*>(v2d) + 3 * (size_t)s_rec[threadIdx.x];
+        float4* dst = reinterpret_cast<float4*>(v2d) + 3 * (size_t)s_rec[s];
         atomicAdd(dst, a);
         atomicAdd(dst + 1, b);
         atomicAdd(reinterpret_cast<float*>(dst + 2), sg[8]);
