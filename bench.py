@@ -302,6 +302,7 @@ def algorithmic_model(js):
     I = sum(rr.n_instances() for rr in js.renderers)
     vis = sum(int((rr.proj.n_tiles[:N * rr.batch.B] > 0).sum().item()) for rr in js.renderers)
     pairs_bwd = sum(int(rr.n_contrib.to(torch.int64).sum().item()) for rr in js.renderers)
+    added = sum(rr.count_added(js.g, js.Rt) for rr in js.renderers)
     n_tiles_total = sum(rr.batch.n_tiles for rr in js.renderers)
     pbytes = N * (44 + 12 * K)
     M_b = int(sum(int(js.view_obs_offset[v + 1] - js.view_obs_offset[v]) for v in js.views))
@@ -314,7 +315,8 @@ def algorithmic_model(js):
         "track": M_b * 24 + min(M_b, js.X.shape[0]) * 24,
         "adam": (N * (7 + 4 + 3 * K) + js.X.shape[0] * 3) * 4 * 7,
     }
-    return model, dict(instances=I, visible_records=vis, pairs_bwd=pairs_bwd, pixels=P, obs_in_batch=M_b)
+    return model, dict(instances=I, visible_records=vis, pairs_bwd=pairs_bwd, added=added, pixels=P,
+                       obs_in_batch=M_b)
 
 
 def run_ours(args):
@@ -339,6 +341,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         return
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    from paper_2603_04847_gb300.autotune import autotune
+    tune = autotune(js, use_cache=False)
+    js.ensure_capacity()
     use_graph = not args.no_graph
     if use_graph:
         js.capture(warmup=1)
@@ -391,14 +396,23 @@ def run_ours(args):
     # their pair throughput against the FP32 lane peak
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = sms * 128 * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12   # TFLOP/s, FMA = 2
-    FLOP_PER_PAIR = {"render_fwd": 26.0, "raster_bwd": 86.0}
-    if dominant in FLOP_PER_PAIR:
-        fl = counts["pairs_bwd"] * FLOP_PER_PAIR[dominant]
+    # Algorithmic flops of compositing (FMA = 2): every examined position
+    # (sum of n_contrib) costs the alpha test, 10 flops (exponent 8, exp 1,
+    # clamp 1); every composited splat (sum of n_added) costs 9 more in the
+    # forward (transmittance 2, weight 1, colour 6) and 60 more in the
+    # backward (transmittance and reciprocal 3, colour gradient 6,
+    # alpha gradient 15, colour-behind update 6, conic/mean/opacity
+    # gradients 30).
+    ALU = {"render_fwd": (10.0, 9.0), "raster_bwd": (10.0, 60.0)}
+    if dominant in ALU:
+        per_pos, per_add = ALU[dominant]
+        fl = counts["pairs_bwd"] * per_pos + counts["added"] * per_add
         ach = fl / (st_ms[dominant] * 1e-3) / 1e12
         roof = dict(kernel=dominant, bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
                     traffic=None, peak_source="derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (
                         sms, peaks.get("sm_max_mhz", 2070.0)),
-                    work="%d compositing pairs x %.0f flop" % (counts["pairs_bwd"], FLOP_PER_PAIR[dominant]))
+                    work="%d examined positions x %.0f + %d composited splats x %.0f flop" % (
+                        counts["pairs_bwd"], per_pos, counts["added"], per_add))
     else:
         ach = model[dominant] / (st_ms[dominant] * 1e-3) / 1e9
         roof = dict(kernel=dominant, bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak,
@@ -450,6 +464,8 @@ def run_ours(args):
                     data="synthetic",
                     config=dict(workload_desc(args.workload, w), mode=args.mode,
                                 graph=use_graph, l2="flushed between steps (256 MB write)",
+                                tuning=dict(render_batch=tune["render_batch"],
+                                            sort_blocks_per_sm=tune["sort_blocks_per_sm"]),
                                 parallelism="replicas" if ws > 1 else "single GPU"),
                     steps_per_s=1e3 / ms, e2e=e2e, gpu_launches=js.kernels_per_step() * args.steps,
                     roofline=roof, hbm_step=hbm_step, stages=stages, counts=counts, clocks=clk,

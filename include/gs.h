@@ -145,13 +145,38 @@ typedef struct gs_adam {
   const int32_t* step;
 } gs_adam;
 
+/* Launch tuning, process-wide (chosen by an autotuner; results do not
+ * depend on it).  render_batch: splat records staged in shared memory per
+ * round by the compositing kernels (64, 128 or 256); sort_blocks_per_sm:
+ * thread blocks per SM of the radix passes (1..8).  Workspace sizes depend
+ * on sort_blocks_per_sm: query them after changing it.  Not synchronised:
+ * set it while no other thread calls the library. */
+typedef struct gs_tuning {
+  int32_t render_batch;
+  int32_t sort_blocks_per_sm;
+} gs_tuning;
+
+/* One parameter array of gs_adam_update_groups (learning rate per group). */
+typedef struct gs_adam_group {
+  float* p;
+  const float* g;
+  float* m;
+  float* v;
+  int64_t n;
+  float lr;
+  int32_t _pad;
+} gs_adam_group;
+
 /* ---------------------------------------------------------------------- */
 
 int gs_abi_version(void);
+gs_status gs_set_tuning(const gs_tuning* t);
+gs_status gs_get_tuning(gs_tuning* t);
 const char* gs_last_error(void);
 /* sizeof of the ABI structs, for bindings to verify their layout:
  * 0 gs_gaussians, 1 gs_gaussian_grads, 2 gs_cameras, 3 gs_batch,
- * 4 gs_projected, 5 gs_adam.  Returns 0 for an unknown id. */
+ * 4 gs_projected, 5 gs_adam, 6 gs_tuning, 7 gs_adam_group.  Returns 0 for
+ * an unknown id. */
 size_t gs_struct_size(int which);
 /* Number of streaming multiprocessors of the current device (0 on error). */
 int gs_device_sm_count(void);
@@ -202,11 +227,14 @@ gs_status gs_sort_tiles(int32_t n_gaussians, const gs_cameras* cams,
  * C = sum c alpha T + T_final bg.  Writes image [n_pixels,3],
  * T_final [n_pixels] and n_contrib [n_pixels] (position in the tile list,
  * plus one, of the last splat added; 0 if none).  bg: [3] device.
+ * n_added [n_pixels] (may be NULL) receives the number of splats added per
+ * pixel (a diagnostic: the work count of the compositing).
  */
 gs_status gs_render_fwd(const gs_batch* batch, const gs_cameras* cams,
                         const gs_projected* proj, const uint32_t* vals,
                         const uint32_t* ranges, const float* bg, float* image,
-                        float* T_final, uint32_t* n_contrib, gs_stream stream);
+                        float* T_final, uint32_t* n_contrib, uint32_t* n_added,
+                        gs_stream stream);
 
 /*
  * gs_render_bwd — backward of gs_project + gs_render_fwd.
@@ -328,6 +356,11 @@ gs_status pose_se3_update(int32_t n_cams, const float* T0, float* xi,
  * moments m, v (Kingma & Ba, bias-corrected with t = *hp->step). */
 gs_status gs_adam_update(float* p, const float* g, float* m, float* v,
                          int64_t n, const gs_adam* hp, gs_stream stream);
+
+/* gs_adam_update_groups — gs_adam_update on up to 8 arrays in one launch,
+ * each with its own learning rate (hp->lr is ignored). */
+gs_status gs_adam_update_groups(const gs_adam_group* groups, int32_t n_groups,
+                                const gs_adam* hp, gs_stream stream);
 
 /* gs_step_advance — *step += 1 on the device. */
 gs_status gs_step_advance(int32_t* step, gs_stream stream);

@@ -51,7 +51,16 @@ class gs_adam(ctypes.Structure):
                 ("step", c_void_p)]
 
 
-STRUCTS = [gs_gaussians, gs_gaussian_grads, gs_cameras, gs_batch, gs_projected, gs_adam]
+class gs_tuning(ctypes.Structure):
+    _fields_ = [("render_batch", c_int32), ("sort_blocks_per_sm", c_int32)]
+
+
+class gs_adam_group(ctypes.Structure):
+    _fields_ = [("p", c_void_p), ("g", c_void_p), ("m", c_void_p), ("v", c_void_p), ("n", c_int64),
+                ("lr", c_float), ("_pad", c_int32)]
+
+
+STRUCTS = [gs_gaussians, gs_gaussian_grads, gs_cameras, gs_batch, gs_projected, gs_adam, gs_tuning, gs_adam_group]
 
 # name -> (restype, argtypes)
 PROTOTYPES = {
@@ -59,12 +68,15 @@ PROTOTYPES = {
     "gs_last_error": (ctypes.c_char_p, []),
     "gs_struct_size": (c_size_t, [ctypes.c_int]),
     "gs_device_sm_count": (ctypes.c_int, []),
+    "gs_set_tuning": (ctypes.c_int, [c_void_p]),
+    "gs_get_tuning": (ctypes.c_int, [c_void_p]),
+    "gs_adam_update_groups": (ctypes.c_int, [c_void_p, c_int32, c_void_p, c_void_p]),
     "gs_project": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "gs_sort_tiles_workspace": (ctypes.c_int, [c_int32, c_void_p, c_size_t, ctypes.POINTER(c_size_t)]),
     "gs_sort_tiles": (ctypes.c_int, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
                                      c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),
     "gs_render_fwd": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
-                                     c_void_p, c_void_p, c_void_p]),
+                                     c_void_p, c_void_p, c_void_p, c_void_p]),
     "gs_render_bwd_workspace": (ctypes.c_int, [c_int32, c_void_p, ctypes.POINTER(c_size_t)]),
     "gs_render_bwd": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                      c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_void_p,

@@ -201,12 +201,14 @@ def gs_sort_tiles(n: int, cams: Cameras, batch: Batch, proj: Projected, tl: Tile
 
 
 def gs_render_fwd(batch: Batch, cams: Cameras, proj: Projected, tl: TileLists, bg: torch.Tensor,
-                  image: torch.Tensor, T_final: torch.Tensor, n_contrib: torch.Tensor, Rt=None, stream=None):
+                  image: torch.Tensor, T_final: torch.Tensor, n_contrib: torch.Tensor, Rt=None, stream=None,
+                  n_added: torch.Tensor = None):
     lib = _lib.load()
-    _need_cuda(bg, image, T_final, n_contrib)
+    _need_cuda(bg, image, T_final, n_contrib, n_added)
     cc, bc, pc = cams.c(Rt), batch.c(), proj.c()
     check(lib.gs_render_fwd(ctypes.byref(bc), ctypes.byref(cc), ctypes.byref(pc), _p(tl.vals), _p(tl.ranges),
-                            _p(bg), _p(image), _p(T_final), _p(n_contrib), _stream(stream)), "gs_render_fwd")
+                            _p(bg), _p(image), _p(T_final), _p(n_contrib), _p(n_added), _stream(stream)),
+          "gs_render_fwd")
 
 
 def render_bwd_workspace_bytes(n: int, batch: Batch) -> int:
@@ -302,6 +304,30 @@ def gs_adam_update(p, g, m, v, hp, stream=None):
     _need_cuda(p, g, m, v)
     check(lib.gs_adam_update(_p(p), _p(g), _p(m), _p(v), p.numel(), ctypes.byref(hp), _stream(stream)),
           "gs_adam_update")
+
+
+def gs_adam_update_groups(groups, beta1, beta2, eps, step, stream=None):
+    """groups: list of (p, g, m, v, lr), at most 8; one launch."""
+    lib = _lib.load()
+    arr = (_lib.gs_adam_group * len(groups))()
+    for i, (p, g, m, v, lr) in enumerate(groups):
+        _need_cuda(p, g, m, v)
+        arr[i] = _lib.gs_adam_group(p.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(), p.numel(), float(lr), 0)
+    hp = adam_c(0.0, beta1, beta2, eps, step)
+    check(lib.gs_adam_update_groups(arr, len(groups), ctypes.byref(hp), _stream(stream)), "gs_adam_update_groups")
+
+
+def gs_set_tuning(render_batch: int = 256, sort_blocks_per_sm: int = 2):
+    lib = _lib.load()
+    t = _lib.gs_tuning(int(render_batch), int(sort_blocks_per_sm))
+    check(lib.gs_set_tuning(ctypes.byref(t)), "gs_set_tuning")
+
+
+def gs_get_tuning():
+    lib = _lib.load()
+    t = _lib.gs_tuning()
+    check(lib.gs_get_tuning(ctypes.byref(t)), "gs_get_tuning")
+    return dict(render_batch=t.render_batch, sort_blocks_per_sm=t.sort_blocks_per_sm)
 
 
 def gs_step_advance(step, stream=None):

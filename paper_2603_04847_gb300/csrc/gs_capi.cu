@@ -73,6 +73,12 @@ size_t pose_partial_bytes(int N, const gs_batch& b) {
 
 }  // namespace
 
+namespace {
+gs_tuning g_tuning = {256, 2};
+}
+
+const gs_tuning& tuning() { return g_tuning; }
+
 int device_sm_count() {
   static int cache[64] = {0};
   int dev = 0;
@@ -103,11 +109,29 @@ size_t gs_struct_size(int which) {
     case 3: return sizeof(gs_batch);
     case 4: return sizeof(gs_projected);
     case 5: return sizeof(gs_adam);
+    case 6: return sizeof(gs_tuning);
+    case 7: return sizeof(gs_adam_group);
     default: return 0;
   }
 }
 
 int gs_device_sm_count(void) { return device_sm_count(); }
+
+gs_status gs_set_tuning(const gs_tuning* t) {
+  if (!t) return fail(GS_ERR_ARG, "gs_set_tuning: null");
+  if (t->render_batch != 64 && t->render_batch != 128 && t->render_batch != 256)
+    return fail(GS_ERR_ARG, "gs_set_tuning: render_batch must be 64, 128 or 256");
+  if (t->sort_blocks_per_sm < 1 || t->sort_blocks_per_sm > 8)
+    return fail(GS_ERR_ARG, "gs_set_tuning: sort_blocks_per_sm must be 1..8");
+  g_tuning = *t;
+  return GS_OK;
+}
+
+gs_status gs_get_tuning(gs_tuning* t) {
+  if (!t) return fail(GS_ERR_ARG, "gs_get_tuning: null");
+  *t = g_tuning;
+  return GS_OK;
+}
 
 gs_status gs_project(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
                      const gs_projected* out, int32_t* status, gs_stream stream) {
@@ -154,13 +178,13 @@ gs_status gs_sort_tiles(int32_t n_gaussians, const gs_cameras* cams, const gs_ba
 
 gs_status gs_render_fwd(const gs_batch* batch, const gs_cameras* cams, const gs_projected* proj,
                         const uint32_t* vals, const uint32_t* ranges, const float* bg, float* image,
-                        float* T_final, uint32_t* n_contrib, gs_stream stream) {
+                        float* T_final, uint32_t* n_contrib, uint32_t* n_added, gs_stream stream) {
   gs_status s;
   if ((s = check_batch(batch)) || (s = check_cameras(cams)) || (s = check_projected(proj))) return s;
   if (!vals || !ranges || !bg || !image || !T_final || !n_contrib)
     return fail(GS_ERR_ARG, "gs_render_fwd: null argument");
   cudaError_t e = launch_render_fwd(*batch, *cams, *proj, vals, ranges, bg, image, T_final, n_contrib,
-                                    (cudaStream_t)stream);
+                                    n_added, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "gs_render_fwd");
   return GS_OK;
 }
@@ -297,6 +321,23 @@ gs_status gs_adam_update(float* p, const float* g, float* m, float* v, int64_t n
     return fail(GS_ERR_NONFINITE, "gs_adam_update: non-finite hyperparameter");
   cudaError_t e = launch_adam(p, g, m, v, n, *hp, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "gs_adam_update");
+  return GS_OK;
+}
+
+gs_status gs_adam_update_groups(const gs_adam_group* groups, int32_t n_groups, const gs_adam* hp,
+                                gs_stream stream) {
+  if (!groups || !hp || !hp->step || n_groups < 0 || n_groups > 8)
+    return fail(GS_ERR_ARG, "gs_adam_update_groups: bad argument (1..8 groups)");
+  if (!std::isfinite(hp->beta1) || !std::isfinite(hp->beta2) || !std::isfinite(hp->eps))
+    return fail(GS_ERR_NONFINITE, "gs_adam_update_groups: non-finite hyperparameter");
+  for (int i = 0; i < n_groups; ++i) {
+    const gs_adam_group& a = groups[i];
+    if (a.n < 0 || (a.n > 0 && (!a.p || !a.g || !a.m || !a.v)))
+      return fail(GS_ERR_ARG, "gs_adam_update_groups: bad group %d", i);
+    if (!std::isfinite(a.lr)) return fail(GS_ERR_NONFINITE, "gs_adam_update_groups: non-finite lr in group %d", i);
+  }
+  cudaError_t e = launch_adam_groups(groups, n_groups, *hp, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_adam_update_groups");
   return GS_OK;
 }
 

@@ -14,6 +14,8 @@
 namespace gs {
 
 int device_sm_count();
+// Process-wide launch tuning (gs_set_tuning); defaults when never set.
+const gs_tuning& tuning();
 
 cudaError_t launch_project_fwd(const gs_gaussians& g, const gs_cameras& cams, const gs_batch& batch,
                                const gs_projected& out, int32_t* status, cudaStream_t st);
@@ -32,7 +34,8 @@ cudaError_t launch_sort_tiles(int N, const gs_cameras& cams, const gs_batch& bat
 
 cudaError_t launch_render_fwd(const gs_batch& batch, const gs_cameras& cams, const gs_projected& proj,
                               const uint32_t* vals, const uint32_t* ranges, const float* bg,
-                              float* image, float* T_final, uint32_t* n_contrib, cudaStream_t st);
+                              float* image, float* T_final, uint32_t* n_contrib, uint32_t* n_added,
+                              cudaStream_t st);
 cudaError_t launch_render_bwd(const gs_batch& batch, const gs_cameras& cams, const gs_projected& proj,
                               const uint32_t* vals, const uint32_t* ranges, const float* bg,
                               const float* image, const float* T_final, const uint32_t* n_contrib,
@@ -52,6 +55,7 @@ cudaError_t launch_pose_update(int V, const float* T0, float* xi, const double* 
                                float* m, float* v, const gs_adam* hp, float* Rt_out, cudaStream_t st);
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, const gs_adam& hp,
                         cudaStream_t st);
+cudaError_t launch_adam_groups(const gs_adam_group* groups, int n_groups, const gs_adam& hp, cudaStream_t st);
 cudaError_t launch_step_advance(int32_t* step, cudaStream_t st);
 
 // Error reporting and argument checks shared with entry points outside

@@ -170,6 +170,63 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
   }
 }
 
+// Several Adam groups in one launch: the index space is cut into chunks of
+// kAdamChunk elements, chunk c belonging to the group whose chunk range holds
+// it; 16-byte aligned groups use 128-bit loads and stores.
+constexpr int kAdamChunk = 4096;
+constexpr int kAdamMaxGroups = 8;
+
+struct AdamGroups {
+  gs_adam_group g[kAdamMaxGroups];
+  int chunk_start[kAdamMaxGroups + 1];
+  int n;
+};
+
+__device__ inline void adam_elem(float& p, float g, float& m, float& v, float a, float beta1, float beta2,
+                                 float rb2, float eps) {
+  m = beta1 * m + (1.f - beta1) * g;
+  v = beta2 * v + (1.f - beta2) * g * g;
+  p -= a * m / (sqrtf(v * rb2) + eps);
+}
+
+__global__ void __launch_bounds__(256) adam_groups_kernel(AdamGroups G, float beta1, float beta2, float eps,
+                                                          const int32_t* __restrict__ step) {
+  const int t = *step;
+  const float bc1 = 1.f - powf(beta1, (float)t);
+  const float rb2 = 1.f / (1.f - powf(beta2, (float)t));
+  const int n_chunks = G.chunk_start[G.n];
+  for (int c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+    int gi = 0;
+    while (c >= G.chunk_start[gi + 1]) ++gi;
+    const gs_adam_group A = G.g[gi];
+    const int64_t lo = (int64_t)(c - G.chunk_start[gi]) * kAdamChunk;
+    const int64_t hi = min(lo + (int64_t)kAdamChunk, A.n);
+    const float a = A.lr / bc1;
+    const bool vec = (((uintptr_t)A.p | (uintptr_t)A.g | (uintptr_t)A.m | (uintptr_t)A.v) & 15) == 0;
+    if (vec) {
+      const int64_t hi4 = lo + ((hi - lo) & ~(int64_t)3);
+      for (int64_t i = lo + 4 * threadIdx.x; i < hi4; i += 4 * blockDim.x) {
+        float4 p = *reinterpret_cast<float4*>(A.p + i);
+        const float4 g = *reinterpret_cast<const float4*>(A.g + i);
+        float4 m = *reinterpret_cast<float4*>(A.m + i);
+        float4 v = *reinterpret_cast<float4*>(A.v + i);
+        adam_elem(p.x, g.x, m.x, v.x, a, beta1, beta2, rb2, eps);
+        adam_elem(p.y, g.y, m.y, v.y, a, beta1, beta2, rb2, eps);
+        adam_elem(p.z, g.z, m.z, v.z, a, beta1, beta2, rb2, eps);
+        adam_elem(p.w, g.w, m.w, v.w, a, beta1, beta2, rb2, eps);
+        *reinterpret_cast<float4*>(A.p + i) = p;
+        *reinterpret_cast<float4*>(A.m + i) = m;
+        *reinterpret_cast<float4*>(A.v + i) = v;
+      }
+      for (int64_t i = hi4 + threadIdx.x; i < hi; i += blockDim.x)
+        adam_elem(A.p[i], A.g[i], A.m[i], A.v[i], a, beta1, beta2, rb2, eps);
+    } else {
+      for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        adam_elem(A.p[i], A.g[i], A.m[i], A.v[i], a, beta1, beta2, rb2, eps);
+    }
+  }
+}
+
 __global__ void step_advance_kernel(int32_t* step) { *step += 1; }
 
 __global__ void pose_partial_finalize_kernel(const double* __restrict__ partial, int n_blocks,
@@ -217,6 +274,22 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n,
   const int64_t want = (n + threads - 1) / threads;
   const int blocks = (int)std::min<int64_t>(want, (int64_t)device_sm_count() * 8);
   adam_kernel<<<blocks, threads, 0, st>>>(p, g, m, v, n, hp.lr, hp.beta1, hp.beta2, hp.eps, hp.step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam_groups(const gs_adam_group* groups, int n_groups, const gs_adam& hp, cudaStream_t st) {
+  AdamGroups G;
+  G.n = n_groups;
+  G.chunk_start[0] = 0;
+  for (int i = 0; i < n_groups; ++i) {
+    G.g[i] = groups[i];
+    G.chunk_start[i + 1] = G.chunk_start[i] + (int)((groups[i].n + kAdamChunk - 1) / kAdamChunk);
+  }
+  for (int i = n_groups; i < kAdamMaxGroups; ++i) G.chunk_start[i + 1] = G.chunk_start[n_groups];
+  const int n_chunks = G.chunk_start[n_groups];
+  if (n_chunks == 0) return cudaSuccess;
+  const int blocks = std::min(n_chunks, device_sm_count() * 8);
+  adam_groups_kernel<<<blocks, 256, 0, st>>>(G, hp.beta1, hp.beta2, hp.eps, hp.step);
   return cudaGetLastError();
 }
 

@@ -138,22 +138,41 @@ __device__ inline void view_geo(const GaussGeo& G, const SlotCam& c, float near_
   V.dir[2] = d2 * idn;
 }
 
+constexpr int kProjThreads = 128;
+
+// SH coefficients of the block's Gaussians [j0, j0 + n_local), contiguous in
+// global memory, loaded with coalesced reads into shared memory transposed
+// (coefficient-major, one padded column per thread) so that each thread then
+// reads its own 3K values without bank conflicts.
+template <int KK>
+__device__ inline void load_sh_block(const float* __restrict__ sh, int j0, int n_local,
+                                     float (*s_sh)[kProjThreads + 1]) {
+  const float* src = sh + (size_t)j0 * KK;
+  const int total = n_local * KK;
+  for (int f = threadIdx.x; f < total; f += kProjThreads) {
+    const int jl = f / KK;
+    s_sh[f - jl * KK][jl] = src[f];
+  }
+}
+
 template <int DEG>
-__global__ void __launch_bounds__(256) project_fwd_kernel(gs_gaussians g, gs_cameras cams,
-                                                          gs_batch batch, gs_projected out,
-                                                          int32_t* status) {
+__global__ void __launch_bounds__(kProjThreads) project_fwd_kernel(gs_gaussians g, gs_cameras cams,
+                                                                   gs_batch batch, gs_projected out,
+                                                                   int32_t* status) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   __shared__ SlotCam sc[GS_MAX_BATCH];
+  __shared__ float s_sh[K * 3][kProjThreads + 1];
   load_slot_cams(cams, batch, sc);
-  __syncthreads();
   const int N = g.n;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = blockIdx.x * kProjThreads;
+  load_sh_block<K * 3>(g.sh, j0, min(kProjThreads, N - j0), s_sh);
+  __syncthreads();
+  const int j = j0 + threadIdx.x;
   if (j >= N) return;
   const GaussGeo G = load_geo(g, j);
   float shv[K * 3];
-  const float* shp = g.sh + (size_t)j * K * 3;
 #pragma unroll
-  for (int i = 0; i < K * 3; ++i) shv[i] = shp[i];
+  for (int i = 0; i < K * 3; ++i) shv[i] = s_sh[i][threadIdx.x];
   bool ok = G.ok;
 #pragma unroll
   for (int i = 0; i < K * 3; ++i) ok = ok && finitef(shv[i]);
@@ -211,19 +230,34 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(gs_gaussians g, gs_cam
 // 0 mean2d x, 1 mean2d y, 2 conic a, 3 conic b, 4 conic c, 5 opacity,
 // 6..8 colour, 9..11 unused.
 template <int DEG>
-__global__ void __launch_bounds__(256) project_bwd_kernel(gs_gaussians g, gs_cameras cams,
-                                                          gs_batch batch, gs_projected proj,
-                                                          const float* __restrict__ v2d,
-                                                          gs_gaussian_grads dg,
-                                                          double* __restrict__ partial) {
+constexpr size_t project_bwd_smem() {
+  return sizeof(float) * 2 * (DEG + 1) * (DEG + 1) * 3 * (kProjThreads + 1);
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(kProjThreads, 3) project_bwd_kernel(gs_gaussians g, gs_cameras cams,
+                                                                      gs_batch batch, gs_projected proj,
+                                                                      const float* __restrict__ v2d,
+                                                                      gs_gaussian_grads dg,
+                                                                      double* __restrict__ partial) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   __shared__ SlotCam sc[GS_MAX_BATCH];
   __shared__ double s_tan[GS_MAX_BATCH * 6];
+  // dynamic: coefficients and their gradient accumulators, one padded
+  // column per thread
+  extern __shared__ float s_dyn[];
+  float (*s_sh)[kProjThreads + 1] = reinterpret_cast<float (*)[kProjThreads + 1]>(s_dyn);
+  float (*s_vsh)[kProjThreads + 1] = reinterpret_cast<float (*)[kProjThreads + 1]>(s_dyn + K * 3 * (kProjThreads + 1));
   load_slot_cams(cams, batch, sc);
   for (int i = threadIdx.x; i < batch.B * 6; i += blockDim.x) s_tan[i] = 0.0;
-  __syncthreads();
   const int N = g.n;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = blockIdx.x * kProjThreads;
+  const int n_local = min(kProjThreads, N - j0);
+  load_sh_block<K * 3>(g.sh, j0, n_local, s_sh);
+#pragma unroll
+  for (int i = 0; i < K * 3; ++i) s_vsh[i][threadIdx.x] = 0.f;
+  __syncthreads();
+  const int j = j0 + threadIdx.x;
   const bool active = j < N;
   GaussGeo G;
   if (active) G = load_geo(g, j);
@@ -232,26 +266,32 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(gs_gaussians g, gs_cam
 #pragma unroll
   for (int i = 0; i < 9; ++i) GM[i] = 0.f;
   float vol = 0.f;
-  float vsh[K * 3];
-#pragma unroll
-  for (int i = 0; i < K * 3; ++i) vsh[i] = 0.f;
   bool any = false;
-  const float* shp = g.sh + (size_t)(active ? j : 0) * K * 3;
 
+  // Screen-space gradients of invisible records are zero (the compositing
+  // backward zeroes all records first), so every view's record can be read
+  // unconditionally; the next view's is loaded while this one is processed.
+  const float4* vrec = reinterpret_cast<const float4*>(v2d);
+  float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb4 = na;
+  float ncol = 0.f;
+  if (active) {
+    na = vrec[3 * (size_t)j];
+    nb4 = vrec[3 * (size_t)j + 1];
+    ncol = vrec[3 * (size_t)j + 2].x;
+  }
   for (int b = 0; b < batch.B; ++b) {
     float tan[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const size_t rec = (size_t)b * N + j;
-    bool live = active && proj.n_tiles[rec] != 0;
-    float4 va, vb;
-    float vcol_b = 0.f;
-    if (live) {
-      const float4* vp = reinterpret_cast<const float4*>(v2d) + 3 * rec;
-      va = vp[0];
-      vb = vp[1];
-      vcol_b = vp[2].x;
-      live = (va.x != 0.f) || (va.y != 0.f) || (va.z != 0.f) || (va.w != 0.f) ||
-             (vb.x != 0.f) || (vb.y != 0.f) || (vb.z != 0.f) || (vb.w != 0.f) || (vcol_b != 0.f);
+    const float4 va = na, vb = nb4;
+    const float vcol_b = ncol;
+    if (active && b + 1 < batch.B) {
+      const size_t nrec = (size_t)(b + 1) * N + j;
+      na = vrec[3 * nrec];
+      nb4 = vrec[3 * nrec + 1];
+      ncol = vrec[3 * nrec + 2].x;
     }
+    const bool live = active && ((va.x != 0.f) || (va.y != 0.f) || (va.z != 0.f) || (va.w != 0.f) ||
+                                 (vb.x != 0.f) || (vb.y != 0.f) || (vb.z != 0.f) || (vb.w != 0.f) ||
+                                 (vcol_b != 0.f));
     if (live) {
       any = true;
       const SlotCam& c = sc[b];
@@ -268,16 +308,17 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(gs_gaussians g, gs_cam
       for (int ch = 0; ch < 3; ++ch) {
         float raw = 0.5f;
 #pragma unroll
-        for (int k = 0; k < K; ++k) raw += shp[3 * k + ch] * Y[k];
+        for (int k = 0; k < K; ++k) raw += s_sh[3 * k + ch][threadIdx.x] * Y[k];
         if (raw < 0.f) vcol[ch] = 0.f;
       }
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const float s0 = shp[3 * k], s1 = shp[3 * k + 1], s2 = shp[3 * k + 2];
+        const float s0 = s_sh[3 * k][threadIdx.x], s1 = s_sh[3 * k + 1][threadIdx.x],
+                    s2 = s_sh[3 * k + 2][threadIdx.x];
         wk[k] = s0 * vcol[0] + s1 * vcol[1] + s2 * vcol[2];
-        vsh[3 * k] += Y[k] * vcol[0];
-        vsh[3 * k + 1] += Y[k] * vcol[1];
-        vsh[3 * k + 2] += Y[k] * vcol[2];
+        s_vsh[3 * k][threadIdx.x] += Y[k] * vcol[0];
+        s_vsh[3 * k + 1][threadIdx.x] += Y[k] * vcol[1];
+        s_vsh[3 * k + 2][threadIdx.x] += Y[k] * vcol[2];
       }
       float vdir[3] = {0.f, 0.f, 0.f};
       sh_basis_grad_dot(DEG, V.dir[0], V.dir[1], V.dir[2], wk, vdir);
@@ -427,9 +468,18 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(gs_gaussians g, gs_cam
 #pragma unroll
     for (int i = 0; i < 3; ++i) gm[i] += vmu[i];
     dg.opacity_logit[j] += vol * G.o * (1.f - G.o);
-    float* gsh = dg.sh + (size_t)j * K * 3;
-#pragma unroll
-    for (int i = 0; i < K * 3; ++i) gsh[i] += vsh[i];
+  }
+  // SH gradients: through shared memory, then one coalesced read-modify-write
+  // of the block's contiguous slice of dg.sh
+  __syncthreads();
+  {
+    float* dst = dg.sh + (size_t)j0 * K * 3;
+    const int total = n_local * K * 3;
+    for (int f = threadIdx.x; f < total; f += kProjThreads) {
+      const int jl = f / (K * 3);
+      const float gv = s_vsh[f - jl * K * 3][jl];
+      if (gv != 0.f) dst[f] += gv;
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < batch.B * 6; i += blockDim.x)
@@ -441,7 +491,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(gs_gaussians g, gs_cam
 cudaError_t launch_project_fwd(const gs_gaussians& g, const gs_cameras& cams,
                                const gs_batch& batch, const gs_projected& out, int32_t* status,
                                cudaStream_t st) {
-  const int threads = 256;
+  const int threads = kProjThreads;
   const int blocks = (g.n + threads - 1) / threads;
   if (blocks == 0) return cudaSuccess;
   switch (g.sh_degree) {
@@ -453,22 +503,40 @@ cudaError_t launch_project_fwd(const gs_gaussians& g, const gs_cameras& cams,
   return cudaGetLastError();
 }
 
-int project_bwd_blocks(int n) { return (n + 255) / 256; }
+int project_bwd_blocks(int n) { return (n + kProjThreads - 1) / kProjThreads; }
+
+template <int DEG>
+cudaError_t launch_project_bwd_deg(const gs_gaussians& g, const gs_cameras& cams, const gs_batch& batch,
+                                   const gs_projected& proj, const float* v2d, const gs_gaussian_grads& dg,
+                                   double* partial, int blocks, cudaStream_t st) {
+  constexpr size_t smem = project_bwd_smem<DEG>();
+  // the opt-in for more than 48 KB of shared memory, once per device
+  static bool configured[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
+    e = cudaFuncSetAttribute(project_bwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) configured[dev] = true;
+  }
+  project_bwd_kernel<DEG><<<blocks, kProjThreads, smem, st>>>(g, cams, batch, proj, v2d, dg, partial);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_project_bwd(const gs_gaussians& g, const gs_cameras& cams,
                                const gs_batch& batch, const gs_projected& proj, const float* v2d,
                                const gs_gaussian_grads& dg, double* partial,
                                double* g_pose_tangent, cudaStream_t st) {
-  const int threads = 256;
   const int blocks = project_bwd_blocks(g.n);
   if (blocks == 0) return cudaSuccess;
+  cudaError_t e;
   switch (g.sh_degree) {
-    case 0: project_bwd_kernel<0><<<blocks, threads, 0, st>>>(g, cams, batch, proj, v2d, dg, partial); break;
-    case 1: project_bwd_kernel<1><<<blocks, threads, 0, st>>>(g, cams, batch, proj, v2d, dg, partial); break;
-    case 2: project_bwd_kernel<2><<<blocks, threads, 0, st>>>(g, cams, batch, proj, v2d, dg, partial); break;
-    default: project_bwd_kernel<3><<<blocks, threads, 0, st>>>(g, cams, batch, proj, v2d, dg, partial); break;
+    case 0: e = launch_project_bwd_deg<0>(g, cams, batch, proj, v2d, dg, partial, blocks, st); break;
+    case 1: e = launch_project_bwd_deg<1>(g, cams, batch, proj, v2d, dg, partial, blocks, st); break;
+    case 2: e = launch_project_bwd_deg<2>(g, cams, batch, proj, v2d, dg, partial, blocks, st); break;
+    default: e = launch_project_bwd_deg<3>(g, cams, batch, proj, v2d, dg, partial, blocks, st); break;
   }
-  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_pose_partials_finalize(partial, blocks, batch, cams.n_cams, g_pose_tangent, st);
 }

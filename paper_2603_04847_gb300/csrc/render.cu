@@ -8,7 +8,8 @@
 // and the loop overhead are paid once per two pixels, and in the backward
 // one warp reduction covers 64 pixels.
 //
-// Splat records are staged in shared memory 256 at a time.  Staging turns
+// Splat records are staged in shared memory kBatch at a time (64, 128 or 256,
+// chosen by the autotuner through gs_set_tuning).  Staging turns
 // each record into the exponent form alpha_raw = 2^e with
 //   e = A dx^2 + B dx dy + C dy^2 + log2(opacity),
 //   A = -a/(2 ln 2), B = -b/ln 2, C = -c/(2 ln 2)  (conic a, b, c),
@@ -32,7 +33,6 @@ namespace {
 
 constexpr int kTile = 16;
 constexpr int kThreads = 128;  // 2 pixels per thread
-constexpr int kBatch = 256;    // splats staged per round
 constexpr float kLn2 = 0.69314718055994531f;
 constexpr float kHalfLog2e = 0.72134752044448170f;  // 1 / (2 ln 2)
 
@@ -130,10 +130,11 @@ __device__ inline float splat_exponent(const float4 q, float Adx, float dx, floa
   return __fmaf_rn(t, dx, s);
 }
 
+template <int kBatch>
 __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
     gs_batch batch, gs_cameras cams, const float4* __restrict__ splat, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ ranges, const float* __restrict__ bg, float* __restrict__ image,
-    float* __restrict__ T_final, uint32_t* __restrict__ n_contrib) {
+    float* __restrict__ T_final, uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ n_added) {
   __shared__ TileInfo ti;
   __shared__ float2 s_m[kBatch];
   __shared__ float4 s_q[kBatch];
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
   const uint32_t start = ranges[2 * gt], end = ranges[2 * gt + 1];
   float T0 = 1.f, T1 = 1.f;
   float C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
-  uint32_t last0 = 0, last1 = 0;
+  uint32_t last0 = 0, last1 = 0, add0 = 0, add1 = 0;
   bool done0 = !in0, done1 = !in1;
   for (uint32_t base = start; base < end; base += kBatch) {
     if (__syncthreads_count(done0 && done1) == kThreads) break;
@@ -187,6 +188,7 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
           C02 += c.z * w;
           T0 = Tn;
           last0 = pos1;
+          ++add0;
         }
       }
       if (c1) {
@@ -200,6 +202,7 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
           C12 += c.z * w;
           T1 = Tn;
           last1 = pos1;
+          ++add1;
         }
       }
     }
@@ -211,6 +214,7 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
     image[3 * p + 2] = C02 + T0 * bg[2];
     T_final[p] = T0;
     n_contrib[p] = last0;
+    if (n_added) n_added[p] = add0;
   }
   if (in1) {
     const size_t p = (size_t)ti.px_offset + (size_t)v1 * ti.W + u;
@@ -219,6 +223,7 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
     image[3 * p + 2] = C12 + T1 * bg[2];
     T_final[p] = T1;
     n_contrib[p] = last1;
+    if (n_added) n_added[p] = add1;
   }
 }
 
@@ -314,6 +319,7 @@ __device__ inline void load_pixel(PixBwd& P, bool inside, size_t p, const TileIn
   if (P.v0 == 0.f && P.v1 == 0.f && P.v2 == 0.f) P.nc = 0;
 }
 
+template <int kBatch>
 __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
     gs_batch batch, gs_cameras cams, const float4* __restrict__ splat, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ ranges, const float* __restrict__ bg, const float* __restrict__ image,
@@ -438,11 +444,24 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
 
 cudaError_t launch_render_fwd(const gs_batch& batch, const gs_cameras& cams, const gs_projected& proj,
                               const uint32_t* vals, const uint32_t* ranges, const float* bg,
-                              float* image, float* T_final, uint32_t* n_contrib, cudaStream_t st) {
+                              float* image, float* T_final, uint32_t* n_contrib, uint32_t* n_added,
+                              cudaStream_t st) {
   if (batch.n_tiles == 0) return cudaSuccess;
-  render_fwd_kernel<<<batch.n_tiles, kThreads, 0, st>>>(
-      batch, cams, reinterpret_cast<const float4*>(proj.splat), vals, ranges, bg, image, T_final,
-      n_contrib);
+  const float4* sp = reinterpret_cast<const float4*>(proj.splat);
+  switch (tuning().render_batch) {
+    case 64:
+      render_fwd_kernel<64><<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, sp, vals, ranges, bg, image, T_final,
+                                                                n_contrib, n_added);
+      break;
+    case 128:
+      render_fwd_kernel<128><<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, sp, vals, ranges, bg, image,
+                                                                 T_final, n_contrib, n_added);
+      break;
+    default:
+      render_fwd_kernel<256><<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, sp, vals, ranges, bg, image,
+                                                                 T_final, n_contrib, n_added);
+      break;
+  }
   return cudaGetLastError();
 }
 
@@ -452,9 +471,23 @@ cudaError_t launch_render_bwd(const gs_batch& batch, const gs_cameras& cams, con
                               const float* v_image, const float* target, float l1_weight,
                               double* loss, float* v2d, cudaStream_t st) {
   if (batch.n_tiles == 0) return cudaSuccess;
-  render_bwd_kernel<<<batch.n_tiles, kThreads, 0, st>>>(
-      batch, cams, reinterpret_cast<const float4*>(proj.splat), vals, ranges, bg, image, T_final,
-      n_contrib, v_image, target, l1_weight, loss, v2d);
+  const float4* sp = reinterpret_cast<const float4*>(proj.splat);
+  switch (tuning().render_batch) {
+    case 64:
+      render_bwd_kernel<64><<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, sp, vals, ranges, bg, image, T_final,
+                                                                n_contrib, v_image, target, l1_weight, loss, v2d);
+      break;
+    case 128:
+      render_bwd_kernel<128><<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, sp, vals, ranges, bg, image,
+                                                                 T_final, n_contrib, v_image, target, l1_weight,
+                                                                 loss, v2d);
+      break;
+    default:
+      render_bwd_kernel<256><<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, sp, vals, ranges, bg, image,
+                                                                 T_final, n_contrib, v_image, target, l1_weight,
+                                                                 loss, v2d);
+      break;
+  }
   return cudaGetLastError();
 }
 

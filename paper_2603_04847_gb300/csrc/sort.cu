@@ -211,6 +211,15 @@ __global__ void __launch_bounds__(256) duplicate_kernel(gs_projected proj, const
 // Stable LSD radix sort of (uint32 key, uint32 value) pairs, 8-bit digits.
 // The item count is either host-known (n_dev == nullptr) or read on the
 // device, clamped to the buffer capacity.
+//
+// Each block takes a contiguous chunk of the items and each of its warps a
+// contiguous segment of the chunk.  The histogram pass counts digits per
+// warp segment; one scan over (digit, block, warp) gives every warp the
+// output offset of each digit; the scatter pass then lets every warp place
+// its segment on its own, with a warp-private running offset per digit and
+// the rank of each item among equal digits of its 32-item round.  No block
+// barrier is needed while scattering, and the order of equal digits is kept
+// because segments are contiguous and offsets follow (block, warp) order.
 
 constexpr int kRadixThreads = 512;
 constexpr int kRadixWarps = kRadixThreads / 32;
@@ -219,11 +228,14 @@ __device__ inline uint32_t radix_count(const uint32_t* n_dev, uint32_t n_host, s
   return n_dev ? (uint32_t)min((size_t)*n_dev, capacity) : n_host;
 }
 
-__device__ inline void chunk_of(uint32_t n, int nb, int blk, uint32_t& lo, uint32_t& hi) {
+// Items [lo, hi) of warp `warp` in block `blk`.
+__device__ inline void segment_of(uint32_t n, int nb, int blk, int warp, uint32_t& lo, uint32_t& hi) {
   uint32_t chunk = (n + nb - 1) / nb;
   chunk = (chunk + kRadixThreads - 1) / kRadixThreads * kRadixThreads;
-  lo = min((uint32_t)blk * chunk, n);
-  hi = min(lo + chunk, n);
+  const uint32_t seg = chunk / kRadixWarps;  // a multiple of 32
+  const uint32_t b0 = (uint32_t)blk * chunk;
+  lo = min(b0 + (uint32_t)warp * seg, n);
+  hi = min(lo + seg, min(b0 + chunk, n));
 }
 
 __global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const uint32_t* __restrict__ keys,
@@ -234,98 +246,90 @@ __global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const uint32_
   for (int i = threadIdx.x; i < kRadixWarps * 256; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
   const uint32_t n = radix_count(n_dev, n_host, capacity);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t lo, hi;
-  chunk_of(n, gridDim.x, blockIdx.x, lo, hi);
-  const int warp = threadIdx.x >> 5;
-  for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const uint32_t d = (keys[i] >> shift) & 0xffu;
-    atomicAdd(&h[warp][d], 1u);
-  }
+  segment_of(n, gridDim.x, blockIdx.x, warp, lo, hi);
+  for (uint32_t i = lo + lane; i < hi; i += 32) atomicAdd(&h[warp][(keys[i] >> shift) & 0xffu], 1u);
   __syncthreads();
-  for (int d = threadIdx.x; d < 256; d += blockDim.x) {
-    uint32_t s = 0;
-#pragma unroll
-    for (int w = 0; w < kRadixWarps; ++w) s += h[w][d];
-    hist[(size_t)d * gridDim.x + blockIdx.x] = s;
+  // layout [digit][block][warp]
+  const size_t row = (size_t)gridDim.x * kRadixWarps;
+  for (int e = threadIdx.x; e < kRadixWarps * 256; e += blockDim.x) {
+    const int d = e / kRadixWarps, w = e % kRadixWarps;
+    hist[(size_t)d * row + (size_t)blockIdx.x * kRadixWarps + w] = h[w][d];
   }
 }
 
-// Block d: exclusive scan over the NB block counts of digit d, in place;
+// Block d: exclusive scan over the row of digit d ((block, warp) order), in
+// place, in one blocked pass (each thread a run of consecutive entries);
 // digit total to totals[d].
-__global__ void __launch_bounds__(256) radix_scan_kernel(uint32_t* hist, int nb, uint32_t* totals) {
+__global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* hist, int row_len, uint32_t* totals) {
   __shared__ uint32_t sm[32];
-  __shared__ uint32_t carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  uint32_t* row = hist + (size_t)blockIdx.x * nb;
-  for (int base = 0; base < nb; base += blockDim.x) {
-    const int k = base + threadIdx.x;
-    const uint32_t v = k < nb ? row[k] : 0u;
-    uint32_t tot;
-    const uint32_t ex = block_exclusive_scan_u32(v, &tot, sm);
-    if (k < nb) row[k] = carry + ex;
-    __syncthreads();
-    if (threadIdx.x == 0) carry += tot;
-    __syncthreads();
+  uint32_t* row = hist + (size_t)blockIdx.x * row_len;
+  const int per = (row_len + blockDim.x - 1) / blockDim.x;
+  const int lo = min((int)threadIdx.x * per, row_len), hi = min(lo + per, row_len);
+  uint32_t s = 0;
+  for (int k = lo; k < hi; ++k) s += row[k];
+  uint32_t tot;
+  uint32_t run = block_exclusive_scan_u32(s, &tot, sm);
+  for (int k = lo; k < hi; ++k) {
+    const uint32_t v = row[k];
+    row[k] = run;
+    run += v;
   }
-  if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+  if (threadIdx.x == 0) totals[blockIdx.x] = tot;
 }
 
 __global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* n_dev, uint32_t n_host, size_t capacity, int shift,
     const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals) {
-  __shared__ uint32_t run[256];
-  __shared__ uint32_t wcnt[kRadixWarps][256];
+  __shared__ uint32_t dbase[256];
+  __shared__ uint32_t wbase[kRadixWarps][256];
   __shared__ uint32_t sm[32];
-  // digit base = exclusive scan of the digit totals
   {
     const uint32_t t = threadIdx.x < 256 ? totals[threadIdx.x] : 0u;
     const uint32_t ex = block_exclusive_scan_u32(t, nullptr, sm);
-    if (threadIdx.x < 256) run[threadIdx.x] = ex + hist[(size_t)threadIdx.x * gridDim.x + blockIdx.x];
+    if (threadIdx.x < 256) dbase[threadIdx.x] = ex;
   }
-  for (int i = threadIdx.x; i < kRadixWarps * 256; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+  __syncthreads();
+  const size_t row = (size_t)gridDim.x * kRadixWarps;
+  for (int e = threadIdx.x; e < kRadixWarps * 256; e += blockDim.x) {
+    const int d = e / kRadixWarps, w = e % kRadixWarps;
+    wbase[w][d] = dbase[d] + hist[(size_t)d * row + (size_t)blockIdx.x * kRadixWarps + w];
+  }
   __syncthreads();
   const uint32_t n = radix_count(n_dev, n_host, capacity);
-  uint32_t lo, hi;
-  chunk_of(n, gridDim.x, blockIdx.x, lo, hi);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  // the next round's items are loaded while this round is ranked
-  uint32_t i = lo + threadIdx.x;
+  uint32_t lo, hi;
+  segment_of(n, gridDim.x, blockIdx.x, warp, lo, hi);
+  uint32_t* my = wbase[warp];
+  uint32_t i = lo + lane;
   uint32_t k = 0, v = 0;
   if (i < hi) {
     k = kin[i];
     v = vin[i];
   }
-  for (uint32_t base = lo; base < hi; base += kRadixThreads) {
+  for (uint32_t base = lo; base < hi; base += 32) {
     const bool valid = i < hi;
-    const uint32_t inext = i + kRadixThreads;
+    const uint32_t inext = i + 32;
     uint32_t kn = 0, vn = 0;
-    if (inext < hi) {
+    if (inext < hi) {  // next round's items load while this one is placed
       kn = kin[inext];
       vn = vin[inext];
     }
     const uint32_t d = valid ? (k >> shift) & 0xffu : 256u + (uint32_t)lane;  // unique sentinel
-    __syncwarp();
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const uint32_t rank = __popc(peers & lt_mask);
-    const bool leader = (peers & lt_mask) == 0;
-    if (valid && leader) wcnt[warp][d] = __popc(peers);
-    __syncthreads();
+    uint32_t pos = 0;
+    if (valid) pos = my[d] + rank;
+    __syncwarp();
     if (valid) {
-      uint32_t pre = 0;
-      for (int w = 0; w < warp; ++w) pre += wcnt[w][d];
-      const uint32_t pos = run[d] + pre + rank;
       kout[pos] = k;
       vout[pos] = v;
+      if ((peers & lt_mask) == 0) my[d] += __popc(peers);
     }
-    __syncthreads();
-    if (valid && leader) {
-      atomicAdd(&run[d], (uint32_t)__popc(peers));
-      wcnt[warp][d] = 0;
-    }
-    __syncthreads();
+    __syncwarp();
     i = inext;
     k = kn;
     v = vn;
@@ -380,13 +384,13 @@ SortWs sort_ws_layout(void* base, size_t M, size_t capacity, int nb) {
   w.tile_sums = (unsigned long long*)take(((M + kScanTile - 1) / kScanTile) * 8 + 8);
   w.tiles_alt = (uint32_t*)take(capacity * 4);
   w.vals_alt = (uint32_t*)take(capacity * 4);
-  w.hist = (uint32_t*)take((size_t)256 * nb * 4);
+  w.hist = (uint32_t*)take((size_t)256 * nb * kRadixWarps * 4);
   w.totals = (uint32_t*)take(256 * 4);
   w.bytes = o;
   return w;
 }
 
-int radix_blocks() { return 2 * device_sm_count(); }
+int radix_blocks() { return tuning().sort_blocks_per_sm * device_sm_count(); }
 
 // Stable LSD passes over bits [0, bits) of (kA, vA); kA/vA point at the
 // sorted result afterwards.
@@ -394,7 +398,7 @@ void radix_sort_u32(uint32_t*& kA, uint32_t*& vA, uint32_t*& kB, uint32_t*& vB, 
                     uint32_t n_host, size_t capacity, int bits, SortWs& w, int nb, cudaStream_t st) {
   for (int shift = 0; shift < bits; shift += 8) {
     radix_hist_kernel<<<nb, kRadixThreads, 0, st>>>(kA, n_dev, n_host, capacity, shift, w.hist);
-    radix_scan_kernel<<<256, 256, 0, st>>>(w.hist, nb, w.totals);
+    radix_scan_kernel<<<256, 1024, 0, st>>>(w.hist, nb * kRadixWarps, w.totals);
     radix_scatter_kernel<<<nb, kRadixThreads, 0, st>>>(kA, vA, kB, vB, n_dev, n_host, capacity, shift, w.hist,
                                                        w.totals);
     std::swap(kA, kB);

@@ -11,7 +11,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from .core import (Batch, Cameras, Gaussians, Projected, TileLists, adam_c, gs_adam_update, gs_project,
+from .core import (Batch, Cameras, Gaussians, Projected, TileLists, adam_c, gs_adam_update, gs_adam_update_groups,
+                   gs_project,
                    gs_project_bwd, gs_raster_bwd, gs_render_fwd, gs_sort_tiles, gs_step_advance, gs_zero,
                    new_status, pose_se3_update, render_bwd_workspace_bytes, track_reproj_fwd_bwd,
                    track_workspace_bytes)
@@ -60,6 +61,16 @@ class Renderer:
         mark("raster_bwd")
         gs_project_bwd(g, self.cams, self.batch, self.proj, dg, g_tangent, self.ws_bwd, Rt)
         mark("project_bwd")
+
+    def count_added(self, g: Gaussians, Rt: torch.Tensor = None) -> int:
+        """Re-runs the forward with the per-pixel added-splat counter and
+        returns the total number of splats composited (a diagnostic)."""
+        n_added = torch.zeros_like(self.n_contrib)
+        gs_project(g, self.cams, self.batch, self.proj, self.status, Rt)
+        gs_sort_tiles(self.n, self.cams, self.batch, self.proj, self.tl, self.status, Rt)
+        gs_render_fwd(self.batch, self.cams, self.proj, self.tl, self.bg, self.image, self.T_final,
+                      self.n_contrib, Rt, n_added=n_added)
+        return int(n_added.to(torch.int64).sum().item())
 
     def n_instances(self) -> int:
         return int(self.tl.n_instances.item()) & 0xffffffff
@@ -210,13 +221,14 @@ class JointStep:
         mark("track")
         gs_step_advance(self.step_no)
         ext = h.scene_extent
-        self._adam(self.g.mean, self.dg.mean, self.m.mean, self.v.mean, h.lr_mean * ext)
-        self._adam(self.g.log_scale, self.dg.log_scale, self.m.log_scale, self.v.log_scale, h.lr_log_scale)
-        self._adam(self.g.quat, self.dg.quat, self.m.quat, self.v.quat, h.lr_quat)
-        self._adam(self.g.opacity_logit, self.dg.opacity_logit, self.m.opacity_logit, self.v.opacity_logit,
-                   h.lr_opacity)
-        self._adam(self.g.sh, self.dg.sh, self.m.sh, self.v.sh, h.lr_sh)
-        self._adam(self.X, self.gX, self.mX, self.vX, h.lr_track * ext)
+        gs_adam_update_groups([
+            (self.g.mean, self.dg.mean, self.m.mean, self.v.mean, h.lr_mean * ext),
+            (self.g.log_scale, self.dg.log_scale, self.m.log_scale, self.v.log_scale, h.lr_log_scale),
+            (self.g.quat, self.dg.quat, self.m.quat, self.v.quat, h.lr_quat),
+            (self.g.opacity_logit, self.dg.opacity_logit, self.m.opacity_logit, self.v.opacity_logit,
+             h.lr_opacity),
+            (self.g.sh, self.dg.sh, self.m.sh, self.v.sh, h.lr_sh),
+            (self.X, self.gX, self.mX, self.vX, h.lr_track * ext)], h.beta1, h.beta2, h.eps, self.step_no)
         mark("adam")
         hp = adam_c(h.lr_pose, h.beta1, h.beta2, h.eps, self.step_no)
         pose_se3_update(self.T0, self.xi, self.g_tan, self.g_xi, self.m_xi, self.v_xi, hp, self.Rt)
@@ -231,8 +243,8 @@ class JointStep:
             # duplicate 1, tile sort 3 per pass, ranges 1; render fwd 1;
             # raster bwd 1; project bwd + finalize 2
             per_render += 1 + (1 + 12 + 3 + 1 + 3 * ((tbits + 7) // 8) + 1) + 1 + 1 + 2
-        # track + finalize 2, step advance 1, Adam 6, pose 1
-        return per_render + 2 + 1 + 6 + 1
+        # track + finalize 2, step advance 1, Adam (all groups) 1, pose 1
+        return per_render + 2 + 1 + 1 + 1
 
     # -- CUDA graph ----------------------------------------------------------
     def capture(self, warmup: int = 1):

@@ -164,3 +164,50 @@ def test_graph_replay_matches_eager_and_plain():
         np.testing.assert_allclose(z, x, rtol=1e-4, atol=1e-6)
     assert eager.status_flags() == 0
     assert int(eager.step_no.item()) == 3 and int(graphed.step_no.item()) == 3
+
+
+def test_every_tuning_candidate_gives_the_same_image_and_lists():
+    """The autotuner's candidates change only how work is split: images,
+    per-pixel state and sorted lists are bit-identical under all of them."""
+    from paper_2603_04847_gb300.autotune import CANDIDATES
+    from paper_2603_04847_gb300.core import gs_get_tuning, gs_set_tuning
+    w = synth.make_workload("batched", n_gaussians=6000, n_views=3, width=(150, 260), height=(100, 190), n_tracks=10)
+    saved = gs_get_tuning()
+    ref = None
+    try:
+        for rb, sb in CANDIDATES:
+            gs_set_tuning(rb, sb)
+            r, *_ = gpu_forward(w["scene"], w["wh"], w["K"], w["Rt"], [0, 1, 2])
+            n = r.n_instances()
+            out = [r.image.cpu().numpy(), r.T_final.cpu().numpy(), r.n_contrib.cpu().numpy(),
+                   r.tl.vals.cpu().numpy()[:n], r.tl.ranges.cpu().numpy()]
+            if ref is None:
+                ref = out
+            else:
+                for a, b in zip(out, ref):
+                    np.testing.assert_array_equal(a, b)
+    finally:
+        gs_set_tuning(saved["render_batch"], saved["sort_blocks_per_sm"])
+
+
+def test_adam_groups_match_oracle():
+    from paper_2603_04847_gb300.core import gs_adam_update_groups
+    rng = np.random.default_rng(6)
+    sizes = [1, 7, 4096, 4097, 20003, 3]
+    lrs = [1e-3, 5e-3, 2e-2, 1e-4, 3e-3, 1.0]
+    host = [[f32(rng.normal(size=n)) for _ in range(4)] for n in sizes]
+    for h in host:
+        h[3] = np.abs(h[3])
+    dev = [[torch.tensor(a, dtype=torch.float32, device="cuda") for a in h] for h in host]
+    # an unaligned view exercises the scalar path
+    base = torch.zeros(20004 + 1, dtype=torch.float32, device="cuda")
+    dev[4][0] = base[1:20004]
+    dev[4][0].copy_(torch.tensor(host[4][0], device="cuda"))
+    step = torch.tensor([4], dtype=torch.int32, device="cuda")
+    gs_adam_update_groups([(d[0], d[1], d[2], d[3], lr) for d, lr in zip(dev, lrs)], 0.9, 0.999, 1e-15, step)
+    torch.cuda.synchronize()
+    for h, d, lr in zip(host, dev, lrs):
+        p, g, m, v = (a.copy() for a in h)
+        oracle.adam(p, g, m, v, lr, 0.9, 0.999, 1e-15, 4)
+        np.testing.assert_allclose(d[0].cpu().numpy(), p, rtol=1e-5, atol=3e-7 * max(1.0, lr * 1e3))
+        np.testing.assert_allclose(d[2].cpu().numpy(), m, rtol=1e-5, atol=3e-7)
