@@ -253,17 +253,30 @@ def make_step(inp, views, mode, lambda_ba):
     return js
 
 
-def time_graph(js, steps, flush, use_graph=True):
+def time_graph(js, steps, flush, use_graph=True, batches=None):
+    """Per-step device times (ms).  With `batches` (pinned [steps, B] int32
+    view ids), each timed step first copies its view ids to the device."""
     import torch
     st = torch.cuda.current_stream()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for i in range(steps):
         flush.zero_()
         evs[i][0].record(st)
+        if batches is not None:
+            set_views_async(js, batches[i])
         js.run() if use_graph else js.step()
         evs[i][1].record(st)
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in evs]
+
+
+def set_views_async(js, views_pinned):
+    """Device copy of a batch's view ids (same per-slot sizes), no host sync."""
+    js.batch.views.copy_(views_pinned, non_blocking=True)
+    if js.mode != "batched":
+        for b, sb in enumerate(js.slot_batches):
+            sb.views.copy_(views_pinned[b:b + 1], non_blocking=True)
+    js.views = views_pinned.numpy().astype(np.int64)
 
 
 def stage_times(js, reps, flush):
@@ -335,6 +348,15 @@ def run_ours(args):
     W = w["workload"]
     views = list(range(min(W.batch, W.n_views)))
     js = make_step(inp, views, args.mode, W.lambda_ba)
+    # random batches (Algorithm 1, "Sample image indices") when the workload
+    # has more views than one batch; all of them share the batch's layout
+    n_batches = args.warmup + args.steps + max(3, args.steps // 2) + 8
+    rng = np.random.default_rng(1234)
+    batch_list = None
+    if W.n_views > W.batch:
+        import synth
+        batch_list = torch.tensor(np.stack(synth.batches(rng, W.n_views, W.batch, n_batches)).astype(np.int32)
+                                  ).pin_memory()
     if args.profile_steps:
         for _ in range(args.profile_steps):
             js.step()
@@ -347,8 +369,17 @@ def run_ours(args):
     use_graph = not args.no_graph
     if use_graph:
         js.capture(warmup=1)
+    bcur = 0
     for _ in range(args.warmup):
         flush.zero_()
+        if batch_list is not None:
+            # every batch has its own instance count: grow the buffers to the
+            # largest seen (with headroom) before timing
+            set_views_async(js, batch_list[bcur])
+            bcur += 1
+            js.ensure_capacity()
+            if use_graph and js.graph is None:
+                js.capture(warmup=0)
         js.run() if use_graph else js.step()
     torch.cuda.synchronize()
     flags = js.status_flags()
@@ -362,7 +393,10 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.mark_on()
-    times = time_graph(js, args.steps, flush, use_graph)
+    times = time_graph(js, args.steps, flush, use_graph,
+                       None if batch_list is None else batch_list[bcur:bcur + args.steps])
+    if batch_list is not None:
+        bcur += args.steps
     torch.cuda.synchronize()
     clocks.mark_off()
     tot = torch.tensor([sum(times)], dtype=torch.float64, device=dev)
@@ -370,6 +404,8 @@ def run_ours(args):
         dist.barrier()
         dist.all_reduce(tot, op=dist.ReduceOp.MAX)
     clk = clocks.stop()
+    if js.status_flags():
+        raise RuntimeError("device status flags %d during the timed steps" % js.status_flags())
     ms = tot.item() / args.steps
     P = js.batch.n_pixels
     value = ws * P / 1e6 / (ms / 1e3)
@@ -428,28 +464,41 @@ def run_ours(args):
         for _ in range(2):
             flush.zero_()
             jp.step()
-        pt = time_graph(jp, max(3, min(args.steps, 10)), flush, use_graph=False)
+        npl = max(3, min(args.steps, 10))
+        pt = time_graph(jp, npl, flush, False, None if batch_list is None else batch_list[:npl])
         pms = sum(pt) / len(pt)
         plain = dict(ms_per_step=pms, value=P / 1e6 / (pms / 1e3), launches_per_step=jp.kernels_per_step())
         del jp
 
-    # end to end through the public API: targets H2D from pinned memory every
-    # step, graph replay, loss D2H
-    host_tgt = js.target_batch.cpu().pin_memory()
+    # end to end through the public API: every step copies its views' target
+    # images from pinned host memory into the device dataset buffer (one copy
+    # per view), then runs the step (which gathers them), then reads the loss
+    host_tgt = inp["targets"].cpu().pin_memory()
+    off = inp["off"]
     loss_host = torch.zeros(2, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     e2e_t = []
-    for _ in range(max(3, args.steps // 2)):
+    h2d = 0
+    for i in range(max(3, args.steps // 2)):
+        if batch_list is not None:
+            vi = batch_list[bcur % len(batch_list)]
+            bcur += 1
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        js.target_batch.copy_(host_tgt, non_blocking=True)
+        if batch_list is not None:
+            set_views_async(js, vi)
+        h2d = 0
+        for v in js.views:
+            a, e = int(off[v]), int(off[v + 1])
+            inp["targets"][a:e].copy_(host_tgt[a:e], non_blocking=True)
+            h2d += (e - a) * 12
         js.run() if use_graph else js.step()
         loss_host.copy_(js.loss, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = statistics.median(e2e_t)
-    e2e = dict(value=ws * P / 1e6 / e2e_s, unit=UNIT, h2d_bytes_per_step=int(host_tgt.numel() * 4),
+    e2e = dict(value=ws * P / 1e6 / e2e_s, unit=UNIT, h2d_bytes_per_step=int(h2d + (32 if batch_list is not None else 0)),
                d2h_bytes_per_step=16, ms_per_step=e2e_s * 1e3)
 
     cpu = None

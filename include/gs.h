@@ -365,6 +365,17 @@ gs_status gs_adam_update_groups(const gs_adam_group* groups, int32_t n_groups,
 /* gs_step_advance — *step += 1 on the device. */
 gs_status gs_step_advance(int32_t* step, gs_stream stream);
 
+/* gs_gather_view_pixels — for every slot b of the batch, copies the
+ * per-pixel data of camera views[b] from a dataset buffer holding all
+ * cameras (camera v's pixels start at element src_px_offset[v], [V+1]) into
+ * slot b's place in a batch-packed buffer (px_offset[b]); `channels` floats
+ * per pixel.  Used to fetch a batch's target images (Algorithm 1, "Sample
+ * image indices") without the host reading the view ids, so a captured step
+ * stays valid when only the device copy of views changes. */
+gs_status gs_gather_view_pixels(const float* src, const int64_t* src_px_offset,
+                                const gs_cameras* cams, const gs_batch* batch,
+                                int32_t channels, float* dst, gs_stream stream);
+
 /* gs_zero — set `bytes` bytes at ptr to zero on the stream. */
 gs_status gs_zero(void* ptr, size_t bytes, gs_stream stream);
 

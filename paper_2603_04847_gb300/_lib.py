@@ -98,6 +98,7 @@ PROTOTYPES = {
     "gs_adam_update": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     "gs_step_advance": (ctypes.c_int, [c_void_p, c_void_p]),
     "gs_zero": (ctypes.c_int, [c_void_p, c_size_t, c_void_p]),
+    "gs_gather_view_pixels": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
 }
 
 _lib = None

@@ -133,6 +133,20 @@ class Batch:
         self.px_offset = torch.as_tensor(px, device=device)
         self.tile_offset = torch.as_tensor(to.astype(np.int32), device=device)
 
+    def same_layout(self, cams: "Cameras", views) -> bool:
+        """True when `views` has the per-slot sizes of the current batch."""
+        wh = cams.wh_host[np.asarray(views, dtype=np.int64).reshape(-1)]
+        return len(wh) == self.B and np.array_equal(wh[:, 0], self.W) and np.array_equal(wh[:, 1], self.H)
+
+    def set_views(self, cams: "Cameras", views):
+        """Replaces the batch's views by views of the same sizes, in place on
+        the device (buffers, kernels and captured graphs stay valid)."""
+        if not self.same_layout(cams, views):
+            raise ValueError("set_views needs views with the same per-slot sizes")
+        views = np.asarray(views, dtype=np.int64).reshape(-1)
+        self.views_host = views
+        self.views.copy_(torch.as_tensor(views.astype(np.int32)), non_blocking=False)
+
     def c(self):
         return _lib.gs_batch(self.B, self.tile, self.views.data_ptr(), self.px_offset.data_ptr(),
                              self.tile_offset.data_ptr(), self.n_pixels, self.n_tiles, 0)
@@ -334,6 +348,16 @@ def gs_step_advance(step, stream=None):
     lib = _lib.load()
     _need_cuda(step)
     check(lib.gs_step_advance(_p(step), _stream(stream)), "gs_step_advance")
+
+
+def gs_gather_view_pixels(src: torch.Tensor, src_px_offset: torch.Tensor, cams: Cameras, batch: Batch,
+                          dst: torch.Tensor, stream=None):
+    lib = _lib.load()
+    _need_cuda(src, src_px_offset, dst)
+    cc, bc = cams.c(), batch.c()
+    ch = src.shape[1] if src.dim() > 1 else 1
+    check(lib.gs_gather_view_pixels(_p(src), _p(src_px_offset), ctypes.byref(cc), ctypes.byref(bc), int(ch), _p(dst),
+                                    _stream(stream)), "gs_gather_view_pixels")
 
 
 def gs_zero(t: torch.Tensor, stream=None):

@@ -348,6 +348,17 @@ gs_status gs_step_advance(int32_t* step, gs_stream stream) {
   return GS_OK;
 }
 
+gs_status gs_gather_view_pixels(const float* src, const int64_t* src_px_offset, const gs_cameras* cams,
+                                const gs_batch* batch, int32_t channels, float* dst, gs_stream stream) {
+  gs_status s;
+  if ((s = check_cameras(cams)) || (s = check_batch(batch))) return s;
+  if (!src || !src_px_offset || !dst || channels < 1)
+    return fail(GS_ERR_ARG, "gs_gather_view_pixels: bad argument");
+  cudaError_t e = launch_gather_view_pixels(src, src_px_offset, *cams, *batch, channels, dst, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_gather_view_pixels");
+  return GS_OK;
+}
+
 gs_status gs_zero(void* ptr, size_t bytes, gs_stream stream) {
   if (bytes == 0) return GS_OK;
   if (!ptr) return fail(GS_ERR_ARG, "gs_zero: null");

@@ -57,6 +57,8 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n,
                         cudaStream_t st);
 cudaError_t launch_adam_groups(const gs_adam_group* groups, int n_groups, const gs_adam& hp, cudaStream_t st);
 cudaError_t launch_step_advance(int32_t* step, cudaStream_t st);
+cudaError_t launch_gather_view_pixels(const float* src, const int64_t* src_px_offset, const gs_cameras& cams,
+                                      const gs_batch& batch, int channels, float* dst, cudaStream_t st);
 
 // Error reporting and argument checks shared with entry points outside
 // gs_capi.cu.

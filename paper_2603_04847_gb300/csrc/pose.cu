@@ -229,6 +229,23 @@ __global__ void __launch_bounds__(256) adam_groups_kernel(AdamGroups G, float be
 
 __global__ void step_advance_kernel(int32_t* step) { *step += 1; }
 
+// blockIdx.y = slot; the slot's pixels are copied with a grid-stride loop
+// over its floats.
+__global__ void __launch_bounds__(256) gather_view_pixels_kernel(const float* __restrict__ src,
+                                                                 const int64_t* __restrict__ src_px_offset,
+                                                                 gs_cameras cams, gs_batch batch, int channels,
+                                                                 float* __restrict__ dst) {
+  const int b = blockIdx.y;
+  const int v = slot_view(cams, batch, b);
+  const int64_t n_dst = (batch.px_offset[b + 1] - batch.px_offset[b]) * channels;
+  const int64_t n_src = (src_px_offset[v + 1] - src_px_offset[v]) * channels;
+  const int64_t n = n_dst < n_src ? n_dst : n_src;
+  const float* s = src + src_px_offset[v] * channels;
+  float* d = dst + batch.px_offset[b] * channels;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = s[i];
+}
+
 __global__ void pose_partial_finalize_kernel(const double* __restrict__ partial, int n_blocks,
                                              gs_batch batch, int n_cams, double* g_pose_tangent) {
   const int b = blockIdx.x / 6, i = blockIdx.x % 6;
@@ -290,6 +307,14 @@ cudaError_t launch_adam_groups(const gs_adam_group* groups, int n_groups, const 
   if (n_chunks == 0) return cudaSuccess;
   const int blocks = std::min(n_chunks, device_sm_count() * 8);
   adam_groups_kernel<<<blocks, 256, 0, st>>>(G, hp.beta1, hp.beta2, hp.eps, hp.step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_view_pixels(const float* src, const int64_t* src_px_offset, const gs_cameras& cams,
+                                      const gs_batch& batch, int channels, float* dst, cudaStream_t st) {
+  if (batch.n_pixels == 0) return cudaSuccess;
+  const int gx = std::max(1, std::min(4 * device_sm_count() / std::max(batch.B, 1) + 1, 1024));
+  gather_view_pixels_kernel<<<dim3(gx, batch.B), 256, 0, st>>>(src, src_px_offset, cams, batch, channels, dst);
   return cudaGetLastError();
 }
 

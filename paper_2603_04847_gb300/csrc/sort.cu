@@ -212,56 +212,56 @@ __global__ void __launch_bounds__(256) duplicate_kernel(gs_projected proj, const
 // The item count is either host-known (n_dev == nullptr) or read on the
 // device, clamped to the buffer capacity.
 //
-// Each block takes a contiguous chunk of the items and each of its warps a
-// contiguous segment of the chunk.  The histogram pass counts digits per
-// warp segment; one scan over (digit, block, warp) gives every warp the
-// output offset of each digit; the scatter pass then lets every warp place
-// its segment on its own, with a warp-private running offset per digit and
-// the rank of each item among equal digits of its 32-item round.  No block
-// barrier is needed while scattering, and the order of equal digits is kept
-// because segments are contiguous and offsets follow (block, warp) order.
+// Each block owns a contiguous chunk of the items (a multiple of the 4096-item
+// tile).  Pass = histogram per block, scan per digit over blocks, scatter.
+// The scatter works tile by tile: every warp ranks its own 256 contiguous
+// items (8 rounds of 32) against a warp-private running count per digit;
+// one block step turns the per-warp counts into offsets within the tile;
+// items are staged digit-sorted in shared memory and then written out in
+// that order, so consecutive threads write consecutive addresses of a
+// digit's run (full sectors, not one scattered word per item).  Equal
+// digits keep their input order: tiles, warps, rounds and lanes are all
+// taken in input order.
 
-constexpr int kRadixThreads = 512;
-constexpr int kRadixWarps = kRadixThreads / 32;
+constexpr int kSortThreads = 512;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kWarpItems = 256;                       // 8 rounds of 32 per warp
+constexpr int kTileItems = kSortWarps * kWarpItems;   // 4096
 
 __device__ inline uint32_t radix_count(const uint32_t* n_dev, uint32_t n_host, size_t capacity) {
   return n_dev ? (uint32_t)min((size_t)*n_dev, capacity) : n_host;
 }
 
-// Items [lo, hi) of warp `warp` in block `blk`.
-__device__ inline void segment_of(uint32_t n, int nb, int blk, int warp, uint32_t& lo, uint32_t& hi) {
+__device__ inline void chunk_of(uint32_t n, int nb, int blk, uint32_t& lo, uint32_t& hi) {
   uint32_t chunk = (n + nb - 1) / nb;
-  chunk = (chunk + kRadixThreads - 1) / kRadixThreads * kRadixThreads;
-  const uint32_t seg = chunk / kRadixWarps;  // a multiple of 32
-  const uint32_t b0 = (uint32_t)blk * chunk;
-  lo = min(b0 + (uint32_t)warp * seg, n);
-  hi = min(lo + seg, min(b0 + chunk, n));
+  chunk = (chunk + kTileItems - 1) / kTileItems * kTileItems;
+  lo = min((uint32_t)blk * chunk, n);
+  hi = min(lo + chunk, n);
 }
 
-__global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const uint32_t* __restrict__ keys,
-                                                                   const uint32_t* n_dev, uint32_t n_host,
-                                                                   size_t capacity, int shift,
-                                                                   uint32_t* __restrict__ hist) {
-  __shared__ uint32_t h[kRadixWarps][256];
-  for (int i = threadIdx.x; i < kRadixWarps * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t* __restrict__ keys,
+                                                                  const uint32_t* n_dev, uint32_t n_host,
+                                                                  size_t capacity, int shift,
+                                                                  uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[kSortWarps][256];
+  for (int i = threadIdx.x; i < kSortWarps * 256; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
   const uint32_t n = radix_count(n_dev, n_host, capacity);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t lo, hi;
-  segment_of(n, gridDim.x, blockIdx.x, warp, lo, hi);
-  for (uint32_t i = lo + lane; i < hi; i += 32) atomicAdd(&h[warp][(keys[i] >> shift) & 0xffu], 1u);
+  chunk_of(n, gridDim.x, blockIdx.x, lo, hi);
+  const int warp = threadIdx.x >> 5;
+  for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&h[warp][(keys[i] >> shift) & 0xffu], 1u);
   __syncthreads();
-  // layout [digit][block][warp]
-  const size_t row = (size_t)gridDim.x * kRadixWarps;
-  for (int e = threadIdx.x; e < kRadixWarps * 256; e += blockDim.x) {
-    const int d = e / kRadixWarps, w = e % kRadixWarps;
-    hist[(size_t)d * row + (size_t)blockIdx.x * kRadixWarps + w] = h[w][d];
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) t += h[w][d];
+    hist[(size_t)d * gridDim.x + blockIdx.x] = t;
   }
 }
 
-// Block d: exclusive scan over the row of digit d ((block, warp) order), in
-// place, in one blocked pass (each thread a run of consecutive entries);
-// digit total to totals[d].
+// Block d: exclusive scan over the row of digit d (block order), in place,
+// in one blocked pass; digit total to totals[d].
 __global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* hist, int row_len, uint32_t* totals) {
   __shared__ uint32_t sm[32];
   uint32_t* row = hist + (size_t)blockIdx.x * row_len;
@@ -279,60 +279,93 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* hist, int ro
   if (threadIdx.x == 0) totals[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* n_dev, uint32_t n_host, size_t capacity, int shift,
     const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals) {
-  __shared__ uint32_t dbase[256];
-  __shared__ uint32_t wbase[kRadixWarps][256];
+  __shared__ uint32_t s_base[256];     // global start of this block's next items of each digit
+  __shared__ uint32_t s_tot[256];      // items of each digit in the current tile
+  __shared__ uint32_t s_dstart[256];   // exclusive scan of s_tot
+  __shared__ uint16_t s_wrun[kSortWarps][256];
+  __shared__ uint32_t s_keys[kTileItems];
+  __shared__ uint32_t s_vals[kTileItems];
   __shared__ uint32_t sm[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   {
-    const uint32_t t = threadIdx.x < 256 ? totals[threadIdx.x] : 0u;
+    const uint32_t t = tid < 256 ? totals[tid] : 0u;
     const uint32_t ex = block_exclusive_scan_u32(t, nullptr, sm);
-    if (threadIdx.x < 256) dbase[threadIdx.x] = ex;
+    if (tid < 256) s_base[tid] = ex + hist[(size_t)tid * gridDim.x + blockIdx.x];
   }
-  __syncthreads();
-  const size_t row = (size_t)gridDim.x * kRadixWarps;
-  for (int e = threadIdx.x; e < kRadixWarps * 256; e += blockDim.x) {
-    const int d = e / kRadixWarps, w = e % kRadixWarps;
-    wbase[w][d] = dbase[d] + hist[(size_t)d * row + (size_t)blockIdx.x * kRadixWarps + w];
-  }
-  __syncthreads();
   const uint32_t n = radix_count(n_dev, n_host, capacity);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned lt_mask = (1u << lane) - 1u;
   uint32_t lo, hi;
-  segment_of(n, gridDim.x, blockIdx.x, warp, lo, hi);
-  uint32_t* my = wbase[warp];
-  uint32_t i = lo + lane;
-  uint32_t k = 0, v = 0;
-  if (i < hi) {
-    k = kin[i];
-    v = vin[i];
-  }
-  for (uint32_t base = lo; base < hi; base += 32) {
-    const bool valid = i < hi;
-    const uint32_t inext = i + 32;
-    uint32_t kn = 0, vn = 0;
-    if (inext < hi) {  // next round's items load while this one is placed
-      kn = kin[inext];
-      vn = vin[inext];
-    }
-    const uint32_t d = valid ? (k >> shift) & 0xffu : 256u + (uint32_t)lane;  // unique sentinel
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t rank = __popc(peers & lt_mask);
-    uint32_t pos = 0;
-    if (valid) pos = my[d] + rank;
+  chunk_of(n, gridDim.x, blockIdx.x, lo, hi);
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (uint32_t tile = lo; tile < hi; tile += kTileItems) {
+    const uint32_t tile_n = min((uint32_t)kTileItems, hi - tile);
+    for (int d = lane; d < 256; d += 32) s_wrun[warp][d] = 0;
     __syncwarp();
-    if (valid) {
-      kout[pos] = k;
-      vout[pos] = v;
-      if ((peers & lt_mask) == 0) my[d] += __popc(peers);
+    // 1. warp-local stable ranking of the warp's 8 rounds of 32 items
+    uint32_t k[8], v[8], r[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const uint32_t li = (uint32_t)(warp * kWarpItems + s * 32 + lane);
+      const bool valid = li < tile_n;
+      k[s] = valid ? kin[tile + li] : 0u;
+      v[s] = valid ? vin[tile + li] : 0u;
     }
-    __syncwarp();
-    i = inext;
-    k = kn;
-    v = vn;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const uint32_t li = (uint32_t)(warp * kWarpItems + s * 32 + lane);
+      const bool valid = li < tile_n;
+      const uint32_t d = valid ? (k[s] >> shift) & 0xffu : 256u + (uint32_t)lane;  // unique sentinel
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      r[s] = valid ? (uint32_t)s_wrun[warp][d] + __popc(peers & lt_mask) : 0u;
+      __syncwarp();
+      if (valid && (peers & lt_mask) == 0) s_wrun[warp][d] += (uint16_t)__popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    // 2. per digit: offsets of the warps within the tile, tile totals
+    if (tid < 256) {
+      uint32_t acc = 0;
+#pragma unroll
+      for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t c = s_wrun[w][tid];
+        s_wrun[w][tid] = (uint16_t)acc;
+        acc += c;
+      }
+      s_tot[tid] = acc;
+    }
+    __syncthreads();
+    {
+      const uint32_t t = tid < 256 ? s_tot[tid] : 0u;
+      const uint32_t ex = block_exclusive_scan_u32(t, nullptr, sm);
+      if (tid < 256) s_dstart[tid] = ex;
+    }
+    __syncthreads();
+    // 3. stage digit-sorted in shared memory
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const uint32_t li = (uint32_t)(warp * kWarpItems + s * 32 + lane);
+      if (li < tile_n) {
+        const uint32_t d = (k[s] >> shift) & 0xffu;
+        const uint32_t p = s_dstart[d] + s_wrun[warp][d] + r[s];
+        s_keys[p] = k[s];
+        s_vals[p] = v[s];
+      }
+    }
+    __syncthreads();
+    // 4. write runs: consecutive threads, consecutive positions of a digit
+    for (uint32_t p = tid; p < tile_n; p += kSortThreads) {
+      const uint32_t key = s_keys[p];
+      const uint32_t d = (key >> shift) & 0xffu;
+      const uint32_t pos = s_base[d] + (p - s_dstart[d]);
+      kout[pos] = key;
+      vout[pos] = s_vals[p];
+    }
+    __syncthreads();
+    if (tid < 256) s_base[tid] += s_tot[tid];
+    __syncthreads();
   }
 }
 
@@ -384,7 +417,7 @@ SortWs sort_ws_layout(void* base, size_t M, size_t capacity, int nb) {
   w.tile_sums = (unsigned long long*)take(((M + kScanTile - 1) / kScanTile) * 8 + 8);
   w.tiles_alt = (uint32_t*)take(capacity * 4);
   w.vals_alt = (uint32_t*)take(capacity * 4);
-  w.hist = (uint32_t*)take((size_t)256 * nb * kRadixWarps * 4);
+  w.hist = (uint32_t*)take((size_t)256 * nb * 4);
   w.totals = (uint32_t*)take(256 * 4);
   w.bytes = o;
   return w;
@@ -397,9 +430,9 @@ int radix_blocks() { return tuning().sort_blocks_per_sm * device_sm_count(); }
 void radix_sort_u32(uint32_t*& kA, uint32_t*& vA, uint32_t*& kB, uint32_t*& vB, const uint32_t* n_dev,
                     uint32_t n_host, size_t capacity, int bits, SortWs& w, int nb, cudaStream_t st) {
   for (int shift = 0; shift < bits; shift += 8) {
-    radix_hist_kernel<<<nb, kRadixThreads, 0, st>>>(kA, n_dev, n_host, capacity, shift, w.hist);
-    radix_scan_kernel<<<256, 1024, 0, st>>>(w.hist, nb * kRadixWarps, w.totals);
-    radix_scatter_kernel<<<nb, kRadixThreads, 0, st>>>(kA, vA, kB, vB, n_dev, n_host, capacity, shift, w.hist,
+    radix_hist_kernel<<<nb, kSortThreads, 0, st>>>(kA, n_dev, n_host, capacity, shift, w.hist);
+    radix_scan_kernel<<<256, 1024, 0, st>>>(w.hist, nb, w.totals);
+    radix_scatter_kernel<<<nb, kSortThreads, 0, st>>>(kA, vA, kB, vB, n_dev, n_host, capacity, shift, w.hist,
                                                        w.totals);
     std::swap(kA, kB);
     std::swap(vA, vB);

@@ -12,7 +12,7 @@ import torch
 
 from . import _lib
 from .core import (Batch, Cameras, Gaussians, Projected, TileLists, adam_c, gs_adam_update, gs_adam_update_groups,
-                   gs_project,
+                   gs_gather_view_pixels, gs_project,
                    gs_project_bwd, gs_raster_bwd, gs_render_fwd, gs_sort_tiles, gs_step_advance, gs_zero,
                    new_status, pose_se3_update, render_bwd_workspace_bytes, track_reproj_fwd_bwd,
                    track_workspace_bytes)
@@ -149,6 +149,7 @@ class JointStep:
         self.obs_point, self.obs_xy, self.view_obs_offset = obs_point, obs_xy, view_obs_offset
         self.targets = targets                  # all views, packed by target_px_offset
         self.target_px_offset = np.asarray(target_px_offset, dtype=np.int64)
+        self.target_px_offset_dev = torch.as_tensor(self.target_px_offset, device=device)
         self.loss = torch.zeros(2, dtype=torch.float64, device=device)   # [L_photo, sum rho]
         self.n_masked = torch.zeros(1, dtype=torch.int32, device=device)
         self.step_no = torch.zeros(1, dtype=torch.int32, device=device)
@@ -178,12 +179,22 @@ class JointStep:
         self.graph = None
 
     def load_targets(self):
-        """Gathers the batch's target images into slot order (one device
-        copy per view)."""
-        for b, v in enumerate(self.views):
-            a, e = int(self.target_px_offset[v]), int(self.target_px_offset[v + 1])
-            d = int(self.batch.px_offset_host[b])
-            self.target_batch[d:d + (e - a)].copy_(self.targets[a:e], non_blocking=True)
+        """Gathers the batch's target images into slot order on the device
+        (the step does this itself; this is for use outside a step)."""
+        gs_gather_view_pixels(self.targets, self.target_px_offset_dev, self.cams, self.batch, self.target_batch)
+
+    def next_batch(self, views):
+        """Switches to another batch of views.  Views of the same per-slot
+        sizes are swapped in place on the device, so a captured graph stays
+        valid; other sizes re-allocate (and drop the graph)."""
+        if self.batch.same_layout(self.cams, views):
+            self.batch.set_views(self.cams, views)
+            if self.mode != "batched":
+                for b, v in zip(self.slot_batches, np.asarray(views).reshape(-1)):
+                    b.set_views(self.cams, [v])
+            self.views = np.asarray(views, dtype=np.int64)
+        else:
+            self.set_batch(views)
 
     def ensure_capacity(self):
         grew = False
@@ -203,6 +214,7 @@ class JointStep:
         h = self.h
         for t in self.dg.tensors() + [self.gX, self.g_tan, self.loss, self.n_masked]:
             gs_zero(t)
+        gs_gather_view_pixels(self.targets, self.target_px_offset_dev, self.cams, self.batch, self.target_batch)
         mark("zero")
         if self.mode == "batched":
             r = self.renderers[0]
@@ -243,8 +255,9 @@ class JointStep:
             # duplicate 1, tile sort 3 per pass, ranges 1; render fwd 1;
             # raster bwd 1; project bwd + finalize 2
             per_render += 1 + (1 + 12 + 3 + 1 + 3 * ((tbits + 7) // 8) + 1) + 1 + 1 + 2
-        # track + finalize 2, step advance 1, Adam (all groups) 1, pose 1
-        return per_render + 2 + 1 + 1 + 1
+        # target gather 1, track + finalize 2, step advance 1, Adam (all
+        # groups) 1, pose 1
+        return per_render + 1 + 2 + 1 + 1 + 1
 
     # -- CUDA graph ----------------------------------------------------------
     def capture(self, warmup: int = 1):
