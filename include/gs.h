@@ -66,8 +66,11 @@ enum {
   GS_FLAG_CAPACITY = 1,   /* more tile instances than `capacity`: the sort
                              and renders ran on a truncated list; re-run
                              with a larger capacity                      */
-  GS_FLAG_NONFINITE = 2   /* a Gaussian had a non-finite parameter and was
+  GS_FLAG_NONFINITE = 2,  /* a Gaussian had a non-finite parameter and was
                              treated as invisible                         */
+  GS_FLAG_SORT_STALL = 4  /* a sort block gave up waiting (after 2^20
+                             polls) for a predecessor block's digit
+                             counts: the tile lists are invalid          */
 };
 
 #define GS_ABI_VERSION 1
@@ -135,6 +138,9 @@ typedef struct gs_projected {
   uint16_t* rect;   /* [B*N,4] tile rectangle x0, y0, x1, y1 (inclusive,
                        tile units, within the view)                      */
   uint32_t* n_tiles;/* [B*N]   tiles touched; 0 = invisible in that view   */
+  uint32_t* depth_key; /* [B*N] depth sort key: float bits of the camera
+                       depth if visible (positive floats order like their
+                       bits), 0xffffffff if not                          */
 } gs_projected;
 
 /* Adam hyperparameters.  `step` points to a DEVICE int32 holding the
@@ -148,9 +154,9 @@ typedef struct gs_adam {
 /* Launch tuning, process-wide (chosen by an autotuner; results do not
  * depend on it).  render_batch: splat records staged in shared memory per
  * round by the compositing kernels (64, 128 or 256); sort_blocks_per_sm:
- * thread blocks per SM of the radix passes (1..8).  Workspace sizes depend
- * on sort_blocks_per_sm: query them after changing it.  Not synchronised:
- * set it while no other thread calls the library. */
+ * grid of the sort's grid-stride kernels (histogram, zeroing, ranges), in
+ * 2048-thread units per SM (1..8).  Not synchronised: set it while no other
+ * thread calls the library. */
 typedef struct gs_tuning {
   int32_t render_batch;
   int32_t sort_blocks_per_sm;
@@ -208,7 +214,11 @@ gs_status gs_project(const gs_gaussians* g, const gs_cameras* cams,
  * back by the library, so the call can be captured in a CUDA graph.  If it
  * exceeds `capacity`, GS_FLAG_CAPACITY is set and only the first `capacity`
  * instances (in depth order) are sorted and rendered; re-run with more.
- * tiles/vals: [capacity] uint32; ranges: [2 * batch->n_tiles]; ws: see query.
+ * tiles/vals: [capacity] uint32 (tiles 16-byte aligned); ranges:
+ * [2 * batch->n_tiles]; ws: see query (256-byte aligned).  Reads the
+ * depth_key and n_tiles arrays gs_project wrote.  Each radix pass is one
+ * kernel whose blocks wait (bounded) on the counts of the blocks before
+ * them; a wait that runs out sets GS_FLAG_SORT_STALL.
  */
 gs_status gs_sort_tiles_workspace(int32_t n_gaussians, const gs_batch* batch,
                                   size_t capacity, size_t* ws_bytes);

@@ -16,6 +16,7 @@ c_int32, c_int64, c_float, c_void_p, c_size_t = (ctypes.c_int32, ctypes.c_int64,
 GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_NONFINITE, GS_ERR_UNSUPPORTED = range(6)
 GS_FLAG_CAPACITY = 1
 GS_FLAG_NONFINITE = 2
+GS_FLAG_SORT_STALL = 4
 GS_MAX_BATCH = 64
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_ARG", 2: "GS_ERR_CAPACITY", 3: "GS_ERR_CUDA",
                 4: "GS_ERR_NONFINITE", 5: "GS_ERR_UNSUPPORTED"}
@@ -43,7 +44,7 @@ class gs_batch(ctypes.Structure):
 
 
 class gs_projected(ctypes.Structure):
-    _fields_ = [("splat", c_void_p), ("rect", c_void_p), ("n_tiles", c_void_p)]
+    _fields_ = [("splat", c_void_p), ("rect", c_void_p), ("n_tiles", c_void_p), ("depth_key", c_void_p)]
 
 
 class gs_adam(ctypes.Structure):

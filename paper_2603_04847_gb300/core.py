@@ -159,16 +159,18 @@ class Batch:
 
 class Projected:
     """Per-(slot, Gaussian) records: splat [B*N,12] f32, rect [B*N,4] u16,
-    n_tiles [B*N] u32 (int16/int32 storage)."""
+    n_tiles [B*N] u32, depth_key [B*N] u32 (int16/int32 storage)."""
 
     def __init__(self, n: int, B: int, device="cuda"):
         M = n * B
         self.splat = torch.empty((max(M, 1), 12), dtype=torch.float32, device=device)
         self.rect = torch.empty((max(M, 1), 4), dtype=torch.int16, device=device)
         self.n_tiles = torch.zeros((max(M, 1),), dtype=torch.int32, device=device)
+        self.depth_key = torch.empty((max(M, 1),), dtype=torch.int32, device=device)
 
     def c(self):
-        return _lib.gs_projected(self.splat.data_ptr(), self.rect.data_ptr(), self.n_tiles.data_ptr())
+        return _lib.gs_projected(self.splat.data_ptr(), self.rect.data_ptr(), self.n_tiles.data_ptr(),
+                                 self.depth_key.data_ptr())
 
 
 class TileLists:

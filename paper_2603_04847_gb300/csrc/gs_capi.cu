@@ -58,9 +58,9 @@ gs_status check_batch(const gs_batch* b) {
 
 gs_status check_projected(const gs_projected* p) {
   if (!p) return fail(GS_ERR_ARG, "projected: null");
-  if (!p->splat || !p->rect || !p->n_tiles) return fail(GS_ERR_ARG, "projected: null array");
-  if (!aligned(p->splat, 16) || !aligned(p->rect, 8))
-    return fail(GS_ERR_ARG, "projected: splat must be 16-byte and rect 8-byte aligned");
+  if (!p->splat || !p->rect || !p->n_tiles || !p->depth_key) return fail(GS_ERR_ARG, "projected: null array");
+  if (!aligned(p->splat, 16) || !aligned(p->rect, 8) || !aligned(p->depth_key, 16))
+    return fail(GS_ERR_ARG, "projected: splat and depth_key must be 16-byte, rect 8-byte aligned");
   return GS_OK;
 }
 
@@ -168,6 +168,7 @@ gs_status gs_sort_tiles(int32_t n_gaussians, const gs_cameras* cams, const gs_ba
   if (capacity == 0 || capacity >= 0xffffffffull)
     return fail(GS_ERR_CAPACITY, "gs_sort_tiles: capacity must be in [1, 2^32 - 1)");
   if (!aligned(ws, 256)) return fail(GS_ERR_ARG, "gs_sort_tiles: ws must be 256-byte aligned");
+  if (!aligned(tiles, 16)) return fail(GS_ERR_ARG, "gs_sort_tiles: tiles must be 16-byte aligned");
   const size_t need = sort_workspace_bytes(n_gaussians, *batch, capacity);
   if (ws_bytes < need) return fail(GS_ERR_ARG, "gs_sort_tiles: workspace %zu < %zu bytes", ws_bytes, need);
   cudaError_t e = launch_sort_tiles(n_gaussians, *cams, *batch, *proj, tiles, vals, capacity, ranges,

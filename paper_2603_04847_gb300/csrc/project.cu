@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(kProjThreads) project_fwd_kernel(gs_gaussians 
     const size_t rec = (size_t)b * N + j;
     const SlotCam& c = sc[b];
     uint32_t ntiles = 0;
+    uint32_t dkey = 0xffffffffu;
     if (ok && opaque_enough) {
       ViewGeo V;
       view_geo(G, c, cams.near_plane, cams.far_plane, V);
@@ -202,6 +203,7 @@ __global__ void __launch_bounds__(kProjThreads) project_fwd_kernel(gs_gaussians 
           const int tx0 = (int)x0 / T, ty0 = (int)y0 / T;
           const int tx1 = (int)x1 / T, ty1 = (int)y1 / T;
           ntiles = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+          dkey = __float_as_uint(V.xc[2]);
           float Y[K];
           sh_basis(DEG, V.dir[0], V.dir[1], V.dir[2], Y);
           float col[3];
@@ -223,6 +225,7 @@ __global__ void __launch_bounds__(kProjThreads) project_fwd_kernel(gs_gaussians 
       }
     }
     out.n_tiles[rec] = ntiles;
+    out.depth_key[rec] = dkey;
   }
 }
 

@@ -1,11 +1,12 @@
 // Per-tile duplication and depth ordering of projected splats.
 //
 //   depth sort  stable LSD radix sort of the B*N records r = b*N + j by the
-//               float bits of their camera depth (invisible records last);
-//               ties keep record order, i.e. index order within a view
+//               float bits of their camera depth (keys written by the
+//               projection; invisible records last); ties keep record
+//               order, i.e. index order within a view
 //   scan        exclusive prefix sum of tiles-touched in depth order
-//   duplicate   one (global tile, r) instance per covered tile, emitted in
-//               depth order
+//   expand      one (global tile, r) instance per covered tile, emitted in
+//               depth order; each block owns one contiguous output range
 //   tile sort   stable LSD radix sort of the instances by tile id, over the
 //               bits the largest tile id uses only
 //   ranges      [start, end) per global tile
@@ -14,11 +15,19 @@
 // moves far fewer bytes than sorting 12-byte instances by a 47-bit
 // (tile, depth) key, and gives the same order: (tile, depth, j).
 //
+// Each radix pass is ONE kernel (the single-sweep form with decoupled
+// look-back): the digit counts of every pass are known before the first
+// pass (one histogram of the depth keys; the tile-id histogram is counted
+// while the instances are emitted), so a block only needs, per digit, the
+// number of smaller-indexed items carrying that digit, which it gets from
+// the counts its predecessor blocks publish.  Blocks take their 4096-item
+// tile from an atomic counter, so every block a tile waits on is already
+// running; each wait is bounded and raises GS_FLAG_SORT_STALL when the
+// bound runs out instead of hanging.
+//
 // The instance count stays on the device: every kernel after the scan reads
 // it, and all grids are sized from host-known bounds (records, capacity, SM
-// count), so the whole stage can be captured in a CUDA graph.  Each radix
-// pass is the classic three-kernel form (per-block digit histogram,
-// per-digit scan over blocks, stable scatter); no block waits on another.
+// count), so the whole stage can be captured in a CUDA graph.
 #include "gs_internal.h"
 
 namespace gs {
@@ -27,7 +36,31 @@ namespace {
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
-constexpr int kScanTile = kScanThreads * kScanItems;  // 2048 items per tile
+constexpr int kScanTile = kScanThreads * kScanItems;  // 2048 records per scan block
+
+constexpr int kSortThreads = 512;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kRounds = 8;                            // rounds of 32 items per warp
+constexpr int kWarpItems = 32 * kRounds;              // 256
+constexpr int kTileItems = kSortWarps * kWarpItems;   // 4096 items per radix tile
+constexpr int kMaxDigits = 4;                         // 32-bit keys, 8-bit digits
+
+// Look-back words: state in the top two bits, count in the low 62.
+constexpr unsigned long long kLbAggregate = 1ull << 62;  // this tile's own count
+constexpr unsigned long long kLbInclusive = 2ull << 62;  // count over tiles 0..t
+constexpr unsigned long long kLbCount = (1ull << 62) - 1;
+constexpr int kSpinLimit = 1 << 20;   // polls of one unpublished word
+constexpr int kLbWindow = 8;          // predecessors read per look-back step
+
+__device__ inline void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ inline unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 
 __device__ inline uint32_t block_exclusive_scan_u32(uint32_t v, uint32_t* total, uint32_t* sm) {
   // sm: >= 32 words.  Returns exclusive prefix of v over the block.
@@ -57,31 +90,235 @@ __device__ inline uint32_t block_exclusive_scan_u32(uint32_t v, uint32_t* total,
   return warp_prefix + x - v;
 }
 
-// Depth sort keys: float bits of the depth (positive, so the bits order like
-// the values) for visible records, all ones for invisible ones.
-__global__ void __launch_bounds__(256) depth_keys_kernel(gs_projected proj, uint32_t M,
-                                                         uint32_t* __restrict__ keys,
-                                                         uint32_t* __restrict__ vals) {
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < M; r += gridDim.x * blockDim.x) {
-    const bool vis = proj.n_tiles[r] != 0;
-    keys[r] = vis ? __float_as_uint(reinterpret_cast<const float4*>(proj.splat)[3 * (size_t)r].w)
-                  : 0xffffffffu;
-    vals[r] = r;
+// Zeroes, per call: the digit histograms, the tile counters, the look-back
+// words of the depth passes, the ranges and the instance count.
+struct SortZero {
+  uint32_t* ghist;                 // [2 * kMaxDigits * 256]
+  uint32_t* counters;              // [2 * kMaxDigits]
+  unsigned long long* lb_depth;    // [kMaxDigits * depth tiles * 256]
+  size_t lb_depth_words;
+  uint32_t* ranges;                // [2 * n_tiles]
+  size_t ranges_words;
+  uint32_t* n_instances;
+};
+
+__global__ void __launch_bounds__(256) sort_zero_kernel(SortZero z) {
+  const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, step = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = i0; i < 2 * kMaxDigits * 256; i += step) z.ghist[i] = 0;
+  for (size_t i = i0; i < 2 * kMaxDigits; i += step) z.counters[i] = 0;
+  for (size_t i = i0; i < z.lb_depth_words; i += step) z.lb_depth[i] = 0;
+  for (size_t i = i0; i < z.ranges_words; i += step) z.ranges[i] = 0;
+  if (i0 == 0) *z.n_instances = 0;
+}
+
+// Counts of each 8-bit digit of keys[0, n), for digits 0..n_digits-1:
+// ghist[d * 256 + v] += number of keys whose digit d is v.  keys 16-byte
+// aligned.  A thread whose four keys share a digit value adds them at once
+// (the high digits of nearby depths mostly agree).
+__global__ void __launch_bounds__(256) digit_hist_kernel(const uint32_t* __restrict__ keys, uint32_t n,
+                                                         int n_digits, uint32_t* __restrict__ ghist) {
+  __shared__ uint32_t h[kMaxDigits][256];
+  for (int i = threadIdx.x; i < kMaxDigits * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t nv = n / 4;
+  const uint4* k4 = reinterpret_cast<const uint4*>(keys);
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+    const uint4 q = k4[i];
+    for (int d = 0; d < n_digits; ++d) {
+      const int s = 8 * d;
+      const uint32_t a = (q.x >> s) & 0xffu, b = (q.y >> s) & 0xffu;
+      const uint32_t c = (q.z >> s) & 0xffu, e = (q.w >> s) & 0xffu;
+      if (a == b && b == c && c == e) {
+        atomicAdd(&h[d][a], 4u);
+      } else {
+        atomicAdd(&h[d][a], 1u);
+        atomicAdd(&h[d][b], 1u);
+        atomicAdd(&h[d][c], 1u);
+        atomicAdd(&h[d][e], 1u);
+      }
+    }
+  }
+  for (uint32_t i = 4 * nv + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    for (int d = 0; d < n_digits; ++d) atomicAdd(&h[d][(keys[i] >> (8 * d)) & 0xffu], 1u);
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_digits * 256; i += blockDim.x) {
+    const uint32_t c = (&h[0][0])[i];
+    if (c) atomicAdd(&ghist[i], c);
   }
 }
 
-// Sum of n_tiles[order[k]] per scan tile (64-bit to detect overflow).
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ in,
-                                                                   const uint32_t* __restrict__ order,
-                                                                   size_t M,
-                                                                   unsigned long long* tile_sums) {
+// One stable radix pass over the 8-bit digit at `shift`.
+//   kin/vin    input keys / values; vin == nullptr means value = index
+//   kout/vout  output; kout may be nullptr (keys not needed afterwards)
+//   ghist      [256] counts of this digit over all n items
+//   gather     if gather_src: gather_dst[pos] = gather_src[value] as well
+// Per tile: every warp ranks its 256 contiguous items (8 rounds of 32)
+// against a warp-private running count per digit (peers found with one
+// ballot per digit bit, which measured faster than a warp match); one block step turns the per-warp counts into
+// offsets within the tile and the tile's digit counts, which are published
+// for the successors; items are staged digit-sorted in shared memory; the
+// look-back adds up the counts of the preceding tiles per digit; the staged
+// items are written out in order, so consecutive threads write consecutive
+// addresses of a digit's run.  Equal digits keep their input
+// order: tiles, warps, rounds and lanes are all taken in input order.
+__global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, const uint32_t* n_dev, uint32_t n_host, size_t capacity, int shift,
+    const uint32_t* __restrict__ ghist, unsigned long long* lookback, uint32_t* tile_counter,
+    const uint32_t* __restrict__ gather_src, uint32_t* __restrict__ gather_dst, int32_t* status) {
+  __shared__ uint32_t s_base[256];    // output position of this tile's first item of each digit
+  __shared__ uint32_t s_tot[256];     // items of each digit in this tile
+  __shared__ uint32_t s_dstart[256];  // exclusive scan of s_tot
+  __shared__ uint16_t s_wrun[kSortWarps][256];
+  __shared__ uint32_t s_keys[kTileItems];
+  __shared__ uint32_t s_vals[kTileItems];
+  __shared__ uint32_t sm[32];
+  __shared__ uint32_t s_tile;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+  for (int d = lane; d < 256; d += 32) s_wrun[warp][d] = 0;
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const uint32_t n = n_dev ? (uint32_t)min((size_t)*n_dev, capacity) : n_host;
+  if ((size_t)t * kTileItems >= n) return;  // block-uniform
+  const uint32_t tile0 = t * kTileItems;
+  const uint32_t tile_n = min((uint32_t)kTileItems, n - tile0);
+
+  // 1. load the keys and rank within the warp
+  uint32_t k[kRounds], v[kRounds], r[kRounds];
+#pragma unroll
+  for (int s = 0; s < kRounds; ++s) {
+    const uint32_t li = (uint32_t)(warp * kWarpItems + s * 32 + lane);
+    k[s] = li < tile_n ? kin[tile0 + li] : 0u;
+  }
+  const unsigned lt_mask = (1u << lane) - 1u;
+#pragma unroll
+  for (int s = 0; s < kRounds; ++s) {
+    const uint32_t li = (uint32_t)(warp * kWarpItems + s * 32 + lane);
+    const bool valid = li < tile_n;
+    const uint32_t d = (k[s] >> shift) & 0xffu;
+    unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const unsigned m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+      peers &= ((d >> b) & 1u) ? m : ~m;
+    }
+    r[s] = valid ? (uint32_t)s_wrun[warp][d] + __popc(peers & lt_mask) : 0u;
+    __syncwarp();
+    if (valid && (peers & lt_mask) == 0) s_wrun[warp][d] += (uint16_t)__popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+
+  // values are first needed in step 4: load them now
+#pragma unroll
+  for (int s = 0; s < kRounds; ++s) {
+    const uint32_t li = (uint32_t)(warp * kWarpItems + s * 32 + lane);
+    v[s] = li < tile_n ? (vin ? vin[tile0 + li] : tile0 + li) : 0u;
+  }
+
+  // 2. per digit: offsets of the warps within the tile, the tile's count,
+  //    published at once so that successors need not wait for step 5
+  if (tid < 256) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+      const uint32_t c = s_wrun[w][tid];
+      s_wrun[w][tid] = (uint16_t)acc;
+      acc += c;
+    }
+    s_tot[tid] = acc;
+    st_relaxed_u64(&lookback[(size_t)t * 256 + tid], (t == 0 ? kLbInclusive : kLbAggregate) | acc);
+  }
+  __syncthreads();
+
+  // 3. digit starts within the tile and over all items
+  const uint32_t ex_local = block_exclusive_scan_u32(tid < 256 ? s_tot[tid] : 0u, nullptr, sm);
+  if (tid < 256) s_dstart[tid] = ex_local;
+  const uint32_t ex_global = block_exclusive_scan_u32(tid < 256 ? ghist[tid] : 0u, nullptr, sm);
+
+  // 4. stage digit-sorted in shared memory (before the look-back, which
+  //    then finds more predecessors done)
+#pragma unroll
+  for (int s = 0; s < kRounds; ++s) {
+    const uint32_t li = (uint32_t)(warp * kWarpItems + s * 32 + lane);
+    if (li < tile_n) {
+      const uint32_t d = (k[s] >> shift) & 0xffu;
+      const uint32_t p = s_dstart[d] + s_wrun[warp][d] + r[s];
+      s_keys[p] = k[s];
+      s_vals[p] = v[s];
+    }
+  }
+
+  // 5. look-back: items of digit d in tiles 0..t-1.  The words of kLbWindow
+  //    predecessors are read at once and summed back to the nearest
+  //    inclusive one; an unpublished word is polled again (bounded).
+  if (tid < 256) {
+    unsigned long long before = 0;
+    long long j = (long long)t - 1;
+    int polls = 0;
+    while (j >= 0) {
+      unsigned long long w[kLbWindow];
+#pragma unroll
+      for (int q = 0; q < kLbWindow; ++q)
+        w[q] = j - q >= 0 ? ld_relaxed_u64(&lookback[(size_t)(j - q) * 256 + tid]) : kLbInclusive;
+      int adv = 0;
+      bool found = false, blocked = false;
+#pragma unroll
+      for (int q = 0; q < kLbWindow; ++q) {
+        if (!found && !blocked) {
+          const unsigned long long state = w[q] >> 62;
+          if (state == 0) {
+            blocked = true;
+          } else {
+            before += w[q] & kLbCount;
+            ++adv;
+            found = state != 1;
+          }
+        }
+      }
+      if (found) break;
+      j -= adv;
+      if (adv == 0) {
+        if (++polls > kSpinLimit) {
+          set_flag(status, GS_FLAG_SORT_STALL);
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    if (t > 0) st_relaxed_u64(&lookback[(size_t)t * 256 + tid], kLbInclusive | (before + s_tot[tid]));
+    s_base[tid] = ex_global + (uint32_t)before;
+  }
+  __syncthreads();
+
+  // 6. write runs: consecutive threads, consecutive positions of a digit
+#pragma unroll
+  for (int i = 0; i < kRounds; ++i) {
+    const uint32_t p = (uint32_t)(tid + i * kSortThreads);
+    if (p < tile_n) {
+      const uint32_t key = s_keys[p];
+      const uint32_t d = (key >> shift) & 0xffu;
+      const uint32_t pos = s_base[d] + (p - s_dstart[d]);
+      const uint32_t val = s_vals[p];
+      if (kout) kout[pos] = key;
+      vout[pos] = val;
+      if (gather_src) gather_dst[pos] = gather_src[val];
+    }
+  }
+}
+
+// Sum of in[k] per scan block (64-bit to detect overflow).
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ in, size_t M,
+                                                                   unsigned long long* block_sums) {
   __shared__ unsigned long long red[kScanThreads / 32];
   const size_t base = (size_t)blockIdx.x * kScanTile;
   unsigned long long s = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const size_t k = base + (size_t)i * kScanThreads + threadIdx.x;
-    if (k < M) s += in[order[k]];
+    if (k < M) s += in[k];
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
@@ -90,79 +327,51 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
     for (int w = 0; w < kScanThreads / 32; ++w) t += red[w];
-    tile_sums[blockIdx.x] = t;
+    block_sums[blockIdx.x] = t;
   }
 }
 
-// Exclusive scan of the tile sums in one block; writes the instance count
+// Exclusive scan of the block sums in one block; writes the instance count
 // and raises GS_FLAG_CAPACITY when it exceeds the capacity.
-__global__ void __launch_bounds__(1024) scan_tiles_kernel(unsigned long long* tile_sums, int n_tiles,
-                                                          size_t capacity, uint32_t* n_instances,
-                                                          int32_t* status) {
+__global__ void __launch_bounds__(1024) scan_blocks_kernel(unsigned long long* block_sums, int n_blocks,
+                                                           size_t capacity, uint32_t* n_instances,
+                                                           int32_t* status) {
   __shared__ unsigned long long sm[32];
-  const int per = (n_tiles + blockDim.x - 1) / blockDim.x;
-  const int lo = threadIdx.x * per;
-  const int hi = min(lo + per, n_tiles);
-  unsigned long long s = 0;
-  for (int k = lo; k < hi; ++k) s += tile_sums[k];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long x = s;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, off);
-    if (lane >= off) x += y;
-  }
-  if (lane == 31) sm[warp] = x;
+  __shared__ unsigned long long carry;
+  if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  if (warp == 0) {
-    const int nw = blockDim.x >> 5;
-    unsigned long long w = lane < nw ? sm[lane] : 0ull;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int base = 0; base < n_blocks; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const unsigned long long v = i < n_blocks ? block_sums[i] : 0ull;
+    unsigned long long x = v;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xffffffffu, w, off);
-      if (lane >= off) w += y;
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, off);
+      if (lane >= off) x += y;
     }
-    if (lane < nw) sm[lane] = w;
+    if (lane == 31) sm[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned long long w = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0ull;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, w, off);
+        if (lane >= off) w += y;
+      }
+      sm[lane] = w;
+    }
+    __syncthreads();
+    const unsigned long long excl = carry + (warp > 0 ? sm[warp - 1] : 0ull) + x - v;
+    if (i < n_blocks) block_sums[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+    __syncthreads();
   }
-  __syncthreads();
-  unsigned long long run = (warp > 0 ? sm[warp - 1] : 0ull) + x - s;
-  for (int k = lo; k < hi; ++k) {
-    const unsigned long long v = tile_sums[k];
-    tile_sums[k] = run;
-    run += v;
-  }
-  if (threadIdx.x == blockDim.x - 1) {
-    // the full count (saturated to 32 bits) tells the host how much capacity
-    // it needs; every consumer uses min(count, capacity)
-    const unsigned long long total = run;
-    if (total > (unsigned long long)capacity) set_flag(status, GS_FLAG_CAPACITY);
+  if (threadIdx.x == 0) {
+    const unsigned long long total = carry;
     *n_instances = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
-  }
-}
-
-__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t* __restrict__ in,
-                                                                  const uint32_t* __restrict__ order,
-                                                                  size_t M,
-                                                                  const unsigned long long* tile_offs,
-                                                                  uint32_t* __restrict__ out) {
-  __shared__ uint32_t sm[32];
-  const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
-  uint32_t v[kScanItems];
-  uint32_t s = 0;
-#pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    const size_t k = base + i;
-    v[i] = k < M ? in[order[k]] : 0u;
-    s += v[i];
-  }
-  const uint32_t ex = block_exclusive_scan_u32(s, nullptr, sm);
-  // offsets beyond 2^32 cannot be valid instances (capacity < 2^32): clamp
-  unsigned long long run = tile_offs[blockIdx.x] + ex;
-#pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    const size_t k = base + i;
-    if (k < M) out[k] = run > 0xffffffffull ? 0xffffffffu : (uint32_t)run;
-    run += v[i];
+    if (total > capacity) set_flag(status, GS_FLAG_CAPACITY);
   }
 }
 
@@ -171,238 +380,172 @@ struct SlotTiles {
   int tile_offset;
 };
 
-// Instances in depth order: position k of the depth-sorted records emits
-// its tiles at offs[k] onwards.
-__global__ void __launch_bounds__(256) duplicate_kernel(gs_projected proj, const uint32_t* __restrict__ order,
-                                                        const uint32_t* __restrict__ offs, int N, gs_cameras cams,
-                                                        gs_batch batch, uint32_t* __restrict__ tiles,
-                                                        uint32_t* __restrict__ vals, size_t capacity,
-                                                        int32_t* status) {
+// Emits the instances of 2048 depth-sorted records.  Their instances are
+// one contiguous output range (from the scan), written coalesced: output q
+// of the block belongs to the record i with off[i] <= q < off[i+1]
+// (searched in shared memory) and is its (q - off[i])-th covered tile in
+// row-major order.  Also counts the tile-id digits for the tile sort and
+// zeroes a share of the tile sort's look-back words.
+__global__ void __launch_bounds__(kScanThreads) expand_kernel(
+    const uint32_t* __restrict__ ntd, const uint32_t* __restrict__ order, size_t M,
+    const unsigned long long* __restrict__ block_offs, gs_projected proj, int N, gs_cameras cams,
+    gs_batch batch, uint32_t* __restrict__ tiles, uint32_t* __restrict__ vals, size_t capacity,
+    const uint32_t* n_instances, int n_digits, uint32_t* __restrict__ ghist,
+    unsigned long long* __restrict__ lb_tile, size_t lb_tile_stride) {
+  __shared__ uint32_t s_off[kScanTile + 1];
+  __shared__ uint32_t s_rec[kScanTile];
+  __shared__ ushort4 s_rect[kScanTile];
+  __shared__ uint8_t s_slot[kScanTile];
   __shared__ SlotTiles st[GS_MAX_BATCH];
-  for (int b = threadIdx.x; b < batch.B; b += blockDim.x) {
+  __shared__ uint32_t h[kMaxDigits][256];
+  __shared__ uint32_t sm[32];
+  const int tid = threadIdx.x;
+  for (int b = tid; b < batch.B; b += blockDim.x) {
     const int v = slot_view(cams, batch, b);
     st[b].tiles_x = (cams.wh[2 * v] + batch.tile - 1) / batch.tile;
     st[b].tile_offset = batch.tile_offset[b];
   }
-  __syncthreads();
-  const size_t M = (size_t)batch.B * N;
-  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < M;
-       k += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t r = order[k];
-    const uint32_t n = proj.n_tiles[r];
-    if (n == 0) continue;
-    const int b = (int)(r / (uint32_t)N);
-    const ushort4 rc = reinterpret_cast<const ushort4*>(proj.rect)[r];
-    size_t o = offs[k];
-    if (o + n > capacity) set_flag(status, GS_FLAG_CAPACITY);
-    const int tx_n = st[b].tiles_x, t0 = st[b].tile_offset;
-    for (int ty = rc.y; ty <= rc.w; ++ty)
-      for (int tx = rc.x; tx <= rc.z; ++tx) {
-        if (o < capacity) {
-          tiles[o] = (uint32_t)(t0 + ty * tx_n + tx);
-          vals[o] = r;
-        }
-        ++o;
-      }
-  }
-}
+  for (int i = tid; i < kMaxDigits * 256; i += blockDim.x) (&h[0][0])[i] = 0;
 
-// ---------------------------------------------------------------------------
-// Stable LSD radix sort of (uint32 key, uint32 value) pairs, 8-bit digits.
-// The item count is either host-known (n_dev == nullptr) or read on the
-// device, clamped to the buffer capacity.
-//
-// Each block owns a contiguous chunk of the items (a multiple of the 4096-item
-// tile).  Pass = histogram per block, scan per digit over blocks, scatter.
-// The scatter works tile by tile: every warp ranks its own 256 contiguous
-// items (8 rounds of 32) against a warp-private running count per digit;
-// one block step turns the per-warp counts into offsets within the tile;
-// items are staged digit-sorted in shared memory and then written out in
-// that order, so consecutive threads write consecutive addresses of a
-// digit's run (full sectors, not one scattered word per item).  Equal
-// digits keep their input order: tiles, warps, rounds and lanes are all
-// taken in input order.
-
-constexpr int kSortThreads = 512;
-constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kWarpItems = 256;                       // 8 rounds of 32 per warp
-constexpr int kTileItems = kSortWarps * kWarpItems;   // 4096
-
-__device__ inline uint32_t radix_count(const uint32_t* n_dev, uint32_t n_host, size_t capacity) {
-  return n_dev ? (uint32_t)min((size_t)*n_dev, capacity) : n_host;
-}
-
-__device__ inline void chunk_of(uint32_t n, int nb, int blk, uint32_t& lo, uint32_t& hi) {
-  uint32_t chunk = (n + nb - 1) / nb;
-  chunk = (chunk + kTileItems - 1) / kTileItems * kTileItems;
-  lo = min((uint32_t)blk * chunk, n);
-  hi = min(lo + chunk, n);
-}
-
-__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t* __restrict__ keys,
-                                                                  const uint32_t* n_dev, uint32_t n_host,
-                                                                  size_t capacity, int shift,
-                                                                  uint32_t* __restrict__ hist) {
-  __shared__ uint32_t h[kSortWarps][256];
-  for (int i = threadIdx.x; i < kSortWarps * 256; i += blockDim.x) (&h[0][0])[i] = 0;
-  __syncthreads();
-  const uint32_t n = radix_count(n_dev, n_host, capacity);
-  uint32_t lo, hi;
-  chunk_of(n, gridDim.x, blockIdx.x, lo, hi);
-  const int warp = threadIdx.x >> 5;
-  for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&h[warp][(keys[i] >> shift) & 0xffu], 1u);
-  __syncthreads();
-  for (int d = threadIdx.x; d < 256; d += blockDim.x) {
-    uint32_t t = 0;
-#pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) t += h[w][d];
-    hist[(size_t)d * gridDim.x + blockIdx.x] = t;
-  }
-}
-
-// Block d: exclusive scan over the row of digit d (block order), in place,
-// in one blocked pass; digit total to totals[d].
-__global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* hist, int row_len, uint32_t* totals) {
-  __shared__ uint32_t sm[32];
-  uint32_t* row = hist + (size_t)blockIdx.x * row_len;
-  const int per = (row_len + blockDim.x - 1) / blockDim.x;
-  const int lo = min((int)threadIdx.x * per, row_len), hi = min(lo + per, row_len);
-  uint32_t s = 0;
-  for (int k = lo; k < hi; ++k) s += row[k];
-  uint32_t tot;
-  uint32_t run = block_exclusive_scan_u32(s, &tot, sm);
-  for (int k = lo; k < hi; ++k) {
-    const uint32_t v = row[k];
-    row[k] = run;
-    run += v;
-  }
-  if (threadIdx.x == 0) totals[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
-    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, const uint32_t* n_dev, uint32_t n_host, size_t capacity, int shift,
-    const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals) {
-  __shared__ uint32_t s_base[256];     // global start of this block's next items of each digit
-  __shared__ uint32_t s_tot[256];      // items of each digit in the current tile
-  __shared__ uint32_t s_dstart[256];   // exclusive scan of s_tot
-  __shared__ uint16_t s_wrun[kSortWarps][256];
-  __shared__ uint32_t s_keys[kTileItems];
-  __shared__ uint32_t s_vals[kTileItems];
-  __shared__ uint32_t sm[32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // zero the look-back words of the tile sort's tiles that will be used
   {
-    const uint32_t t = tid < 256 ? totals[tid] : 0u;
-    const uint32_t ex = block_exclusive_scan_u32(t, nullptr, sm);
-    if (tid < 256) s_base[tid] = ex + hist[(size_t)tid * gridDim.x + blockIdx.x];
+    const size_t n_used = min((size_t)*n_instances, capacity);
+    const size_t words = ((n_used + kTileItems - 1) / kTileItems) * 256;
+    for (int p = 0; p < n_digits; ++p)
+      for (size_t i = (size_t)blockIdx.x * blockDim.x + tid; i < words; i += (size_t)gridDim.x * blockDim.x)
+        lb_tile[p * lb_tile_stride + i] = 0;
   }
-  const uint32_t n = radix_count(n_dev, n_host, capacity);
-  uint32_t lo, hi;
-  chunk_of(n, gridDim.x, blockIdx.x, lo, hi);
-  const unsigned lt_mask = (1u << lane) - 1u;
-  for (uint32_t tile = lo; tile < hi; tile += kTileItems) {
-    const uint32_t tile_n = min((uint32_t)kTileItems, hi - tile);
-    for (int d = lane; d < 256; d += 32) s_wrun[warp][d] = 0;
-    __syncwarp();
-    // 1. warp-local stable ranking of the warp's 8 rounds of 32 items
-    uint32_t k[8], v[8], r[8];
+
+  const size_t base = (size_t)blockIdx.x * kScanTile;
+  uint32_t c[kScanItems], rr[kScanItems];
+  uint32_t s = 0;
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      const uint32_t li = (uint32_t)(warp * kWarpItems + s * 32 + lane);
-      const bool valid = li < tile_n;
-      k[s] = valid ? kin[tile + li] : 0u;
-      v[s] = valid ? vin[tile + li] : 0u;
-    }
+  for (int i = 0; i < kScanItems; ++i) {
+    const size_t k = base + (size_t)tid * kScanItems + i;
+    c[i] = k < M ? ntd[k] : 0u;
+    rr[i] = k < M ? order[k] : 0u;
+    s += c[i];
+  }
+  ushort4 rc[kScanItems];
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      const uint32_t li = (uint32_t)(warp * kWarpItems + s * 32 + lane);
-      const bool valid = li < tile_n;
-      const uint32_t d = valid ? (k[s] >> shift) & 0xffu : 256u + (uint32_t)lane;  // unique sentinel
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
-      r[s] = valid ? (uint32_t)s_wrun[warp][d] + __popc(peers & lt_mask) : 0u;
-      __syncwarp();
-      if (valid && (peers & lt_mask) == 0) s_wrun[warp][d] += (uint16_t)__popc(peers);
-      __syncwarp();
-    }
-    __syncthreads();
-    // 2. per digit: offsets of the warps within the tile, tile totals
-    if (tid < 256) {
-      uint32_t acc = 0;
+  for (int i = 0; i < kScanItems; ++i)
+    if (c[i]) rc[i] = reinterpret_cast<const ushort4*>(proj.rect)[rr[i]];
+  uint32_t total;
+  uint32_t run = block_exclusive_scan_u32(s, &total, sm);
 #pragma unroll
-      for (int w = 0; w < kSortWarps; ++w) {
-        const uint32_t c = s_wrun[w][tid];
-        s_wrun[w][tid] = (uint16_t)acc;
-        acc += c;
-      }
-      s_tot[tid] = acc;
+  for (int i = 0; i < kScanItems; ++i) {
+    const int li = tid * kScanItems + i;
+    s_off[li] = run;
+    run += c[i];
+    if (c[i]) {
+      s_rec[li] = rr[i];
+      s_rect[li] = rc[i];
+      s_slot[li] = (uint8_t)(rr[i] / (uint32_t)N);
     }
-    __syncthreads();
-    {
-      const uint32_t t = tid < 256 ? s_tot[tid] : 0u;
-      const uint32_t ex = block_exclusive_scan_u32(t, nullptr, sm);
-      if (tid < 256) s_dstart[tid] = ex;
-    }
-    __syncthreads();
-    // 3. stage digit-sorted in shared memory
+  }
+  if (tid == 0) s_off[kScanTile] = total;
+  __syncthreads();
+
+  // Each warp emits one contiguous chunk of the block's outputs, 32 at a
+  // time.  Output q belongs to the largest i with s_off[i] <= q (then
+  // s_off[i+1] > q, so record i is not empty).  Visible records are never
+  // empty and come first in depth order, so the 32 outputs from the record
+  // of the chunk's current position on span at most 32 records: search that
+  // window, and the whole block only where the window misses.
+  const unsigned long long g0 = block_offs[blockIdx.x];
+  const uint32_t n_out = g0 >= capacity ? 0u : (uint32_t)min((unsigned long long)total, capacity - g0);
+  const int lane = tid & 31, warp = tid >> 5, n_warps = kScanThreads / 32;
+  const uint32_t chunk = ((n_out + n_warps - 1) / n_warps + 31) & ~31u;
+  const uint32_t q_lo = min(n_out, (uint32_t)warp * chunk), q_hi = min(n_out, q_lo + chunk);
+  int i_lo = 0;
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      const uint32_t li = (uint32_t)(warp * kWarpItems + s * 32 + lane);
-      if (li < tile_n) {
-        const uint32_t d = (k[s] >> shift) & 0xffu;
-        const uint32_t p = s_dstart[d] + s_wrun[warp][d] + r[s];
-        s_keys[p] = k[s];
-        s_vals[p] = v[s];
-      }
+  for (int step = kScanTile / 2; step > 0; step >>= 1)
+    if (s_off[i_lo + step] <= q_lo) i_lo += step;
+  for (uint32_t q0 = q_lo; q0 < q_hi; q0 += 32) {
+    const uint32_t q = q0 + lane;
+    int i = i_lo;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+      if (i + step <= kScanTile && s_off[i + step] <= q) i += step;
+    if (s_off[i + 1] <= q) {  // window missed (only with empty records inside)
+      i = 0;
+      for (int step = kScanTile / 2; step > 0; step >>= 1)
+        if (s_off[i + step] <= q) i += step;
     }
-    __syncthreads();
-    // 4. write runs: consecutive threads, consecutive positions of a digit
-    for (uint32_t p = tid; p < tile_n; p += kSortThreads) {
-      const uint32_t key = s_keys[p];
-      const uint32_t d = (key >> shift) & 0xffu;
-      const uint32_t pos = s_base[d] + (p - s_dstart[d]);
-      kout[pos] = key;
-      vout[pos] = s_vals[p];
+    i_lo = __shfl_sync(0xffffffffu, i, 31);
+    if (q < q_hi) {
+      const uint32_t j = q - s_off[i];
+      const ushort4 r4 = s_rect[i];
+      const uint32_t w = (uint32_t)(r4.z - r4.x + 1);
+      const uint32_t jy = j / w, jx = j - jy * w;
+      const SlotTiles sl = st[s_slot[i]];
+      const uint32_t tile = (uint32_t)(sl.tile_offset + (int)(r4.y + jy) * sl.tiles_x + (int)(r4.x + jx));
+      tiles[g0 + q] = tile;
+      vals[g0 + q] = s_rec[i];
+      for (int d = 0; d < n_digits; ++d) atomicAdd(&h[d][(tile >> (8 * d)) & 0xffu], 1u);
     }
-    __syncthreads();
-    if (tid < 256) s_base[tid] += s_tot[tid];
-    __syncthreads();
+  }
+  __syncthreads();
+  for (int i = tid; i < n_digits * 256; i += blockDim.x) {
+    const uint32_t cnt = (&h[0][0])[i];
+    if (cnt) atomicAdd(&ghist[i], cnt);
   }
 }
 
+// ranges[2t], ranges[2t+1] = first and one-past-last position of tile t in
+// the sorted tiles[0, n); four items per thread (tiles 16-byte aligned).
 __global__ void __launch_bounds__(256) tile_ranges_kernel(const uint32_t* __restrict__ tiles,
                                                           const uint32_t* n_dev, size_t capacity,
                                                           uint32_t* __restrict__ ranges) {
   const uint32_t n = (uint32_t)min((size_t)*n_dev, capacity);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t t = tiles[i];
-    if (i == 0) {
-      ranges[2 * t] = 0;
+  const uint32_t nq = (uint32_t)(((size_t)n + 3) / 4);
+  for (uint32_t qi = blockIdx.x * blockDim.x + threadIdx.x; qi < nq; qi += gridDim.x * blockDim.x) {
+    const uint32_t i0 = 4 * qi;
+    uint32_t t[4];
+    if ((size_t)i0 + 4 <= n) {
+      const uint4 q = reinterpret_cast<const uint4*>(tiles)[qi];
+      t[0] = q.x, t[1] = q.y, t[2] = q.z, t[3] = q.w;
     } else {
-      const uint32_t p = tiles[i - 1];
-      if (p != t) {
-        ranges[2 * p + 1] = i;
-        ranges[2 * t] = i;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) t[e] = i0 + e < n ? tiles[i0 + e] : 0u;
+    }
+    uint32_t prev = i0 > 0 ? tiles[i0 - 1] : 0u;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const uint32_t i = i0 + e;
+      if (i < n) {
+        if (i == 0) {
+          ranges[2 * t[e]] = 0;
+        } else if (prev != t[e]) {
+          ranges[2 * prev + 1] = i;
+          ranges[2 * t[e]] = i;
+        }
+        if (i == n - 1) ranges[2 * t[e] + 1] = n;
+        prev = t[e];
       }
     }
-    if (i == n - 1) ranges[2 * t + 1] = n;
   }
 }
 
 inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+size_t radix_tiles(size_t items) { return (items + kTileItems - 1) / kTileItems; }
+
 struct SortWs {
   uint32_t* dkeys[2];   // depth keys, double-buffered [M]
   uint32_t* dvals[2];   // record ids [M]
-  uint32_t* offs;       // instance offset per depth-sorted record [M]
-  unsigned long long* tile_sums;
+  uint32_t* ntd;        // tiles touched, in depth order [M]
+  unsigned long long* block_sums;
   uint32_t* tiles_alt;  // [capacity]
   uint32_t* vals_alt;   // [capacity]
-  uint32_t* hist;
-  uint32_t* totals;
+  uint32_t* ghist;      // [2][kMaxDigits][256]: depth digits, tile digits
+  uint32_t* counters;   // [2][kMaxDigits] tile counters per pass
+  unsigned long long* lb_depth;  // [kMaxDigits][depth tiles][256]
+  unsigned long long* lb_tile;   // [tile passes][instance tiles][256]
   size_t bytes;
 };
 
-SortWs sort_ws_layout(void* base, size_t M, size_t capacity, int nb) {
+SortWs sort_ws_layout(void* base, size_t M, size_t capacity, int tile_passes) {
   SortWs w;
   char* p = (char*)base;
   size_t o = 0;
@@ -413,30 +556,24 @@ SortWs sort_ws_layout(void* base, size_t M, size_t capacity, int nb) {
   };
   for (int i = 0; i < 2; ++i) w.dkeys[i] = (uint32_t*)take(M * 4);
   for (int i = 0; i < 2; ++i) w.dvals[i] = (uint32_t*)take(M * 4);
-  w.offs = (uint32_t*)take(M * 4);
-  w.tile_sums = (unsigned long long*)take(((M + kScanTile - 1) / kScanTile) * 8 + 8);
+  w.ntd = (uint32_t*)take(M * 4);
+  w.block_sums = (unsigned long long*)take(((M + kScanTile - 1) / kScanTile) * 8 + 8);
   w.tiles_alt = (uint32_t*)take(capacity * 4);
   w.vals_alt = (uint32_t*)take(capacity * 4);
-  w.hist = (uint32_t*)take((size_t)256 * nb * 4);
-  w.totals = (uint32_t*)take(256 * 4);
+  w.ghist = (uint32_t*)take(2 * kMaxDigits * 256 * 4);
+  w.counters = (uint32_t*)take(2 * kMaxDigits * 4);
+  w.lb_depth = (unsigned long long*)take(kMaxDigits * radix_tiles(M) * 256 * 8);
+  w.lb_tile = (unsigned long long*)take((size_t)tile_passes * radix_tiles(capacity) * 256 * 8);
   w.bytes = o;
   return w;
 }
 
-int radix_blocks() { return tuning().sort_blocks_per_sm * device_sm_count(); }
-
-// Stable LSD passes over bits [0, bits) of (kA, vA); kA/vA point at the
-// sorted result afterwards.
-void radix_sort_u32(uint32_t*& kA, uint32_t*& vA, uint32_t*& kB, uint32_t*& vB, const uint32_t* n_dev,
-                    uint32_t n_host, size_t capacity, int bits, SortWs& w, int nb, cudaStream_t st) {
-  for (int shift = 0; shift < bits; shift += 8) {
-    radix_hist_kernel<<<nb, kSortThreads, 0, st>>>(kA, n_dev, n_host, capacity, shift, w.hist);
-    radix_scan_kernel<<<256, 1024, 0, st>>>(w.hist, nb, w.totals);
-    radix_scatter_kernel<<<nb, kSortThreads, 0, st>>>(kA, vA, kB, vB, n_dev, n_host, capacity, shift, w.hist,
-                                                       w.totals);
-    std::swap(kA, kB);
-    std::swap(vA, vB);
-  }
+// Grid of a grid-stride kernel: enough blocks for the items, at most
+// sort_blocks_per_sm x 2048 threads per SM.
+int grid_stride_blocks(size_t items, int threads) {
+  const size_t want = (items + threads - 1) / threads;
+  const size_t cap = (size_t)tuning().sort_blocks_per_sm * device_sm_count() * (2048 / threads);
+  return (int)std::max<size_t>(1, std::min(want, cap));
 }
 
 }  // namespace
@@ -448,7 +585,8 @@ int sort_tile_bits(int n_tiles_total) {
 }
 
 size_t sort_workspace_bytes(int N, const gs_batch& batch, size_t capacity) {
-  return sort_ws_layout(nullptr, (size_t)batch.B * N, capacity, radix_blocks()).bytes;
+  const int passes = (sort_tile_bits(batch.n_tiles) + 7) / 8;
+  return sort_ws_layout(nullptr, (size_t)batch.B * N, capacity, passes).bytes;
 }
 
 cudaError_t launch_sort_tiles(int N, const gs_cameras& cams, const gs_batch& batch,
@@ -456,46 +594,70 @@ cudaError_t launch_sort_tiles(int N, const gs_cameras& cams, const gs_batch& bat
                               size_t capacity, uint32_t* ranges, uint32_t* n_instances, void* ws,
                               int32_t* status, cudaStream_t st) {
   const size_t M = (size_t)batch.B * N;
-  const int nb = radix_blocks();
-  SortWs w = sort_ws_layout(ws, M, capacity, nb);
-  cudaError_t e;
-  e = cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)batch.n_tiles, st);
-  if (e != cudaSuccess) return e;
-  const int n_scan_tiles = (int)((M + kScanTile - 1) / kScanTile);
-  if (n_scan_tiles == 0) return cudaMemsetAsync(n_instances, 0, 4, st);
-
-  // 1. stable depth sort of the records (32-bit keys, host-known count)
-  const int grid = (int)std::min<size_t>((M + 255) / 256, (size_t)nb * 8);
-  depth_keys_kernel<<<grid, 256, 0, st>>>(proj, (uint32_t)M, w.dkeys[0], w.dvals[0]);
-  uint32_t *dkA = w.dkeys[0], *dvA = w.dvals[0], *dkB = w.dkeys[1], *dvB = w.dvals[1];
-  radix_sort_u32(dkA, dvA, dkB, dvB, nullptr, (uint32_t)M, M, 32, w, nb, st);
-  const uint32_t* order = dvA;
-
-  // 2. instance offsets in depth order
-  scan_reduce_kernel<<<n_scan_tiles, kScanThreads, 0, st>>>(proj.n_tiles, order, M, w.tile_sums);
-  scan_tiles_kernel<<<1, 1024, 0, st>>>(w.tile_sums, n_scan_tiles, capacity, n_instances, status);
-  scan_apply_kernel<<<n_scan_tiles, kScanThreads, 0, st>>>(proj.n_tiles, order, M, w.tile_sums, w.offs);
-
-  // 3. duplicate into whichever buffer leaves the tile-sorted result in
-  //    tiles/vals, then 4. stable sort by tile id
   const int tbits = sort_tile_bits(batch.n_tiles);
   const int passes = (tbits + 7) / 8;
+  SortWs w = sort_ws_layout(ws, M, capacity, passes);
+  uint32_t* ghist_depth = w.ghist;
+  uint32_t* ghist_tile = w.ghist + kMaxDigits * 256;
+
+  SortZero z{w.ghist, w.counters, w.lb_depth, kMaxDigits * radix_tiles(M) * 256, ranges,
+             2 * (size_t)batch.n_tiles, n_instances};
+  sort_zero_kernel<<<grid_stride_blocks(std::max(z.lb_depth_words, z.ranges_words), 256), 256, 0, st>>>(z);
+  const int n_scan_blocks = (int)((M + kScanTile - 1) / kScanTile);
+  if (n_scan_blocks == 0) return cudaGetLastError();
+
+  // 1. stable depth sort of the records: keys from the projection, values
+  //    = record ids; the last pass writes no keys but gathers n_tiles
+  digit_hist_kernel<<<grid_stride_blocks(M / 4 + 1, 256), 256, 0, st>>>(proj.depth_key, (uint32_t)M, kMaxDigits,
+                                                                         ghist_depth);
+  const int depth_grid = (int)radix_tiles(M);
+  const size_t lbd_stride = radix_tiles(M) * 256;
+  const uint32_t* kin = proj.depth_key;
+  const uint32_t* vin = nullptr;
+  for (int pass = 0; pass < kMaxDigits; ++pass) {
+    const bool last = pass == kMaxDigits - 1;
+    uint32_t* ko = last ? nullptr : w.dkeys[pass & 1];
+    uint32_t* vo = w.dvals[pass & 1];
+    onesweep_kernel<<<depth_grid, kSortThreads, 0, st>>>(
+        kin, vin, ko, vo, nullptr, (uint32_t)M, M, 8 * pass, ghist_depth + 256 * pass,
+        w.lb_depth + lbd_stride * pass, w.counters + pass, last ? proj.n_tiles : nullptr, last ? w.ntd : nullptr,
+        status);
+    kin = ko;
+    vin = vo;
+  }
+  const uint32_t* order = vin;
+
+  // 2. instance offsets in depth order, 3. expand into whichever buffer
+  //    leaves the tile-sorted result in tiles/vals, 4. stable tile sort
+  scan_reduce_kernel<<<n_scan_blocks, kScanThreads, 0, st>>>(w.ntd, M, w.block_sums);
+  scan_blocks_kernel<<<1, 1024, 0, st>>>(w.block_sums, n_scan_blocks, capacity, n_instances, status);
   uint32_t* kA = (passes & 1) ? w.tiles_alt : tiles;
   uint32_t* vA = (passes & 1) ? w.vals_alt : vals;
   uint32_t* kB = (passes & 1) ? tiles : w.tiles_alt;
   uint32_t* vB = (passes & 1) ? vals : w.vals_alt;
-  duplicate_kernel<<<grid, 256, 0, st>>>(proj, order, w.offs, N, cams, batch, kA, vA, capacity, status);
-  radix_sort_u32(kA, vA, kB, vB, n_instances, 0, capacity, tbits, w, nb, st);
+  const size_t lbt_stride = radix_tiles(capacity) * 256;
+  expand_kernel<<<n_scan_blocks, kScanThreads, 0, st>>>(w.ntd, order, M, w.block_sums, proj, N, cams, batch, kA, vA,
+                                                         capacity, n_instances, passes, ghist_tile, w.lb_tile,
+                                                         lbt_stride);
+  const int tile_grid = (int)radix_tiles(capacity);
+  for (int pass = 0; pass < passes; ++pass) {
+    onesweep_kernel<<<tile_grid, kSortThreads, 0, st>>>(kA, vA, kB, vB, n_instances, 0, capacity, 8 * pass,
+                                                         ghist_tile + 256 * pass, w.lb_tile + lbt_stride * pass,
+                                                         w.counters + kMaxDigits + pass, nullptr, nullptr, status);
+    std::swap(kA, kB);
+    std::swap(vA, vB);
+  }
 
   // 5. ranges
-  tile_ranges_kernel<<<nb * 4, 256, 0, st>>>(tiles, n_instances, capacity, ranges);
+  tile_ranges_kernel<<<grid_stride_blocks(capacity / 4 + 1, 256), 256, 0, st>>>(tiles, n_instances, capacity,
+                                                                                 ranges);
   return cudaGetLastError();
 }
 
 int sort_kernel_count(const gs_batch& batch) {
   const int passes = (sort_tile_bits(batch.n_tiles) + 7) / 8;
-  // depth keys 1, depth sort 4 x 3, scan 3, duplicate 1, tile sort 3 / pass, ranges 1
-  return 1 + 4 * 3 + 3 + 1 + 3 * passes + 1;
+  // zero 1, depth histogram 1, depth passes 4, scan 2, expand 1, tile passes, ranges 1
+  return 1 + 1 + kMaxDigits + 2 + 1 + passes + 1;
 }
 
 }  // namespace gs

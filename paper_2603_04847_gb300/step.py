@@ -251,10 +251,10 @@ class JointStep:
         per_render = 0
         for b in self.slot_batches:
             tbits = int(math.ceil(math.log2(b.n_tiles))) if b.n_tiles > 1 else 0
-            # project 1; sort: depth keys 1, depth sort 4 x 3, scan 3,
-            # duplicate 1, tile sort 3 per pass, ranges 1; render fwd 1;
+            # project 1; sort: zero 1, depth histogram 1, depth passes 4,
+            # scan 2, expand 1, one per tile pass, ranges 1; render fwd 1;
             # raster bwd 1; project bwd + finalize 2
-            per_render += 1 + (1 + 12 + 3 + 1 + 3 * ((tbits + 7) // 8) + 1) + 1 + 1 + 2
+            per_render += 1 + (1 + 1 + 4 + 2 + 1 + (tbits + 7) // 8 + 1) + 1 + 1 + 2
         # target gather 1, track + finalize 2, step advance 1, Adam (all
         # groups) 1, pose 1
         return per_render + 1 + 2 + 1 + 1 + 1
