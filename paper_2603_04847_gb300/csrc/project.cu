@@ -9,8 +9,8 @@
 // warp.  The backward recomputes the forward from the parameters (nothing
 // but the screen-space gradients is read back) and keeps the parameter
 // gradients of all views in registers; the per-view pose tangent is
-// reduced warp -> block (shared double) -> per-block partial, and a second
-// kernel sums the partials in a fixed order.
+// reduced warp (FP32 shuffles) -> block (FP32, fixed order) -> per-block
+// double partial, and a second kernel sums the partials in a fixed order.
 #include "gs_internal.h"
 
 namespace gs {
@@ -245,14 +245,16 @@ __global__ void __launch_bounds__(kProjThreads, 3) project_bwd_kernel(gs_gaussia
                                                                       double* __restrict__ partial) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   __shared__ SlotCam sc[GS_MAX_BATCH];
-  __shared__ double s_tan[GS_MAX_BATCH * 6];
+  // per warp and view: the warp's six pose-tangent sums (FP32: the FP64
+  // pipe is a small fraction of the FP32 rate; one conversion per block)
+  __shared__ float s_tan[kProjThreads / 32][GS_MAX_BATCH * 6];
   // dynamic: coefficients and their gradient accumulators, one padded
   // column per thread
   extern __shared__ float s_dyn[];
   float (*s_sh)[kProjThreads + 1] = reinterpret_cast<float (*)[kProjThreads + 1]>(s_dyn);
   float (*s_vsh)[kProjThreads + 1] = reinterpret_cast<float (*)[kProjThreads + 1]>(s_dyn + K * 3 * (kProjThreads + 1));
   load_slot_cams(cams, batch, sc);
-  for (int i = threadIdx.x; i < batch.B * 6; i += blockDim.x) s_tan[i] = 0.0;
+  for (int i = threadIdx.x; i < (kProjThreads / 32) * GS_MAX_BATCH * 6; i += blockDim.x) (&s_tan[0][0])[i] = 0.f;
   const int N = g.n;
   const int j0 = blockIdx.x * kProjThreads;
   const int n_local = min(kProjThreads, N - j0);
@@ -419,20 +421,19 @@ __global__ void __launch_bounds__(kProjThreads, 3) project_bwd_kernel(gs_gaussia
       tan[4] += V.xc[2] * vxc[0] - V.xc[0] * vxc[2];
       tan[5] += V.xc[0] * vxc[1] - V.xc[1] * vxc[0];
     }
-    // warp reduce the 6 tangent values, one shared double add per warp
+    // warp reduce the 6 tangent values into the warp's own slots
     const unsigned any_live = __ballot_sync(0xffffffffu, live);
     if (any_live) {
+      const int lane = threadIdx.x & 31;
+      float mine = 0.f;
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
         float v = tan[i];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        tan[i] = v;
+        if (lane == i) mine = v;
       }
-      if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int i = 0; i < 6; ++i) atomicAdd(&s_tan[6 * b + i], (double)tan[i]);
-      }
+      if (lane < 6) s_tan[threadIdx.x >> 5][6 * b + lane] = mine;
     }
   }
 
@@ -485,8 +486,12 @@ __global__ void __launch_bounds__(kProjThreads, 3) project_bwd_kernel(gs_gaussia
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < batch.B * 6; i += blockDim.x)
-    partial[(size_t)blockIdx.x * batch.B * 6 + i] = s_tan[i];
+  for (int i = threadIdx.x; i < batch.B * 6; i += blockDim.x) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < kProjThreads / 32; ++w) t += s_tan[w][i];
+    partial[(size_t)blockIdx.x * batch.B * 6 + i] = (double)t;
+  }
 }
 
 }  // namespace
