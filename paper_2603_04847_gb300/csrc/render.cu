@@ -130,6 +130,25 @@ __device__ inline float splat_exponent(const float4 q, float Adx, float dx, floa
   return __fmaf_rn(t, dx, s);
 }
 
+// Positions s < min(cnt, limit) of the staged batch whose mask has this
+// warp's bit, in increasing order, into list; returns how many.  Warp-wide.
+template <int kBatch>
+__device__ inline int warp_list(const uint32_t* s_mask, uint32_t wbit, int cnt, int limit, uint8_t* list,
+                                int lane) {
+  const int lim = min(cnt, limit);
+  int n = 0;
+#pragma unroll
+  for (int c = 0; c < kBatch; c += 32) {
+    const int s = c + lane;
+    const bool hit = s < lim && (s_mask[s] & wbit);
+    const unsigned b = __ballot_sync(0xffffffffu, hit);
+    if (hit) list[n + __popc(b & ((1u << lane) - 1u))] = (uint8_t)s;
+    n += __popc(b);
+  }
+  __syncwarp();
+  return n;
+}
+
 template <int kBatch>
 __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
     gs_batch batch, gs_cameras cams, const float4* __restrict__ splat, const uint32_t* __restrict__ vals,
@@ -140,12 +159,14 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
   __shared__ float4 s_q[kBatch];
   __shared__ float4 s_c[kBatch];
   __shared__ uint32_t s_mask[kBatch];
+  __shared__ uint8_t s_list[kThreads / 32][kBatch];
   const int gt = blockIdx.x;
   find_tile(batch, cams, gt, &ti);
   __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int lx, ly;
   tile_pixels(threadIdx.x, lx, ly);
-  const uint32_t wbit = 1u << (threadIdx.x >> 5);
+  const uint32_t wbit = 1u << warp;
   const int u = ti.tx * kTile + lx, v0 = ti.ty * kTile + ly, v1 = v0 + 4;
   const bool in0 = u < ti.W && v0 < ti.H, in1 = u < ti.W && v1 < ti.H;
   const float px = (float)u + 0.5f, py0 = (float)v0 + 0.5f, py1 = (float)v1 + 0.5f;
@@ -155,6 +176,10 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
   float C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
   uint32_t last0 = 0, last1 = 0, add0 = 0, add1 = 0;
   bool done0 = !in0, done1 = !in1;
+  // a finished pixel gets an unreachable threshold, so the per-splat test
+  // is one compare (alpha = min(0.99, alpha_raw) >= 1/255 iff
+  // alpha_raw >= 1/255)
+  float thr0 = done0 ? 2.f : kAlphaMin, thr1 = done1 ? 2.f : kAlphaMin;
   for (uint32_t base = start; base < end; base += kBatch) {
     if (__syncthreads_count(done0 && done1) == kThreads) break;
     for (int s = threadIdx.x; s < kBatch; s += kThreads) {
@@ -163,24 +188,27 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)kBatch, end - base);
-    for (int k = 0; k < cnt; ++k) {
-      if (done0 && done1) break;
-      if (!(s_mask[k] & wbit)) continue;  // uniform across the warp
+    const int n_mine = warp_list<kBatch>(s_mask, wbit, cnt, kBatch, s_list[warp], lane);
+    if (done0 && done1) continue;
+    for (int i = 0; i < n_mine; ++i) {
+      const int k = s_list[warp][i];
       const float2 m = s_m[k];
       const float4 q = s_q[k];
       const float dx = px - m.x;
       const float Adx = __fmul_rn(q.x, dx);
-      const float a0 = fminf(kAlphaMax, ex2_approx(splat_exponent(q, Adx, dx, py0 - m.y)));
-      const float a1 = fminf(kAlphaMax, ex2_approx(splat_exponent(q, Adx, dx, py1 - m.y)));
-      const bool c0 = !done0 && a0 >= kAlphaMin;
-      const bool c1 = !done1 && a1 >= kAlphaMin;
+      const float r0 = ex2_approx(splat_exponent(q, Adx, dx, py0 - m.y));
+      const float r1 = ex2_approx(splat_exponent(q, Adx, dx, py1 - m.y));
+      const bool c0 = r0 >= thr0;
+      const bool c1 = r1 >= thr1;
       if (!(c0 || c1)) continue;
       const float4 c = s_c[k];
       const uint32_t pos1 = base - start + (uint32_t)k + 1u;
       if (c0) {
+        const float a0 = fminf(kAlphaMax, r0);
         const float Tn = T0 * (1.f - a0);
         if (Tn < kTMin) {
           done0 = true;
+          thr0 = 2.f;
         } else {
           const float w = a0 * T0;
           C00 += c.x * w;
@@ -192,9 +220,11 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
         }
       }
       if (c1) {
+        const float a1 = fminf(kAlphaMax, r1);
         const float Tn = T1 * (1.f - a1);
         if (Tn < kTMin) {
           done1 = true;
+          thr1 = 2.f;
         } else {
           const float w = a1 * T1;
           C10 += c.x * w;
@@ -205,6 +235,7 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
           ++add1;
         }
       }
+      if (done0 && done1) break;
     }
   }
   if (in0) {
@@ -331,6 +362,7 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
   __shared__ float4 s_q[kBatch];
   __shared__ float4 s_c[kBatch];
   __shared__ uint32_t s_mask[kBatch];
+  __shared__ uint8_t s_list[kThreads / 32][kBatch];
   __shared__ uint32_t s_rec[kBatch];
   __shared__ float s_g[kBatch][9];
   __shared__ uint32_t s_max;
@@ -382,11 +414,13 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
       for (int i = 0; i < 9; ++i) s_g[s][i] = 0.f;
     }
     __syncthreads();
-    for (int k = cnt - 1; k >= 0; --k) {
+    // this warp's splats: before all its pixels' last contributor and able
+    // to reach its 8x8 block; walked back to front
+    const int n_mine =
+        warp_list<kBatch>(s_mask, wbit, cnt, (int)warp_nc - bstart, s_list[threadIdx.x >> 5], lane);
+    for (int i = n_mine - 1; i >= 0; --i) {
+      const int k = s_list[threadIdx.x >> 5][i];
       const uint32_t pos = (uint32_t)(bstart + k);
-      // uniform across the warp: past all its pixels' last contributor, or
-      // the splat cannot reach its 8x8 block
-      if (pos >= warp_nc || !(s_mask[k] & wbit)) continue;
       const float2 m = s_m[k];
       const float4 q = s_q[k];
       const float dx = px - m.x;
