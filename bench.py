@@ -301,6 +301,34 @@ def stage_times(js, reps, flush):
     return {k: v / reps for k, v in acc.items()}
 
 
+# stage -> committed ncu summary holding that kernel's DRAM bytes per launch
+NCU_SUMMARY = {"raster_bwd": "render_bwd_mid_8x1237x822_200k.md"}
+
+
+def ncu_traffic(stage, workload, js):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch of the stage's
+    kernel, from its committed ncu summary -- only while the kernel source,
+    the workload and the staging batch are those the capture was taken on
+    (else None: the counters no longer describe this kernel)."""
+    import hashlib
+    from paper_2603_04847_gb300.core import gs_get_tuning
+    name = NCU_SUMMARY.get(stage)
+    if name is None:
+        return None
+    try:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            kv = dict(line.strip().split(": ", 1) for line in f if ": " in line and line.startswith("    "))
+        with open(os.path.join(ROOT, kv["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, KeyError, ValueError):
+        return None
+    if sha != kv.get("source_sha256") or workload != kv.get("workload"):
+        return None
+    if str(gs_get_tuning()["render_batch"]) != kv.get("render_batch"):
+        return None
+    return int(kv["traffic_bytes_per_launch"])
+
+
 def algorithmic_model(js):
     """Algorithmic bytes per stage (each intermediate written once and read
     once; the sort as one read + one write of its 12-byte pairs) and the
@@ -440,19 +468,20 @@ def run_ours(args):
     # alpha gradient 15, colour-behind update 6, conic/mean/opacity
     # gradients 30).
     ALU = {"render_fwd": (10.0, 9.0), "raster_bwd": (10.0, 60.0)}
+    traffic = ncu_traffic(dominant, args.workload, js)
     if dominant in ALU:
         per_pos, per_add = ALU[dominant]
         fl = counts["pairs_bwd"] * per_pos + counts["added"] * per_add
         ach = fl / (st_ms[dominant] * 1e-3) / 1e12
         roof = dict(kernel=dominant, bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
-                    traffic=None, peak_source="derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (
+                    traffic=traffic, peak_source="derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (
                         sms, peaks.get("sm_max_mhz", 2070.0)),
                     work="%d examined positions x %.0f + %d composited splats x %.0f flop" % (
                         counts["pairs_bwd"], per_pos, counts["added"], per_add))
     else:
         ach = model[dominant] / (st_ms[dominant] * 1e-3) / 1e9
         roof = dict(kernel=dominant, bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak,
-                    traffic=None, peak_source=peak_src)
+                    traffic=traffic, peak_source=peak_src)
     step_bytes = sum(model.values())
     hbm_step = dict(algorithmic_bytes=step_bytes, GBps=step_bytes / (ms * 1e-3) / 1e9,
                     frac=step_bytes / (ms * 1e-3) / 1e9 / hbm_peak)

@@ -1,6 +1,6 @@
 """Autotuner of the launch parameters (gs_set_tuning): splat records staged
-per round by the compositing kernels, and thread blocks per SM of the radix
-passes.  Every candidate gives the same result (the parameters change only
+per round by the compositing kernels, and the grid (blocks per SM) of the
+sort's grid-stride kernels.  Every candidate gives the same result (the parameters change only
 how work is split); the tuner times the caller's own joint step under each
 and keeps the fastest, cached per (GPU, SM count, workload shape)."""
 from __future__ import annotations
@@ -29,7 +29,8 @@ def _key(js) -> str:
 
 
 def _realloc(js):
-    """Sort workspaces depend on blocks per SM: re-create them."""
+    """Re-create the sort workspaces and drop the captured graph, whose
+    launches carry the old grids."""
     for r in js.renderers:
         r.tl = TileLists(r.n, r.batch, r.tl.capacity, r.image.device)
     js.graph = None
