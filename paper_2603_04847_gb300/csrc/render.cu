@@ -289,11 +289,16 @@ struct PixBwd {
 };
 
 // Backward of one accepted splat at one pixel (alpha_raw = 2^e, alpha its
-// clamp); adds this pixel's screen-space gradients into g:
-// 0 mean2d x, 1 mean2d y, 2 conic a, 3 conic b, 4 conic c, 5 opacity,
-// 6..8 colour.
-__device__ inline void bwd_pixel(PixBwd& P, const float4 q, const float4 c, float dx, float dy, float araw,
-                                 float alpha, float* g) {
+// clamp); adds this pixel's terms into g.  With u = alpha dL/dalpha (so
+// dL/dq = -u/2 for q = a dx^2 + 2 b dx dy + c dy^2, d = pixel - mean) the
+// conic, mean and opacity gradients are linear in the moments
+//   g0 = sum u dx, g1 = sum u dy, g2 = sum u dx^2, g3 = sum u dx dy,
+//   g4 = sum u dy^2, g5 = sum dL/dalpha alpha_raw
+// (pixels where alpha is clamped at 0.99 contribute none), which are
+// accumulated instead and mapped to gradients once per splat
+// (moments_to_grad); g6..8 are the colour gradients.
+__device__ inline void bwd_pixel(PixBwd& P, const float4 c, float dx, float dy, float araw, float alpha,
+                                 float* g) {
   const float ra = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 0.01
   const float Tk = P.T * ra;                      // transmittance before this splat
   const float w = alpha * Tk;
@@ -306,17 +311,27 @@ __device__ inline void bwd_pixel(PixBwd& P, const float4 q, const float4 c, floa
   P.S2 += c.z * w;
   P.T = Tk;
   if (araw < kAlphaMax) {
-    // dalpha/dq = -alpha/2 with q = a dx^2 + 2 b dx dy + c dy^2, d = pixel - mean;
-    // a = -2 ln2 A, b = -ln2 B, c = -2 ln2 C
-    const float vq = -0.5f * alpha * va;
-    const float t = 2.f * kLn2 * vq;
-    g[0] += t * (2.f * q.x * dx + q.y * dy);
-    g[1] += t * (q.y * dx + 2.f * q.z * dy);
-    g[2] += vq * dx * dx;
-    g[3] += 2.f * vq * dx * dy;
-    g[4] += vq * dy * dy;
-    g[5] += va * araw * c.w;  // dalpha/do = exp(-q/2) = alpha_raw / o
+    const float u = alpha * va;
+    const float udx = u * dx, udy = u * dy;
+    g[0] += udx;
+    g[1] += udy;
+    g[2] += udx * dx;
+    g[3] += udx * dy;
+    g[4] += udy * dy;
+    g[5] += va * araw;
   }
+}
+
+// Screen-space gradient record of a splat from its summed moments (see
+// bwd_pixel), with the staged exponent form q = (A, B, C, log2 o), A =
+// -a/(2 ln 2), B = -b/ln 2, C = -c/(2 ln 2), and inv_o = 1/o:
+//   dL/dmean = -dL/dd = sum u (a dx + b dy, b dx + c dy)
+//            = -ln 2 (2A M0 + B M1, B M0 + 2C M1)
+//   dL/da = -M2/2, dL/db = -M3, dL/dc = -M4/2, dL/do = M5 / o.
+__device__ inline void moments_to_grad(const float* M, float4 q, float inv_o, float4& ga, float4& gb) {
+  ga = make_float4(-kLn2 * (2.f * q.x * M[0] + q.y * M[1]), -kLn2 * (q.y * M[0] + 2.f * q.z * M[1]), -0.5f * M[2],
+                   -M[3]);
+  gb = make_float4(-0.5f * M[4], M[5] * inv_o, M[6], M[7]);
 }
 
 __device__ inline void load_pixel(PixBwd& P, bool inside, size_t p, const TileInfo& ti, const float* bg,
@@ -435,7 +450,7 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
         const float alpha = fminf(kAlphaMax, araw);
         if (alpha >= kAlphaMin) {
           contrib = true;
-          bwd_pixel(P0, q, s_c[k], dx, dy, araw, alpha, g);
+          bwd_pixel(P0, s_c[k], dx, dy, araw, alpha, g);
         }
       }
       if (pos < P1.nc) {
@@ -444,7 +459,7 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
         const float alpha = fminf(kAlphaMax, araw);
         if (alpha >= kAlphaMin) {
           contrib = true;
-          bwd_pixel(P1, q, s_c[k], dx, dy, araw, alpha, g);
+          bwd_pixel(P1, s_c[k], dx, dy, araw, alpha, g);
         }
       }
       if (__ballot_sync(0xffffffffu, contrib)) {
@@ -459,11 +474,11 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
     __syncthreads();
     for (int s = threadIdx.x; s < cnt; s += kThreads) {
       const float* sg = s_g[s];
-      const float4 a = make_float4(sg[0], sg[1], sg[2], sg[3]);
-      const float4 b = make_float4(sg[4], sg[5], sg[6], sg[7]);
-      const bool nz = a.x != 0.f || a.y != 0.f || a.z != 0.f || a.w != 0.f || b.x != 0.f || b.y != 0.f ||
-                      b.z != 0.f || b.w != 0.f || sg[8] != 0.f;
+      const bool nz = sg[0] != 0.f || sg[1] != 0.f || sg[2] != 0.f || sg[3] != 0.f || sg[4] != 0.f ||
+                      sg[5] != 0.f || sg[6] != 0.f || sg[7] != 0.f || sg[8] != 0.f;
       if (nz) {
+        float4 a, b;
+        moments_to_grad(sg, s_q[s], s_c[s].w, a, b);
         float4* dst = reinterpret_cast<float4*>(v2d) + 3 * (size_t)s_rec[s];
         atomicAdd(dst, a);
         atomicAdd(dst + 1, b);
