@@ -283,8 +283,11 @@ __device__ inline float warp_sum8_transposed(const float* v, int lane) {
 }
 
 // Per-pixel backward state.
+// The colour composited behind the current splat, S, enters the gradient
+// only through v . S (v = dL/dC is fixed per pixel), so that dot product is
+// carried instead of S.
 struct PixBwd {
-  float T, S0, S1, S2, v0, v1, v2;
+  float T, vS, v0, v1, v2;
   uint32_t nc;
 };
 
@@ -305,10 +308,9 @@ __device__ inline void bwd_pixel(PixBwd& P, const float4 c, float dx, float dy, 
   g[6] += w * P.v0;
   g[7] += w * P.v1;
   g[8] += w * P.v2;
-  const float va = P.v0 * (c.x * Tk - P.S0 * ra) + P.v1 * (c.y * Tk - P.S1 * ra) + P.v2 * (c.z * Tk - P.S2 * ra);
-  P.S0 += c.x * w;
-  P.S1 += c.y * w;
-  P.S2 += c.z * w;
+  const float vc = P.v0 * c.x + P.v1 * c.y + P.v2 * c.z;
+  const float va = vc * Tk - P.vS * ra;  // dL/dalpha = v . (c T_k - S / (1 - alpha))
+  P.vS += vc * w;
   P.T = Tk;
   if (araw < kAlphaMax) {
     const float u = alpha * va;
@@ -339,15 +341,12 @@ __device__ inline void load_pixel(PixBwd& P, bool inside, size_t p, const TileIn
                                   const uint32_t* __restrict__ n_contrib, const float* __restrict__ v_image,
                                   const float* __restrict__ target, float l1_weight, float& lsum) {
   P.T = 1.f;
-  P.S0 = P.S1 = P.S2 = 0.f;
+  P.vS = 0.f;
   P.v0 = P.v1 = P.v2 = 0.f;
   P.nc = 0;
   if (!inside) return;
   P.T = T_final[p];
   P.nc = n_contrib[p];
-  P.S0 = P.T * bg[0];
-  P.S1 = P.T * bg[1];
-  P.S2 = P.T * bg[2];
   if (v_image) {
     P.v0 = v_image[3 * p];
     P.v1 = v_image[3 * p + 1];
@@ -362,6 +361,7 @@ __device__ inline void load_pixel(PixBwd& P, bool inside, size_t p, const TileIn
     P.v2 = d2 > 0.f ? s : (d2 < 0.f ? -s : 0.f);
     lsum += s * (fabsf(d0) + fabsf(d1) + fabsf(d2));
   }
+  P.vS = P.T * (P.v0 * bg[0] + P.v1 * bg[1] + P.v2 * bg[2]);
   if (P.v0 == 0.f && P.v1 == 0.f && P.v2 == 0.f) P.nc = 0;
 }
 
