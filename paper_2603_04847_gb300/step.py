@@ -284,3 +284,76 @@ class JointStep:
         for r in self.renderers:
             f |= int(r.status.item())
         return f
+
+
+class TargetStream:
+    """Feeds a JointStep its target images from pinned host memory, one
+    step ahead, on a copy stream (Algorithm 1, "Sample a batch of views",
+    with the dataset kept on the host).
+
+    Two device copies of the dataset layout alternate: while step i runs and
+    its gather reads copy i % 2, the views of step i + 1 are uploaded into
+    the other copy.  A step waits for its own upload; an upload waits for
+    the step that last read its copy.  Attach before capturing the step's
+    graph (the gather's source pointers change).
+
+        ts = TargetStream(js, host_targets, px_offset)
+        ts.put(views_0)
+        for i in range(n):
+            ts.begin()            # current stream waits for this step's upload
+            js.run()
+            ts.end()
+            ts.put(views_next)    # overlaps the step just enqueued
+    """
+
+    def __init__(self, js: JointStep, host_targets: torch.Tensor, px_offset):
+        if not host_targets.is_pinned():
+            raise ValueError("TargetStream: host_targets must be in pinned memory")
+        dev = js.targets.device
+        self.js = js
+        self.host = host_targets
+        self.off = np.asarray(px_offset, dtype=np.int64)
+        self.P = int(self.off[-1])
+        self.buf = torch.zeros((2 * max(self.P, 1), 3), dtype=torch.float32, device=dev)
+        self.off_host = [torch.as_tensor(self.off + h * self.P).pin_memory() for h in (0, 1)]
+        self.off_dev = torch.as_tensor(self.off, device=dev).clone()
+        self.copy_stream = torch.cuda.Stream(device=dev)
+        self.uploaded = [torch.cuda.Event(), torch.cuda.Event()]
+        self.released = [torch.cuda.Event(), torch.cuda.Event()]
+        self.next_half = 0   # copy the next put() fills
+        self.cur_half = 0    # copy the next begin() uses
+        self.last_bytes = 0
+        js.targets = self.buf
+        js.target_px_offset_dev = self.off_dev
+        js.graph = None
+
+    def put(self, views) -> int:
+        """Enqueues the upload of these views' targets; returns its bytes."""
+        h = self.next_half
+        cs = self.copy_stream
+        cs.wait_event(self.released[h])
+        n = 0
+        with torch.cuda.stream(cs):
+            base = h * self.P
+            for v in np.asarray(views).reshape(-1):
+                a, e = int(self.off[v]), int(self.off[v + 1])
+                self.buf[base + a:base + e].copy_(self.host[a:e], non_blocking=True)
+                n += (e - a) * 12
+        self.uploaded[h].record(cs)
+        self.next_half = 1 - h
+        self.last_bytes = n
+        return n
+
+    def begin(self):
+        """On the current stream: wait for this step's upload and point the
+        gather at its copy (8 (V+1) bytes copied)."""
+        h = self.cur_half
+        st = torch.cuda.current_stream()
+        st.wait_event(self.uploaded[h])
+        self.off_dev.copy_(self.off_host[h], non_blocking=True)
+
+    def end(self):
+        """On the current stream, after the step: its copy may be refilled."""
+        h = self.cur_half
+        self.released[h].record(torch.cuda.current_stream())
+        self.cur_half = 1 - h

@@ -166,6 +166,37 @@ def test_graph_replay_matches_eager_and_plain():
     assert int(eager.step_no.item()) == 3 and int(graphed.step_no.item()) == 3
 
 
+def test_target_stream_matches_device_resident_targets():
+    """Streaming each step's targets from pinned host memory one step ahead
+    (TargetStream: two alternating device copies filled on a copy stream)
+    gives the same training trajectory as targets resident on the device,
+    with the view batch changing every step."""
+    from paper_2603_04847_gb300.step import TargetStream
+    plan = [[4, 1, 3], [0, 2, 4], [1, 0, 2], [3, 4, 0]]
+    ref = _joint("batched")
+    for views in plan:
+        ref.next_batch(views)
+        ref.ensure_capacity()
+        ref.step()
+    torch.cuda.synchronize()
+    js = _joint("batched")
+    host = js.targets.cpu().pin_memory()
+    ts = TargetStream(js, host, js.target_px_offset)
+    ts.put(plan[0])
+    for i, views in enumerate(plan):
+        ts.begin()
+        js.next_batch(views)
+        js.ensure_capacity()
+        js.step()
+        ts.end()
+        if i + 1 < len(plan):
+            ts.put(plan[i + 1])
+    torch.cuda.synchronize()
+    for x, y in zip(_state(ref), _state(js)):
+        np.testing.assert_allclose(y, x, rtol=1e-4, atol=1e-6)
+    assert js.status_flags() == 0
+
+
 def test_every_tuning_candidate_gives_the_same_image_and_lists():
     """The autotuner's candidates change only how work is split: images,
     per-pixel state and sorted lists are bit-identical under all of them."""
