@@ -50,7 +50,7 @@ constexpr unsigned long long kLbAggregate = 1ull << 62;  // this tile's own coun
 constexpr unsigned long long kLbInclusive = 2ull << 62;  // count over tiles 0..t
 constexpr unsigned long long kLbCount = (1ull << 62) - 1;
 constexpr int kSpinLimit = 1 << 20;   // polls of one unpublished word
-constexpr int kLbWindow = 8;          // predecessors read per look-back step
+constexpr int kLbWindow = 4;          // predecessors read per look-back step
 
 __device__ inline void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
