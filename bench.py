@@ -324,7 +324,7 @@ def ncu_traffic(stage, workload, js):
         return None
     if sha != kv.get("source_sha256") or workload != kv.get("workload"):
         return None
-    if str(gs_get_tuning()["render_batch"]) != kv.get("render_batch"):
+    if str(gs_get_tuning()["render_bwd_batch"]) != kv.get("render_bwd_batch"):
         return None
     return int(kv["traffic_bytes_per_launch"])
 
@@ -561,7 +561,8 @@ def run_ours(args):
                     data="synthetic",
                     config=dict(workload_desc(args.workload, w), mode=args.mode,
                                 graph=use_graph, l2="flushed between steps (256 MB write)",
-                                tuning=dict(render_batch=tune["render_batch"],
+                                tuning=dict(render_fwd_batch=tune["render_fwd_batch"],
+                                            render_bwd_batch=tune["render_bwd_batch"],
                                             sort_blocks_per_sm=tune["sort_blocks_per_sm"]),
                                 parallelism="replicas" if ws > 1 else "single GPU"),
                     steps_per_s=1e3 / ms, e2e=e2e, gpu_launches=js.kernels_per_step() * args.steps,

@@ -73,7 +73,7 @@ enum {
                              counts: the tile lists are invalid          */
 };
 
-#define GS_ABI_VERSION 1
+#define GS_ABI_VERSION 2
 #define GS_MAX_BATCH 64   /* views per call */
 
 typedef struct CUstream_st* gs_stream; /* = cudaStream_t */
@@ -152,13 +152,14 @@ typedef struct gs_adam {
 } gs_adam;
 
 /* Launch tuning, process-wide (chosen by an autotuner; results do not
- * depend on it).  render_batch: splat records staged in shared memory per
- * round by the compositing kernels (64, 128 or 256); sort_blocks_per_sm:
- * grid of the sort's grid-stride kernels (histogram, zeroing, ranges), in
- * 2048-thread units per SM (1..8).  Not synchronised: set it while no other
- * thread calls the library. */
+ * depend on it).  render_fwd_batch, render_bwd_batch: splat records staged
+ * in shared memory per round by the compositing forward and backward (64,
+ * 128 or 256 each); sort_blocks_per_sm: grid of the sort's grid-stride
+ * kernels (histogram, zeroing, ranges), in 2048-thread units per SM (1..8).
+ * Not synchronised: set it while no other thread calls the library. */
 typedef struct gs_tuning {
-  int32_t render_batch;
+  int32_t render_fwd_batch;
+  int32_t render_bwd_batch;
   int32_t sort_blocks_per_sm;
 } gs_tuning;
 

@@ -53,7 +53,7 @@ class gs_adam(ctypes.Structure):
 
 
 class gs_tuning(ctypes.Structure):
-    _fields_ = [("render_batch", c_int32), ("sort_blocks_per_sm", c_int32)]
+    _fields_ = [("render_fwd_batch", c_int32), ("render_bwd_batch", c_int32), ("sort_blocks_per_sm", c_int32)]
 
 
 class gs_adam_group(ctypes.Structure):
@@ -126,7 +126,7 @@ def load(path: str = LIB_PATH):
         if lib.gs_struct_size(i) != ctypes.sizeof(s):
             raise GsError("ABI mismatch for %s: C %d vs ctypes %d" % (s.__name__, lib.gs_struct_size(i),
                                                                       ctypes.sizeof(s)))
-    if lib.gs_abi_version() != 1:
+    if lib.gs_abi_version() != 2:
         raise GsError("unexpected libgs ABI version")
     _lib = lib
     return lib

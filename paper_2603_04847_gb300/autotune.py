@@ -1,8 +1,11 @@
 """Autotuner of the launch parameters (gs_set_tuning): splat records staged
-per round by the compositing kernels, and the grid (blocks per SM) of the
-sort's grid-stride kernels.  Every candidate gives the same result (the parameters change only
-how work is split); the tuner times the caller's own joint step under each
-and keeps the fastest, cached per (GPU, SM count, workload shape)."""
+per round by the compositing forward and by its backward, and the grid
+(blocks per SM) of the sort's grid-stride kernels.  Every candidate gives the
+same result (the parameters change only how work is split).  The tuner runs
+the caller's own joint step: the two staging batches are chosen from the
+forward's and the backward's own stage times, then the sort grid from the
+whole step's time; the result is cached per (GPU, SM count, workload
+shape)."""
 from __future__ import annotations
 
 import json
@@ -12,7 +15,11 @@ import torch
 
 from .core import TileLists, gs_get_tuning, gs_set_tuning
 
-CANDIDATES = [(rb, sb) for rb in (64, 128, 256) for sb in (1, 2, 4)]
+RENDER_BATCHES = (64, 128, 256)
+SORT_BLOCKS = (1, 2, 4)
+# (render_fwd_batch, render_bwd_batch, sort_blocks_per_sm) settings the
+# tuner tries; all must give identical results
+CANDIDATES = [(rb, rb, 2) for rb in RENDER_BATCHES] + [(256, 128, sb) for sb in SORT_BLOCKS]
 
 
 def _cache_path():
@@ -36,6 +43,11 @@ def _realloc(js):
     js.graph = None
 
 
+def _median(xs):
+    xs = sorted(xs)
+    return xs[len(xs) // 2]
+
+
 def _time_step(js, reps: int) -> float:
     st = torch.cuda.current_stream()
     js.step()
@@ -47,8 +59,40 @@ def _time_step(js, reps: int) -> float:
         b.record(st)
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))
-    times.sort()
-    return times[len(times) // 2]
+    return _median(times)
+
+
+def _time_stages(js, reps: int, names=("render_fwd", "raster_bwd")) -> dict:
+    """Median device time (ms) of the named stages of the step."""
+    st = torch.cuda.current_stream()
+    js.step()
+    acc = {n: [] for n in names}
+    for _ in range(reps):
+        marks = []
+
+        def mark(name):
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(st)
+            marks.append((name, e))
+
+        first = torch.cuda.Event(enable_timing=True)
+        first.record(st)
+        js.step(mark)
+        torch.cuda.synchronize()
+        tot = {n: 0.0 for n in names}
+        prev = first
+        for name, e in marks:
+            if name in tot:
+                tot[name] += prev.elapsed_time(e)
+            prev = e
+        for n in names:
+            acc[n].append(tot[n])
+    return {n: _median(v) for n, v in acc.items()}
+
+
+def _set(rf, rb, sb, js):
+    gs_set_tuning(rf, rb, sb)
+    _realloc(js)
 
 
 def autotune(js, reps: int = 5, use_cache: bool = True, cache_path: str = None) -> dict:
@@ -65,29 +109,31 @@ def autotune(js, reps: int = 5, use_cache: bool = True, cache_path: str = None) 
             cache = {}
     if use_cache and key in cache:
         t = cache[key]
-        gs_set_tuning(t["render_batch"], t["sort_blocks_per_sm"])
-        _realloc(js)
+        _set(t["render_fwd_batch"], t["render_bwd_batch"], t["sort_blocks_per_sm"], js)
         return dict(t, cached=True)
     timings = {}
-    for rb, sb in CANDIDATES:
-        gs_set_tuning(rb, sb)
-        _realloc(js)
-        timings["%d/%d" % (rb, sb)] = _time_step(js, reps)
-    best = min(timings, key=timings.get)
-    rb, sb = (int(x) for x in best.split("/"))
-    gs_set_tuning(rb, sb)
-    _realloc(js)
-    result = dict(render_batch=rb, sort_blocks_per_sm=sb, ms=timings[best], timings=timings)
+    sb0 = gs_get_tuning()["sort_blocks_per_sm"]
+    stage = {}
+    for rb in RENDER_BATCHES:
+        _set(rb, rb, sb0, js)
+        stage[rb] = _time_stages(js, reps)
+        timings["stages@%d" % rb] = stage[rb]
+    rf = min(RENDER_BATCHES, key=lambda r: stage[r]["render_fwd"])
+    rbw = min(RENDER_BATCHES, key=lambda r: stage[r]["raster_bwd"])
+    step_ms = {}
+    for sb in SORT_BLOCKS:
+        _set(rf, rbw, sb, js)
+        step_ms[sb] = _time_step(js, reps)
+        timings["step@sort%d" % sb] = step_ms[sb]
+    sb = min(SORT_BLOCKS, key=step_ms.get)
+    _set(rf, rbw, sb, js)
+    best = dict(render_fwd_batch=rf, render_bwd_batch=rbw, sort_blocks_per_sm=sb, ms=step_ms[sb])
     if use_cache:
-        cache[key] = dict(render_batch=rb, sort_blocks_per_sm=sb, ms=timings[best])
+        cache[key] = best
         try:
             os.makedirs(os.path.dirname(cache_path), exist_ok=True)
             with open(cache_path, "w") as f:
                 json.dump(cache, f, indent=1)
         except OSError:
             pass
-    return dict(result, cached=False)
-
-
-def current() -> dict:
-    return gs_get_tuning()
+    return dict(best, timings=timings, cached=False)

@@ -333,9 +333,9 @@ def gs_adam_update_groups(groups, beta1, beta2, eps, step, stream=None):
     check(lib.gs_adam_update_groups(arr, len(groups), ctypes.byref(hp), _stream(stream)), "gs_adam_update_groups")
 
 
-def gs_set_tuning(render_batch: int = 256, sort_blocks_per_sm: int = 2):
+def gs_set_tuning(render_fwd_batch: int = 256, render_bwd_batch: int = 128, sort_blocks_per_sm: int = 2):
     lib = _lib.load()
-    t = _lib.gs_tuning(int(render_batch), int(sort_blocks_per_sm))
+    t = _lib.gs_tuning(int(render_fwd_batch), int(render_bwd_batch), int(sort_blocks_per_sm))
     check(lib.gs_set_tuning(ctypes.byref(t)), "gs_set_tuning")
 
 
@@ -343,7 +343,8 @@ def gs_get_tuning():
     lib = _lib.load()
     t = _lib.gs_tuning()
     check(lib.gs_get_tuning(ctypes.byref(t)), "gs_get_tuning")
-    return dict(render_batch=t.render_batch, sort_blocks_per_sm=t.sort_blocks_per_sm)
+    return dict(render_fwd_batch=t.render_fwd_batch, render_bwd_batch=t.render_bwd_batch,
+                sort_blocks_per_sm=t.sort_blocks_per_sm)
 
 
 def gs_step_advance(step, stream=None):

@@ -74,7 +74,7 @@ size_t pose_partial_bytes(int N, const gs_batch& b) {
 }  // namespace
 
 namespace {
-gs_tuning g_tuning = {256, 2};
+gs_tuning g_tuning = {256, 128, 2};
 }
 
 const gs_tuning& tuning() { return g_tuning; }
@@ -119,8 +119,9 @@ int gs_device_sm_count(void) { return device_sm_count(); }
 
 gs_status gs_set_tuning(const gs_tuning* t) {
   if (!t) return fail(GS_ERR_ARG, "gs_set_tuning: null");
-  if (t->render_batch != 64 && t->render_batch != 128 && t->render_batch != 256)
-    return fail(GS_ERR_ARG, "gs_set_tuning: render_batch must be 64, 128 or 256");
+  for (int32_t rb : {t->render_fwd_batch, t->render_bwd_batch})
+    if (rb != 64 && rb != 128 && rb != 256)
+      return fail(GS_ERR_ARG, "gs_set_tuning: render_fwd_batch and render_bwd_batch must be 64, 128 or 256");
   if (t->sort_blocks_per_sm < 1 || t->sort_blocks_per_sm > 8)
     return fail(GS_ERR_ARG, "gs_set_tuning: sort_blocks_per_sm must be 1..8");
   g_tuning = *t;

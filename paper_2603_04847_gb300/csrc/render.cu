@@ -9,22 +9,27 @@
 // one warp reduction covers 64 pixels.
 //
 // Splat records are staged in shared memory kBatch at a time (64, 128 or 256,
-// chosen by the autotuner through gs_set_tuning).  Staging turns
-// each record into the exponent form alpha_raw = 2^e with
+// chosen for the forward and the backward separately by the autotuner
+// through gs_set_tuning).  Staging turns each record into the exponent form
+// alpha_raw = 2^e with
 //   e = A dx^2 + B dx dy + C dy^2 + log2(opacity),
 //   A = -a/(2 ln 2), B = -b/ln 2, C = -c/(2 ln 2)  (conic a, b, c),
 // so that the alpha >= 1/255 test is one compare and one exp2 per pixel, and
 // computes a 4-bit mask of the warps whose 8x8 block the splat's support can
-// reach (a conservative bounding box): a warp skips splats without its bit
-// with one uniform branch.  Forward and backward evaluate alpha with the same
-// function on the same staged values, so they take identical decisions.
+// reach (a conservative bounding box).  Each warp then compacts the staged
+// splats with its bit into a list (ballots) and walks only those.  Forward
+// and backward evaluate alpha with the same function on the same staged
+// values, so they take identical decisions.
 //
 // The backward recomputes compositing back to front from T_final (only
 // T_final and n_contrib are stored per pixel).  All lanes of a warp walk the
-// same splat in lockstep, so its nine screen-space gradients are reduced in
-// registers — a transposing warp reduction (9 shuffles for 8 values + 5 for
-// the ninth) — then added in shared memory by 9 lanes per warp, and written
-// with one vector atomic per splat per tile.
+// same splat in lockstep, so its nine per-splat sums (colour gradients and
+// the moments of the conic/mean/opacity gradients) are reduced in registers
+// — a transposing warp reduction (9 shuffles for 8 values + 5 for the
+// ninth) — then stored by 9 lanes into the warp's own shared-memory slots
+// (kBatch <= 128; with 256 the warps share one slot set through shared
+// atomics), summed over the warps per splat, and written with one vector
+// atomic per splat per tile.
 #include "gs_internal.h"
 
 namespace gs {
@@ -379,7 +384,8 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
   __shared__ uint32_t s_mask[kBatch];
   __shared__ uint8_t s_list[kThreads / 32][kBatch];
   __shared__ uint32_t s_rec[kBatch];
-  __shared__ float s_g[kBatch][9];
+  constexpr int kSlots = kBatch <= 128 ? kThreads / 32 : 1;   // per-warp gradient slots
+  __shared__ float s_g[kSlots][kBatch][9];
   __shared__ uint32_t s_max;
   __shared__ float s_loss[kThreads / 32];
   const int gt = blockIdx.x;
@@ -426,7 +432,9 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
         stage_splat(s, r, splat, x0, y0, s_m, s_q, s_c, s_mask);
       }
 #pragma unroll
-      for (int i = 0; i < 9; ++i) s_g[s][i] = 0.f;
+      for (int w = 0; w < kSlots; ++w)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) s_g[w][s][i] = 0.f;
     }
     __syncthreads();
     // this warp's splats: before all its pixels' last contributor and able
@@ -467,13 +475,26 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
         float s9 = g[8];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s9 += __shfl_xor_sync(0xffffffffu, s9, off);
-        if ((lane & 3) == 0) atomicAdd(&s_g[k][(lane >> 2) & 7], s8);
-        if (lane == 1) atomicAdd(&s_g[k][8], s9);
+        if constexpr (kSlots > 1) {
+          float* dst = s_g[threadIdx.x >> 5][k];
+          if ((lane & 3) == 0) dst[(lane >> 2) & 7] = s8;
+          if (lane == 1) dst[8] = s9;
+        } else {
+          if ((lane & 3) == 0) atomicAdd(&s_g[0][k][(lane >> 2) & 7], s8);
+          if (lane == 1) atomicAdd(&s_g[0][k][8], s9);
+        }
       }
     }
     __syncthreads();
     for (int s = threadIdx.x; s < cnt; s += kThreads) {
-      const float* sg = s_g[s];
+      float sg[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        float acc = 0.f;
+#pragma unroll
+        for (int w = 0; w < kSlots; ++w) acc += s_g[w][s][i];
+        sg[i] = acc;
+      }
       const bool nz = sg[0] != 0.f || sg[1] != 0.f || sg[2] != 0.f || sg[3] != 0.f || sg[4] != 0.f ||
                       sg[5] != 0.f || sg[6] != 0.f || sg[7] != 0.f || sg[8] != 0.f;
       if (nz) {
@@ -497,7 +518,7 @@ cudaError_t launch_render_fwd(const gs_batch& batch, const gs_cameras& cams, con
                               cudaStream_t st) {
   if (batch.n_tiles == 0) return cudaSuccess;
   const float4* sp = reinterpret_cast<const float4*>(proj.splat);
-  switch (tuning().render_batch) {
+  switch (tuning().render_fwd_batch) {
     case 64:
       render_fwd_kernel<64><<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, sp, vals, ranges, bg, image, T_final,
                                                                 n_contrib, n_added);
@@ -521,7 +542,7 @@ cudaError_t launch_render_bwd(const gs_batch& batch, const gs_cameras& cams, con
                               double* loss, float* v2d, cudaStream_t st) {
   if (batch.n_tiles == 0) return cudaSuccess;
   const float4* sp = reinterpret_cast<const float4*>(proj.splat);
-  switch (tuning().render_batch) {
+  switch (tuning().render_bwd_batch) {
     case 64:
       render_bwd_kernel<64><<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, sp, vals, ranges, bg, image, T_final,
                                                                 n_contrib, v_image, target, l1_weight, loss, v2d);

@@ -206,8 +206,8 @@ def test_every_tuning_candidate_gives_the_same_image_and_lists():
     saved = gs_get_tuning()
     ref = None
     try:
-        for rb, sb in CANDIDATES:
-            gs_set_tuning(rb, sb)
+        for rf, rb, sb in CANDIDATES:
+            gs_set_tuning(rf, rb, sb)
             r, *_ = gpu_forward(w["scene"], w["wh"], w["K"], w["Rt"], [0, 1, 2])
             n = r.n_instances()
             out = [r.image.cpu().numpy(), r.T_final.cpu().numpy(), r.n_contrib.cpu().numpy(),
@@ -218,7 +218,7 @@ def test_every_tuning_candidate_gives_the_same_image_and_lists():
                 for a, b in zip(out, ref):
                     np.testing.assert_array_equal(a, b)
     finally:
-        gs_set_tuning(saved["render_batch"], saved["sort_blocks_per_sm"])
+        gs_set_tuning(saved["render_fwd_batch"], saved["render_bwd_batch"], saved["sort_blocks_per_sm"])
 
 
 def test_adam_groups_match_oracle():
