@@ -43,11 +43,15 @@ class Renderer:
                                   device=device)
         self.status = new_status(device)
 
-    def forward(self, g: Gaussians, Rt: torch.Tensor = None, mark=_nomark):
+    def forward(self, g: Gaussians, Rt: torch.Tensor = None, mark=_nomark, after_sort=None):
+        """Projection, tile sort, compositing; `after_sort()` (if given) is
+        called between the sort and the compositing."""
         gs_project(g, self.cams, self.batch, self.proj, self.status, Rt)
         mark("project")
         gs_sort_tiles(self.n, self.cams, self.batch, self.proj, self.tl, self.status, Rt)
         mark("sort")
+        if after_sort is not None:
+            after_sort()
         gs_render_fwd(self.batch, self.cams, self.proj, self.tl, self.bg, self.image, self.T_final,
                       self.n_contrib, Rt)
         mark("render_fwd")
@@ -204,29 +208,51 @@ class JointStep:
             self.graph = None
         return grew
 
+    def _side_stream(self) -> torch.cuda.Stream:
+        if getattr(self, "_side", None) is None:
+            self._side = torch.cuda.Stream(device=self.device)
+        return self._side
+
     # -- the step ----------------------------------------------------------
     def _adam(self, p, g, m, v, lr):
         gs_adam_update(p, g, m, v, adam_c(lr, self.h.beta1, self.h.beta2, self.h.eps, self.step_no))
 
     def step(self, mark=_nomark):
         """One training iteration; `mark(name)` is called after each stage
-        (for event timing)."""
+        (for event timing).  The gradient zeroing and the target gather run
+        on a side stream, forked after the first view's sort so that these
+        memory-bound copies overlap the compute-bound compositing rather
+        than the memory-bound projection, and joined before the first
+        backward."""
         h = self.h
-        for t in self.dg.tensors() + [self.gX, self.g_tan, self.loss, self.n_masked]:
-            gs_zero(t)
-        gs_gather_view_pixels(self.targets, self.target_px_offset_dev, self.cams, self.batch, self.target_batch)
-        mark("zero")
-        if self.mode == "batched":
-            r = self.renderers[0]
-            r.forward(self.g, self.Rt, mark)
-            r.backward(self.g, self.dg, self.g_tan, target=self.target_batch, l1_weight=h.l1_weight,
-                       loss=self.loss[0:1], Rt=self.Rt, mark=mark)
-        else:
-            for b, r in enumerate(self.renderers):
+        main = torch.cuda.current_stream()
+        side = self._side_stream()
+
+        def fork():
+            side.wait_stream(main)
+            with torch.cuda.stream(side):
+                for t in self.dg.tensors() + [self.gX, self.g_tan, self.loss, self.n_masked]:
+                    gs_zero(t)
+                gs_gather_view_pixels(self.targets, self.target_px_offset_dev, self.cams, self.batch,
+                                      self.target_batch)
+
+        joined = False
+        for b, r in enumerate(self.renderers):
+            r.forward(self.g, self.Rt, mark, after_sort=fork if b == 0 else None)
+            if not joined:
+                main.wait_stream(side)
+                joined = True
+            if self.mode == "batched":
+                tgt = self.target_batch
+            else:
                 a, e = int(self.batch.px_offset_host[b]), int(self.batch.px_offset_host[b + 1])
-                r.forward(self.g, self.Rt, mark)
-                r.backward(self.g, self.dg, self.g_tan, target=self.target_batch[a:e], l1_weight=h.l1_weight,
-                           loss=self.loss[0:1], Rt=self.Rt, mark=mark)
+                tgt = self.target_batch[a:e]
+            r.backward(self.g, self.dg, self.g_tan, target=tgt, l1_weight=h.l1_weight, loss=self.loss[0:1],
+                       Rt=self.Rt, mark=mark)
+        if not joined:
+            fork()
+            main.wait_stream(side)
+        mark("zero")
         track_reproj_fwd_bwd(self.X, self.obs_point, self.obs_xy, self.view_obs_offset, self.cams, self.batch,
                              h.huber_delta, h.lambda_ba, self.loss[1:2], self.gX, self.g_tan, self.n_masked,
                              self.track_ws, self.Rt)
