@@ -209,8 +209,10 @@ class JointStep:
         return grew
 
     def _side_stream(self) -> torch.cuda.Stream:
+        # high priority: its few short kernels get SM slots as soon as the
+        # compositing grid frees any, instead of queueing behind all of it
         if getattr(self, "_side", None) is None:
-            self._side = torch.cuda.Stream(device=self.device)
+            self._side = torch.cuda.Stream(device=self.device, priority=-1)
         return self._side
 
     # -- the step ----------------------------------------------------------
@@ -219,11 +221,10 @@ class JointStep:
 
     def step(self, mark=_nomark):
         """One training iteration; `mark(name)` is called after each stage
-        (for event timing).  The gradient zeroing and the target gather run
-        on a side stream, forked after the first view's sort so that these
-        memory-bound copies overlap the compute-bound compositing rather
-        than the memory-bound projection, and joined before the first
-        backward."""
+        (for event timing).  The gradient zeroing, the target gather and the
+        track term run on a side stream, forked after the first view's sort
+        so that they overlap the compute-bound compositing rather than the
+        memory-bound projection, and joined before the first backward."""
         h = self.h
         main = torch.cuda.current_stream()
         side = self._side_stream()
@@ -235,6 +236,11 @@ class JointStep:
                     gs_zero(t)
                 gs_gather_view_pixels(self.targets, self.target_px_offset_dev, self.cams, self.batch,
                                       self.target_batch)
+                # the track term: done before the join, so its += into the
+                # pose tangent precedes the projection backward's
+                track_reproj_fwd_bwd(self.X, self.obs_point, self.obs_xy, self.view_obs_offset, self.cams,
+                                     self.batch, h.huber_delta, h.lambda_ba, self.loss[1:2], self.gX, self.g_tan,
+                                     self.n_masked, self.track_ws, self.Rt)
 
         joined = False
         for b, r in enumerate(self.renderers):
@@ -253,9 +259,6 @@ class JointStep:
             fork()
             main.wait_stream(side)
         mark("zero")
-        track_reproj_fwd_bwd(self.X, self.obs_point, self.obs_xy, self.view_obs_offset, self.cams, self.batch,
-                             h.huber_delta, h.lambda_ba, self.loss[1:2], self.gX, self.g_tan, self.n_masked,
-                             self.track_ws, self.Rt)
         mark("track")
         gs_step_advance(self.step_no)
         ext = h.scene_extent
