@@ -245,10 +245,25 @@ def gpu_inputs(name, device):
                 targets=targets, off=off)
 
 
-def make_step(inp, views, mode, lambda_ba):
+def tuning_trials(tune):
+    """Best eager step time (ms) the autotuner measured per tile size, and
+    per tile size the forward/backward stage times per staging batch."""
+    t = tune.get("timings", {})
+    out = {}
+    for k, v in t.items():
+        tile, what = k.split("/", 1)
+        d = out.setdefault(tile, {})
+        if what.startswith("step@"):
+            d["step_ms"] = min(d.get("step_ms", float("inf")), v)
+        else:
+            d[what.replace("stages@", "batch")] = {n: round(x, 4) for n, x in v.items()}
+    return out
+
+
+def make_step(inp, views, mode, lambda_ba, tile=16):
     from paper_2603_04847_gb300 import Hyper, JointStep
     js = JointStep(inp["g"], inp["cams"], inp["X"], inp["obs_point"], inp["obs_xy"], inp["view_obs_offset"],
-                   inp["targets"], inp["off"], views, Hyper(lambda_ba=lambda_ba), mode=mode)
+                   inp["targets"], inp["off"], views, Hyper(lambda_ba=lambda_ba), mode=mode, tile=tile)
     js.ensure_capacity()
     return js
 
@@ -324,7 +339,7 @@ def ncu_traffic(stage, workload, js):
         return None
     if sha != kv.get("source_sha256") or workload != kv.get("workload"):
         return None
-    if str(gs_get_tuning()["render_bwd_batch"]) != kv.get("render_bwd_batch"):
+    if str(gs_get_tuning()["render_bwd_batch"]) != kv.get("render_bwd_batch") or str(js.tile) != kv.get("tile"):
         return None
     return int(kv["traffic_bytes_per_launch"])
 
@@ -497,7 +512,7 @@ def run_ours(args):
     # plain one-view-per-launch form on the same inputs (eager, no graph)
     plain = None
     if not args.no_plain and args.mode == "batched":
-        jp = make_step(inp, views, "plain", W.lambda_ba)
+        jp = make_step(inp, views, "plain", W.lambda_ba, tile=js.tile)
         for _ in range(2):
             flush.zero_()
             jp.step()
@@ -561,9 +576,10 @@ def run_ours(args):
                     data="synthetic",
                     config=dict(workload_desc(args.workload, w), mode=args.mode,
                                 graph=use_graph, l2="flushed between steps (256 MB write)",
-                                tuning=dict(render_fwd_batch=tune["render_fwd_batch"],
+                                tuning=dict(tile=tune["tile"], render_fwd_batch=tune["render_fwd_batch"],
                                             render_bwd_batch=tune["render_bwd_batch"],
-                                            sort_blocks_per_sm=tune["sort_blocks_per_sm"]),
+                                            sort_blocks_per_sm=tune["sort_blocks_per_sm"],
+                                            trials=tuning_trials(tune)),
                                 parallelism="replicas" if ws > 1 else "single GPU"),
                     steps_per_s=1e3 / ms, e2e=e2e, gpu_launches=js.kernels_per_step() * args.steps,
                     roofline=roof, hbm_step=hbm_step, stages=stages, counts=counts, clocks=clk,

@@ -1,10 +1,12 @@
-"""Autotuner of the launch parameters (gs_set_tuning): splat records staged
-per round by the compositing forward and by its backward, and the grid
-(blocks per SM) of the sort's grid-stride kernels.  Every candidate gives the
-same result (the parameters change only how work is split).  The tuner runs
-the caller's own joint step: the two staging batches are chosen from the
-forward's and the backward's own stage times, then the sort grid from the
-whole step's time; the result is cached per (GPU, SM count, workload
+"""Autotuner of the launch parameters: the tile size (16 or 32 pixels, a
+property of the step's batch), and through gs_set_tuning the splat records
+staged per round by the compositing forward and by its backward, and the
+grid (blocks per SM) of the sort's grid-stride kernels.  Every candidate
+gives the same images and gradients (the parameters change only how work is
+split).  The tuner runs the caller's own joint step: per tile size, the two
+staging batches are chosen from the forward's and the backward's own stage
+times, then the sort grid from the whole step's time; the tile size with the
+fastest step wins.  The result is cached per (GPU, SM count, workload
 shape)."""
 from __future__ import annotations
 
@@ -15,6 +17,7 @@ import torch
 
 from .core import TileLists, gs_get_tuning, gs_set_tuning
 
+TILES = (16, 32)
 RENDER_BATCHES = (64, 128, 256)
 SORT_BLOCKS = (1, 2, 4)
 # (render_fwd_batch, render_bwd_batch, sort_blocks_per_sm) settings the
@@ -30,9 +33,8 @@ def _cache_path():
 def _key(js) -> str:
     p = torch.cuda.get_device_properties(torch.cuda.current_device())
     g = js.g
-    return "%s|%d|N=%d|K=%d|B=%d|P=%d|tiles=%d|%s" % (
-        p.name, p.multi_processor_count, g.n, g.sh.shape[1], js.batch.B, js.batch.n_pixels, js.batch.n_tiles,
-        js.mode)
+    return "%s|%d|N=%d|K=%d|B=%d|P=%d|%s" % (
+        p.name, p.multi_processor_count, g.n, g.sh.shape[1], js.batch.B, js.batch.n_pixels, js.mode)
 
 
 def _realloc(js):
@@ -109,25 +111,35 @@ def autotune(js, reps: int = 5, use_cache: bool = True, cache_path: str = None) 
             cache = {}
     if use_cache and key in cache:
         t = cache[key]
+        js.set_tile(t["tile"])
         _set(t["render_fwd_batch"], t["render_bwd_batch"], t["sort_blocks_per_sm"], js)
+        js.ensure_capacity()
         return dict(t, cached=True)
     timings = {}
     sb0 = gs_get_tuning()["sort_blocks_per_sm"]
-    stage = {}
-    for rb in RENDER_BATCHES:
-        _set(rb, rb, sb0, js)
-        stage[rb] = _time_stages(js, reps)
-        timings["stages@%d" % rb] = stage[rb]
-    rf = min(RENDER_BATCHES, key=lambda r: stage[r]["render_fwd"])
-    rbw = min(RENDER_BATCHES, key=lambda r: stage[r]["raster_bwd"])
-    step_ms = {}
-    for sb in SORT_BLOCKS:
-        _set(rf, rbw, sb, js)
-        step_ms[sb] = _time_step(js, reps)
-        timings["step@sort%d" % sb] = step_ms[sb]
-    sb = min(SORT_BLOCKS, key=step_ms.get)
-    _set(rf, rbw, sb, js)
-    best = dict(render_fwd_batch=rf, render_bwd_batch=rbw, sort_blocks_per_sm=sb, ms=step_ms[sb])
+    per_tile = {}
+    for tile in TILES:
+        js.set_tile(tile)
+        js.ensure_capacity()
+        stage = {}
+        for rb in RENDER_BATCHES:
+            _set(rb, rb, sb0, js)
+            stage[rb] = _time_stages(js, reps)
+            timings["tile%d/stages@%d" % (tile, rb)] = stage[rb]
+        rf = min(RENDER_BATCHES, key=lambda r: stage[r]["render_fwd"])
+        rbw = min(RENDER_BATCHES, key=lambda r: stage[r]["raster_bwd"])
+        step_ms = {}
+        for sb in SORT_BLOCKS:
+            _set(rf, rbw, sb, js)
+            step_ms[sb] = _time_step(js, reps)
+            timings["tile%d/step@sort%d" % (tile, sb)] = step_ms[sb]
+        sb = min(SORT_BLOCKS, key=step_ms.get)
+        per_tile[tile] = dict(tile=tile, render_fwd_batch=rf, render_bwd_batch=rbw, sort_blocks_per_sm=sb,
+                              ms=step_ms[sb])
+    best = min(per_tile.values(), key=lambda t: t["ms"])
+    js.set_tile(best["tile"])
+    _set(best["render_fwd_batch"], best["render_bwd_batch"], best["sort_blocks_per_sm"], js)
+    js.ensure_capacity()
     if use_cache:
         cache[key] = best
         try:

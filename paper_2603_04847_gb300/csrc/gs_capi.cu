@@ -50,7 +50,7 @@ gs_status check_cameras(const gs_cameras* c) {
 gs_status check_batch(const gs_batch* b) {
   if (!b) return fail(GS_ERR_ARG, "batch: null");
   if (b->B < 1 || b->B > GS_MAX_BATCH) return fail(GS_ERR_ARG, "batch: B must be 1..%d", GS_MAX_BATCH);
-  if (b->tile != 16) return fail(GS_ERR_UNSUPPORTED, "batch: tile %d unsupported (16)", b->tile);
+  if (b->tile != 16 && b->tile != 32) return fail(GS_ERR_UNSUPPORTED, "batch: tile %d unsupported (16 or 32)", b->tile);
   if (!b->views || !b->px_offset || !b->tile_offset) return fail(GS_ERR_ARG, "batch: null array");
   if (b->n_pixels < 0 || b->n_tiles < 0) return fail(GS_ERR_ARG, "batch: negative sizes");
   return GS_OK;

@@ -2,8 +2,10 @@
 // (Algorithm 1 "Rasterize"), and its backward pass with the L1 term of Eq. 5
 // fused in.
 //
-// One thread block of 128 threads per 16x16 tile of any view in the batch.
-// Each warp owns an 8x8 block of the tile and each thread two pixels of it,
+// One thread block per tile of any view in the batch (16x16 tiles: 128
+// threads; 32x32 tiles: 512 threads; the batch's tile size is chosen by the
+// autotuner).  Each warp owns an 8x8 block of the tile and each thread two
+// pixels of it,
 // (x, y) and (x, y + 4): the per-splat shared-memory loads, the cull test
 // and the loop overhead are paid once per two pixels, and in the backward
 // one warp reduction covers 64 pixels.
@@ -36,8 +38,15 @@ namespace gs {
 
 namespace {
 
-constexpr int kTile = 16;
-constexpr int kThreads = 128;  // 2 pixels per thread
+// Tile shapes: kTile x kTile pixels per block, two pixels per thread, an
+// 8x8 pixel block per warp.
+template <int kTile>
+struct Shape {
+  static constexpr int kThreads = kTile * kTile / 2;
+  static constexpr int kWarps = kThreads / 32;
+  static constexpr int kWarpsX = kTile / 8;
+  static_assert(kWarps <= 32, "one mask bit per warp");
+};
 constexpr float kLn2 = 0.69314718055994531f;
 constexpr float kHalfLog2e = 0.72134752044448170f;  // 1 / (2 ln 2)
 
@@ -49,6 +58,7 @@ struct TileInfo {
   float inv_norm;  // 1 / (3 W H) for the per-view L1 mean
 };
 
+template <int kTile>
 __device__ inline void find_tile(const gs_batch& batch, const gs_cameras& cams, int gt, TileInfo* ti) {
   if (threadIdx.x == 0) {
     int lo = 0, hi = batch.B - 1;
@@ -72,13 +82,15 @@ __device__ inline void find_tile(const gs_batch& batch, const gs_cameras& cams, 
   }
 }
 
-// Pixels of thread `tid` in its 16x16 tile: warp w covers the 8x8 block at
-// ((w & 1) * 8, (w >> 1) * 8); lane l the pixels (l & 7, l >> 3) and
-// (l & 7, (l >> 3) + 4) in it.
+// Pixels of thread `tid` in its tile: warp w covers the 8x8 block at
+// ((w % kWarpsX) * 8, (w / kWarpsX) * 8); lane l the pixels (l & 7, l >> 3)
+// and (l & 7, (l >> 3) + 4) in it.
+template <int kTile>
 __device__ inline void tile_pixels(int tid, int& lx, int& ly) {
+  constexpr int kWX = Shape<kTile>::kWarpsX;
   const int w = tid >> 5, l = tid & 31;
-  lx = (w & 1) * 8 + (l & 7);
-  ly = (w >> 1) * 8 + (l >> 3);
+  lx = (w % kWX) * 8 + (l & 7);
+  ly = (w / kWX) * 8 + (l >> 3);
 }
 
 // Bit w set iff the bounding box of the splat's support {q <= q_max} can
@@ -86,15 +98,17 @@ __device__ inline void tile_pixels(int tid, int& lx, int& ly) {
 // The box is widened by 2 % + 0.01 in q and 0.01 px: the FP32 evaluation of
 // alpha for strongly anisotropic conics carries relative errors of that
 // order, so no pixel whose alpha can pass the test is ever skipped.
+template <int kTile>
 __device__ inline uint32_t warp_mask(const float4 xyo, const float4 con, float x0, float y0) {
+  constexpr int kWX = Shape<kTile>::kWarpsX;
   const float detc = con.x * con.z - con.y * con.y;
   const float qc = (con.w + 1e-3f) * 1.02f + 0.01f;
   const float rx = sqrtf(qc * con.z / detc) + 0.01f;
   const float ry = sqrtf(qc * con.x / detc) + 0.01f;
   uint32_t m = 0;
 #pragma unroll
-  for (int w = 0; w < 4; ++w) {
-    const float bx0 = x0 + (float)((w & 1) * 8) + 0.5f, by0 = y0 + (float)((w >> 1) * 8) + 0.5f;
+  for (int w = 0; w < Shape<kTile>::kWarps; ++w) {
+    const float bx0 = x0 + (float)((w % kWX) * 8) + 0.5f, by0 = y0 + (float)((w / kWX) * 8) + 0.5f;
     const bool hit = (xyo.x + rx >= bx0) && (xyo.x - rx <= bx0 + 7.f) && (xyo.y + ry >= by0) &&
                      (xyo.y - ry <= by0 + 7.f);
     m |= hit ? (1u << w) : 0u;
@@ -115,6 +129,7 @@ __device__ inline float lg2_approx(float x) {
 }
 
 // Stages record r into slot `s` of the shared arrays.
+template <int kTile>
 __device__ inline void stage_splat(int s, uint32_t r, const float4* __restrict__ splat, float x0, float y0,
                                    float2* s_m, float4* s_q, float4* s_c, uint32_t* s_mask) {
   const float4 xyo = splat[3 * (size_t)r];
@@ -123,7 +138,7 @@ __device__ inline void stage_splat(int s, uint32_t r, const float4* __restrict__
   s_m[s] = make_float2(xyo.x, xyo.y);
   s_q[s] = make_float4(-kHalfLog2e * con.x, -2.f * kHalfLog2e * con.y, -kHalfLog2e * con.z, lg2_approx(xyo.z));
   s_c[s] = make_float4(col.x, col.y, col.z, 1.f / xyo.z);
-  s_mask[s] = warp_mask(xyo, con, x0, y0);
+  s_mask[s] = warp_mask<kTile>(xyo, con, x0, y0);
 }
 
 // Exponent e of alpha_raw = 2^e at offset (dx, dy), given Adx = A * dx.
@@ -154,11 +169,12 @@ __device__ inline int warp_list(const uint32_t* s_mask, uint32_t wbit, int cnt, 
   return n;
 }
 
-template <int kBatch>
-__global__ void __launch_bounds__(kThreads) render_fwd_kernel(
+template <int kTile, int kBatch>
+__global__ void __launch_bounds__(Shape<kTile>::kThreads) render_fwd_kernel(
     gs_batch batch, gs_cameras cams, const float4* __restrict__ splat, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ ranges, const float* __restrict__ bg, float* __restrict__ image,
     float* __restrict__ T_final, uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ n_added) {
+  constexpr int kThreads = Shape<kTile>::kThreads;
   __shared__ TileInfo ti;
   __shared__ float2 s_m[kBatch];
   __shared__ float4 s_q[kBatch];
@@ -166,11 +182,11 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
   __shared__ uint32_t s_mask[kBatch];
   __shared__ uint8_t s_list[kThreads / 32][kBatch];
   const int gt = blockIdx.x;
-  find_tile(batch, cams, gt, &ti);
+  find_tile<kTile>(batch, cams, gt, &ti);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int lx, ly;
-  tile_pixels(threadIdx.x, lx, ly);
+  tile_pixels<kTile>(threadIdx.x, lx, ly);
   const uint32_t wbit = 1u << warp;
   const int u = ti.tx * kTile + lx, v0 = ti.ty * kTile + ly, v1 = v0 + 4;
   const bool in0 = u < ti.W && v0 < ti.H, in1 = u < ti.W && v1 < ti.H;
@@ -189,7 +205,7 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(
     if (__syncthreads_count(done0 && done1) == kThreads) break;
     for (int s = threadIdx.x; s < kBatch; s += kThreads) {
       const uint32_t idx = base + s;
-      if (idx < end) stage_splat(s, vals[idx], splat, x0, y0, s_m, s_q, s_c, s_mask);
+      if (idx < end) stage_splat<kTile>(s, vals[idx], splat, x0, y0, s_m, s_q, s_c, s_mask);
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)kBatch, end - base);
@@ -370,13 +386,14 @@ __device__ inline void load_pixel(PixBwd& P, bool inside, size_t p, const TileIn
   if (P.v0 == 0.f && P.v1 == 0.f && P.v2 == 0.f) P.nc = 0;
 }
 
-template <int kBatch>
-__global__ void __launch_bounds__(kThreads) render_bwd_kernel(
+template <int kTile, int kBatch>
+__global__ void __launch_bounds__(Shape<kTile>::kThreads) render_bwd_kernel(
     gs_batch batch, gs_cameras cams, const float4* __restrict__ splat, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ ranges, const float* __restrict__ bg, const float* __restrict__ image,
     const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
     const float* __restrict__ v_image, const float* __restrict__ target, float l1_weight, double* loss,
     float* __restrict__ v2d) {
+  constexpr int kThreads = Shape<kTile>::kThreads;
   __shared__ TileInfo ti;
   __shared__ float2 s_m[kBatch];
   __shared__ float4 s_q[kBatch];
@@ -384,17 +401,20 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
   __shared__ uint32_t s_mask[kBatch];
   __shared__ uint8_t s_list[kThreads / 32][kBatch];
   __shared__ uint32_t s_rec[kBatch];
-  constexpr int kSlots = kBatch <= 128 ? kThreads / 32 : 1;   // per-warp gradient slots
+  // per-warp gradient slots where they fit in shared memory, else one set
+  // shared by the warps through shared atomics
+  constexpr int kW = Shape<kTile>::kWarps;
+  constexpr int kSlots = kBatch * (48 + 37 * kW) <= 45000 ? kW : 1;
   __shared__ float s_g[kSlots][kBatch][9];
   __shared__ uint32_t s_max;
   __shared__ float s_loss[kThreads / 32];
   const int gt = blockIdx.x;
   if (threadIdx.x == 0) s_max = 0;
-  find_tile(batch, cams, gt, &ti);
+  find_tile<kTile>(batch, cams, gt, &ti);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   int lx, ly;
-  tile_pixels(threadIdx.x, lx, ly);
+  tile_pixels<kTile>(threadIdx.x, lx, ly);
   const uint32_t wbit = 1u << (threadIdx.x >> 5);
   const int u = ti.tx * kTile + lx, v0 = ti.ty * kTile + ly, v1 = v0 + 4;
   const bool in0 = u < ti.W && v0 < ti.H, in1 = u < ti.W && v1 < ti.H;
@@ -429,7 +449,7 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
       if (s < cnt) {
         const uint32_t r = vals[start + bstart + s];
         s_rec[s] = r;
-        stage_splat(s, r, splat, x0, y0, s_m, s_q, s_c, s_mask);
+        stage_splat<kTile>(s, r, splat, x0, y0, s_m, s_q, s_c, s_mask);
       }
 #pragma unroll
       for (int w = 0; w < kSlots; ++w)
@@ -512,26 +532,66 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
 
 }  // namespace
 
+namespace {
+
+template <int kTile, int kBatch>
+void render_fwd_launch(const gs_batch& batch, const gs_cameras& cams, const float4* sp, const uint32_t* vals,
+                       const uint32_t* ranges, const float* bg, float* image, float* T_final,
+                       uint32_t* n_contrib, uint32_t* n_added, cudaStream_t st) {
+  render_fwd_kernel<kTile, kBatch><<<batch.n_tiles, Shape<kTile>::kThreads, 0, st>>>(
+      batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, n_added);
+}
+
+template <int kTile>
+void render_fwd_tile(int rb, const gs_batch& batch, const gs_cameras& cams, const float4* sp,
+                     const uint32_t* vals, const uint32_t* ranges, const float* bg, float* image, float* T_final,
+                     uint32_t* n_contrib, uint32_t* n_added, cudaStream_t st) {
+  if (rb == 64)
+    render_fwd_launch<kTile, 64>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, n_added, st);
+  else if (rb == 128)
+    render_fwd_launch<kTile, 128>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, n_added, st);
+  else
+    render_fwd_launch<kTile, 256>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, n_added, st);
+}
+
+template <int kTile, int kBatch>
+void render_bwd_launch(const gs_batch& batch, const gs_cameras& cams, const float4* sp, const uint32_t* vals,
+                       const uint32_t* ranges, const float* bg, const float* image, const float* T_final,
+                       const uint32_t* n_contrib, const float* v_image, const float* target, float l1_weight,
+                       double* loss, float* v2d, cudaStream_t st) {
+  render_bwd_kernel<kTile, kBatch><<<batch.n_tiles, Shape<kTile>::kThreads, 0, st>>>(
+      batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image, target, l1_weight, loss, v2d);
+}
+
+template <int kTile>
+void render_bwd_tile(int rb, const gs_batch& batch, const gs_cameras& cams, const float4* sp,
+                     const uint32_t* vals, const uint32_t* ranges, const float* bg, const float* image,
+                     const float* T_final, const uint32_t* n_contrib, const float* v_image, const float* target,
+                     float l1_weight, double* loss, float* v2d, cudaStream_t st) {
+  if (rb == 64)
+    render_bwd_launch<kTile, 64>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image, target,
+                                 l1_weight, loss, v2d, st);
+  else if (rb == 128)
+    render_bwd_launch<kTile, 128>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image, target,
+                                  l1_weight, loss, v2d, st);
+  else
+    render_bwd_launch<kTile, 256>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image, target,
+                                  l1_weight, loss, v2d, st);
+}
+
+}  // namespace
+
 cudaError_t launch_render_fwd(const gs_batch& batch, const gs_cameras& cams, const gs_projected& proj,
                               const uint32_t* vals, const uint32_t* ranges, const float* bg,
                               float* image, float* T_final, uint32_t* n_contrib, uint32_t* n_added,
                               cudaStream_t st) {
   if (batch.n_tiles == 0) return cudaSuccess;
   const float4* sp = reinterpret_cast<const float4*>(proj.splat);
-  switch (tuning().render_fwd_batch) {
-    case 64:
-      render_fwd_kernel<64><<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, sp, vals, ranges, bg, image, T_final,
-                                                                n_contrib, n_added);
-      break;
-    case 128:
-      render_fwd_kernel<128><<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, sp, vals, ranges, bg, image,
-                                                                 T_final, n_contrib, n_added);
-      break;
-    default:
-      render_fwd_kernel<256><<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, sp, vals, ranges, bg, image,
-                                                                 T_final, n_contrib, n_added);
-      break;
-  }
+  const int rb = tuning().render_fwd_batch;
+  if (batch.tile == 32)
+    render_fwd_tile<32>(rb, batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, n_added, st);
+  else
+    render_fwd_tile<16>(rb, batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, n_added, st);
   return cudaGetLastError();
 }
 
@@ -542,22 +602,13 @@ cudaError_t launch_render_bwd(const gs_batch& batch, const gs_cameras& cams, con
                               double* loss, float* v2d, cudaStream_t st) {
   if (batch.n_tiles == 0) return cudaSuccess;
   const float4* sp = reinterpret_cast<const float4*>(proj.splat);
-  switch (tuning().render_bwd_batch) {
-    case 64:
-      render_bwd_kernel<64><<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, sp, vals, ranges, bg, image, T_final,
-                                                                n_contrib, v_image, target, l1_weight, loss, v2d);
-      break;
-    case 128:
-      render_bwd_kernel<128><<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, sp, vals, ranges, bg, image,
-                                                                 T_final, n_contrib, v_image, target, l1_weight,
-                                                                 loss, v2d);
-      break;
-    default:
-      render_bwd_kernel<256><<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, sp, vals, ranges, bg, image,
-                                                                 T_final, n_contrib, v_image, target, l1_weight,
-                                                                 loss, v2d);
-      break;
-  }
+  const int rb = tuning().render_bwd_batch;
+  if (batch.tile == 32)
+    render_bwd_tile<32>(rb, batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image, target,
+                        l1_weight, loss, v2d, st);
+  else
+    render_bwd_tile<16>(rb, batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image, target,
+                        l1_weight, loss, v2d, st);
   return cudaGetLastError();
 }
 

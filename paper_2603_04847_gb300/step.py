@@ -130,8 +130,9 @@ class JointStep:
     def __init__(self, gaussians: Gaussians, cams: Cameras, X: torch.Tensor, obs_point: torch.Tensor,
                  obs_xy: torch.Tensor, view_obs_offset: torch.Tensor, targets: torch.Tensor,
                  target_px_offset: np.ndarray, views, hyper: Hyper = None, mode: str = "batched",
-                 capacity: int = 0, device="cuda"):
+                 capacity: int = 0, device="cuda", tile: int = 16):
         self.h = hyper or Hyper()
+        self.tile = int(tile)
         self.mode = mode
         self.g = gaussians
         self.dg = Gaussians.zeros_like(gaussians)
@@ -166,13 +167,13 @@ class JointStep:
     def set_batch(self, views):
         views = np.asarray(views, dtype=np.int64)
         self.views = views
-        self.batch = Batch(self.cams, views, device=self.device)
+        self.batch = Batch(self.cams, views, tile=self.tile, device=self.device)
         n = self.g.n
         if self.mode == "batched":
             self.renderers = [Renderer(n, self.cams, self.batch, self._capacity, device=self.device)]
             self.slot_batches = [self.batch]
         else:
-            self.slot_batches = [Batch(self.cams, [v], device=self.device) for v in views]
+            self.slot_batches = [Batch(self.cams, [v], tile=self.tile, device=self.device) for v in views]
             cap = self._capacity // max(len(views), 1)
             self.renderers = [Renderer(n, self.cams, b, cap, device=self.device) for b in self.slot_batches]
         self.track_ws = torch.empty(max(track_workspace_bytes(self.batch), 256), dtype=torch.uint8,
@@ -186,6 +187,18 @@ class JointStep:
         """Gathers the batch's target images into slot order on the device
         (the step does this itself; this is for use outside a step)."""
         gs_gather_view_pixels(self.targets, self.target_px_offset_dev, self.cams, self.batch, self.target_batch)
+
+    def set_tile(self, tile: int):
+        """Switches the tile size (16 or 32 pixels): re-allocates the batch's
+        buffers (instance capacity kept) and drops the captured graph."""
+        if int(tile) == self.tile:
+            return
+        self.tile = int(tile)
+        caps = [r.tl.capacity for r in self.renderers]
+        self.set_batch(self.views)
+        for r, cap in zip(self.renderers, caps):
+            if r.tl.capacity < cap:
+                r.tl = TileLists(r.n, r.batch, cap, r.image.device)
 
     def next_batch(self, views):
         """Switches to another batch of views.  Views of the same per-slot

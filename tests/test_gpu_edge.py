@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import synth
-from _gpu import f32, gpu_forward, knife_mask, oracle_cam, oracle_scene, rel_linf
+from _gpu import f32, gpu_backward, gpu_forward, knife_mask, oracle_cam, oracle_scene, rel_linf
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -195,6 +195,26 @@ def test_target_stream_matches_device_resident_targets():
     for x, y in zip(_state(ref), _state(js)):
         np.testing.assert_allclose(y, x, rtol=1e-4, atol=1e-6)
     assert js.status_flags() == 0
+
+
+def test_tile_sizes_give_identical_images_and_gradients():
+    """16- and 32-pixel tiles composite the same splats in the same order at
+    every pixel (a splat missing from a pixel's 16-tile list cannot reach
+    it), so images and transmittance are bit-identical and gradients agree
+    to rounding of the order of the per-tile atomic sums."""
+    w = synth.make_workload("batched", n_gaussians=8000, n_views=3, width=(150, 260), height=(100, 190), n_tracks=10)
+    outs = []
+    for tile in (16, 32):
+        r, g, *_ = gpu_forward(w["scene"], w["wh"], w["K"], w["Rt"], [2, 0, 1], tile=tile)
+        rng = np.random.default_rng(9)
+        v = rng.normal(0, 1, (r.batch.n_pixels, 3))
+        got = gpu_backward(r, g, v_image=v)
+        outs.append((r.image.cpu().numpy(), r.T_final.cpu().numpy(), got))
+    (i16, t16, g16), (i32, t32, g32) = outs
+    np.testing.assert_array_equal(i32, i16)
+    np.testing.assert_array_equal(t32, t16)
+    for k in ("mean", "log_scale", "quat", "opacity_logit", "sh", "tangent"):
+        np.testing.assert_allclose(g32[k], g16[k], rtol=1e-4, atol=1e-6 * np.abs(g16[k]).max())
 
 
 def test_every_tuning_candidate_gives_the_same_image_and_lists():

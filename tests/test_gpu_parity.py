@@ -45,9 +45,13 @@ def tiny():
     return w, w["scene"], w["wh"], w["K"], w["Rt"]
 
 
-def test_tiny_forward_image_matches_oracle():
+TILES = pytest.mark.parametrize("tile", [16, 32])
+
+
+@TILES
+def test_tiny_forward_image_matches_oracle(tile):
     w, sc, wh, K, Rt = tiny()
-    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, [0])
+    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, [0], tile=tile)
     cam = oracle_cam(wh, K, Rt, 0)
     ref = oracle.render(oracle_scene(sc), cam, knife_eps=KNIFE_EPS)
     img = r.image.cpu().numpy().reshape(192, 256, 3)
@@ -59,16 +63,17 @@ def test_tiny_forward_image_matches_oracle():
     assert T.min() >= 1e-4 and T.max() <= 1.0
 
 
-def test_tiny_discrete_stage_bit_exact():
+@TILES
+def test_tiny_discrete_stage_bit_exact(tile):
     """Tile sets, per-tile order (depth, index) and ranges equal the
     oracle's discrete stage (plain lexicographic sort of its own FP64
-    rectangles), away from knife edges."""
+    rectangles), away from knife edges, for both tile sizes."""
     w, sc, wh, K, Rt = tiny()
-    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, [0])
+    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, [0], tile=tile)
     cam = oracle_cam(wh, K, Rt, 0)
     osc = oracle_scene(sc)
     proj = oracle.project(osc, cam)
-    vis, trect, knife = oracle_rect_knife(proj, 256, 192, 16)
+    vis, trect, knife = oracle_rect_knife(proj, 256, 192, tile)
     N = g.n
     n_tiles = r.proj.n_tiles.cpu().numpy()[:N].astype(np.int64)
     rect = r.proj.rect.cpu().numpy()[:N].astype(np.int64) & 0xFFFF
@@ -81,7 +86,7 @@ def test_tiny_discrete_stage_bit_exact():
     np.testing.assert_array_equal(n_tiles[both], ((trect[both, 2] - trect[both, 0] + 1) *
                                                   (trect[both, 3] - trect[both, 1] + 1)))
     # order within every tile
-    t_o, d_o, g_o = oracle.tile_lists(proj, 256, 192, 16)
+    t_o, d_o, g_o = oracle.tile_lists(proj, 256, 192, tile)
     keep = ~knife[g_o]
     t_o, d_o, g_o = t_o[keep], d_o[keep], g_o[keep]
     n_inst = r.n_instances()
@@ -108,9 +113,10 @@ def test_tiny_discrete_stage_bit_exact():
     np.testing.assert_array_equal(ranges[:, 1] - ranges[:, 0], counts_k)
 
 
-def test_tiny_n_contrib_matches_oracle_positions():
+@TILES
+def test_tiny_n_contrib_matches_oracle_positions(tile):
     w, sc, wh, K, Rt = tiny()
-    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, [0])
+    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, [0], tile=tile)
     cam = oracle_cam(wh, K, Rt, 0)
     ref = oracle.render(oracle_scene(sc), cam, knife_eps=KNIFE_EPS)
     nc = r.n_contrib.cpu().numpy().reshape(192, 256)
@@ -123,7 +129,7 @@ def test_tiny_n_contrib_matches_oracle_positions():
         for u in range(0, 256, 5):
             if not ok[v, u]:
                 continue
-            t = (v // 16) * 16 + u // 16
+            t = (v // tile) * ((256 + tile - 1) // tile) + u // tile
             s, e = ranges[t]
             if last[v, u] < 0:
                 assert nc[v, u] == 0
@@ -142,11 +148,12 @@ def _compare_grads(got, ref, view=0, tol=GRAD_TOL):
     assert e <= tol, "pose tangent: %.3g" % e
 
 
-def test_tiny_backward_random_cotangent():
+@TILES
+def test_tiny_backward_random_cotangent(tile):
     """dL/dparams and the pose tangent for L = <w, image> with a seeded
     random w (knife-edge pixels zeroed on both sides)."""
     w, sc, wh, K, Rt = tiny()
-    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, [0])
+    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, [0], tile=tile)
     cam = oracle_cam(wh, K, Rt, 0)
     osc = oracle_scene(sc)
     ref = oracle.render(osc, cam, knife_eps=KNIFE_EPS)
@@ -180,13 +187,14 @@ def small_batched(n=4000, views=4, seed=None):
                                n_tracks=300, seed=seed)
 
 
-def test_batched_uneven_views_forward_backward():
+@TILES
+def test_batched_uneven_views_forward_backward(tile):
     """Several views of uneven, ragged resolution in one launch per stage:
     images and gradients against the oracle view by view."""
     w = small_batched()
     sc, wh, K, Rt = w["scene"], w["wh"], w["K"], w["Rt"]
     views = [2, 0, 3, 1]
-    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, views)
+    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, views, tile=tile)
     osc = oracle_scene(sc)
     img = r.image.cpu().numpy()
     rng = np.random.default_rng(3)
