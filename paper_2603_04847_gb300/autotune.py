@@ -17,7 +17,9 @@ import torch
 
 from .core import TileLists, gs_get_tuning, gs_set_tuning
 
-TILES = (16, 32)
+# the usual winner last, so that the step is left as it was tried (no
+# rebuild of the batch buffers after the trials)
+TILES = (32, 16)
 RENDER_BATCHES = (64, 128, 256)
 SORT_BLOCKS = (1, 2, 4)
 # (render_fwd_batch, render_bwd_batch, sort_blocks_per_sm) settings the
