@@ -37,6 +37,7 @@ namespace {
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;  // 2048 records per scan block
+constexpr int kExpandStage = 4096;                    // instances staged per expand window
 
 constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
@@ -381,21 +382,19 @@ struct SlotTiles {
 };
 
 // Emits the instances of 2048 depth-sorted records.  Their instances are
-// one contiguous output range (from the scan), written coalesced: output q
-// of the block belongs to the record i with off[i] <= q < off[i+1]
-// (searched in shared memory) and is its (q - off[i])-th covered tile in
-// row-major order.  Also counts the tile-id digits for the tile sort and
-// zeroes a share of the tile sort's look-back words.
+// one contiguous output range (from the scan); each thread's 8 records are
+// contiguous within it.  Instance j of a record is its j-th covered tile in
+// row-major order.  The instances are staged in shared memory per window and
+// written out coalesced.  Also counts the tile-id digits for the tile sort
+// and zeroes a share of the tile sort's look-back words.
 __global__ void __launch_bounds__(kScanThreads) expand_kernel(
     const uint32_t* __restrict__ ntd, const uint32_t* __restrict__ order, size_t M,
     const unsigned long long* __restrict__ block_offs, gs_projected proj, int N, gs_cameras cams,
     gs_batch batch, uint32_t* __restrict__ tiles, uint32_t* __restrict__ vals, size_t capacity,
     const uint32_t* n_instances, int n_digits, uint32_t* __restrict__ ghist,
     unsigned long long* __restrict__ lb_tile, size_t lb_tile_stride) {
-  __shared__ uint32_t s_off[kScanTile + 1];
-  __shared__ uint32_t s_rec[kScanTile];
-  __shared__ ushort4 s_rect[kScanTile];
-  __shared__ uint8_t s_slot[kScanTile];
+  __shared__ uint32_t s_t[kExpandStage];
+  __shared__ uint32_t s_v[kExpandStage];
   __shared__ SlotTiles st[GS_MAX_BATCH];
   __shared__ uint32_t h[kMaxDigits][256];
   __shared__ uint32_t sm[32];
@@ -430,62 +429,54 @@ __global__ void __launch_bounds__(kScanThreads) expand_kernel(
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i)
     if (c[i]) rc[i] = reinterpret_cast<const ushort4*>(proj.rect)[rr[i]];
-  uint32_t total;
-  uint32_t run = block_exclusive_scan_u32(s, &total, sm);
+  uint32_t slot[kScanItems];
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    const int li = tid * kScanItems + i;
-    s_off[li] = run;
-    run += c[i];
-    if (c[i]) {
-      s_rec[li] = rr[i];
-      s_rect[li] = rc[i];
-      s_slot[li] = (uint8_t)(rr[i] / (uint32_t)N);
-    }
-  }
-  if (tid == 0) s_off[kScanTile] = total;
-  __syncthreads();
+  for (int i = 0; i < kScanItems; ++i) slot[i] = c[i] ? rr[i] / (uint32_t)N : 0u;
+  uint32_t total;
+  const uint32_t my0 = block_exclusive_scan_u32(s, &total, sm);  // this thread's first output
 
-  // Each warp emits one contiguous chunk of the block's outputs, 32 at a
-  // time.  Output q belongs to the largest i with s_off[i] <= q (then
-  // s_off[i+1] > q, so record i is not empty).  Visible records are never
-  // empty and come first in depth order, so the 32 outputs from the record
-  // of the chunk's current position on span at most 32 records: search that
-  // window, and the whole block only where the window misses.
+  // The thread's records are contiguous in depth order, so their instances
+  // are the contiguous outputs [my0, my0 + s) of the block.  Per window of
+  // kExpandStage outputs, every thread writes its records' instances into
+  // shared memory (walking each rectangle row-major from the window's
+  // start), then the block copies the window out coalesced and counts the
+  // tile-id digits.
   const unsigned long long g0 = block_offs[blockIdx.x];
   const uint32_t n_out = g0 >= capacity ? 0u : (uint32_t)min((unsigned long long)total, capacity - g0);
-  const int lane = tid & 31, warp = tid >> 5, n_warps = kScanThreads / 32;
-  const uint32_t chunk = ((n_out + n_warps - 1) / n_warps + 31) & ~31u;
-  const uint32_t q_lo = min(n_out, (uint32_t)warp * chunk), q_hi = min(n_out, q_lo + chunk);
-  int i_lo = 0;
+  for (uint32_t w0 = 0; w0 < n_out; w0 += kExpandStage) {
+    const uint32_t w1 = min(w0 + (uint32_t)kExpandStage, n_out);
+    uint32_t q = my0;
 #pragma unroll
-  for (int step = kScanTile / 2; step > 0; step >>= 1)
-    if (s_off[i_lo + step] <= q_lo) i_lo += step;
-  for (uint32_t q0 = q_lo; q0 < q_hi; q0 += 32) {
-    const uint32_t q = q0 + lane;
-    int i = i_lo;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1)
-      if (i + step <= kScanTile && s_off[i + step] <= q) i += step;
-    if (s_off[i + 1] <= q) {  // window missed (only with empty records inside)
-      i = 0;
-      for (int step = kScanTile / 2; step > 0; step >>= 1)
-        if (s_off[i + step] <= q) i += step;
+    for (int i = 0; i < kScanItems; ++i) {
+      const uint32_t lo = max(q, w0), hi = min(q + c[i], w1);
+      if (lo < hi) {
+        const ushort4 r4 = rc[i];
+        const SlotTiles sl = st[slot[i]];
+        const uint32_t w = (uint32_t)(r4.z - r4.x + 1);
+        const uint32_t j = lo - q;
+        const uint32_t jy = j / w;
+        uint32_t jx = j - jy * w;
+        uint32_t row = (uint32_t)(sl.tile_offset + (int)(r4.y + jy) * sl.tiles_x + (int)r4.x);
+        for (uint32_t p = lo; p < hi; ++p) {
+          s_t[p - w0] = row + jx;
+          s_v[p - w0] = rr[i];
+          if (++jx == w) {
+            jx = 0;
+            row += (uint32_t)sl.tiles_x;
+          }
+        }
+      }
+      q += c[i];
     }
-    i_lo = __shfl_sync(0xffffffffu, i, 31);
-    if (q < q_hi) {
-      const uint32_t j = q - s_off[i];
-      const ushort4 r4 = s_rect[i];
-      const uint32_t w = (uint32_t)(r4.z - r4.x + 1);
-      const uint32_t jy = j / w, jx = j - jy * w;
-      const SlotTiles sl = st[s_slot[i]];
-      const uint32_t tile = (uint32_t)(sl.tile_offset + (int)(r4.y + jy) * sl.tiles_x + (int)(r4.x + jx));
-      tiles[g0 + q] = tile;
-      vals[g0 + q] = s_rec[i];
+    __syncthreads();
+    for (uint32_t p = tid; p < w1 - w0; p += kScanThreads) {
+      const uint32_t tile = s_t[p];
+      tiles[g0 + w0 + p] = tile;
+      vals[g0 + w0 + p] = s_v[p];
       for (int d = 0; d < n_digits; ++d) atomicAdd(&h[d][(tile >> (8 * d)) & 0xffu], 1u);
     }
+    __syncthreads();
   }
-  __syncthreads();
   for (int i = tid; i < n_digits * 256; i += blockDim.x) {
     const uint32_t cnt = (&h[0][0])[i];
     if (cnt) atomicAdd(&ghist[i], cnt);
