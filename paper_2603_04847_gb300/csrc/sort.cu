@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(256) digit_hist_kernel(const uint32_t* __restr
 //   kout/vout  output; kout may be nullptr (keys not needed afterwards)
 //   ghist      [256] counts of this digit over all n items
 //   gather     if gather_src: gather_dst[pos] = gather_src[value] as well
+//              (8-byte elements)
 // Per tile: every warp ranks its 256 contiguous items (8 rounds of 32)
 // against a warp-private running count per digit (peers found with one
 // ballot per digit bit, which measured faster than a warp match); one block step turns the per-warp counts into
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* n_dev, uint32_t n_host, size_t capacity, int shift,
     const uint32_t* __restrict__ ghist, unsigned long long* lookback, uint32_t* tile_counter,
-    const uint32_t* __restrict__ gather_src, uint32_t* __restrict__ gather_dst, int32_t* status) {
+    const uint2* __restrict__ gather_src, uint2* __restrict__ gather_dst, int32_t* status) {
   __shared__ uint32_t s_base[256];    // output position of this tile's first item of each digit
   __shared__ uint32_t s_tot[256];     // items of each digit in this tile
   __shared__ uint32_t s_dstart[256];  // exclusive scan of s_tot
@@ -310,16 +311,29 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
   }
 }
 
-// Sum of in[k] per scan block (64-bit to detect overflow).
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ in, size_t M,
+// Tiles touched by the record at depth position k: the area of its tile
+// rectangle for the visible records (the first n_visible in depth order),
+// none for the others (whose rectangles were not written).
+__device__ inline uint32_t rect_area(ushort4 r) {
+  return (uint32_t)(r.z - r.x + 1) * (uint32_t)(r.w - r.y + 1);
+}
+
+__device__ inline size_t visible_records(size_t M, const uint32_t* ghist_depth) {
+  return M - ghist_depth[(kMaxDigits - 1) * 256 + 255];  // invisible keys are all ones
+}
+
+// Sum of tiles touched per scan block (64-bit to detect overflow).
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const ushort4* __restrict__ rectd, size_t M,
+                                                                   const uint32_t* __restrict__ ghist_depth,
                                                                    unsigned long long* block_sums) {
   __shared__ unsigned long long red[kScanThreads / 32];
   const size_t base = (size_t)blockIdx.x * kScanTile;
+  const size_t n_vis = visible_records(M, ghist_depth);
   unsigned long long s = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const size_t k = base + (size_t)i * kScanThreads + threadIdx.x;
-    if (k < M) s += in[k];
+    if (k < n_vis) s += rect_area(rectd[k]);
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
@@ -388,7 +402,8 @@ struct SlotTiles {
 // written out coalesced.  Also counts the tile-id digits for the tile sort
 // and zeroes a share of the tile sort's look-back words.
 __global__ void __launch_bounds__(kScanThreads) expand_kernel(
-    const uint32_t* __restrict__ ntd, const uint32_t* __restrict__ order, size_t M,
+    const ushort4* __restrict__ rectd, const uint32_t* __restrict__ order, size_t M,
+    const uint32_t* __restrict__ ghist_depth,
     const unsigned long long* __restrict__ block_offs, gs_projected proj, int N, gs_cameras cams,
     gs_batch batch, uint32_t* __restrict__ tiles, uint32_t* __restrict__ vals, size_t capacity,
     const uint32_t* n_instances, int n_digits, uint32_t* __restrict__ ghist,
@@ -416,19 +431,19 @@ __global__ void __launch_bounds__(kScanThreads) expand_kernel(
   }
 
   const size_t base = (size_t)blockIdx.x * kScanTile;
+  const size_t n_vis = visible_records(M, ghist_depth);
   uint32_t c[kScanItems], rr[kScanItems];
+  ushort4 rc[kScanItems];
   uint32_t s = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const size_t k = base + (size_t)tid * kScanItems + i;
-    c[i] = k < M ? ntd[k] : 0u;
-    rr[i] = k < M ? order[k] : 0u;
+    const bool vis = k < n_vis;
+    rc[i] = vis ? rectd[k] : make_ushort4(0, 0, 0, 0);
+    rr[i] = vis ? order[k] : 0u;
+    c[i] = vis ? rect_area(rc[i]) : 0u;
     s += c[i];
   }
-  ushort4 rc[kScanItems];
-#pragma unroll
-  for (int i = 0; i < kScanItems; ++i)
-    if (c[i]) rc[i] = reinterpret_cast<const ushort4*>(proj.rect)[rr[i]];
   uint32_t slot[kScanItems];
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) slot[i] = c[i] ? rr[i] / (uint32_t)N : 0u;
@@ -525,7 +540,7 @@ size_t radix_tiles(size_t items) { return (items + kTileItems - 1) / kTileItems;
 struct SortWs {
   uint32_t* dkeys[2];   // depth keys, double-buffered [M]
   uint32_t* dvals[2];   // record ids [M]
-  uint32_t* ntd;        // tiles touched, in depth order [M]
+  ushort4* rectd;       // tile rectangles, in depth order [M]
   unsigned long long* block_sums;
   uint32_t* tiles_alt;  // [capacity]
   uint32_t* vals_alt;   // [capacity]
@@ -547,7 +562,7 @@ SortWs sort_ws_layout(void* base, size_t M, size_t capacity, int tile_passes) {
   };
   for (int i = 0; i < 2; ++i) w.dkeys[i] = (uint32_t*)take(M * 4);
   for (int i = 0; i < 2; ++i) w.dvals[i] = (uint32_t*)take(M * 4);
-  w.ntd = (uint32_t*)take(M * 4);
+  w.rectd = (ushort4*)take(M * 8);
   w.block_sums = (unsigned long long*)take(((M + kScanTile - 1) / kScanTile) * 8 + 8);
   w.tiles_alt = (uint32_t*)take(capacity * 4);
   w.vals_alt = (uint32_t*)take(capacity * 4);
@@ -598,7 +613,8 @@ cudaError_t launch_sort_tiles(int N, const gs_cameras& cams, const gs_batch& bat
   if (n_scan_blocks == 0) return cudaGetLastError();
 
   // 1. stable depth sort of the records: keys from the projection, values
-  //    = record ids; the last pass writes no keys but gathers n_tiles
+  //    = record ids; the last pass writes no keys but gathers the tile
+  //    rectangles into depth order
   digit_hist_kernel<<<grid_stride_blocks(M / 4 + 1, 256), 256, 0, st>>>(proj.depth_key, (uint32_t)M, kMaxDigits,
                                                                          ghist_depth);
   const int depth_grid = (int)radix_tiles(M);
@@ -611,7 +627,8 @@ cudaError_t launch_sort_tiles(int N, const gs_cameras& cams, const gs_batch& bat
     uint32_t* vo = w.dvals[pass & 1];
     onesweep_kernel<<<depth_grid, kSortThreads, 0, st>>>(
         kin, vin, ko, vo, nullptr, (uint32_t)M, M, 8 * pass, ghist_depth + 256 * pass,
-        w.lb_depth + lbd_stride * pass, w.counters + pass, last ? proj.n_tiles : nullptr, last ? w.ntd : nullptr,
+        w.lb_depth + lbd_stride * pass, w.counters + pass, last ? reinterpret_cast<const uint2*>(proj.rect) : nullptr,
+        last ? reinterpret_cast<uint2*>(w.rectd) : nullptr,
         status);
     kin = ko;
     vin = vo;
@@ -620,14 +637,14 @@ cudaError_t launch_sort_tiles(int N, const gs_cameras& cams, const gs_batch& bat
 
   // 2. instance offsets in depth order, 3. expand into whichever buffer
   //    leaves the tile-sorted result in tiles/vals, 4. stable tile sort
-  scan_reduce_kernel<<<n_scan_blocks, kScanThreads, 0, st>>>(w.ntd, M, w.block_sums);
+  scan_reduce_kernel<<<n_scan_blocks, kScanThreads, 0, st>>>(w.rectd, M, ghist_depth, w.block_sums);
   scan_blocks_kernel<<<1, 1024, 0, st>>>(w.block_sums, n_scan_blocks, capacity, n_instances, status);
   uint32_t* kA = (passes & 1) ? w.tiles_alt : tiles;
   uint32_t* vA = (passes & 1) ? w.vals_alt : vals;
   uint32_t* kB = (passes & 1) ? tiles : w.tiles_alt;
   uint32_t* vB = (passes & 1) ? vals : w.vals_alt;
   const size_t lbt_stride = radix_tiles(capacity) * 256;
-  expand_kernel<<<n_scan_blocks, kScanThreads, 0, st>>>(w.ntd, order, M, w.block_sums, proj, N, cams, batch, kA, vA,
+  expand_kernel<<<n_scan_blocks, kScanThreads, 0, st>>>(w.rectd, order, M, ghist_depth, w.block_sums, proj, N, cams, batch, kA, vA,
                                                          capacity, n_instances, passes, ghist_tile, w.lb_tile,
                                                          lbt_stride);
   const int tile_grid = (int)radix_tiles(capacity);
