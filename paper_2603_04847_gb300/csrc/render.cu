@@ -6,7 +6,7 @@
 // threads; 32x32 tiles: 512 threads; the batch's tile size is chosen by the
 // autotuner).  Each warp owns an 8x8 block of the tile and each thread two
 // pixels of it,
-// (x, y) and (x, y + 4): the per-splat shared-memory loads, the cull test
+// (x, y) and (x + 4, y): the per-splat shared-memory loads, the cull test
 // and the loop overhead are paid once per two pixels, and in the backward
 // one warp reduction covers 64 pixels.
 //
@@ -83,14 +83,15 @@ __device__ inline void find_tile(const gs_batch& batch, const gs_cameras& cams, 
 }
 
 // Pixels of thread `tid` in its tile: warp w covers the 8x8 block at
-// ((w % kWarpsX) * 8, (w / kWarpsX) * 8); lane l the pixels (l & 7, l >> 3)
-// and (l & 7, (l >> 3) + 4) in it.
+// ((w % kWarpsX) * 8, (w / kWarpsX) * 8); lane l the pixels (l & 3, l >> 2)
+// and ((l & 3) + 4, l >> 2) in it — one row, so that the row-dependent part
+// of the exponent is computed once for both.
 template <int kTile>
 __device__ inline void tile_pixels(int tid, int& lx, int& ly) {
   constexpr int kWX = Shape<kTile>::kWarpsX;
   const int w = tid >> 5, l = tid & 31;
-  lx = (w % kWX) * 8 + (l & 7);
-  ly = (w / kWX) * 8 + (l >> 3);
+  lx = (w % kWX) * 8 + (l & 3);
+  ly = (w / kWX) * 8 + (l >> 2);
 }
 
 // Bit w set iff the bounding box of the splat's support {q <= q_max} can
@@ -141,13 +142,17 @@ __device__ inline void stage_splat(int s, uint32_t r, const float4* __restrict__
   s_mask[s] = warp_mask<kTile>(xyo, con, x0, y0);
 }
 
-// Exponent e of alpha_raw = 2^e at offset (dx, dy), given Adx = A * dx.
-// Written with explicit roundings so that every kernel computes the same
-// value from the same staged inputs.
-__device__ inline float splat_exponent(const float4 q, float Adx, float dx, float dy) {
-  const float t = __fmaf_rn(q.y, dy, Adx);                  // A dx + B dy
-  const float s = __fmaf_rn(__fmul_rn(q.z, dy), dy, q.w);   // C dy^2 + log2 o
-  return __fmaf_rn(t, dx, s);
+// Exponent e = A dx^2 + B dx dy + C dy^2 + log2 o of alpha_raw = 2^e at
+// offset (dx, dy), from the row terms Bdy = B dy and sy = C dy^2 + log2 o
+// (row_terms).  Written with explicit roundings so that every kernel
+// computes the same value from the same staged inputs.
+__device__ inline void row_terms(const float4 q, float dy, float& Bdy, float& sy) {
+  Bdy = __fmul_rn(q.y, dy);
+  sy = __fmaf_rn(__fmul_rn(q.z, dy), dy, q.w);
+}
+
+__device__ inline float splat_exponent(const float4 q, float dx, float Bdy, float sy) {
+  return __fmaf_rn(__fmaf_rn(q.x, dx, Bdy), dx, sy);
 }
 
 // Positions s < min(cnt, limit) of the staged batch whose mask has this
@@ -188,9 +193,9 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads) render_fwd_kernel(
   int lx, ly;
   tile_pixels<kTile>(threadIdx.x, lx, ly);
   const uint32_t wbit = 1u << warp;
-  const int u = ti.tx * kTile + lx, v0 = ti.ty * kTile + ly, v1 = v0 + 4;
-  const bool in0 = u < ti.W && v0 < ti.H, in1 = u < ti.W && v1 < ti.H;
-  const float px = (float)u + 0.5f, py0 = (float)v0 + 0.5f, py1 = (float)v1 + 0.5f;
+  const int u0 = ti.tx * kTile + lx, u1 = u0 + 4, v = ti.ty * kTile + ly;
+  const bool in0 = u0 < ti.W && v < ti.H, in1 = u1 < ti.W && v < ti.H;
+  const float px0 = (float)u0 + 0.5f, px1 = (float)u1 + 0.5f, py = (float)v + 0.5f;
   const float x0 = (float)(ti.tx * kTile), y0 = (float)(ti.ty * kTile);
   const uint32_t start = ranges[2 * gt], end = ranges[2 * gt + 1];
   float T0 = 1.f, T1 = 1.f;
@@ -215,10 +220,10 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads) render_fwd_kernel(
       const int k = s_list[warp][i];
       const float2 m = s_m[k];
       const float4 q = s_q[k];
-      const float dx = px - m.x;
-      const float Adx = __fmul_rn(q.x, dx);
-      const float r0 = ex2_approx(splat_exponent(q, Adx, dx, py0 - m.y));
-      const float r1 = ex2_approx(splat_exponent(q, Adx, dx, py1 - m.y));
+      float Bdy, sy;
+      row_terms(q, py - m.y, Bdy, sy);
+      const float r0 = ex2_approx(splat_exponent(q, px0 - m.x, Bdy, sy));
+      const float r1 = ex2_approx(splat_exponent(q, px1 - m.x, Bdy, sy));
       const bool c0 = r0 >= thr0;
       const bool c1 = r1 >= thr1;
       if (!(c0 || c1)) continue;
@@ -260,7 +265,7 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads) render_fwd_kernel(
     }
   }
   if (in0) {
-    const size_t p = (size_t)ti.px_offset + (size_t)v0 * ti.W + u;
+    const size_t p = (size_t)ti.px_offset + (size_t)v * ti.W + u0;
     image[3 * p + 0] = C00 + T0 * bg[0];
     image[3 * p + 1] = C01 + T0 * bg[1];
     image[3 * p + 2] = C02 + T0 * bg[2];
@@ -269,7 +274,7 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads) render_fwd_kernel(
     if (n_added) n_added[p] = add0;
   }
   if (in1) {
-    const size_t p = (size_t)ti.px_offset + (size_t)v1 * ti.W + u;
+    const size_t p = (size_t)ti.px_offset + (size_t)v * ti.W + u1;
     image[3 * p + 0] = C10 + T1 * bg[0];
     image[3 * p + 1] = C11 + T1 * bg[1];
     image[3 * p + 2] = C12 + T1 * bg[2];
@@ -416,16 +421,16 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads) render_bwd_kernel(
   int lx, ly;
   tile_pixels<kTile>(threadIdx.x, lx, ly);
   const uint32_t wbit = 1u << (threadIdx.x >> 5);
-  const int u = ti.tx * kTile + lx, v0 = ti.ty * kTile + ly, v1 = v0 + 4;
-  const bool in0 = u < ti.W && v0 < ti.H, in1 = u < ti.W && v1 < ti.H;
-  const float px = (float)u + 0.5f, py0 = (float)v0 + 0.5f, py1 = (float)v1 + 0.5f;
+  const int u0 = ti.tx * kTile + lx, u1 = u0 + 4, v = ti.ty * kTile + ly;
+  const bool in0 = u0 < ti.W && v < ti.H, in1 = u1 < ti.W && v < ti.H;
+  const float px0 = (float)u0 + 0.5f, px1 = (float)u1 + 0.5f, py = (float)v + 0.5f;
   const float x0 = (float)(ti.tx * kTile), y0 = (float)(ti.ty * kTile);
   const uint32_t start = ranges[2 * gt];
   float lsum = 0.f;
   PixBwd P0, P1;
-  load_pixel(P0, in0, (size_t)ti.px_offset + (size_t)v0 * ti.W + u, ti, bg, image, T_final, n_contrib, v_image,
+  load_pixel(P0, in0, (size_t)ti.px_offset + (size_t)v * ti.W + u0, ti, bg, image, T_final, n_contrib, v_image,
              target, l1_weight, lsum);
-  load_pixel(P1, in1, (size_t)ti.px_offset + (size_t)v1 * ti.W + u, ti, bg, image, T_final, n_contrib, v_image,
+  load_pixel(P1, in1, (size_t)ti.px_offset + (size_t)v * ti.W + u1, ti, bg, image, T_final, n_contrib, v_image,
              target, l1_weight, lsum);
   const uint32_t nc_max = max(P0.nc, P1.nc);
   if (nc_max) atomicMax(&s_max, nc_max);
@@ -466,15 +471,16 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads) render_bwd_kernel(
       const uint32_t pos = (uint32_t)(bstart + k);
       const float2 m = s_m[k];
       const float4 q = s_q[k];
-      const float dx = px - m.x;
-      const float Adx = __fmul_rn(q.x, dx);
+      const float dy = py - m.y;
+      float Bdy, sy;
+      row_terms(q, dy, Bdy, sy);
       float g[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) g[i] = 0.f;
       bool contrib = false;
       if (pos < P0.nc) {
-        const float dy = py0 - m.y;
-        const float araw = ex2_approx(splat_exponent(q, Adx, dx, dy));
+        const float dx = px0 - m.x;
+        const float araw = ex2_approx(splat_exponent(q, dx, Bdy, sy));
         const float alpha = fminf(kAlphaMax, araw);
         if (alpha >= kAlphaMin) {
           contrib = true;
@@ -482,8 +488,8 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads) render_bwd_kernel(
         }
       }
       if (pos < P1.nc) {
-        const float dy = py1 - m.y;
-        const float araw = ex2_approx(splat_exponent(q, Adx, dx, dy));
+        const float dx = px1 - m.x;
+        const float araw = ex2_approx(splat_exponent(q, dx, Bdy, sy));
         const float alpha = fminf(kAlphaMax, araw);
         if (alpha >= kAlphaMin) {
           contrib = true;
