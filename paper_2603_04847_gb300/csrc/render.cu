@@ -393,8 +393,10 @@ __device__ inline void load_pixel(PixBwd& P, bool inside, size_t p, const TileIn
   if (P.v0 == 0.f && P.v1 == 0.f && P.v2 == 0.f) P.nc = 0;
 }
 
+// 9 blocks of 16x16 per SM (56 registers, no spills) measured ~2 % faster
+// than the 8 that 64 registers allow
 template <int kTile, int kBatch>
-__global__ void __launch_bounds__(Shape<kTile>::kThreads) render_bwd_kernel(
+__global__ void __launch_bounds__(Shape<kTile>::kThreads, (kTile == 16 ? 9 : 2)) render_bwd_kernel(
     gs_batch batch, gs_cameras cams, const float4* __restrict__ splat, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ ranges, const float* __restrict__ bg, const float* __restrict__ image,
     const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
