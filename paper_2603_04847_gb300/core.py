@@ -333,7 +333,7 @@ def gs_adam_update_groups(groups, beta1, beta2, eps, step, stream=None):
     check(lib.gs_adam_update_groups(arr, len(groups), ctypes.byref(hp), _stream(stream)), "gs_adam_update_groups")
 
 
-def gs_set_tuning(render_fwd_batch: int = 256, render_bwd_batch: int = 128, sort_blocks_per_sm: int = 2):
+def gs_set_tuning(render_fwd_batch: int = 128, render_bwd_batch: int = 64, sort_blocks_per_sm: int = 1):
     lib = _lib.load()
     t = _lib.gs_tuning(int(render_fwd_batch), int(render_bwd_batch), int(sort_blocks_per_sm))
     check(lib.gs_set_tuning(ctypes.byref(t)), "gs_set_tuning")

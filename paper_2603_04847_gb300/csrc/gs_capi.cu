@@ -74,7 +74,7 @@ size_t pose_partial_bytes(int N, const gs_batch& b) {
 }  // namespace
 
 namespace {
-gs_tuning g_tuning = {256, 128, 2};
+gs_tuning g_tuning = {128, 64, 1};  // what the autotuner picks on the benchmark workloads
 }
 
 const gs_tuning& tuning() { return g_tuning; }
