@@ -144,14 +144,81 @@ constexpr int kProjThreads = 128;
 // global memory, loaded with coalesced reads into shared memory transposed
 // (coefficient-major, one padded column per thread) so that each thread then
 // reads its own 3K values without bank conflicts.
+// A full block whose slice is 16-byte aligned issues all its vector loads
+// before the first shared-memory store, so it waits one memory latency
+// rather than one per loop trip.
 template <int KK>
 __device__ inline void load_sh_block(const float* __restrict__ sh, int j0, int n_local,
                                      float (*s_sh)[kProjThreads + 1]) {
   const float* src = sh + (size_t)j0 * KK;
+  if (n_local == kProjThreads && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+    constexpr int kVec = KK * kProjThreads / 4;
+    constexpr int kIt = (kVec + kProjThreads - 1) / kProjThreads;
+    const float4* src4 = reinterpret_cast<const float4*>(src);
+    float4 v[kIt];
+#pragma unroll
+    for (int u = 0; u < kIt; ++u) {
+      const int q = u * kProjThreads + threadIdx.x;
+      if (q < kVec) v[u] = src4[q];
+    }
+#pragma unroll
+    for (int u = 0; u < kIt; ++u) {
+      const int q = u * kProjThreads + threadIdx.x;
+      if (q < kVec) {
+        const float c[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int f = 4 * q + e;
+          const int jl = f / KK;
+          s_sh[f - jl * KK][jl] = c[e];
+        }
+      }
+    }
+    return;
+  }
   const int total = n_local * KK;
   for (int f = threadIdx.x; f < total; f += kProjThreads) {
     const int jl = f / KK;
     s_sh[f - jl * KK][jl] = src[f];
+  }
+}
+
+// dst[f] += column-major shared sums for the block's contiguous slice of
+// [n_local, KK] gradients; the full-block, aligned case reads all of its
+// slice before the first store (one memory latency per block).
+template <int KK>
+__device__ inline void add_sh_block(float* __restrict__ dst, int n_local, float (*s_v)[kProjThreads + 1]) {
+  if (n_local == kProjThreads && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+    constexpr int kVec = KK * kProjThreads / 4;
+    constexpr int kIt = (kVec + kProjThreads - 1) / kProjThreads;
+    float4* dst4 = reinterpret_cast<float4*>(dst);
+    float4 v[kIt];
+#pragma unroll
+    for (int u = 0; u < kIt; ++u) {
+      const int q = u * kProjThreads + threadIdx.x;
+      if (q < kVec) v[u] = dst4[q];
+    }
+#pragma unroll
+    for (int u = 0; u < kIt; ++u) {
+      const int q = u * kProjThreads + threadIdx.x;
+      if (q < kVec) {
+        float c[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int f = 4 * q + e;
+          const int jl = f / KK;
+          c[e] += s_v[f - jl * KK][jl];
+        }
+        dst4[q] = make_float4(c[0], c[1], c[2], c[3]);
+      }
+    }
+    return;
+  }
+  const int total = n_local * KK;
+  for (int f = threadIdx.x; f < total; f += kProjThreads) {
+    const int jl = f / KK;
+    const float gv = s_v[f - jl * KK][jl];
+    if (gv != 0.f) dst[f] += gv;
   }
 }
 
@@ -438,17 +505,29 @@ __global__ void __launch_bounds__(kProjThreads, 3) project_bwd_kernel(gs_gaussia
   }
 
   if (active && any) {
+    // the accumulators are read before any of them is written, so the
+    // thread waits one memory latency for all of them
+    float* gls = dg.log_scale + 3 * (size_t)j;
+    float4* gq = reinterpret_cast<float4*>(dg.quat) + j;
+    float* gm = dg.mean + 3 * (size_t)j;
+    float acc_ls[3], acc_mu[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      acc_ls[k] = gls[k];
+      acc_mu[k] = gm[k];
+    }
+    float4 cur = *gq;
+    float acc_o = dg.opacity_logit[j];
     // --- M = R diag(s): G_R = G_M diag(s), dL/ds_c = sum_r G_M[r][c] R[r][c]
     float GR[9];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
       for (int k = 0; k < 3; ++k) GR[3 * r + k] = GM[3 * r + k] * G.s[k];
-    float* gls = dg.log_scale + 3 * (size_t)j;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const float gs = GM[k] * G.R[k] + GM[3 + k] * G.R[3 + k] + GM[6 + k] * G.R[6 + k];
-      gls[k] += gs * G.s[k];
+      gls[k] = acc_ls[k] + gs * G.s[k];
     }
     const float w = G.qn[0], x = G.qn[1], y = G.qn[2], zq = G.qn[3];
     float vq[4];
@@ -461,30 +540,19 @@ __global__ void __launch_bounds__(kProjThreads, 3) project_bwd_kernel(gs_gaussia
     vq[3] = -4.f * zq * GR[0] - 2.f * w * GR[1] + 2.f * x * GR[2] + 2.f * w * GR[3] -
             4.f * zq * GR[4] + 2.f * y * GR[5] + 2.f * x * GR[6] + 2.f * y * GR[7];
     const float dq = vq[0] * w + vq[1] * x + vq[2] * y + vq[3] * zq;
-    float4* gq = reinterpret_cast<float4*>(dg.quat) + j;
-    float4 cur = *gq;
     cur.x += (vq[0] - dq * w) * G.qinv;
     cur.y += (vq[1] - dq * x) * G.qinv;
     cur.z += (vq[2] - dq * y) * G.qinv;
     cur.w += (vq[3] - dq * zq) * G.qinv;
     *gq = cur;
-    float* gm = dg.mean + 3 * (size_t)j;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) gm[i] += vmu[i];
-    dg.opacity_logit[j] += vol * G.o * (1.f - G.o);
+    for (int i = 0; i < 3; ++i) gm[i] = acc_mu[i] + vmu[i];
+    dg.opacity_logit[j] = acc_o + vol * G.o * (1.f - G.o);
   }
   // SH gradients: through shared memory, then one coalesced read-modify-write
   // of the block's contiguous slice of dg.sh
   __syncthreads();
-  {
-    float* dst = dg.sh + (size_t)j0 * K * 3;
-    const int total = n_local * K * 3;
-    for (int f = threadIdx.x; f < total; f += kProjThreads) {
-      const int jl = f / (K * 3);
-      const float gv = s_vsh[f - jl * K * 3][jl];
-      if (gv != 0.f) dst[f] += gv;
-    }
-  }
+  add_sh_block<K * 3>(dg.sh + (size_t)j0 * K * 3, n_local, s_vsh);
   __syncthreads();
   for (int i = threadIdx.x; i < batch.B * 6; i += blockDim.x) {
     float t = 0.f;
