@@ -29,17 +29,37 @@ struct GaussGeo {
   bool ok;
 };
 
-__device__ inline GaussGeo load_geo(const gs_gaussians& g, int j) {
-  GaussGeo G;
+// The raw parameters of one Gaussian, loaded apart from the arithmetic on
+// them so that a kernel can issue these loads together with its others.
+struct GeoRaw {
+  float mu[3], ls[3];
+  float4 q;
+  float ol;
+};
+
+__device__ inline GeoRaw load_geo_raw(const gs_gaussians& g, int j) {
+  GeoRaw r;
   const float* m = g.mean + 3 * (size_t)j;
   const float* ls = g.log_scale + 3 * (size_t)j;
-  const float4 q = reinterpret_cast<const float4*>(g.quat)[j];
-  G.ol = g.opacity_logit[j];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    r.mu[i] = m[i];
+    r.ls[i] = ls[i];
+  }
+  r.q = reinterpret_cast<const float4*>(g.quat)[j];
+  r.ol = g.opacity_logit[j];
+  return r;
+}
+
+__device__ inline GaussGeo make_geo(const GeoRaw& r) {
+  GaussGeo G;
+  const float4 q = r.q;
+  G.ol = r.ol;
   bool ok = true;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    G.mu[i] = m[i];
-    const float l = ls[i];
+    G.mu[i] = r.mu[i];
+    const float l = r.ls[i];
     ok = ok && finitef(G.mu[i]) && finitef(l);
     G.s[i] = expf(l);
   }
@@ -236,7 +256,7 @@ __global__ void __launch_bounds__(kProjThreads) project_fwd_kernel(gs_gaussians 
   __syncthreads();
   const int j = j0 + threadIdx.x;
   if (j >= N) return;
-  const GaussGeo G = load_geo(g, j);
+  const GaussGeo G = make_geo(load_geo_raw(g, j));
   float shv[K * 3];
 #pragma unroll
   for (int i = 0; i < K * 3; ++i) shv[i] = s_sh[i][threadIdx.x];
@@ -320,19 +340,31 @@ __global__ void __launch_bounds__(kProjThreads, 3) project_bwd_kernel(gs_gaussia
   extern __shared__ float s_dyn[];
   float (*s_sh)[kProjThreads + 1] = reinterpret_cast<float (*)[kProjThreads + 1]>(s_dyn);
   float (*s_vsh)[kProjThreads + 1] = reinterpret_cast<float (*)[kProjThreads + 1]>(s_dyn + K * 3 * (kProjThreads + 1));
-  load_slot_cams(cams, batch, sc);
   for (int i = threadIdx.x; i < (kProjThreads / 32) * GS_MAX_BATCH * 6; i += blockDim.x) (&s_tan[0][0])[i] = 0.f;
   const int N = g.n;
   const int j0 = blockIdx.x * kProjThreads;
   const int n_local = min(kProjThreads, N - j0);
+  const int j = j0 + threadIdx.x;
+  const bool active = j < N;
+  // the parameters and the first view's record are loaded together with
+  // the SH block, before the barrier
+  GeoRaw raw;
+  const float4* vrec = reinterpret_cast<const float4*>(v2d);
+  float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb4 = na;
+  float ncol = 0.f;
+  if (active) {
+    raw = load_geo_raw(g, j);
+    na = vrec[3 * (size_t)j];
+    nb4 = vrec[3 * (size_t)j + 1];
+    ncol = vrec[3 * (size_t)j + 2].x;
+  }
+  load_slot_cams(cams, batch, sc);
   load_sh_block<K * 3>(g.sh, j0, n_local, s_sh);
 #pragma unroll
   for (int i = 0; i < K * 3; ++i) s_vsh[i][threadIdx.x] = 0.f;
   __syncthreads();
-  const int j = j0 + threadIdx.x;
-  const bool active = j < N;
   GaussGeo G;
-  if (active) G = load_geo(g, j);
+  if (active) G = make_geo(raw);
   float vmu[3] = {0.f, 0.f, 0.f};
   float GM[9];
 #pragma unroll
@@ -343,14 +375,6 @@ __global__ void __launch_bounds__(kProjThreads, 3) project_bwd_kernel(gs_gaussia
   // Screen-space gradients of invisible records are zero (the compositing
   // backward zeroes all records first), so every view's record can be read
   // unconditionally; the next view's is loaded while this one is processed.
-  const float4* vrec = reinterpret_cast<const float4*>(v2d);
-  float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb4 = na;
-  float ncol = 0.f;
-  if (active) {
-    na = vrec[3 * (size_t)j];
-    nb4 = vrec[3 * (size_t)j + 1];
-    ncol = vrec[3 * (size_t)j + 2].x;
-  }
   for (int b = 0; b < batch.B; ++b) {
     float tan[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const float4 va = na, vb = nb4;
