@@ -94,25 +94,40 @@ __device__ inline void tile_pixels(int tid, int& lx, int& ly) {
   ly = (w / kWX) * 8 + (l >> 2);
 }
 
-// Bit w set iff the bounding box of the splat's support {q <= q_max} can
-// reach a pixel centre of warp w's 8x8 block in the tile at pixel (x0, y0).
-// The box is widened by 2 % + 0.01 in q and 0.01 px: the FP32 evaluation of
-// alpha for strongly anisotropic conics carries relative errors of that
-// order, so no pixel whose alpha can pass the test is ever skipped.
+// Bit w set iff the splat's support {q <= q_max} can reach a pixel centre
+// of warp w's 8x8 block in the tile at pixel (x0, y0).  The test is exact
+// for the ellipse against the block's rectangle of pixel centres: the
+// minimum of q over the rectangle is 0 when the mean lies inside it, else
+// it is reached on the edge line facing the mean in x or the one in y, where
+// the line minimum of q = c (dy + (b/c) dx)^2 + (det/c) dx^2 (resp. with x, y
+// and a, c exchanged) is taken at the clamped stationary point.  Both forms
+// are sums of non-negative terms, so FP32 evaluation loses nothing to
+// cancellation.  q_max is widened by 2 % + 0.01 and the rectangle by 0.01 px:
+// the FP32 evaluation of alpha for strongly anisotropic conics carries
+// relative errors of that order, so no pixel whose alpha can pass the test
+// is ever skipped.
 template <int kTile>
 __device__ inline uint32_t warp_mask(const float4 xyo, const float4 con, float x0, float y0) {
   constexpr int kWX = Shape<kTile>::kWarpsX;
-  const float detc = con.x * con.z - con.y * con.y;
+  const float a = con.x, b = con.y, c = con.z;
+  const float det = a * c - b * b;
   const float qc = (con.w + 1e-3f) * 1.02f + 0.01f;
-  const float rx = sqrtf(qc * con.z / detc) + 0.01f;
-  const float ry = sqrtf(qc * con.x / detc) + 0.01f;
+  const float ia = __frcp_rn(a), ic = __frcp_rn(c);
+  const float ba = b * ia, bc = b * ic, da = det * ia, dc = det * ic;
   uint32_t m = 0;
 #pragma unroll
   for (int w = 0; w < Shape<kTile>::kWarps; ++w) {
-    const float bx0 = x0 + (float)((w % kWX) * 8) + 0.5f, by0 = y0 + (float)((w / kWX) * 8) + 0.5f;
-    const bool hit = (xyo.x + rx >= bx0) && (xyo.x - rx <= bx0 + 7.f) && (xyo.y + ry >= by0) &&
-                     (xyo.y - ry <= by0 + 7.f);
-    m |= hit ? (1u << w) : 0u;
+    const float bx0 = x0 + (float)((w % kWX) * 8) + 0.49f, by0 = y0 + (float)((w / kWX) * 8) + 0.49f;
+    const float bx1 = bx0 + 7.02f, by1 = by0 + 7.02f;
+    // on the vertical line through the rectangle's x nearest the mean
+    const float dx = fminf(fmaxf(xyo.x, bx0), bx1) - xyo.x;
+    const float ev = fminf(fmaxf(xyo.y - bc * dx, by0), by1) - xyo.y + bc * dx;
+    const float qv = c * ev * ev + dc * dx * dx;
+    // on the horizontal line through the rectangle's y nearest the mean
+    const float dy = fminf(fmaxf(xyo.y, by0), by1) - xyo.y;
+    const float eh = fminf(fmaxf(xyo.x - ba * dy, bx0), bx1) - xyo.x + ba * dy;
+    const float qh = a * eh * eh + da * dy * dy;
+    m |= (fminf(qv, qh) <= qc) ? (1u << w) : 0u;
   }
   return m;
 }
