@@ -274,6 +274,12 @@ class JointStep:
         mark("zero")
         mark("track")
         gs_step_advance(self.step_no)
+        # the pose update (one small kernel, independent of the parameter
+        # update) runs on the side stream beside Adam
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            hp = adam_c(h.lr_pose, h.beta1, h.beta2, h.eps, self.step_no)
+            pose_se3_update(self.T0, self.xi, self.g_tan, self.g_xi, self.m_xi, self.v_xi, hp, self.Rt)
         ext = h.scene_extent
         gs_adam_update_groups([
             (self.g.mean, self.dg.mean, self.m.mean, self.v.mean, h.lr_mean * ext),
@@ -284,8 +290,7 @@ class JointStep:
             (self.g.sh, self.dg.sh, self.m.sh, self.v.sh, h.lr_sh),
             (self.X, self.gX, self.mX, self.vX, h.lr_track * ext)], h.beta1, h.beta2, h.eps, self.step_no)
         mark("adam")
-        hp = adam_c(h.lr_pose, h.beta1, h.beta2, h.eps, self.step_no)
-        pose_se3_update(self.T0, self.xi, self.g_tan, self.g_xi, self.m_xi, self.v_xi, hp, self.Rt)
+        main.wait_stream(side)
         mark("pose")
 
     def kernels_per_step(self) -> int:
