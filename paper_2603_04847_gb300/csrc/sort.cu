@@ -188,7 +188,9 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
   const uint32_t tile_n = min((uint32_t)kTileItems, n - tile0);
 
   // 1. load the keys and rank within the warp
-  uint32_t k[kRounds], v[kRounds], r[kRounds];
+  // ranks within the warp's digit run are < 256 (at most 7 earlier rounds
+  // of 32 plus 31 lanes): four to a register
+  uint32_t k[kRounds], rp[kRounds / 4];
 #pragma unroll
   for (int s = 0; s < kRounds; ++s) {
     const uint32_t li = (uint32_t)(warp * kWarpItems + s * 32 + lane);
@@ -206,19 +208,14 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
       const unsigned m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
       peers &= ((d >> b) & 1u) ? m : ~m;
     }
-    r[s] = valid ? (uint32_t)s_wrun[warp][d] + __popc(peers & lt_mask) : 0u;
+    const uint32_t rank = valid ? (uint32_t)s_wrun[warp][d] + __popc(peers & lt_mask) : 0u;
+    rp[s >> 2] = (s & 3) ? (rp[s >> 2] | (rank << (8 * (s & 3)))) : rank;
     __syncwarp();
     if (valid && (peers & lt_mask) == 0) s_wrun[warp][d] += (uint16_t)__popc(peers);
     __syncwarp();
   }
   __syncthreads();
 
-  // values are first needed in step 4: load them now
-#pragma unroll
-  for (int s = 0; s < kRounds; ++s) {
-    const uint32_t li = (uint32_t)(warp * kWarpItems + s * 32 + lane);
-    v[s] = li < tile_n ? (vin ? vin[tile0 + li] : tile0 + li) : 0u;
-  }
 
   // 2. per digit: offsets of the warps within the tile, the tile's count,
   //    published at once so that successors need not wait for step 5
@@ -247,9 +244,9 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
     const uint32_t li = (uint32_t)(warp * kWarpItems + s * 32 + lane);
     if (li < tile_n) {
       const uint32_t d = (k[s] >> shift) & 0xffu;
-      const uint32_t p = s_dstart[d] + s_wrun[warp][d] + r[s];
+      const uint32_t p = s_dstart[d] + s_wrun[warp][d] + ((rp[s >> 2] >> (8 * (s & 3))) & 0xffu);
       s_keys[p] = k[s];
-      s_vals[p] = v[s];
+      s_vals[p] = vin ? vin[tile0 + li] : tile0 + li;
     }
   }
 
