@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
   // 1. load the keys and rank within the warp
   // ranks within the warp's digit run are < 256 (at most 7 earlier rounds
   // of 32 plus 31 lanes): four to a register
-  uint32_t k[kRounds], rp[kRounds / 4];
+  static_assert(kRounds <= 8, "a rank must fit in 8 bits");
+  uint32_t k[kRounds], rp[(kRounds + 3) / 4];
 #pragma unroll
   for (int s = 0; s < kRounds; ++s) {
     const uint32_t li = (uint32_t)(warp * kWarpItems + s * 32 + lane);
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
   __syncthreads();
 
   // 6. write runs: consecutive threads, consecutive positions of a digit
-#pragma unroll
+#pragma unroll 2
   for (int i = 0; i < kRounds; ++i) {
     const uint32_t p = (uint32_t)(tid + i * kSortThreads);
     if (p < tile_n) {
