@@ -569,14 +569,24 @@ def run_ours(args):
     if use_graph:
         js.capture()
     loss_host = torch.zeros(2, dtype=torch.float64).pin_memory()
-    n_e2e = max(3, args.steps // 2)
+    n_e2e = max(10, args.steps)
     plan = []
-    for i in range(n_e2e):
+    for i in range(n_e2e + 1):
         if batch_list is not None:
             plan.append(batch_list[bcur % len(batch_list)])
             bcur += 1
         else:
             plan.append(None)
+    # one untimed pass first: the first replay of a freshly captured graph
+    # also uploads it to the device
+    ts.put(js.views if plan[0] is None else plan[0].numpy())
+    ts.begin()
+    if plan[0] is not None:
+        set_views_async(js, plan[0])
+    js.run() if use_graph else js.step()
+    ts.end()
+    torch.cuda.synchronize()
+    plan = plan[1:]
     flush.zero_()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
