@@ -16,7 +16,8 @@ Passages restated (GloSplat, arXiv 2603.04847):
   * Eq. 6 (Huber reprojection loss on track points, delta = 1 px);
   * the projection pi(K, T, X) = proj(K (R X + t)) after Algorithm 1;
   * T_i = T_i^(0) (+) dT_i (Algorithm 1), read as Exp(xi) T0.
-Every reading of a point the paper leaves open is listed in the design doc.
+Where the paper leaves a point open the oracle takes the published 3DGS
+convention its rasterizer follows, stated beside the code that applies it.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 (closed forms, invariants, library special cases and central finite

@@ -3,8 +3,9 @@
  *
  * Plain loops, double precision, no tiling except in orc_render_tiled, which
  * exists only to pin the tile-invariance of the support rule.  Each function
- * cites the passage of the paper it restates; the readings of silent or
- * ambiguous points are those listed in DESIGN.md ("Readings").
+ * cites the passage of the paper it restates; a silent or ambiguous point
+ * takes the published 3DGS convention, stated where it is applied (the
+ * compositing constants below, for instance).
  */
 #include "gs_oracle.h"
 

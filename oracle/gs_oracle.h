@@ -10,7 +10,8 @@
  *     "Projection function" bullet after Algorithm 1;
  *   - EWA splatting, SH colour and front-to-back alpha compositing, which the
  *     paper delegates to its rasterizer (Sec. 3.3 "Implementation"); every
- *     point the paper leaves open follows the readings listed in the design doc;
+ *     point the paper leaves open follows the published 3DGS convention,
+ *     stated beside the code that applies it;
  *   - per-pixel brute-force compositing over ALL visible Gaussians of a view,
  *     ordered by (camera depth, index): no tiles;
  *   - hand-derived reverse-mode derivatives of all of the above, the Huber

@@ -1,6 +1,7 @@
 """Pins of the oracle's forward renderer against closed forms, invariants and
 brute force (no GPU).  The oracle restates the rasterizer that Sec. 3.3 of
-the paper delegates to gsplat; the readings are listed in the design doc."""
+the paper delegates to gsplat, with that rasterizer's published conventions
+where the paper is silent."""
 import math
 
 import numpy as np
