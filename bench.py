@@ -8,8 +8,8 @@ Default workload: 8 cameras 1237x822 on a sphere looking at the scene,
 views in every step, batched and captured in a CUDA graph.  Prints one JSON
 line (metric: Mpix*views/s of the joint fwd+bwd step).
 
---impl reference times the FP64 CPU oracle (the only reference this build
-has) on a bounded pixel sample of the same workload.
+--impl reference times the FP64 CPU oracle (the paper publishes no code to
+compare against) on a bounded pixel sample of the same workload.
 --gpus N under torchrun runs N independent replicas (weak scaling).
 """
 from __future__ import annotations
