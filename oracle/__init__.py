@@ -12,7 +12,8 @@ plain lexicographic sort (a library primitive) over the oracle's own
 projected records.
 
 Passages restated (GloSplat, arXiv 2603.04847):
-  * Eq. 5 (L1 part of the photometric loss) and Algorithm 1 "Rasterize";
+  * Eq. 5 (the photometric loss: its L1 part, and its SSIM part in numpy
+    below) and Algorithm 1 "Rasterize";
   * Eq. 6 (Huber reprojection loss on track points, delta = 1 px);
   * the projection pi(K, T, X) = proj(K (R X + t)) after Algorithm 1;
   * T_i = T_i^(0) (+) dT_i (Algorithm 1), read as Exp(xi) T0.
@@ -255,6 +256,88 @@ def l1_loss_grad(image, target, weight=1.0):
     n = image.size
     d = image - target
     return weight * np.abs(d).sum() / n, weight * np.sign(d) / n
+
+
+# SSIM of Eq. 5.  The paper names the term and its weight (lambda_SSIM = 0.2)
+# but not the window; the oracle takes the structural similarity index of
+# Wang et al. (2004) as 3DGS trains with it: an 11x11 Gaussian window with
+# sigma = 1.5 (1-D taps normalised to sum 1), C1 = 0.01^2, C2 = 0.03^2
+# (dynamic range 1), each colour channel on its own, zero padding outside the
+# image with the window not renormalised there, and the mean of the SSIM map
+# over pixels and channels.
+SSIM_RADIUS = 5
+SSIM_SIGMA = 1.5
+SSIM_C1 = 0.01 ** 2
+SSIM_C2 = 0.03 ** 2
+
+
+def ssim_window():
+    """The 1-D taps w[-5..5] of the separable SSIM window."""
+    k = np.arange(-SSIM_RADIUS, SSIM_RADIUS + 1, dtype=np.float64)
+    w = np.exp(-k * k / (2.0 * SSIM_SIGMA * SSIM_SIGMA))
+    return w / w.sum()
+
+
+def window_sum(a):
+    """sum over i, j in [-5, 5] of w[i] w[j] a[y + i, x + j] for every pixel
+    (y, x) of a [H, W, C] array, with a = 0 outside the image."""
+    a = _f64(a)
+    H, W = a.shape[:2]
+    r = SSIM_RADIUS
+    w = ssim_window()
+    pad = np.zeros((H + 2 * r, W + 2 * r) + a.shape[2:])
+    pad[r:r + H, r:r + W] = a
+    out = np.zeros_like(a)
+    for i in range(2 * r + 1):
+        for j in range(2 * r + 1):
+            out += w[i] * w[j] * pad[i:i + H, j:j + W]
+    return out
+
+
+def ssim_map(x, y):
+    """Per-pixel, per-channel SSIM of images x, y [H, W, C] and the local
+    statistics it is made of (window means, variances, covariance)."""
+    x, y = _f64(x), _f64(y)
+    mx, my = window_sum(x), window_sum(y)
+    vx = window_sum(x * x) - mx * mx
+    vy = window_sum(y * y) - my * my
+    cxy = window_sum(x * y) - mx * my
+    A1 = 2.0 * mx * my + SSIM_C1
+    A2 = 2.0 * cxy + SSIM_C2
+    B1 = mx * mx + my * my + SSIM_C1
+    B2 = vx + vy + SSIM_C2
+    return A1 * A2 / (B1 * B2), dict(mx=mx, my=my, vx=vx, vy=vy, cxy=cxy, A1=A1, A2=A2, B1=B1, B2=B2)
+
+
+def photo_loss_grad(image, target, l1_weight=0.8, ssim_weight=0.2):
+    """Eq. 5 for one view (image, target [H, W, 3]):
+        L = l1_weight * mean |x - y| + ssim_weight * (1 - mean SSIM(x, y))
+    (lambda_SSIM = 0.2 gives the paper's weights 0.8 and 0.2) and dL/dx.
+
+    The SSIM gradient is the chain rule through the window sums: with
+    S = A1 A2 / (B1 B2) a function of the window means mx, my and of the
+    window sums Exx = window_sum(x^2), Exy = window_sum(x y) (vx = Exx - mx^2,
+    cxy = Exy - mx my), and g = -ssim_weight / n for n = H W C,
+        M1 = g dS/dmx,  M2 = g dS/dExx,  M3 = g dS/dExy   (per pixel),
+        dL/dx = window_sum(M1) + 2 x window_sum(M2) + y window_sum(M3),
+    the window sum being its own adjoint (symmetric window, zero padding).
+    The L1 part uses sign(0) = 0."""
+    x, y = _f64(image), _f64(target)
+    n = x.size
+    S, st = ssim_map(x, y)
+    mx, my, A1, A2, B1, B2 = st["mx"], st["my"], st["A1"], st["A2"], st["B1"], st["B2"]
+    dS_dmx = 2.0 * my * A2 / (B1 * B2) - 2.0 * mx * S / B1   # vx, cxy held fixed
+    dS_dvx = -S / B2
+    dS_dcxy = 2.0 * A1 / (B1 * B2)
+    g = -ssim_weight / n
+    M1 = g * (dS_dmx - 2.0 * mx * dS_dvx - my * dS_dcxy)
+    M2 = g * dS_dvx
+    M3 = g * dS_dcxy
+    grad = window_sum(M1) + 2.0 * x * window_sum(M2) + y * window_sum(M3)
+    d = x - y
+    grad = grad + l1_weight * np.sign(d) / n
+    loss = l1_weight * np.abs(d).sum() / n + ssim_weight * (1.0 - S.sum() / n)
+    return loss, grad
 
 
 def track(X, obs_point, obs_cam, obs_xy, cams, delta=1.0, weight=1.0, with_abs=False):
