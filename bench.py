@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain one-view-per-launch timing")
+    ap.add_argument("--lambda-ssim", type=float, default=0.0,
+                    help="SSIM weight of Eq. 5 (the paper: 0.2); 0 = the L1 photometric term alone")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run this many eager steps and exit (for ncu launch lists)")
     return ap.parse_args()
@@ -260,7 +262,7 @@ def tuning_trials(tune):
     return out
 
 
-def tune_child(workload, mode, local, cache_path):
+def tune_child(workload, mode, local, cache_path, lambda_ssim=0.0):
     """Autotunes the step of `workload` on GPU `local` and writes the result
     (with its trial timings) to the tuning cache at cache_path."""
     import json
@@ -270,7 +272,7 @@ def tune_child(workload, mode, local, cache_path):
     inp = gpu_inputs(workload, "cuda:%d" % local)
     W = inp["w"]["workload"]
     views = list(range(min(W.batch, W.n_views)))
-    js = make_step(inp, views, mode, W.lambda_ba)
+    js = make_step(inp, views, mode, W.lambda_ba, lambda_ssim=lambda_ssim)
     tune = autotune(js, use_cache=True, cache_path=cache_path)
     with open(cache_path) as f:
         cache = json.load(f)
@@ -280,10 +282,11 @@ def tune_child(workload, mode, local, cache_path):
         json.dump(cache, f)
 
 
-def make_step(inp, views, mode, lambda_ba, tile=16):
+def make_step(inp, views, mode, lambda_ba, tile=16, lambda_ssim=0.0):
     from paper_2603_04847_gb300 import Hyper, JointStep
     js = JointStep(inp["g"], inp["cams"], inp["X"], inp["obs_point"], inp["obs_xy"], inp["view_obs_offset"],
-                   inp["targets"], inp["off"], views, Hyper(lambda_ba=lambda_ba), mode=mode, tile=tile)
+                   inp["targets"], inp["off"], views, Hyper(lambda_ba=lambda_ba, lambda_ssim=lambda_ssim), mode=mode,
+                   tile=tile)
     js.ensure_capacity()
     return js
 
@@ -415,7 +418,7 @@ def run_ours(args):
         import tempfile
         tune_cache = os.path.join(tempfile.mkdtemp(prefix="gs_tune_"), "autotune.json")
         child = multiprocessing.get_context("spawn").Process(
-            target=tune_child, args=(args.workload, args.mode, local, tune_cache))
+            target=tune_child, args=(args.workload, args.mode, local, tune_cache, args.lambda_ssim))
         child.start()
         child.join()
         if child.exitcode != 0:
@@ -424,7 +427,7 @@ def run_ours(args):
     w = inp["w"]
     W = w["workload"]
     views = list(range(min(W.batch, W.n_views)))
-    js = make_step(inp, views, args.mode, W.lambda_ba)
+    js = make_step(inp, views, args.mode, W.lambda_ba, lambda_ssim=args.lambda_ssim)
     # random batches (Algorithm 1, "Sample image indices") when the workload
     # has more views than one batch; all of them share the batch's layout
     n_batches = args.warmup + args.steps + max(3, args.steps // 2) + 8
@@ -549,7 +552,7 @@ def run_ours(args):
     # plain one-view-per-launch form on the same inputs (eager, no graph)
     plain = None
     if not args.no_plain and args.mode == "batched":
-        jp = make_step(inp, views, "plain", W.lambda_ba, tile=js.tile)
+        jp = make_step(inp, views, "plain", W.lambda_ba, tile=js.tile, lambda_ssim=args.lambda_ssim)
         for _ in range(2):
             flush.zero_()
             jp.step()
@@ -622,6 +625,7 @@ def run_ours(args):
                     ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
                     data="synthetic",
                     config=dict(workload_desc(args.workload, w), mode=args.mode,
+                                lambda_ssim=args.lambda_ssim,
                                 graph=use_graph, l2="flushed between steps (256 MB write)",
                                 tuning=dict(tile=tune["tile"], render_fwd_batch=tune["render_fwd_batch"],
                                             render_bwd_batch=tune["render_bwd_batch"],

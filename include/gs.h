@@ -9,6 +9,7 @@
  *   gs_sort_tiles     scan, per-tile duplication, depth-key radix sort and
  *                     per-tile ranges                        ("Rasterize")
  *   gs_render_fwd     front-to-back alpha compositing        ("Rasterize")
+ *   gs_photo_loss     Eq. 5 with its SSIM term: loss and dL/dimage
  *   gs_render_bwd     L1 gradient of Eq. 5 (fused) + compositing backward
  *                     + projection backward with pose gradient
  *                     (Algorithm 1 "Backpropagate"; Sec. 3.3: poses are
@@ -271,6 +272,32 @@ gs_status gs_render_bwd(const gs_gaussians* g, const gs_cameras* cams,
                         float l1_weight, double* loss,
                         const gs_gaussian_grads* dg, double* g_pose_tangent,
                         void* ws, size_t ws_bytes, gs_stream stream);
+
+/*
+ * gs_photo_loss — the photometric loss of Eq. 5 (Algorithm 1, "L_photo")
+ * of every slot of the batch, and its gradient with respect to the rendered
+ * image, to be passed to gs_render_bwd / gs_raster_bwd as v_image:
+ *   loss += sum_b [ l1_weight * mean_b |image - target|
+ *                   + ssim_weight * (1 - mean_b SSIM(image, target)) ]
+ * with mean_b over the 3 W_b H_b values of slot b; the paper's weights are
+ * l1_weight = 1 - lambda_SSIM = 0.8, ssim_weight = lambda_SSIM = 0.2.
+ * v_image [n_pixels,3] = dL/dimage, overwritten (sign(0) = 0 in the L1
+ * part).  SSIM is the index of Wang et al. (2004) as 3DGS trains with it
+ * (the paper fixes only its weight): per colour channel, an 11x11 Gaussian
+ * window of sigma 1.5 whose 1-D taps sum to 1, C1 = 0.01^2, C2 = 0.03^2,
+ * zero padding outside the view (the window is not renormalised there).
+ * image, target: [n_pixels,3] in the batch's pixel layout (slot b's W_b x
+ * H_b pixels, row-major, from px_offset[b]); loss: device double, may be
+ * NULL.  ws: gs_photo_loss_workspace() bytes (nine floats per pixel, the
+ * per-pixel factors of the SSIM gradient).  GS_ERR_ARG for a NULL image,
+ * target or v_image, a negative or non-finite weight, or a short workspace.
+ */
+gs_status gs_photo_loss_workspace(const gs_batch* batch, size_t* ws_bytes);
+gs_status gs_photo_loss(const gs_cameras* cams, const gs_batch* batch,
+                        const float* image, const float* target,
+                        float l1_weight, float ssim_weight, double* loss,
+                        float* v_image, void* ws, size_t ws_bytes,
+                        gs_stream stream);
 
 /*
  * The two halves of gs_render_bwd, callable separately (same arguments and

@@ -6,7 +6,7 @@ The compute path is libgs (hand-written CUDA for sm_103a behind the C ABI
 in include/gs.h).  This package only marshals arguments; it raises if the
 library is missing and has no CPU fallback."""
 from ._lib import GsError, load  # noqa: F401
-from .core import (Batch, Cameras, Gaussians, Projected, TileLists, gs_adam_update, gs_project,  # noqa: F401
-                   gs_render_bwd, gs_render_fwd, gs_sort_tiles, gs_step_advance, gs_zero, pose_se3_update,
+from .core import (Batch, Cameras, Gaussians, Projected, TileLists, gs_adam_update, gs_photo_loss,  # noqa: F401
+                   gs_project, gs_render_bwd, gs_render_fwd, gs_sort_tiles, gs_step_advance, gs_zero, pose_se3_update,
                    track_reproj_fwd_bwd)
 from .step import Hyper, JointStep, Renderer  # noqa: F401

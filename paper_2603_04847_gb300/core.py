@@ -269,6 +269,26 @@ def gs_project_bwd(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, d
           "gs_project_bwd")
 
 
+def photo_loss_workspace_bytes(batch: Batch) -> int:
+    lib = _lib.load()
+    bc = batch.c()
+    ws = ctypes.c_size_t(0)
+    check(lib.gs_photo_loss_workspace(ctypes.byref(bc), ctypes.byref(ws)), "gs_photo_loss_workspace")
+    return ws.value
+
+
+def gs_photo_loss(cams: Cameras, batch: Batch, image: torch.Tensor, target: torch.Tensor, l1_weight: float,
+                  ssim_weight: float, loss, v_image: torch.Tensor, ws: torch.Tensor, Rt=None, stream=None):
+    """Eq. 5 (L1 + SSIM) of every slot: loss (device double [1], may be
+    None) += the batch's photometric loss; v_image [P,3] = dL/dimage."""
+    lib = _lib.load()
+    _need_cuda(image, target, v_image, ws, loss)
+    cc, bc = cams.c(Rt), batch.c()
+    check(lib.gs_photo_loss(ctypes.byref(cc), ctypes.byref(bc), _p(image), _p(target), float(l1_weight),
+                            float(ssim_weight), _p(loss), _p(v_image), _p(ws), ws.numel() * ws.element_size(),
+                            _stream(stream)), "gs_photo_loss")
+
+
 def track_workspace_bytes(batch: Batch) -> int:
     lib = _lib.load()
     ws = ctypes.c_size_t(0)

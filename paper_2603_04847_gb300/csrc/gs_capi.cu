@@ -350,6 +350,30 @@ gs_status gs_step_advance(int32_t* step, gs_stream stream) {
   return GS_OK;
 }
 
+gs_status gs_photo_loss_workspace(const gs_batch* batch, size_t* ws_bytes) {
+  gs_status s;
+  if ((s = check_batch(batch))) return s;
+  if (!ws_bytes) return fail(GS_ERR_ARG, "gs_photo_loss_workspace: null ws_bytes");
+  *ws_bytes = photo_loss_ws_bytes(batch->n_pixels);
+  return GS_OK;
+}
+
+gs_status gs_photo_loss(const gs_cameras* cams, const gs_batch* batch, const float* image, const float* target,
+                        float l1_weight, float ssim_weight, double* loss, float* v_image, void* ws,
+                        size_t ws_bytes, gs_stream stream) {
+  gs_status s;
+  if ((s = check_cameras(cams)) || (s = check_batch(batch))) return s;
+  if (!image || !target || !v_image) return fail(GS_ERR_ARG, "gs_photo_loss: null image, target or v_image");
+  if (!std::isfinite(l1_weight) || !std::isfinite(ssim_weight) || l1_weight < 0.f || ssim_weight < 0.f)
+    return fail(GS_ERR_ARG, "gs_photo_loss: weights must be finite and >= 0");
+  if (batch->n_pixels > 0 && (!ws || ws_bytes < photo_loss_ws_bytes(batch->n_pixels)))
+    return fail(GS_ERR_ARG, "gs_photo_loss: workspace needs %zu bytes", photo_loss_ws_bytes(batch->n_pixels));
+  cudaError_t e = launch_photo_loss(*batch, *cams, image, target, l1_weight, ssim_weight, loss, v_image,
+                                    reinterpret_cast<float*>(ws), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_photo_loss");
+  return GS_OK;
+}
+
 gs_status gs_gather_view_pixels(const float* src, const int64_t* src_px_offset, const gs_cameras* cams,
                                 const gs_batch* batch, int32_t channels, float* dst, gs_stream stream) {
   gs_status s;

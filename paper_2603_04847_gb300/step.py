@@ -12,7 +12,7 @@ import torch
 
 from . import _lib
 from .core import (Batch, Cameras, Gaussians, Projected, TileLists, adam_c, gs_adam_update, gs_adam_update_groups,
-                   gs_gather_view_pixels, gs_project,
+                   gs_gather_view_pixels, gs_photo_loss, gs_project, photo_loss_workspace_bytes,
                    gs_project_bwd, gs_raster_bwd, gs_render_fwd, gs_sort_tiles, gs_step_advance, gs_zero,
                    new_status, pose_se3_update, render_bwd_workspace_bytes, track_reproj_fwd_bwd,
                    track_workspace_bytes)
@@ -112,7 +112,12 @@ class Hyper:
     scene_extent: float = 1.0
     lambda_ba: float = 1e-4       # Sec. 3.3 total objective
     huber_delta: float = 1.0      # Eq. 6
-    l1_weight: float = 1.0        # L1 part of Eq. 5 (SSIM term not in this step)
+    l1_weight: float = 1.0        # weight of the photometric term, Eq. 5
+    # lambda_SSIM of Eq. 5 (the paper trains with 0.2).  0 keeps the L1 part
+    # alone, fused into the compositing backward; > 0 runs gs_photo_loss
+    # (L1 weighted 1 - lambda, SSIM lambda) and feeds its dL/dimage to the
+    # backward.  Read when the batch is set.
+    lambda_ssim: float = 0.0
 
 
 class JointStep:
@@ -178,6 +183,13 @@ class JointStep:
             self.renderers = [Renderer(n, self.cams, b, cap, device=self.device) for b in self.slot_batches]
         self.track_ws = torch.empty(max(track_workspace_bytes(self.batch), 256), dtype=torch.uint8,
                                     device=self.device)
+        self.ssim_on = self.h.lambda_ssim > 0.0
+        for r in self.renderers:
+            r.v_image = r.ws_photo = None
+            if self.ssim_on:
+                r.v_image = torch.empty((max(r.batch.n_pixels, 1), 3), dtype=torch.float32, device=self.device)
+                r.ws_photo = torch.empty(max(photo_loss_workspace_bytes(r.batch), 256), dtype=torch.uint8,
+                                         device=self.device)
         self.target_batch = torch.empty((max(self.batch.n_pixels, 1), 3), dtype=torch.float32,
                                         device=self.device)
         self.load_targets()
@@ -266,8 +278,16 @@ class JointStep:
             else:
                 a, e = int(self.batch.px_offset_host[b]), int(self.batch.px_offset_host[b + 1])
                 tgt = self.target_batch[a:e]
-            r.backward(self.g, self.dg, self.g_tan, target=tgt, l1_weight=h.l1_weight, loss=self.loss[0:1],
-                       Rt=self.Rt, mark=mark)
+            if self.ssim_on:
+                lam = h.lambda_ssim
+                gs_photo_loss(self.cams, r.batch, r.image, tgt, h.l1_weight * (1.0 - lam), h.l1_weight * lam,
+                              self.loss[0:1], r.v_image, r.ws_photo, self.Rt)
+                mark("photo")
+                r.backward(self.g, self.dg, self.g_tan, v_image=r.v_image, loss=self.loss[0:1], Rt=self.Rt,
+                           mark=mark)
+            else:
+                r.backward(self.g, self.dg, self.g_tan, target=tgt, l1_weight=h.l1_weight, loss=self.loss[0:1],
+                           Rt=self.Rt, mark=mark)
         if not joined:
             fork()
             main.wait_stream(side)
@@ -302,6 +322,8 @@ class JointStep:
             # scan 2, expand 1, one per tile pass, ranges 1; render fwd 1;
             # raster bwd 1; project bwd + finalize 2
             per_render += 1 + (1 + 1 + 4 + 2 + 1 + (tbits + 7) // 8 + 1) + 1 + 1 + 2
+            if self.ssim_on:
+                per_render += 2  # photometric loss forward + backward
         # target gather 1, track + finalize 2, step advance 1, Adam (all
         # groups) 1, pose 1
         return per_render + 1 + 2 + 1 + 1 + 1
