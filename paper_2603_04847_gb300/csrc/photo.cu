@@ -14,13 +14,15 @@
 //   dL/dx = w*M1 + 2 x (w*M2) + y (w*M3) + l1_w sign(x - y) / n,
 // the window sum being its own adjoint (symmetric taps, zero padding).
 //
-// Two kernels, one 256-thread block per 16x16 pixel block (a tile of the
-// batch holds one or four of them): the forward stages x and y of one
-// channel with a 5-pixel halo in shared memory, runs the window as a
-// horizontal pass over the 26 staged rows and a vertical pass per pixel,
-// and writes M1..M3 (planar, channel-major) and the block's loss; the
-// backward stages M1..M3 the same way and writes v_image.  Both are bound
-// by FP32 issue (~55 FMAs per window quantity per pixel and channel).
+// Two kernels, one 256-thread block per 32x32 pixel block (a 32-pixel tile
+// of the batch, or four 16-pixel tiles): the forward stages x and y of one
+// channel with a 5-pixel halo in shared memory; the horizontal pass gives
+// each thread four consecutive outputs of a staged row (14 inputs read once
+// for 4 x 5 window sums), the vertical pass four consecutive outputs of a
+// column (14 rows of the five horizontal sums); it writes M1..M3 (planar,
+// channel-major) and the block's loss.  The backward stages M1..M3 the same
+// way and writes v_image.  Shared-memory rows are padded so that both
+// passes are free of bank conflicts.
 #include "gs_internal.h"
 
 namespace gs {
@@ -29,9 +31,11 @@ namespace {
 
 constexpr int kR = 5;              // window radius
 constexpr int kTaps = 2 * kR + 1;  // 11
-constexpr int kBE = 16;            // pixel block edge
-constexpr int kSE = kBE + 2 * kR;  // staged edge: 26
-constexpr int kThreads = kBE * kBE;
+constexpr int kBE = 32;            // pixel block edge
+constexpr int kSE = kBE + 2 * kR;  // staged edge: 42
+constexpr int kThreads = 256;
+constexpr int kRun = 4;            // consecutive outputs per thread in each pass
+constexpr int kRunH5 = 2;          // the forward's horizontal pass (five sums): two
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 
@@ -51,15 +55,16 @@ __device__ inline void window_taps(float* w) {
 
 struct PixBlock {
   int W, H;      // the slot's view size
-  int u0, v0;    // first pixel of the 16x16 block
+  int u0, v0;    // first pixel of the 32x32 block
   int64_t px;    // the slot's first pixel in the batch layout
   float inv_n;   // 1 / (3 W H)
+  int valid;     // 0: this tile anchors no block (16-pixel tiles: odd x or y)
 };
 
-// 16x16 block `sub` of global tile gt (tile edge batch.tile): the slot by
-// binary search over tile_offset.  Thread 0 only.
-__device__ inline void find_pixel_block(const gs_batch& batch, const gs_cameras& cams, int gt, int sub,
-                                        PixBlock* out) {
+// The 32x32 block anchored at global tile gt (tile edge batch.tile, 16 or
+// 32): the slot by binary search over tile_offset.  A 16-pixel tile anchors
+// a block when both of its tile coordinates are even.  Thread 0 only.
+__device__ inline void find_pixel_block(const gs_batch& batch, const gs_cameras& cams, int gt, PixBlock* out) {
   int lo = 0, hi = batch.B - 1;
   while (lo < hi) {  // last slot with tile_offset[slot] <= gt
     const int mid = (lo + hi + 1) >> 1;
@@ -73,28 +78,49 @@ __device__ inline void find_pixel_block(const gs_batch& batch, const gs_cameras&
   const int T = batch.tile;
   const int tiles_x = (b.W + T - 1) / T;
   const int l = gt - batch.tile_offset[lo];
-  const int per = T / kBE;
-  b.u0 = (l % tiles_x) * T + (sub % per) * kBE;
-  b.v0 = (l / tiles_x) * T + (sub / per) * kBE;
+  const int tx = l % tiles_x, ty = l / tiles_x;
+  b.valid = (T == kBE) || ((tx % 2) == 0 && (ty % 2) == 0);
+  b.u0 = tx * T;
+  b.v0 = ty * T;
   b.px = batch.px_offset[lo];
   b.inv_n = 1.f / (3.f * (float)b.W * (float)b.H);
   *out = b;
 }
 
-// Stages channel c of the per-pixel array a (interleaved [.., 3] when
-// planar_stride == 0, else planar a[c * planar_stride + p]) around block b
-// into s (zero outside the view).
-__device__ inline void stage(const float* __restrict__ a, int c, int64_t planar_stride, const PixBlock& b,
-                             float (*s)[kSE + 1]) {
-  for (int i = threadIdx.x; i < kSE * kSE; i += kThreads) {
+// Stages channel c of NA per-pixel arrays around block b into s[0..NA)
+// (zero outside the view).  Array k is interleaved [.., 3] when
+// planar_stride == 0, else planar a[c * planar_stride + p].  Every load of
+// the thread is issued before its first shared-memory store, so a block
+// waits one memory latency per staging, not one per loop trip.
+template <int NA>
+__device__ inline void stage(const float* const* a, int c, int64_t planar_stride, const PixBlock& b,
+                             float (*const* s)[kSE + 1]) {
+  constexpr int kIt = (kSE * kSE + kThreads - 1) / kThreads;
+  // the slot's channel-c base of each array; offsets within a view are
+  // 32-bit (a view holds far fewer than 2^31 values)
+  const float* base[NA];
+  const int step = planar_stride ? 1 : 3;
+#pragma unroll
+  for (int k = 0; k < NA; ++k) base[k] = a[k] + (planar_stride ? c * planar_stride + b.px : 3 * b.px + c);
+  float val[NA][kIt];
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) {
+    const int i = threadIdx.x + it * kThreads;
     const int r = i / kSE, q = i - r * kSE;
     const int u = b.u0 - kR + q, v = b.v0 - kR + r;
-    float val = 0.f;
-    if (u >= 0 && u < b.W && v >= 0 && v < b.H) {
-      const int64_t p = b.px + (int64_t)v * b.W + u;
-      val = planar_stride ? a[c * planar_stride + p] : a[3 * p + c];
+    const bool in = i < kSE * kSE && u >= 0 && u < b.W && v >= 0 && v < b.H;
+    const int off = (v * b.W + u) * step;
+#pragma unroll
+    for (int k = 0; k < NA; ++k) val[k][it] = in ? base[k][off] : 0.f;
+  }
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) {
+    const int i = threadIdx.x + it * kThreads;
+    if (i < kSE * kSE) {
+      const int r = i / kSE, q = i - r * kSE;
+#pragma unroll
+      for (int k = 0; k < NA; ++k) s[k][r][q] = val[k][it];
     }
-    s[r][q] = val;
   }
 }
 
@@ -109,77 +135,121 @@ __device__ inline float block_sum(float v, float* red) {
   return t;  // valid in thread 0
 }
 
-__global__ void __launch_bounds__(kThreads) photo_fwd_kernel(gs_batch batch, gs_cameras cams,
+// Horizontal window sums of NQ staged arrays: hs[q][r][q0 + o] for the
+// kRun outputs of each task (staged row r, first output q0); each input is
+// read once per task.  f(j) returns the NQ values of staged column q0 + j.
+template <int NQ, int RUN, typename F>
+__device__ inline void horizontal_pass(const float* w, float (*hs)[kSE][kBE + 1], F f) {
+  constexpr int kGroups = kBE / RUN;
+  for (int t = threadIdx.x; t < kSE * kGroups; t += kThreads) {
+    const int r = t / kGroups, q0 = (t % kGroups) * RUN;
+    float a[RUN][NQ];
+#pragma unroll
+    for (int o = 0; o < RUN; ++o)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) a[o][q] = 0.f;
+#pragma unroll
+    for (int j = 0; j < RUN + 2 * kR; ++j) {
+      float val[NQ];
+      f(r, q0 + j, val);
+#pragma unroll
+      for (int o = 0; o < RUN; ++o) {
+        const int k = j - o;
+        if (k >= 0 && k < kTaps) {
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) a[o][q] = fmaf(w[k], val[q], a[o][q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < RUN; ++o)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) hs[q][r][q0 + o] = a[o][q];
+  }
+}
+
+// Vertical window sums of the NQ horizontal sums for the RUN outputs of
+// column col from row row0: m[o][q].
+template <int NQ, int RUN>
+__device__ inline void vertical_pass(const float* w, float (*hs)[kSE][kBE + 1], int col, int row0,
+                                     float (*m)[NQ]) {
+#pragma unroll
+  for (int o = 0; o < RUN; ++o)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) m[o][q] = 0.f;
+#pragma unroll
+  for (int j = 0; j < RUN + 2 * kR; ++j) {
+    float val[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) val[q] = hs[q][row0 + j][col];
+#pragma unroll
+    for (int o = 0; o < RUN; ++o) {
+      const int k = j - o;
+      if (k >= 0 && k < kTaps) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) m[o][q] = fmaf(w[k], val[q], m[o][q]);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 3) photo_fwd_kernel(gs_batch batch, gs_cameras cams,
                                                              const float* __restrict__ image,
                                                              const float* __restrict__ target, float l1_w,
                                                              float ssim_w, double* loss, float* __restrict__ m1,
                                                              float* __restrict__ m2, float* __restrict__ m3) {
   __shared__ float sx[kSE][kSE + 1], sy[kSE][kSE + 1];
-  __shared__ float hs[5][kSE][kBE];  // horizontal sums of x, y, x^2, y^2, x y
+  __shared__ float hs[5][kSE][kBE + 1];  // horizontal sums of x, y, x^2, y^2, x y
   __shared__ PixBlock blk;
   __shared__ float red[kThreads / 32];
   float w[kTaps];
   window_taps(w);
-  const int tx = threadIdx.x % kBE, ty = threadIdx.x / kBE;
-  const int64_t P = batch.n_pixels;
-  const int subs = (batch.tile / kBE) * (batch.tile / kBE);
+  if (threadIdx.x == 0) find_pixel_block(batch, cams, blockIdx.x, &blk);
+  __syncthreads();
+  const PixBlock b = blk;
   float acc = 0.f;
-  for (int sub = 0; sub < subs; ++sub) {
-    if (threadIdx.x == 0) find_pixel_block(batch, cams, blockIdx.x, sub, &blk);
-    __syncthreads();
-    const PixBlock b = blk;
-    __syncthreads();  // blk is rewritten by the next sub-block
-    if (b.u0 >= b.W || b.v0 >= b.H) continue;  // block-uniform
-    const int u = b.u0 + tx, v = b.v0 + ty;
-    const bool inside = u < b.W && v < b.H;
-    const int64_t p = b.px + (int64_t)v * b.W + u;
+  if (b.valid && b.u0 < b.W && b.v0 < b.H) {  // block-uniform
+    const int64_t P = batch.n_pixels;
+    const int col = threadIdx.x % kBE, row0 = (threadIdx.x / kBE) * kRun;
     for (int c = 0; c < 3; ++c) {
-      stage(image, c, 0, b, sx);
-      stage(target, c, 0, b, sy);
+      {
+        const float* src[2] = {image, target};
+        float (*dst[2])[kSE + 1] = {sx, sy};
+        stage<2>(src, c, 0, b, dst);
+      }
       __syncthreads();
-      for (int i = threadIdx.x; i < kSE * kBE; i += kThreads) {
-        const int r = i / kBE, q = i - r * kBE;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+      horizontal_pass<5, kRunH5>(w, hs, [&](int r, int q, float* val) {
+        const float xv = sx[r][q], yv = sy[r][q];
+        val[0] = xv;
+        val[1] = yv;
+        val[2] = xv * xv;
+        val[3] = yv * yv;
+        val[4] = xv * yv;
+      });
+      __syncthreads();
+      float m[kRun][5];
+      vertical_pass<5, kRun>(w, hs, col, row0, m);
 #pragma unroll
-        for (int k = 0; k < kTaps; ++k) {
-          const float xv = sx[r][q + k], yv = sy[r][q + k];
-          a0 = fmaf(w[k], xv, a0);
-          a1 = fmaf(w[k], yv, a1);
-          a2 = fmaf(w[k], xv * xv, a2);
-          a3 = fmaf(w[k], yv * yv, a3);
-          a4 = fmaf(w[k], xv * yv, a4);
+      for (int o = 0; o < kRun; ++o) {
+        const int u = b.u0 + col, v = b.v0 + row0 + o;
+        if (u < b.W && v < b.H) {
+          const float mx = m[o][0], my = m[o][1];
+          const float vx = m[o][2] - mx * mx, vy = m[o][3] - my * my, cxy = m[o][4] - mx * my;
+          const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
+          const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
+          const float D = 1.f / (B1 * B2);
+          const float S = A1 * A2 * D;
+          const float dS_dmx = 2.f * my * A2 * D - 2.f * mx * S / B1;
+          const float dS_dvx = -S / B2;
+          const float dS_dcxy = 2.f * A1 * D;
+          const float g = -ssim_w * b.inv_n;
+          const int64_t p = b.px + (int64_t)v * b.W + u;
+          m1[c * P + p] = g * (dS_dmx - 2.f * mx * dS_dvx - my * dS_dcxy);
+          m2[c * P + p] = g * dS_dvx;
+          m3[c * P + p] = g * dS_dcxy;
+          const float d = sx[row0 + o + kR][col + kR] - sy[row0 + o + kR][col + kR];
+          acc += b.inv_n * (ssim_w * (1.f - S) + l1_w * fabsf(d));
         }
-        hs[0][r][q] = a0;
-        hs[1][r][q] = a1;
-        hs[2][r][q] = a2;
-        hs[3][r][q] = a3;
-        hs[4][r][q] = a4;
-      }
-      __syncthreads();
-      float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
-#pragma unroll
-      for (int k = 0; k < kTaps; ++k) {
-        mx = fmaf(w[k], hs[0][ty + k][tx], mx);
-        my = fmaf(w[k], hs[1][ty + k][tx], my);
-        exx = fmaf(w[k], hs[2][ty + k][tx], exx);
-        eyy = fmaf(w[k], hs[3][ty + k][tx], eyy);
-        exy = fmaf(w[k], hs[4][ty + k][tx], exy);
-      }
-      if (inside) {
-        const float vx = exx - mx * mx, vy = eyy - my * my, cxy = exy - mx * my;
-        const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
-        const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
-        const float D = 1.f / (B1 * B2);
-        const float S = A1 * A2 * D;
-        const float dS_dmx = 2.f * my * A2 * D - 2.f * mx * S / B1;
-        const float dS_dvx = -S / B2;
-        const float dS_dcxy = 2.f * A1 * D;
-        const float g = -ssim_w * b.inv_n;
-        m1[c * P + p] = g * (dS_dmx - 2.f * mx * dS_dvx - my * dS_dcxy);
-        m2[c * P + p] = g * dS_dvx;
-        m3[c * P + p] = g * dS_dcxy;
-        const float d = sx[ty + kR][tx + kR] - sy[ty + kR][tx + kR];
-        acc += b.inv_n * (ssim_w * (1.f - S) + l1_w * fabsf(d));
       }
       __syncthreads();  // the staged arrays are rewritten for the next channel
     }
@@ -188,7 +258,7 @@ __global__ void __launch_bounds__(kThreads) photo_fwd_kernel(gs_batch batch, gs_
   if (threadIdx.x == 0 && loss != nullptr && t != 0.f) atomicAdd(loss, (double)t);
 }
 
-__global__ void __launch_bounds__(kThreads) photo_bwd_kernel(gs_batch batch, gs_cameras cams,
+__global__ void __launch_bounds__(kThreads, 3) photo_bwd_kernel(gs_batch batch, gs_cameras cams,
                                                              const float* __restrict__ image,
                                                              const float* __restrict__ target, float l1_w,
                                                              const float* __restrict__ m1,
@@ -196,56 +266,43 @@ __global__ void __launch_bounds__(kThreads) photo_bwd_kernel(gs_batch batch, gs_
                                                              const float* __restrict__ m3,
                                                              float* __restrict__ v_image) {
   __shared__ float s1[kSE][kSE + 1], s2[kSE][kSE + 1], s3[kSE][kSE + 1];
-  __shared__ float hs[3][kSE][kBE];
+  __shared__ float hs[3][kSE][kBE + 1];
   __shared__ PixBlock blk;
   float w[kTaps];
   window_taps(w);
-  const int tx = threadIdx.x % kBE, ty = threadIdx.x / kBE;
+  if (threadIdx.x == 0) find_pixel_block(batch, cams, blockIdx.x, &blk);
+  __syncthreads();
+  const PixBlock b = blk;
+  if (!(b.valid && b.u0 < b.W && b.v0 < b.H)) return;  // block-uniform
   const int64_t P = batch.n_pixels;
-  const int subs = (batch.tile / kBE) * (batch.tile / kBE);
-  for (int sub = 0; sub < subs; ++sub) {
-    if (threadIdx.x == 0) find_pixel_block(batch, cams, blockIdx.x, sub, &blk);
+  const int col = threadIdx.x % kBE, row0 = (threadIdx.x / kBE) * kRun;
+  for (int c = 0; c < 3; ++c) {
+    {
+      const float* src[3] = {m1, m2, m3};
+      float (*dst[3])[kSE + 1] = {s1, s2, s3};
+      stage<3>(src, c, P, b, dst);
+    }
     __syncthreads();
-    const PixBlock b = blk;
+    horizontal_pass<3, kRun>(w, hs, [&](int r, int q, float* val) {
+      val[0] = s1[r][q];
+      val[1] = s2[r][q];
+      val[2] = s3[r][q];
+    });
     __syncthreads();
-    if (b.u0 >= b.W || b.v0 >= b.H) continue;  // block-uniform
-    const int u = b.u0 + tx, v = b.v0 + ty;
-    const bool inside = u < b.W && v < b.H;
-    const int64_t p = b.px + (int64_t)v * b.W + u;
-    for (int c = 0; c < 3; ++c) {
-      stage(m1, c, P, b, s1);
-      stage(m2, c, P, b, s2);
-      stage(m3, c, P, b, s3);
-      __syncthreads();
-      for (int i = threadIdx.x; i < kSE * kBE; i += kThreads) {
-        const int r = i / kBE, q = i - r * kBE;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    float f[kRun][3];
+    vertical_pass<3, kRun>(w, hs, col, row0, f);
 #pragma unroll
-        for (int k = 0; k < kTaps; ++k) {
-          a0 = fmaf(w[k], s1[r][q + k], a0);
-          a1 = fmaf(w[k], s2[r][q + k], a1);
-          a2 = fmaf(w[k], s3[r][q + k], a2);
-        }
-        hs[0][r][q] = a0;
-        hs[1][r][q] = a1;
-        hs[2][r][q] = a2;
-      }
-      __syncthreads();
-      float f1 = 0.f, f2 = 0.f, f3 = 0.f;
-#pragma unroll
-      for (int k = 0; k < kTaps; ++k) {
-        f1 = fmaf(w[k], hs[0][ty + k][tx], f1);
-        f2 = fmaf(w[k], hs[1][ty + k][tx], f2);
-        f3 = fmaf(w[k], hs[2][ty + k][tx], f3);
-      }
-      if (inside) {
+    for (int o = 0; o < kRun; ++o) {
+      const int u = b.u0 + col, v = b.v0 + row0 + o;
+      if (u < b.W && v < b.H) {
+        const int64_t p = b.px + (int64_t)v * b.W + u;
         const float xv = image[3 * p + c], yv = target[3 * p + c];
         const float d = xv - yv;
         const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-        v_image[3 * p + c] = f1 + 2.f * xv * f2 + yv * f3 + l1_w * b.inv_n * sgn;
+        v_image[3 * p + c] = f[o][0] + 2.f * xv * f[o][1] + yv * f[o][2] + l1_w * b.inv_n * sgn;
       }
-      __syncthreads();
     }
+    __syncthreads();
   }
 }
 
