@@ -288,9 +288,11 @@ gs_status gs_render_bwd(const gs_gaussians* g, const gs_cameras* cams,
  * zero padding outside the view (the window is not renormalised there).
  * image, target: [n_pixels,3] in the batch's pixel layout (slot b's W_b x
  * H_b pixels, row-major, from px_offset[b]); loss: device double, may be
- * NULL.  ws: gs_photo_loss_workspace() bytes (nine floats per pixel, the
- * per-pixel factors of the SSIM gradient).  GS_ERR_ARG for a NULL image,
- * target or v_image, a negative or non-finite weight, or a short workspace.
+ * NULL.  ws: gs_photo_loss_workspace() bytes, 4-byte aligned (nine floats
+ * per pixel, the per-pixel factors of the SSIM gradient, and a list of the
+ * batch's 32x32 pixel blocks).  GS_ERR_ARG for a NULL image, target or
+ * v_image, a negative or non-finite weight, or a short or misaligned
+ * workspace.
  */
 gs_status gs_photo_loss_workspace(const gs_batch* batch, size_t* ws_bytes);
 gs_status gs_photo_loss(const gs_cameras* cams, const gs_batch* batch,

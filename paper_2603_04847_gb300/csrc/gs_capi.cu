@@ -354,7 +354,7 @@ gs_status gs_photo_loss_workspace(const gs_batch* batch, size_t* ws_bytes) {
   gs_status s;
   if ((s = check_batch(batch))) return s;
   if (!ws_bytes) return fail(GS_ERR_ARG, "gs_photo_loss_workspace: null ws_bytes");
-  *ws_bytes = photo_loss_ws_bytes(batch->n_pixels);
+  *ws_bytes = photo_loss_ws_bytes(batch->n_pixels, batch->n_tiles);
   return GS_OK;
 }
 
@@ -366,8 +366,10 @@ gs_status gs_photo_loss(const gs_cameras* cams, const gs_batch* batch, const flo
   if (!image || !target || !v_image) return fail(GS_ERR_ARG, "gs_photo_loss: null image, target or v_image");
   if (!std::isfinite(l1_weight) || !std::isfinite(ssim_weight) || l1_weight < 0.f || ssim_weight < 0.f)
     return fail(GS_ERR_ARG, "gs_photo_loss: weights must be finite and >= 0");
-  if (batch->n_pixels > 0 && (!ws || ws_bytes < photo_loss_ws_bytes(batch->n_pixels)))
-    return fail(GS_ERR_ARG, "gs_photo_loss: workspace needs %zu bytes", photo_loss_ws_bytes(batch->n_pixels));
+  const size_t need = photo_loss_ws_bytes(batch->n_pixels, batch->n_tiles);
+  if (batch->n_pixels > 0 && (!ws || ws_bytes < need))
+    return fail(GS_ERR_ARG, "gs_photo_loss: workspace needs %zu bytes", need);
+  if (!aligned(ws, 4)) return fail(GS_ERR_ARG, "gs_photo_loss: workspace must be 4-byte aligned");
   cudaError_t e = launch_photo_loss(*batch, *cams, image, target, l1_weight, ssim_weight, loss, v_image,
                                     reinterpret_cast<float*>(ws), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "gs_photo_loss");

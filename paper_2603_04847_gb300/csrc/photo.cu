@@ -135,6 +135,29 @@ __device__ inline float block_sum(float v, float* red) {
   return t;  // valid in thread 0
 }
 
+// The tiles of the batch that anchor a 32x32 block (all of them for 32-pixel
+// tiles, those with both tile coordinates even for 16-pixel ones), compacted
+// into list[0 .. *count) in no particular order (each block writes its own
+// pixels; only the loss's summation order depends on it).
+__global__ void __launch_bounds__(256) photo_blocks_kernel(gs_batch batch, gs_cameras cams, uint32_t* count,
+                                                           uint32_t* list) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  bool valid = false;
+  if (gt < batch.n_tiles) {
+    PixBlock b;
+    find_pixel_block(batch, cams, gt, &b);
+    valid = b.valid;
+  }
+  const unsigned ballot = __ballot_sync(0xffffffffu, valid);
+  if (ballot == 0u) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(ballot) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(ballot));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (valid) list[base + __popc(ballot & ((1u << lane) - 1u))] = (uint32_t)gt;
+}
+
 // Horizontal window sums of NQ staged arrays: hs[q][r][q0 + o] for the
 // kRun outputs of each task (staged row r, first output q0); each input is
 // read once per task.  f(j) returns the NQ values of staged column q0 + j.
@@ -194,6 +217,8 @@ __device__ inline void vertical_pass(const float* w, float (*hs)[kSE][kBE + 1], 
 }
 
 __global__ void __launch_bounds__(kThreads, 3) photo_fwd_kernel(gs_batch batch, gs_cameras cams,
+                                                             const uint32_t* __restrict__ count,
+                                                             const uint32_t* __restrict__ list,
                                                              const float* __restrict__ image,
                                                              const float* __restrict__ target, float l1_w,
                                                              float ssim_w, double* loss, float* __restrict__ m1,
@@ -202,9 +227,10 @@ __global__ void __launch_bounds__(kThreads, 3) photo_fwd_kernel(gs_batch batch, 
   __shared__ float hs[5][kSE][kBE + 1];  // horizontal sums of x, y, x^2, y^2, x y
   __shared__ PixBlock blk;
   __shared__ float red[kThreads / 32];
+  if (blockIdx.x >= *count) return;  // the grid is sized for every tile
+  if (threadIdx.x == 0) find_pixel_block(batch, cams, (int)list[blockIdx.x], &blk);
   float w[kTaps];
   window_taps(w);
-  if (threadIdx.x == 0) find_pixel_block(batch, cams, blockIdx.x, &blk);
   __syncthreads();
   const PixBlock b = blk;
   float acc = 0.f;
@@ -259,6 +285,8 @@ __global__ void __launch_bounds__(kThreads, 3) photo_fwd_kernel(gs_batch batch, 
 }
 
 __global__ void __launch_bounds__(kThreads, 3) photo_bwd_kernel(gs_batch batch, gs_cameras cams,
+                                                             const uint32_t* __restrict__ count,
+                                                             const uint32_t* __restrict__ list,
                                                              const float* __restrict__ image,
                                                              const float* __restrict__ target, float l1_w,
                                                              const float* __restrict__ m1,
@@ -268,9 +296,10 @@ __global__ void __launch_bounds__(kThreads, 3) photo_bwd_kernel(gs_batch batch, 
   __shared__ float s1[kSE][kSE + 1], s2[kSE][kSE + 1], s3[kSE][kSE + 1];
   __shared__ float hs[3][kSE][kBE + 1];
   __shared__ PixBlock blk;
+  if (blockIdx.x >= *count) return;  // the grid is sized for every tile
+  if (threadIdx.x == 0) find_pixel_block(batch, cams, (int)list[blockIdx.x], &blk);
   float w[kTaps];
   window_taps(w);
-  if (threadIdx.x == 0) find_pixel_block(batch, cams, blockIdx.x, &blk);
   __syncthreads();
   const PixBlock b = blk;
   if (!(b.valid && b.u0 < b.W && b.v0 < b.H)) return;  // block-uniform
@@ -308,7 +337,9 @@ __global__ void __launch_bounds__(kThreads, 3) photo_bwd_kernel(gs_batch batch, 
 
 }  // namespace
 
-size_t photo_loss_ws_bytes(int64_t n_pixels) { return (size_t)n_pixels * 9 * sizeof(float); }
+size_t photo_loss_ws_bytes(int64_t n_pixels, int32_t n_tiles) {
+  return (size_t)n_pixels * 9 * sizeof(float) + ((size_t)n_tiles + 1) * sizeof(uint32_t);
+}
 
 cudaError_t launch_photo_loss(const gs_batch& batch, const gs_cameras& cams, const float* image,
                               const float* target, float l1_weight, float ssim_weight, double* loss,
@@ -318,10 +349,15 @@ cudaError_t launch_photo_loss(const gs_batch& batch, const gs_cameras& cams, con
   float* m1 = ws;
   float* m2 = ws + 3 * P;
   float* m3 = ws + 6 * P;
-  photo_fwd_kernel<<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, image, target, l1_weight, ssim_weight, loss,
-                                                       m1, m2, m3);
-  photo_bwd_kernel<<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, image, target, l1_weight, m1, m2, m3,
-                                                       v_image);
+  uint32_t* count = reinterpret_cast<uint32_t*>(ws + 9 * P);
+  uint32_t* list = count + 1;
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  photo_blocks_kernel<<<(batch.n_tiles + 255) / 256, 256, 0, st>>>(batch, cams, count, list);
+  photo_fwd_kernel<<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, count, list, image, target, l1_weight,
+                                                       ssim_weight, loss, m1, m2, m3);
+  photo_bwd_kernel<<<batch.n_tiles, kThreads, 0, st>>>(batch, cams, count, list, image, target, l1_weight, m1, m2,
+                                                       m3, v_image);
   return cudaGetLastError();
 }
 

@@ -323,7 +323,7 @@ class JointStep:
             # raster bwd 1; project bwd + finalize 2
             per_render += 1 + (1 + 1 + 4 + 2 + 1 + (tbits + 7) // 8 + 1) + 1 + 1 + 2
             if self.ssim_on:
-                per_render += 2  # photometric loss forward + backward
+                per_render += 3  # photometric loss: block list, forward, backward
         # target gather 1, track + finalize 2, step advance 1, Adam (all
         # groups) 1, pose 1
         return per_render + 1 + 2 + 1 + 1 + 1
