@@ -306,6 +306,16 @@ __global__ void __launch_bounds__(kThreads, 3) photo_bwd_kernel(gs_batch batch, 
   const int64_t P = batch.n_pixels;
   const int col = threadIdx.x % kBE, row0 = (threadIdx.x / kBE) * kRun;
   for (int c = 0; c < 3; ++c) {
+    // this thread's four pixels of the channel, read along with the staging
+    float xv[kRun], yv[kRun];
+#pragma unroll
+    for (int o = 0; o < kRun; ++o) {
+      const int u = b.u0 + col, v = b.v0 + row0 + o;
+      const int64_t p = b.px + (int64_t)v * b.W + u;
+      const bool in = u < b.W && v < b.H;
+      xv[o] = in ? image[3 * p + c] : 0.f;
+      yv[o] = in ? target[3 * p + c] : 0.f;
+    }
     {
       const float* src[3] = {m1, m2, m3};
       float (*dst[3])[kSE + 1] = {s1, s2, s3};
@@ -325,10 +335,9 @@ __global__ void __launch_bounds__(kThreads, 3) photo_bwd_kernel(gs_batch batch, 
       const int u = b.u0 + col, v = b.v0 + row0 + o;
       if (u < b.W && v < b.H) {
         const int64_t p = b.px + (int64_t)v * b.W + u;
-        const float xv = image[3 * p + c], yv = target[3 * p + c];
-        const float d = xv - yv;
+        const float d = xv[o] - yv[o];
         const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-        v_image[3 * p + c] = f[o][0] + 2.f * xv * f[o][1] + yv * f[o][2] + l1_w * b.inv_n * sgn;
+        v_image[3 * p + c] = f[o][0] + 2.f * xv[o] * f[o][1] + yv[o] * f[o][2] + l1_w * b.inv_n * sgn;
       }
     }
     __syncthreads();
