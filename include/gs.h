@@ -292,7 +292,7 @@ gs_status gs_render_bwd(const gs_gaussians* g, const gs_cameras* cams,
  * per pixel, the per-pixel factors of the SSIM gradient, and a list of the
  * batch's 32x32 pixel blocks).  GS_ERR_ARG for a NULL image, target or
  * v_image, a negative or non-finite weight, or a short or misaligned
- * workspace.
+ * workspace; GS_ERR_UNSUPPORTED above (2^31 - 1) / 3 pixels in the batch.
  */
 gs_status gs_photo_loss_workspace(const gs_batch* batch, size_t* ws_bytes);
 gs_status gs_photo_loss(const gs_cameras* cams, const gs_batch* batch,

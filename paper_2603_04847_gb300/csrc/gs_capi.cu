@@ -366,6 +366,9 @@ gs_status gs_photo_loss(const gs_cameras* cams, const gs_batch* batch, const flo
   if (!image || !target || !v_image) return fail(GS_ERR_ARG, "gs_photo_loss: null image, target or v_image");
   if (!std::isfinite(l1_weight) || !std::isfinite(ssim_weight) || l1_weight < 0.f || ssim_weight < 0.f)
     return fail(GS_ERR_ARG, "gs_photo_loss: weights must be finite and >= 0");
+  // the kernels index a view's values with 32-bit offsets
+  if (batch->n_pixels > (int64_t)(INT32_MAX / 3))
+    return fail(GS_ERR_UNSUPPORTED, "gs_photo_loss: more than %d pixels in the batch", INT32_MAX / 3);
   const size_t need = photo_loss_ws_bytes(batch->n_pixels, batch->n_tiles);
   if (batch->n_pixels > 0 && (!ws || ws_bytes < need))
     return fail(GS_ERR_ARG, "gs_photo_loss: workspace needs %zu bytes", need);

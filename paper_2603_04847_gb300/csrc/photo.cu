@@ -63,7 +63,7 @@ struct PixBlock {
 
 // The 32x32 block anchored at global tile gt (tile edge batch.tile, 16 or
 // 32): the slot by binary search over tile_offset.  A 16-pixel tile anchors
-// a block when both of its tile coordinates are even.  Thread 0 only.
+// a block when both of its tile coordinates are even.  One thread's work.
 __device__ inline void find_pixel_block(const gs_batch& batch, const gs_cameras& cams, int gt, PixBlock* out) {
   int lo = 0, hi = batch.B - 1;
   while (lo < hi) {  // last slot with tile_offset[slot] <= gt
