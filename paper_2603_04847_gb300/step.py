@@ -118,6 +118,10 @@ class Hyper:
     # (L1 weighted 1 - lambda, SSIM lambda) and feeds its dL/dimage to the
     # backward.  Read when the batch is set.
     lambda_ssim: float = 0.0
+    # The paper's ablation variants (Sec. 4 ablations): freeze_poses keeps
+    # T = T0 (no pose update); lambda_ba = 0 is the photometric-only variant
+    # (the track term is not run at all).
+    freeze_poses: bool = False
 
 
 class JointStep:
@@ -135,8 +139,12 @@ class JointStep:
     def __init__(self, gaussians: Gaussians, cams: Cameras, X: torch.Tensor, obs_point: torch.Tensor,
                  obs_xy: torch.Tensor, view_obs_offset: torch.Tensor, targets: torch.Tensor,
                  target_px_offset: np.ndarray, views, hyper: Hyper = None, mode: str = "batched",
-                 capacity: int = 0, device="cuda", tile: int = 16):
+                 capacity: int = 0, device="cuda", tile: int = 16, merged_tracks: bool = False):
+        # merged_tracks: the "merged tracks" ablation variant, X_k = mu of a
+        # Gaussian (obs_point then indexes Gaussians; X is ignored): the track
+        # term reads the Gaussian means and adds its gradient into theirs
         self.h = hyper or Hyper()
+        self.merged_tracks = bool(merged_tracks)
         self.tile = int(tile)
         self.mode = mode
         self.g = gaussians
@@ -152,8 +160,10 @@ class JointStep:
         self.m_xi = torch.zeros_like(self.xi)
         self.v_xi = torch.zeros_like(self.xi)
         self.g_tan = torch.zeros((V, 6), dtype=torch.float64, device=device)
+        if self.merged_tracks:
+            X = self.g.mean
         self.X = X
-        self.gX = torch.zeros_like(X)
+        self.gX = self.dg.mean if self.merged_tracks else torch.zeros_like(X)
         self.mX = torch.zeros_like(X)
         self.vX = torch.zeros_like(X)
         self.obs_point, self.obs_xy, self.view_obs_offset = obs_point, obs_xy, view_obs_offset
@@ -257,15 +267,18 @@ class JointStep:
         def fork():
             side.wait_stream(main)
             with torch.cuda.stream(side):
-                for t in self.dg.tensors() + [self.gX, self.g_tan, self.loss, self.n_masked]:
+                extra = [] if self.merged_tracks else [self.gX]   # merged: gX is dg.mean
+                for t in self.dg.tensors() + extra + [self.g_tan, self.loss, self.n_masked]:
                     gs_zero(t)
                 gs_gather_view_pixels(self.targets, self.target_px_offset_dev, self.cams, self.batch,
                                       self.target_batch)
                 # the track term: done before the join, so its += into the
-                # pose tangent precedes the projection backward's
-                track_reproj_fwd_bwd(self.X, self.obs_point, self.obs_xy, self.view_obs_offset, self.cams,
-                                     self.batch, h.huber_delta, h.lambda_ba, self.loss[1:2], self.gX, self.g_tan,
-                                     self.n_masked, self.track_ws, self.Rt)
+                # pose tangent (and, merged, into dg.mean) precedes the
+                # projection backward's; not run at all when lambda_BA = 0
+                if h.lambda_ba != 0.0:
+                    track_reproj_fwd_bwd(self.X, self.obs_point, self.obs_xy, self.view_obs_offset, self.cams,
+                                         self.batch, h.huber_delta, h.lambda_ba, self.loss[1:2], self.gX,
+                                         self.g_tan, self.n_masked, self.track_ws, self.Rt)
 
         joined = False
         for b, r in enumerate(self.renderers):
@@ -297,18 +310,21 @@ class JointStep:
         # the pose update (one small kernel, independent of the parameter
         # update) runs on the side stream beside Adam
         side.wait_stream(main)
-        with torch.cuda.stream(side):
-            hp = adam_c(h.lr_pose, h.beta1, h.beta2, h.eps, self.step_no)
-            pose_se3_update(self.T0, self.xi, self.g_tan, self.g_xi, self.m_xi, self.v_xi, hp, self.Rt)
+        if not h.freeze_poses:
+            with torch.cuda.stream(side):
+                hp = adam_c(h.lr_pose, h.beta1, h.beta2, h.eps, self.step_no)
+                pose_se3_update(self.T0, self.xi, self.g_tan, self.g_xi, self.m_xi, self.v_xi, hp, self.Rt)
         ext = h.scene_extent
-        gs_adam_update_groups([
+        groups = [
             (self.g.mean, self.dg.mean, self.m.mean, self.v.mean, h.lr_mean * ext),
             (self.g.log_scale, self.dg.log_scale, self.m.log_scale, self.v.log_scale, h.lr_log_scale),
             (self.g.quat, self.dg.quat, self.m.quat, self.v.quat, h.lr_quat),
             (self.g.opacity_logit, self.dg.opacity_logit, self.m.opacity_logit, self.v.opacity_logit,
              h.lr_opacity),
-            (self.g.sh, self.dg.sh, self.m.sh, self.v.sh, h.lr_sh),
-            (self.X, self.gX, self.mX, self.vX, h.lr_track * ext)], h.beta1, h.beta2, h.eps, self.step_no)
+            (self.g.sh, self.dg.sh, self.m.sh, self.v.sh, h.lr_sh)]
+        if not self.merged_tracks:   # merged, the means' group updates the track points
+            groups.append((self.X, self.gX, self.mX, self.vX, h.lr_track * ext))
+        gs_adam_update_groups(groups, h.beta1, h.beta2, h.eps, self.step_no)
         mark("adam")
         main.wait_stream(side)
         mark("pose")
@@ -324,9 +340,10 @@ class JointStep:
             per_render += 1 + (1 + 1 + 4 + 2 + 1 + (tbits + 7) // 8 + 1) + 1 + 1 + 2
             if self.ssim_on:
                 per_render += 3  # photometric loss: block list, forward, backward
-        # target gather 1, track + finalize 2, step advance 1, Adam (all
-        # groups) 1, pose 1
-        return per_render + 1 + 2 + 1 + 1 + 1
+        # target gather 1, track + finalize 2 (unless lambda_BA = 0), step
+        # advance 1, Adam (all groups) 1, pose 1 (unless frozen)
+        return (per_render + 1 + (2 if self.h.lambda_ba != 0.0 else 0) + 1 + 1 +
+                (0 if self.h.freeze_poses else 1))
 
     # -- CUDA graph ----------------------------------------------------------
     def capture(self, warmup: int = 1):
