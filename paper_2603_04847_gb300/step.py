@@ -118,7 +118,7 @@ class Hyper:
     # (L1 weighted 1 - lambda, SSIM lambda) and feeds its dL/dimage to the
     # backward.  Read when the batch is set.
     lambda_ssim: float = 0.0
-    # The paper's ablation variants (Sec. 4 ablations): freeze_poses keeps
+    # Variants of the paper's extended ablation study: freeze_poses keeps
     # T = T0 (no pose update); lambda_ba = 0 is the photometric-only variant
     # (the track term is not run at all).
     freeze_poses: bool = False
