@@ -398,6 +398,21 @@ def algorithmic_model(js):
                        obs_in_batch=M_b)
 
 
+def slowest_rank_time(local_time: float, device="cpu") -> float:
+    """Whole-job time of a replica run (any unit): every rank's timed region
+    ends at a barrier and the job took as long as its slowest rank (MAX over
+    ranks).  With no process group (one rank) it is the local time.  Works
+    on any backend (NCCL with a CUDA device, gloo on the CPU)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(local_time)
+    t = torch.tensor([float(local_time)], dtype=torch.float64, device=device)
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -490,14 +505,11 @@ def run_ours(args):
         bcur += args.steps
     torch.cuda.synchronize()
     clocks.mark_off()
-    tot = torch.tensor([sum(times)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.barrier()
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    tot = slowest_rank_time(sum(times), dev)   # ms, as time_graph returns
     clk = clocks.stop()
     if js.status_flags():
         raise RuntimeError("device status flags %d during the timed steps" % js.status_flags())
-    ms = tot.item() / args.steps
+    ms = tot / args.steps
     P = js.batch.n_pixels
     value = ws * P / 1e6 / (ms / 1e3)
 
@@ -605,7 +617,7 @@ def run_ours(args):
             h2d_total += ts.put(js.views if plan[i + 1] is None else plan[i + 1].numpy())
         loss_host.copy_(js.loss, non_blocking=True)
         torch.cuda.current_stream().synchronize()
-    e2e_s = (time.perf_counter() - t0) / n_e2e
+    e2e_s = slowest_rank_time((time.perf_counter() - t0) / n_e2e, dev)
     if js.status_flags():
         raise RuntimeError("device status flags %d during the end-to-end steps" % js.status_flags())
     h2d_step = h2d_total / n_e2e + 8 * len(inp["off"]) + (32 if batch_list is not None else 0)
