@@ -17,6 +17,8 @@ Passages restated (GloSplat, arXiv 2603.04847):
   * Eq. 6 (Huber reprojection loss on track points, delta = 1 px);
   * the projection pi(K, T, X) = proj(K (R X + t)) after Algorithm 1;
   * T_i = T_i^(0) (+) dT_i (Algorithm 1), read as Exp(xi) T0.
+  * Eq. 4 (the SfM bundle adjustment: Levenberg-Marquardt over SE(3) poses
+    and points on the Huber reprojection objective), in ``ba.py``.
 Where the paper leaves a point open the oracle takes the published 3DGS
 convention its rasterizer follows, stated beside the code that applies it.
 
