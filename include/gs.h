@@ -10,6 +10,7 @@
  *                     per-tile ranges                        ("Rasterize")
  *   gs_render_fwd     front-to-back alpha compositing        ("Rasterize")
  *   gs_photo_loss     Eq. 5 with its SSIM term: loss and dL/dimage
+ *   sfm_ba_assemble   Eq. 4: the normal-equation blocks of one LM iteration
  *   gs_render_bwd     L1 gradient of Eq. 5 (fused) + compositing backward
  *                     + projection backward with pose gradient
  *                     (Algorithm 1 "Backpropagate"; Sec. 3.3: poses are
@@ -376,6 +377,33 @@ gs_status track_reproj_fwd_bwd_static(const float* X, int32_t n_points,
                                       float weight, double* loss,
                                       float* grad_X, double* g_pose_tangent,
                                       uint32_t* n_masked, gs_stream stream);
+
+/*
+ * sfm_ba_assemble — the iteratively reweighted Gauss-Newton blocks of one
+ * Levenberg-Marquardt iteration of the SfM bundle adjustment of Eq. 4
+ * (Sec. 3.2, "Bundle Adjustment"), over n_obs observations o = (camera
+ * obs_cam[o], point obs_point[o], pixel obs_xy[o]) with the residual
+ * r = pi_i(X_k) - x (pi of Eq. 4, poses and intrinsics from cams) and the
+ * Huber weight w = rho'(|r|^2) (rho as for Eq. 6: s for s <= delta^2, else
+ * 2 delta sqrt(s) - delta^2).  Pose derivatives are taken with respect to
+ * a left perturbation T <- Exp(d) T, d = (rho, phi).  Accumulated (+=), in
+ * double precision:
+ *   U  [V,36]  sum w Jp^T Jp per camera (row-major 6x6)
+ *   Vp [P,9]   sum w JX^T JX per point (row-major 3x3)
+ *   gc [V,6]   sum w Jp^T r per camera;   gp [P,3]  sum w JX^T r per point
+ *   objective  sum rho(|r|^2) (device double, may be NULL)
+ * and written per observation: Wo [n_obs,18] = w Jp^T JX (row-major 6x3).
+ * An observation whose camera depth is <= cams->near_plane, or whose camera
+ * or point index is out of range, contributes nothing (its Wo row is zero).
+ * All arrays are device memory owned by the caller; the arithmetic is
+ * double precision.  GS_ERR_ARG for null arrays or negative sizes.
+ */
+gs_status sfm_ba_assemble(const float* X, int32_t n_points,
+                          const gs_cameras* cams, const int32_t* obs_point,
+                          const int32_t* obs_cam, const float* obs_xy,
+                          int64_t n_obs, float delta, double* U, double* Vp,
+                          double* gc, double* gp, double* Wo,
+                          double* objective, gs_stream stream);
 
 /*
  * pose_se3_update — pose composition of Algorithm 1 (T_i = T_i^(0) (+)

@@ -289,6 +289,19 @@ def gs_photo_loss(cams: Cameras, batch: Batch, image: torch.Tensor, target: torc
                             _stream(stream)), "gs_photo_loss")
 
 
+def sfm_ba_assemble(X: torch.Tensor, cams: Cameras, obs_point: torch.Tensor, obs_cam: torch.Tensor,
+                    obs_xy: torch.Tensor, delta: float, U, Vp, gc, gp, Wo, objective=None, Rt=None, stream=None):
+    """The IRLS normal-equation blocks of one LM iteration of Eq. 4 (all
+    float64 outputs, += except Wo): U [V,36], Vp [P,9], gc [V,6], gp [P,3],
+    Wo [M,18], objective [1]."""
+    lib = _lib.load()
+    _need_cuda(X, obs_point, obs_cam, obs_xy, U, Vp, gc, gp, Wo, objective)
+    cc = cams.c(Rt)
+    check(lib.sfm_ba_assemble(_p(X), X.shape[0], ctypes.byref(cc), _p(obs_point), _p(obs_cam), _p(obs_xy),
+                              obs_point.shape[0], float(delta), _p(U), _p(Vp), _p(gc), _p(gp), _p(Wo),
+                              _p(objective), _stream(stream)), "sfm_ba_assemble")
+
+
 def track_workspace_bytes(batch: Batch) -> int:
     lib = _lib.load()
     ws = ctypes.c_size_t(0)

@@ -379,6 +379,24 @@ gs_status gs_photo_loss(const gs_cameras* cams, const gs_batch* batch, const flo
   return GS_OK;
 }
 
+gs_status sfm_ba_assemble(const float* X, int32_t n_points, const gs_cameras* cams, const int32_t* obs_point,
+                          const int32_t* obs_cam, const float* obs_xy, int64_t n_obs, float delta, double* U,
+                          double* Vp, double* gc, double* gp, double* Wo, double* objective, gs_stream stream) {
+  gs_status s;
+  if ((s = check_cameras(cams))) return s;
+  if (n_points < 0 || n_obs < 0) return fail(GS_ERR_ARG, "sfm_ba_assemble: negative sizes");
+  if (!U || !gc) return fail(GS_ERR_ARG, "sfm_ba_assemble: null camera blocks");
+  if (n_points > 0 && (!X || !Vp || !gp)) return fail(GS_ERR_ARG, "sfm_ba_assemble: null point arrays");
+  if (n_obs > 0 && (!obs_point || !obs_cam || !obs_xy || !Wo))
+    return fail(GS_ERR_ARG, "sfm_ba_assemble: null observation arrays");
+  if (!aligned(obs_xy, 8)) return fail(GS_ERR_ARG, "sfm_ba_assemble: obs_xy must be 8-byte aligned");
+  if (!std::isfinite(delta) || delta <= 0.f) return fail(GS_ERR_ARG, "sfm_ba_assemble: delta must be > 0");
+  cudaError_t e = launch_ba_assemble(X, n_points, *cams, obs_point, obs_cam, obs_xy, n_obs, delta, U, Vp, gc, gp,
+                                     Wo, objective, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sfm_ba_assemble");
+  return GS_OK;
+}
+
 gs_status gs_gather_view_pixels(const float* src, const int64_t* src_px_offset, const gs_cameras* cams,
                                 const gs_batch* batch, int32_t channels, float* dst, gs_stream stream) {
   gs_status s;

@@ -57,6 +57,10 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n,
                         cudaStream_t st);
 cudaError_t launch_adam_groups(const gs_adam_group* groups, int n_groups, const gs_adam& hp, cudaStream_t st);
 cudaError_t launch_step_advance(int32_t* step, cudaStream_t st);
+cudaError_t launch_ba_assemble(const float* X, int n_points, const gs_cameras& cams, const int32_t* obs_point,
+                               const int32_t* obs_cam, const float* obs_xy, int64_t n_obs, float delta, double* U,
+                               double* Vp, double* gc, double* gp, double* Wo, double* objective,
+                               cudaStream_t st);
 size_t photo_loss_ws_bytes(int64_t n_pixels, int32_t n_tiles);
 cudaError_t launch_photo_loss(const gs_batch& batch, const gs_cameras& cams, const float* image,
                               const float* target, float l1_weight, float ssim_weight, double* loss,

@@ -1,0 +1,82 @@
+"""Parity of sfm_ba_assemble (the normal-equation blocks of one LM iteration
+of Eq. 4) with the FP64 oracle (oracle/ba.py), on the float32-rounded
+inputs the GPU receives."""
+import numpy as np
+import pytest
+
+from oracle import ba
+from test_oracle_ba import _problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_04847_gb300 import build
+    build.build()
+
+
+def _r32(a):
+    return np.asarray(a, np.float32).astype(np.float64)
+
+
+def _run(X, Rt, K, op, oc, xy, delta):
+    from paper_2603_04847_gb300 import Cameras
+    from paper_2603_04847_gb300.core import sfm_ba_assemble
+    V, P, M = Rt.shape[0], X.shape[0], len(op)
+    cams = Cameras.from_numpy(np.tile([400, 300], (V, 1)), K, Rt)
+    dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    z = lambda *s: torch.zeros(s, dtype=torch.float64, device="cuda")
+    U, Vp, gc, gp, Wo, obj = z(V, 36), z(P, 9), z(V, 6), z(P, 3), torch.full((M, 18), np.nan, dtype=torch.float64,
+                                                                            device="cuda"), z(1)
+    sfm_ba_assemble(dev(X, torch.float32), cams, dev(op, torch.int32), dev(oc, torch.int32),
+                    dev(xy, torch.float32), delta, U, Vp, gc, gp, Wo, obj)
+    torch.cuda.synchronize()
+    return [t.cpu().numpy() for t in (U, Vp, gc, gp, Wo, obj)]
+
+
+def _close(a, b, tol=1e-9):
+    den = max(np.abs(b).max(), 1e-300)
+    return np.abs(a - b).max() <= tol * den
+
+
+def _check(got, X, Rt, K, op, oc, xy, delta, valid=None):
+    U, Vp, gc, gp, Wo, obj = got
+    sel = np.ones(len(op), bool) if valid is None else valid
+    Ue, We, Ve, gce, gpe = ba.normal_equations(_r32(X), _r32(Rt), _r32(K), op[sel], oc[sel], _r32(xy)[sel], delta)
+    assert _close(U.reshape(-1, 6, 6), Ue)
+    assert _close(Vp.reshape(-1, 3, 3), Ve)
+    assert _close(gc, gce) and _close(gp, gpe)
+    assert _close(Wo[sel].reshape(-1, 6, 3), We)
+    assert not np.any(Wo[~sel])
+    L = ba.objective(_r32(X), _r32(Rt), _r32(K), op[sel], oc[sel], _r32(xy)[sel], delta)
+    assert abs(obj[0] - L) <= 1e-9 * L
+
+
+def test_blocks_match_the_oracle_sorted_by_camera():
+    X, Rt, K, op, oc, xy = _problem(3, n_cams=5, n_pts=40, pix_noise=1.0, outliers=6)
+    _check(_run(X, Rt, K, op, oc, xy, 1.0), X, Rt, K, op, oc, xy, 1.0)
+
+
+def test_blocks_match_the_oracle_unsorted_with_invalid_observations():
+    """Shuffled observations (warps mix cameras), one point behind camera 0
+    and one observation of a point index out of range: both contribute
+    nothing."""
+    X, Rt, K, op, oc, xy = _problem(8, n_cams=4, n_pts=30, pix_noise=2.0, outliers=4)
+    R0, t0 = Rt[0, :9].reshape(3, 3), Rt[0, 9:]
+    centre = -R0.T @ t0
+    X = np.vstack([X, centre - 1.0 * R0[2]])                      # behind camera 0
+    P = X.shape[0]
+    op = np.concatenate([op, [P - 1, P + 7]]).astype(np.int32)
+    oc = np.concatenate([oc, [0, 1]]).astype(np.int32)
+    xy = np.vstack([xy, [[10.0, 10.0], [20.0, 20.0]]])
+    perm = np.random.default_rng(9).permutation(len(op))
+    op, oc, xy = op[perm], oc[perm], xy[perm]
+    valid = op < P
+    _, _, front = ba.residuals(_r32(X), _r32(Rt), _r32(K), np.minimum(op, P - 1), oc, _r32(xy))
+    valid &= front
+    assert (~valid).sum() == 2
+    _check(_run(X, Rt, K, op, oc, xy, 1.0), X, Rt, K, op, oc, xy, 1.0, valid=valid)
