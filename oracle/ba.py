@@ -157,15 +157,16 @@ def solve_dense(U, Wb, Vb, gc, gp, obs_point, obs_cam, lam):
     return dc, d[nc:].reshape(P, 3)
 
 
-def solve_schur(U, Wb, Vb, gc, gp, obs_point, obs_cam, lam):
-    """The same system with the points eliminated:
-    S = U - sum_k W_ik V_k^-1 W_jk^T, S d_cam = -gc + sum_k W_ik V_k^-1 gp_k,
-    d_pt_k = V_k^-1 (-gp_k - sum_i W_ik^T d_cam_i)."""
+def schur_system(U, Wb, Vb, gc, gp, obs_point, obs_cam, lam):
+    """The damped system with the points eliminated, over all cameras:
+    S = U - sum_k W_ik V_k^-1 W_jk^T  [6V, 6V],
+    rhs = -gc + sum_k W_ik V_k^-1 gp_k  [6V],
+    and the damped point blocks' inverses V_k^-1 [P,3,3] (W_ik summed over
+    the observations of camera i and point k)."""
     U, Vb, gc, gp = _regularise(U, Vb, gc, gp)
     V, P = U.shape[0], Vb.shape[0]
     Ud, Vd = _damp(U, lam), _damp(Vb, lam)
     Vinv = np.linalg.inv(Vd)
-    # W_ik summed over the observations of (i, k)
     Wik = {}
     for o, (i, k) in enumerate(zip(obs_cam, obs_point)):
         Wik[(int(i), int(k))] = Wik.get((int(i), int(k)), 0.0) + Wb[o]
@@ -181,16 +182,29 @@ def solve_schur(U, Wb, Vb, gc, gp, obs_point, obs_cam, lam):
             rhs[6 * i:6 * i + 6] += Wi @ Vinv[k] @ gp[k]
             for j, Wj in lst:
                 S[6 * i:6 * i + 6, 6 * j:6 * j + 6] -= Wi @ Vinv[k] @ Wj.T
-    dcr = np.linalg.solve(S[6:, 6:], rhs[6:])   # camera 0 held fixed
-    dc = np.zeros((V, 6))
-    dc[1:] = dcr.reshape(V - 1, 6)
-    dp = np.zeros((P, 3))
-    for k in range(P):
-        b = -gp[k].copy()
+    return S, rhs, Vinv, by_point, gp
+
+
+def back_substitute(Vinv, gp_reg, by_point, dc):
+    """d_pt_k = V_k^-1 (-gp_k - sum_i W_ik^T d_cam_i)."""
+    dp = np.zeros((Vinv.shape[0], 3))
+    for k in range(Vinv.shape[0]):
+        b = -gp_reg[k].copy()
         for i, Wi in by_point.get(k, []):
             b -= Wi.T @ dc[i]
         dp[k] = Vinv[k] @ b
-    return dc, dp
+    return dp
+
+
+def solve_schur(U, Wb, Vb, gc, gp, obs_point, obs_cam, lam):
+    """The same system as solve_dense with the points eliminated
+    (schur_system), the reduced camera system solved with camera 0 held
+    fixed, then the points back-substituted."""
+    S, rhs, Vinv, by_point, gp_reg = schur_system(U, Wb, Vb, gc, gp, obs_point, obs_cam, lam)
+    V = U.shape[0]
+    dc = np.zeros((V, 6))
+    dc[1:] = np.linalg.solve(S[6:, 6:], rhs[6:]).reshape(V - 1, 6)
+    return dc, back_substitute(Vinv, gp_reg, by_point, dc)
 
 
 def se3_exp(d):
