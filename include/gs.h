@@ -11,6 +11,8 @@
  *   gs_render_fwd     front-to-back alpha compositing        ("Rasterize")
  *   gs_photo_loss     Eq. 5 with its SSIM term: loss and dL/dimage
  *   sfm_ba_assemble   Eq. 4: the normal-equation blocks of one LM iteration
+ *   sfm_ba_schur, sfm_ba_back_substitute   Eq. 4: point elimination and
+ *                     back-substitution
  *   gs_render_bwd     L1 gradient of Eq. 5 (fused) + compositing backward
  *                     + projection backward with pose gradient
  *                     (Algorithm 1 "Backpropagate"; Sec. 3.3: poses are
@@ -404,6 +406,42 @@ gs_status sfm_ba_assemble(const float* X, int32_t n_points,
                           int64_t n_obs, float delta, double* U, double* Vp,
                           double* gc, double* gp, double* Wo,
                           double* objective, gs_stream stream);
+
+/*
+ * sfm_ba_schur — eliminates the points from the damped normal equations of
+ * one LM iteration of Eq. 4 (the blocks of sfm_ba_assemble):
+ *   S [6V,6V] = U_d - sum_k W_ik V_k^-1 W_jk^T   (row-major, written),
+ *   rhs [6V]  = -gc + sum_k W_ik V_k^-1 gp_k      (written),
+ *   Vinv [P,9] = V_k^-1 of the damped point blocks (written),
+ * with the Marquardt damping A_d = A + lambda diag(A) of every camera block
+ * U_i and point block V_k; a block with no observation (all zero) is taken
+ * as the identity with a zero right-hand side.  The observations of point
+ * k are point_obs[point_obs_offset[k] .. point_obs_offset[k+1]), a CSR list
+ * the caller builds (offsets non-decreasing, [P+1]); entries outside
+ * [0, n_obs) and cameras outside [0, V) are skipped.  No camera is singled
+ * out: a caller holds camera 0 fixed by solving without its six rows and
+ * columns.  Double precision; device arrays owned by the caller.
+ */
+gs_status sfm_ba_schur(int32_t n_cams, int32_t n_points, int64_t n_obs,
+                       const double* U, const double* Vp, const double* gc,
+                       const double* gp, const double* Wo,
+                       const int32_t* obs_cam, const int64_t* point_obs_offset,
+                       const int32_t* point_obs, double lambda, double* S,
+                       double* rhs, double* Vinv, gs_stream stream);
+
+/*
+ * sfm_ba_back_substitute — the points' step once the cameras' step
+ * dc [V,6] is known: dp_k = V_k^-1 (-gp_k - sum_i W_ik^T dc_i), dp [P,3]
+ * written (Vinv from sfm_ba_schur; a point with no observation gets 0).
+ * Same observation lists and skipping rules as sfm_ba_schur.
+ */
+gs_status sfm_ba_back_substitute(int32_t n_cams, int32_t n_points,
+                                 int64_t n_obs, const double* Vinv,
+                                 const double* Vp, const double* gp,
+                                 const double* Wo, const int32_t* obs_cam,
+                                 const int64_t* point_obs_offset,
+                                 const int32_t* point_obs, const double* dc,
+                                 double* dp, gs_stream stream);
 
 /*
  * pose_se3_update — pose composition of Algorithm 1 (T_i = T_i^(0) (+)

@@ -302,6 +302,25 @@ def sfm_ba_assemble(X: torch.Tensor, cams: Cameras, obs_point: torch.Tensor, obs
                               _p(objective), _stream(stream)), "sfm_ba_assemble")
 
 
+def sfm_ba_schur(U, Vp, gc, gp, Wo, obs_cam, point_obs_offset, point_obs, lam: float, S, rhs, Vinv, stream=None):
+    """Points eliminated from the damped LM system of Eq. 4: S [6V,6V], rhs
+    [6V], Vinv [P,9] written (float64 device tensors)."""
+    lib = _lib.load()
+    _need_cuda(U, Vp, gc, gp, Wo, obs_cam, point_obs_offset, point_obs, S, rhs, Vinv)
+    check(lib.sfm_ba_schur(U.shape[0], Vp.shape[0], obs_cam.shape[0], _p(U), _p(Vp), _p(gc), _p(gp), _p(Wo),
+                           _p(obs_cam), _p(point_obs_offset), _p(point_obs), float(lam), _p(S), _p(rhs), _p(Vinv),
+                           _stream(stream)), "sfm_ba_schur")
+
+
+def sfm_ba_back_substitute(Vinv, Vp, gp, Wo, obs_cam, point_obs_offset, point_obs, dc, dp, stream=None):
+    """dp [P,3] = V_k^-1 (-gp_k - sum_i W_ik^T dc_i) (written)."""
+    lib = _lib.load()
+    _need_cuda(Vinv, Vp, gp, Wo, obs_cam, point_obs_offset, point_obs, dc, dp)
+    check(lib.sfm_ba_back_substitute(dc.shape[0], Vp.shape[0], obs_cam.shape[0], _p(Vinv), _p(Vp), _p(gp), _p(Wo),
+                                     _p(obs_cam), _p(point_obs_offset), _p(point_obs), _p(dc), _p(dp),
+                                     _stream(stream)), "sfm_ba_back_substitute")
+
+
 def track_workspace_bytes(batch: Batch) -> int:
     lib = _lib.load()
     ws = ctypes.c_size_t(0)

@@ -141,4 +141,145 @@ cudaError_t launch_ba_assemble(const float* X, int n_points, const gs_cameras& c
   return cudaGetLastError();
 }
 
+// Elimination of the points (Schur complement) from the damped system of
+// one LM iteration:
+//   S = U_d - sum_k W_ik V_k^-1 W_jk^T,   rhs = -gc + sum_k W_ik V_k^-1 gp_k,
+// U_d = U + lambda diag(U), V_d likewise; a camera or point block with no
+// observation (all zero) becomes the identity with a zero right-hand side.
+// The observations of a point come as a CSR list (point_obs_offset,
+// point_obs).  The sum over pairs of observations of a point equals the
+// product of the per-camera sums of W (the expression is bilinear), so
+// repeated (camera, point) pairs need no merging.
+namespace {
+
+__device__ inline bool block_empty(const double* A, int n) {
+  for (int a = 0; a < n; ++a)
+    if (A[a] != 0.0) return false;
+  return true;
+}
+
+__global__ void __launch_bounds__(64) ba_camera_init_kernel(int V, const double* __restrict__ U,
+                                                            const double* __restrict__ gc, double lambda,
+                                                            double* __restrict__ S, double* __restrict__ rhs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  const double* Ui = U + 36 * (size_t)i;
+  const bool empty = block_empty(Ui, 36);
+  const size_t n = 6 * (size_t)V;
+  for (int a = 0; a < 6; ++a) {
+    for (int b = 0; b < 6; ++b) {
+      double v = empty ? (a == b ? 1.0 : 0.0) : Ui[6 * a + b];
+      if (a == b) v += lambda * v;
+      S[(6 * (size_t)i + a) * n + 6 * (size_t)i + b] = v;
+    }
+    rhs[6 * (size_t)i + a] = empty ? 0.0 : -gc[6 * (size_t)i + a];
+  }
+}
+
+// The damped point block's inverse (adjugate over determinant; the block is
+// symmetric positive definite after damping) and the point's right-hand side.
+__device__ inline void point_block(const double* __restrict__ Vp, const double* __restrict__ gp, int k,
+                                   double lambda, double* Vi, double* g) {
+  const double* A = Vp + 9 * (size_t)k;
+  const bool empty = block_empty(A, 9);
+  double M[9];
+  for (int a = 0; a < 9; ++a) M[a] = empty ? ((a % 4) == 0 ? 1.0 : 0.0) : A[a];
+  M[0] += lambda * M[0];
+  M[4] += lambda * M[4];
+  M[8] += lambda * M[8];
+  const double c00 = M[4] * M[8] - M[5] * M[7], c01 = M[5] * M[6] - M[3] * M[8], c02 = M[3] * M[7] - M[4] * M[6];
+  const double c10 = M[2] * M[7] - M[1] * M[8], c11 = M[0] * M[8] - M[2] * M[6], c12 = M[1] * M[6] - M[0] * M[7];
+  const double c20 = M[1] * M[5] - M[2] * M[4], c21 = M[2] * M[3] - M[0] * M[5], c22 = M[0] * M[4] - M[1] * M[3];
+  const double id = 1.0 / (M[0] * c00 + M[1] * c01 + M[2] * c02);
+  Vi[0] = c00 * id; Vi[1] = c10 * id; Vi[2] = c20 * id;
+  Vi[3] = c01 * id; Vi[4] = c11 * id; Vi[5] = c21 * id;
+  Vi[6] = c02 * id; Vi[7] = c12 * id; Vi[8] = c22 * id;
+  for (int a = 0; a < 3; ++a) g[a] = empty ? 0.0 : gp[3 * (size_t)k + a];
+}
+
+__global__ void __launch_bounds__(128) ba_point_schur_kernel(
+    int V, int P, int64_t M, const double* __restrict__ Vp, const double* __restrict__ gp,
+    const double* __restrict__ Wo, const int32_t* __restrict__ obs_cam, const int64_t* __restrict__ off,
+    const int32_t* __restrict__ point_obs, double lambda, double* __restrict__ Vinv, double* __restrict__ S,
+    double* __restrict__ rhs) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P) return;
+  double Vi[9], g[3];
+  point_block(Vp, gp, k, lambda, Vi, g);
+  for (int a = 0; a < 9; ++a) Vinv[9 * (size_t)k + a] = Vi[a];
+  const size_t n = 6 * (size_t)V;
+  for (int64_t p = off[k]; p < off[k + 1]; ++p) {
+    const int64_t oa = point_obs[p];
+    if (oa < 0 || oa >= M) continue;
+    const int ca = obs_cam[oa];
+    if ((unsigned)ca >= (unsigned)V) continue;
+    const double* Wa = Wo + 18 * oa;
+    double Y[18];  // W_a V^-1, 6x3
+    for (int r = 0; r < 6; ++r)
+      for (int c = 0; c < 3; ++c)
+        Y[3 * r + c] = Wa[3 * r] * Vi[c] + Wa[3 * r + 1] * Vi[3 + c] + Wa[3 * r + 2] * Vi[6 + c];
+    for (int r = 0; r < 6; ++r)
+      atomicAdd(&rhs[6 * (size_t)ca + r], Y[3 * r] * g[0] + Y[3 * r + 1] * g[1] + Y[3 * r + 2] * g[2]);
+    for (int64_t q = off[k]; q < off[k + 1]; ++q) {
+      const int64_t ob = point_obs[q];
+      if (ob < 0 || ob >= M) continue;
+      const int cb = obs_cam[ob];
+      if ((unsigned)cb >= (unsigned)V) continue;
+      const double* Wb = Wo + 18 * ob;
+      for (int r = 0; r < 6; ++r)
+        for (int c = 0; c < 6; ++c)
+          atomicAdd(&S[(6 * (size_t)ca + r) * n + 6 * (size_t)cb + c],
+                    -(Y[3 * r] * Wb[3 * c] + Y[3 * r + 1] * Wb[3 * c + 1] + Y[3 * r + 2] * Wb[3 * c + 2]));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) ba_back_substitute_kernel(
+    int V, int P, int64_t M, const double* __restrict__ Vinv, const double* __restrict__ Vp,
+    const double* __restrict__ gp, const double* __restrict__ Wo, const int32_t* __restrict__ obs_cam,
+    const int64_t* __restrict__ off, const int32_t* __restrict__ point_obs, const double* __restrict__ dc,
+    double* __restrict__ dp) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P) return;
+  const bool empty = block_empty(Vp + 9 * (size_t)k, 9);
+  double b[3];
+  for (int a = 0; a < 3; ++a) b[a] = empty ? 0.0 : -gp[3 * (size_t)k + a];
+  for (int64_t p = off[k]; p < off[k + 1]; ++p) {
+    const int64_t o = point_obs[p];
+    if (o < 0 || o >= M) continue;
+    const int c = obs_cam[o];
+    if ((unsigned)c >= (unsigned)V) continue;
+    const double* W = Wo + 18 * o;
+    for (int a = 0; a < 3; ++a)
+      for (int r = 0; r < 6; ++r) b[a] -= W[3 * r + a] * dc[6 * (size_t)c + r];
+  }
+  const double* Vi = Vinv + 9 * (size_t)k;
+  for (int a = 0; a < 3; ++a) dp[3 * (size_t)k + a] = Vi[3 * a] * b[0] + Vi[3 * a + 1] * b[1] + Vi[3 * a + 2] * b[2];
+}
+
+}  // namespace
+
+cudaError_t launch_ba_schur(int V, int P, int64_t M, const double* U, const double* Vp, const double* gc,
+                            const double* gp, const double* Wo, const int32_t* obs_cam, const int64_t* point_obs_offset,
+                            const int32_t* point_obs, double lambda, double* S, double* rhs, double* Vinv,
+                            cudaStream_t st) {
+  if (V == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(S, 0, sizeof(double) * 36 * (size_t)V * (size_t)V, st);
+  if (e != cudaSuccess) return e;
+  ba_camera_init_kernel<<<(V + 63) / 64, 64, 0, st>>>(V, U, gc, lambda, S, rhs);
+  if (P > 0)
+    ba_point_schur_kernel<<<(P + 127) / 128, 128, 0, st>>>(V, P, M, Vp, gp, Wo, obs_cam, point_obs_offset, point_obs,
+                                                            lambda, Vinv, S, rhs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ba_back_substitute(int V, int P, int64_t M, const double* Vinv, const double* Vp, const double* gp,
+                                      const double* Wo, const int32_t* obs_cam, const int64_t* point_obs_offset,
+                                      const int32_t* point_obs, const double* dc, double* dp, cudaStream_t st) {
+  if (P == 0) return cudaSuccess;
+  ba_back_substitute_kernel<<<(P + 127) / 128, 128, 0, st>>>(V, P, M, Vinv, Vp, gp, Wo, obs_cam, point_obs_offset,
+                                                              point_obs, dc, dp);
+  return cudaGetLastError();
+}
+
 }  // namespace gs

@@ -397,6 +397,35 @@ gs_status sfm_ba_assemble(const float* X, int32_t n_points, const gs_cameras* ca
   return GS_OK;
 }
 
+gs_status sfm_ba_schur(int32_t n_cams, int32_t n_points, int64_t n_obs, const double* U, const double* Vp,
+                       const double* gc, const double* gp, const double* Wo, const int32_t* obs_cam,
+                       const int64_t* point_obs_offset, const int32_t* point_obs, double lambda, double* S,
+                       double* rhs, double* Vinv, gs_stream stream) {
+  if (n_cams < 0 || n_points < 0 || n_obs < 0) return fail(GS_ERR_ARG, "sfm_ba_schur: negative sizes");
+  if (n_cams > 0 && (!U || !gc || !S || !rhs)) return fail(GS_ERR_ARG, "sfm_ba_schur: null camera arrays");
+  if (n_points > 0 && (!Vp || !gp || !Vinv || !point_obs_offset || (n_obs > 0 && (!Wo || !obs_cam || !point_obs))))
+    return fail(GS_ERR_ARG, "sfm_ba_schur: null point or observation arrays");
+  if (!std::isfinite(lambda) || lambda < 0.0) return fail(GS_ERR_ARG, "sfm_ba_schur: lambda must be >= 0");
+  cudaError_t e = launch_ba_schur(n_cams, n_points, n_obs, U, Vp, gc, gp, Wo, obs_cam, point_obs_offset, point_obs,
+                                  lambda, S, rhs, Vinv, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sfm_ba_schur");
+  return GS_OK;
+}
+
+gs_status sfm_ba_back_substitute(int32_t n_cams, int32_t n_points, int64_t n_obs, const double* Vinv,
+                                 const double* Vp, const double* gp, const double* Wo, const int32_t* obs_cam,
+                                 const int64_t* point_obs_offset, const int32_t* point_obs, const double* dc,
+                                 double* dp, gs_stream stream) {
+  if (n_cams < 0 || n_points < 0 || n_obs < 0) return fail(GS_ERR_ARG, "sfm_ba_back_substitute: negative sizes");
+  if (n_points > 0 && (!Vinv || !Vp || !gp || !dp || !point_obs_offset || !dc ||
+                       (n_obs > 0 && (!Wo || !obs_cam || !point_obs))))
+    return fail(GS_ERR_ARG, "sfm_ba_back_substitute: null argument");
+  cudaError_t e = launch_ba_back_substitute(n_cams, n_points, n_obs, Vinv, Vp, gp, Wo, obs_cam, point_obs_offset,
+                                            point_obs, dc, dp, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sfm_ba_back_substitute");
+  return GS_OK;
+}
+
 gs_status gs_gather_view_pixels(const float* src, const int64_t* src_px_offset, const gs_cameras* cams,
                                 const gs_batch* batch, int32_t channels, float* dst, gs_stream stream) {
   gs_status s;

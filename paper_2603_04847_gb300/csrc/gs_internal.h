@@ -61,6 +61,13 @@ cudaError_t launch_ba_assemble(const float* X, int n_points, const gs_cameras& c
                                const int32_t* obs_cam, const float* obs_xy, int64_t n_obs, float delta, double* U,
                                double* Vp, double* gc, double* gp, double* Wo, double* objective,
                                cudaStream_t st);
+cudaError_t launch_ba_schur(int V, int P, int64_t M, const double* U, const double* Vp, const double* gc,
+                            const double* gp, const double* Wo, const int32_t* obs_cam, const int64_t* point_obs_offset,
+                            const int32_t* point_obs, double lambda, double* S, double* rhs, double* Vinv,
+                            cudaStream_t st);
+cudaError_t launch_ba_back_substitute(int V, int P, int64_t M, const double* Vinv, const double* Vp, const double* gp,
+                                      const double* Wo, const int32_t* obs_cam, const int64_t* point_obs_offset,
+                                      const int32_t* point_obs, const double* dc, double* dp, cudaStream_t st);
 size_t photo_loss_ws_bytes(int64_t n_pixels, int32_t n_tiles);
 cudaError_t launch_photo_loss(const gs_batch& batch, const gs_cameras& cams, const float* image,
                               const float* target, float l1_weight, float ssim_weight, double* loss,

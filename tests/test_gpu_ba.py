@@ -23,7 +23,7 @@ def _r32(a):
     return np.asarray(a, np.float32).astype(np.float64)
 
 
-def _run(X, Rt, K, op, oc, xy, delta):
+def _assemble(X, Rt, K, op, oc, xy, delta):
     from paper_2603_04847_gb300 import Cameras
     from paper_2603_04847_gb300.core import sfm_ba_assemble
     V, P, M = Rt.shape[0], X.shape[0], len(op)
@@ -32,10 +32,16 @@ def _run(X, Rt, K, op, oc, xy, delta):
     z = lambda *s: torch.zeros(s, dtype=torch.float64, device="cuda")
     U, Vp, gc, gp, Wo, obj = z(V, 36), z(P, 9), z(V, 6), z(P, 3), torch.full((M, 18), np.nan, dtype=torch.float64,
                                                                             device="cuda"), z(1)
-    sfm_ba_assemble(dev(X, torch.float32), cams, dev(op, torch.int32), dev(oc, torch.int32),
-                    dev(xy, torch.float32), delta, U, Vp, gc, gp, Wo, obj)
+    oc_d = dev(oc, torch.int32)
+    sfm_ba_assemble(dev(X, torch.float32), cams, dev(op, torch.int32), oc_d, dev(xy, torch.float32), delta,
+                    U, Vp, gc, gp, Wo, obj)
+    return U, Vp, gc, gp, Wo, obj, oc_d
+
+
+def _run(X, Rt, K, op, oc, xy, delta):
+    out = _assemble(X, Rt, K, op, oc, xy, delta)[:6]
     torch.cuda.synchronize()
-    return [t.cpu().numpy() for t in (U, Vp, gc, gp, Wo, obj)]
+    return [t.cpu().numpy() for t in out]
 
 
 def _close(a, b, tol=1e-9):
@@ -80,3 +86,43 @@ def test_blocks_match_the_oracle_unsorted_with_invalid_observations():
     valid &= front
     assert (~valid).sum() == 2
     _check(_run(X, Rt, K, op, oc, xy, 1.0), X, Rt, K, op, oc, xy, 1.0, valid=valid)
+
+
+def _by_point(op, P):
+    """CSR lists of each point's observations (in-range points only)."""
+    ok = (op >= 0) & (op < P)
+    ids = np.nonzero(ok)[0]
+    ids = ids[np.argsort(op[ids], kind="stable")]
+    off = np.concatenate([[0], np.cumsum(np.bincount(op[ok], minlength=P))]).astype(np.int64)
+    return off, ids.astype(np.int32)
+
+
+@pytest.mark.parametrize("lam", [1e-6, 1e-3, 1.0])
+def test_schur_elimination_and_back_substitution_match_the_oracle(lam):
+    from paper_2603_04847_gb300.core import sfm_ba_back_substitute, sfm_ba_schur
+    X, Rt, K, op, oc, xy = _problem(3, n_cams=5, n_pts=40, pix_noise=1.0, outliers=6)
+    X = np.vstack([X, [[0.3, 0.2, 0.1]]])          # a point nobody observes
+    V, P = Rt.shape[0], X.shape[0]
+    U, Vp, gc, gp, Wo, _, oc_d = _assemble(X, Rt, K, op, oc, xy, 1.0)
+    off, ids = _by_point(op, P)
+    dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    off_d, ids_d = dev(off, torch.int64), dev(ids, torch.int32)
+    S = torch.full((6 * V, 6 * V), np.nan, dtype=torch.float64, device="cuda")
+    rhs = torch.full((6 * V,), np.nan, dtype=torch.float64, device="cuda")
+    Vinv = torch.full((P, 9), np.nan, dtype=torch.float64, device="cuda")
+    sfm_ba_schur(U, Vp, gc, gp, Wo, oc_d, off_d, ids_d, lam, S, rhs, Vinv)
+    blocks = ba.normal_equations(_r32(X), _r32(Rt), _r32(K), op, oc, _r32(xy), 1.0)
+    S_e, rhs_e, Vinv_e, by_point, gp_reg = ba.schur_system(*blocks, op, oc, lam)
+    dc = np.zeros((V, 6))
+    dc[1:] = np.linalg.solve(S_e[6:, 6:], rhs_e[6:]).reshape(V - 1, 6)
+    dp_e = ba.back_substitute(Vinv_e, gp_reg, by_point, dc)
+    dp = torch.full((P, 3), np.nan, dtype=torch.float64, device="cuda")
+    sfm_ba_back_substitute(Vinv, Vp, gp, Wo, oc_d, off_d, ids_d, dev(dc, torch.float64), dp)
+    torch.cuda.synchronize()
+    assert _close(S.cpu().numpy(), S_e) and _close(rhs.cpu().numpy(), rhs_e)
+    assert _close(Vinv.cpu().numpy().reshape(-1, 3, 3), Vinv_e)
+    assert _close(dp.cpu().numpy(), dp_e)
+    assert not np.any(dp.cpu().numpy()[-1])         # the unobserved point stays put
+    # the whole step equals the oracle's dense solve of the undivided system
+    dc_d, dp_d = ba.solve_dense(*blocks, op, oc, lam)
+    assert _close(dc, dc_d, 1e-7) and _close(dp.cpu().numpy(), dp_d, 1e-7)
