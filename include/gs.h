@@ -11,8 +11,8 @@
  *   gs_render_fwd     front-to-back alpha compositing        ("Rasterize")
  *   gs_photo_loss     Eq. 5 with its SSIM term: loss and dL/dimage
  *   sfm_ba_assemble   Eq. 4: the normal-equation blocks of one LM iteration
- *   sfm_ba_schur, sfm_ba_back_substitute   Eq. 4: point elimination and
- *                     back-substitution
+ *   sfm_ba_schur, sfm_ba_solve_cameras, sfm_ba_back_substitute   Eq. 4:
+ *                     point elimination, camera solve, back-substitution
  *   gs_render_bwd     L1 gradient of Eq. 5 (fused) + compositing backward
  *                     + projection backward with pose gradient
  *                     (Algorithm 1 "Backpropagate"; Sec. 3.3: poses are
@@ -72,9 +72,11 @@ enum {
                              with a larger capacity                      */
   GS_FLAG_NONFINITE = 2,  /* a Gaussian had a non-finite parameter and was
                              treated as invisible                         */
-  GS_FLAG_SORT_STALL = 4  /* a sort block gave up waiting (after 2^20
+  GS_FLAG_SORT_STALL = 4, /* a sort block gave up waiting (after 2^20
                              polls) for a predecessor block's digit
                              counts: the tile lists are invalid          */
+  GS_FLAG_NOT_SPD = 8     /* a bundle-adjustment camera system had a pivot
+                             <= 0: its step was set to zero              */
 };
 
 #define GS_ABI_VERSION 2
@@ -435,6 +437,19 @@ gs_status sfm_ba_schur(int32_t n_cams, int32_t n_points, int64_t n_obs,
  * written (Vinv from sfm_ba_schur; a point with no observation gets 0).
  * Same observation lists and skipping rules as sfm_ba_schur.
  */
+/*
+ * sfm_ba_solve_cameras — solves the reduced camera system of sfm_ba_schur
+ * with camera 0 held fixed: S' dc' = rhs' over cameras 1..V-1, S' being S
+ * without camera 0's six rows and columns.  S is overwritten (its lower
+ * triangle below camera 0 holds the Cholesky factor of S'); dc [V,6] is
+ * written, row 0 zero.  One thread block factors the whole system
+ * (O(n^3 / 6) flops for n = 6 (V - 1)): meant for up to a few hundred
+ * cameras.  A pivot <= 0 leaves dc zero and ORs GS_FLAG_NOT_SPD into the
+ * device word *status (may be NULL).
+ */
+gs_status sfm_ba_solve_cameras(int32_t n_cams, double* S, const double* rhs,
+                               double* dc, int32_t* status, gs_stream stream);
+
 gs_status sfm_ba_back_substitute(int32_t n_cams, int32_t n_points,
                                  int64_t n_obs, const double* Vinv,
                                  const double* Vp, const double* gp,

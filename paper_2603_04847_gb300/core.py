@@ -312,6 +312,15 @@ def sfm_ba_schur(U, Vp, gc, gp, Wo, obs_cam, point_obs_offset, point_obs, lam: f
                            _stream(stream)), "sfm_ba_schur")
 
 
+def sfm_ba_solve_cameras(S, rhs, dc, status=None, stream=None):
+    """dc [V,6] of the reduced camera system with camera 0 fixed (S is
+    overwritten by its factor)."""
+    lib = _lib.load()
+    _need_cuda(S, rhs, dc, status)
+    check(lib.sfm_ba_solve_cameras(dc.shape[0], _p(S), _p(rhs), _p(dc), _p(status), _stream(stream)),
+          "sfm_ba_solve_cameras")
+
+
 def sfm_ba_back_substitute(Vinv, Vp, gp, Wo, obs_cam, point_obs_offset, point_obs, dc, dp, stream=None):
     """dp [P,3] = V_k^-1 (-gp_k - sum_i W_ik^T dc_i) (written)."""
     lib = _lib.load()

@@ -257,6 +257,76 @@ __global__ void __launch_bounds__(128) ba_back_substitute_kernel(
   for (int a = 0; a < 3; ++a) dp[3 * (size_t)k + a] = Vi[3 * a] * b[0] + Vi[3 * a + 1] * b[1] + Vi[3 * a + 2] * b[2];
 }
 
+// The reduced camera system with camera 0 held fixed, S' dc' = rhs' (S' =
+// S without camera 0's six rows and columns), solved by an in-place
+// Cholesky factorization S' = L L^T (L over the lower triangle of S') and
+// two triangular solves, in one thread block.  A first version for up to a
+// few hundred cameras: O(n^3 / 6) flops for n = 6 (V - 1).  A pivot that is
+// not positive (S' not positive definite) leaves dc zero and sets a flag.
+__device__ inline double block_sum_d(double v, double* red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  __syncthreads();  // red is reused by consecutive calls
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;  // in every thread
+}
+
+__global__ void __launch_bounds__(1024) ba_cholesky_solve_kernel(int V, double* __restrict__ S,
+                                                                 const double* __restrict__ rhs,
+                                                                 double* __restrict__ dc, int32_t* status) {
+  __shared__ double red[32];
+  __shared__ int bad;
+  const int n = 6 * (V - 1);
+  const size_t ld = 6 * (size_t)V;
+  double* A = S + 6 * ld + 6;
+  const double* b = rhs + 6;
+  double* x = dc + 6;
+  for (int a = threadIdx.x; a < 6; a += blockDim.x) dc[a] = 0.0;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = A[j * ld + j];
+      if (d > 0.0 && isfinite(d)) A[j * ld + j] = sqrt(d);
+      else bad = 1;
+    }
+    __syncthreads();
+    if (bad) break;  // block-uniform
+    const double djj = A[j * ld + j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * ld + j] /= djj;
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      const double aij = A[i * ld + j];
+      for (int k = j + 1; k <= i; ++k) A[i * ld + k] -= aij * A[k * ld + j];
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = 0.0;
+    if (threadIdx.x == 0 && status) atomicOr(status, GS_FLAG_NOT_SPD);
+    return;
+  }
+  // L y = b (y kept in x)
+  for (int i = 0; i < n; ++i) {
+    double part = 0.0;
+    for (int k = threadIdx.x; k < i; k += blockDim.x) part += A[i * ld + k] * x[k];
+    const double sum = block_sum_d(part, red);
+    if (threadIdx.x == 0) x[i] = (b[i] - sum) / A[i * ld + i];
+    __syncthreads();
+  }
+  // L^T x = y
+  for (int i = n - 1; i >= 0; --i) {
+    double part = 0.0;
+    for (int k = i + 1 + threadIdx.x; k < n; k += blockDim.x) part += A[k * ld + i] * x[k];
+    const double sum = block_sum_d(part, red);
+    if (threadIdx.x == 0) x[i] = (x[i] - sum) / A[i * ld + i];
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_ba_schur(int V, int P, int64_t M, const double* U, const double* Vp, const double* gc,
@@ -270,6 +340,13 @@ cudaError_t launch_ba_schur(int V, int P, int64_t M, const double* U, const doub
   if (P > 0)
     ba_point_schur_kernel<<<(P + 127) / 128, 128, 0, st>>>(V, P, M, Vp, gp, Wo, obs_cam, point_obs_offset, point_obs,
                                                             lambda, Vinv, S, rhs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ba_solve_cameras(int V, double* S, const double* rhs, double* dc, int32_t* status,
+                                   cudaStream_t st) {
+  if (V <= 0) return cudaSuccess;
+  ba_cholesky_solve_kernel<<<1, 1024, 0, st>>>(V, S, rhs, dc, status);
   return cudaGetLastError();
 }
 

@@ -412,6 +412,15 @@ gs_status sfm_ba_schur(int32_t n_cams, int32_t n_points, int64_t n_obs, const do
   return GS_OK;
 }
 
+gs_status sfm_ba_solve_cameras(int32_t n_cams, double* S, const double* rhs, double* dc, int32_t* status,
+                               gs_stream stream) {
+  if (n_cams < 0) return fail(GS_ERR_ARG, "sfm_ba_solve_cameras: negative n_cams");
+  if (n_cams > 0 && (!S || !rhs || !dc)) return fail(GS_ERR_ARG, "sfm_ba_solve_cameras: null argument");
+  cudaError_t e = launch_ba_solve_cameras(n_cams, S, rhs, dc, status, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sfm_ba_solve_cameras");
+  return GS_OK;
+}
+
 gs_status sfm_ba_back_substitute(int32_t n_cams, int32_t n_points, int64_t n_obs, const double* Vinv,
                                  const double* Vp, const double* gp, const double* Wo, const int32_t* obs_cam,
                                  const int64_t* point_obs_offset, const int32_t* point_obs, const double* dc,

@@ -126,3 +126,32 @@ def test_schur_elimination_and_back_substitution_match_the_oracle(lam):
     # the whole step equals the oracle's dense solve of the undivided system
     dc_d, dp_d = ba.solve_dense(*blocks, op, oc, lam)
     assert _close(dc, dc_d, 1e-7) and _close(dp.cpu().numpy(), dp_d, 1e-7)
+
+
+@pytest.mark.parametrize("lam", [1e-6, 1e-3, 1.0])
+def test_one_lm_step_on_the_gpu_equals_the_oracle_dense_solve(lam):
+    """assemble -> eliminate the points -> solve the cameras (camera 0
+    fixed) -> back-substitute: the step equals the oracle's dense solve."""
+    from paper_2603_04847_gb300.core import sfm_ba_back_substitute, sfm_ba_schur, sfm_ba_solve_cameras
+    X, Rt, K, op, oc, xy = _problem(11, n_cams=6, n_pts=50, pix_noise=1.0, outliers=5)
+    V, P = Rt.shape[0], X.shape[0]
+    U, Vp, gc, gp, Wo, _, oc_d = _assemble(X, Rt, K, op, oc, xy, 1.0)
+    off, ids = _by_point(op, P)
+    dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    off_d, ids_d = dev(off, torch.int64), dev(ids, torch.int32)
+    S = torch.empty((6 * V, 6 * V), dtype=torch.float64, device="cuda")
+    rhs = torch.empty(6 * V, dtype=torch.float64, device="cuda")
+    Vinv = torch.empty((P, 9), dtype=torch.float64, device="cuda")
+    dc = torch.full((V, 6), np.nan, dtype=torch.float64, device="cuda")
+    dp = torch.full((P, 3), np.nan, dtype=torch.float64, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sfm_ba_schur(U, Vp, gc, gp, Wo, oc_d, off_d, ids_d, lam, S, rhs, Vinv)
+    sfm_ba_solve_cameras(S, rhs, dc, status)
+    sfm_ba_back_substitute(Vinv, Vp, gp, Wo, oc_d, off_d, ids_d, dc, dp)
+    torch.cuda.synchronize()
+    blocks = ba.normal_equations(_r32(X), _r32(Rt), _r32(K), op, oc, _r32(xy), 1.0)
+    dc_e, dp_e = ba.solve_dense(*blocks, op, oc, lam)
+    assert int(status.item()) == 0
+    got_c, got_p = dc.cpu().numpy(), dp.cpu().numpy()
+    assert not np.any(got_c[0])
+    assert _close(got_c, dc_e, 1e-7) and _close(got_p, dp_e, 1e-7)
