@@ -450,6 +450,27 @@ gs_status sfm_ba_schur(int32_t n_cams, int32_t n_points, int64_t n_obs,
 gs_status sfm_ba_solve_cameras(int32_t n_cams, double* S, const double* rhs,
                                double* dc, int32_t* status, gs_stream stream);
 
+/*
+ * sfm_ba_objective — the objective of Eq. 4 alone, sum rho(|r|^2) over the
+ * observations (same readings and skipping rules as sfm_ba_assemble),
+ * added (+=) to the device double *objective.
+ */
+gs_status sfm_ba_objective(const float* X, int32_t n_points,
+                           const gs_cameras* cams, const int32_t* obs_point,
+                           const int32_t* obs_cam, const float* obs_xy,
+                           int64_t n_obs, float delta, double* objective,
+                           gs_stream stream);
+
+/*
+ * sfm_ba_apply_step — the trial parameters of an LM step: T_i' =
+ * Exp(dc_i) T_i (left perturbation, translation first, computed in double
+ * and stored as float into Rt_out [V,12]) and X_k' = X_k + dp_k (X_out
+ * [P,3]).  Outputs must not alias the inputs.
+ */
+gs_status sfm_ba_apply_step(int32_t n_cams, int32_t n_points, const float* Rt,
+                            const float* X, const double* dc, const double* dp,
+                            float* Rt_out, float* X_out, gs_stream stream);
+
 gs_status sfm_ba_back_substitute(int32_t n_cams, int32_t n_points,
                                  int64_t n_obs, const double* Vinv,
                                  const double* Vp, const double* gp,

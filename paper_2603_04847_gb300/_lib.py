@@ -104,6 +104,10 @@ PROTOTYPES = {
     "sfm_ba_schur": (ctypes.c_int, [c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_void_p, c_void_p, ctypes.c_double, c_void_p, c_void_p, c_void_p,
                                     c_void_p]),
+    "sfm_ba_objective": (ctypes.c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,
+                                        c_float, c_void_p, c_void_p]),
+    "sfm_ba_apply_step": (ctypes.c_int, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                         c_void_p, c_void_p]),
     "sfm_ba_solve_cameras": (ctypes.c_int, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sfm_ba_back_substitute": (ctypes.c_int, [c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p, c_void_p,
                                               c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

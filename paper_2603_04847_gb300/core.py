@@ -312,6 +312,23 @@ def sfm_ba_schur(U, Vp, gc, gp, Wo, obs_cam, point_obs_offset, point_obs, lam: f
                            _stream(stream)), "sfm_ba_schur")
 
 
+def sfm_ba_objective(X, cams: Cameras, obs_point, obs_cam, obs_xy, delta: float, objective, Rt=None, stream=None):
+    """objective (device double [1]) += the objective of Eq. 4."""
+    lib = _lib.load()
+    _need_cuda(X, obs_point, obs_cam, obs_xy, objective)
+    cc = cams.c(Rt)
+    check(lib.sfm_ba_objective(_p(X), X.shape[0], ctypes.byref(cc), _p(obs_point), _p(obs_cam), _p(obs_xy),
+                               obs_point.shape[0], float(delta), _p(objective), _stream(stream)), "sfm_ba_objective")
+
+
+def sfm_ba_apply_step(Rt, X, dc, dp, Rt_out, X_out, stream=None):
+    """Rt_out = Exp(dc) Rt per camera, X_out = X + dp (float32 outputs)."""
+    lib = _lib.load()
+    _need_cuda(Rt, X, dc, dp, Rt_out, X_out)
+    check(lib.sfm_ba_apply_step(Rt.shape[0], X.shape[0], _p(Rt), _p(X), _p(dc), _p(dp), _p(Rt_out), _p(X_out),
+                                _stream(stream)), "sfm_ba_apply_step")
+
+
 def sfm_ba_solve_cameras(S, rhs, dc, status=None, stream=None):
     """dc [V,6] of the reduced camera system with camera 0 fixed (S is
     overwritten by its factor)."""

@@ -24,6 +24,8 @@ __device__ inline double warp_sum_d(double v) {
   return v;
 }
 
+// kBlocks false: the objective alone (a trial step's), nothing else written.
+template <bool kBlocks>
 __global__ void __launch_bounds__(256) ba_assemble_kernel(
     const float* __restrict__ X, int n_points, gs_cameras cams, const int32_t* __restrict__ obs_point,
     const int32_t* __restrict__ obs_cam, const float2* __restrict__ obs_xy, int64_t M, double delta,
@@ -82,13 +84,15 @@ __global__ void __launch_bounds__(256) ba_assemble_kernel(
         }
       }
     }
-    double* wo = Wo + 18 * o;
+    if constexpr (kBlocks) {
+      double* wo = Wo + 18 * o;
 #pragma unroll
-    for (int a = 0; a < 6; ++a)
+      for (int a = 0; a < 6; ++a)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) wo[3 * a + c] = w * (jp[0][a] * jx[0][c] + jp[1][a] * jx[1][c]);
+        for (int c = 0; c < 3; ++c) wo[3 * a + c] = w * (jp[0][a] * jx[0][c] + jp[1][a] * jx[1][c]);
+    }
   }
-  if (valid) {
+  if (kBlocks && valid) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
 #pragma unroll
@@ -100,7 +104,9 @@ __global__ void __launch_bounds__(256) ba_assemble_kernel(
   const unsigned vm = __ballot_sync(0xffffffffu, valid);
   if (vm != 0u) {  // warp-uniform
     const int cref = __shfl_sync(0xffffffffu, cam, __ffs(vm) - 1);
-    if (__all_sync(0xffffffffu, !valid || cam == cref)) {
+    if (!kBlocks) {
+      // objective only
+    } else if (__all_sync(0xffffffffu, !valid || cam == cref)) {
 #pragma unroll
       for (int a = 0; a < 6; ++a) {
 #pragma unroll
@@ -135,9 +141,79 @@ cudaError_t launch_ba_assemble(const float* X, int n_points, const gs_cameras& c
                                cudaStream_t st) {
   if (n_obs == 0) return cudaSuccess;
   const int64_t blocks = (n_obs + 255) / 256;
-  ba_assemble_kernel<<<(unsigned)blocks, 256, 0, st>>>(X, n_points, cams, obs_point, obs_cam,
-                                                       reinterpret_cast<const float2*>(obs_xy), n_obs,
-                                                       (double)delta, U, Vp, gc, gp, Wo, objective);
+  if (U == nullptr)
+    ba_assemble_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(X, n_points, cams, obs_point, obs_cam,
+                                                                reinterpret_cast<const float2*>(obs_xy), n_obs,
+                                                                (double)delta, U, Vp, gc, gp, Wo, objective);
+  else
+    ba_assemble_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(X, n_points, cams, obs_point, obs_cam,
+                                                               reinterpret_cast<const float2*>(obs_xy), n_obs,
+                                                               (double)delta, U, Vp, gc, gp, Wo, objective);
+  return cudaGetLastError();
+}
+
+// The trial parameters of a step: T_i' = Exp(dc_i) T_i (left perturbation,
+// translation first; computed in double, stored as float) and
+// X_k' = X_k + dp_k.  Exp of d = (rho, phi): R = I + a [phi]x + b [phi]x^2,
+// t = (I + b [phi]x + c [phi]x^2) rho with a = sin(th)/th,
+// b = (1 - cos(th))/th^2, c = (th - sin(th))/th^3 (th = |phi|; their
+// first-order limits below th = 1e-8).
+namespace {
+
+__global__ void __launch_bounds__(128) ba_apply_kernel(int V, int P, const float* __restrict__ Rt,
+                                                       const float* __restrict__ X, const double* __restrict__ dc,
+                                                       const double* __restrict__ dp, float* __restrict__ Rt_out,
+                                                       float* __restrict__ X_out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < V) {
+    const double* d = dc + 6 * (size_t)t;
+    const double p0 = d[3], p1 = d[4], p2 = d[5];
+    const double th = sqrt(p0 * p0 + p1 * p1 + p2 * p2);
+    double a, b, c;
+    if (th < 1e-8) {
+      a = 1.0;
+      b = 0.5;
+      c = 1.0 / 6.0;
+    } else {
+      const double s = sin(th), co = cos(th);
+      a = s / th;
+      b = (1.0 - co) / (th * th);
+      c = (th - s) / (th * th * th);
+    }
+    const double Wx[9] = {0.0, -p2, p1, p2, 0.0, -p0, -p1, p0, 0.0};
+    double W2[9];
+    for (int r = 0; r < 3; ++r)
+      for (int q = 0; q < 3; ++q) W2[3 * r + q] = Wx[3 * r] * Wx[q] + Wx[3 * r + 1] * Wx[3 + q] + Wx[3 * r + 2] * Wx[6 + q];
+    double E[9], J[9];
+    for (int e = 0; e < 9; ++e) {
+      const double I = (e % 4) == 0 ? 1.0 : 0.0;
+      E[e] = I + a * Wx[e] + b * W2[e];
+      J[e] = I + b * Wx[e] + c * W2[e];
+    }
+    const float* T = Rt + 12 * (size_t)t;
+    double R[9], tv[3];
+    for (int e = 0; e < 9; ++e) R[e] = T[e];
+    for (int e = 0; e < 3; ++e) tv[e] = T[9 + e];
+    float* O = Rt_out + 12 * (size_t)t;
+    for (int r = 0; r < 3; ++r) {
+      for (int q = 0; q < 3; ++q)
+        O[3 * r + q] = (float)(E[3 * r] * R[q] + E[3 * r + 1] * R[3 + q] + E[3 * r + 2] * R[6 + q]);
+      const double jr = J[3 * r] * d[0] + J[3 * r + 1] * d[1] + J[3 * r + 2] * d[2];
+      O[9 + r] = (float)(E[3 * r] * tv[0] + E[3 * r + 1] * tv[1] + E[3 * r + 2] * tv[2] + jr);
+    }
+  }
+  if (t < P) {
+    for (int e = 0; e < 3; ++e) X_out[3 * (size_t)t + e] = (float)((double)X[3 * (size_t)t + e] + dp[3 * (size_t)t + e]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_ba_apply(int V, int P, const float* Rt, const float* X, const double* dc, const double* dp,
+                            float* Rt_out, float* X_out, cudaStream_t st) {
+  const int n = V > P ? V : P;
+  if (n == 0) return cudaSuccess;
+  ba_apply_kernel<<<(n + 127) / 128, 128, 0, st>>>(V, P, Rt, X, dc, dp, Rt_out, X_out);
   return cudaGetLastError();
 }
 

@@ -412,6 +412,35 @@ gs_status sfm_ba_schur(int32_t n_cams, int32_t n_points, int64_t n_obs, const do
   return GS_OK;
 }
 
+gs_status sfm_ba_objective(const float* X, int32_t n_points, const gs_cameras* cams, const int32_t* obs_point,
+                           const int32_t* obs_cam, const float* obs_xy, int64_t n_obs, float delta, double* objective,
+                           gs_stream stream) {
+  gs_status s;
+  if ((s = check_cameras(cams))) return s;
+  if (n_points < 0 || n_obs < 0) return fail(GS_ERR_ARG, "sfm_ba_objective: negative sizes");
+  if (!objective) return fail(GS_ERR_ARG, "sfm_ba_objective: null objective");
+  if (n_obs > 0 && (!obs_point || !obs_cam || !obs_xy || (n_points > 0 && !X)))
+    return fail(GS_ERR_ARG, "sfm_ba_objective: null observation arrays");
+  if (!aligned(obs_xy, 8)) return fail(GS_ERR_ARG, "sfm_ba_objective: obs_xy must be 8-byte aligned");
+  if (!std::isfinite(delta) || delta <= 0.f) return fail(GS_ERR_ARG, "sfm_ba_objective: delta must be > 0");
+  cudaError_t e = launch_ba_assemble(X, n_points, *cams, obs_point, obs_cam, obs_xy, n_obs, delta, nullptr, nullptr,
+                                     nullptr, nullptr, nullptr, objective, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sfm_ba_objective");
+  return GS_OK;
+}
+
+gs_status sfm_ba_apply_step(int32_t n_cams, int32_t n_points, const float* Rt, const float* X, const double* dc,
+                            const double* dp, float* Rt_out, float* X_out, gs_stream stream) {
+  if (n_cams < 0 || n_points < 0) return fail(GS_ERR_ARG, "sfm_ba_apply_step: negative sizes");
+  if ((n_cams > 0 && (!Rt || !dc || !Rt_out)) || (n_points > 0 && (!X || !dp || !X_out)))
+    return fail(GS_ERR_ARG, "sfm_ba_apply_step: null argument");
+  if ((n_cams > 0 && Rt == Rt_out) || (n_points > 0 && X == X_out))
+    return fail(GS_ERR_ARG, "sfm_ba_apply_step: outputs alias inputs");
+  cudaError_t e = launch_ba_apply(n_cams, n_points, Rt, X, dc, dp, Rt_out, X_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sfm_ba_apply_step");
+  return GS_OK;
+}
+
 gs_status sfm_ba_solve_cameras(int32_t n_cams, double* S, const double* rhs, double* dc, int32_t* status,
                                gs_stream stream) {
   if (n_cams < 0) return fail(GS_ERR_ARG, "sfm_ba_solve_cameras: negative n_cams");

@@ -65,6 +65,8 @@ cudaError_t launch_ba_schur(int V, int P, int64_t M, const double* U, const doub
                             const double* gp, const double* Wo, const int32_t* obs_cam, const int64_t* point_obs_offset,
                             const int32_t* point_obs, double lambda, double* S, double* rhs, double* Vinv,
                             cudaStream_t st);
+cudaError_t launch_ba_apply(int V, int P, const float* Rt, const float* X, const double* dc, const double* dp,
+                            float* Rt_out, float* X_out, cudaStream_t st);
 cudaError_t launch_ba_solve_cameras(int V, double* S, const double* rhs, double* dc, int32_t* status,
                                    cudaStream_t st);
 cudaError_t launch_ba_back_substitute(int V, int P, int64_t M, const double* Vinv, const double* Vp, const double* gp,

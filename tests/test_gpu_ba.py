@@ -155,3 +155,44 @@ def test_one_lm_step_on_the_gpu_equals_the_oracle_dense_solve(lam):
     got_c, got_p = dc.cpu().numpy(), dp.cpu().numpy()
     assert not np.any(got_c[0])
     assert _close(got_c, dc_e, 1e-7) and _close(got_p, dp_e, 1e-7)
+
+
+def _perturbed(seed_problem, seed_noise, n_cams, n_pts, pix_noise=0.0, outliers=0, dpose=0.01, dpt=0.02):
+    X, Rt, K, op, oc, xy = _problem(seed_problem, n_cams=n_cams, n_pts=n_pts, pix_noise=pix_noise, outliers=outliers)
+    rng = np.random.default_rng(seed_noise)
+    dc = rng.normal(0, dpose, (Rt.shape[0], 6))
+    dc[0] = 0.0
+    X0, Rt0 = ba.apply_update(X, Rt, dc, rng.normal(0, dpt, X.shape))
+    return _r32(X0), _r32(Rt0), _r32(K), op, oc, _r32(xy)
+
+
+def _adjuster(X0, Rt0, K, op, oc, xy):
+    from paper_2603_04847_gb300 import Cameras
+    from paper_2603_04847_gb300.ba import BundleAdjuster
+    cams = Cameras.from_numpy(np.tile([400, 300], (Rt0.shape[0], 1)), K, Rt0)
+    X = torch.as_tensor(X0, dtype=torch.float32, device="cuda")
+    return BundleAdjuster(cams, X, op, oc, xy, delta=1.0, lam=1e-4)
+
+
+def test_gpu_lm_first_iteration_matches_the_oracle():
+    X0, Rt0, K, op, oc, xy = _perturbed(4, 5, 4, 20, pix_noise=0.5, outliers=3)
+    adj = _adjuster(X0, Rt0, K, op, oc, xy)
+    L0 = ba.objective(X0, Rt0, K, op, oc, xy, 1.0)
+    assert abs(adj.objective - L0) <= 1e-9 * L0
+    accepted = adj.step()
+    Xo, Rto, hist = ba.lm(X0, Rt0, K, op, oc, xy, delta=1.0, iters=1, lam=1e-4)
+    assert accepted == (hist[1] < hist[0])
+    assert np.abs(adj.X.cpu().numpy() - Xo).max() <= 1e-5
+    assert np.abs(adj.Rt.cpu().numpy() - Rto).max() <= 1e-5
+    assert abs(adj.objective - hist[1]) <= 1e-4 * hist[1]
+
+
+def test_gpu_lm_recovers_a_noiseless_problem():
+    X0, Rt0, K, op, oc, xy = _perturbed(4, 5, 4, 20)
+    adj = _adjuster(X0, Rt0, K, op, oc, xy)
+    hist = adj.run(30)
+    assert hist[0] > 1.0
+    assert hist[-1] < 1e-6 * hist[0]
+    assert all(b <= a for a, b in zip(hist[:-1], hist[1:]))
+    np.testing.assert_array_equal(adj.Rt.cpu().numpy()[0], np.float32(Rt0[0]))
+    assert adj.status_flags() == 0
