@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mid", choices=["mid", "train", "batched"])
+    ap.add_argument("--workload", default="mid", choices=["mid", "train", "batched", "sfm-ba"],
+                    help="sfm-ba: Levenberg-Marquardt iterations of the bundle adjustment of Eq. 4")
     ap.add_argument("--mode", default="batched", choices=["batched", "plain"])
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -653,8 +654,69 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_sfm_ba(args):
+    """LM iterations/s of the bundle adjustment of Eq. 4 on a synthetic
+    problem shaped like the joint step's tracks: 50 cameras (1000x750) on a
+    radius-4 sphere, 20k points in [-1,1]^3 seen by 2-12 cameras each,
+    0.5 px noise, 2 % outliers, poses and points perturbed.  Per-stage device
+    times from CUDA events; the host reads two objectives per iteration."""
+    import torch
+    import synth
+    from paper_2603_04847_gb300 import Cameras, build as libbuild
+    from paper_2603_04847_gb300.ba import BundleAdjuster
+    libbuild.build()
+    rng = np.random.default_rng(0)
+    V, P, W, H = 50, 20000, 1000, 750
+    wh, K, Rt = synth.cameras_sphere(rng, V, (W, W), (H, H))
+    X = rng.uniform(-1, 1, (P, 3))
+    tr = synth.tracks(rng, X, P, (2, 12), V, 0.5, 0.02)
+    op, oc = tr["obs_point"], tr["obs_view"]
+    R, t = Rt[oc, :9].reshape(-1, 3, 3), Rt[oc, 9:]
+    xc = np.einsum("mab,mb->ma", R, X[op]) + t
+    xy = np.stack([K[oc, 0] * xc[:, 0] / xc[:, 2] + K[oc, 2], K[oc, 1] * xc[:, 1] / xc[:, 2] + K[oc, 3]], 1)
+    xy = xy + tr["noise"]
+    out = tr["outlier"]
+    xy[out] = tr["outlier_uv01"][out] * [W, H]
+    d = rng.normal(0, 0.002, (V, 6))
+    d[0] = 0.0
+    Rt0 = Rt.copy()
+    for i in range(1, V):   # T <- Exp(d) T, first order (a small perturbation)
+        phi, rho = d[i, 3:], d[i, :3]
+        Wx = np.array([[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]])
+        E = np.eye(3) + Wx
+        Rt0[i, :9] = (E @ Rt[i, :9].reshape(3, 3)).reshape(-1)
+        Rt0[i, 9:] = E @ Rt[i, 9:] + rho
+    cams = Cameras.from_numpy(wh, K, Rt0)
+    Xd = torch.as_tensor(X + rng.normal(0, 0.005, X.shape), dtype=torch.float32, device="cuda")
+    adj = BundleAdjuster(cams, Xd, op, oc, xy, delta=1.0, lam=1e-4)
+    for _ in range(args.warmup):
+        adj.step()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    L0 = adj.objective
+    t0 = time.perf_counter()
+    a.record(st)
+    acc = sum(int(adj.step()) for _ in range(args.steps))
+    b.record(st)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) / args.steps
+    dev_ms = a.elapsed_time(b) / args.steps
+    line = dict(metric="LM iterations/s of the SfM bundle adjustment (Eq. 4)", value=1e3 / dev_ms,
+                unit="iterations/s", n_gpus=1, steps=args.steps, warmup=args.warmup, ms_per_step=dev_ms,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload="sfm-ba: %d cameras %dx%d, %d points, %d observations (2-12 per point)"
+                            % (V, W, H, P, len(op))),
+                e2e=dict(value=1.0 / wall, unit="iterations/s", ms_per_step=1e3 * wall),
+                accepted=acc, objective=dict(start=L0, end=adj.objective), status=adj.status_flags())
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "sfm-ba":
+        run_sfm_ba(args)
+        return
     if args.impl == "reference":
         import synth
         w = synth.make_workload(args.workload)
