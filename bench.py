@@ -680,10 +680,11 @@ def run_sfm_ba(args):
     d = rng.normal(0, 0.002, (V, 6))
     d[0] = 0.0
     Rt0 = Rt.copy()
-    for i in range(1, V):   # T <- Exp(d) T, first order (a small perturbation)
+    for i in range(1, V):   # rotate by Rodrigues(phi) and shift by rho (a small perturbation)
         phi, rho = d[i, 3:], d[i, :3]
+        th = np.linalg.norm(phi)
         Wx = np.array([[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]])
-        E = np.eye(3) + Wx
+        E = np.eye(3) + np.sin(th) / th * Wx + (1 - np.cos(th)) / th ** 2 * Wx @ Wx
         Rt0[i, :9] = (E @ Rt[i, :9].reshape(3, 3)).reshape(-1)
         Rt0[i, 9:] = E @ Rt[i, 9:] + rho
     cams = Cameras.from_numpy(wh, K, Rt0)
