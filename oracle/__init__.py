@@ -19,6 +19,7 @@ Passages restated (GloSplat, arXiv 2603.04847):
   * T_i = T_i^(0) (+) dT_i (Algorithm 1), read as Exp(xi) T0.
   * Eq. 4 (the SfM bundle adjustment: Levenberg-Marquardt over SE(3) poses
     and points on the Huber reprojection objective), in ``ba.py``.
+  * the MCMC densification rules the paper cites (Sec. 3.3), in ``mcmc.py``.
 Where the paper leaves a point open the oracle takes the published 3DGS
 convention its rasterizer follows, stated beside the code that applies it.
 
