@@ -13,6 +13,7 @@
  *   sfm_ba_assemble   Eq. 4: the normal-equation blocks of one LM iteration
  *   sfm_ba_schur, sfm_ba_solve_cameras, sfm_ba_back_substitute   Eq. 4:
  *                     point elimination, camera solve, back-substitution
+ *   gs_mcmc_relocate, gs_mcmc_noise   the MCMC densification (Sec. 3.3)
  *   gs_render_bwd     L1 gradient of Eq. 5 (fused) + compositing backward
  *                     + projection backward with pose gradient
  *                     (Algorithm 1 "Backpropagate"; Sec. 3.3: poses are
@@ -503,6 +504,41 @@ gs_status gs_adam_update(float* p, const float* g, float* m, float* v,
  * each with its own learning rate (hp->lr is ignored). */
 gs_status gs_adam_update_groups(const gs_adam_group* groups, int32_t n_groups,
                                 const gs_adam* hp, gs_stream stream);
+
+/*
+ * gs_mcmc_relocate — the relocation step of the MCMC densification the
+ * paper trains with (Sec. 3.3; Algorithm 1 "Relocate / add Gaussians"),
+ * with the cited method's rules, in place on the N Gaussians' parameters
+ * (same layouts as gs_gaussians):
+ *  - a Gaussian is dead when sigmoid(opacity_logit) <= 0.005;
+ *  - the dead one of rank r (index order among the dead) draws a live
+ *    source with the uniform u[r] in [0,1): the first j whose cumulative
+ *    live opacity exceeds u[r] times the total (dead ranks >= n_u, or no
+ *    live Gaussian, are left as they are; src -1);
+ *  - a source drawn c times and its copies become N = c + 1 identical
+ *    Gaussians with opacity o_N = 1 - (1 - o)^(1/N) and scales
+ *    s o / sum_{m=1..N} C(N,m) (-1)^(m-1) o_N^m / sqrt(m);
+ *  - each dead Gaussian then copies its source's (reset) parameters.
+ * src [N] (int32) gets each Gaussian's source or -1; n_dead (device uint32,
+ * may be NULL) the number of dead Gaussians.  ws: gs_mcmc_workspace(N)
+ * bytes.  GS_ERR_ARG for null arrays, negative sizes or a short workspace.
+ */
+gs_status gs_mcmc_workspace(int32_t n, size_t* ws_bytes);
+gs_status gs_mcmc_relocate(int32_t n, int32_t sh_degree, float* mean,
+                           float* log_scale, float* quat, float* opacity_logit,
+                           float* sh, const double* u, int32_t n_u,
+                           int32_t* src, uint32_t* n_dead, void* ws,
+                           size_t ws_bytes, gs_stream stream);
+
+/*
+ * gs_mcmc_noise — the cited method's noise on the means (the MCMC
+ * exploration term): mean += noise_lr * sigmoid(-100 (o - 0.005)) *
+ * Sigma eta, Sigma = R diag(exp(log_scale))^2 R^T, eta [N,3] given
+ * (standard normal draws).  Computed in double, stored as float.
+ */
+gs_status gs_mcmc_noise(int32_t n, float* mean, const float* log_scale,
+                        const float* quat, const float* opacity_logit,
+                        const float* eta, float noise_lr, gs_stream stream);
 
 /* gs_step_advance — *step += 1 on the device. */
 gs_status gs_step_advance(int32_t* step, gs_stream stream);

@@ -101,6 +101,11 @@ PROTOTYPES = {
     "gs_zero": (ctypes.c_int, [c_void_p, c_size_t, c_void_p]),
     "gs_gather_view_pixels": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "gs_photo_loss_workspace": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_size_t)]),
+    "gs_mcmc_workspace": (ctypes.c_int, [c_int32, ctypes.POINTER(c_size_t)]),
+    "gs_mcmc_relocate": (ctypes.c_int, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                        c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "gs_mcmc_noise": (ctypes.c_int, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float,
+                                     c_void_p]),
     "sfm_ba_schur": (ctypes.c_int, [c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_void_p, c_void_p, ctypes.c_double, c_void_p, c_void_p, c_void_p,
                                     c_void_p]),

@@ -347,6 +347,27 @@ def sfm_ba_back_substitute(Vinv, Vp, gp, Wo, obs_cam, point_obs_offset, point_ob
                                      _stream(stream)), "sfm_ba_back_substitute")
 
 
+def gs_mcmc_relocate(g: Gaussians, u: torch.Tensor, src: torch.Tensor, n_dead=None, stream=None):
+    """MCMC relocation of the dead Gaussians of g in place (u: float64
+    uniforms, one per dead Gaussian in index order; src [N] int32 out)."""
+    lib = _lib.load()
+    _need_cuda(*g.tensors(), u, src, n_dead)
+    ws_bytes = ctypes.c_size_t(0)
+    check(lib.gs_mcmc_workspace(g.n, ctypes.byref(ws_bytes)), "gs_mcmc_workspace")
+    ws = torch.empty(max(ws_bytes.value, 256), dtype=torch.uint8, device=g.mean.device)
+    check(lib.gs_mcmc_relocate(g.n, g.sh_degree, _p(g.mean), _p(g.log_scale), _p(g.quat), _p(g.opacity_logit),
+                               _p(g.sh), _p(u), u.numel(), _p(src), _p(n_dead), _p(ws), ws.numel(),
+                               _stream(stream)), "gs_mcmc_relocate")
+
+
+def gs_mcmc_noise(g: Gaussians, eta: torch.Tensor, noise_lr: float, stream=None):
+    """mean += noise_lr * sigmoid(-100 (o - 0.005)) * Sigma eta, in place."""
+    lib = _lib.load()
+    _need_cuda(*g.tensors(), eta)
+    check(lib.gs_mcmc_noise(g.n, _p(g.mean), _p(g.log_scale), _p(g.quat), _p(g.opacity_logit), _p(eta),
+                            float(noise_lr), _stream(stream)), "gs_mcmc_noise")
+
+
 def track_workspace_bytes(batch: Batch) -> int:
     lib = _lib.load()
     ws = ctypes.c_size_t(0)

@@ -464,6 +464,39 @@ gs_status sfm_ba_back_substitute(int32_t n_cams, int32_t n_points, int64_t n_obs
   return GS_OK;
 }
 
+gs_status gs_mcmc_workspace(int32_t n, size_t* ws_bytes) {
+  if (n < 0 || !ws_bytes) return fail(GS_ERR_ARG, "gs_mcmc_workspace: bad argument");
+  *ws_bytes = mcmc_ws_bytes(n);
+  return GS_OK;
+}
+
+gs_status gs_mcmc_relocate(int32_t n, int32_t sh_degree, float* mean, float* log_scale, float* quat,
+                           float* opacity_logit, float* sh, const double* u, int32_t n_u, int32_t* src,
+                           uint32_t* n_dead, void* ws, size_t ws_bytes, gs_stream stream) {
+  if (n < 0 || n_u < 0 || sh_degree < 0 || sh_degree > 3) return fail(GS_ERR_ARG, "gs_mcmc_relocate: bad sizes");
+  if (n > 0 && (!mean || !log_scale || !quat || !opacity_logit || !sh || !src || !ws))
+    return fail(GS_ERR_ARG, "gs_mcmc_relocate: null argument");
+  if (n_u > 0 && !u) return fail(GS_ERR_ARG, "gs_mcmc_relocate: null u");
+  if (n > 0 && ws_bytes < mcmc_ws_bytes(n))
+    return fail(GS_ERR_ARG, "gs_mcmc_relocate: workspace needs %zu bytes", mcmc_ws_bytes(n));
+  if (!aligned(ws, 16)) return fail(GS_ERR_ARG, "gs_mcmc_relocate: workspace must be 16-byte aligned");
+  cudaError_t e = launch_mcmc_relocate(n, sh_degree, mean, log_scale, quat, opacity_logit, sh, u, n_u, src, n_dead,
+                                       ws, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_mcmc_relocate");
+  return GS_OK;
+}
+
+gs_status gs_mcmc_noise(int32_t n, float* mean, const float* log_scale, const float* quat, const float* opacity_logit,
+                        const float* eta, float noise_lr, gs_stream stream) {
+  if (n < 0) return fail(GS_ERR_ARG, "gs_mcmc_noise: negative n");
+  if (n > 0 && (!mean || !log_scale || !quat || !opacity_logit || !eta))
+    return fail(GS_ERR_ARG, "gs_mcmc_noise: null argument");
+  if (!std::isfinite(noise_lr)) return fail(GS_ERR_ARG, "gs_mcmc_noise: noise_lr");
+  cudaError_t e = launch_mcmc_noise(n, mean, log_scale, quat, opacity_logit, eta, noise_lr, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_mcmc_noise");
+  return GS_OK;
+}
+
 gs_status gs_gather_view_pixels(const float* src, const int64_t* src_px_offset, const gs_cameras* cams,
                                 const gs_batch* batch, int32_t channels, float* dst, gs_stream stream) {
   gs_status s;

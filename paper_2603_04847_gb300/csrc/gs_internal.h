@@ -72,6 +72,12 @@ cudaError_t launch_ba_solve_cameras(int V, double* S, const double* rhs, double*
 cudaError_t launch_ba_back_substitute(int V, int P, int64_t M, const double* Vinv, const double* Vp, const double* gp,
                                       const double* Wo, const int32_t* obs_cam, const int64_t* point_obs_offset,
                                       const int32_t* point_obs, const double* dc, double* dp, cudaStream_t st);
+size_t mcmc_ws_bytes(int n);
+cudaError_t launch_mcmc_relocate(int n, int sh_degree, float* mean, float* log_scale, float* quat, float* logit,
+                                 float* sh, const double* u, int n_u, int32_t* src, uint32_t* n_dead, void* ws,
+                                 cudaStream_t st);
+cudaError_t launch_mcmc_noise(int n, float* mean, const float* log_scale, const float* quat, const float* logit,
+                              const float* eta, float lr, cudaStream_t st);
 size_t photo_loss_ws_bytes(int64_t n_pixels, int32_t n_tiles);
 cudaError_t launch_photo_loss(const gs_batch& batch, const gs_cameras& cams, const float* image,
                               const float* target, float l1_weight, float ssim_weight, double* loss,

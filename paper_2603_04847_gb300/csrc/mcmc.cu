@@ -1,0 +1,292 @@
+// MCMC densification (Sec. 3.3, "stochastic density control via MCMC-based
+// densification"; Algorithm 1 "Relocate / add Gaussians"), with the cited
+// method's rules:
+//  * a Gaussian is dead when sigmoid(logit) <= 0.005;
+//  * each dead Gaussian, in index order, takes the parameters of the live one
+//    drawn by its uniform u: the first j whose cumulative live opacity
+//    exceeds u times the total;
+//  * a source drawn c times becomes N = c + 1 identical Gaussians with
+//    o_N = 1 - (1 - o)^(1/N) and scales s o / D_N,
+//    D_N = sum_{m=1..N} C(N, m) (-1)^(m-1) o_N^m / sqrt(m)
+//    (the stacked copies composite to the source's alpha at the centre and
+//    to the same alpha integral along a line through it; D_N is the
+//    front-to-back double sum over copies and powers collapsed with the
+//    hockey-stick identity);
+//  * noise on the means: mu += lr sigmoid(-100 (o - 0.005)) Sigma eta.
+// Passes: a two-level scan gives the cumulative live opacity (FP64) and each
+// dead Gaussian's rank; draws are binary searches with atomic copy counts;
+// then the sources are reset and the dead ones copy them.
+#include "gs_internal.h"
+
+namespace gs {
+
+namespace {
+
+constexpr int kThr = 256;
+constexpr double kDead = 0.005;
+
+__device__ inline double opacity_of(float logit) { return 1.0 / (1.0 + exp(-(double)logit)); }
+
+struct McmcWs {
+  double* cdf;     // [n] inclusive cumulative live opacity
+  int32_t* rank;   // [n] rank among the dead, -1 if live
+  int32_t* count;  // [n] times drawn as a source
+  double* bsum;    // [nb] per block, then exclusive over blocks
+  int32_t* bcnt;   // [nb]
+  double* total;   // [1]
+};
+
+inline size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+McmcWs mcmc_layout(void* base, int n, size_t* bytes) {
+  const int nb = (n + kThr - 1) / kThr;
+  char* p = (char*)base;
+  size_t o = 0;
+  McmcWs w;
+  w.cdf = (double*)(p + o); o += al(8 * (size_t)n);
+  w.rank = (int32_t*)(p + o); o += al(4 * (size_t)n);
+  w.count = (int32_t*)(p + o); o += al(4 * (size_t)n);
+  w.bsum = (double*)(p + o); o += al(8 * (size_t)nb);
+  w.bcnt = (int32_t*)(p + o); o += al(4 * (size_t)nb);
+  w.total = (double*)(p + o); o += al(8);
+  if (bytes) *bytes = o;
+  return w;
+}
+
+// Block-wide inclusive scan of a double and exclusive scan of an int.
+__device__ inline void block_scan(double v, int c, double* incl, int* excl, double* s_d, int* s_i) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double x = v;
+  int y = c;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const double a = __shfl_up_sync(0xffffffffu, x, off);
+    const int b = __shfl_up_sync(0xffffffffu, y, off);
+    if (lane >= off) {
+      x += a;
+      y += b;
+    }
+  }
+  if (lane == 31) {
+    s_d[warp] = x;
+    s_i[warp] = y;
+  }
+  __syncthreads();
+  double dbase = 0.0;
+  int ibase = 0;
+  for (int w = 0; w < warp; ++w) {
+    dbase += s_d[w];
+    ibase += s_i[w];
+  }
+  *incl = dbase + x;
+  *excl = ibase + y - c;
+}
+
+__global__ void __launch_bounds__(kThr) mcmc_reduce_kernel(int n, const float* __restrict__ logit,
+                                                           double* __restrict__ bsum, int32_t* __restrict__ bcnt) {
+  __shared__ double s_d[kThr / 32];
+  __shared__ int s_i[kThr / 32];
+  const int i = blockIdx.x * kThr + threadIdx.x;
+  double v = 0.0;
+  int c = 0;
+  if (i < n) {
+    const double o = opacity_of(logit[i]);
+    if (o <= kDead) c = 1;
+    else v = o;
+  }
+  double incl;
+  int excl;
+  block_scan(v, c, &incl, &excl, s_d, s_i);
+  if (threadIdx.x == kThr - 1) {
+    bsum[blockIdx.x] = incl;
+    bcnt[blockIdx.x] = excl + c;
+  }
+}
+
+// Exclusive scan of the per-block sums in place, by one block with a carry.
+__global__ void __launch_bounds__(kThr) mcmc_blocks_kernel(int nb, double* __restrict__ bsum, int32_t* __restrict__ bcnt,
+                                                           double* __restrict__ total, uint32_t* __restrict__ n_dead) {
+  __shared__ double s_d[kThr / 32];
+  __shared__ int s_i[kThr / 32];
+  __shared__ double carry_d;
+  __shared__ int carry_i;
+  if (threadIdx.x == 0) {
+    carry_d = 0.0;
+    carry_i = 0;
+  }
+  __syncthreads();
+  for (int base = 0; base < nb; base += kThr) {
+    const int i = base + threadIdx.x;
+    const double v = i < nb ? bsum[i] : 0.0;
+    const int c = i < nb ? bcnt[i] : 0;
+    double incl;
+    int excl;
+    block_scan(v, c, &incl, &excl, s_d, s_i);
+    const double cd = carry_d;
+    const int ci = carry_i;
+    if (i < nb) {
+      bsum[i] = cd + incl - v;
+      bcnt[i] = ci + excl;
+    }
+    __syncthreads();
+    if (threadIdx.x == kThr - 1) {
+      carry_d = cd + incl;
+      carry_i = ci + excl + c;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *total = carry_d;
+    if (n_dead) *n_dead = (uint32_t)carry_i;
+  }
+}
+
+__global__ void __launch_bounds__(kThr) mcmc_apply_kernel(int n, const float* __restrict__ logit,
+                                                          const double* __restrict__ bsum,
+                                                          const int32_t* __restrict__ bcnt, double* __restrict__ cdf,
+                                                          int32_t* __restrict__ rank, int32_t* __restrict__ count) {
+  __shared__ double s_d[kThr / 32];
+  __shared__ int s_i[kThr / 32];
+  const int i = blockIdx.x * kThr + threadIdx.x;
+  double v = 0.0;
+  int c = 0;
+  if (i < n) {
+    const double o = opacity_of(logit[i]);
+    if (o <= kDead) c = 1;
+    else v = o;
+  }
+  double incl;
+  int excl;
+  block_scan(v, c, &incl, &excl, s_d, s_i);
+  if (i < n) {
+    cdf[i] = bsum[blockIdx.x] + incl;
+    rank[i] = c ? bcnt[blockIdx.x] + excl : -1;
+    count[i] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kThr) mcmc_draw_kernel(int n, const int32_t* __restrict__ rank,
+                                                         const double* __restrict__ cdf,
+                                                         const double* __restrict__ total, const double* __restrict__ u,
+                                                         int n_u, int32_t* __restrict__ src,
+                                                         int32_t* __restrict__ count) {
+  const int i = blockIdx.x * kThr + threadIdx.x;
+  if (i >= n) return;
+  const int r = rank[i];
+  const double T = *total;
+  int s = -1;
+  if (r >= 0 && r < n_u && T > 0.0) {
+    const double target = u[r] * T;
+    int lo = 0, hi = n - 1;  // first j with cdf[j] > target (cdf[n-1] = T > target)
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (cdf[mid] > target) hi = mid;
+      else lo = mid + 1;
+    }
+    s = lo;
+    atomicAdd(&count[s], 1);
+  }
+  src[i] = s;
+}
+
+__global__ void __launch_bounds__(kThr) mcmc_reset_kernel(int n, float* __restrict__ logit,
+                                                          float* __restrict__ log_scale,
+                                                          const int32_t* __restrict__ count) {
+  const int j = blockIdx.x * kThr + threadIdx.x;
+  if (j >= n || count[j] == 0) return;
+  const int N = count[j] + 1;
+  const double o = opacity_of(logit[j]);
+  const double oN = 1.0 - pow(1.0 - o, 1.0 / N);
+  double den = 0.0, binom = 1.0, p = 1.0;
+  for (int m = 1; m <= N; ++m) {
+    binom = binom * (double)(N - m + 1) / (double)m;
+    p *= oN;
+    den += ((m & 1) ? 1.0 : -1.0) * binom * p / sqrt((double)m);
+  }
+  logit[j] = (float)log(oN / (1.0 - oN));
+  const double ds = log(o / den);
+  for (int a = 0; a < 3; ++a) log_scale[3 * (size_t)j + a] = (float)((double)log_scale[3 * (size_t)j + a] + ds);
+}
+
+__global__ void __launch_bounds__(kThr) mcmc_copy_kernel(int n, int K3, const int32_t* __restrict__ src,
+                                                         float* __restrict__ mean, float* __restrict__ log_scale,
+                                                         float* __restrict__ quat, float* __restrict__ logit,
+                                                         float* __restrict__ sh) {
+  const int i = blockIdx.x * kThr + threadIdx.x;
+  if (i >= n) return;
+  const int s = src[i];
+  if (s < 0) return;
+  for (int a = 0; a < 3; ++a) {
+    mean[3 * (size_t)i + a] = mean[3 * (size_t)s + a];
+    log_scale[3 * (size_t)i + a] = log_scale[3 * (size_t)s + a];
+  }
+  for (int a = 0; a < 4; ++a) quat[4 * (size_t)i + a] = quat[4 * (size_t)s + a];
+  logit[i] = logit[s];
+  for (int a = 0; a < K3; ++a) sh[(size_t)K3 * i + a] = sh[(size_t)K3 * s + a];
+}
+
+__global__ void __launch_bounds__(kThr) mcmc_noise_kernel(int n, float* __restrict__ mean,
+                                                          const float* __restrict__ log_scale,
+                                                          const float* __restrict__ quat,
+                                                          const float* __restrict__ logit,
+                                                          const float* __restrict__ eta, double lr) {
+  const int i = blockIdx.x * kThr + threadIdx.x;
+  if (i >= n) return;
+  const double o = opacity_of(logit[i]);
+  const double gate = 1.0 / (1.0 + exp(100.0 * (o - kDead)));
+  double q[4];
+  double qq = 0.0;
+  for (int a = 0; a < 4; ++a) {
+    q[a] = quat[4 * (size_t)i + a];
+    qq += q[a] * q[a];
+  }
+  const double iq = 1.0 / sqrt(qq);
+  const double w = q[0] * iq, x = q[1] * iq, y = q[2] * iq, z = q[3] * iq;
+  const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                       2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                       2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
+  double s2[3], e[3], Rte[3];
+  for (int a = 0; a < 3; ++a) {
+    const double s = exp((double)log_scale[3 * (size_t)i + a]);
+    s2[a] = s * s;
+    e[a] = eta[3 * (size_t)i + a];
+  }
+  for (int a = 0; a < 3; ++a) Rte[a] = R[a] * e[0] + R[3 + a] * e[1] + R[6 + a] * e[2];   // R^T eta
+  for (int a = 0; a < 3; ++a) {
+    const double v = R[3 * a] * s2[0] * Rte[0] + R[3 * a + 1] * s2[1] * Rte[1] + R[3 * a + 2] * s2[2] * Rte[2];
+    mean[3 * (size_t)i + a] = (float)((double)mean[3 * (size_t)i + a] + lr * gate * v);
+  }
+}
+
+}  // namespace
+
+size_t mcmc_ws_bytes(int n) {
+  size_t b = 0;
+  mcmc_layout(nullptr, n, &b);
+  return b;
+}
+
+cudaError_t launch_mcmc_relocate(int n, int sh_degree, float* mean, float* log_scale, float* quat, float* logit,
+                                 float* sh, const double* u, int n_u, int32_t* src, uint32_t* n_dead, void* ws,
+                                 cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  McmcWs w = mcmc_layout(ws, n, nullptr);
+  const int nb = (n + kThr - 1) / kThr;
+  const int K3 = 3 * (sh_degree + 1) * (sh_degree + 1);
+  mcmc_reduce_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt);
+  mcmc_blocks_kernel<<<1, kThr, 0, st>>>(nb, w.bsum, w.bcnt, w.total, n_dead);
+  mcmc_apply_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt, w.cdf, w.rank, w.count);
+  mcmc_draw_kernel<<<nb, kThr, 0, st>>>(n, w.rank, w.cdf, w.total, u, n_u, src, w.count);
+  mcmc_reset_kernel<<<nb, kThr, 0, st>>>(n, logit, log_scale, w.count);
+  mcmc_copy_kernel<<<nb, kThr, 0, st>>>(n, K3, src, mean, log_scale, quat, logit, sh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mcmc_noise(int n, float* mean, const float* log_scale, const float* quat, const float* logit,
+                              const float* eta, float lr, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  mcmc_noise_kernel<<<(n + kThr - 1) / kThr, kThr, 0, st>>>(n, mean, log_scale, quat, logit, eta, (double)lr);
+  return cudaGetLastError();
+}
+
+}  // namespace gs
