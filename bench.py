@@ -3,13 +3,18 @@ Algorithm 1 over a batch of views: projection, tile sort, compositing,
 fused L1 + backward with pose gradient, Huber track term, Adam on
 Gaussians, track points and SE(3) pose deltas).
 
-Default workload: 8 cameras 1237x822 on a sphere looking at the scene,
-200k Gaussians with SH degree 3, 20k tracks with 2..12 observations, all 8
-views in every step, batched and captured in a CUDA graph.  Prints one JSON
-line (metric: Mpix*views/s of the joint fwd+bwd step).
+Default workload (`large`): 1000 cameras of uneven resolution (960..1920 x
+540..1080) on a sphere looking at the scene, 5M Gaussians with SH degree 3,
+400k tracks with 2..40 observations each over the views that see them; each
+step trains on 16 random views, batched (one launch per stage for all 16,
+the batch laid out on the device) and captured in one CUDA graph.  Other
+workloads: train (8 of 200 views 1600x1066, 3M Gaussians), batched (32
+uneven views, 1M), mid (8 views 1237x822, 200k).  Prints one JSON line
+(metric: Mpix*views/s of the joint fwd+bwd step).
 
 --impl reference times the FP64 CPU oracle (the paper publishes no code to
-compare against) on a bounded pixel sample of the same workload.
+compare against) on a bounded pixel sample of the same workload, over all
+host cores.
 --gpus N under torchrun runs N independent replicas (weak scaling).
 """
 from __future__ import annotations
@@ -30,6 +35,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+import synth  # noqa: E402  (seeded random draws only)
+
 METRIC = "joint fwd+bwd steps/s (Mpix·views/s) incl. pose+track grads; % HBM roofline"
 UNIT = "Mpix*views/s"
 
@@ -40,11 +47,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mid", choices=["mid", "train", "batched", "sfm-ba"],
-                    help="sfm-ba: Levenberg-Marquardt iterations of the bundle adjustment of Eq. 4")
+    ap.add_argument("--workload", default="large", choices=["large", "train", "batched", "mid", "sfm-ba"],
+                    help="large (default): 16 random views of 1000 uneven ones (960-1920 x 540-1080), 5M "
+                         "Gaussians; sfm-ba: Levenberg-Marquardt iterations of the bundle adjustment of Eq. 4")
     ap.add_argument("--mode", default="batched", choices=["batched", "plain"])
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain one-view-per-launch timing")
     ap.add_argument("--lambda-ssim", type=float, default=0.0,
@@ -70,69 +78,229 @@ def workload_desc(name, w):
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle leg
+# CPU oracle leg: the FP64 oracle as it stands, timed on a bounded sample of
+# the workload, on one spawned process per host core.  Each process renders
+# its own share of the sampled pixels (forward and backward over all
+# Gaussians, per pixel by brute force); the scene's arrays are written once
+# as .npy files that every process maps read-only.
 
-def oracle_sample_step(w, n_pix, rng):
-    """One bounded sample of the workload on the FP64 oracle: forward and
-    backward (random cotangent) of n_pix pixels of view 0 over all its
-    Gaussians, plus the track term of view 0's observations.  Returns
-    (seconds, pixels)."""
+SCENE_KEYS = ("mean", "log_scale", "quat", "opacity_logit", "sh")
+
+
+def np_visible(X, wh, K, Rt, near=0.01):
+    """bool [n, V]: point X_k in view v's image with depth > near (pinhole
+    projection of the track points, used to draw the track observations)."""
+    R = np.asarray(Rt)[:, :9].reshape(-1, 3, 3)
+    t = np.asarray(Rt)[:, 9:]
+    Xc = np.einsum("vij,nj->nvi", R, np.asarray(X, dtype=np.float64)) + t[None]
+    z = Xc[..., 2]
+    zs = np.where(z > near, z, 1.0)
+    u = K[None, :, 0] * Xc[..., 0] / zs + K[None, :, 2]
+    v = K[None, :, 1] * Xc[..., 1] / zs + K[None, :, 3]
+    return (z > near) & (u >= 0) & (u < wh[None, :, 0]) & (v >= 0) & (v < wh[None, :, 1])
+
+
+def scene_files(scene: dict, d: str) -> str:
+    for k in SCENE_KEYS:
+        np.save(os.path.join(d, k + ".npy"), np.ascontiguousarray(scene[k], dtype=np.float64))
+    return d
+
+
+def _oracle_job(job):
+    """One process's share of a sample (runs in a spawned worker): forward
+    and backward of its pixels of one view, plus the view's track term when
+    given.  Returns the seconds its oracle calls took."""
+    scene_dir, cam_args, pix, v, trk = job
     import oracle
-    sc = oracle.Scene(**w["scene"])
-    K, Rt, wh = w["K"], w["Rt"], w["wh"]
-    cam = oracle.camera_from_rt(int(wh[0][0]), int(wh[0][1]), K[0], Rt[0])
-    W, H = int(wh[0][0]), int(wh[0][1])
-    pix = np.stack([rng.integers(W // 4, 3 * W // 4, n_pix), rng.integers(H // 4, 3 * H // 4, n_pix)], 1)
+    arrs = {k: np.load(os.path.join(scene_dir, k + ".npy"), mmap_mode="r") for k in SCENE_KEYS}
+    sc = oracle.Scene(**arrs)
+    cam = oracle.camera_from_rt(*cam_args)
+    t0 = time.perf_counter()
+    if len(pix):
+        oracle.render(sc, cam, pixels=pix)
+        oracle.render_bwd(sc, cam, v, pixels=pix)
+    if trk is not None:
+        X, op, xy = trk
+        oracle.track(X, op, np.zeros(len(op), np.int32), xy, [cam], 1.0, 0.1)
+    return time.perf_counter() - t0
+
+
+class OraclePool:
+    """Spawned worker processes for the oracle (spawn: safe beside a CUDA
+    context).  `procs` processes; at most one per host core, fewer when the
+    host memory would not hold one oracle working set per process."""
+
+    def __init__(self, n_gaussians: int, procs: int = 0):
+        import multiprocessing
+        cores = os.cpu_count() or 1
+        try:
+            mem = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+        except (ValueError, OSError, AttributeError):
+            mem = 64 << 30
+        per_proc = 400 * max(n_gaussians, 1) + (256 << 20)   # projected records, sort buffers
+        fit = max(1, int(0.4 * mem // per_proc))
+        self.procs = max(1, min(procs or cores, cores, fit))
+        self.pool = multiprocessing.get_context("spawn").Pool(self.procs)
+
+    def run(self, scene_dir, cam_args, pix, v, trk=None, procs=None):
+        """Wall seconds of one sample split over `procs` processes (default
+        all); the track term goes to the first share."""
+        n = procs or self.procs
+        parts = np.array_split(np.arange(len(pix)), n)
+        jobs = [(scene_dir, cam_args, pix[p], v[p], trk if i == 0 else None) for i, p in enumerate(parts)]
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_job, jobs, chunksize=1)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _view0_sample(w, rng, n_pix):
+    W, H = int(w["wh"][0][0]), int(w["wh"][0][1])
+    pix = np.stack([rng.integers(0, W, n_pix), rng.integers(0, H, n_pix)], 1).astype(np.int32)
     v = rng.normal(size=(n_pix, 3))
+    return pix, v
+
+
+def _view0_track(w, rng):
     tr = w["tracks"]
     sel = tr["obs_view"] == 0
-    X = tr["X"]
-    xy = rng.uniform(0, W, (int(sel.sum()), 2))
-    t0 = time.perf_counter()
-    oracle.render(sc, cam, pixels=pix)
-    oracle.render_bwd(sc, cam, v, pixels=pix)
-    oracle.track(X, tr["obs_point"][sel], tr["obs_view"][sel] * 0, xy, [cam], 1.0, 0.1)
-    return time.perf_counter() - t0, n_pix
+    W = float(w["wh"][0][0])
+    return tr["X"], tr["obs_point"][sel], rng.uniform(0, W, (int(sel.sum()), 2))
 
 
-def cpu_baseline(w, seconds):
+def _cam0(w):
+    return (int(w["wh"][0][0]), int(w["wh"][0][1]), w["K"][0], w["Rt"][0])
+
+
+def calibrate(pool, w, scene_dir, rng, procs, trk):
+    """Wall seconds of a call with no pixel work (`fixed`) and per pixel per
+    process (`per_px`): a first call warms the processes (imports, page
+    mapping) and is discarded; then one and three pixels per process."""
+    cam = _cam0(w)
+    pix, v = _view0_sample(w, rng, procs)
+    pool.run(scene_dir, cam, pix, v, trk, procs)
+    t1 = pool.run(scene_dir, cam, pix, v, trk, procs)
+    pix, v = _view0_sample(w, rng, 3 * procs)
+    t3 = pool.run(scene_dir, cam, pix, v, trk, procs)
+    per_px = max((t3 - t1) / 2.0, 0.02 * t1, 1e-6)
+    return max(t1 - per_px, 0.0), per_px
+
+
+def timed_sample(pool, w, scene_dir, rng, seconds, procs):
+    """Pixels per second of the oracle on `procs` processes over random
+    pixels of view 0 (plus its track term), the sample sized to about
+    `seconds` of wall time.  Returns (px/s, pixels, wall seconds)."""
+    trk = _view0_track(w, rng)
+    fixed, per_px = calibrate(pool, w, scene_dir, rng, procs, trk)
+    n = int(max(1, min(20000, (seconds - fixed) / per_px))) * procs
+    pix, v = _view0_sample(w, rng, n)
+    t = pool.run(scene_dir, _cam0(w), pix, v, trk, procs)
+    return n / t, n, t
+
+
+def config_timing(pool, name, rng, shrink, seconds):
+    """The oracle on one small configuration: all cores over its full frame,
+    one core over a pixel sample.  Returns a dict with both rates and the
+    cost per evaluated (pixel, visible Gaussian) pair of the all-cores run."""
+    import tempfile
+    import oracle
+    w = synth.make_workload(name, **shrink)
+    d = scene_files(w["scene"], tempfile.mkdtemp(prefix="gs_orc_"))
+    W, H = int(w["wh"][0][0]), int(w["wh"][0][1])
+    cam = _cam0(w)
+    pix = np.stack(np.meshgrid(np.arange(W), np.arange(H)), -1).reshape(-1, 2).astype(np.int32)
+    v = rng.normal(size=(len(pix), 3))
+    t_all = pool.run(d, cam, pix, v)
+    proj = oracle.project(oracle.Scene(**w["scene"]), oracle.camera_from_rt(*cam))
+    g_v = int((proj[:, oracle.P["visible"]] > 0).sum())
+    rate1, n1, t1 = timed_sample(pool, w, d, rng, seconds, 1)
+    return dict(view="%dx%d" % (W, H), gaussians=w["workload"].n_gaussians if not shrink.get("n_gaussians")
+                else shrink["n_gaussians"], visible=g_v,
+                all_cores=dict(value=len(pix) / t_all / 1e6, seconds=t_all, pixels=len(pix)),
+                one_core=dict(value=rate1 / 1e6, seconds=t1, pixels=n1),
+                s_per_pair=t_all * pool.procs / (len(pix) * max(g_v, 1)))
+
+
+def cpu_baseline(w, seconds, counts=None):
+    """The oracle on the machine's host cores, in the metric's unit:
+       value        all cores, a bounded random pixel sample of view 0 of the
+                    benchmark workload (forward + backward over all its
+                    Gaussians, plus view 0's track term);
+       single_core  the same on one process;
+       configs      the tiny configuration (full frame) and a reduced mid
+                    one (1 view 320x214, 20k Gaussians SH3) measured, and
+       extrapolated the benchmark step from the reduced mid configuration's
+                    cost per (pixel, visible Gaussian), linear in
+                    sum_v P_v G_v (G_v from the GPU step's own counts)."""
+    import tempfile
     rng = np.random.default_rng(123)
-    t, n = oracle_sample_step(w, 16, rng)
-    per_px = max(t / n, 1e-6)
-    n_pix = int(max(16, min(20000, seconds / per_px)))
-    t, n = oracle_sample_step(w, n_pix, rng)
-    return dict(value=n / 1e6 / t, unit=UNIT, cores=1, kind="oracle",
-                sample="fwd+bwd of %d random pixels of view 0 (%dx%d) over all %d Gaussians + view-0 "
-                       "track term, single-threaded FP64 C oracle, %.1f s" % (
-                           n, int(w["wh"][0][0]), int(w["wh"][0][1]), w["workload"].n_gaussians, t))
+    pool = OraclePool(w["workload"].n_gaussians)
+    try:
+        d = scene_files(w["scene"], tempfile.mkdtemp(prefix="gs_orc_"))
+        rate, n, t = timed_sample(pool, w, d, rng, seconds, pool.procs)
+        rate1, n1, t1 = timed_sample(pool, w, d, rng, seconds / 2, 1)
+        cfg = dict(tiny=config_timing(pool, "tiny", rng, {}, 4.0),
+                   mid_reduced=config_timing(pool, "mid", rng, dict(n_gaussians=20000, n_views=1, width=(320, 320),
+                                                                    height=(214, 214), n_tracks=10), 4.0))
+    finally:
+        pool.close()
+    W, H = int(w["wh"][0][0]), int(w["wh"][0][1])
+    out = dict(value=rate / 1e6, unit=UNIT, cores=pool.procs, host_cores=os.cpu_count(), kind="oracle",
+               sample="fwd+bwd of %d random pixels of view 0 (%dx%d) over all %d Gaussians + view-0 track "
+                      "term, FP64 C oracle, %d processes, %.1f s wall" % (n, W, H, w["workload"].n_gaussians,
+                                                                          pool.procs, t),
+               single_core=dict(value=rate1 / 1e6, pixels=n1, seconds=t1), configs=cfg)
+    if counts and counts.get("pairs_brute"):
+        c = cfg["mid_reduced"]["s_per_pair"]
+        t_step = c * counts["pairs_brute"] / pool.procs
+        out["extrapolated"] = dict(value=counts["pixels"] / t_step / 1e6, unit=UNIT,
+                                   basis="extrapolated: %.3g s per (pixel, visible Gaussian) from mid_reduced "
+                                         "x %d pairs (sum_v P_v G_v of the step) / %d processes" % (
+                                             c, counts["pairs_brute"], pool.procs))
+    return out
 
 
 def run_reference(args, w):
+    """The reference arm: the oracle as it stands on the host cores, each
+    step a bounded pixel sample of view 0 of the same workload (all cores),
+    sized so that the whole run ends within a few minutes."""
+    import tempfile
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle
     oracle.build()
     rng = np.random.default_rng(0)
-    t, n = oracle_sample_step(w, 16, rng)
-    per_px = max(t / n, 1e-6)
-    budget = 150.0 / max(args.steps + args.warmup, 1)   # whole run within a few minutes
-    n_pix = int(max(8, min(5000, budget / per_px)))
-    for _ in range(args.warmup):
-        oracle_sample_step(w, n_pix, rng)
-    times = []
-    for _ in range(args.steps):
-        t, n = oracle_sample_step(w, n_pix, rng)
-        times.append(t)
+    pool = OraclePool(w["workload"].n_gaussians)
+    try:
+        d = scene_files(w["scene"], tempfile.mkdtemp(prefix="gs_orc_"))
+        cam = _cam0(w)
+        trk = _view0_track(w, rng)
+        # the calibration's three calls are warm-up steps
+        fixed, per_px = calibrate(pool, w, d, rng, pool.procs, trk)
+        budget = 150.0 / max(args.steps + args.warmup, 1)
+        n_pix = pool.procs * int(max(1, min(5000, (budget - fixed) / per_px)))
+        for _ in range(max(args.warmup - 3, 0)):
+            pix, v = _view0_sample(w, rng, n_pix)
+            pool.run(d, cam, pix, v, trk)
+        times = []
+        for _ in range(args.steps):
+            pix, v = _view0_sample(w, rng, n_pix)
+            times.append(pool.run(d, cam, pix, v, trk))
+    finally:
+        pool.close()
     tot = sum(times)
     value = n_pix * args.steps / 1e6 / tot
+    sample = ("fwd+bwd of %d random pixels of view 0 over all Gaussians + view-0 track term per step, FP64 C "
+              "oracle on %d processes" % (n_pix, pool.procs))
     line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus,
                 steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * tot / args.steps,
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                 config=dict(workload_desc(args.workload, w), sample="%d pixels of view 0 per step" % n_pix),
-                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle",
-                                  sample="fwd+bwd of %d random pixels of view 0 over all Gaussians + "
-                                         "view-0 track term per step" % n_pix),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=pool.procs, kind="oracle", sample=sample),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -204,15 +372,36 @@ class ClockSampler:
         return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons), samples=len(sm))
 
 
-def gpu_inputs(name, device):
-    """Synthetic workload on the device.  Targets are renders of the
-    ground-truth scene at the ground-truth poses; track observations are the
-    projections of the track points at those poses plus the workload's pixel
-    noise (and outliers)."""
+def torch_visible(device):
+    """visible(X, wh, K, Rt) for synth.tracks, evaluated with torch on the
+    device (the pinhole projection of the track points)."""
     import torch
-    import synth
+
+    def visible(X, wh, K, Rt):
+        Xt = torch.as_tensor(np.asarray(X), dtype=torch.float64, device=device)
+        Rtt = torch.as_tensor(np.asarray(Rt), dtype=torch.float64, device=device)
+        Kt = torch.as_tensor(np.asarray(K), dtype=torch.float64, device=device)
+        wht = torch.as_tensor(np.asarray(wh), dtype=torch.float64, device=device)
+        Xc = torch.einsum("vij,nj->nvi", Rtt[:, :9].reshape(-1, 3, 3), Xt) + Rtt[None, :, 9:]
+        z = Xc[..., 2]
+        zs = torch.where(z > 0.01, z, torch.ones_like(z))
+        u = Kt[None, :, 0] * Xc[..., 0] / zs + Kt[None, :, 2]
+        v = Kt[None, :, 1] * Xc[..., 1] / zs + Kt[None, :, 3]
+        ok = (z > 0.01) & (u >= 0) & (u < wht[None, :, 0]) & (v >= 0) & (v < wht[None, :, 1])
+        return ok.cpu().numpy()
+    return visible
+
+
+def gpu_inputs(name, device, w=None):
+    """Synthetic workload on the device.  Targets are renders of the
+    ground-truth scene at the ground-truth poses (16 views per launch, one
+    batch laid out on the device and reused); track observations are the
+    projections of the track points at those poses plus the workload's pixel
+    noise (and outliers), drawn over the views that see each point."""
+    import torch
     from paper_2603_04847_gb300 import Batch, Cameras, Gaussians, Renderer
-    w = synth.make_workload(name)
+    if w is None:
+        w = synth.make_workload(name, visible=torch_visible(device))
     wh, K = w["wh"], w["K"]
     V = len(wh)
     cams_gt = Cameras.from_numpy(wh, K, w["Rt_gt"], device=device)
@@ -220,14 +409,20 @@ def gpu_inputs(name, device):
     P = (wh[:, 0].astype(np.int64) * wh[:, 1])
     off = np.concatenate([[0], np.cumsum(P)])
     targets = torch.empty((int(off[-1]), 3), dtype=torch.float32, device=device)
-    for v0 in range(0, V, 16):
-        views = list(range(v0, min(V, v0 + 16)))
-        b = Batch(cams_gt, views, device=device)
-        r = Renderer(g_gt.n, cams_gt, b, device=device)
+    nb = min(16, V)
+    b = Batch(cams_gt, list(range(nb)), device=device, capacity=Batch.capacity_for(cams_gt, nb))
+    r = Renderer(g_gt.n, cams_gt, b, device=device)
+    for v0 in range(0, V, nb):
+        views = list(range(v0, min(V, v0 + nb)))
+        if len(views) < nb:
+            b = Batch(cams_gt, views, device=device)
+            r = Renderer(g_gt.n, cams_gt, b, device=device)
+        else:
+            b.set_views(cams_gt, views)
         r.ensure_capacity(g_gt)
         r.forward(g_gt)
-        targets[int(off[v0]):int(off[views[-1] + 1])].copy_(r.image)
-        del r
+        targets[int(off[v0]):int(off[views[-1] + 1])].copy_(r.image[:b.pixels])
+    del r
     tr = w["tracks"]
     X = torch.as_tensor(tr["X"], dtype=torch.float32, device=device)
     Rt = torch.as_tensor(w["Rt_gt"], dtype=torch.float32, device=device)
@@ -248,6 +443,11 @@ def gpu_inputs(name, device):
                 targets=targets, off=off)
 
 
+def uneven(w) -> bool:
+    W = w["workload"]
+    return W.width[0] != W.width[1] or W.height[0] != W.height[1]
+
+
 def tuning_trials(tune):
     """Best eager step time (ms) the autotuner measured per tile size, and
     per tile size the forward/backward stage times per staging batch."""
@@ -263,17 +463,23 @@ def tuning_trials(tune):
     return out
 
 
-def tune_child(workload, mode, local, cache_path, lambda_ssim=0.0):
+def tune_child(workload, mode, local, cache_path, lambda_ssim=0.0, w_path=None):
     """Autotunes the step of `workload` on GPU `local` and writes the result
-    (with its trial timings) to the tuning cache at cache_path."""
+    (with its trial timings) to the tuning cache at cache_path.  w_path: the
+    synthetic workload pickled by the parent (saves drawing it again)."""
     import json
+    import pickle
     import torch
     torch.cuda.set_device(local)
     from paper_2603_04847_gb300.autotune import autotune
-    inp = gpu_inputs(workload, "cuda:%d" % local)
+    w = None
+    if w_path:
+        with open(w_path, "rb") as f:
+            w = pickle.load(f)
+    inp = gpu_inputs(workload, "cuda:%d" % local, w)
     W = inp["w"]["workload"]
     views = list(range(min(W.batch, W.n_views)))
-    js = make_step(inp, views, mode, W.lambda_ba, lambda_ssim=lambda_ssim)
+    js = make_step(inp, views, mode, W.lambda_ba, lambda_ssim=lambda_ssim, dynamic=uneven(inp["w"]))
     tune = autotune(js, use_cache=True, cache_path=cache_path)
     with open(cache_path) as f:
         cache = json.load(f)
@@ -283,11 +489,11 @@ def tune_child(workload, mode, local, cache_path, lambda_ssim=0.0):
         json.dump(cache, f)
 
 
-def make_step(inp, views, mode, lambda_ba, tile=16, lambda_ssim=0.0):
+def make_step(inp, views, mode, lambda_ba, tile=16, lambda_ssim=0.0, dynamic=False):
     from paper_2603_04847_gb300 import Hyper, JointStep
     js = JointStep(inp["g"], inp["cams"], inp["X"], inp["obs_point"], inp["obs_xy"], inp["view_obs_offset"],
                    inp["targets"], inp["off"], views, Hyper(lambda_ba=lambda_ba, lambda_ssim=lambda_ssim), mode=mode,
-                   tile=tile)
+                   tile=tile, dynamic_batch=dynamic)
     js.ensure_capacity()
     return js
 
@@ -310,12 +516,22 @@ def time_graph(js, steps, flush, use_graph=True, batches=None):
 
 
 def set_views_async(js, views_pinned):
-    """Device copy of a batch's view ids (same per-slot sizes), no host sync."""
+    """Device copy of a batch's view ids, no host sync: views of the same
+    per-slot sizes, or any views of a batch laid out on the device (the
+    step recomputes its offsets).  The host copies of the layout follow."""
     js.batch.views.copy_(views_pinned, non_blocking=True)
+    vs = views_pinned.numpy().astype(np.int64)
+    js.batch._set_host(js.cams, vs)
     if js.mode != "batched":
         for b, sb in enumerate(js.slot_batches):
             sb.views.copy_(views_pinned[b:b + 1], non_blocking=True)
-    js.views = views_pinned.numpy().astype(np.int64)
+            sb._set_host(js.cams, vs[b:b + 1])
+    js.views = vs
+
+
+def batch_pixels(cams, views) -> int:
+    wh = cams.wh_host[np.asarray(views, dtype=np.int64).reshape(-1)]
+    return int((wh[:, 0] * wh[:, 1]).sum())
 
 
 def stage_times(js, reps, flush):
@@ -373,17 +589,21 @@ def algorithmic_model(js):
     once; the sort as one read + one write of its 12-byte pairs) and the
     compositing pair counts, from this step's own device counters."""
     import torch
-    r = js.renderers[0]
     g = js.g
     N = g.n
     K = g.sh.shape[1]
     B = js.batch.B
-    P = js.batch.n_pixels
+    P = js.batch.pixels
     I = sum(rr.n_instances() for rr in js.renderers)
-    vis = sum(int((rr.proj.n_tiles[:N * rr.batch.B] > 0).sum().item()) for rr in js.renderers)
-    pairs_bwd = sum(int(rr.n_contrib.to(torch.int64).sum().item()) for rr in js.renderers)
+    vis_slot = [(rr.proj.n_tiles[:N * rr.batch.B].reshape(rr.batch.B, N) > 0).sum(1).cpu().numpy()
+                for rr in js.renderers]
+    vis = int(sum(int(v.sum()) for v in vis_slot))
+    # brute-force pairs sum_v P_v G_v (the oracle's per-pixel loop)
+    pairs_brute = int(sum(int((np.diff(rr.batch.px_offset_host) * v).sum())
+                          for rr, v in zip(js.renderers, vis_slot)))
+    pairs_bwd = sum(int(rr.n_contrib[:rr.batch.pixels].to(torch.int64).sum().item()) for rr in js.renderers)
     added = sum(rr.count_added(js.g, js.Rt) for rr in js.renderers)
-    n_tiles_total = sum(rr.batch.n_tiles for rr in js.renderers)
+    n_tiles_total = sum(int(rr.batch.tile_offset_host[-1]) for rr in js.renderers)
     pbytes = N * (44 + 12 * K)
     M_b = int(sum(int(js.view_obs_offset[v + 1] - js.view_obs_offset[v]) for v in js.views))
     model = {
@@ -396,7 +616,7 @@ def algorithmic_model(js):
         "adam": (N * (7 + 4 + 3 * K) + js.X.shape[0] * 3) * 4 * 7,
     }
     return model, dict(instances=I, visible_records=vis, pairs_bwd=pairs_bwd, added=added, pixels=P,
-                       obs_in_batch=M_b)
+                       obs_in_batch=M_b, pairs_brute=pairs_brute)
 
 
 def slowest_rank_time(local_time: float, device="cpu") -> float:
@@ -414,7 +634,15 @@ def slowest_rank_time(local_time: float, device="cpu") -> float:
     return float(t.item())
 
 
+def spread(xs):
+    """median, p10, p90 of a list of numbers."""
+    a = np.asarray(xs, dtype=np.float64)
+    return dict(median=float(np.median(a)), p10=float(np.percentile(a, 10)), p90=float(np.percentile(a, 90)))
+
+
 def run_ours(args):
+    import pickle
+    import tempfile
     import torch
     import torch.distributed as dist
     ws, rank, local = dist_env()
@@ -424,36 +652,41 @@ def run_ours(args):
     dev = "cuda:%d" % local
     from paper_2603_04847_gb300 import build as libbuild
     libbuild.build()
-    import synth
+    w = synth.make_workload(args.workload, visible=torch_visible(dev))
     tune_cache = None
     if not args.profile_steps:
         # tune in a child process, which writes the tuning cache this process
         # then reads: a process that has run the other tile size's kernels
         # measured ~2 % slower with the chosen one
         import multiprocessing
-        import tempfile
-        tune_cache = os.path.join(tempfile.mkdtemp(prefix="gs_tune_"), "autotune.json")
+        tdir = tempfile.mkdtemp(prefix="gs_tune_")
+        tune_cache = os.path.join(tdir, "autotune.json")
+        w_path = os.path.join(tdir, "workload.pkl")
+        with open(w_path, "wb") as f:
+            pickle.dump(w, f, protocol=4)
         child = multiprocessing.get_context("spawn").Process(
-            target=tune_child, args=(args.workload, args.mode, local, tune_cache, args.lambda_ssim))
+            target=tune_child, args=(args.workload, args.mode, local, tune_cache, args.lambda_ssim, w_path))
         child.start()
         child.join()
         if child.exitcode != 0:
             raise RuntimeError("autotuning process failed (exit code %s)" % child.exitcode)
-    inp = gpu_inputs(args.workload, dev)
-    w = inp["w"]
+    inp = gpu_inputs(args.workload, dev, w)
     W = w["workload"]
+    dyn = uneven(w)
     views = list(range(min(W.batch, W.n_views)))
-    js = make_step(inp, views, args.mode, W.lambda_ba, lambda_ssim=args.lambda_ssim)
+    js = make_step(inp, views, args.mode, W.lambda_ba, lambda_ssim=args.lambda_ssim, dynamic=dyn)
     # random batches (Algorithm 1, "Sample image indices") when the workload
-    # has more views than one batch; all of them share the batch's layout
-    n_batches = args.warmup + args.steps + max(3, args.steps // 2) + 8
+    # has more views than one batch
+    n_batches = args.warmup + args.steps + max(10, args.steps) + 8
     rng = np.random.default_rng(1234)
     batch_list = None
     if W.n_views > W.batch:
-        import synth
         batch_list = torch.tensor(np.stack(synth.batches(rng, W.n_views, W.batch, n_batches)).astype(np.int32)
                                   ).pin_memory()
     if args.profile_steps:
+        if batch_list is not None:
+            set_views_async(js, batch_list[0])
+        js.ensure_capacity()
         for _ in range(args.profile_steps):
             js.step()
         torch.cuda.synchronize()
@@ -480,19 +713,17 @@ def run_ours(args):
     for _ in range(args.warmup):
         flush.zero_()
         if batch_list is not None:
-            # every batch has its own instance count: grow the buffers to the
-            # largest seen (with headroom) before timing
             set_views_async(js, batch_list[bcur])
             bcur += 1
-            js.ensure_capacity()
-            if use_graph and js.graph is None:
-                js.capture(warmup=0)
         js.run() if use_graph else js.step()
     torch.cuda.synchronize()
     flags = js.status_flags()
     if flags:
         raise RuntimeError("device status flags %d after warm-up" % flags)
 
+    timed_batches = None if batch_list is None else batch_list[bcur:bcur + args.steps]
+    px_steps = ([js.batch.pixels] * args.steps if timed_batches is None else
+                [batch_pixels(js.cams, timed_batches[i].numpy()) for i in range(args.steps)])
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.5)
@@ -500,8 +731,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.mark_on()
-    times = time_graph(js, args.steps, flush, use_graph,
-                       None if batch_list is None else batch_list[bcur:bcur + args.steps])
+    times = time_graph(js, args.steps, flush, use_graph, timed_batches)
     if batch_list is not None:
         bcur += args.steps
     torch.cuda.synchronize()
@@ -511,8 +741,9 @@ def run_ours(args):
     if js.status_flags():
         raise RuntimeError("device status flags %d during the timed steps" % js.status_flags())
     ms = tot / args.steps
-    P = js.batch.n_pixels
-    value = ws * P / 1e6 / (ms / 1e3)
+    P_mean = sum(px_steps) / len(px_steps)
+    value = ws * sum(px_steps) / 1e6 / (tot / 1e3)
+    per_step = dict(ms=spread(times), value=spread([p / 1e6 / (t / 1e3) for p, t in zip(px_steps, times)]))
 
     # per-stage event timing of the same step (eager), for the roofline
     st_ms = stage_times(js, 5, flush)
@@ -559,20 +790,31 @@ def run_ours(args):
         roof = dict(kernel=dominant, bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak,
                     traffic=traffic, peak_source=peak_src)
     step_bytes = sum(model.values())
+    step_ms_now = sum(v for k, v in st_ms.items())
     hbm_step = dict(algorithmic_bytes=step_bytes, GBps=step_bytes / (ms * 1e-3) / 1e9,
-                    frac=step_bytes / (ms * 1e-3) / 1e9 / hbm_peak)
+                    frac=step_bytes / (ms * 1e-3) / 1e9 / hbm_peak,
+                    note="bytes of the stage-timed batch over the mean graph-replay step time")
 
     # plain one-view-per-launch form on the same inputs (eager, no graph)
     plain = None
     if not args.no_plain and args.mode == "batched":
-        jp = make_step(inp, views, "plain", W.lambda_ba, tile=js.tile, lambda_ssim=args.lambda_ssim)
-        for _ in range(2):
-            flush.zero_()
-            jp.step()
+        jp = make_step(inp, views, "plain", W.lambda_ba, tile=js.tile, lambda_ssim=args.lambda_ssim, dynamic=dyn)
         npl = max(3, min(args.steps, 10))
-        pt = time_graph(jp, npl, flush, False, None if batch_list is None else batch_list[:npl])
+        pb = None if batch_list is None else batch_list[:npl]
+        if pb is not None:
+            for i in range(npl):
+                set_views_async(jp, pb[i])
+                jp.ensure_capacity()
+        for i in range(2):
+            flush.zero_()
+            if pb is not None:
+                set_views_async(jp, pb[i])
+            jp.step()
+        pt = time_graph(jp, npl, flush, False, pb)
+        ppx = [js.batch.pixels] * npl if pb is None else [batch_pixels(js.cams, pb[i].numpy()) for i in range(npl)]
         pms = sum(pt) / len(pt)
-        plain = dict(ms_per_step=pms, value=P / 1e6 / (pms / 1e3), launches_per_step=jp.kernels_per_step())
+        plain = dict(ms_per_step=pms, value=sum(ppx) / 1e6 / (sum(pt) / 1e3), launches_per_step=jp.kernels_per_step(),
+                     ms=spread(pt))
         del jp
 
     # end to end through the public API: every step's target images come
@@ -603,6 +845,7 @@ def run_ours(args):
     ts.end()
     torch.cuda.synchronize()
     plan = plan[1:]
+    e2e_px = sum(js.batch.pixels if p is None else batch_pixels(js.cams, p.numpy()) for p in plan[:n_e2e])
     flush.zero_()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -618,12 +861,12 @@ def run_ours(args):
             h2d_total += ts.put(js.views if plan[i + 1] is None else plan[i + 1].numpy())
         loss_host.copy_(js.loss, non_blocking=True)
         torch.cuda.current_stream().synchronize()
-    e2e_s = slowest_rank_time((time.perf_counter() - t0) / n_e2e, dev)
+    e2e_s = slowest_rank_time(time.perf_counter() - t0, dev)
     if js.status_flags():
         raise RuntimeError("device status flags %d during the end-to-end steps" % js.status_flags())
-    h2d_step = h2d_total / n_e2e + 8 * len(inp["off"]) + (32 if batch_list is not None else 0)
-    e2e = dict(value=ws * P / 1e6 / e2e_s, unit=UNIT, h2d_bytes_per_step=int(h2d_step),
-               d2h_bytes_per_step=16, ms_per_step=e2e_s * 1e3,
+    h2d_step = h2d_total / n_e2e + 8 * len(inp["off"]) + (4 * W.batch if batch_list is not None else 0)
+    e2e = dict(value=ws * e2e_px / 1e6 / e2e_s, unit=UNIT, h2d_bytes_per_step=int(h2d_step),
+               d2h_bytes_per_step=16, ms_per_step=e2e_s * 1e3 / n_e2e,
                pipeline="targets uploaded one step ahead on a copy stream (pinned host -> HBM)",
                l2="no flush inside the pipelined loop; the step's working set is larger than L2")
 
@@ -631,13 +874,17 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        cpu = cpu_baseline(w, args.cpu_seconds)
+        cpu = cpu_baseline(w, args.cpu_seconds, counts)
 
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
                     ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
                     data="synthetic",
                     config=dict(workload_desc(args.workload, w), mode=args.mode,
+                                batches="random %d of %d views per step%s" % (
+                                    W.batch, W.n_views, ", uneven sizes, laid out on the device" if dyn else "")
+                                if batch_list is not None else "all views every step",
+                                mean_pixels_per_step=P_mean,
                                 lambda_ssim=args.lambda_ssim,
                                 graph=use_graph, l2="flushed between steps (256 MB write)",
                                 tuning=dict(tile=tune["tile"], render_fwd_batch=tune["render_fwd_batch"],
@@ -645,7 +892,8 @@ def run_ours(args):
                                             sort_blocks_per_sm=tune["sort_blocks_per_sm"],
                                             trials=tuning_trials(tune)),
                                 parallelism="replicas" if ws > 1 else "single GPU"),
-                    steps_per_s=1e3 / ms, e2e=e2e, gpu_launches=js.kernels_per_step() * args.steps,
+                    steps_per_s=1e3 / ms, per_step=per_step, e2e=e2e,
+                    gpu_launches=js.kernels_per_step() * args.steps,
                     roofline=roof, hbm_step=hbm_step, stages=stages, counts=counts, clocks=clk,
                     cpu_baseline=cpu, plain=plain)
         print(json.dumps(line), flush=True)
@@ -719,8 +967,7 @@ def main():
         run_sfm_ba(args)
         return
     if args.impl == "reference":
-        import synth
-        w = synth.make_workload(args.workload)
+        w = synth.make_workload(args.workload, visible=np_visible)
         run_reference(args, w)
         return
     run_ours(args)

@@ -13,7 +13,8 @@
  *   sfm_ba_assemble   Eq. 4: the normal-equation blocks of one LM iteration
  *   sfm_ba_schur, sfm_ba_solve_cameras, sfm_ba_back_substitute   Eq. 4:
  *                     point elimination, camera solve, back-substitution
- *   gs_mcmc_relocate, gs_mcmc_noise   the MCMC densification (Sec. 3.3)
+ *   gs_mcmc_relocate, gs_mcmc_grow, gs_mcmc_noise, gs_mcmc_reset_moments
+ *                     the MCMC densification (Sec. 3.3)
  *   gs_render_bwd     L1 gradient of Eq. 5 (fused) + compositing backward
  *                     + projection backward with pose gradient
  *                     (Algorithm 1 "Backpropagate"; Sec. 3.3: poses are
@@ -75,12 +76,14 @@ enum {
                              treated as invisible                         */
   GS_FLAG_SORT_STALL = 4, /* a sort block gave up waiting (after 2^20
                              polls) for a predecessor block's digit
-                             counts: the tile lists are invalid          */
+                             counts: the sort stopped there, every tile
+                             list is empty and the renders show only the
+                             background                                   */
   GS_FLAG_NOT_SPD = 8     /* a bundle-adjustment camera system had a pivot
                              <= 0: its step was set to zero              */
 };
 
-#define GS_ABI_VERSION 2
+#define GS_ABI_VERSION 3
 #define GS_MAX_BATCH 64   /* views per call */
 
 typedef struct CUstream_st* gs_stream; /* = cudaStream_t */
@@ -124,15 +127,22 @@ typedef struct gs_cameras {
  * Slot b renders camera views[b].  Per-slot images are packed one after
  * another: pixel (u, v) of slot b is element px_offset[b] + v * W + u of
  * every per-pixel buffer; its tiles are global tiles tile_offset[b] ..
- * tile_offset[b+1]-1, row-major within the view. */
+ * tile_offset[b+1]-1, row-major within the view.
+ * n_pixels and n_tiles are host-side sizes of the batch's per-pixel and
+ * per-tile buffers: px_offset[B] <= n_pixels and tile_offset[B] <= n_tiles.
+ * They are equal for a batch laid out on the host; a batch whose views
+ * change on the device between calls (gs_batch_layout) gives its capacity,
+ * and the kernels then read the views' own extent from px_offset[B] and
+ * tile_offset[B].  A slot with no tiles (tile_offset[b+1] == tile_offset[b])
+ * is skipped. */
 typedef struct gs_batch {
   int32_t B;                  /* 1..GS_MAX_BATCH                            */
-  int32_t tile;               /* tile edge in pixels: 16                    */
+  int32_t tile;               /* tile edge in pixels: 16 or 32              */
   const int32_t* views;       /* [B]   device                               */
   const int64_t* px_offset;   /* [B+1] device                               */
   const int32_t* tile_offset; /* [B+1] device                               */
-  int64_t n_pixels;           /* host copy of px_offset[B]                  */
-  int32_t n_tiles;            /* host copy of tile_offset[B]                */
+  int64_t n_pixels;           /* per-pixel buffer size, >= px_offset[B]     */
+  int32_t n_tiles;            /* per-tile buffer size, >= tile_offset[B]    */
   int32_t _pad;
 } gs_batch;
 
@@ -163,11 +173,16 @@ typedef struct gs_adam {
  * in shared memory per round by the compositing forward and backward (64,
  * 128 or 256 each); sort_blocks_per_sm: grid of the sort's grid-stride
  * kernels (histogram, zeroing, ranges), in 2048-thread units per SM (1..8).
+ * sort_spin_limit: polls of an unpublished predecessor after which a radix
+ * block gives up waiting (GS_FLAG_SORT_STALL): 0 = the default 2^20; a
+ * negative value -n is a test hook in which no predecessor is ever seen
+ * published, so every wait gives up after n polls (n >= 1).
  * Not synchronised: set it while no other thread calls the library. */
 typedef struct gs_tuning {
   int32_t render_fwd_batch;
   int32_t render_bwd_batch;
   int32_t sort_blocks_per_sm;
+  int32_t sort_spin_limit;
 } gs_tuning;
 
 /* One parameter array of gs_adam_update_groups (learning rate per group). */
@@ -181,6 +196,45 @@ typedef struct gs_adam_group {
   int32_t _pad;
 } gs_adam_group;
 
+/* Double-precision counterparts of gs_gaussians, gs_gaussian_grads,
+ * gs_cameras and gs_projected, for the FP64 instantiation of the projection
+ * and compositing kernels (the *_f64 entry points): the same fields, the
+ * same layouts, with double elements.  quat and splat must be 16-byte
+ * aligned. */
+typedef struct gs_gaussians_f64 {
+  int32_t n;
+  int32_t sh_degree;
+  const double* mean;
+  const double* log_scale;
+  const double* quat;
+  const double* opacity_logit;
+  const double* sh;
+} gs_gaussians_f64;
+
+typedef struct gs_gaussian_grads_f64 {
+  double* mean;
+  double* log_scale;
+  double* quat;
+  double* opacity_logit;
+  double* sh;
+} gs_gaussian_grads_f64;
+
+typedef struct gs_cameras_f64 {
+  int32_t n_cams;
+  const int32_t* wh;
+  const double* K;
+  const double* Rt;
+  double near_plane;
+  double far_plane;
+} gs_cameras_f64;
+
+typedef struct gs_projected_f64 {
+  double* splat;     /* [B*N,12], the layout of gs_projected.splat */
+  uint16_t* rect;
+  uint32_t* n_tiles;
+  uint32_t* depth_key; /* float bits of the camera depth rounded to float */
+} gs_projected_f64;
+
 /* ---------------------------------------------------------------------- */
 
 int gs_abi_version(void);
@@ -189,8 +243,9 @@ gs_status gs_get_tuning(gs_tuning* t);
 const char* gs_last_error(void);
 /* sizeof of the ABI structs, for bindings to verify their layout:
  * 0 gs_gaussians, 1 gs_gaussian_grads, 2 gs_cameras, 3 gs_batch,
- * 4 gs_projected, 5 gs_adam, 6 gs_tuning, 7 gs_adam_group.  Returns 0 for
- * an unknown id. */
+ * 4 gs_projected, 5 gs_adam, 6 gs_tuning, 7 gs_adam_group,
+ * 8 gs_gaussians_f64, 9 gs_gaussian_grads_f64, 10 gs_cameras_f64,
+ * 11 gs_projected_f64.  Returns 0 for an unknown id. */
 size_t gs_struct_size(int which);
 /* Number of streaming multiprocessors of the current device (0 on error). */
 int gs_device_sm_count(void);
@@ -495,6 +550,67 @@ gs_status pose_se3_update(int32_t n_cams, const float* T0, float* xi,
                           float* v, const gs_adam* hp, float* Rt_out,
                           gs_stream stream);
 
+/*
+ * FP64 instantiation of the projection and compositing: the same kernels as
+ * gs_project, gs_sort_tiles, gs_render_fwd, gs_raster_bwd, gs_project_bwd
+ * and gs_render_bwd (same algorithm, same order of operations, same
+ * arguments and rules) computing in double, for checking the differentiable
+ * path against finite differences at double precision (Algorithm 1,
+ * "Backpropagate").  Per-pixel buffers (image, T_final, v_image, target,
+ * bg) are double; the tile lists are shared with the FP32 path (the depth
+ * key is the float rounding of the double depth, so depths within float
+ * rounding of each other keep index order).  The compositing kernels stage
+ * 64 splats per round whatever the tuning says.  The workspace of
+ * gs_render_bwd_f64 holds double screen-space records.
+ */
+gs_status gs_project_f64(const gs_gaussians_f64* g, const gs_cameras_f64* cams,
+                         const gs_batch* batch, const gs_projected_f64* out,
+                         int32_t* status, gs_stream stream);
+gs_status gs_sort_tiles_f64(int32_t n_gaussians, const gs_cameras_f64* cams,
+                            const gs_batch* batch,
+                            const gs_projected_f64* proj, uint32_t* tiles,
+                            uint32_t* vals, size_t capacity, uint32_t* ranges,
+                            uint32_t* n_instances, void* ws, size_t ws_bytes,
+                            int32_t* status, gs_stream stream);
+gs_status gs_render_fwd_f64(const gs_batch* batch, const gs_cameras_f64* cams,
+                            const gs_projected_f64* proj, const uint32_t* vals,
+                            const uint32_t* ranges, const double* bg,
+                            double* image, double* T_final, uint32_t* n_contrib,
+                            uint32_t* n_added, gs_stream stream);
+gs_status gs_render_bwd_workspace_f64(int32_t n_gaussians,
+                                      const gs_batch* batch, size_t* ws_bytes);
+gs_status gs_raster_bwd_f64(const gs_gaussians_f64* g,
+                            const gs_cameras_f64* cams, const gs_batch* batch,
+                            const gs_projected_f64* proj, const uint32_t* vals,
+                            const uint32_t* ranges, const double* bg,
+                            const double* image, const double* T_final,
+                            const uint32_t* n_contrib, const double* v_image,
+                            const double* target, double l1_weight,
+                            double* loss, void* ws, size_t ws_bytes,
+                            gs_stream stream);
+gs_status gs_project_bwd_f64(const gs_gaussians_f64* g,
+                             const gs_cameras_f64* cams, const gs_batch* batch,
+                             const gs_projected_f64* proj,
+                             const gs_gaussian_grads_f64* dg,
+                             double* g_pose_tangent, void* ws, size_t ws_bytes,
+                             gs_stream stream);
+gs_status gs_render_bwd_f64(const gs_gaussians_f64* g,
+                            const gs_cameras_f64* cams, const gs_batch* batch,
+                            const gs_projected_f64* proj, const uint32_t* vals,
+                            const uint32_t* ranges, const double* bg,
+                            const double* image, const double* T_final,
+                            const uint32_t* n_contrib, const double* v_image,
+                            const double* target, double l1_weight,
+                            double* loss, const gs_gaussian_grads_f64* dg,
+                            double* g_pose_tangent, void* ws, size_t ws_bytes,
+                            gs_stream stream);
+/* pose_se3_update_f64 — pose_se3_update on double arrays (T0, xi, g_xi, m,
+ * v, Rt_out), for the FP64 path. */
+gs_status pose_se3_update_f64(int32_t n_cams, const double* T0, double* xi,
+                              const double* g_tangent, double* g_xi, double* m,
+                              double* v, const gs_adam* hp, double* Rt_out,
+                              gs_stream stream);
+
 /* gs_adam_update — one Adam step on n floats p with gradient g and
  * moments m, v (Kingma & Ba, bias-corrected with t = *hp->step). */
 gs_status gs_adam_update(float* p, const float* g, float* m, float* v,
@@ -518,9 +634,14 @@ gs_status gs_adam_update_groups(const gs_adam_group* groups, int32_t n_groups,
  *  - a source drawn c times and its copies become N = c + 1 identical
  *    Gaussians with opacity o_N = 1 - (1 - o)^(1/N) and scales
  *    s o / sum_{m=1..N} C(N,m) (-1)^(m-1) o_N^m / sqrt(m);
+ *    (o_N, then bounded to [0.005, 1 - 2^-23], the scale taking the
+ *    unbounded o_N: a copy is never born dead and its logit stays finite);
  *  - each dead Gaussian then copies its source's (reset) parameters.
- * src [N] (int32) gets each Gaussian's source or -1; n_dead (device uint32,
- * may be NULL) the number of dead Gaussians.  ws: gs_mcmc_workspace(N)
+ * A draw always lands on a live Gaussian.  src [N] (int32) gets each
+ * Gaussian's source or -1; n_dead (device uint32, may be NULL) the number
+ * of dead Gaussians.  The Adam moments are not touched: the cited method
+ * restarts them for every relocated Gaussian and its source, which
+ * gs_mcmc_reset_moments(N, src, N, 0, ...) does.  ws: gs_mcmc_workspace(N)
  * bytes.  GS_ERR_ARG for null arrays, negative sizes or a short workspace.
  */
 gs_status gs_mcmc_workspace(int32_t n, size_t* ws_bytes);
@@ -529,6 +650,39 @@ gs_status gs_mcmc_relocate(int32_t n, int32_t sh_degree, float* mean,
                            float* sh, const double* u, int32_t n_u,
                            int32_t* src, uint32_t* n_dead, void* ws,
                            size_t ws_bytes, gs_stream stream);
+
+/*
+ * gs_mcmc_grow — the growth step of the same densification (Sec. 3.3, "max
+ * 3M Gaussians"; Algorithm 1 "Relocate / add Gaussians"), with the cited
+ * method's rule: n_add new Gaussians are appended after the n existing ones
+ * (the caller picks n_add; the cited rule is min(cap, floor(1.05 n)) - n).
+ * New Gaussian k draws a live source with the uniform u[k] in [0,1) exactly
+ * as gs_mcmc_relocate draws for a dead one; a source drawn c times has its
+ * opacity and scales reset for N = c + 1 as there; row n + k then copies
+ * its source's reset parameters.  The parameter arrays must hold n + n_add
+ * rows (rows n.. are overwritten); u [n_add] double; src [n_add] (int32)
+ * gets each new Gaussian's source (-1 when none is live, the row then left
+ * as it was).  ws: gs_mcmc_workspace(n) bytes.  Restart the moments with
+ * gs_mcmc_reset_moments(n + n_add, src, n_add, n, ...).
+ */
+gs_status gs_mcmc_grow(int32_t n, int32_t n_add, int32_t sh_degree, float* mean,
+                       float* log_scale, float* quat, float* opacity_logit,
+                       float* sh, const double* u, int32_t* src, void* ws,
+                       size_t ws_bytes, gs_stream stream);
+
+/*
+ * gs_mcmc_reset_moments — zeroes the Adam moments (m and v of up to 8
+ * gs_adam_group entries; p, g and lr are not read) of the Gaussians that a
+ * relocation or a growth step wrote, as the cited method restarts them: for
+ * every k < n_src with src[k] >= 0, rows row0 + k and src[k].  Each group
+ * holds n_rows rows of n / n_rows floats.  GS_ERR_ARG for more than 8
+ * groups, a group size that is not a multiple of n_rows, or row0 + n_src >
+ * n_rows.
+ */
+gs_status gs_mcmc_reset_moments(int32_t n_rows, const int32_t* src,
+                                int32_t n_src, int32_t row0,
+                                const gs_adam_group* groups, int32_t n_groups,
+                                gs_stream stream);
 
 /*
  * gs_mcmc_noise — the cited method's noise on the means (the MCMC
@@ -553,6 +707,21 @@ gs_status gs_step_advance(int32_t* step, gs_stream stream);
 gs_status gs_gather_view_pixels(const float* src, const int64_t* src_px_offset,
                                 const gs_cameras* cams, const gs_batch* batch,
                                 int32_t channels, float* dst, gs_stream stream);
+
+/* gs_batch_layout — the batch's offsets from its view ids, on the device
+ * (Algorithm 1, "Sample image indices", for a batch whose views are chosen
+ * on the device or swapped between replays of a captured step):
+ *   px_offset[b + 1] = px_offset[b] + W_v H_v,
+ *   tile_offset[b + 1] = tile_offset[b] + ceil(W_v / T) ceil(H_v / T)
+ * for v = batch->views[b], T = batch->tile, px_offset[0] = tile_offset[0]
+ * = 0.  px_offset [B+1] (8-byte aligned) and tile_offset [B+1] are device
+ * arrays, normally the batch's own.  batch->n_pixels and batch->n_tiles are
+ * the capacity: the first slot whose pixels or tiles would exceed it, and
+ * every later slot, gets zero pixels and tiles (so they are not rendered)
+ * and GS_FLAG_CAPACITY is OR-ed into *status (may be NULL). */
+gs_status gs_batch_layout(const gs_cameras* cams, const gs_batch* batch,
+                          int64_t* px_offset, int32_t* tile_offset,
+                          int32_t* status, gs_stream stream);
 
 /* gs_zero — set `bytes` bytes at ptr to zero on the stream. */
 gs_status gs_zero(void* ptr, size_t bytes, gs_stream stream);

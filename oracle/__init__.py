@@ -16,7 +16,9 @@ Passages restated (GloSplat, arXiv 2603.04847):
     below) and Algorithm 1 "Rasterize";
   * Eq. 6 (Huber reprojection loss on track points, delta = 1 px);
   * the projection pi(K, T, X) = proj(K (R X + t)) after Algorithm 1;
-  * T_i = T_i^(0) (+) dT_i (Algorithm 1), read as Exp(xi) T0.
+  * T_i = T_i^(0) (+) dT_i (Algorithm 1), read as Exp(xi) T0;
+  * one whole iteration of Algorithm 1 (joint_step): the pieces above
+    composed in the algorithm's order, with Adam on every group.
   * Eq. 4 (the SfM bundle adjustment: Levenberg-Marquardt over SE(3) poses
     and points on the Huber reprojection objective), in ``ba.py``.
   * the MCMC densification rules the paper cites (Sec. 3.3), in ``mcmc.py``.
@@ -424,6 +426,98 @@ def pose_update(T0, xi, g_tangent, m=None, v=None, lr=1e-5, beta1=0.9, beta2=0.9
                          int(bool(use_adam)), float(lr), float(beta1), float(beta2),
                          float(eps), int(step), _ptr(Rt))
     return g_xi, Rt
+
+
+def joint_step(params, X, T0, xi, wh, K, views, targets, obs_point, obs_view, obs_xy, hyper, state, step,
+               merged_tracks=False, bg=(0.0, 0.0, 0.0)):
+    """One iteration of Algorithm 1 (the joint optimisation loop) on a batch
+    of views, in its order:
+      1. compose the poses T_i = Exp(xi_i) T0_i                ("Apply pose adjustment");
+      2. render every view of the batch and take the L1 part of Eq. 5,
+         l1_weight * mean |I^ - I| per view, summed over the batch  ("Rasterize", "L_photo");
+      3. the track term of Eq. 6 over the batch's observations, Huber with
+         delta = huber_delta, weighted by lambda_BA (skipped at 0)  ("Joint BA loss");
+      4. backpropagate both into the Gaussians, the track points and the
+         per-camera pose tangents                                  ("Backpropagate");
+      5. one Adam step on every Gaussian parameter group, on the track points
+         and, unless freeze_poses, on the pose deltas (then recompose T_i)  ("Update").
+    params: dict of the five raw Gaussian arrays (float64, updated copies are
+    returned); X [K,3] track points (with merged_tracks the observations index
+    the Gaussians and the track gradient goes into the means); T0 [V,12],
+    xi [V,6]; targets: {view: image [H,W,3]}; obs_view holds each
+    observation's camera; hyper: dict with lr_mean, lr_log_scale, lr_quat,
+    lr_opacity, lr_sh, lr_track, lr_pose, beta1, beta2, eps, scene_extent,
+    lambda_ba, huber_delta, l1_weight, freeze_poses; state: dict of Adam
+    moments (created on first use, updated in place); step: the 1-based
+    Adam step.  Returns dict(params, X, xi, Rt, grads, g_X, tangent,
+    tangent_abs, loss_photo, loss_ba): the updated parameters, the
+    gradients of the iteration (tangent_abs: the sums of the absolute
+    per-term pose-tangent contributions) and the two loss terms (loss_ba the
+    unweighted sum of rho)."""
+    h = hyper
+    p = {k: np.array(v, np.float64, copy=True) for k, v in params.items()}
+    X = np.array(X, np.float64, copy=True)
+    xi = np.array(xi, np.float64, copy=True).reshape(-1, 6)
+    T0 = np.asarray(T0, np.float64).reshape(-1, 12)
+    V = T0.shape[0]
+    # 1. poses of this iteration
+    Rt = np.stack([pose_update(T0[i:i + 1], xi[i:i + 1].copy(), np.zeros((1, 6)), use_adam=False)[1][0]
+                   for i in range(V)])
+    cams = [camera_from_rt(int(wh[i][0]), int(wh[i][1]), K[i], Rt[i]) for i in range(V)]
+    sc = Scene(p["mean"], p["log_scale"], p["quat"], p["opacity_logit"], p["sh"])
+    grads = {k: np.zeros_like(v) for k, v in p.items()}
+    tangent = np.zeros((V, 6))
+    tangent_abs = np.zeros((V, 6))
+    loss_photo = 0.0
+    # 2.-4. photometric term of every view of the batch and its backward
+    for v in views:
+        img = render(sc, cams[v], bg=bg)["image"]
+        lv, dv = l1_loss_grad(img, targets[v], weight=h["l1_weight"])
+        loss_photo += lv
+        g = render_bwd(sc, cams[v], dv, bg=bg)
+        for k in grads:
+            grads[k] += g[k].reshape(grads[k].shape)
+        tangent[v] += g["tangent"]
+        tangent_abs[v] += g["tangent_abs"]
+    # 3.-4. the track term over the observations of the batch's views
+    loss_ba = 0.0
+    g_X = np.zeros_like(p["mean"] if merged_tracks else X)
+    if h["lambda_ba"] != 0.0:
+        sel = np.isin(np.asarray(obs_view), np.asarray(views))
+        pts = p["mean"] if merged_tracks else X
+        loss_ba, g_X, tan_t, _, tabs = track(pts, np.asarray(obs_point)[sel], np.asarray(obs_view)[sel],
+                                             np.asarray(obs_xy)[sel], cams, h["huber_delta"], h["lambda_ba"],
+                                             with_abs=True)
+        tangent += tan_t
+        tangent_abs += tabs
+        if merged_tracks:
+            grads["mean"] += g_X
+    # 5. Adam on every group, then the poses
+    ext = h["scene_extent"]
+    lrs = dict(mean=h["lr_mean"] * ext, log_scale=h["lr_log_scale"], quat=h["lr_quat"],
+               opacity_logit=h["lr_opacity"], sh=h["lr_sh"])
+    for k in p:
+        m = state.setdefault("m_" + k, np.zeros(p[k].size))
+        vv = state.setdefault("v_" + k, np.zeros(p[k].size))
+        flat = p[k].reshape(-1).copy()
+        adam(flat, grads[k].reshape(-1), m, vv, lrs[k], h["beta1"], h["beta2"], h["eps"], step)
+        p[k] = flat.reshape(p[k].shape)
+    if not merged_tracks:
+        m = state.setdefault("m_X", np.zeros(X.size))
+        vv = state.setdefault("v_X", np.zeros(X.size))
+        flat = X.reshape(-1).copy()
+        adam(flat, g_X.reshape(-1), m, vv, h["lr_track"] * ext, h["beta1"], h["beta2"], h["eps"], step)
+        X = flat.reshape(X.shape)
+    else:
+        X = p["mean"]
+    Rt_new = Rt
+    if not h["freeze_poses"]:
+        m = state.setdefault("m_xi", np.zeros((V, 6)))
+        vv = state.setdefault("v_xi", np.zeros((V, 6)))
+        _, Rt_new = pose_update(T0, xi, tangent, m, vv, lr=h["lr_pose"], beta1=h["beta1"], beta2=h["beta2"],
+                                eps=h["eps"], step=step)
+    return dict(params=p, X=X, xi=xi, Rt=Rt_new, grads=grads, g_X=g_X, tangent=tangent, tangent_abs=tangent_abs,
+                loss_photo=loss_photo, loss_ba=loss_ba)
 
 
 def tile_lists(proj: np.ndarray, width: int, height: int, tile: int):

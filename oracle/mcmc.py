@@ -16,6 +16,17 @@ Readings (the cited method's published rules):
         s_N = s * o / sum_{i=1..N} sum_{k=0..i-1} C(i-1, k) (-1)^k o_N^(k+1) / sqrt(k+1)
     (the same integral of the composited alpha along a line through the
     centre; scales per axis, so the covariance scales by the square);
+    The reset opacity is then bounded to [0.005, 1 - 2^-23] (the cited
+    method's bounds: a copy is never born dead, and its logit stays finite),
+    the scale being computed from the unbounded o_N;
+  * growth ("add Gaussians", up to the cap): n_add = min(cap, floor(1.05 n))
+    - n new Gaussians, each drawn like a relocation source (probability
+    proportional to opacity, live ones only) by its own uniform; the drawn
+    sources are reset by the same rule (N = times drawn + 1) and the new
+    Gaussians, appended after the n existing ones in the order of the
+    uniforms, copy their source's reset parameters;
+  * the Adam moments of every Gaussian written by relocation or growth (the
+    copies and their sources) restart from zero;
   * noise on the means: mu += noise_lr * sigmoid(-100 (o - 0.005)) * Sigma eta
     with Sigma = R diag(s)^2 R^T the Gaussian's covariance and eta ~ N(0, I)
     given.
@@ -27,6 +38,8 @@ from math import comb
 import numpy as np
 
 DEAD_OPACITY = 0.005
+MAX_OPACITY = 1.0 - 2.0 ** -23     # 1 - float32 epsilon
+GROWTH_RATE = 0.05
 NOISE_K = 100.0
 
 
@@ -34,16 +47,21 @@ def sigmoid(x):
     return 1.0 / (1.0 + np.exp(-np.asarray(x, np.float64)))
 
 
-def relocated_opacity_scale(o, s, N):
+def relocated_opacity_scale(o, s, N, bounded=True):
     """Opacity and per-axis scales of each of N identical Gaussians that
-    replace one of opacity o and scales s (N = 1 leaves them unchanged)."""
+    replace one of opacity o and scales s (N = 1 leaves them unchanged);
+    bounded: the opacity clipped to [0.005, 1 - 2^-23] after the scale is
+    formed."""
     o = float(o)
     oN = 1.0 - (1.0 - o) ** (1.0 / N)
     den = 0.0
     for i in range(1, N + 1):
         for k in range(i):
             den += comb(i - 1, k) * (-1.0) ** k * oN ** (k + 1) / np.sqrt(k + 1.0)
-    return oN, np.asarray(s, np.float64) * o / den
+    sN = np.asarray(s, np.float64) * o / den
+    if bounded:
+        oN = min(max(oN, DEAD_OPACITY), MAX_OPACITY)
+    return oN, sN
 
 
 def draw_sources(opacity, dead, u):
@@ -66,14 +84,40 @@ def relocate(params, u):
     if len(dead_idx) == 0 or dead.all():
         return p, np.zeros(0, np.int64)
     src = draw_sources(o, dead, np.asarray(u)[:len(dead_idx)])
-    counts = np.bincount(src, minlength=len(o))
+    _reset_sources(p, np.bincount(src, minlength=len(o)))
+    for d, j in zip(dead_idx, src):
+        for k in p:
+            p[k][d] = p[k][j]
+    return p, src
+
+
+def n_grow(n, cap, rate=GROWTH_RATE):
+    """Gaussians the growth step adds to n: min(cap, floor((1 + rate) n)) - n
+    (never negative)."""
+    return max(0, min(int(cap), int(np.floor((1.0 + rate) * n))) - int(n))
+
+
+def _reset_sources(p, counts):
+    o = sigmoid(p["opacity_logit"])
     for j in np.nonzero(counts)[0]:
         oN, sN = relocated_opacity_scale(o[j], np.exp(p["log_scale"][j]), int(counts[j]) + 1)
         p["opacity_logit"][j] = np.log(oN / (1.0 - oN))
         p["log_scale"][j] = np.log(sN)
-    for d, j in zip(dead_idx, src):
-        for k in p:
-            p[k][d] = p[k][j]
+
+
+def grow(params, u):
+    """The growth step with one uniform per new Gaussian (len(u) of them):
+    returns the n + len(u) Gaussians and each new one's source."""
+    p = {k: np.array(v, np.float64, copy=True) for k, v in params.items()}
+    o = sigmoid(p["opacity_logit"])
+    dead = o <= DEAD_OPACITY
+    u = np.asarray(u, np.float64)
+    if len(u) == 0 or dead.all():
+        return p, np.zeros(0, np.int64)
+    src = draw_sources(o, dead, u)
+    _reset_sources(p, np.bincount(src, minlength=len(o)))
+    for k in p:
+        p[k] = np.concatenate([p[k], p[k][src]], axis=0)
     return p, src
 
 

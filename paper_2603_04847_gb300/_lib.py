@@ -53,7 +53,8 @@ class gs_adam(ctypes.Structure):
 
 
 class gs_tuning(ctypes.Structure):
-    _fields_ = [("render_fwd_batch", c_int32), ("render_bwd_batch", c_int32), ("sort_blocks_per_sm", c_int32)]
+    _fields_ = [("render_fwd_batch", c_int32), ("render_bwd_batch", c_int32), ("sort_blocks_per_sm", c_int32),
+                ("sort_spin_limit", c_int32)]
 
 
 class gs_adam_group(ctypes.Structure):
@@ -61,7 +62,25 @@ class gs_adam_group(ctypes.Structure):
                 ("lr", c_float), ("_pad", c_int32)]
 
 
-STRUCTS = [gs_gaussians, gs_gaussian_grads, gs_cameras, gs_batch, gs_projected, gs_adam, gs_tuning, gs_adam_group]
+class gs_gaussians_f64(ctypes.Structure):
+    _fields_ = gs_gaussians._fields_
+
+
+class gs_gaussian_grads_f64(ctypes.Structure):
+    _fields_ = gs_gaussian_grads._fields_
+
+
+class gs_cameras_f64(ctypes.Structure):
+    _fields_ = [("n_cams", c_int32), ("wh", c_void_p), ("K", c_void_p), ("Rt", c_void_p),
+                ("near_plane", ctypes.c_double), ("far_plane", ctypes.c_double)]
+
+
+class gs_projected_f64(ctypes.Structure):
+    _fields_ = gs_projected._fields_
+
+
+STRUCTS = [gs_gaussians, gs_gaussian_grads, gs_cameras, gs_batch, gs_projected, gs_adam, gs_tuning, gs_adam_group,
+           gs_gaussians_f64, gs_gaussian_grads_f64, gs_cameras_f64, gs_projected_f64]
 
 # name -> (restype, argtypes)
 PROTOTYPES = {
@@ -99,6 +118,7 @@ PROTOTYPES = {
     "gs_adam_update": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     "gs_step_advance": (ctypes.c_int, [c_void_p, c_void_p]),
     "gs_zero": (ctypes.c_int, [c_void_p, c_size_t, c_void_p]),
+    "gs_batch_layout": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "gs_gather_view_pixels": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "gs_photo_loss_workspace": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_size_t)]),
     "gs_mcmc_workspace": (ctypes.c_int, [c_int32, ctypes.POINTER(c_size_t)]),
@@ -106,6 +126,9 @@ PROTOTYPES = {
                                         c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "gs_mcmc_noise": (ctypes.c_int, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float,
                                      c_void_p]),
+    "gs_mcmc_grow": (ctypes.c_int, [c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "gs_mcmc_reset_moments": (ctypes.c_int, [c_int32, c_void_p, c_int32, c_int32, c_void_p, c_int32, c_void_p]),
     "sfm_ba_schur": (ctypes.c_int, [c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_void_p, c_void_p, ctypes.c_double, c_void_p, c_void_p, c_void_p,
                                     c_void_p]),
@@ -121,6 +144,22 @@ PROTOTYPES = {
                                        c_void_p]),
     "gs_photo_loss": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_float, c_void_p,
                                      c_void_p, c_void_p, c_size_t, c_void_p]),
+    "gs_project_f64": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "gs_sort_tiles_f64": (ctypes.c_int, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
+                                         c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),
+    "gs_render_fwd_f64": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                         c_void_p, c_void_p, c_void_p, c_void_p]),
+    "gs_render_bwd_workspace_f64": (ctypes.c_int, [c_int32, c_void_p, ctypes.POINTER(c_size_t)]),
+    "gs_raster_bwd_f64": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_double,
+                                         c_void_p, c_void_p, c_size_t, c_void_p]),
+    "gs_project_bwd_f64": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                          c_size_t, c_void_p]),
+    "gs_render_bwd_f64": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_double,
+                                         c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "pose_se3_update_f64": (ctypes.c_int, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                           c_void_p, c_void_p, c_void_p]),
 }
 
 _lib = None
@@ -147,7 +186,7 @@ def load(path: str = LIB_PATH):
         if lib.gs_struct_size(i) != ctypes.sizeof(s):
             raise GsError("ABI mismatch for %s: C %d vs ctypes %d" % (s.__name__, lib.gs_struct_size(i),
                                                                       ctypes.sizeof(s)))
-    if lib.gs_abi_version() != 2:
+    if lib.gs_abi_version() != 3:
         raise GsError("unexpected libgs ABI version")
     _lib = lib
     return lib

@@ -51,23 +51,37 @@ class Gaussians:
     def tensors(self):
         return [self.mean, self.log_scale, self.quat, self.opacity_logit, self.sh]
 
+    @property
+    def f64(self) -> bool:
+        """float64 parameters: the FP64 instantiation of the kernels."""
+        return self.mean.dtype == torch.float64
+
+    def _check_dtype(self):
+        dt = self.mean.dtype
+        if dt not in (torch.float32, torch.float64) or any(t.dtype != dt for t in self.tensors()):
+            raise ValueError("Gaussian parameters must all be float32 or all float64")
+
     def c(self):
         _need_cuda(*self.tensors())
-        return _lib.gs_gaussians(self.n, self.sh_degree, self.mean.data_ptr(), self.log_scale.data_ptr(),
-                                 self.quat.data_ptr(), self.opacity_logit.data_ptr(), self.sh.data_ptr())
+        self._check_dtype()
+        cls = _lib.gs_gaussians_f64 if self.f64 else _lib.gs_gaussians
+        return cls(self.n, self.sh_degree, self.mean.data_ptr(), self.log_scale.data_ptr(),
+                   self.quat.data_ptr(), self.opacity_logit.data_ptr(), self.sh.data_ptr())
 
     def grads_c(self):
         _need_cuda(*self.tensors())
-        return _lib.gs_gaussian_grads(self.mean.data_ptr(), self.log_scale.data_ptr(), self.quat.data_ptr(),
-                                      self.opacity_logit.data_ptr(), self.sh.data_ptr())
+        self._check_dtype()
+        cls = _lib.gs_gaussian_grads_f64 if self.f64 else _lib.gs_gaussian_grads
+        return cls(self.mean.data_ptr(), self.log_scale.data_ptr(), self.quat.data_ptr(),
+                   self.opacity_logit.data_ptr(), self.sh.data_ptr())
 
     @staticmethod
     def zeros_like(g: "Gaussians") -> "Gaussians":
         return Gaussians(*[torch.zeros_like(t) for t in g.tensors()])
 
     @staticmethod
-    def from_numpy(d: dict, device="cuda") -> "Gaussians":
-        f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=device).contiguous()
+    def from_numpy(d: dict, device="cuda", dtype=torch.float32) -> "Gaussians":
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=device).contiguous()
         return Gaussians(f(d["mean"]), f(d["log_scale"]), f(d["quat"]), f(d["opacity_logit"]).reshape(-1),
                          f(d["sh"]))
 
@@ -91,7 +105,19 @@ class Cameras:
     def V(self):
         return self.wh.shape[0]
 
-    def c(self, Rt: torch.Tensor = None):
+    def c(self, Rt: torch.Tensor = None, f64: bool = False):
+        """The C struct; f64: gs_cameras_f64 with the intrinsics in double
+        and Rt (if given) float64."""
+        if f64:
+            if getattr(self, "_K64", None) is None:
+                self._K64 = self.K.to(torch.float64).contiguous()
+            Rt = self.Rt.to(torch.float64).contiguous() if Rt is None else Rt
+            if Rt.dtype != torch.float64:
+                raise ValueError("the FP64 path needs float64 poses")
+            self._Rt64_keep = Rt
+            _need_cuda(self.wh, self._K64, Rt)
+            return _lib.gs_cameras_f64(self.V, self.wh.data_ptr(), self._K64.data_ptr(), Rt.data_ptr(),
+                                       float(self.near), float(self.far))
         Rt = self.Rt if Rt is None else Rt
         _need_cuda(self.wh, self.K, Rt)
         return _lib.gs_cameras(self.V, self.wh.data_ptr(), self.K.data_ptr(), Rt.data_ptr(),
@@ -105,47 +131,104 @@ class Cameras:
                        near, far, np.asarray(wh).astype(np.int64))
 
 
+def _layout_host(wh: np.ndarray, tile: int):
+    """Pixel and tile offsets [B+1] of views of sizes wh [B,2]."""
+    W, H = wh[:, 0].astype(np.int64), wh[:, 1].astype(np.int64)
+    px = np.zeros(len(W) + 1, dtype=np.int64)
+    px[1:] = np.cumsum(W * H)
+    to = np.zeros(len(W) + 1, dtype=np.int64)
+    to[1:] = np.cumsum(((W + tile - 1) // tile) * ((H + tile - 1) // tile))
+    return px, to
+
+
 class Batch:
     """A batch of views rendered together; per-slot images packed in slot
-    order (pixel offsets) and tiles numbered globally (tile offsets)."""
+    order (pixel offsets) and tiles numbered globally (tile offsets).
 
-    def __init__(self, cams: Cameras, views, tile: int = TILE, device="cuda"):
+    capacity=None sizes the batch's buffers for exactly these views.  With
+    capacity=(n_pixels, n_tiles) the buffers hold any views whose totals fit,
+    and the offsets are recomputed on the device from the device copy of the
+    view ids (gs_batch_layout): views of other sizes can then be swapped in
+    without re-allocating, including between replays of a captured step."""
+
+    def __init__(self, cams: Cameras, views, tile: int = TILE, device="cuda", capacity=None):
         views = np.asarray(views, dtype=np.int64).reshape(-1)
         if not 1 <= len(views) <= _lib.GS_MAX_BATCH:
             raise ValueError("batch size must be 1..%d" % _lib.GS_MAX_BATCH)
+        self.tile = tile
+        self.B = len(views)
+        self._set_host(cams, views)
+        self.dynamic = capacity is not None
+        if self.dynamic:
+            self.n_pixels, self.n_tiles = int(capacity[0]), int(capacity[1])
+            if self.pixels > self.n_pixels or int(self.tile_offset_host[-1]) > self.n_tiles:
+                raise ValueError("views exceed the batch capacity")
+        else:
+            self.n_pixels = self.pixels
+            self.n_tiles = int(self.tile_offset_host[-1])
+        self.views = torch.as_tensor(views.astype(np.int32), device=device)
+        self.px_offset = torch.as_tensor(self.px_offset_host, device=device)
+        self.tile_offset = torch.as_tensor(self.tile_offset_host.astype(np.int32), device=device)
+
+    def _set_host(self, cams: Cameras, views):
         wh = cams.wh_host[views]
         self.views_host = views
         self.W = wh[:, 0].copy()
         self.H = wh[:, 1].copy()
-        px = np.zeros(len(views) + 1, dtype=np.int64)
-        px[1:] = np.cumsum(self.W * self.H)
-        tx = (self.W + tile - 1) // tile
-        ty = (self.H + tile - 1) // tile
-        to = np.zeros(len(views) + 1, dtype=np.int64)
-        to[1:] = np.cumsum(tx * ty)
-        self.px_offset_host = px
-        self.tile_offset_host = to
-        self.tile = tile
-        self.B = len(views)
-        self.n_pixels = int(px[-1])
-        self.n_tiles = int(to[-1])
-        self.views = torch.as_tensor(views.astype(np.int32), device=device)
-        self.px_offset = torch.as_tensor(px, device=device)
-        self.tile_offset = torch.as_tensor(to.astype(np.int32), device=device)
+        self.px_offset_host, self.tile_offset_host = _layout_host(wh, self.tile)
+
+    @property
+    def pixels(self) -> int:
+        """Pixels of the current views (n_pixels is the buffers' size)."""
+        return int(self.px_offset_host[-1])
+
+    @staticmethod
+    def capacity_for(cams: Cameras, B: int, tile: int = TILE, views=None):
+        """(n_pixels, n_tiles) that hold any B of `views` (default: all
+        cameras): the sums over the B largest views."""
+        wh = cams.wh_host if views is None else cams.wh_host[np.asarray(views, dtype=np.int64).reshape(-1)]
+        W, H = wh[:, 0].astype(np.int64), wh[:, 1].astype(np.int64)
+        px = np.sort(W * H)[::-1][:B].sum()
+        tl = np.sort(((W + tile - 1) // tile) * ((H + tile - 1) // tile))[::-1][:B].sum()
+        return int(px), int(tl)
+
+    def fits(self, cams: "Cameras", views) -> bool:
+        views = np.asarray(views, dtype=np.int64).reshape(-1)
+        if len(views) != self.B:
+            return False
+        px, to = _layout_host(cams.wh_host[views], self.tile)
+        return int(px[-1]) <= self.n_pixels and int(to[-1]) <= self.n_tiles
 
     def same_layout(self, cams: "Cameras", views) -> bool:
-        """True when `views` has the per-slot sizes of the current batch."""
+        """True when `views` can replace the current ones in place: any
+        views within the capacity of a device-laid-out batch, else views of
+        the current per-slot sizes."""
+        if self.dynamic:
+            return self.fits(cams, views)
         wh = cams.wh_host[np.asarray(views, dtype=np.int64).reshape(-1)]
         return len(wh) == self.B and np.array_equal(wh[:, 0], self.W) and np.array_equal(wh[:, 1], self.H)
 
-    def set_views(self, cams: "Cameras", views):
-        """Replaces the batch's views by views of the same sizes, in place on
-        the device (buffers, kernels and captured graphs stay valid)."""
+    def set_views(self, cams: "Cameras", views, stream=None):
+        """Replaces the batch's views in place on the device (buffers,
+        kernels and captured graphs stay valid).  A device-laid-out batch
+        recomputes its offsets on the stream; otherwise the views must have
+        the current per-slot sizes."""
         if not self.same_layout(cams, views):
-            raise ValueError("set_views needs views with the same per-slot sizes")
+            raise ValueError("set_views: the views do not fit this batch's layout or capacity")
         views = np.asarray(views, dtype=np.int64).reshape(-1)
-        self.views_host = views
-        self.views.copy_(torch.as_tensor(views.astype(np.int32)), non_blocking=False)
+        self._set_host(cams, views)
+        st = torch.cuda.current_stream() if stream is None else stream
+        with torch.cuda.stream(st):
+            self.views.copy_(torch.as_tensor(views.astype(np.int32)), non_blocking=False)
+            if self.dynamic:
+                self.layout(cams, stream=st)
+
+    def layout(self, cams: "Cameras", status: torch.Tensor = None, stream=None):
+        """gs_batch_layout on this batch's own offset arrays."""
+        lib = _lib.load()
+        cc, bc = cams.c(), self.c()
+        check(lib.gs_batch_layout(ctypes.byref(cc), ctypes.byref(bc), _p(self.px_offset), _p(self.tile_offset),
+                                  _p(status), _stream(stream)), "gs_batch_layout")
 
     def c(self):
         return _lib.gs_batch(self.B, self.tile, self.views.data_ptr(), self.px_offset.data_ptr(),
@@ -158,19 +241,24 @@ class Batch:
 
 
 class Projected:
-    """Per-(slot, Gaussian) records: splat [B*N,12] f32, rect [B*N,4] u16,
-    n_tiles [B*N] u32, depth_key [B*N] u32 (int16/int32 storage)."""
+    """Per-(slot, Gaussian) records: splat [B*N,12] (float32, or float64 for
+    the FP64 path), rect [B*N,4] u16, n_tiles [B*N] u32, depth_key [B*N]
+    u32 (int16/int32 storage)."""
 
-    def __init__(self, n: int, B: int, device="cuda"):
+    def __init__(self, n: int, B: int, device="cuda", dtype=torch.float32):
         M = n * B
-        self.splat = torch.empty((max(M, 1), 12), dtype=torch.float32, device=device)
+        self.splat = torch.empty((max(M, 1), 12), dtype=dtype, device=device)
         self.rect = torch.empty((max(M, 1), 4), dtype=torch.int16, device=device)
         self.n_tiles = torch.zeros((max(M, 1),), dtype=torch.int32, device=device)
         self.depth_key = torch.empty((max(M, 1),), dtype=torch.int32, device=device)
 
+    @property
+    def f64(self) -> bool:
+        return self.splat.dtype == torch.float64
+
     def c(self):
-        return _lib.gs_projected(self.splat.data_ptr(), self.rect.data_ptr(), self.n_tiles.data_ptr(),
-                                 self.depth_key.data_ptr())
+        cls = _lib.gs_projected_f64 if self.f64 else _lib.gs_projected
+        return cls(self.splat.data_ptr(), self.rect.data_ptr(), self.n_tiles.data_ptr(), self.depth_key.data_ptr())
 
 
 class TileLists:
@@ -199,21 +287,27 @@ def new_status(device="cuda"):
 # thin wrappers, same names as the C entry points
 
 
+def _fn(lib, name, f64):
+    """The entry point `name`, or its FP64 instantiation `name_f64`."""
+    return getattr(lib, name + "_f64") if f64 else getattr(lib, name)
+
+
 def gs_project(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, status: torch.Tensor,
                Rt: torch.Tensor = None, stream=None):
     lib = _lib.load()
-    gc, cc, bc, pc = g.c(), cams.c(Rt), batch.c(), proj.c()
-    check(lib.gs_project(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc),
-                         _p(status), _stream(stream)), "gs_project")
+    gc, cc, bc, pc = g.c(), cams.c(Rt, f64=g.f64), batch.c(), proj.c()
+    check(_fn(lib, "gs_project", g.f64)(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc),
+                                        _p(status), _stream(stream)), "gs_project")
 
 
 def gs_sort_tiles(n: int, cams: Cameras, batch: Batch, proj: Projected, tl: TileLists, status: torch.Tensor,
                   Rt: torch.Tensor = None, stream=None):
     lib = _lib.load()
-    cc, bc, pc = cams.c(Rt), batch.c(), proj.c()
-    check(lib.gs_sort_tiles(n, ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc), _p(tl.tiles), _p(tl.vals),
-                            tl.capacity, _p(tl.ranges), _p(tl.n_instances), _p(tl.ws), tl.ws.numel(),
-                            _p(status), _stream(stream)), "gs_sort_tiles")
+    cc, bc, pc = cams.c(Rt, f64=proj.f64), batch.c(), proj.c()
+    check(_fn(lib, "gs_sort_tiles", proj.f64)(n, ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc), _p(tl.tiles),
+                                              _p(tl.vals), tl.capacity, _p(tl.ranges), _p(tl.n_instances),
+                                              _p(tl.ws), tl.ws.numel(), _p(status), _stream(stream)),
+          "gs_sort_tiles")
 
 
 def gs_render_fwd(batch: Batch, cams: Cameras, proj: Projected, tl: TileLists, bg: torch.Tensor,
@@ -221,17 +315,18 @@ def gs_render_fwd(batch: Batch, cams: Cameras, proj: Projected, tl: TileLists, b
                   n_added: torch.Tensor = None):
     lib = _lib.load()
     _need_cuda(bg, image, T_final, n_contrib, n_added)
-    cc, bc, pc = cams.c(Rt), batch.c(), proj.c()
-    check(lib.gs_render_fwd(ctypes.byref(bc), ctypes.byref(cc), ctypes.byref(pc), _p(tl.vals), _p(tl.ranges),
-                            _p(bg), _p(image), _p(T_final), _p(n_contrib), _p(n_added), _stream(stream)),
+    cc, bc, pc = cams.c(Rt, f64=proj.f64), batch.c(), proj.c()
+    check(_fn(lib, "gs_render_fwd", proj.f64)(ctypes.byref(bc), ctypes.byref(cc), ctypes.byref(pc), _p(tl.vals),
+                                              _p(tl.ranges), _p(bg), _p(image), _p(T_final), _p(n_contrib),
+                                              _p(n_added), _stream(stream)),
           "gs_render_fwd")
 
 
-def render_bwd_workspace_bytes(n: int, batch: Batch) -> int:
+def render_bwd_workspace_bytes(n: int, batch: Batch, f64: bool = False) -> int:
     lib = _lib.load()
     ws = ctypes.c_size_t(0)
     bc = batch.c()
-    check(lib.gs_render_bwd_workspace(n, ctypes.byref(bc), ctypes.byref(ws)), "gs_render_bwd_workspace")
+    check(_fn(lib, "gs_render_bwd_workspace", f64)(n, ctypes.byref(bc), ctypes.byref(ws)), "gs_render_bwd_workspace")
     return ws.value
 
 
@@ -240,11 +335,12 @@ def gs_render_bwd(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, tl
                   loss, dg: Gaussians, g_pose_tangent: torch.Tensor, ws: torch.Tensor, Rt=None, stream=None):
     lib = _lib.load()
     _need_cuda(bg, T_final, n_contrib, g_pose_tangent, ws, image, v_image, target, loss)
-    gc, cc, bc, pc, dgc = g.c(), cams.c(Rt), batch.c(), proj.c(), dg.grads_c()
-    check(lib.gs_render_bwd(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc),
-                            _p(tl.vals), _p(tl.ranges), _p(bg), _p(image), _p(T_final), _p(n_contrib),
-                            _p(v_image), _p(target), float(l1_weight), _p(loss), ctypes.byref(dgc),
-                            _p(g_pose_tangent), _p(ws), ws.numel(), _stream(stream)), "gs_render_bwd")
+    gc, cc, bc, pc, dgc = g.c(), cams.c(Rt, f64=g.f64), batch.c(), proj.c(), dg.grads_c()
+    check(_fn(lib, "gs_render_bwd", g.f64)(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc),
+                                           _p(tl.vals), _p(tl.ranges), _p(bg), _p(image), _p(T_final),
+                                           _p(n_contrib), _p(v_image), _p(target), float(l1_weight), _p(loss),
+                                           ctypes.byref(dgc), _p(g_pose_tangent), _p(ws), ws.numel(),
+                                           _stream(stream)), "gs_render_bwd")
 
 
 def gs_raster_bwd(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, tl: TileLists, bg, image,
@@ -252,20 +348,21 @@ def gs_raster_bwd(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, tl
                   stream=None):
     lib = _lib.load()
     _need_cuda(bg, T_final, n_contrib, ws, image, v_image, target, loss)
-    gc, cc, bc, pc = g.c(), cams.c(Rt), batch.c(), proj.c()
-    check(lib.gs_raster_bwd(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc),
-                            _p(tl.vals), _p(tl.ranges), _p(bg), _p(image), _p(T_final), _p(n_contrib),
-                            _p(v_image), _p(target), float(l1_weight), _p(loss), _p(ws), ws.numel(),
-                            _stream(stream)), "gs_raster_bwd")
+    gc, cc, bc, pc = g.c(), cams.c(Rt, f64=g.f64), batch.c(), proj.c()
+    check(_fn(lib, "gs_raster_bwd", g.f64)(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc),
+                                           _p(tl.vals), _p(tl.ranges), _p(bg), _p(image), _p(T_final),
+                                           _p(n_contrib), _p(v_image), _p(target), float(l1_weight), _p(loss),
+                                           _p(ws), ws.numel(), _stream(stream)), "gs_raster_bwd")
 
 
 def gs_project_bwd(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, dg: Gaussians,
                    g_pose_tangent: torch.Tensor, ws: torch.Tensor, Rt=None, stream=None):
     lib = _lib.load()
     _need_cuda(g_pose_tangent, ws)
-    gc, cc, bc, pc, dgc = g.c(), cams.c(Rt), batch.c(), proj.c(), dg.grads_c()
-    check(lib.gs_project_bwd(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc),
-                             ctypes.byref(dgc), _p(g_pose_tangent), _p(ws), ws.numel(), _stream(stream)),
+    gc, cc, bc, pc, dgc = g.c(), cams.c(Rt, f64=g.f64), batch.c(), proj.c(), dg.grads_c()
+    check(_fn(lib, "gs_project_bwd", g.f64)(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc),
+                                            ctypes.byref(pc), ctypes.byref(dgc), _p(g_pose_tangent), _p(ws),
+                                            ws.numel(), _stream(stream)),
           "gs_project_bwd")
 
 
@@ -360,6 +457,34 @@ def gs_mcmc_relocate(g: Gaussians, u: torch.Tensor, src: torch.Tensor, n_dead=No
                                _stream(stream)), "gs_mcmc_relocate")
 
 
+def gs_mcmc_grow(g: Gaussians, n: int, u: torch.Tensor, src: torch.Tensor, stream=None):
+    """Growth step: g holds n live rows plus room for len(u) more; rows
+    n.. receive the new Gaussians (u: float64 uniforms, one per new
+    Gaussian; src [len(u)] int32 out: each new one's source)."""
+    lib = _lib.load()
+    _need_cuda(*g.tensors(), u, src)
+    n_add = u.numel()
+    if n + n_add > g.n:
+        raise ValueError("gs_mcmc_grow: the parameter arrays hold %d rows, need %d" % (g.n, n + n_add))
+    ws_bytes = ctypes.c_size_t(0)
+    check(lib.gs_mcmc_workspace(n, ctypes.byref(ws_bytes)), "gs_mcmc_workspace")
+    ws = torch.empty(max(ws_bytes.value, 256), dtype=torch.uint8, device=g.mean.device)
+    check(lib.gs_mcmc_grow(n, n_add, g.sh_degree, _p(g.mean), _p(g.log_scale), _p(g.quat), _p(g.opacity_logit),
+                           _p(g.sh), _p(u), _p(src), _p(ws), ws.numel(), _stream(stream)), "gs_mcmc_grow")
+
+
+def gs_mcmc_reset_moments(n_rows: int, src: torch.Tensor, row0: int, moments, stream=None):
+    """Zero rows row0 + k and src[k] (src[k] >= 0) of every (m, v) pair in
+    `moments` (tensors with n_rows rows)."""
+    lib = _lib.load()
+    arr = (_lib.gs_adam_group * len(moments))()
+    for i, (m, v) in enumerate(moments):
+        _need_cuda(m, v)
+        arr[i] = _lib.gs_adam_group(0, 0, m.data_ptr(), v.data_ptr(), m.numel(), 0.0, 0)
+    check(lib.gs_mcmc_reset_moments(n_rows, _p(src), src.numel(), row0, arr, len(moments), _stream(stream)),
+          "gs_mcmc_reset_moments")
+
+
 def gs_mcmc_noise(g: Gaussians, eta: torch.Tensor, noise_lr: float, stream=None):
     """mean += noise_lr * sigmoid(-100 (o - 0.005)) * Sigma eta, in place."""
     lib = _lib.load()
@@ -406,11 +531,13 @@ def adam_c(lr, beta1, beta2, eps, step: torch.Tensor):
 
 
 def pose_se3_update(T0, xi, g_tangent, g_xi, m, v, hp, Rt_out, stream=None):
-    """hp: gs_adam struct or None (gradient map and recomposition only)."""
+    """hp: gs_adam struct or None (gradient map and recomposition only).
+    float64 T0, xi, ... run the FP64 instantiation."""
     lib = _lib.load()
     _need_cuda(T0, xi, g_tangent, g_xi, m, v, Rt_out)
-    check(lib.pose_se3_update(T0.shape[0], _p(T0), _p(xi), _p(g_tangent), _p(g_xi), _p(m), _p(v),
-                              None if hp is None else ctypes.byref(hp), _p(Rt_out), _stream(stream)),
+    f64 = T0.dtype == torch.float64
+    check(_fn(lib, "pose_se3_update", f64)(T0.shape[0], _p(T0), _p(xi), _p(g_tangent), _p(g_xi), _p(m), _p(v),
+                                           None if hp is None else ctypes.byref(hp), _p(Rt_out), _stream(stream)),
           "pose_se3_update")
 
 
@@ -432,9 +559,10 @@ def gs_adam_update_groups(groups, beta1, beta2, eps, step, stream=None):
     check(lib.gs_adam_update_groups(arr, len(groups), ctypes.byref(hp), _stream(stream)), "gs_adam_update_groups")
 
 
-def gs_set_tuning(render_fwd_batch: int = 128, render_bwd_batch: int = 64, sort_blocks_per_sm: int = 1):
+def gs_set_tuning(render_fwd_batch: int = 128, render_bwd_batch: int = 64, sort_blocks_per_sm: int = 1,
+                  sort_spin_limit: int = 0):
     lib = _lib.load()
-    t = _lib.gs_tuning(int(render_fwd_batch), int(render_bwd_batch), int(sort_blocks_per_sm))
+    t = _lib.gs_tuning(int(render_fwd_batch), int(render_bwd_batch), int(sort_blocks_per_sm), int(sort_spin_limit))
     check(lib.gs_set_tuning(ctypes.byref(t)), "gs_set_tuning")
 
 
@@ -443,7 +571,7 @@ def gs_get_tuning():
     t = _lib.gs_tuning()
     check(lib.gs_get_tuning(ctypes.byref(t)), "gs_get_tuning")
     return dict(render_fwd_batch=t.render_fwd_batch, render_bwd_batch=t.render_bwd_batch,
-                sort_blocks_per_sm=t.sort_blocks_per_sm)
+                sort_blocks_per_sm=t.sort_blocks_per_sm, sort_spin_limit=t.sort_spin_limit)
 
 
 def gs_step_advance(step, stream=None):

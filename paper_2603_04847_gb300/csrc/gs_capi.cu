@@ -64,9 +64,39 @@ gs_status check_projected(const gs_projected* p) {
   return GS_OK;
 }
 
+gs_status check_gaussians(const gs_gaussians_f64* g) {
+  if (!g) return fail(GS_ERR_ARG, "gaussians: null");
+  if (g->n < 0) return fail(GS_ERR_ARG, "gaussians: n < 0");
+  if (g->sh_degree < 0 || g->sh_degree > 3) return fail(GS_ERR_ARG, "gaussians: sh_degree must be 0..3");
+  if (g->n > 0 && (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->sh))
+    return fail(GS_ERR_ARG, "gaussians: null array");
+  if (!aligned(g->quat, 16)) return fail(GS_ERR_ARG, "gaussians: quat must be 16-byte aligned");
+  return GS_OK;
+}
+
+gs_status check_cameras(const gs_cameras_f64* c) {
+  if (!c) return fail(GS_ERR_ARG, "cameras: null");
+  if (c->n_cams < 1) return fail(GS_ERR_ARG, "cameras: n_cams < 1");
+  if (!c->wh || !c->K || !c->Rt) return fail(GS_ERR_ARG, "cameras: null array");
+  if (!std::isfinite(c->near_plane) || !std::isfinite(c->far_plane))
+    return fail(GS_ERR_NONFINITE, "cameras: non-finite near/far");
+  if (!(c->near_plane > 0.0) || !(c->far_plane > c->near_plane))
+    return fail(GS_ERR_ARG, "cameras: need 0 < near < far");
+  return GS_OK;
+}
+
+gs_status check_projected(const gs_projected_f64* p) {
+  if (!p) return fail(GS_ERR_ARG, "projected: null");
+  if (!p->splat || !p->rect || !p->n_tiles || !p->depth_key) return fail(GS_ERR_ARG, "projected: null array");
+  if (!aligned(p->splat, 16) || !aligned(p->rect, 8) || !aligned(p->depth_key, 16))
+    return fail(GS_ERR_ARG, "projected: splat and depth_key must be 16-byte, rect 8-byte aligned");
+  return GS_OK;
+}
+
 inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t v2d_bytes(int N, const gs_batch& b) { return align_up((size_t)b.B * N * 12 * sizeof(float)); }
+size_t v2d_bytes_f64(int N, const gs_batch& b) { return align_up((size_t)b.B * N * 12 * sizeof(double)); }
 size_t pose_partial_bytes(int N, const gs_batch& b) {
   return align_up((size_t)project_bwd_blocks(N) * b.B * 6 * sizeof(double));
 }
@@ -74,7 +104,7 @@ size_t pose_partial_bytes(int N, const gs_batch& b) {
 }  // namespace
 
 namespace {
-gs_tuning g_tuning = {128, 64, 1};  // what the autotuner picks on the benchmark workloads
+gs_tuning g_tuning = {128, 64, 1, 0};  // what the autotuner picks on the benchmark workloads
 }
 
 const gs_tuning& tuning() { return g_tuning; }
@@ -111,6 +141,10 @@ size_t gs_struct_size(int which) {
     case 5: return sizeof(gs_adam);
     case 6: return sizeof(gs_tuning);
     case 7: return sizeof(gs_adam_group);
+    case 8: return sizeof(gs_gaussians_f64);
+    case 9: return sizeof(gs_gaussian_grads_f64);
+    case 10: return sizeof(gs_cameras_f64);
+    case 11: return sizeof(gs_projected_f64);
     default: return 0;
   }
 }
@@ -124,6 +158,8 @@ gs_status gs_set_tuning(const gs_tuning* t) {
       return fail(GS_ERR_ARG, "gs_set_tuning: render_fwd_batch and render_bwd_batch must be 64, 128 or 256");
   if (t->sort_blocks_per_sm < 1 || t->sort_blocks_per_sm > 8)
     return fail(GS_ERR_ARG, "gs_set_tuning: sort_blocks_per_sm must be 1..8");
+  if (t->sort_spin_limit < -(1 << 20) || t->sort_spin_limit > (1 << 24))
+    return fail(GS_ERR_ARG, "gs_set_tuning: sort_spin_limit must be in [-2^20, 2^24]");
   g_tuning = *t;
   return GS_OK;
 }
@@ -267,6 +303,141 @@ gs_status gs_render_bwd(const gs_gaussians* g, const gs_cameras* cams, const gs_
   return gs_project_bwd(g, cams, batch, proj, dg, g_pose_tangent, ws, ws_bytes, stream);
 }
 
+/* ---- FP64 instantiation of the projection and compositing -------------- */
+
+gs_status gs_project_f64(const gs_gaussians_f64* g, const gs_cameras_f64* cams, const gs_batch* batch,
+                         const gs_projected_f64* out, int32_t* status, gs_stream stream) {
+  gs_status s;
+  if ((s = check_gaussians(g)) || (s = check_cameras(cams)) || (s = check_batch(batch)) ||
+      (s = check_projected(out)))
+    return s;
+  if ((unsigned long long)batch->B * (unsigned long long)g->n >= 0xffffffffull)
+    return fail(GS_ERR_ARG, "gs_project_f64: B*N must be < 2^32");
+  cudaError_t e = launch_project_fwd_f64(*g, *cams, *batch, *out, status, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_project_f64");
+  return GS_OK;
+}
+
+gs_status gs_sort_tiles_f64(int32_t n_gaussians, const gs_cameras_f64* cams, const gs_batch* batch,
+                            const gs_projected_f64* proj, uint32_t* tiles, uint32_t* vals, size_t capacity,
+                            uint32_t* ranges, uint32_t* n_instances, void* ws, size_t ws_bytes, int32_t* status,
+                            gs_stream stream) {
+  gs_status s;
+  if ((s = check_cameras(cams)) || (s = check_projected(proj))) return s;
+  // the sort reads only the image sizes of the cameras and the rectangles,
+  // tile counts and depth keys of the records, which both paths share
+  gs_cameras c32{cams->n_cams, cams->wh, reinterpret_cast<const float*>(cams->K),
+                 reinterpret_cast<const float*>(cams->Rt), 0.01f, 1e10f};
+  gs_projected p32{reinterpret_cast<float*>(proj->splat), proj->rect, proj->n_tiles, proj->depth_key};
+  return gs_sort_tiles(n_gaussians, &c32, batch, &p32, tiles, vals, capacity, ranges, n_instances, ws, ws_bytes,
+                       status, stream);
+}
+
+gs_status gs_render_fwd_f64(const gs_batch* batch, const gs_cameras_f64* cams, const gs_projected_f64* proj,
+                            const uint32_t* vals, const uint32_t* ranges, const double* bg, double* image,
+                            double* T_final, uint32_t* n_contrib, uint32_t* n_added, gs_stream stream) {
+  gs_status s;
+  if ((s = check_batch(batch)) || (s = check_cameras(cams)) || (s = check_projected(proj))) return s;
+  if (!vals || !ranges || !bg || !image || !T_final || !n_contrib)
+    return fail(GS_ERR_ARG, "gs_render_fwd_f64: null argument");
+  cudaError_t e = launch_render_fwd_f64(*batch, *cams, *proj, vals, ranges, bg, image, T_final, n_contrib,
+                                        n_added, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_render_fwd_f64");
+  return GS_OK;
+}
+
+gs_status gs_render_bwd_workspace_f64(int32_t n_gaussians, const gs_batch* batch, size_t* ws_bytes) {
+  gs_status s;
+  if ((s = check_batch(batch))) return s;
+  if (!ws_bytes || n_gaussians < 0) return fail(GS_ERR_ARG, "gs_render_bwd_workspace_f64: bad argument");
+  *ws_bytes = v2d_bytes_f64(n_gaussians, *batch) + pose_partial_bytes(n_gaussians, *batch);
+  return GS_OK;
+}
+
+namespace {
+gs_status check_bwd_common_f64(const gs_gaussians_f64* g, const gs_cameras_f64* cams, const gs_batch* batch,
+                               const gs_projected_f64* proj, void* ws, size_t ws_bytes, const char* who) {
+  gs_status s;
+  if ((s = check_gaussians(g)) || (s = check_cameras(cams)) || (s = check_batch(batch)) ||
+      (s = check_projected(proj)))
+    return s;
+  if (!ws) return fail(GS_ERR_ARG, "%s: null workspace", who);
+  if (!aligned(ws, 256)) return fail(GS_ERR_ARG, "%s: ws must be 256-byte aligned", who);
+  const size_t need = v2d_bytes_f64(g->n, *batch) + pose_partial_bytes(g->n, *batch);
+  if (ws_bytes < need) return fail(GS_ERR_ARG, "%s: workspace %zu < %zu bytes", who, ws_bytes, need);
+  return GS_OK;
+}
+}  // namespace
+
+gs_status gs_raster_bwd_f64(const gs_gaussians_f64* g, const gs_cameras_f64* cams, const gs_batch* batch,
+                            const gs_projected_f64* proj, const uint32_t* vals, const uint32_t* ranges,
+                            const double* bg, const double* image, const double* T_final,
+                            const uint32_t* n_contrib, const double* v_image, const double* target,
+                            double l1_weight, double* loss, void* ws, size_t ws_bytes, gs_stream stream) {
+  gs_status s;
+  if ((s = check_bwd_common_f64(g, cams, batch, proj, ws, ws_bytes, "gs_raster_bwd_f64"))) return s;
+  if (!vals || !ranges || !bg || !T_final || !n_contrib)
+    return fail(GS_ERR_ARG, "gs_raster_bwd_f64: null argument");
+  if (!v_image && (!target || !image))
+    return fail(GS_ERR_ARG, "gs_raster_bwd_f64: need v_image, or image and target for the fused L1");
+  if (!v_image && !std::isfinite(l1_weight)) return fail(GS_ERR_NONFINITE, "gs_raster_bwd_f64: l1_weight");
+  cudaStream_t st = (cudaStream_t)stream;
+  double* v2d = reinterpret_cast<double*>(ws);
+  cudaError_t e = cudaMemsetAsync(v2d, 0, (size_t)batch->B * g->n * 12 * sizeof(double), st);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_raster_bwd_f64 memset");
+  e = launch_render_bwd_f64(*batch, *cams, *proj, vals, ranges, bg, image, T_final, n_contrib, v_image, target,
+                            l1_weight, loss, v2d, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_raster_bwd_f64");
+  return GS_OK;
+}
+
+gs_status gs_project_bwd_f64(const gs_gaussians_f64* g, const gs_cameras_f64* cams, const gs_batch* batch,
+                             const gs_projected_f64* proj, const gs_gaussian_grads_f64* dg, double* g_pose_tangent,
+                             void* ws, size_t ws_bytes, gs_stream stream) {
+  gs_status s;
+  if ((s = check_bwd_common_f64(g, cams, batch, proj, ws, ws_bytes, "gs_project_bwd_f64"))) return s;
+  if (!dg || !g_pose_tangent) return fail(GS_ERR_ARG, "gs_project_bwd_f64: null argument");
+  if (!dg->mean || !dg->log_scale || !dg->quat || !dg->opacity_logit || !dg->sh)
+    return fail(GS_ERR_ARG, "gs_project_bwd_f64: null gradient array");
+  if (!aligned(dg->quat, 16)) return fail(GS_ERR_ARG, "gs_project_bwd_f64: grad quat must be 16-byte aligned");
+  const size_t vb = v2d_bytes_f64(g->n, *batch);
+  double* v2d = reinterpret_cast<double*>(ws);
+  double* partial = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + vb);
+  cudaError_t e = launch_project_bwd_f64(*g, *cams, *batch, *proj, v2d, *dg, partial, g_pose_tangent,
+                                         (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_project_bwd_f64");
+  return GS_OK;
+}
+
+gs_status gs_render_bwd_f64(const gs_gaussians_f64* g, const gs_cameras_f64* cams, const gs_batch* batch,
+                            const gs_projected_f64* proj, const uint32_t* vals, const uint32_t* ranges,
+                            const double* bg, const double* image, const double* T_final,
+                            const uint32_t* n_contrib, const double* v_image, const double* target,
+                            double l1_weight, double* loss, const gs_gaussian_grads_f64* dg,
+                            double* g_pose_tangent, void* ws, size_t ws_bytes, gs_stream stream) {
+  if (!dg || !g_pose_tangent) return fail(GS_ERR_ARG, "gs_render_bwd_f64: null argument");
+  gs_status s = gs_raster_bwd_f64(g, cams, batch, proj, vals, ranges, bg, image, T_final, n_contrib, v_image,
+                                  target, l1_weight, loss, ws, ws_bytes, stream);
+  if (s != GS_OK) return s;
+  return gs_project_bwd_f64(g, cams, batch, proj, dg, g_pose_tangent, ws, ws_bytes, stream);
+}
+
+gs_status pose_se3_update_f64(int32_t n_cams, const double* T0, double* xi, const double* g_tangent,
+                              double* g_xi, double* m, double* v, const gs_adam* hp, double* Rt_out,
+                              gs_stream stream) {
+  if (n_cams < 0 || (n_cams > 0 && (!T0 || !xi || !g_tangent || !Rt_out)))
+    return fail(GS_ERR_ARG, "pose_se3_update_f64: null argument");
+  if (hp) {
+    if (!m || !v || !hp->step) return fail(GS_ERR_ARG, "pose_se3_update_f64: Adam needs m, v and step");
+    if (!std::isfinite(hp->lr) || !std::isfinite(hp->beta1) || !std::isfinite(hp->beta2) ||
+        !std::isfinite(hp->eps))
+      return fail(GS_ERR_NONFINITE, "pose_se3_update_f64: non-finite hyperparameter");
+  }
+  cudaError_t e = launch_pose_update_f64(n_cams, T0, xi, g_tangent, g_xi, m, v, hp, Rt_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pose_se3_update_f64");
+  return GS_OK;
+}
+
 gs_status track_reproj_workspace(const gs_batch* batch, size_t* ws_bytes) {
   gs_status s;
   if ((s = check_batch(batch))) return s;
@@ -347,6 +518,18 @@ gs_status gs_step_advance(int32_t* step, gs_stream stream) {
   if (!step) return fail(GS_ERR_ARG, "gs_step_advance: null");
   cudaError_t e = launch_step_advance(step, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "gs_step_advance");
+  return GS_OK;
+}
+
+gs_status gs_batch_layout(const gs_cameras* cams, const gs_batch* batch, int64_t* px_offset,
+                          int32_t* tile_offset, int32_t* status, gs_stream stream) {
+  gs_status s;
+  if ((s = check_cameras(cams)) || (s = check_batch(batch))) return s;
+  if (!px_offset || !tile_offset) return fail(GS_ERR_ARG, "gs_batch_layout: null offset array");
+  if (!aligned(px_offset, 8) || !aligned(tile_offset, 4))
+    return fail(GS_ERR_ARG, "gs_batch_layout: px_offset must be 8-byte, tile_offset 4-byte aligned");
+  cudaError_t e = launch_batch_layout(*cams, *batch, px_offset, tile_offset, status, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_batch_layout");
   return GS_OK;
 }
 
@@ -483,6 +666,38 @@ gs_status gs_mcmc_relocate(int32_t n, int32_t sh_degree, float* mean, float* log
   cudaError_t e = launch_mcmc_relocate(n, sh_degree, mean, log_scale, quat, opacity_logit, sh, u, n_u, src, n_dead,
                                        ws, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "gs_mcmc_relocate");
+  return GS_OK;
+}
+
+gs_status gs_mcmc_grow(int32_t n, int32_t n_add, int32_t sh_degree, float* mean, float* log_scale, float* quat,
+                       float* opacity_logit, float* sh, const double* u, int32_t* src, void* ws, size_t ws_bytes,
+                       gs_stream stream) {
+  if (n < 0 || n_add < 0 || sh_degree < 0 || sh_degree > 3) return fail(GS_ERR_ARG, "gs_mcmc_grow: bad sizes");
+  if ((long long)n + n_add > INT32_MAX) return fail(GS_ERR_ARG, "gs_mcmc_grow: n + n_add must be < 2^31");
+  if (n_add > 0 && (!mean || !log_scale || !quat || !opacity_logit || !sh || !u || !src))
+    return fail(GS_ERR_ARG, "gs_mcmc_grow: null argument");
+  if (n_add > 0 && (!ws || ws_bytes < mcmc_ws_bytes(n)))
+    return fail(GS_ERR_ARG, "gs_mcmc_grow: workspace needs %zu bytes", mcmc_ws_bytes(n));
+  if (!aligned(ws, 16)) return fail(GS_ERR_ARG, "gs_mcmc_grow: workspace must be 16-byte aligned");
+  cudaError_t e = launch_mcmc_grow(n, n_add, sh_degree, mean, log_scale, quat, opacity_logit, sh, u, src, ws,
+                                   (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_mcmc_grow");
+  return GS_OK;
+}
+
+gs_status gs_mcmc_reset_moments(int32_t n_rows, const int32_t* src, int32_t n_src, int32_t row0,
+                                const gs_adam_group* groups, int32_t n_groups, gs_stream stream) {
+  if (n_rows <= 0 || n_src < 0 || row0 < 0 || n_groups < 0 || n_groups > 8)
+    return fail(GS_ERR_ARG, "gs_mcmc_reset_moments: bad sizes (1..8 groups)");
+  if (n_src > 0 && (!src || (n_groups > 0 && !groups))) return fail(GS_ERR_ARG, "gs_mcmc_reset_moments: null argument");
+  if ((long long)row0 + n_src > n_rows) return fail(GS_ERR_ARG, "gs_mcmc_reset_moments: rows past n_rows");
+  for (int g = 0; g < n_groups; ++g) {
+    if (!groups[g].m || !groups[g].v) return fail(GS_ERR_ARG, "gs_mcmc_reset_moments: null moments");
+    if (groups[g].n <= 0 || groups[g].n % n_rows != 0)
+      return fail(GS_ERR_ARG, "gs_mcmc_reset_moments: group %d size is not a multiple of n_rows", g);
+  }
+  cudaError_t e = launch_mcmc_reset_moments(n_rows, src, n_src, row0, groups, n_groups, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_mcmc_reset_moments");
   return GS_OK;
 }
 

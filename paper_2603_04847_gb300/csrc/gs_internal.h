@@ -20,6 +20,11 @@ const gs_tuning& tuning();
 cudaError_t launch_project_fwd(const gs_gaussians& g, const gs_cameras& cams, const gs_batch& batch,
                                const gs_projected& out, int32_t* status, cudaStream_t st);
 int project_bwd_blocks(int n);
+cudaError_t launch_project_fwd_f64(const gs_gaussians_f64& g, const gs_cameras_f64& cams, const gs_batch& batch,
+                                   const gs_projected_f64& out, int32_t* status, cudaStream_t st);
+cudaError_t launch_project_bwd_f64(const gs_gaussians_f64& g, const gs_cameras_f64& cams, const gs_batch& batch,
+                                   const gs_projected_f64& proj, const double* v2d, const gs_gaussian_grads_f64& dg,
+                                   double* partial, double* g_pose_tangent, cudaStream_t st);
 cudaError_t launch_project_bwd(const gs_gaussians& g, const gs_cameras& cams, const gs_batch& batch,
                                const gs_projected& proj, const float* v2d, const gs_gaussian_grads& dg,
                                double* partial, double* g_pose_tangent, cudaStream_t st);
@@ -42,6 +47,15 @@ cudaError_t launch_render_bwd(const gs_batch& batch, const gs_cameras& cams, con
                               const float* v_image, const float* target, float l1_weight,
                               double* loss, float* v2d, cudaStream_t st);
 
+cudaError_t launch_render_fwd_f64(const gs_batch& batch, const gs_cameras_f64& cams, const gs_projected_f64& proj,
+                                  const uint32_t* vals, const uint32_t* ranges, const double* bg, double* image,
+                                  double* T_final, uint32_t* n_contrib, uint32_t* n_added, cudaStream_t st);
+cudaError_t launch_render_bwd_f64(const gs_batch& batch, const gs_cameras_f64& cams, const gs_projected_f64& proj,
+                                  const uint32_t* vals, const uint32_t* ranges, const double* bg,
+                                  const double* image, const double* T_final, const uint32_t* n_contrib,
+                                  const double* v_image, const double* target, double l1_weight, double* loss,
+                                  double* v2d, cudaStream_t st);
+
 int track_blocks();
 size_t track_workspace_bytes(const gs_batch& batch);
 cudaError_t launch_track(const float* X, int n_points, const int32_t* obs_point, const float* obs_xy,
@@ -53,10 +67,14 @@ cudaError_t launch_pose_partials_finalize(const double* partial, int n_blocks, c
                                           int n_cams, double* g_pose_tangent, cudaStream_t st);
 cudaError_t launch_pose_update(int V, const float* T0, float* xi, const double* g_tangent, float* g_xi,
                                float* m, float* v, const gs_adam* hp, float* Rt_out, cudaStream_t st);
+cudaError_t launch_pose_update_f64(int V, const double* T0, double* xi, const double* g_tangent, double* g_xi,
+                                   double* m, double* v, const gs_adam* hp, double* Rt_out, cudaStream_t st);
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, const gs_adam& hp,
                         cudaStream_t st);
 cudaError_t launch_adam_groups(const gs_adam_group* groups, int n_groups, const gs_adam& hp, cudaStream_t st);
 cudaError_t launch_step_advance(int32_t* step, cudaStream_t st);
+cudaError_t launch_batch_layout(const gs_cameras& cams, const gs_batch& batch, int64_t* px_offset,
+                                int32_t* tile_offset, int32_t* status, cudaStream_t st);
 cudaError_t launch_ba_assemble(const float* X, int n_points, const gs_cameras& cams, const int32_t* obs_point,
                                const int32_t* obs_cam, const float* obs_xy, int64_t n_obs, float delta, double* U,
                                double* Vp, double* gc, double* gp, double* Wo, double* objective,
@@ -76,6 +94,10 @@ size_t mcmc_ws_bytes(int n);
 cudaError_t launch_mcmc_relocate(int n, int sh_degree, float* mean, float* log_scale, float* quat, float* logit,
                                  float* sh, const double* u, int n_u, int32_t* src, uint32_t* n_dead, void* ws,
                                  cudaStream_t st);
+cudaError_t launch_mcmc_grow(int n, int n_add, int sh_degree, float* mean, float* log_scale, float* quat,
+                             float* logit, float* sh, const double* u, int32_t* src, void* ws, cudaStream_t st);
+cudaError_t launch_mcmc_reset_moments(int n_rows, const int32_t* src, int n_src, int row0,
+                                      const gs_adam_group* groups, int n_groups, cudaStream_t st);
 cudaError_t launch_mcmc_noise(int n, float* mean, const float* log_scale, const float* quat, const float* logit,
                               const float* eta, float lr, cudaStream_t st);
 size_t photo_loss_ws_bytes(int64_t n_pixels, int32_t n_tiles);

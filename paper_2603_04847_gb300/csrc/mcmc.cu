@@ -12,10 +12,18 @@
 //    to the same alpha integral along a line through it; D_N is the
 //    front-to-back double sum over copies and powers collapsed with the
 //    hockey-stick identity);
+//    the reset opacity is then bounded to [0.005, 1 - 2^-23] (a copy is never
+//    born dead and its logit stays finite);
+//  * growth: each new Gaussian (appended after the n existing ones) draws a
+//    live source like a relocation does, the drawn sources are reset by the
+//    same rule and the new ones copy them;
 //  * noise on the means: mu += lr sigmoid(-100 (o - 0.005)) Sigma eta.
 // Passes: a two-level scan gives the cumulative live opacity (FP64) and each
 // dead Gaussian's rank; draws are binary searches with atomic copy counts;
-// then the sources are reset and the dead ones copy them.
+// then the sources are reset and the dead (or new) ones copy them.  A draw
+// always lands on a live Gaussian: its target is below cdf[n-1] itself, and
+// a search that ends on a dead one (possible only where the two scan levels
+// round differently) moves on to the nearest live one.
 #include "gs_internal.h"
 
 namespace gs {
@@ -24,6 +32,7 @@ namespace {
 
 constexpr int kThr = 256;
 constexpr double kDead = 0.005;
+constexpr double kMaxOpacity = 1.0 - 1.1920928955078125e-07;  // 1 - 2^-23
 
 __device__ inline double opacity_of(float logit) { return 1.0 / (1.0 + exp(-(double)logit)); }
 
@@ -53,8 +62,11 @@ McmcWs mcmc_layout(void* base, int n, size_t* bytes) {
   return w;
 }
 
-// Block-wide inclusive scan of a double and exclusive scan of an int.
-__device__ inline void block_scan(double v, int c, double* incl, int* excl, double* s_d, int* s_i) {
+// Block-wide inclusive and exclusive scans of a double and exclusive scan of
+// an int.  The exclusive double prefix is the inclusive one of the thread
+// before (not inclusive - v, which rounds differently).
+__device__ inline void block_scan(double v, int c, double* incl, int* excl, double* s_d, int* s_i,
+                                  double* excl_d = nullptr) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double x = v;
   int y = c;
@@ -67,6 +79,7 @@ __device__ inline void block_scan(double v, int c, double* incl, int* excl, doub
       y += b;
     }
   }
+  const double xprev = __shfl_up_sync(0xffffffffu, x, 1);
   if (lane == 31) {
     s_d[warp] = x;
     s_i[warp] = y;
@@ -80,6 +93,7 @@ __device__ inline void block_scan(double v, int c, double* incl, int* excl, doub
   }
   *incl = dbase + x;
   *excl = ibase + y - c;
+  if (excl_d) *excl_d = lane > 0 ? dbase + xprev : dbase;
 }
 
 __global__ void __launch_bounds__(kThr) mcmc_reduce_kernel(int n, const float* __restrict__ logit,
@@ -119,13 +133,13 @@ __global__ void __launch_bounds__(kThr) mcmc_blocks_kernel(int nb, double* __res
     const int i = base + threadIdx.x;
     const double v = i < nb ? bsum[i] : 0.0;
     const int c = i < nb ? bcnt[i] : 0;
-    double incl;
+    double incl, excl_d;
     int excl;
-    block_scan(v, c, &incl, &excl, s_d, s_i);
+    block_scan(v, c, &incl, &excl, s_d, s_i, &excl_d);
     const double cd = carry_d;
     const int ci = carry_i;
     if (i < nb) {
-      bsum[i] = cd + incl - v;
+      bsum[i] = cd + excl_d;
       bcnt[i] = ci + excl;
     }
     __syncthreads();
@@ -165,28 +179,54 @@ __global__ void __launch_bounds__(kThr) mcmc_apply_kernel(int n, const float* __
   }
 }
 
+// The live Gaussian that uniform u draws: the first j with cdf[j] > u T,
+// T = cdf[n-1] (so some j qualifies for any u in [0, 1)); a dead one there
+// (only where the scan's two levels round apart) gives way to the next live
+// one, or the previous one at the end.  -1 when no Gaussian is live.
+__device__ inline int draw_live(int n, double u, const double* __restrict__ cdf, const int32_t* __restrict__ rank) {
+  const double T = cdf[n - 1];
+  if (!(T > 0.0)) return -1;
+  const double target = u * T;
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (cdf[mid] > target) hi = mid;
+    else lo = mid + 1;
+  }
+  int s = lo;
+  while (s < n && rank[s] >= 0) ++s;
+  if (s == n) {
+    s = lo;
+    while (s >= 0 && rank[s] >= 0) --s;
+  }
+  return s;
+}
+
 __global__ void __launch_bounds__(kThr) mcmc_draw_kernel(int n, const int32_t* __restrict__ rank,
-                                                         const double* __restrict__ cdf,
-                                                         const double* __restrict__ total, const double* __restrict__ u,
+                                                         const double* __restrict__ cdf, const double* __restrict__ u,
                                                          int n_u, int32_t* __restrict__ src,
                                                          int32_t* __restrict__ count) {
   const int i = blockIdx.x * kThr + threadIdx.x;
   if (i >= n) return;
   const int r = rank[i];
-  const double T = *total;
   int s = -1;
-  if (r >= 0 && r < n_u && T > 0.0) {
-    const double target = u[r] * T;
-    int lo = 0, hi = n - 1;  // first j with cdf[j] > target (cdf[n-1] = T > target)
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (cdf[mid] > target) hi = mid;
-      else lo = mid + 1;
-    }
-    s = lo;
-    atomicAdd(&count[s], 1);
+  if (r >= 0 && r < n_u) {
+    s = draw_live(n, u[r], cdf, rank);
+    if (s >= 0) atomicAdd(&count[s], 1);
   }
   src[i] = s;
+}
+
+// Growth: new Gaussian k (row n + k) draws its source with u[k].
+__global__ void __launch_bounds__(kThr) mcmc_grow_draw_kernel(int n, int n_add, const int32_t* __restrict__ rank,
+                                                              const double* __restrict__ cdf,
+                                                              const double* __restrict__ u, int32_t* __restrict__ src,
+                                                              int32_t* __restrict__ count) {
+  const int k = blockIdx.x * kThr + threadIdx.x;
+  if (k >= n_add) return;
+  const int s = draw_live(n, u[k], cdf, rank);
+  if (s >= 0) atomicAdd(&count[s], 1);
+  src[k] = s;
 }
 
 __global__ void __launch_bounds__(kThr) mcmc_reset_kernel(int n, float* __restrict__ logit,
@@ -203,7 +243,8 @@ __global__ void __launch_bounds__(kThr) mcmc_reset_kernel(int n, float* __restri
     p *= oN;
     den += ((m & 1) ? 1.0 : -1.0) * binom * p / sqrt((double)m);
   }
-  logit[j] = (float)log(oN / (1.0 - oN));
+  const double oB = fmin(fmax(oN, kDead), kMaxOpacity);   // the scale keeps the unbounded o_N
+  logit[j] = (float)log(oB / (1.0 - oB));
   const double ds = log(o / den);
   for (int a = 0; a < 3; ++a) log_scale[3 * (size_t)j + a] = (float)((double)log_scale[3 * (size_t)j + a] + ds);
 }
@@ -223,6 +264,49 @@ __global__ void __launch_bounds__(kThr) mcmc_copy_kernel(int n, int K3, const in
   for (int a = 0; a < 4; ++a) quat[4 * (size_t)i + a] = quat[4 * (size_t)s + a];
   logit[i] = logit[s];
   for (int a = 0; a < K3; ++a) sh[(size_t)K3 * i + a] = sh[(size_t)K3 * s + a];
+}
+
+// Growth: row n + k copies the (reset) parameters of its source src[k].
+__global__ void __launch_bounds__(kThr) mcmc_grow_copy_kernel(int n, int n_add, int K3, const int32_t* __restrict__ src,
+                                                              float* __restrict__ mean, float* __restrict__ log_scale,
+                                                              float* __restrict__ quat, float* __restrict__ logit,
+                                                              float* __restrict__ sh) {
+  const int k = blockIdx.x * kThr + threadIdx.x;
+  if (k >= n_add) return;
+  const int s = src[k];
+  if (s < 0) return;
+  const size_t i = (size_t)n + k;
+  for (int a = 0; a < 3; ++a) {
+    mean[3 * i + a] = mean[3 * (size_t)s + a];
+    log_scale[3 * i + a] = log_scale[3 * (size_t)s + a];
+  }
+  for (int a = 0; a < 4; ++a) quat[4 * i + a] = quat[4 * (size_t)s + a];
+  logit[i] = logit[s];
+  for (int a = 0; a < K3; ++a) sh[(size_t)K3 * i + a] = sh[(size_t)K3 * s + a];
+}
+
+// Zeroes the Adam moments of row row0 + k and of row src[k], for every k
+// with src[k] >= 0, in every group (row width = group n / n_rows).
+struct MomentGroups {
+  float* m[8];
+  float* v[8];
+  int width[8];
+  int n;
+};
+
+__global__ void __launch_bounds__(kThr) mcmc_reset_moments_kernel(int n_src, const int32_t* __restrict__ src,
+                                                                  int row0, MomentGroups G) {
+  const int k = blockIdx.x * kThr + threadIdx.x;
+  if (k >= n_src) return;
+  const int s = src[k];
+  if (s < 0) return;
+  const size_t rows[2] = {(size_t)row0 + k, (size_t)s};
+  for (int g = 0; g < G.n; ++g)
+    for (int r = 0; r < 2; ++r)
+      for (int a = 0; a < G.width[g]; ++a) {
+        G.m[g][rows[r] * G.width[g] + a] = 0.f;
+        G.v[g][rows[r] * G.width[g] + a] = 0.f;
+      }
 }
 
 __global__ void __launch_bounds__(kThr) mcmc_noise_kernel(int n, float* __restrict__ mean,
@@ -276,9 +360,39 @@ cudaError_t launch_mcmc_relocate(int n, int sh_degree, float* mean, float* log_s
   mcmc_reduce_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt);
   mcmc_blocks_kernel<<<1, kThr, 0, st>>>(nb, w.bsum, w.bcnt, w.total, n_dead);
   mcmc_apply_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt, w.cdf, w.rank, w.count);
-  mcmc_draw_kernel<<<nb, kThr, 0, st>>>(n, w.rank, w.cdf, w.total, u, n_u, src, w.count);
+  mcmc_draw_kernel<<<nb, kThr, 0, st>>>(n, w.rank, w.cdf, u, n_u, src, w.count);
   mcmc_reset_kernel<<<nb, kThr, 0, st>>>(n, logit, log_scale, w.count);
   mcmc_copy_kernel<<<nb, kThr, 0, st>>>(n, K3, src, mean, log_scale, quat, logit, sh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mcmc_grow(int n, int n_add, int sh_degree, float* mean, float* log_scale, float* quat,
+                             float* logit, float* sh, const double* u, int32_t* src, void* ws, cudaStream_t st) {
+  if (n == 0 || n_add == 0) return cudaSuccess;
+  McmcWs w = mcmc_layout(ws, n, nullptr);
+  const int nb = (n + kThr - 1) / kThr;
+  const int nba = (n_add + kThr - 1) / kThr;
+  const int K3 = 3 * (sh_degree + 1) * (sh_degree + 1);
+  mcmc_reduce_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt);
+  mcmc_blocks_kernel<<<1, kThr, 0, st>>>(nb, w.bsum, w.bcnt, w.total, nullptr);
+  mcmc_apply_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt, w.cdf, w.rank, w.count);
+  mcmc_grow_draw_kernel<<<nba, kThr, 0, st>>>(n, n_add, w.rank, w.cdf, u, src, w.count);
+  mcmc_reset_kernel<<<nb, kThr, 0, st>>>(n, logit, log_scale, w.count);
+  mcmc_grow_copy_kernel<<<nba, kThr, 0, st>>>(n, n_add, K3, src, mean, log_scale, quat, logit, sh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mcmc_reset_moments(int n_rows, const int32_t* src, int n_src, int row0,
+                                      const gs_adam_group* groups, int n_groups, cudaStream_t st) {
+  if (n_src == 0 || n_groups == 0) return cudaSuccess;
+  MomentGroups G;
+  G.n = n_groups;
+  for (int g = 0; g < n_groups; ++g) {
+    G.m[g] = groups[g].m;
+    G.v[g] = groups[g].v;
+    G.width[g] = (int)(groups[g].n / n_rows);
+  }
+  mcmc_reset_moments_kernel<<<(n_src + kThr - 1) / kThr, kThr, 0, st>>>(n_src, src, row0, G);
   return cudaGetLastError();
 }
 

@@ -79,7 +79,7 @@ __device__ inline void find_pixel_block(const gs_batch& batch, const gs_cameras&
   const int tiles_x = (b.W + T - 1) / T;
   const int l = gt - batch.tile_offset[lo];
   const int tx = l % tiles_x, ty = l / tiles_x;
-  b.valid = (T == kBE) || ((tx % 2) == 0 && (ty % 2) == 0);
+  b.valid = ((T == kBE) || ((tx % 2) == 0 && (ty % 2) == 0)) && slot_consistent(batch, lo, b.W, b.H);
   b.u0 = tx * T;
   b.v0 = ty * T;
   b.px = batch.px_offset[lo];
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(256) photo_blocks_kernel(gs_batch batch, gs_ca
                                                            uint32_t* list) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   bool valid = false;
-  if (gt < batch.n_tiles) {
+  if (gt < batch.n_tiles && gt < batch.tile_offset[batch.B]) {
     PixBlock b;
     find_pixel_block(batch, cams, gt, &b);
     valid = b.valid;

@@ -3,7 +3,8 @@
 //    adjustment"), the SE(3) gradient map g_xi = Jl(xi)^T g_tangent with the
 //    closed-form left Jacobian of SE(3) (Barfoot, State Estimation for
 //    Robotics), and an Adam step on xi (Sec. 3.3: Adam, lr 1e-5).  One
-//    thread per camera; FP32 except for the series coefficients.
+//    thread per camera; FP32 except for the series coefficients (a
+//    double instantiation serves the FP64 path).
 //  - Adam on parameter arrays (Algorithm 1, "Update Gaussians" / "Update
 //    track points"), elementwise and HBM-bound.
 //  - the fixed-order sum of per-block pose partials used by the projection
@@ -14,13 +15,15 @@ namespace gs {
 
 namespace {
 
-__device__ inline void skew(const float* w, float* S) {
-  S[0] = 0.f;   S[1] = -w[2]; S[2] = w[1];
-  S[3] = w[2];  S[4] = 0.f;   S[5] = -w[0];
-  S[6] = -w[1]; S[7] = w[0];  S[8] = 0.f;
+template <typename T>
+__device__ inline void skew(const T* w, T* S) {
+  S[0] = T(0);  S[1] = -w[2]; S[2] = w[1];
+  S[3] = w[2];  S[4] = T(0);  S[5] = -w[0];
+  S[6] = -w[1]; S[7] = w[0];  S[8] = T(0);
 }
 
-__device__ inline void mm3(const float* A, const float* B, float* C) {
+template <typename T>
+__device__ inline void mm3(const T* A, const T* B, T* C) {
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -34,53 +37,61 @@ __device__ inline void mm3(const float* A, const float* B, float* C) {
 // c3 = (2 th - 3 sin th + th cos th) / (2 th^5) (c1 = C).  They cancel badly
 // in single precision, so they alone are formed in double (one sincos);
 // Taylor series near 0.
+template <typename T>
 struct Se3Coef {
-  float A, B, C, c2, c3;
+  T A, B, C, c2, c3;
 };
 
-__device__ inline Se3Coef se3_coef(double th) {
-  Se3Coef k;
+template <typename T>
+__device__ inline Se3Coef<T> se3_coef(double th) {
+  Se3Coef<T> k;
   const double t2 = th * th;
   if (th < 1e-3) {
-    k.A = (float)(1.0 - t2 / 6.0 + t2 * t2 / 120.0);
-    k.B = (float)(0.5 - t2 / 24.0 + t2 * t2 / 720.0);
-    k.C = (float)(1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0);
-    k.c2 = (float)(1.0 / 24.0 - t2 / 720.0 + t2 * t2 / 40320.0);
-    k.c3 = (float)(1.0 / 120.0 - t2 / 2520.0);
+    k.A = (T)(1.0 - t2 / 6.0 + t2 * t2 / 120.0);
+    k.B = (T)(0.5 - t2 / 24.0 + t2 * t2 / 720.0);
+    k.C = (T)(1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0);
+    k.c2 = (T)(1.0 / 24.0 - t2 / 720.0 + t2 * t2 / 40320.0);
+    k.c3 = (T)(1.0 / 120.0 - t2 / 2520.0);
   } else {
     double s, c;
     sincos(th, &s, &c);
-    k.A = (float)(s / th);
-    k.B = (float)((1.0 - c) / t2);
-    k.C = (float)((th - s) / (t2 * th));
-    k.c2 = (float)((t2 + 2.0 * c - 2.0) / (2.0 * t2 * t2));
-    k.c3 = (float)((2.0 * th - 3.0 * s + th * c) / (2.0 * t2 * t2 * th));
+    k.A = (T)(s / th);
+    k.B = (T)((1.0 - c) / t2);
+    k.C = (T)((th - s) / (t2 * th));
+    k.c2 = (T)((t2 + 2.0 * c - 2.0) / (2.0 * t2 * t2));
+    k.c3 = (T)((2.0 * th - 3.0 * s + th * c) / (2.0 * t2 * t2 * th));
   }
   return k;
 }
 
-__global__ void pose_update_kernel(int V, const float* __restrict__ T0, float* __restrict__ xi,
-                                   const double* __restrict__ g_tangent, float* __restrict__ g_xi,
-                                   float* __restrict__ m, float* __restrict__ v, int use_adam,
-                                   float lr, float beta1, float beta2, float eps,
-                                   const int32_t* __restrict__ step, float* __restrict__ Rt_out) {
+__device__ inline float gexp2(float x) { return exp2f(x); }
+__device__ inline double gexp2(double x) { return exp2(x); }
+__device__ inline float glog2(float x) { return log2f(x); }
+__device__ inline double glog2(double x) { return log2(x); }
+
+template <typename T>
+__global__ void pose_update_kernel(int V, const T* __restrict__ T0, T* __restrict__ xi,
+                                   const double* __restrict__ g_tangent, T* __restrict__ g_xi,
+                                   T* __restrict__ m, T* __restrict__ v, int use_adam,
+                                   T lr, T beta1, T beta2, T eps,
+                                   const int32_t* __restrict__ step, T* __restrict__ Rt_out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V) return;
-  float x[6];
+  T x[6];
 #pragma unroll
   for (int c = 0; c < 6; ++c) x[c] = xi[6 * i + c];
-  const float* rho = x;
-  const float* phi = x + 3;
+  const T* rho = x;
+  const T* phi = x + 3;
   const double th = sqrt((double)phi[0] * phi[0] + (double)phi[1] * phi[1] + (double)phi[2] * phi[2]);
-  Se3Coef k = se3_coef(th);
-  float P[9], Rh[9], P2[9];
+  Se3Coef<T> k = se3_coef<T>(th);
+  T P[9], Rh[9], P2[9];
   skew(phi, P);
   skew(rho, Rh);
   mm3(P, P, P2);
-  float Jl[9];
+  T Jl[9];
 #pragma unroll
-  for (int e = 0; e < 9; ++e) Jl[e] = ((e % 4) == 0 ? 1.f : 0.f) + k.B * P[e] + k.C * P2[e];
-  float PR[9], RP[9], PRP[9], PPR[9], RPP[9], PRPP[9], PPRP[9], Q[9];
+  for (int e = 0; e < 9; ++e) Jl[e] = ((e % 4) == 0 ? T(1) : T(0)) + k.B * P[e] + k.C * P2[e];
+  T PR[9], RP[9], PRP[9], PPR[9], RPP[9], PRPP[9], PPRP[9], Q[9];
   mm3(P, Rh, PR);
   mm3(Rh, P, RP);
   mm3(PR, P, PRP);
@@ -90,14 +101,14 @@ __global__ void pose_update_kernel(int V, const float* __restrict__ T0, float* _
   mm3(P, PRP, PPRP);
 #pragma unroll
   for (int e = 0; e < 9; ++e)
-    Q[e] = 0.5f * Rh[e] + k.C * (PR[e] + RP[e] + PRP[e]) + k.c2 * (PPR[e] + RPP[e] - 3.f * PRP[e]) +
+    Q[e] = T(0.5) * Rh[e] + k.C * (PR[e] + RP[e] + PRP[e]) + k.c2 * (PPR[e] + RPP[e] - T(3) * PRP[e]) +
            k.c3 * (PRPP[e] + PPRP[e]);
   // g_xi = Jl^T g with Jl = [[Jl, Q], [0, Jl]]
   const double* gd = g_tangent + 6 * i;
-  float g[6];
+  T g[6];
 #pragma unroll
-  for (int c = 0; c < 6; ++c) g[c] = (float)gd[c];
-  float gx[6];
+  for (int c = 0; c < 6; ++c) g[c] = (T)gd[c];
+  T gx[6];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     gx[c] = Jl[c] * g[0] + Jl[3 + c] * g[1] + Jl[6 + c] * g[2];
@@ -108,43 +119,43 @@ __global__ void pose_update_kernel(int V, const float* __restrict__ T0, float* _
 #pragma unroll
     for (int c = 0; c < 6; ++c) g_xi[6 * i + c] = gx[c];
   if (use_adam) {
-    const float t = (float)*step;
-    const float bc1 = 1.f - exp2f(t * log2f(beta1));
-    const float bc2 = 1.f - exp2f(t * log2f(beta2));
+    const T t = (T)*step;
+    const T bc1 = T(1) - gexp2(t * glog2(beta1));
+    const T bc2 = T(1) - gexp2(t * glog2(beta2));
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      const float mm = beta1 * m[6 * i + c] + (1.f - beta1) * gx[c];
-      const float vv = beta2 * v[6 * i + c] + (1.f - beta2) * gx[c] * gx[c];
+      const T mm = beta1 * m[6 * i + c] + (T(1) - beta1) * gx[c];
+      const T vv = beta2 * v[6 * i + c] + (T(1) - beta2) * gx[c] * gx[c];
       m[6 * i + c] = mm;
       v[6 * i + c] = vv;
-      x[c] -= lr * (mm / bc1) / (sqrtf(vv / bc2) + eps);
+      x[c] -= lr * (mm / bc1) / (gsqrt(vv / bc2) + eps);
       xi[6 * i + c] = x[c];
     }
     const double th2 = sqrt((double)x[3] * x[3] + (double)x[4] * x[4] + (double)x[5] * x[5]);
-    k = se3_coef(th2);
+    k = se3_coef<T>(th2);
     skew(x + 3, P);
     mm3(P, P, P2);
   }
   // Rt_out = Exp(xi) T0
-  float ER[9], EV[9];
+  T ER[9], EV[9];
 #pragma unroll
   for (int e = 0; e < 9; ++e) {
-    const float I = (e % 4) == 0 ? 1.f : 0.f;
+    const T I = (e % 4) == 0 ? T(1) : T(0);
     ER[e] = I + k.A * P[e] + k.B * P2[e];
     EV[e] = I + k.B * P[e] + k.C * P2[e];
   }
-  float Et[3];
+  T Et[3];
 #pragma unroll
   for (int r = 0; r < 3; ++r) Et[r] = EV[3 * r] * x[0] + EV[3 * r + 1] * x[1] + EV[3 * r + 2] * x[2];
-  const float* T = T0 + 12 * i;
-  float R0[9], t0[3];
+  const T* Tp = T0 + 12 * i;
+  T R0[9], t0[3];
 #pragma unroll
-  for (int e = 0; e < 9; ++e) R0[e] = T[e];
+  for (int e = 0; e < 9; ++e) R0[e] = Tp[e];
 #pragma unroll
-  for (int e = 0; e < 3; ++e) t0[e] = T[9 + e];
-  float R[9];
+  for (int e = 0; e < 3; ++e) t0[e] = Tp[9 + e];
+  T R[9];
   mm3(ER, R0, R);
-  float* out = Rt_out + 12 * i;
+  T* out = Rt_out + 12 * i;
 #pragma unroll
   for (int e = 0; e < 9; ++e) out[e] = R[e];
 #pragma unroll
@@ -246,23 +257,59 @@ __global__ void __launch_bounds__(256) gather_view_pixels_kernel(const float* __
     d[i] = s[i];
 }
 
+// Per-slot pixel and tile offsets of a batch from its view ids and the
+// cameras' sizes (one thread: B <= GS_MAX_BATCH slots).  The batch's
+// n_pixels / n_tiles are the capacity of its buffers: the first slot that
+// would pass either, and every slot after it, gets no pixels and no tiles
+// (GS_FLAG_CAPACITY), so no kernel can index past the buffers.
+__global__ void batch_layout_kernel(gs_cameras cams, gs_batch batch, int64_t* __restrict__ px_offset,
+                                    int32_t* __restrict__ tile_offset, int32_t* status) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const long long T = batch.tile;
+  long long px = 0, tl = 0;
+  bool full = false;
+  px_offset[0] = 0;
+  tile_offset[0] = 0;
+  for (int b = 0; b < batch.B; ++b) {
+    const int v = slot_view(cams, batch, b);
+    const long long W = max(cams.wh[2 * v], 0), H = max(cams.wh[2 * v + 1], 0);
+    const long long np = W * H, nt = ((W + T - 1) / T) * ((H + T - 1) / T);
+    if (!full && px + np <= batch.n_pixels && tl + nt <= (long long)batch.n_tiles) {
+      px += np;
+      tl += nt;
+    } else if (!full) {
+      full = true;
+      set_flag(status, GS_FLAG_CAPACITY);
+    }
+    px_offset[b + 1] = px;
+    tile_offset[b + 1] = (int32_t)tl;
+  }
+}
+
+// g_pose_tangent[v] += the partials of every slot rendering camera v, in a
+// fixed order.  A camera may fill several slots of a batch: the block of its
+// first slot sums them all (slot order, then block order) and the blocks of
+// its other slots do nothing, so no two blocks write one camera's entries.
 __global__ void pose_partial_finalize_kernel(const double* __restrict__ partial, int n_blocks,
                                              gs_batch batch, int n_cams, double* g_pose_tangent) {
   const int b = blockIdx.x / 6, i = blockIdx.x % 6;
+  const int v = batch.views[b];
+  for (int b2 = 0; b2 < b; ++b2)
+    if (batch.views[b2] == v) return;  // block-uniform: an earlier slot owns camera v
   __shared__ double red[256];
   double s = 0.0;
-  for (int k = threadIdx.x; k < n_blocks; k += blockDim.x)
-    s += partial[(size_t)k * batch.B * 6 + 6 * b + i];
+  for (int b2 = b; b2 < batch.B; ++b2) {
+    if (batch.views[b2] != v) continue;
+    for (int k = threadIdx.x; k < n_blocks; k += blockDim.x)
+      s += partial[(size_t)k * batch.B * 6 + 6 * b2 + i];
+  }
   red[threadIdx.x] = s;
   __syncthreads();
   for (int off = blockDim.x / 2; off > 0; off >>= 1) {
     if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    const int v = batch.views[b];
-    if ((unsigned)v < (unsigned)n_cams) g_pose_tangent[6 * v + i] += red[0];
-  }
+  if (threadIdx.x == 0 && (unsigned)v < (unsigned)n_cams) g_pose_tangent[6 * v + i] += red[0];
 }
 
 }  // namespace
@@ -274,14 +321,27 @@ cudaError_t launch_pose_partials_finalize(const double* partial, int n_blocks, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_pose_update(int V, const float* T0, float* xi, const double* g_tangent, float* g_xi,
-                               float* m, float* v, const gs_adam* hp, float* Rt_out, cudaStream_t st) {
+namespace {
+template <typename T>
+cudaError_t pose_update_t(int V, const T* T0, T* xi, const double* g_tangent, T* g_xi, T* m, T* v,
+                          const gs_adam* hp, T* Rt_out, cudaStream_t st) {
   if (V == 0) return cudaSuccess;
   const int threads = 128;
-  pose_update_kernel<<<(V + threads - 1) / threads, threads, 0, st>>>(
-      V, T0, xi, g_tangent, g_xi, m, v, hp ? 1 : 0, hp ? hp->lr : 0.f, hp ? hp->beta1 : 0.f,
-      hp ? hp->beta2 : 0.f, hp ? hp->eps : 0.f, hp ? hp->step : nullptr, Rt_out);
+  pose_update_kernel<T><<<(V + threads - 1) / threads, threads, 0, st>>>(
+      V, T0, xi, g_tangent, g_xi, m, v, hp ? 1 : 0, hp ? (T)hp->lr : T(0), hp ? (T)hp->beta1 : T(0),
+      hp ? (T)hp->beta2 : T(0), hp ? (T)hp->eps : T(0), hp ? hp->step : nullptr, Rt_out);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_pose_update(int V, const float* T0, float* xi, const double* g_tangent, float* g_xi,
+                               float* m, float* v, const gs_adam* hp, float* Rt_out, cudaStream_t st) {
+  return pose_update_t<float>(V, T0, xi, g_tangent, g_xi, m, v, hp, Rt_out, st);
+}
+
+cudaError_t launch_pose_update_f64(int V, const double* T0, double* xi, const double* g_tangent, double* g_xi,
+                                   double* m, double* v, const gs_adam* hp, double* Rt_out, cudaStream_t st) {
+  return pose_update_t<double>(V, T0, xi, g_tangent, g_xi, m, v, hp, Rt_out, st);
 }
 
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, const gs_adam& hp,
@@ -315,6 +375,12 @@ cudaError_t launch_gather_view_pixels(const float* src, const int64_t* src_px_of
   if (batch.n_pixels == 0) return cudaSuccess;
   const int gx = std::max(1, std::min(4 * device_sm_count() / std::max(batch.B, 1) + 1, 1024));
   gather_view_pixels_kernel<<<dim3(gx, batch.B), 256, 0, st>>>(src, src_px_offset, cams, batch, channels, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_layout(const gs_cameras& cams, const gs_batch& batch, int64_t* px_offset,
+                                int32_t* tile_offset, int32_t* status, cudaStream_t st) {
+  batch_layout_kernel<<<1, 32, 0, st>>>(cams, batch, px_offset, tile_offset, status);
   return cudaGetLastError();
 }
 

@@ -32,6 +32,11 @@
 // (kBatch <= 128; with 256 the warps share one slot set through shared
 // atomics), summed over the warps per splat, and written with one vector
 // atomic per splat per tile.
+//
+// The kernels are templates on the scalar type: the FP32 instantiation is
+// the product path; the FP64 one (double records, exact exp2/log2 in place
+// of the approximate units, 64 splats staged per round) exists to check the
+// path against finite differences in double precision.
 #include "gs_internal.h"
 
 namespace gs {
@@ -47,19 +52,94 @@ struct Shape {
   static constexpr int kWarpsX = kTile / 8;
   static_assert(kWarps <= 32, "one mask bit per warp");
 };
-constexpr float kLn2 = 0.69314718055994531f;
-constexpr float kHalfLog2e = 0.72134752044448170f;  // 1 / (2 ln 2)
 
+template <typename T>
+struct RC;
+template <>
+struct RC<float> {
+  static constexpr float ln2 = 0.69314718055994531f;
+  static constexpr float half_log2e = 0.72134752044448170f;  // 1 / (2 ln 2)
+};
+template <>
+struct RC<double> {
+  static constexpr double ln2 = 0.69314718055994531;
+  static constexpr double half_log2e = 0.72134752044448170;
+};
+
+// Vector types of the staged records.
+template <typename T>
+struct V2;
+template <typename T>
+struct V4;
+template <>
+struct V2<float> {
+  using type = float2;
+};
+template <>
+struct V4<float> {
+  using type = float4;
+};
+struct alignas(16) dbl4 {
+  double x, y, z, w;
+};
+template <>
+struct V2<double> {
+  using type = double2;
+};
+template <>
+struct V4<double> {
+  using type = dbl4;
+};
+template <typename T>
+using v2_t = typename V2<T>::type;
+template <typename T>
+using v4_t = typename V4<T>::type;
+
+__device__ inline float2 mk2(float a, float b) { return make_float2(a, b); }
+__device__ inline double2 mk2(double a, double b) { return make_double2(a, b); }
+__device__ inline float4 mk4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+__device__ inline dbl4 mk4(double a, double b, double c, double d) { return dbl4{a, b, c, d}; }
+
+// The approximate FP32 units of the product path; exact in FP64.
+__device__ inline float ex2a(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ inline double ex2a(double x) { return exp2(x); }
+__device__ inline float lg2a(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ inline double lg2a(double x) { return log2(x); }
+__device__ inline float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ inline double rcp_rn(double x) { return 1.0 / x; }
+__device__ inline float recip_fast(float x) { return __fdividef(1.f, x); }
+__device__ inline double recip_fast(double x) { return 1.0 / x; }
+__device__ inline float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ inline double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ inline float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ inline double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename T>
 struct TileInfo {
   int slot;
+  int ok;          // the slot's offsets hold its view (else nothing to do)
   int W, H;
   int tx, ty;
   long long px_offset;
-  float inv_norm;  // 1 / (3 W H) for the per-view L1 mean
+  T inv_norm;      // 1 / (3 W H) for the per-view L1 mean
 };
 
-template <int kTile>
-__device__ inline void find_tile(const gs_batch& batch, const gs_cameras& cams, int gt, TileInfo* ti) {
+// The cameras' image sizes (all the compositing needs of them).
+struct Sizes {
+  int n_cams;
+  const int32_t* wh;
+};
+
+template <int kTile, typename T>
+__device__ inline void find_tile(const gs_batch& batch, const Sizes& cams, int gt, TileInfo<T>* ti) {
   if (threadIdx.x == 0) {
     int lo = 0, hi = batch.B - 1;
     while (lo < hi) {  // last slot with tile_offset[slot] <= gt
@@ -67,8 +147,8 @@ __device__ inline void find_tile(const gs_batch& batch, const gs_cameras& cams, 
       if (batch.tile_offset[mid] <= gt) lo = mid;
       else hi = mid - 1;
     }
-    const int v = slot_view(cams, batch, lo);
-    TileInfo t;
+    const int v = slot_view_n(cams.n_cams, batch, lo);
+    TileInfo<T> t;
     t.slot = lo;
     t.W = cams.wh[2 * v];
     t.H = cams.wh[2 * v + 1];
@@ -77,7 +157,8 @@ __device__ inline void find_tile(const gs_batch& batch, const gs_cameras& cams, 
     t.tx = l % tiles_x;
     t.ty = l / tiles_x;
     t.px_offset = batch.px_offset[lo];
-    t.inv_norm = 1.f / (3.f * (float)t.W * (float)t.H);
+    t.inv_norm = T(1) / (T(3) * (T)t.W * (T)t.H);
+    t.ok = slot_consistent(batch, lo, t.W, t.H);
     *ti = t;
   }
 }
@@ -106,68 +187,75 @@ __device__ inline void tile_pixels(int tid, int& lx, int& ly) {
 // the FP32 evaluation of alpha for strongly anisotropic conics carries
 // relative errors of that order, so no pixel whose alpha can pass the test
 // is ever skipped.
-template <int kTile>
-__device__ inline uint32_t warp_mask(const float4 xyo, const float4 con, float x0, float y0) {
+template <int kTile, typename T>
+__device__ inline uint32_t warp_mask(T mx, T my, T a, T b, T c, T qmax, T x0, T y0) {
   constexpr int kWX = Shape<kTile>::kWarpsX;
-  const float a = con.x, b = con.y, c = con.z;
-  const float det = a * c - b * b;
-  const float qc = (con.w + 1e-3f) * 1.02f + 0.01f;
-  const float ia = __frcp_rn(a), ic = __frcp_rn(c);
-  const float ba = b * ia, bc = b * ic, da = det * ia, dc = det * ic;
+  const T det = a * c - b * b;
+  const T qc = (qmax + T(1e-3f)) * T(1.02f) + T(0.01f);
+  const T ia = rcp_rn(a), ic = rcp_rn(c);
+  const T ba = b * ia, bc = b * ic, da = det * ia, dc = det * ic;
   uint32_t m = 0;
 #pragma unroll
   for (int w = 0; w < Shape<kTile>::kWarps; ++w) {
-    const float bx0 = x0 + (float)((w % kWX) * 8) + 0.49f, by0 = y0 + (float)((w / kWX) * 8) + 0.49f;
-    const float bx1 = bx0 + 7.02f, by1 = by0 + 7.02f;
+    const T bx0 = x0 + (T)((w % kWX) * 8) + T(0.49f), by0 = y0 + (T)((w / kWX) * 8) + T(0.49f);
+    const T bx1 = bx0 + T(7.02f), by1 = by0 + T(7.02f);
     // on the vertical line through the rectangle's x nearest the mean
-    const float dx = fminf(fmaxf(xyo.x, bx0), bx1) - xyo.x;
-    const float ev = fminf(fmaxf(xyo.y - bc * dx, by0), by1) - xyo.y + bc * dx;
-    const float qv = c * ev * ev + dc * dx * dx;
+    const T dx = gmin(gmax(mx, bx0), bx1) - mx;
+    const T ev = gmin(gmax(my - bc * dx, by0), by1) - my + bc * dx;
+    const T qv = c * ev * ev + dc * dx * dx;
     // on the horizontal line through the rectangle's y nearest the mean
-    const float dy = fminf(fmaxf(xyo.y, by0), by1) - xyo.y;
-    const float eh = fminf(fmaxf(xyo.x - ba * dy, bx0), bx1) - xyo.x + ba * dy;
-    const float qh = a * eh * eh + da * dy * dy;
-    m |= (fminf(qv, qh) <= qc) ? (1u << w) : 0u;
+    const T dy = gmin(gmax(my, by0), by1) - my;
+    const T eh = gmin(gmax(mx - ba * dy, bx0), bx1) - mx + ba * dy;
+    const T qh = a * eh * eh + da * dy * dy;
+    m |= (gmin(qv, qh) <= qc) ? (1u << w) : 0u;
   }
   return m;
 }
 
-__device__ inline float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
+// The 12 scalars of record r.
+__device__ inline void load_record(const float* splat, uint32_t r, float (&v)[12]) {
+  const float4* p = reinterpret_cast<const float4*>(splat) + 3 * (size_t)r;
+  const float4 a = p[0], b = p[1], c = p[2];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w;
 }
-
-__device__ inline float lg2_approx(float x) {
-  float y;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
+__device__ inline void load_record(const double* splat, uint32_t r, double (&v)[12]) {
+  const double2* p = reinterpret_cast<const double2*>(splat) + 6 * (size_t)r;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const double2 q = p[i];
+    v[2 * i] = q.x;
+    v[2 * i + 1] = q.y;
+  }
 }
 
 // Stages record r into slot `s` of the shared arrays.
-template <int kTile>
-__device__ inline void stage_splat(int s, uint32_t r, const float4* __restrict__ splat, float x0, float y0,
-                                   float2* s_m, float4* s_q, float4* s_c, uint32_t* s_mask) {
-  const float4 xyo = splat[3 * (size_t)r];
-  const float4 con = splat[3 * (size_t)r + 1];
-  const float4 col = splat[3 * (size_t)r + 2];
-  s_m[s] = make_float2(xyo.x, xyo.y);
-  s_q[s] = make_float4(-kHalfLog2e * con.x, -2.f * kHalfLog2e * con.y, -kHalfLog2e * con.z, lg2_approx(xyo.z));
-  s_c[s] = make_float4(col.x, col.y, col.z, 1.f / xyo.z);
-  s_mask[s] = warp_mask<kTile>(xyo, con, x0, y0);
+template <int kTile, typename T>
+__device__ inline void stage_splat(int s, uint32_t r, const T* __restrict__ splat, T x0, T y0, v2_t<T>* s_m,
+                                   v4_t<T>* s_q, v4_t<T>* s_c, uint32_t* s_mask) {
+  T v[12];
+  load_record(splat, r, v);
+  const T k = RC<T>::half_log2e;
+  s_m[s] = mk2(v[0], v[1]);
+  s_q[s] = mk4(-k * v[4], T(-2) * k * v[5], -k * v[6], lg2a(v[2]));
+  s_c[s] = mk4(v[8], v[9], v[10], T(1) / v[2]);
+  s_mask[s] = warp_mask<kTile>(v[0], v[1], v[4], v[5], v[6], v[7], x0, y0);
 }
 
 // Exponent e = A dx^2 + B dx dy + C dy^2 + log2 o of alpha_raw = 2^e at
 // offset (dx, dy), from the row terms Bdy = B dy and sy = C dy^2 + log2 o
 // (row_terms).  Written with explicit roundings so that every kernel
 // computes the same value from the same staged inputs.
-__device__ inline void row_terms(const float4 q, float dy, float& Bdy, float& sy) {
-  Bdy = __fmul_rn(q.y, dy);
-  sy = __fmaf_rn(__fmul_rn(q.z, dy), dy, q.w);
+template <typename Q, typename T>
+__device__ inline void row_terms(const Q q, T dy, T& Bdy, T& sy) {
+  Bdy = mul_rn(q.y, dy);
+  sy = fma_rn(mul_rn(q.z, dy), dy, q.w);
 }
 
-__device__ inline float splat_exponent(const float4 q, float dx, float Bdy, float sy) {
-  return __fmaf_rn(__fmaf_rn(q.x, dx, Bdy), dx, sy);
+template <typename Q, typename T>
+__device__ inline T splat_exponent(const Q q, T dx, T Bdy, T sy) {
+  return fma_rn(fma_rn(q.x, dx, Bdy), dx, sy);
 }
 
 // Positions s < min(cnt, limit) of the staged batch whose mask has this
@@ -189,40 +277,56 @@ __device__ inline int warp_list(const uint32_t* s_mask, uint32_t wbit, int cnt, 
   return n;
 }
 
-// 10 blocks of 16x16 per SM (48 registers, no spills) measured 3 % faster
-// than the 8 that 64 registers allow
-template <int kTile, int kBatch, bool kCountAdded>
-__global__ void __launch_bounds__(Shape<kTile>::kThreads, (kTile == 16 ? 10 : 2)) render_fwd_kernel(
-    gs_batch batch, gs_cameras cams, const float4* __restrict__ splat, const uint32_t* __restrict__ vals,
-    const uint32_t* __restrict__ ranges, const float* __restrict__ bg, float* __restrict__ image,
-    float* __restrict__ T_final, uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ n_added) {
+// Blocks per SM: 10 of 16x16 for the FP32 forward (48 registers, no
+// spills) measured 3 % faster than the 8 that 64 registers allow; 9 for the
+// FP32 backward (56 registers, ~2 % faster than 8).  The FP64 checking
+// path takes what it needs.
+template <typename T, int kTile>
+constexpr int fwd_min_blocks() {
+  return sizeof(T) == 4 ? (kTile == 16 ? 10 : 2) : 1;
+}
+template <typename T, int kTile>
+constexpr int bwd_min_blocks() {
+  return sizeof(T) == 4 ? (kTile == 16 ? 9 : 2) : 1;
+}
+
+template <typename T, int kTile, int kBatch, bool kCountAdded>
+__global__ void __launch_bounds__(Shape<kTile>::kThreads, (fwd_min_blocks<T, kTile>())) render_fwd_kernel(
+    gs_batch batch, Sizes cams, const T* __restrict__ splat, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ ranges, const T* __restrict__ bg, T* __restrict__ image,
+    T* __restrict__ T_final, uint32_t* __restrict__ n_contrib, uint32_t* __restrict__ n_added) {
   constexpr int kThreads = Shape<kTile>::kThreads;
-  __shared__ TileInfo ti;
-  __shared__ float2 s_m[kBatch];
-  __shared__ float4 s_q[kBatch];
-  __shared__ float4 s_c[kBatch];
+  __shared__ TileInfo<T> ti;
+  __shared__ v2_t<T> s_m[kBatch];
+  __shared__ v4_t<T> s_q[kBatch];
+  __shared__ v4_t<T> s_c[kBatch];
   __shared__ uint32_t s_mask[kBatch];
   __shared__ uint8_t s_list[kThreads / 32][kBatch];
   const int gt = blockIdx.x;
+  // the grid covers the batch's tile capacity; tiles past the views' own
+  // end (a batch laid out on the device) have nothing to do
+  if (gt >= batch.tile_offset[batch.B]) return;
   find_tile<kTile>(batch, cams, gt, &ti);
   __syncthreads();
+  if (!ti.ok) return;  // block-uniform
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int lx, ly;
   tile_pixels<kTile>(threadIdx.x, lx, ly);
   const uint32_t wbit = 1u << warp;
   const int u0 = ti.tx * kTile + lx, u1 = u0 + 4, v = ti.ty * kTile + ly;
   const bool in0 = u0 < ti.W && v < ti.H, in1 = u1 < ti.W && v < ti.H;
-  const float px0 = (float)u0 + 0.5f, px1 = (float)u1 + 0.5f, py = (float)v + 0.5f;
-  const float x0 = (float)(ti.tx * kTile), y0 = (float)(ti.ty * kTile);
+  const T px0 = (T)u0 + T(0.5), px1 = (T)u1 + T(0.5), py = (T)v + T(0.5);
+  const T x0 = (T)(ti.tx * kTile), y0 = (T)(ti.ty * kTile);
   const uint32_t start = ranges[2 * gt], end = ranges[2 * gt + 1];
-  float T0 = 1.f, T1 = 1.f;
-  float C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
+  const T amin = Consts<T>::alpha_min, amax = Consts<T>::alpha_max, tmin = Consts<T>::t_min;
+  T T0 = T(1), T1 = T(1);
+  T C00 = T(0), C01 = T(0), C02 = T(0), C10 = T(0), C11 = T(0), C12 = T(0);
   uint32_t last0 = 0, last1 = 0, add0 = 0, add1 = 0;
   bool done0 = !in0, done1 = !in1;
   // a finished pixel gets an unreachable threshold, so the per-splat test
   // is one compare (alpha = min(0.99, alpha_raw) >= 1/255 iff
   // alpha_raw >= 1/255)
-  float thr0 = done0 ? 2.f : kAlphaMin, thr1 = done1 ? 2.f : kAlphaMin;
+  T thr0 = done0 ? T(2) : amin, thr1 = done1 ? T(2) : amin;
   for (uint32_t base = start; base < end; base += kBatch) {
     if (__syncthreads_count(done0 && done1) == kThreads) break;
     for (int s = threadIdx.x; s < kBatch; s += kThreads) {
@@ -235,25 +339,25 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (kTile == 16 ? 10 : 2)
     if (done0 && done1) continue;
     for (int i = 0; i < n_mine; ++i) {
       const int k = s_list[warp][i];
-      const float2 m = s_m[k];
-      const float4 q = s_q[k];
-      float Bdy, sy;
+      const v2_t<T> m = s_m[k];
+      const v4_t<T> q = s_q[k];
+      T Bdy, sy;
       row_terms(q, py - m.y, Bdy, sy);
-      const float r0 = ex2_approx(splat_exponent(q, px0 - m.x, Bdy, sy));
-      const float r1 = ex2_approx(splat_exponent(q, px1 - m.x, Bdy, sy));
+      const T r0 = ex2a(splat_exponent(q, px0 - m.x, Bdy, sy));
+      const T r1 = ex2a(splat_exponent(q, px1 - m.x, Bdy, sy));
       const bool c0 = r0 >= thr0;
       const bool c1 = r1 >= thr1;
       if (!(c0 || c1)) continue;
-      const float4 c = s_c[k];
+      const v4_t<T> c = s_c[k];
       const uint32_t pos1 = base - start + (uint32_t)k + 1u;
       if (c0) {
-        const float a0 = fminf(kAlphaMax, r0);
-        const float Tn = T0 * (1.f - a0);
-        if (Tn < kTMin) {
+        const T a0 = gmin(amax, r0);
+        const T Tn = T0 * (T(1) - a0);
+        if (Tn < tmin) {
           done0 = true;
-          thr0 = 2.f;
+          thr0 = T(2);
         } else {
-          const float w = a0 * T0;
+          const T w = a0 * T0;
           C00 += c.x * w;
           C01 += c.y * w;
           C02 += c.z * w;
@@ -263,13 +367,13 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (kTile == 16 ? 10 : 2)
         }
       }
       if (c1) {
-        const float a1 = fminf(kAlphaMax, r1);
-        const float Tn = T1 * (1.f - a1);
-        if (Tn < kTMin) {
+        const T a1 = gmin(amax, r1);
+        const T Tn = T1 * (T(1) - a1);
+        if (Tn < tmin) {
           done1 = true;
-          thr1 = 2.f;
+          thr1 = T(2);
         } else {
-          const float w = a1 * T1;
+          const T w = a1 * T1;
           C10 += c.x * w;
           C11 += c.y * w;
           C12 += c.z * w;
@@ -303,23 +407,24 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (kTile == 16 ? 10 : 2)
 
 // Sum of v[0..7] over the warp, transposed: afterwards lane L holds the sum
 // of element ((L >> 2) & 7).  9 shuffles instead of 40.
-__device__ inline float warp_sum8_transposed(const float* v, int lane) {
+template <typename T>
+__device__ inline T warp_sum8_transposed(const T* v, int lane) {
   const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
-  float a[4];
+  T a[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const float send = h16 ? v[i] : v[i + 4];
-    const float keep = h16 ? v[i + 4] : v[i];
+    const T send = h16 ? v[i] : v[i + 4];
+    const T keep = h16 ? v[i + 4] : v[i];
     a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
   }
-  float b[2];
+  T b[2];
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    const float send = h8 ? a[i] : a[i + 2];
-    const float keep = h8 ? a[i + 2] : a[i];
+    const T send = h8 ? a[i] : a[i + 2];
+    const T keep = h8 ? a[i + 2] : a[i];
     b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
   }
-  float c = (h4 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, h4 ? b[0] : b[1], 4);
+  T c = (h4 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, h4 ? b[0] : b[1], 4);
   c += __shfl_xor_sync(0xffffffffu, c, 2);
   c += __shfl_xor_sync(0xffffffffu, c, 1);
   return c;
@@ -329,8 +434,9 @@ __device__ inline float warp_sum8_transposed(const float* v, int lane) {
 // The colour composited behind the current splat, S, enters the gradient
 // only through v . S (v = dL/dC is fixed per pixel), so that dot product is
 // carried instead of S.
+template <typename T>
 struct PixBwd {
-  float T, vS, v0, v1, v2;
+  T T_, vS, v0, v1, v2;
   uint32_t nc;
 };
 
@@ -343,21 +449,21 @@ struct PixBwd {
 // (pixels where alpha is clamped at 0.99 contribute none), which are
 // accumulated instead and mapped to gradients once per splat
 // (moments_to_grad); g6..8 are the colour gradients.
-__device__ inline void bwd_pixel(PixBwd& P, const float4 c, float dx, float dy, float araw, float alpha,
-                                 float* g) {
-  const float ra = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 0.01
-  const float Tk = P.T * ra;                      // transmittance before this splat
-  const float w = alpha * Tk;
+template <typename T, typename C4>
+__device__ inline void bwd_pixel(PixBwd<T>& P, const C4 c, T dx, T dy, T araw, T alpha, T* g) {
+  const T ra = recip_fast(T(1) - alpha);  // 1 - alpha >= 0.01
+  const T Tk = P.T_ * ra;                 // transmittance before this splat
+  const T w = alpha * Tk;
   g[6] += w * P.v0;
   g[7] += w * P.v1;
   g[8] += w * P.v2;
-  const float vc = P.v0 * c.x + P.v1 * c.y + P.v2 * c.z;
-  const float va = vc * Tk - P.vS * ra;  // dL/dalpha = v . (c T_k - S / (1 - alpha))
+  const T vc = P.v0 * c.x + P.v1 * c.y + P.v2 * c.z;
+  const T va = vc * Tk - P.vS * ra;  // dL/dalpha = v . (c T_k - S / (1 - alpha))
   P.vS += vc * w;
-  P.T = Tk;
-  if (araw < kAlphaMax) {
-    const float u = alpha * va;
-    const float udx = u * dx, udy = u * dy;
+  P.T_ = Tk;
+  if (araw < Consts<T>::alpha_max) {
+    const T u = alpha * va;
+    const T udx = u * dx, udy = u * dy;
     g[0] += udx;
     g[1] += udy;
     g[2] += udx * dx;
@@ -372,81 +478,104 @@ __device__ inline void bwd_pixel(PixBwd& P, const float4 c, float dx, float dy, 
 // -a/(2 ln 2), B = -b/ln 2, C = -c/(2 ln 2), and inv_o = 1/o:
 //   dL/dmean = -dL/dd = sum u (a dx + b dy, b dx + c dy)
 //            = -ln 2 (2A M0 + B M1, B M0 + 2C M1)
-//   dL/da = -M2/2, dL/db = -M3, dL/dc = -M4/2, dL/do = M5 / o.
-__device__ inline void moments_to_grad(const float* M, float4 q, float inv_o, float4& ga, float4& gb) {
-  ga = make_float4(-kLn2 * (2.f * q.x * M[0] + q.y * M[1]), -kLn2 * (q.y * M[0] + 2.f * q.z * M[1]), -0.5f * M[2],
-                   -M[3]);
-  gb = make_float4(-0.5f * M[4], M[5] * inv_o, M[6], M[7]);
+//   dL/da = -M2/2, dL/db = -M3, dL/dc = -M4/2, dL/do = M5 / o;
+// written into the record (mean2d x, y, conic a, b, c, opacity, colour).
+template <typename T, typename Q4>
+__device__ inline void moments_to_grad(const T* M, Q4 q, T inv_o, T* r) {
+  const T l2 = RC<T>::ln2;
+  r[0] = -l2 * (T(2) * q.x * M[0] + q.y * M[1]);
+  r[1] = -l2 * (q.y * M[0] + T(2) * q.z * M[1]);
+  r[2] = T(-0.5) * M[2];
+  r[3] = -M[3];
+  r[4] = T(-0.5) * M[4];
+  r[5] = M[5] * inv_o;
+  r[6] = M[6];
+  r[7] = M[7];
+  r[8] = M[8];
 }
 
-__device__ inline void load_pixel(PixBwd& P, bool inside, size_t p, const TileInfo& ti, const float* bg,
-                                  const float* __restrict__ image, const float* __restrict__ T_final,
-                                  const uint32_t* __restrict__ n_contrib, const float* __restrict__ v_image,
-                                  const float* __restrict__ target, float l1_weight, float& lsum) {
-  P.T = 1.f;
-  P.vS = 0.f;
-  P.v0 = P.v1 = P.v2 = 0.f;
+// record r of v2d += g[0..8] (one vector atomic per 4 floats in FP32).
+__device__ inline void add_record(float* v2d, uint32_t r, const float* g) {
+  float4* dst = reinterpret_cast<float4*>(v2d) + 3 * (size_t)r;
+  atomicAdd(dst, make_float4(g[0], g[1], g[2], g[3]));
+  atomicAdd(dst + 1, make_float4(g[4], g[5], g[6], g[7]));
+  atomicAdd(reinterpret_cast<float*>(dst + 2), g[8]);
+}
+__device__ inline void add_record(double* v2d, uint32_t r, const double* g) {
+  double* dst = v2d + 12 * (size_t)r;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) atomicAdd(dst + i, g[i]);
+}
+
+template <typename T>
+__device__ inline void load_pixel(PixBwd<T>& P, bool inside, size_t p, const TileInfo<T>& ti, const T* bg,
+                                  const T* __restrict__ image, const T* __restrict__ T_final,
+                                  const uint32_t* __restrict__ n_contrib, const T* __restrict__ v_image,
+                                  const T* __restrict__ target, T l1_weight, T& lsum) {
+  P.T_ = T(1);
+  P.vS = T(0);
+  P.v0 = P.v1 = P.v2 = T(0);
   P.nc = 0;
   if (!inside) return;
-  P.T = T_final[p];
+  P.T_ = T_final[p];
   P.nc = n_contrib[p];
   if (v_image) {
     P.v0 = v_image[3 * p];
     P.v1 = v_image[3 * p + 1];
     P.v2 = v_image[3 * p + 2];
   } else {
-    const float s = l1_weight * ti.inv_norm;
-    const float d0 = image[3 * p] - target[3 * p];
-    const float d1 = image[3 * p + 1] - target[3 * p + 1];
-    const float d2 = image[3 * p + 2] - target[3 * p + 2];
-    P.v0 = d0 > 0.f ? s : (d0 < 0.f ? -s : 0.f);
-    P.v1 = d1 > 0.f ? s : (d1 < 0.f ? -s : 0.f);
-    P.v2 = d2 > 0.f ? s : (d2 < 0.f ? -s : 0.f);
-    lsum += s * (fabsf(d0) + fabsf(d1) + fabsf(d2));
+    const T s = l1_weight * ti.inv_norm;
+    const T d0 = image[3 * p] - target[3 * p];
+    const T d1 = image[3 * p + 1] - target[3 * p + 1];
+    const T d2 = image[3 * p + 2] - target[3 * p + 2];
+    P.v0 = d0 > T(0) ? s : (d0 < T(0) ? -s : T(0));
+    P.v1 = d1 > T(0) ? s : (d1 < T(0) ? -s : T(0));
+    P.v2 = d2 > T(0) ? s : (d2 < T(0) ? -s : T(0));
+    lsum += s * (fabs(d0) + fabs(d1) + fabs(d2));
   }
-  P.vS = P.T * (P.v0 * bg[0] + P.v1 * bg[1] + P.v2 * bg[2]);
-  if (P.v0 == 0.f && P.v1 == 0.f && P.v2 == 0.f) P.nc = 0;
+  P.vS = P.T_ * (P.v0 * bg[0] + P.v1 * bg[1] + P.v2 * bg[2]);
+  if (P.v0 == T(0) && P.v1 == T(0) && P.v2 == T(0)) P.nc = 0;
 }
 
-// 9 blocks of 16x16 per SM (56 registers, no spills) measured ~2 % faster
-// than the 8 that 64 registers allow
-template <int kTile, int kBatch>
-__global__ void __launch_bounds__(Shape<kTile>::kThreads, (kTile == 16 ? 9 : 2)) render_bwd_kernel(
-    gs_batch batch, gs_cameras cams, const float4* __restrict__ splat, const uint32_t* __restrict__ vals,
-    const uint32_t* __restrict__ ranges, const float* __restrict__ bg, const float* __restrict__ image,
-    const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
-    const float* __restrict__ v_image, const float* __restrict__ target, float l1_weight, double* loss,
-    float* __restrict__ v2d) {
+template <typename T, int kTile, int kBatch>
+__global__ void __launch_bounds__(Shape<kTile>::kThreads, (bwd_min_blocks<T, kTile>())) render_bwd_kernel(
+    gs_batch batch, Sizes cams, const T* __restrict__ splat, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ ranges, const T* __restrict__ bg, const T* __restrict__ image,
+    const T* __restrict__ T_final, const uint32_t* __restrict__ n_contrib, const T* __restrict__ v_image,
+    const T* __restrict__ target, T l1_weight, double* loss, T* __restrict__ v2d) {
   constexpr int kThreads = Shape<kTile>::kThreads;
-  __shared__ TileInfo ti;
-  __shared__ float2 s_m[kBatch];
-  __shared__ float4 s_q[kBatch];
-  __shared__ float4 s_c[kBatch];
+  __shared__ TileInfo<T> ti;
+  __shared__ v2_t<T> s_m[kBatch];
+  __shared__ v4_t<T> s_q[kBatch];
+  __shared__ v4_t<T> s_c[kBatch];
   __shared__ uint32_t s_mask[kBatch];
   __shared__ uint8_t s_list[kThreads / 32][kBatch];
   __shared__ uint32_t s_rec[kBatch];
   // per-warp gradient slots where they fit in shared memory, else one set
   // shared by the warps through shared atomics
   constexpr int kW = Shape<kTile>::kWarps;
-  constexpr int kSlots = kBatch * (48 + 37 * kW) <= 45000 ? kW : 1;
-  __shared__ float s_g[kSlots][kBatch][9];
+  constexpr int kSlots =
+      kBatch * ((int)(10 * sizeof(T)) + 8 + kW + (int)(9 * sizeof(T)) * kW) <= 45000 ? kW : 1;
+  __shared__ T s_g[kSlots][kBatch][9];
   __shared__ uint32_t s_max;
-  __shared__ float s_loss[kThreads / 32];
+  __shared__ T s_loss[kThreads / 32];
   const int gt = blockIdx.x;
+  if (gt >= batch.tile_offset[batch.B]) return;  // past the views' tiles
   if (threadIdx.x == 0) s_max = 0;
   find_tile<kTile>(batch, cams, gt, &ti);
   __syncthreads();
+  if (!ti.ok) return;  // block-uniform
   const int lane = threadIdx.x & 31;
   int lx, ly;
   tile_pixels<kTile>(threadIdx.x, lx, ly);
   const uint32_t wbit = 1u << (threadIdx.x >> 5);
   const int u0 = ti.tx * kTile + lx, u1 = u0 + 4, v = ti.ty * kTile + ly;
   const bool in0 = u0 < ti.W && v < ti.H, in1 = u1 < ti.W && v < ti.H;
-  const float px0 = (float)u0 + 0.5f, px1 = (float)u1 + 0.5f, py = (float)v + 0.5f;
-  const float x0 = (float)(ti.tx * kTile), y0 = (float)(ti.ty * kTile);
+  const T px0 = (T)u0 + T(0.5), px1 = (T)u1 + T(0.5), py = (T)v + T(0.5);
+  const T x0 = (T)(ti.tx * kTile), y0 = (T)(ti.ty * kTile);
   const uint32_t start = ranges[2 * gt];
-  float lsum = 0.f;
-  PixBwd P0, P1;
+  T lsum = T(0);
+  PixBwd<T> P0, P1;
   load_pixel(P0, in0, (size_t)ti.px_offset + (size_t)v * ti.W + u0, ti, bg, image, T_final, n_contrib, v_image,
              target, l1_weight, lsum);
   load_pixel(P1, in1, (size_t)ti.px_offset + (size_t)v * ti.W + u1, ti, bg, image, T_final, n_contrib, v_image,
@@ -466,6 +595,7 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (kTile == 16 ? 9 : 2))
   }
   const uint32_t n_end = s_max;  // positions [0, n_end) of the tile list
   const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, nc_max);
+  const T amin = Consts<T>::alpha_min, amax = Consts<T>::alpha_max;
   for (int bend = (int)n_end; bend > 0; bend -= kBatch) {
     const int bstart = max(0, bend - kBatch);
     const int cnt = bend - bstart;
@@ -478,7 +608,7 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (kTile == 16 ? 9 : 2))
 #pragma unroll
       for (int w = 0; w < kSlots; ++w)
 #pragma unroll
-        for (int i = 0; i < 9; ++i) s_g[w][s][i] = 0.f;
+        for (int i = 0; i < 9; ++i) s_g[w][s][i] = T(0);
     }
     __syncthreads();
     // this warp's splats: before all its pixels' last contributor and able
@@ -488,40 +618,40 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (kTile == 16 ? 9 : 2))
     for (int i = n_mine - 1; i >= 0; --i) {
       const int k = s_list[threadIdx.x >> 5][i];
       const uint32_t pos = (uint32_t)(bstart + k);
-      const float2 m = s_m[k];
-      const float4 q = s_q[k];
-      const float dy = py - m.y;
-      float Bdy, sy;
+      const v2_t<T> m = s_m[k];
+      const v4_t<T> q = s_q[k];
+      const T dy = py - m.y;
+      T Bdy, sy;
       row_terms(q, dy, Bdy, sy);
-      float g[9];
+      T g[9];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) g[i] = 0.f;
+      for (int i = 0; i < 9; ++i) g[i] = T(0);
       bool contrib = false;
       if (pos < P0.nc) {
-        const float dx = px0 - m.x;
-        const float araw = ex2_approx(splat_exponent(q, dx, Bdy, sy));
-        const float alpha = fminf(kAlphaMax, araw);
-        if (alpha >= kAlphaMin) {
+        const T dx = px0 - m.x;
+        const T araw = ex2a(splat_exponent(q, dx, Bdy, sy));
+        const T alpha = gmin(amax, araw);
+        if (alpha >= amin) {
           contrib = true;
           bwd_pixel(P0, s_c[k], dx, dy, araw, alpha, g);
         }
       }
       if (pos < P1.nc) {
-        const float dx = px1 - m.x;
-        const float araw = ex2_approx(splat_exponent(q, dx, Bdy, sy));
-        const float alpha = fminf(kAlphaMax, araw);
-        if (alpha >= kAlphaMin) {
+        const T dx = px1 - m.x;
+        const T araw = ex2a(splat_exponent(q, dx, Bdy, sy));
+        const T alpha = gmin(amax, araw);
+        if (alpha >= amin) {
           contrib = true;
           bwd_pixel(P1, s_c[k], dx, dy, araw, alpha, g);
         }
       }
       if (__ballot_sync(0xffffffffu, contrib)) {
-        const float s8 = warp_sum8_transposed(g, lane);
-        float s9 = g[8];
+        const T s8 = warp_sum8_transposed(g, lane);
+        T s9 = g[8];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s9 += __shfl_xor_sync(0xffffffffu, s9, off);
         if constexpr (kSlots > 1) {
-          float* dst = s_g[threadIdx.x >> 5][k];
+          T* dst = s_g[threadIdx.x >> 5][k];
           if ((lane & 3) == 0) dst[(lane >> 2) & 7] = s8;
           if (lane == 1) dst[8] = s9;
         } else {
@@ -532,23 +662,20 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (kTile == 16 ? 9 : 2))
     }
     __syncthreads();
     for (int s = threadIdx.x; s < cnt; s += kThreads) {
-      float sg[9];
+      T sg[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
-        float acc = 0.f;
+        T acc = T(0);
 #pragma unroll
         for (int w = 0; w < kSlots; ++w) acc += s_g[w][s][i];
         sg[i] = acc;
       }
-      const bool nz = sg[0] != 0.f || sg[1] != 0.f || sg[2] != 0.f || sg[3] != 0.f || sg[4] != 0.f ||
-                      sg[5] != 0.f || sg[6] != 0.f || sg[7] != 0.f || sg[8] != 0.f;
+      const bool nz = sg[0] != T(0) || sg[1] != T(0) || sg[2] != T(0) || sg[3] != T(0) || sg[4] != T(0) ||
+                      sg[5] != T(0) || sg[6] != T(0) || sg[7] != T(0) || sg[8] != T(0);
       if (nz) {
-        float4 a, b;
-        moments_to_grad(sg, s_q[s], s_c[s].w, a, b);
-        float4* dst = reinterpret_cast<float4*>(v2d) + 3 * (size_t)s_rec[s];
-        atomicAdd(dst, a);
-        atomicAdd(dst + 1, b);
-        atomicAdd(reinterpret_cast<float*>(dst + 2), sg[8]);
+        T rec[9];
+        moments_to_grad(sg, s_q[s], s_c[s].w, rec);
+        add_record(v2d, s_rec[s], rec);
       }
     }
     __syncthreads();
@@ -559,55 +686,55 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (kTile == 16 ? 9 : 2))
 
 namespace {
 
-template <int kTile, int kBatch>
-void render_fwd_launch(const gs_batch& batch, const gs_cameras& cams, const float4* sp, const uint32_t* vals,
-                       const uint32_t* ranges, const float* bg, float* image, float* T_final,
-                       uint32_t* n_contrib, uint32_t* n_added, cudaStream_t st) {
+template <typename T, int kTile, int kBatch>
+void render_fwd_launch(const gs_batch& batch, const Sizes& cams, const T* sp, const uint32_t* vals,
+                       const uint32_t* ranges, const T* bg, T* image, T* T_final, uint32_t* n_contrib,
+                       uint32_t* n_added, cudaStream_t st) {
   // the per-pixel count of composited splats is a diagnostic: the kernel
   // without it saves two instructions per composited splat
   if (n_added)
-    render_fwd_kernel<kTile, kBatch, true><<<batch.n_tiles, Shape<kTile>::kThreads, 0, st>>>(
+    render_fwd_kernel<T, kTile, kBatch, true><<<batch.n_tiles, Shape<kTile>::kThreads, 0, st>>>(
         batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, n_added);
   else
-    render_fwd_kernel<kTile, kBatch, false><<<batch.n_tiles, Shape<kTile>::kThreads, 0, st>>>(
+    render_fwd_kernel<T, kTile, kBatch, false><<<batch.n_tiles, Shape<kTile>::kThreads, 0, st>>>(
         batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, n_added);
 }
 
 template <int kTile>
-void render_fwd_tile(int rb, const gs_batch& batch, const gs_cameras& cams, const float4* sp,
-                     const uint32_t* vals, const uint32_t* ranges, const float* bg, float* image, float* T_final,
-                     uint32_t* n_contrib, uint32_t* n_added, cudaStream_t st) {
+void render_fwd_tile(int rb, const gs_batch& batch, const Sizes& cams, const float* sp, const uint32_t* vals,
+                     const uint32_t* ranges, const float* bg, float* image, float* T_final, uint32_t* n_contrib,
+                     uint32_t* n_added, cudaStream_t st) {
   if (rb == 64)
-    render_fwd_launch<kTile, 64>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, n_added, st);
+    render_fwd_launch<float, kTile, 64>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, n_added, st);
   else if (rb == 128)
-    render_fwd_launch<kTile, 128>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, n_added, st);
+    render_fwd_launch<float, kTile, 128>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, n_added, st);
   else
-    render_fwd_launch<kTile, 256>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, n_added, st);
+    render_fwd_launch<float, kTile, 256>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, n_added, st);
 }
 
-template <int kTile, int kBatch>
-void render_bwd_launch(const gs_batch& batch, const gs_cameras& cams, const float4* sp, const uint32_t* vals,
-                       const uint32_t* ranges, const float* bg, const float* image, const float* T_final,
-                       const uint32_t* n_contrib, const float* v_image, const float* target, float l1_weight,
-                       double* loss, float* v2d, cudaStream_t st) {
-  render_bwd_kernel<kTile, kBatch><<<batch.n_tiles, Shape<kTile>::kThreads, 0, st>>>(
+template <typename T, int kTile, int kBatch>
+void render_bwd_launch(const gs_batch& batch, const Sizes& cams, const T* sp, const uint32_t* vals,
+                       const uint32_t* ranges, const T* bg, const T* image, const T* T_final,
+                       const uint32_t* n_contrib, const T* v_image, const T* target, T l1_weight, double* loss,
+                       T* v2d, cudaStream_t st) {
+  render_bwd_kernel<T, kTile, kBatch><<<batch.n_tiles, Shape<kTile>::kThreads, 0, st>>>(
       batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image, target, l1_weight, loss, v2d);
 }
 
 template <int kTile>
-void render_bwd_tile(int rb, const gs_batch& batch, const gs_cameras& cams, const float4* sp,
-                     const uint32_t* vals, const uint32_t* ranges, const float* bg, const float* image,
-                     const float* T_final, const uint32_t* n_contrib, const float* v_image, const float* target,
-                     float l1_weight, double* loss, float* v2d, cudaStream_t st) {
+void render_bwd_tile(int rb, const gs_batch& batch, const Sizes& cams, const float* sp, const uint32_t* vals,
+                     const uint32_t* ranges, const float* bg, const float* image, const float* T_final,
+                     const uint32_t* n_contrib, const float* v_image, const float* target, float l1_weight,
+                     double* loss, float* v2d, cudaStream_t st) {
   if (rb == 64)
-    render_bwd_launch<kTile, 64>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image, target,
-                                 l1_weight, loss, v2d, st);
+    render_bwd_launch<float, kTile, 64>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image,
+                                        target, l1_weight, loss, v2d, st);
   else if (rb == 128)
-    render_bwd_launch<kTile, 128>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image, target,
-                                  l1_weight, loss, v2d, st);
+    render_bwd_launch<float, kTile, 128>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image,
+                                         target, l1_weight, loss, v2d, st);
   else
-    render_bwd_launch<kTile, 256>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image, target,
-                                  l1_weight, loss, v2d, st);
+    render_bwd_launch<float, kTile, 256>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image,
+                                         target, l1_weight, loss, v2d, st);
 }
 
 }  // namespace
@@ -617,12 +744,12 @@ cudaError_t launch_render_fwd(const gs_batch& batch, const gs_cameras& cams, con
                               float* image, float* T_final, uint32_t* n_contrib, uint32_t* n_added,
                               cudaStream_t st) {
   if (batch.n_tiles == 0) return cudaSuccess;
-  const float4* sp = reinterpret_cast<const float4*>(proj.splat);
+  const Sizes sz{cams.n_cams, cams.wh};
   const int rb = tuning().render_fwd_batch;
   if (batch.tile == 32)
-    render_fwd_tile<32>(rb, batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, n_added, st);
+    render_fwd_tile<32>(rb, batch, sz, proj.splat, vals, ranges, bg, image, T_final, n_contrib, n_added, st);
   else
-    render_fwd_tile<16>(rb, batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, n_added, st);
+    render_fwd_tile<16>(rb, batch, sz, proj.splat, vals, ranges, bg, image, T_final, n_contrib, n_added, st);
   return cudaGetLastError();
 }
 
@@ -632,14 +759,44 @@ cudaError_t launch_render_bwd(const gs_batch& batch, const gs_cameras& cams, con
                               const float* v_image, const float* target, float l1_weight,
                               double* loss, float* v2d, cudaStream_t st) {
   if (batch.n_tiles == 0) return cudaSuccess;
-  const float4* sp = reinterpret_cast<const float4*>(proj.splat);
+  const Sizes sz{cams.n_cams, cams.wh};
   const int rb = tuning().render_bwd_batch;
   if (batch.tile == 32)
-    render_bwd_tile<32>(rb, batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image, target,
+    render_bwd_tile<32>(rb, batch, sz, proj.splat, vals, ranges, bg, image, T_final, n_contrib, v_image, target,
                         l1_weight, loss, v2d, st);
   else
-    render_bwd_tile<16>(rb, batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image, target,
+    render_bwd_tile<16>(rb, batch, sz, proj.splat, vals, ranges, bg, image, T_final, n_contrib, v_image, target,
                         l1_weight, loss, v2d, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render_fwd_f64(const gs_batch& batch, const gs_cameras_f64& cams, const gs_projected_f64& proj,
+                                  const uint32_t* vals, const uint32_t* ranges, const double* bg, double* image,
+                                  double* T_final, uint32_t* n_contrib, uint32_t* n_added, cudaStream_t st) {
+  if (batch.n_tiles == 0) return cudaSuccess;
+  const Sizes sz{cams.n_cams, cams.wh};
+  if (batch.tile == 32)
+    render_fwd_launch<double, 32, 64>(batch, sz, proj.splat, vals, ranges, bg, image, T_final, n_contrib, n_added,
+                                      st);
+  else
+    render_fwd_launch<double, 16, 64>(batch, sz, proj.splat, vals, ranges, bg, image, T_final, n_contrib, n_added,
+                                      st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render_bwd_f64(const gs_batch& batch, const gs_cameras_f64& cams, const gs_projected_f64& proj,
+                                  const uint32_t* vals, const uint32_t* ranges, const double* bg,
+                                  const double* image, const double* T_final, const uint32_t* n_contrib,
+                                  const double* v_image, const double* target, double l1_weight, double* loss,
+                                  double* v2d, cudaStream_t st) {
+  if (batch.n_tiles == 0) return cudaSuccess;
+  const Sizes sz{cams.n_cams, cams.wh};
+  if (batch.tile == 32)
+    render_bwd_launch<double, 32, 64>(batch, sz, proj.splat, vals, ranges, bg, image, T_final, n_contrib, v_image,
+                                      target, l1_weight, loss, v2d, st);
+  else
+    render_bwd_launch<double, 16, 64>(batch, sz, proj.splat, vals, ranges, bg, image, T_final, n_contrib, v_image,
+                                      target, l1_weight, loss, v2d, st);
   return cudaGetLastError();
 }
 

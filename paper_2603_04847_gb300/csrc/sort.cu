@@ -23,7 +23,12 @@
 // the counts its predecessor blocks publish.  Blocks take their 4096-item
 // tile from an atomic counter, so every block a tile waits on is already
 // running; each wait is bounded and raises GS_FLAG_SORT_STALL when the
-// bound runs out instead of hanging.
+// bound runs out instead of hanging.  A pass that gave up still writes only
+// inside its output (its offsets are partial sums of the true ones), and it
+// sets a stall word in the workspace: every later kernel of the stage reads
+// that word first and does nothing, so the instance count stays 0, the
+// ranges stay zeroed and the renders see empty tiles -- no kernel ever reads
+// the unsorted data.
 //
 // The instance count stays on the device: every kernel after the scan reads
 // it, and all grids are sized from host-known bounds (records, capacity, SM
@@ -50,7 +55,7 @@ constexpr int kMaxDigits = 4;                         // 32-bit keys, 8-bit digi
 constexpr unsigned long long kLbAggregate = 1ull << 62;  // this tile's own count
 constexpr unsigned long long kLbInclusive = 2ull << 62;  // count over tiles 0..t
 constexpr unsigned long long kLbCount = (1ull << 62) - 1;
-constexpr int kSpinLimit = 1 << 20;   // polls of one unpublished word
+constexpr int kSpinLimit = 1 << 20;   // polls of one unpublished word (default)
 constexpr int kLbWindow = 4;          // predecessors read per look-back step
 
 __device__ inline void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
@@ -101,6 +106,7 @@ struct SortZero {
   uint32_t* ranges;                // [2 * n_tiles]
   size_t ranges_words;
   uint32_t* n_instances;
+  uint32_t* stall;                 // [1] set by a pass whose wait ran out
 };
 
 __global__ void __launch_bounds__(256) sort_zero_kernel(SortZero z) {
@@ -109,7 +115,10 @@ __global__ void __launch_bounds__(256) sort_zero_kernel(SortZero z) {
   for (size_t i = i0; i < 2 * kMaxDigits; i += step) z.counters[i] = 0;
   for (size_t i = i0; i < z.lb_depth_words; i += step) z.lb_depth[i] = 0;
   for (size_t i = i0; i < z.ranges_words; i += step) z.ranges[i] = 0;
-  if (i0 == 0) *z.n_instances = 0;
+  if (i0 == 0) {
+    *z.n_instances = 0;
+    *z.stall = 0;
+  }
 }
 
 // Counts of each 8-bit digit of keys[0, n), for digits 0..n_digits-1:
@@ -168,7 +177,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* n_dev, uint32_t n_host, size_t capacity, int shift,
     const uint32_t* __restrict__ ghist, unsigned long long* lookback, uint32_t* tile_counter,
-    const uint2* __restrict__ gather_src, uint2* __restrict__ gather_dst, int32_t* status) {
+    const uint2* __restrict__ gather_src, uint2* __restrict__ gather_dst, uint32_t gather_n, int32_t* status,
+    uint32_t* stall, int spin_limit, int fake_stall) {
   __shared__ uint32_t s_base[256];    // output position of this tile's first item of each digit
   __shared__ uint32_t s_tot[256];     // items of each digit in this tile
   __shared__ uint32_t s_dstart[256];  // exclusive scan of s_tot
@@ -176,11 +186,17 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
   __shared__ uint32_t s_keys[kTileItems];
   __shared__ uint32_t s_vals[kTileItems];
   __shared__ uint32_t sm[32];
-  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_tile, s_stop;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+  if (tid == 0) {
+    // an earlier pass gave up: its output is not sorted, do nothing (read
+    // by one thread: another block of this pass may set it meanwhile)
+    s_stop = *(volatile uint32_t*)stall;
+    if (!s_stop) s_tile = atomicAdd(tile_counter, 1u);
+  }
   for (int d = lane; d < 256; d += 32) s_wrun[warp][d] = 0;
   __syncthreads();
+  if (s_stop) return;  // block-uniform
   const uint32_t t = s_tile;
   const uint32_t n = n_dev ? (uint32_t)min((size_t)*n_dev, capacity) : n_host;
   if ((size_t)t * kTileItems >= n) return;  // block-uniform
@@ -263,6 +279,10 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
 #pragma unroll
       for (int q = 0; q < kLbWindow; ++q)
         w[q] = j - q >= 0 ? ld_relaxed_u64(&lookback[(size_t)(j - q) * 256 + tid]) : kLbInclusive;
+      if (fake_stall) {  // test hook: the predecessors never publish
+#pragma unroll
+        for (int q = 0; q < kLbWindow; ++q) w[q] = 0;
+      }
       int adv = 0;
       bool found = false, blocked = false;
 #pragma unroll
@@ -281,8 +301,9 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
       if (found) break;
       j -= adv;
       if (adv == 0) {
-        if (++polls > kSpinLimit) {
+        if (++polls > spin_limit) {
           set_flag(status, GS_FLAG_SORT_STALL);
+          atomicExch(stall, 1u);
           break;
         }
         __nanosleep(128);
@@ -304,7 +325,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(
       const uint32_t val = s_vals[p];
       if (kout) kout[pos] = key;
       vout[pos] = val;
-      if (gather_src) gather_dst[pos] = gather_src[val];
+      if (gather_src && val < gather_n) gather_dst[pos] = gather_src[val];
     }
   }
 }
@@ -323,10 +344,12 @@ __device__ inline size_t visible_records(size_t M, const uint32_t* ghist_depth) 
 // Sum of tiles touched per scan block (64-bit to detect overflow).
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const ushort4* __restrict__ rectd, size_t M,
                                                                    const uint32_t* __restrict__ ghist_depth,
-                                                                   unsigned long long* block_sums) {
+                                                                   unsigned long long* block_sums,
+                                                                   const uint32_t* stall) {
   __shared__ unsigned long long red[kScanThreads / 32];
   const size_t base = (size_t)blockIdx.x * kScanTile;
-  const size_t n_vis = visible_records(M, ghist_depth);
+  // the depth order is not valid after a stalled pass: no instances
+  const size_t n_vis = *(volatile const uint32_t*)stall ? 0 : visible_records(M, ghist_depth);
   unsigned long long s = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
@@ -405,7 +428,7 @@ __global__ void __launch_bounds__(kScanThreads) expand_kernel(
     const unsigned long long* __restrict__ block_offs, gs_projected proj, int N, gs_cameras cams,
     gs_batch batch, uint32_t* __restrict__ tiles, uint32_t* __restrict__ vals, size_t capacity,
     const uint32_t* n_instances, int n_digits, uint32_t* __restrict__ ghist,
-    unsigned long long* __restrict__ lb_tile, size_t lb_tile_stride) {
+    unsigned long long* __restrict__ lb_tile, size_t lb_tile_stride, const uint32_t* stall) {
   __shared__ uint32_t s_t[kExpandStage];
   __shared__ uint32_t s_v[kExpandStage];
   __shared__ SlotTiles st[GS_MAX_BATCH];
@@ -429,7 +452,7 @@ __global__ void __launch_bounds__(kScanThreads) expand_kernel(
   }
 
   const size_t base = (size_t)blockIdx.x * kScanTile;
-  const size_t n_vis = visible_records(M, ghist_depth);
+  const size_t n_vis = *(volatile const uint32_t*)stall ? 0 : visible_records(M, ghist_depth);
   uint32_t c[kScanItems], rr[kScanItems];
   ushort4 rc[kScanItems];
   uint32_t s = 0;
@@ -500,7 +523,9 @@ __global__ void __launch_bounds__(kScanThreads) expand_kernel(
 // the sorted tiles[0, n); four items per thread (tiles 16-byte aligned).
 __global__ void __launch_bounds__(256) tile_ranges_kernel(const uint32_t* __restrict__ tiles,
                                                           const uint32_t* n_dev, size_t capacity,
-                                                          uint32_t* __restrict__ ranges) {
+                                                          uint32_t* __restrict__ ranges,
+                                                          const uint32_t* stall) {
+  if (*(volatile const uint32_t*)stall) return;  // the lists are not sorted: leave every tile empty
   const uint32_t n = (uint32_t)min((size_t)*n_dev, capacity);
   const uint32_t nq = (uint32_t)(((size_t)n + 3) / 4);
   for (uint32_t qi = blockIdx.x * blockDim.x + threadIdx.x; qi < nq; qi += gridDim.x * blockDim.x) {
@@ -546,6 +571,7 @@ struct SortWs {
   uint32_t* counters;   // [2][kMaxDigits] tile counters per pass
   unsigned long long* lb_depth;  // [kMaxDigits][depth tiles][256]
   unsigned long long* lb_tile;   // [tile passes][instance tiles][256]
+  uint32_t* stall;               // [1] a pass gave up waiting (zeroed per call)
   size_t bytes;
 };
 
@@ -568,6 +594,7 @@ SortWs sort_ws_layout(void* base, size_t M, size_t capacity, int tile_passes) {
   w.counters = (uint32_t*)take(2 * kMaxDigits * 4);
   w.lb_depth = (unsigned long long*)take(kMaxDigits * radix_tiles(M) * 256 * 8);
   w.lb_tile = (unsigned long long*)take((size_t)tile_passes * radix_tiles(capacity) * 256 * 8);
+  w.stall = (uint32_t*)take(4);
   w.bytes = o;
   return w;
 }
@@ -605,7 +632,12 @@ cudaError_t launch_sort_tiles(int N, const gs_cameras& cams, const gs_batch& bat
   uint32_t* ghist_tile = w.ghist + kMaxDigits * 256;
 
   SortZero z{w.ghist, w.counters, w.lb_depth, kMaxDigits * radix_tiles(M) * 256, ranges,
-             2 * (size_t)batch.n_tiles, n_instances};
+             2 * (size_t)batch.n_tiles, n_instances, w.stall};
+  // the wait bound of the look-back; a negative setting is the test hook in
+  // which predecessors never publish (every wait runs out after |value| polls)
+  const int spin_cfg = tuning().sort_spin_limit;
+  const int spin_limit = spin_cfg == 0 ? kSpinLimit : (spin_cfg > 0 ? spin_cfg : -spin_cfg);
+  const int fake_stall = spin_cfg < 0 ? 1 : 0;
   sort_zero_kernel<<<grid_stride_blocks(std::max(z.lb_depth_words, z.ranges_words), 256), 256, 0, st>>>(z);
   const int n_scan_blocks = (int)((M + kScanTile - 1) / kScanTile);
   if (n_scan_blocks == 0) return cudaGetLastError();
@@ -626,8 +658,7 @@ cudaError_t launch_sort_tiles(int N, const gs_cameras& cams, const gs_batch& bat
     onesweep_kernel<<<depth_grid, kSortThreads, 0, st>>>(
         kin, vin, ko, vo, nullptr, (uint32_t)M, M, 8 * pass, ghist_depth + 256 * pass,
         w.lb_depth + lbd_stride * pass, w.counters + pass, last ? reinterpret_cast<const uint2*>(proj.rect) : nullptr,
-        last ? reinterpret_cast<uint2*>(w.rectd) : nullptr,
-        status);
+        last ? reinterpret_cast<uint2*>(w.rectd) : nullptr, (uint32_t)M, status, w.stall, spin_limit, fake_stall);
     kin = ko;
     vin = vo;
   }
@@ -635,7 +666,7 @@ cudaError_t launch_sort_tiles(int N, const gs_cameras& cams, const gs_batch& bat
 
   // 2. instance offsets in depth order, 3. expand into whichever buffer
   //    leaves the tile-sorted result in tiles/vals, 4. stable tile sort
-  scan_reduce_kernel<<<n_scan_blocks, kScanThreads, 0, st>>>(w.rectd, M, ghist_depth, w.block_sums);
+  scan_reduce_kernel<<<n_scan_blocks, kScanThreads, 0, st>>>(w.rectd, M, ghist_depth, w.block_sums, w.stall);
   scan_blocks_kernel<<<1, 1024, 0, st>>>(w.block_sums, n_scan_blocks, capacity, n_instances, status);
   uint32_t* kA = (passes & 1) ? w.tiles_alt : tiles;
   uint32_t* vA = (passes & 1) ? w.vals_alt : vals;
@@ -644,19 +675,20 @@ cudaError_t launch_sort_tiles(int N, const gs_cameras& cams, const gs_batch& bat
   const size_t lbt_stride = radix_tiles(capacity) * 256;
   expand_kernel<<<n_scan_blocks, kScanThreads, 0, st>>>(w.rectd, order, M, ghist_depth, w.block_sums, proj, N, cams, batch, kA, vA,
                                                          capacity, n_instances, passes, ghist_tile, w.lb_tile,
-                                                         lbt_stride);
+                                                         lbt_stride, w.stall);
   const int tile_grid = (int)radix_tiles(capacity);
   for (int pass = 0; pass < passes; ++pass) {
     onesweep_kernel<<<tile_grid, kSortThreads, 0, st>>>(kA, vA, kB, vB, n_instances, 0, capacity, 8 * pass,
                                                          ghist_tile + 256 * pass, w.lb_tile + lbt_stride * pass,
-                                                         w.counters + kMaxDigits + pass, nullptr, nullptr, status);
+                                                         w.counters + kMaxDigits + pass, nullptr, nullptr, 0u, status,
+                                                         w.stall, spin_limit, fake_stall);
     std::swap(kA, kB);
     std::swap(vA, vB);
   }
 
   // 5. ranges
   tile_ranges_kernel<<<grid_stride_blocks(capacity / 4 + 1, 256), 256, 0, st>>>(tiles, n_instances, capacity,
-                                                                                 ranges);
+                                                                                 ranges, w.stall);
   return cudaGetLastError();
 }
 

@@ -29,23 +29,34 @@ class Renderer:
     instance buffers when the sort reported an overflow."""
 
     def __init__(self, n: int, cams: Cameras, batch: Batch, capacity: int = 0, bg=(0.0, 0.0, 0.0),
-                 device="cuda"):
-        self.n, self.cams, self.batch = n, cams, batch
-        self.proj = Projected(n, batch.B, device)
+                 device="cuda", dtype=torch.float32):
+        # dtype float64: the FP64 instantiation of projection and compositing
+        # (the Gaussians passed to forward/backward must be float64 too)
+        self.n, self.cams, self.batch, self.dtype = n, cams, batch, dtype
+        self.proj = Projected(n, batch.B, device, dtype)
         cap = capacity if capacity > 0 else max(1 << 16, 4 * n * batch.B)
         self.tl = TileLists(n, batch, cap, device)
         P = max(batch.n_pixels, 1)
-        self.image = torch.zeros((P, 3), dtype=torch.float32, device=device)
-        self.T_final = torch.zeros(P, dtype=torch.float32, device=device)
+        self.image = torch.zeros((P, 3), dtype=dtype, device=device)
+        self.T_final = torch.zeros(P, dtype=dtype, device=device)
         self.n_contrib = torch.zeros(P, dtype=torch.int32, device=device)
-        self.bg = torch.tensor(bg, dtype=torch.float32, device=device)
-        self.ws_bwd = torch.empty(max(render_bwd_workspace_bytes(n, batch), 256), dtype=torch.uint8,
-                                  device=device)
+        self.bg = torch.tensor(bg, dtype=dtype, device=device)
+        self.ws_bwd = torch.empty(max(render_bwd_workspace_bytes(n, batch, dtype == torch.float64), 256),
+                                  dtype=torch.uint8, device=device)
         self.status = new_status(device)
 
-    def forward(self, g: Gaussians, Rt: torch.Tensor = None, mark=_nomark, after_sort=None):
+    def _layout(self):
+        # a batch laid out on the device: its offsets follow the device copy
+        # of its view ids, which may have changed since the last launch
+        if self.batch.dynamic:
+            self.batch.layout(self.cams, self.status)
+
+    def forward(self, g: Gaussians, Rt: torch.Tensor = None, mark=_nomark, after_sort=None, layout=True):
         """Projection, tile sort, compositing; `after_sort()` (if given) is
-        called between the sort and the compositing."""
+        called between the sort and the compositing.  layout=False: the
+        caller has already laid out a device-laid-out batch on this stream."""
+        if layout:
+            self._layout()
         gs_project(g, self.cams, self.batch, self.proj, self.status, Rt)
         mark("project")
         gs_sort_tiles(self.n, self.cams, self.batch, self.proj, self.tl, self.status, Rt)
@@ -70,6 +81,7 @@ class Renderer:
         """Re-runs the forward with the per-pixel added-splat counter and
         returns the total number of splats composited (a diagnostic)."""
         n_added = torch.zeros_like(self.n_contrib)
+        self._layout()
         gs_project(g, self.cams, self.batch, self.proj, self.status, Rt)
         gs_sort_tiles(self.n, self.cams, self.batch, self.proj, self.tl, self.status, Rt)
         gs_render_fwd(self.batch, self.cams, self.proj, self.tl, self.bg, self.image, self.T_final,
@@ -83,6 +95,7 @@ class Renderer:
         """Runs projection + sort once, reads the instance count and grows
         the buffers if needed.  Returns True when they were resized."""
         self.status.zero_()
+        self._layout()
         gs_project(g, self.cams, self.batch, self.proj, self.status, Rt)
         gs_sort_tiles(self.n, self.cams, self.batch, self.proj, self.tl, self.status, Rt)
         need = self.n_instances()
@@ -139,10 +152,16 @@ class JointStep:
     def __init__(self, gaussians: Gaussians, cams: Cameras, X: torch.Tensor, obs_point: torch.Tensor,
                  obs_xy: torch.Tensor, view_obs_offset: torch.Tensor, targets: torch.Tensor,
                  target_px_offset: np.ndarray, views, hyper: Hyper = None, mode: str = "batched",
-                 capacity: int = 0, device="cuda", tile: int = 16, merged_tracks: bool = False):
+                 capacity: int = 0, device="cuda", tile: int = 16, merged_tracks: bool = False,
+                 dynamic_batch: bool = False):
         # merged_tracks: the "merged tracks" ablation variant, X_k = mu of a
         # Gaussian (obs_point then indexes Gaussians; X is ignored): the track
-        # term reads the Gaussian means and adds its gradient into theirs
+        # term reads the Gaussian means and adds its gradient into theirs.
+        # dynamic_batch: the batch's buffers are sized for any views of the
+        # scene and its layout is recomputed on the device at the start of
+        # every step, so next_batch() takes views of any sizes without
+        # dropping a captured graph (batches of uneven views).
+        self.dynamic_batch = bool(dynamic_batch)
         self.h = hyper or Hyper()
         self.merged_tracks = bool(merged_tracks)
         self.tile = int(tile)
@@ -179,16 +198,20 @@ class JointStep:
         self.set_batch(views)
 
     # -- batch management --------------------------------------------------
+    def _new_batch(self, views):
+        cap = Batch.capacity_for(self.cams, len(views), self.tile) if self.dynamic_batch else None
+        return Batch(self.cams, views, tile=self.tile, device=self.device, capacity=cap)
+
     def set_batch(self, views):
         views = np.asarray(views, dtype=np.int64)
         self.views = views
-        self.batch = Batch(self.cams, views, tile=self.tile, device=self.device)
+        self.batch = self._new_batch(views)
         n = self.g.n
         if self.mode == "batched":
             self.renderers = [Renderer(n, self.cams, self.batch, self._capacity, device=self.device)]
             self.slot_batches = [self.batch]
         else:
-            self.slot_batches = [Batch(self.cams, [v], tile=self.tile, device=self.device) for v in views]
+            self.slot_batches = [self._new_batch([v]) for v in views]
             cap = self._capacity // max(len(views), 1)
             self.renderers = [Renderer(n, self.cams, b, cap, device=self.device) for b in self.slot_batches]
         self.track_ws = torch.empty(max(track_workspace_bytes(self.batch), 256), dtype=torch.uint8,
@@ -200,15 +223,24 @@ class JointStep:
                 r.v_image = torch.empty((max(r.batch.n_pixels, 1), 3), dtype=torch.float32, device=self.device)
                 r.ws_photo = torch.empty(max(photo_loss_workspace_bytes(r.batch), 256), dtype=torch.uint8,
                                          device=self.device)
-        self.target_batch = torch.empty((max(self.batch.n_pixels, 1), 3), dtype=torch.float32,
-                                        device=self.device)
+        # the batch's target images in its pixel layout; the plain form
+        # gathers one view per launch, into one buffer per slot
+        for r in self.renderers:
+            r.target = torch.empty((max(r.batch.n_pixels, 1), 3), dtype=torch.float32, device=self.device)
+        self.target_batch = self.renderers[0].target if self.mode == "batched" else None
         self.load_targets()
         self.graph = None
+
+    def _gather_targets(self):
+        for r in self.renderers:
+            gs_gather_view_pixels(self.targets, self.target_px_offset_dev, self.cams, r.batch, r.target)
 
     def load_targets(self):
         """Gathers the batch's target images into slot order on the device
         (the step does this itself; this is for use outside a step)."""
-        gs_gather_view_pixels(self.targets, self.target_px_offset_dev, self.cams, self.batch, self.target_batch)
+        for r in self.renderers:
+            r._layout()
+        self._gather_targets()
 
     def set_tile(self, tile: int):
         """Switches the tile size (16 or 32 pixels): re-allocates the batch's
@@ -226,12 +258,14 @@ class JointStep:
         """Switches to another batch of views.  Views of the same per-slot
         sizes are swapped in place on the device, so a captured graph stays
         valid; other sizes re-allocate (and drop the graph)."""
-        if self.batch.same_layout(self.cams, views):
-            self.batch.set_views(self.cams, views)
+        vs = np.asarray(views, dtype=np.int64).reshape(-1)
+        if self.batch.same_layout(self.cams, vs) and (
+                self.mode == "batched" or all(b.same_layout(self.cams, [v]) for b, v in zip(self.slot_batches, vs))):
+            self.batch.set_views(self.cams, vs)
             if self.mode != "batched":
-                for b, v in zip(self.slot_batches, np.asarray(views).reshape(-1)):
+                for b, v in zip(self.slot_batches, vs):
                     b.set_views(self.cams, [v])
-            self.views = np.asarray(views, dtype=np.int64)
+            self.views = vs
         else:
             self.set_batch(views)
 
@@ -270,8 +304,7 @@ class JointStep:
                 extra = [] if self.merged_tracks else [self.gX]   # merged: gX is dg.mean
                 for t in self.dg.tensors() + extra + [self.g_tan, self.loss, self.n_masked]:
                     gs_zero(t)
-                gs_gather_view_pixels(self.targets, self.target_px_offset_dev, self.cams, self.batch,
-                                      self.target_batch)
+                self._gather_targets()
                 # the track term: done before the join, so its += into the
                 # pose tangent (and, merged, into dg.mean) precedes the
                 # projection backward's; not run at all when lambda_BA = 0
@@ -280,17 +313,17 @@ class JointStep:
                                          self.batch, h.huber_delta, h.lambda_ba, self.loss[1:2], self.gX,
                                          self.g_tan, self.n_masked, self.track_ws, self.Rt)
 
+        # every slot's offsets first: the side stream gathers all slots'
+        # targets once the first slot is sorted
+        for r in self.renderers:
+            r._layout()
         joined = False
         for b, r in enumerate(self.renderers):
-            r.forward(self.g, self.Rt, mark, after_sort=fork if b == 0 else None)
+            r.forward(self.g, self.Rt, mark, after_sort=fork if b == 0 else None, layout=False)
             if not joined:
                 main.wait_stream(side)
                 joined = True
-            if self.mode == "batched":
-                tgt = self.target_batch
-            else:
-                a, e = int(self.batch.px_offset_host[b]), int(self.batch.px_offset_host[b + 1])
-                tgt = self.target_batch[a:e]
+            tgt = r.target
             if self.ssim_on:
                 lam = h.lambda_ssim
                 gs_photo_loss(self.cams, r.batch, r.image, tgt, h.l1_weight * (1.0 - lam), h.l1_weight * lam,
@@ -340,10 +373,12 @@ class JointStep:
             per_render += 1 + (1 + 1 + 4 + 2 + 1 + (tbits + 7) // 8 + 1) + 1 + 1 + 2
             if self.ssim_on:
                 per_render += 3  # photometric loss: block list, forward, backward
-        # target gather 1, track + finalize 2 (unless lambda_BA = 0), step
-        # advance 1, Adam (all groups) 1, pose 1 (unless frozen)
-        return (per_render + 1 + (2 if self.h.lambda_ba != 0.0 else 0) + 1 + 1 +
-                (0 if self.h.freeze_poses else 1))
+        # target gather 1 per renderer, layout 1 per renderer (dynamic
+        # batches), track + finalize 2 (unless lambda_BA = 0), step advance
+        # 1, Adam (all groups) 1, pose 1 (unless frozen)
+        nr = len(self.renderers)
+        return (per_render + nr + (nr if self.dynamic_batch else 0) + (2 if self.h.lambda_ba != 0.0 else 0) + 1 +
+                1 + (0 if self.h.freeze_poses else 1))
 
     # -- CUDA graph ----------------------------------------------------------
     def capture(self, warmup: int = 1):

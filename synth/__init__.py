@@ -24,7 +24,11 @@ not available; these scenes stand in for them.  Recipes:
   train     200 views 1600x1066, 3M Gaussians SH3, 100k tracks 3..30 obs
             with 5 % outliers uniform over the image; batches of 8 views.
   large     1000 views W ~ U{960..1920}, H ~ U{540..1080}, 5M Gaussians
-            SH3, 400k tracks 2..40 obs, pose noise U[0.5, 3] deg.
+            SH3, 400k tracks 2..40 obs, pose noise U[0.5, 3] deg; batches of
+            16 random views.
+Track observations are drawn over the views that see the track point (in
+the image, positive depth) when the consumer passes its projection as
+`visible`; the benchmark and the full-size tests do.
 For all scenes but `tiny`: means ~ U[-1,1]^3, log-scale ~
 N(ln(0.31 (8/N)^(1/3)), 0.3), SH DC coefficients uniform over the range that
 maps to colour U(0,1), higher bands N(0, 0.05^2); the optimised scene is the
@@ -156,25 +160,46 @@ def perturb_poses(rng: np.random.Generator, Rt: np.ndarray, angle_deg, trans_fra
 
 
 def tracks(rng: np.random.Generator, gt_means: np.ndarray, n_tracks: int, obs_range,
-           n_views: int, pix_noise: float, outlier_frac: float = 0.0):
+           n_views: int, pix_noise: float, outlier_frac: float = 0.0, visible=None, chunk: int = 8192):
     """Track points (a random subset of ground-truth means) and their
-    observations, bucketed by view (view-CSR).  The observation pixel is
-    pi(X) + noise, which the consumer computes; this returns the noise, the
-    outlier mask and uniform outlier positions in [0,1)^2 (to be scaled by
-    the image size)."""
+    observations, bucketed by view (view-CSR).  Each track k draws its count
+    m_k ~ U{lo..hi} and observes min(m_k, #eligible) distinct views chosen
+    uniformly among its eligible ones: every view, or, when `visible` is
+    given, the views where the consumer's projection finds the point in the
+    image with positive depth -- visible(X [n,3]) -> bool [n, n_views] is
+    called on chunks of track points (this module does no projection).  The
+    observation pixel is pi(X) + noise, which the consumer computes; this
+    returns the noise, the outlier mask and uniform outlier positions in
+    [0,1)^2 (to be scaled by the image size)."""
     n_tracks = min(n_tracks, gt_means.shape[0])
     pick = rng.choice(gt_means.shape[0], size=n_tracks, replace=False)
     X = gt_means[pick].copy()
     lo, hi = obs_range
     m = rng.integers(lo, hi + 1, size=n_tracks)
     m = np.minimum(m, n_views)
-    pts, views = [], []
-    for k in range(n_tracks):
-        vs = rng.choice(n_views, size=m[k], replace=False)
-        pts.append(np.full(m[k], k))
-        views.append(vs)
-    obs_point = np.concatenate(pts).astype(np.int32) if pts else np.zeros(0, np.int32)
-    obs_view = np.concatenate(views).astype(np.int32) if views else np.zeros(0, np.int32)
+    if visible is None:
+        pts, views = [], []
+        for k in range(n_tracks):
+            vs = rng.choice(n_views, size=m[k], replace=False)
+            pts.append(np.full(m[k], k))
+            views.append(vs)
+        obs_point = np.concatenate(pts).astype(np.int32) if pts else np.zeros(0, np.int32)
+        obs_view = np.concatenate(views).astype(np.int32) if views else np.zeros(0, np.int32)
+    else:
+        pts, views = [], []
+        for k0 in range(0, n_tracks, chunk):
+            k1 = min(n_tracks, k0 + chunk)
+            vis = np.asarray(visible(X[k0:k1]), dtype=bool).reshape(k1 - k0, n_views)
+            # a uniform random subset of the eligible views: the m_k smallest
+            # of independent uniform keys, ineligible views keyed past 1
+            keys = rng.random((k1 - k0, n_views)) + np.where(vis, 0.0, 2.0)
+            order = np.argsort(keys, axis=1, kind="stable")
+            take = np.arange(n_views)[None, :] < np.minimum(m[k0:k1], vis.sum(1))[:, None]
+            rows, cols = np.nonzero(take)
+            pts.append((k0 + rows).astype(np.int32))
+            views.append(order[rows, cols].astype(np.int32))
+        obs_point = np.concatenate(pts) if pts else np.zeros(0, np.int32)
+        obs_view = np.concatenate(views) if views else np.zeros(0, np.int32)
     order = np.argsort(obs_view, kind="stable")
     obs_point, obs_view = obs_point[order], obs_view[order]
     M = obs_point.shape[0]
@@ -189,8 +214,12 @@ def tracks(rng: np.random.Generator, gt_means: np.ndarray, n_tracks: int, obs_ra
 
 
 def make_workload(name: str, n_gaussians: int | None = None, n_views: int | None = None,
-                  width=None, height=None, n_tracks: int | None = None, seed: int | None = None):
-    """Build every random input of a named workload (optionally shrunk)."""
+                  width=None, height=None, n_tracks: int | None = None, seed: int | None = None,
+                  visible=None):
+    """Build every random input of a named workload (optionally shrunk).
+    visible(X, wh, K, Rt) -> bool [n, V], supplied by the consumer, restricts
+    each track's observations to the views that see its point (the recipe);
+    without it every view is eligible."""
     w = WORKLOADS[name]
     seed = w.seed if seed is None else seed
     rng = np.random.default_rng(seed)
@@ -222,7 +251,8 @@ def make_workload(name: str, n_gaussians: int | None = None, n_views: int | None
     scale = np.exp(gt["log_scale"]).mean(axis=1, keepdims=True)
     cur = {k: v.copy() for k, v in gt.items()}
     cur["mean"] = gt["mean"] + rng.normal(size=gt["mean"].shape) * 0.25 * scale
-    tr = tracks(rng, gt["mean"], T, w.obs_range, V, w.pix_noise, w.outlier_frac)
+    vis = None if visible is None else (lambda X: visible(X, wh, K, Rt_gt))
+    tr = tracks(rng, gt["mean"], T, w.obs_range, V, w.pix_noise, w.outlier_frac, visible=vis)
     out.update(gt=gt, scene=cur, wh=wh, K=K, Rt_gt=Rt_gt, Rt=Rt, tracks=tr)
     return out
 

@@ -262,3 +262,37 @@ def test_adam_groups_match_oracle():
         oracle.adam(p, g, m, v, lr, 0.9, 0.999, 1e-15, 4)
         np.testing.assert_allclose(d[0].cpu().numpy(), p, rtol=1e-5, atol=3e-7 * max(1.0, lr * 1e3))
         np.testing.assert_allclose(d[2].cpu().numpy(), m, rtol=1e-5, atol=3e-7)
+
+
+def test_sort_wait_that_runs_out_flags_a_stall_and_ends():
+    """The radix passes' bounded wait: with the test hook in which no
+    predecessor block is ever seen to publish its digit counts
+    (sort_spin_limit = -4), every wait of a multi-tile pass gives up after 4
+    polls.  GS_FLAG_SORT_STALL is raised, the launches end (the stream
+    synchronises), the sort stops -- no instances, every tile list empty,
+    the image is the background -- and with the default bound back the same
+    buffers render the scene again, identical to a fresh renderer."""
+    from paper_2603_04847_gb300.core import gs_get_tuning, gs_set_tuning
+    from paper_2603_04847_gb300._lib import GS_FLAG_SORT_STALL
+    w = synth.make_workload("tiny", n_gaussians=20000)   # 20000 records: five 4096-item radix tiles
+    wh, K, Rt = _cam_arrays(256, 192)
+    r, g, *_ = gpu_forward(w["scene"], wh, K, Rt, [0])
+    ref_img = r.image.cpu().numpy().copy()
+    assert r.n_instances() > 0 and int(r.status.item()) == 0
+    saved = gs_get_tuning()
+    try:
+        gs_set_tuning(saved["render_fwd_batch"], saved["render_bwd_batch"], saved["sort_blocks_per_sm"], -4)
+        r.status.zero_()
+        r.forward(g)
+        torch.cuda.synchronize()
+        assert int(r.status.item()) & GS_FLAG_SORT_STALL
+        assert r.n_instances() == 0
+        assert not r.tl.ranges.cpu().numpy().any()
+        assert (r.image.cpu().numpy() == 0).all()
+    finally:
+        gs_set_tuning(saved["render_fwd_batch"], saved["render_bwd_batch"], saved["sort_blocks_per_sm"], 0)
+    r.status.zero_()
+    r.forward(g)
+    torch.cuda.synchronize()
+    assert int(r.status.item()) == 0
+    np.testing.assert_array_equal(r.image.cpu().numpy(), ref_img)

@@ -63,7 +63,7 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
     monkeypatch.setenv("WORLD_SIZE", "2")
     monkeypatch.setenv("RANK", "1")
-    monkeypatch.setattr(bench, "oracle_sample_step", boom)
+    monkeypatch.setattr(bench, "OraclePool", boom)
     args = bench.argparse.Namespace(steps=2, warmup=1, gpus=2, workload="mid")
     bench.run_reference(args, synth.make_workload("tiny"))
     assert capsys.readouterr().out == ""

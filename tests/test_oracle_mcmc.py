@@ -20,7 +20,7 @@ def test_one_copy_leaves_a_gaussian_unchanged(o):
 @pytest.mark.parametrize("N", [2, 3, 5, 8])
 def test_stacked_copies_composite_like_the_source(o, N):
     s = 0.7
-    oN, sN = mcmc.relocated_opacity_scale(o, [s], N)
+    oN, sN = mcmc.relocated_opacity_scale(o, [s], N, bounded=False)
     sN = float(sN[0])
     # alpha at the centre after compositing N copies front to back
     assert abs((1.0 - (1.0 - oN) ** N) - o) < 1e-12
@@ -96,3 +96,47 @@ def test_noise_is_gated_by_opacity_and_shaped_by_the_covariance():
     c, s_ = np.cos(0.8), np.sin(0.8)
     R = np.array([[c, -s_, 0], [s_, c, 0], [0, 0, 1]])
     assert np.abs(S - R @ np.diag([0.01, 0.04, 0.09]) @ R.T).max() < 1e-15
+
+
+def test_reset_opacity_is_bounded():
+    """A faint source drawn several times would give copies at or below the
+    dead threshold (o = 0.012, N = 3: o_N = 0.004); an opaque one would give
+    o_N = 1 and an infinite logit.  The bounds keep both inside
+    [0.005, 1 - 2^-23]; the scale is the unbounded rule's."""
+    oN, sN = mcmc.relocated_opacity_scale(0.012, [0.3], 3)
+    oN_u, sN_u = mcmc.relocated_opacity_scale(0.012, [0.3], 3, bounded=False)
+    assert oN_u < 0.005 and oN == 0.005 and np.array_equal(sN, sN_u)
+    o = mcmc.sigmoid(40.0)                          # rounds to 1 in double
+    oN, _ = mcmc.relocated_opacity_scale(o, [0.3], 1)
+    assert oN == mcmc.MAX_OPACITY and np.isfinite(np.log(oN / (1 - oN)))
+
+
+def test_growth_count_rule():
+    assert mcmc.n_grow(100, 1000) == 5
+    assert mcmc.n_grow(990, 1000) == 10
+    assert mcmc.n_grow(1000, 1000) == 0 and mcmc.n_grow(1200, 1000) == 0
+    assert mcmc.n_grow(19, 1000) == 0                 # floor(19.95) = 19
+
+
+def test_growth_appends_reset_copies_of_drawn_sources():
+    rng = np.random.default_rng(5)
+    p = _params(30, rng)
+    p["opacity_logit"][[4, 9]] = -9.0               # dead: never drawn
+    u = rng.uniform(size=6)
+    out, src = mcmc.grow(p, u)
+    assert len(src) == 6 and all(len(out[k]) == 36 for k in out)
+    assert not np.isin(src, [4, 9]).any()
+    np.testing.assert_array_equal(src, mcmc.draw_sources(mcmc.sigmoid(p["opacity_logit"]),
+                                                         mcmc.sigmoid(p["opacity_logit"]) <= mcmc.DEAD_OPACITY, u))
+    for i, j in enumerate(src):
+        for k in p:
+            np.testing.assert_array_equal(out[k][30 + i], out[k][j])
+    counts = np.bincount(src, minlength=30)
+    o0 = mcmc.sigmoid(p["opacity_logit"])
+    for j in np.nonzero(counts)[0]:
+        oN = mcmc.sigmoid(out["opacity_logit"][j])
+        exp = max(1 - (1 - o0[j]) ** (1.0 / (counts[j] + 1)), mcmc.DEAD_OPACITY)
+        assert abs(oN - exp) < 1e-12
+    for j in np.nonzero(counts == 0)[0]:
+        for k in p:
+            np.testing.assert_array_equal(out[k][j], p[k][j])
