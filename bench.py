@@ -47,9 +47,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "train", "batched", "mid", "sfm-ba"],
+    ap.add_argument("--workload", default="large", choices=["large", "train", "batched", "mid", "sfm-ba", "mcmc"],
                     help="large (default): 16 random views of 1000 uneven ones (960-1920 x 540-1080), 5M "
-                         "Gaussians; sfm-ba: Levenberg-Marquardt iterations of the bundle adjustment of Eq. 4")
+                         "Gaussians; sfm-ba: Levenberg-Marquardt iterations of the bundle adjustment of Eq. 4; "
+                         "mcmc: the MCMC densification step on 3M Gaussians")
     ap.add_argument("--mode", default="batched", choices=["batched", "plain"])
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
@@ -912,6 +913,7 @@ def run_sfm_ba(args):
     import synth
     from paper_2603_04847_gb300 import Cameras, build as libbuild
     from paper_2603_04847_gb300.ba import BundleAdjuster
+    from paper_2603_04847_gb300.core import sfm_ba_objective
     libbuild.build()
     rng = np.random.default_rng(0)
     V, P, W, H = 50, 20000, 1000, 750
@@ -938,6 +940,12 @@ def run_sfm_ba(args):
     cams = Cameras.from_numpy(wh, K, Rt0)
     Xd = torch.as_tensor(X + rng.normal(0, 0.005, X.shape), dtype=torch.float32, device="cuda")
     adj = BundleAdjuster(cams, Xd, op, oc, xy, delta=1.0, lam=1e-4)
+    # the robust objective at the true poses and points: a converged LM
+    # ends below it (the optimum also fits part of the pixel noise)
+    truth = torch.zeros(1, dtype=torch.float64, device="cuda")
+    sfm_ba_objective(torch.as_tensor(X, dtype=torch.float32, device="cuda"), Cameras.from_numpy(wh, K, Rt),
+                     adj.obs_point, adj.obs_cam, adj.obs_xy, 1.0, truth)
+    L_start = adj.objective
     for _ in range(args.warmup):
         adj.step()
     torch.cuda.synchronize()
@@ -957,7 +965,110 @@ def run_sfm_ba(args):
                 config=dict(workload="sfm-ba: %d cameras %dx%d, %d points, %d observations (2-12 per point)"
                             % (V, W, H, P, len(op))),
                 e2e=dict(value=1.0 / wall, unit="iterations/s", ms_per_step=1e3 * wall),
-                accepted=acc, objective=dict(start=L0, end=adj.objective), status=adj.status_flags())
+                accepted=acc, objective=dict(start=L_start, after_warmup=L0, end=adj.objective, at_truth=float(truth.item())),
+                status=adj.status_flags())
+    print(json.dumps(line), flush=True)
+
+
+def run_mcmc(args):
+    """MCMC densification steps/s (Sec. 3.3; Algorithm 1 "Relocate / add
+    Gaussians") on the 3M-Gaussian training scene: 5 % of the Gaussians dead
+    (opacity below 0.005), n = 2.86M live rows in arrays of the 3M cap.  One
+    step = relocation of every dead Gaussian, growth by the cited rule
+    min(cap, floor(1.05 n)) - n, the Adam-moment restart of every written row
+    and its source, and the opacity-gated noise on all means.  The random
+    draws are inputs; the parameters are restored outside the timed events
+    before every step, so each step does the same work."""
+    import torch
+    from paper_2603_04847_gb300 import Gaussians, build as libbuild
+    from paper_2603_04847_gb300.core import gs_mcmc_grow, gs_mcmc_noise, gs_mcmc_relocate, gs_mcmc_reset_moments
+    libbuild.build()
+    cap = 3_000_000
+    n = 2_860_000
+    rng = np.random.default_rng(0)
+    w = synth.make_workload("train", n_gaussians=cap, n_views=2, n_tracks=10)
+    sc = {k: v.copy() for k, v in w["scene"].items()}
+    dead = rng.choice(n, int(0.05 * n), replace=False)
+    sc["opacity_logit"][dead] = rng.uniform(-12.0, -5.5, len(dead))
+    sc["opacity_logit"][n:] = -20.0                      # the unused rows up to the cap
+    g0 = Gaussians.from_numpy(sc)
+    g = Gaussians.from_numpy(sc)
+    moments = [(torch.zeros_like(t), torch.zeros_like(t)) for t in g.tensors()]
+    n_add = max(0, min(cap, int(1.05 * n)) - n)   # the cited growth rule, 5 % up to the cap
+    u_dead = torch.as_tensor(rng.uniform(size=n), dtype=torch.float64, device="cuda")
+    u_add = torch.as_tensor(rng.uniform(size=n_add), dtype=torch.float64, device="cuda")
+    eta = torch.as_tensor(rng.normal(size=(cap, 3)), dtype=torch.float32, device="cuda")
+    src = torch.empty(n, dtype=torch.int32, device="cuda")
+    src_add = torch.empty(n_add, dtype=torch.int32, device="cuda")
+    n_dead = torch.zeros(1, dtype=torch.int32, device="cuda")
+    gl = Gaussians(*[t[:n] for t in g.tensors()])
+
+    def step():
+        gs_mcmc_relocate(gl, u_dead, src, n_dead)
+        gs_mcmc_reset_moments(cap, src, 0, moments)
+        gs_mcmc_grow(g, n, u_add, src_add)
+        gs_mcmc_reset_moments(cap, src_add, n, moments)
+        gs_mcmc_noise(Gaussians(*[t[:n + n_add] for t in g.tensors()]), eta[:n + n_add], 0.05)
+
+    def restore():
+        for a, b in zip(g.tensors(), g0.tensors()):
+            a.copy_(b)
+
+    for _ in range(args.warmup):
+        restore()
+        step()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    times = []
+    for _ in range(args.steps):
+        restore()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        step()
+        b.record(st)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    ms = sum(times) / len(times)
+    nd = int(n_dead.item())
+    # algorithmic bytes of one step: relocation reads the opacities three
+    # times (scan, apply, reset), writes the cdf/rank/count words and copies
+    # 59 floats per dead Gaussian; growth the same scan plus 59 floats per
+    # new row; the moment restart zeroes 2 x 59 floats per written row and
+    # source; the noise reads 14 floats and writes 3 per Gaussian
+    K = 59 * 4
+    byt = (n * (4 * 3 + 16) + nd * 2 * K) + (n * (4 * 3 + 16) + n_add * 2 * K) + 2 * (nd + n_add) * 2 * 2 * K + \
+          (n + n_add) * 4 * 17
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    # the oracle on the host: the same step on a bounded sample (20k rows)
+    import time as _time
+    from oracle import mcmc as omcmc
+    ns = 20000
+    ps = {k: np.asarray(v[:ns], np.float64) for k, v in sc.items()}
+    ud = rng.uniform(size=ns)
+    t0 = _time.perf_counter()
+    rel, _ = omcmc.relocate(ps, ud)
+    grown, _ = omcmc.grow(rel, rng.uniform(size=omcmc.n_grow(ns, int(ns * cap / n))))
+    omcmc.noise_means(grown["mean"], grown["log_scale"], grown["quat"], grown["opacity_logit"],
+                      rng.normal(size=grown["mean"].shape), 0.05)
+    t_cpu = _time.perf_counter() - t0
+    line = dict(metric="MCMC densification steps/s (relocate + grow + moment restart + noise)", value=1e3 / ms,
+                unit="steps/s", n_gpus=1, steps=args.steps, warmup=args.warmup, ms_per_step=ms,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32 (FP64 scan)", data="synthetic",
+                config=dict(workload="mcmc: %d of a %d cap Gaussians SH3, %d dead, %d added per step" % (n, cap, nd,
+                                                                                                       n_add)),
+                per_step=dict(ms=spread(times)),
+                roofline=dict(kernel="whole step", bound="hbm", achieved=byt / (ms * 1e-3) / 1e9, peak=hbm,
+                              unit="GB/s", frac=byt / (ms * 1e-3) / 1e9 / hbm, traffic=None,
+                              peak_source="measured" if "hbm_gbs" in peaks else "fallback"),
+                cpu_baseline=dict(value=(ns / n) / t_cpu, unit="steps/s", cores=1, kind="oracle",
+                                  sample="the oracle's relocate + grow + noise on the first %d rows (numpy, FP64), "
+                                         "scaled by rows: %.2f s" % (ns, t_cpu)))
     print(json.dumps(line), flush=True)
 
 
@@ -965,6 +1076,9 @@ def main():
     args = parse()
     if args.workload == "sfm-ba":
         run_sfm_ba(args)
+        return
+    if args.workload == "mcmc":
+        run_mcmc(args)
         return
     if args.impl == "reference":
         w = synth.make_workload(args.workload, visible=np_visible)

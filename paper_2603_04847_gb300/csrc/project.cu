@@ -127,6 +127,7 @@ struct ViewGeo {
   T j00, j02, j11, j12;
   T S2[3];      // 2-D covariance xx xy yy (dilated)
   T det;
+  T idet;       // 1 / det
   T conic[3];
   T m2[2];
   T dir[3];
@@ -174,6 +175,7 @@ __device__ inline void view_geo(const GaussGeo<T>& G, const SlotCamT<T>& c, T ne
   V.visible = V.det > T(0);
   if (!V.visible) return;
   const T idet = T(1) / V.det;
+  V.idet = idet;
   V.conic[0] = V.S2[2] * idet;
   V.conic[1] = -V.S2[1] * idet;
   V.conic[2] = V.S2[0] * idet;
@@ -510,14 +512,14 @@ __global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? 3 : 1) project_
       // e_1, e_2) each component is formed on its own:
       //   G'_ij = e_i^T G_Q e_j,  G_S2'_ij = -G'_ij / (lambda_i lambda_j),
       //   d L / d log s_c = 2 sum_ij G_S2'_ij (e_i . B_c)(e_j . B_c),
-      // with lambda_1 a sum of non-negative terms, lambda_2 = det / lambda_1
-      // and e_1 from the branch without cancellation.
+      // with lambda_1 a sum of non-negative terms, 1 / lambda_2 =
+      // lambda_1 / det and e_1 from the branch without cancellation.
       {
         const T xx = V.S2[0], xy = V.S2[1], yy = V.S2[2];
         const T h = T(0.5) * (xx - yy);
         const T rr = gsqrt(h * h + xy * xy);
         const T l1 = T(0.5) * (xx + yy) + rr;
-        const T l2 = V.det / l1;
+        const T il1 = T(1) / l1, il2 = l1 * V.idet;   // 1/lambda_2 = lambda_1 / det
         T e1x = h >= T(0) ? h + rr : xy, e1y = h >= T(0) ? xy : rr - h;
         const T n2 = e1x * e1x + e1y * e1y;
         if (n2 > T(0)) {
@@ -532,7 +534,7 @@ __global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? 3 : 1) project_
         const T G11 = v_a * e1x * e1x + v_b * e1x * e1y + v_c * e1y * e1y;
         const T G22 = v_a * e2x * e2x + v_b * e2x * e2y + v_c * e2y * e2y;
         const T G12 = v_a * e1x * e2x + hb * (e1x * e2y + e1y * e2x) + v_c * e1y * e2y;
-        const T S11 = -G11 / (l1 * l1), S22 = -G22 / (l2 * l2), S12 = -G12 / (l1 * l2);
+        const T S11 = -G11 * il1 * il1, S22 = -G22 * il2 * il2, S12 = -G12 * il1 * il2;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           const T Bx = V.j00 * V.Mc[k] + V.j02 * V.Mc[6 + k];

@@ -367,10 +367,11 @@ class JointStep:
         per_render = 0
         for b in self.slot_batches:
             tbits = int(math.ceil(math.log2(b.n_tiles))) if b.n_tiles > 1 else 0
-            # project 1; sort: zero 1, depth histogram 1, depth passes 4,
-            # scan 2, expand 1, one per tile pass, ranges 1; render fwd 1;
-            # raster bwd 1; project bwd + finalize 2
-            per_render += 1 + (1 + 1 + 4 + 2 + 1 + (tbits + 7) // 8 + 1) + 1 + 1 + 2
+            tile_passes = min((tbits + 7) // 8, (tbits + 8) // 9)   # 8- or 9-bit digits
+            # project 1; sort: zero 1, depth range 1, depth histogram 1,
+            # depth passes 4, scan 2, expand 1, one per tile pass, ranges 1;
+            # render fwd 1; raster bwd 1; project bwd + finalize 2
+            per_render += 1 + (1 + 1 + 1 + 4 + 2 + 1 + tile_passes + 1) + 1 + 1 + 2
             if self.ssim_on:
                 per_render += 3  # photometric loss: block list, forward, backward
         # target gather 1 per renderer, layout 1 per renderer (dynamic

@@ -1,13 +1,14 @@
 """Parity at the full size of the 8-view 1237x822, 200k-Gaussian SH3
 workload, in the batched launch configuration the benchmark times: sampled
-pixels and sampled Gaussians against the oracle (which computes them one by
-one), and the translation gauge identity of all gradients."""
+pixels and 64 sampled Gaussians against the oracle (which computes them one
+by one), the pose tangent and all 200k Gaussians' gradients of a cotangent
+on sampled pixels, and the translation gauge identity of all gradients."""
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from _gpu import f32, gpu_backward, gpu_forward, knife_mask, oracle_cam, oracle_scene, rel_linf
+from _gpu import f32, gpu_backward, gpu_forward, knife_mask, oracle_cam, oracle_scene, pose_rel_err, rel_linf
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -50,7 +51,7 @@ def test_sampled_gaussian_gradients_match_oracle(mid):
     proj = oracle.project(osc, cam)
     rng = np.random.default_rng(1)
     cand = np.nonzero(proj[:, oracle.P["visible"]] > 0)[0]
-    picks = rng.choice(cand, 4, replace=False)
+    picks = rng.choice(cand, 64, replace=False)
     vimg = np.zeros((batch.n_pixels, 3))
     wv = f32(rng.normal(size=(H, W, 3)))
     rects = []
@@ -69,6 +70,35 @@ def test_sampled_gaussian_gradients_match_oracle(mid):
         gj = np.concatenate([got[k][j].ravel() for k in ("mean", "log_scale", "quat", "opacity_logit", "sh")])
         ej = np.concatenate([e[k][j].ravel() for k in ("mean", "log_scale", "quat", "opacity_logit", "sh")])
         assert rel_linf(gj, ej) <= 1e-3, (j, rel_linf(gj, ej))
+
+
+def sampled_pixel_cotangent(w, r, g, batch, osc, b, n_pix, seed):
+    """A random cotangent on n_pix distinct pixels of slot b (knife-edge
+    pixels zeroed), zero elsewhere: the GPU's gradients of all Gaussians and
+    the view's pose tangent, and the oracle's for exactly those pixels."""
+    v = int(batch.views_host[b])
+    W, H = int(w["wh"][v][0]), int(w["wh"][v][1])
+    rng = np.random.default_rng(seed)
+    flat = rng.choice(W * H, n_pix, replace=False)
+    pix = np.stack([flat % W, flat // W], 1)
+    cam = oracle_cam(w["wh"], w["K"], w["Rt"], v)
+    ref = oracle.render(osc, cam, pixels=pix, knife_eps=1e-4)
+    vals = f32(rng.normal(size=(n_pix, 3)))
+    vals[knife_mask(ref)] = 0.0
+    vimg = np.zeros((batch.n_pixels, 3))
+    vimg[int(batch.px_offset_host[b]) + flat] = vals
+    got = gpu_backward(r, g, v_image=vimg)
+    exp = oracle.render_bwd(osc, cam, vals, pixels=pix)
+    return got, exp, v
+
+
+def test_sampled_pixel_cotangent_pose_tangent_and_all_gradients(mid):
+    w, r, g, cams, batch, osc = mid
+    got, exp, v = sampled_pixel_cotangent(w, r, g, batch, osc, 3, 400, 5)
+    for k in ("mean", "log_scale", "quat", "opacity_logit", "sh"):
+        assert rel_linf(got[k], exp[k]) <= 1e-3, (k, rel_linf(got[k], exp[k]))
+    assert pose_rel_err(got["tangent"][v], exp["tangent"], exp["tangent_abs"]) <= 1e-3
+    assert not np.delete(got["tangent"], v, axis=0).any()
 
 
 def test_translation_gauge_identity_full_size(mid):

@@ -1,14 +1,16 @@
 """Parity at the size of the training-loop step: 8 views of 1600x1066 and
 3M Gaussians SH3 (the first batch of the 200-view training workload), in
 the batched launch configuration the benchmark times: sampled pixels
-against the oracle (which computes them one by one) and the translation
-gauge identity of all gradients."""
+against the oracle (which computes them one by one), the pose tangent and
+all 3M Gaussians' gradients of a cotangent on sampled pixels, and the
+translation gauge identity of all gradients."""
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from _gpu import f32, gpu_backward, gpu_forward, knife_mask, oracle_cam, oracle_scene, rel_linf
+from _gpu import f32, gpu_backward, gpu_forward, knife_mask, oracle_cam, oracle_scene, pose_rel_err, rel_linf
+from test_gpu_fullsize import sampled_pixel_cotangent
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -44,6 +46,14 @@ def test_train_size_sampled_pixels_match_oracle(train):
         assert ok.sum() >= 18
         assert rel_linf(got[ok], ref["image"][ok]) <= 1e-4
         assert (ref["n_added"][ok] > 0).mean() > 0.5
+
+
+def test_train_size_sampled_pixel_cotangent_pose_tangent_and_all_gradients(train):
+    w, r, g, cams, batch, osc, views = train
+    got, exp, v = sampled_pixel_cotangent(w, r, g, batch, osc, 5, 64, 6)
+    for k in ("mean", "log_scale", "quat", "opacity_logit", "sh"):
+        assert rel_linf(got[k], exp[k]) <= 1e-3, (k, rel_linf(got[k], exp[k]))
+    assert pose_rel_err(got["tangent"][v], exp["tangent"], exp["tangent_abs"]) <= 1e-3
 
 
 def test_train_size_translation_gauge_identity(train):

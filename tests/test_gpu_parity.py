@@ -192,14 +192,10 @@ def test_tiny_thin_splats_forward_backward(tile):
     got = gpu_backward(r, g, v_image=wv.reshape(-1, 3))
     exp = oracle.render_bwd(osc, cam, wv)
     errs = {k: rel_linf(got[k], exp[k]) for k in ("mean", "log_scale", "quat", "opacity_logit", "sh")}
-    # the gradients of a short axis' scale and of the rotation pass through
-    # the small eigen-direction of the 3-D covariance, which FP32 resolves
-    # only to ~1e-5 times its condition number (~1e3 here), and the
-    # screen-space sums they start from are accumulated by FP32 atomics in
-    # no fixed order: a 5e-2 bar for those two on this scene, the usual one
-    # for the rest (the compositing masks are checked exactly above)
-    bars = dict(mean=GRAD_TOL, log_scale=5e-2, quat=5e-2, opacity_logit=GRAD_TOL, sh=GRAD_TOL)
-    assert e_img <= IMG_TOL and all(errs[k] <= bars[k] for k in bars), "image %.3g grads %s" % (e_img, errs)
+    # the usual bar on every tensor: the projection backward forms the
+    # log-scale gradient in the eigenframe of each splat's 2-D covariance,
+    # where the long axis' component does not drown in the short axis'
+    assert e_img <= IMG_TOL and all(e <= GRAD_TOL for e in errs.values()), "image %.3g grads %s" % (e_img, errs)
 
 
 def _compare_grads(got, ref, view=0, tol=GRAD_TOL):
@@ -387,3 +383,28 @@ def test_pose_update_and_adam_match_oracle():
     # inputs are O(1): FP32 rounding of the moment updates is ~1e-7 absolute
     np.testing.assert_allclose(pt.cpu().numpy(), po, rtol=1e-5, atol=3e-7)
     np.testing.assert_allclose(mt2.cpu().numpy(), mo2, rtol=1e-5, atol=3e-7)
+
+
+def test_repeat_runs_forward_bit_identical_backward_within_atomic_rounding():
+    """The forward (projection, sort, compositing) is deterministic: two
+    runs give bit-identical images, transmittance, contributor counts and
+    tile lists.  The backward sums each splat's per-tile partials with
+    atomics in whatever order the tiles finish, so two runs of the same
+    backward differ only by FP32 rounding of those sums: within 1e-6
+    (normwise) here, far inside the 1e-3 parity bar -- on the thin-streak
+    scene, where the covariance chain amplifies rounding the most."""
+    w, sc, wh, K, Rt = thin_splats()
+    outs = []
+    for _ in range(2):
+        r, g, cams, batch = gpu_forward(sc, wh, K, Rt, [0])
+        rng = np.random.default_rng(11)
+        v = f32(rng.normal(size=(192 * 256, 3)))
+        got = gpu_backward(r, g, v_image=v)
+        n = r.n_instances()
+        outs.append((r.image.cpu().numpy(), r.T_final.cpu().numpy(), r.n_contrib.cpu().numpy(),
+                     r.tl.vals.cpu().numpy()[:n], got))
+    (i0, t0, c0, l0, g0), (i1, t1, c1, l1, g1) = outs
+    for a, b in ((i0, i1), (t0, t1), (c0, c1), (l0, l1)):
+        np.testing.assert_array_equal(a, b)
+    for k in ("mean", "log_scale", "quat", "opacity_logit", "sh"):
+        assert rel_linf(g1[k], g0[k]) <= 1e-6, k
