@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain one-view-per-launch timing")
     ap.add_argument("--lambda-ssim", type=float, default=0.0,
                     help="SSIM weight of Eq. 5 (the paper: 0.2); 0 = the L1 photometric term alone")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="the compositing backward with run-to-run bit-identical gradients")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run this many eager steps and exit (for ncu launch lists)")
     return ap.parse_args()
@@ -464,7 +466,7 @@ def tuning_trials(tune):
     return out
 
 
-def tune_child(workload, mode, local, cache_path, lambda_ssim=0.0, w_path=None):
+def tune_child(workload, mode, local, cache_path, lambda_ssim=0.0, w_path=None, deterministic=False):
     """Autotunes the step of `workload` on GPU `local` and writes the result
     (with its trial timings) to the tuning cache at cache_path.  w_path: the
     synthetic workload pickled by the parent (saves drawing it again)."""
@@ -480,7 +482,8 @@ def tune_child(workload, mode, local, cache_path, lambda_ssim=0.0, w_path=None):
     inp = gpu_inputs(workload, "cuda:%d" % local, w)
     W = inp["w"]["workload"]
     views = list(range(min(W.batch, W.n_views)))
-    js = make_step(inp, views, mode, W.lambda_ba, lambda_ssim=lambda_ssim, dynamic=uneven(inp["w"]))
+    js = make_step(inp, views, mode, W.lambda_ba, lambda_ssim=lambda_ssim, dynamic=uneven(inp["w"]),
+                   deterministic=deterministic)
     tune = autotune(js, use_cache=True, cache_path=cache_path)
     with open(cache_path) as f:
         cache = json.load(f)
@@ -490,11 +493,11 @@ def tune_child(workload, mode, local, cache_path, lambda_ssim=0.0, w_path=None):
         json.dump(cache, f)
 
 
-def make_step(inp, views, mode, lambda_ba, tile=16, lambda_ssim=0.0, dynamic=False):
+def make_step(inp, views, mode, lambda_ba, tile=16, lambda_ssim=0.0, dynamic=False, deterministic=False):
     from paper_2603_04847_gb300 import Hyper, JointStep
     js = JointStep(inp["g"], inp["cams"], inp["X"], inp["obs_point"], inp["obs_xy"], inp["view_obs_offset"],
                    inp["targets"], inp["off"], views, Hyper(lambda_ba=lambda_ba, lambda_ssim=lambda_ssim), mode=mode,
-                   tile=tile, dynamic_batch=dynamic)
+                   tile=tile, dynamic_batch=dynamic, deterministic=deterministic)
     js.ensure_capacity()
     return js
 
@@ -666,7 +669,8 @@ def run_ours(args):
         with open(w_path, "wb") as f:
             pickle.dump(w, f, protocol=4)
         child = multiprocessing.get_context("spawn").Process(
-            target=tune_child, args=(args.workload, args.mode, local, tune_cache, args.lambda_ssim, w_path))
+            target=tune_child, args=(args.workload, args.mode, local, tune_cache, args.lambda_ssim, w_path,
+                                     args.deterministic))
         child.start()
         child.join()
         if child.exitcode != 0:
@@ -675,7 +679,8 @@ def run_ours(args):
     W = w["workload"]
     dyn = uneven(w)
     views = list(range(min(W.batch, W.n_views)))
-    js = make_step(inp, views, args.mode, W.lambda_ba, lambda_ssim=args.lambda_ssim, dynamic=dyn)
+    js = make_step(inp, views, args.mode, W.lambda_ba, lambda_ssim=args.lambda_ssim, dynamic=dyn,
+                   deterministic=args.deterministic)
     # random batches (Algorithm 1, "Sample image indices") when the workload
     # has more views than one batch
     n_batches = args.warmup + args.steps + max(10, args.steps) + 8
@@ -799,7 +804,8 @@ def run_ours(args):
     # plain one-view-per-launch form on the same inputs (eager, no graph)
     plain = None
     if not args.no_plain and args.mode == "batched":
-        jp = make_step(inp, views, "plain", W.lambda_ba, tile=js.tile, lambda_ssim=args.lambda_ssim, dynamic=dyn)
+        jp = make_step(inp, views, "plain", W.lambda_ba, tile=js.tile, lambda_ssim=args.lambda_ssim, dynamic=dyn,
+                       deterministic=args.deterministic)
         npl = max(3, min(args.steps, 10))
         pb = None if batch_list is None else batch_list[:npl]
         if pb is not None:
@@ -887,6 +893,8 @@ def run_ours(args):
                                 if batch_list is not None else "all views every step",
                                 mean_pixels_per_step=P_mean,
                                 lambda_ssim=args.lambda_ssim,
+                                backward="deterministic (per-instance slots, fixed-order sums)"
+                                if args.deterministic else "atomic (per-tile sums added by FP32 atomics)",
                                 graph=use_graph, l2="flushed between steps (256 MB write)",
                                 tuning=dict(tile=tune["tile"], render_fwd_batch=tune["render_fwd_batch"],
                                             render_bwd_batch=tune["render_bwd_batch"],
@@ -959,12 +967,25 @@ def run_sfm_ba(args):
     torch.cuda.synchronize()
     wall = (time.perf_counter() - t0) / args.steps
     dev_ms = a.elapsed_time(b) / args.steps
+    # per-stage device times of one more iteration (events between stages)
+    marks = [("start", torch.cuda.Event(enable_timing=True))]
+    marks[0][1].record(st)
+
+    def mark(name):
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(st)
+        marks.append((name, e))
+
+    adj.step(mark)
+    torch.cuda.synchronize()
+    stages = {marks[i + 1][0]: marks[i][1].elapsed_time(marks[i + 1][1]) for i in range(len(marks) - 1)}
     line = dict(metric="LM iterations/s of the SfM bundle adjustment (Eq. 4)", value=1e3 / dev_ms,
                 unit="iterations/s", n_gpus=1, steps=args.steps, warmup=args.warmup, ms_per_step=dev_ms,
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                 config=dict(workload="sfm-ba: %d cameras %dx%d, %d points, %d observations (2-12 per point)"
                             % (V, W, H, P, len(op))),
                 e2e=dict(value=1.0 / wall, unit="iterations/s", ms_per_step=1e3 * wall),
+                stages_ms=stages,
                 accepted=acc, objective=dict(start=L_start, after_warmup=L0, end=adj.objective, at_truth=float(truth.item())),
                 status=adj.status_flags())
     print(json.dumps(line), flush=True)
@@ -1029,6 +1050,22 @@ def run_mcmc(args):
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))
     ms = sum(times) / len(times)
+    # per-call device times of one more step (events between the calls)
+    restore()
+    torch.cuda.synchronize()
+    names = ("relocate", "reset_moments_relocated", "grow", "reset_moments_grown", "noise")
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+    calls = (lambda: gs_mcmc_relocate(gl, u_dead, src, n_dead),
+             lambda: gs_mcmc_reset_moments(cap, src, 0, moments),
+             lambda: gs_mcmc_grow(g, n, u_add, src_add),
+             lambda: gs_mcmc_reset_moments(cap, src_add, n, moments),
+             lambda: gs_mcmc_noise(Gaussians(*[t[:n + n_add] for t in g.tensors()]), eta[:n + n_add], 0.05))
+    evs[0].record(st)
+    for c, e in zip(calls, evs[1:]):
+        c()
+        e.record(st)
+    torch.cuda.synchronize()
+    stages = {k: evs[i].elapsed_time(evs[i + 1]) for i, k in enumerate(names)}
     nd = int(n_dead.item())
     # algorithmic bytes of one step: relocation reads the opacities three
     # times (scan, apply, reset), writes the cdf/rank/count words and copies
@@ -1045,15 +1082,16 @@ def run_mcmc(args):
     except OSError:
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
-    # the oracle on the host: the same step on a bounded sample (20k rows)
+    # the oracle on the host: the same step on all n rows (about 10 s of
+    # numpy work)
     import time as _time
     from oracle import mcmc as omcmc
-    ns = 20000
+    ns = n
     ps = {k: np.asarray(v[:ns], np.float64) for k, v in sc.items()}
     ud = rng.uniform(size=ns)
     t0 = _time.perf_counter()
     rel, _ = omcmc.relocate(ps, ud)
-    grown, _ = omcmc.grow(rel, rng.uniform(size=omcmc.n_grow(ns, int(ns * cap / n))))
+    grown, _ = omcmc.grow(rel, rng.uniform(size=omcmc.n_grow(ns, cap)))
     omcmc.noise_means(grown["mean"], grown["log_scale"], grown["quat"], grown["opacity_logit"],
                       rng.normal(size=grown["mean"].shape), 0.05)
     t_cpu = _time.perf_counter() - t0
@@ -1062,13 +1100,13 @@ def run_mcmc(args):
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32 (FP64 scan)", data="synthetic",
                 config=dict(workload="mcmc: %d of a %d cap Gaussians SH3, %d dead, %d added per step" % (n, cap, nd,
                                                                                                        n_add)),
-                per_step=dict(ms=spread(times)),
+                per_step=dict(ms=spread(times)), stages_ms=stages,
                 roofline=dict(kernel="whole step", bound="hbm", achieved=byt / (ms * 1e-3) / 1e9, peak=hbm,
                               unit="GB/s", frac=byt / (ms * 1e-3) / 1e9 / hbm, traffic=None,
                               peak_source="measured" if "hbm_gbs" in peaks else "fallback"),
                 cpu_baseline=dict(value=(ns / n) / t_cpu, unit="steps/s", cores=1, kind="oracle",
-                                  sample="the oracle's relocate + grow + noise on the first %d rows (numpy, FP64), "
-                                         "scaled by rows: %.2f s" % (ns, t_cpu)))
+                                  sample="the oracle's relocate + grow + noise of the same %d rows (numpy, FP64, "
+                                         "one step): %.2f s" % (ns, t_cpu)))
     print(json.dumps(line), flush=True)
 
 

@@ -83,7 +83,7 @@ enum {
                              <= 0: its step was set to zero              */
 };
 
-#define GS_ABI_VERSION 3
+#define GS_ABI_VERSION 4
 #define GS_MAX_BATCH 64   /* views per call */
 
 typedef struct CUstream_st* gs_stream; /* = cudaStream_t */
@@ -333,6 +333,44 @@ gs_status gs_render_bwd(const gs_gaussians* g, const gs_cameras* cams,
                         float l1_weight, double* loss,
                         const gs_gaussian_grads* dg, double* g_pose_tangent,
                         void* ws, size_t ws_bytes, gs_stream stream);
+
+/*
+ * gs_render_bwd_det, gs_raster_bwd_det — the same backward (Algorithm 1,
+ * "Backpropagate"; arguments and rules of gs_render_bwd / gs_raster_bwd)
+ * with results that do not depend on the order in which tiles run: two
+ * calls on the same inputs give bit-identical gradients and loss.  Each
+ * (record, tile) instance writes its sums into a slot of its own; the
+ * per-record sums are then formed in a fixed order (the record's tiles in
+ * row-major order of its tile rectangle), and the fused L1 loss is summed
+ * over the tiles in tile order.  capacity and n_instances: the instance
+ * capacity given to gs_sort_tiles and the count it wrote (device); when
+ * the lists do not hold every instance (GS_FLAG_CAPACITY or
+ * GS_FLAG_SORT_STALL raised by the sort) all screen-space gradients are
+ * zero.  ws: gs_render_bwd_det_workspace() bytes, 256-byte aligned
+ * (its start is laid out like gs_render_bwd's workspace, so gs_project_bwd
+ * takes it too).  Slower than gs_render_bwd (the slots are written and read
+ * once: 36 bytes per instance each way) and the workspace grows with the
+ * capacity.
+ */
+gs_status gs_render_bwd_det_workspace(int32_t n_gaussians, const gs_batch* batch,
+                                      size_t capacity, size_t* ws_bytes);
+gs_status gs_raster_bwd_det(const gs_gaussians* g, const gs_cameras* cams,
+                            const gs_batch* batch, const gs_projected* proj,
+                            const uint32_t* vals, const uint32_t* ranges,
+                            const uint32_t* n_instances, const float* bg, const float* image,
+                            const float* T_final, const uint32_t* n_contrib,
+                            const float* v_image, const float* target,
+                            float l1_weight, double* loss, size_t capacity,
+                            void* ws, size_t ws_bytes, gs_stream stream);
+gs_status gs_render_bwd_det(const gs_gaussians* g, const gs_cameras* cams,
+                            const gs_batch* batch, const gs_projected* proj,
+                            const uint32_t* vals, const uint32_t* ranges,
+                            const uint32_t* n_instances, const float* bg, const float* image,
+                            const float* T_final, const uint32_t* n_contrib,
+                            const float* v_image, const float* target,
+                            float l1_weight, double* loss, size_t capacity,
+                            const gs_gaussian_grads* dg, double* g_pose_tangent,
+                            void* ws, size_t ws_bytes, gs_stream stream);
 
 /*
  * gs_photo_loss — the photometric loss of Eq. 5 (Algorithm 1, "L_photo")

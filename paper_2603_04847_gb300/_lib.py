@@ -106,6 +106,13 @@ PROTOTYPES = {
                                      c_void_p, c_size_t, c_void_p]),
     "gs_project_bwd": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                       c_size_t, c_void_p]),
+    "gs_render_bwd_det_workspace": (ctypes.c_int, [c_int32, c_void_p, c_size_t, ctypes.POINTER(c_size_t)]),
+    "gs_raster_bwd_det": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float,
+                                         c_void_p, c_size_t, c_void_p, c_size_t, c_void_p]),
+    "gs_render_bwd_det": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float,
+                                         c_void_p, c_size_t, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "track_reproj_workspace": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_size_t)]),
     "track_reproj_fwd_bwd": (ctypes.c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                             c_void_p, c_float, c_float, c_void_p, c_void_p, c_void_p,
@@ -186,7 +193,7 @@ def load(path: str = LIB_PATH):
         if lib.gs_struct_size(i) != ctypes.sizeof(s):
             raise GsError("ABI mismatch for %s: C %d vs ctypes %d" % (s.__name__, lib.gs_struct_size(i),
                                                                       ctypes.sizeof(s)))
-    if lib.gs_abi_version() != 3:
+    if lib.gs_abi_version() != 4:
         raise GsError("unexpected libgs ABI version")
     _lib = lib
     return lib

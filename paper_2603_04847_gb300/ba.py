@@ -61,20 +61,27 @@ class BundleAdjuster:
                          Rt=self.Rt)
         self.objective = float(self.obj[0].item())
 
-    def step(self) -> bool:
-        """One LM iteration; returns whether the step was accepted."""
+    def step(self, mark=None) -> bool:
+        """One LM iteration; returns whether the step was accepted.
+        mark(name), if given, is called after each stage's launches."""
+        mark = mark or (lambda name: None)
         for a in (self.U, self.Vp, self.gc, self.gp, self.obj[1:2]):
             gs_zero(a)
         sfm_ba_assemble(self.X, self.cams, self.obs_point, self.obs_cam, self.obs_xy, self.delta, self.U, self.Vp,
                         self.gc, self.gp, self.Wo, None, Rt=self.Rt)
+        mark("assemble")
         sfm_ba_schur(self.U, self.Vp, self.gc, self.gp, self.Wo, self.obs_cam, self.off, self.ids, self.lam, self.S,
                      self.rhs, self.Vinv)
+        mark("schur")
         sfm_ba_solve_cameras(self.S, self.rhs, self.dc, self.status)
+        mark("solve_cameras")
         sfm_ba_back_substitute(self.Vinv, self.Vp, self.gp, self.Wo, self.obs_cam, self.off, self.ids, self.dc,
                                self.dp)
+        mark("back_substitute")
         sfm_ba_apply_step(self.Rt, self.X, self.dc, self.dp, self.Rt_trial, self.X_trial)
         sfm_ba_objective(self.X_trial, self.cams, self.obs_point, self.obs_cam, self.obs_xy, self.delta,
                          self.obj[1:2], Rt=self.Rt_trial)
+        mark("apply_and_objective")
         new = float(self.obj[1].item())
         if new < self.objective:
             self.Rt, self.Rt_trial = self.Rt_trial, self.Rt

@@ -330,6 +330,31 @@ def render_bwd_workspace_bytes(n: int, batch: Batch, f64: bool = False) -> int:
     return ws.value
 
 
+def render_bwd_det_workspace_bytes(n: int, batch: Batch, capacity: int) -> int:
+    lib = _lib.load()
+    ws = ctypes.c_size_t(0)
+    bc = batch.c()
+    check(lib.gs_render_bwd_det_workspace(n, ctypes.byref(bc), int(capacity), ctypes.byref(ws)),
+          "gs_render_bwd_det_workspace")
+    return ws.value
+
+
+def gs_raster_bwd_det(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, tl: TileLists, bg, image,
+                      T_final, n_contrib, v_image, target, l1_weight: float, loss, ws: torch.Tensor, Rt=None,
+                      stream=None):
+    """gs_raster_bwd with tile-order-independent results (gs_raster_bwd_det);
+    ws from render_bwd_det_workspace_bytes(n, batch, tl.capacity)."""
+    lib = _lib.load()
+    if g.f64:
+        raise _lib.GsError("gs_raster_bwd_det is FP32 only")
+    _need_cuda(bg, T_final, n_contrib, ws, image, v_image, target, loss)
+    gc, cc, bc, pc = g.c(), cams.c(Rt), batch.c(), proj.c()
+    check(lib.gs_raster_bwd_det(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc),
+                                _p(tl.vals), _p(tl.ranges), _p(tl.n_instances), _p(bg), _p(image), _p(T_final),
+                                _p(n_contrib), _p(v_image), _p(target), float(l1_weight), _p(loss), tl.capacity,
+                                _p(ws), ws.numel(), _stream(stream)), "gs_raster_bwd_det")
+
+
 def gs_render_bwd(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, tl: TileLists,
                   bg: torch.Tensor, image, T_final, n_contrib, v_image, target, l1_weight: float,
                   loss, dg: Gaussians, g_pose_tangent: torch.Tensor, ws: torch.Tensor, Rt=None, stream=None):

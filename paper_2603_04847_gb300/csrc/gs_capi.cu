@@ -303,6 +303,61 @@ gs_status gs_render_bwd(const gs_gaussians* g, const gs_cameras* cams, const gs_
   return gs_project_bwd(g, cams, batch, proj, dg, g_pose_tangent, ws, ws_bytes, stream);
 }
 
+namespace {
+size_t det_ws_bytes(int N, const gs_batch& b, size_t capacity) {
+  return v2d_bytes(N, b) + pose_partial_bytes(N, b) + render_bwd_det_bytes((size_t)b.B * N, b.n_tiles, capacity);
+}
+}  // namespace
+
+gs_status gs_render_bwd_det_workspace(int32_t n_gaussians, const gs_batch* batch, size_t capacity,
+                                      size_t* ws_bytes) {
+  gs_status s;
+  if ((s = check_batch(batch))) return s;
+  if (!ws_bytes || n_gaussians < 0) return fail(GS_ERR_ARG, "gs_render_bwd_det_workspace: bad argument");
+  if (capacity > 0xffffffffull) return fail(GS_ERR_ARG, "gs_render_bwd_det_workspace: capacity above 2^32 - 1");
+  *ws_bytes = det_ws_bytes(n_gaussians, *batch, capacity);
+  return GS_OK;
+}
+
+gs_status gs_raster_bwd_det(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
+                            const gs_projected* proj, const uint32_t* vals, const uint32_t* ranges,
+                            const uint32_t* n_instances, const float* bg, const float* image, const float* T_final,
+                            const uint32_t* n_contrib, const float* v_image, const float* target,
+                            float l1_weight, double* loss, size_t capacity, void* ws, size_t ws_bytes,
+                            gs_stream stream) {
+  gs_status s;
+  if ((s = check_bwd_common(g, cams, batch, proj, ws, ws_bytes, "gs_raster_bwd_det"))) return s;
+  if (!vals || !ranges || !n_instances || !bg || !T_final || !n_contrib)
+    return fail(GS_ERR_ARG, "gs_raster_bwd_det: null argument");
+  if (!v_image && (!target || !image))
+    return fail(GS_ERR_ARG, "gs_raster_bwd_det: need v_image, or image and target for the fused L1");
+  if (!v_image && !std::isfinite(l1_weight)) return fail(GS_ERR_NONFINITE, "gs_raster_bwd_det: l1_weight");
+  if (capacity > 0xffffffffull) return fail(GS_ERR_ARG, "gs_raster_bwd_det: capacity above 2^32 - 1");
+  const size_t need = det_ws_bytes(g->n, *batch, capacity);
+  if (ws_bytes < need) return fail(GS_ERR_ARG, "gs_raster_bwd_det: workspace %zu < %zu bytes", ws_bytes, need);
+  char* w = static_cast<char*>(ws);
+  float* v2d = reinterpret_cast<float*>(w);
+  void* det = w + v2d_bytes(g->n, *batch) + pose_partial_bytes(g->n, *batch);
+  const cudaError_t e = launch_render_bwd_det(*batch, *cams, *proj, (size_t)batch->B * g->n, vals, ranges,
+                                              n_instances, bg, image, T_final, n_contrib, v_image, target,
+                                              l1_weight, loss, v2d, det, capacity, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_raster_bwd_det");
+  return GS_OK;
+}
+
+gs_status gs_render_bwd_det(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
+                            const gs_projected* proj, const uint32_t* vals, const uint32_t* ranges,
+                            const uint32_t* n_instances, const float* bg, const float* image, const float* T_final,
+                            const uint32_t* n_contrib, const float* v_image, const float* target,
+                            float l1_weight, double* loss, size_t capacity, const gs_gaussian_grads* dg,
+                            double* g_pose_tangent, void* ws, size_t ws_bytes, gs_stream stream) {
+  if (!dg || !g_pose_tangent) return fail(GS_ERR_ARG, "gs_render_bwd_det: null argument");
+  gs_status s = gs_raster_bwd_det(g, cams, batch, proj, vals, ranges, n_instances, bg, image, T_final,
+                                  n_contrib, v_image, target, l1_weight, loss, capacity, ws, ws_bytes, stream);
+  if (s != GS_OK) return s;
+  return gs_project_bwd(g, cams, batch, proj, dg, g_pose_tangent, ws, ws_bytes, stream);
+}
+
 /* ---- FP64 instantiation of the projection and compositing -------------- */
 
 gs_status gs_project_f64(const gs_gaussians_f64* g, const gs_cameras_f64* cams, const gs_batch* batch,

@@ -46,6 +46,16 @@ cudaError_t launch_render_bwd(const gs_batch& batch, const gs_cameras& cams, con
                               const float* image, const float* T_final, const uint32_t* n_contrib,
                               const float* v_image, const float* target, float l1_weight,
                               double* loss, float* v2d, cudaStream_t st);
+// The deterministic backward's scratch (after the v2d records and pose
+// partials): per-record slot bases, scan block sums, one slot of 9 floats
+// per instance of the capacity, and the tiles' loss sums.
+size_t render_bwd_det_bytes(size_t M, int n_tiles, size_t capacity);
+cudaError_t launch_render_bwd_det(const gs_batch& batch, const gs_cameras& cams, const gs_projected& proj,
+                                  size_t M, const uint32_t* vals, const uint32_t* ranges,
+                                  const uint32_t* n_instances, const float* bg, const float* image,
+                                  const float* T_final, const uint32_t* n_contrib, const float* v_image,
+                                  const float* target, float l1_weight, double* loss, float* v2d, void* det_ws,
+                                  size_t capacity, cudaStream_t st);
 
 cudaError_t launch_render_fwd_f64(const gs_batch& batch, const gs_cameras_f64& cams, const gs_projected_f64& proj,
                                   const uint32_t* vals, const uint32_t* ranges, const double* bg, double* image,

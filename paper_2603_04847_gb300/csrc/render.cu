@@ -507,6 +507,35 @@ __device__ inline void add_record(double* v2d, uint32_t r, const double* g) {
   for (int i = 0; i < 9; ++i) atomicAdd(dst + i, g[i]);
 }
 
+// Outputs of the deterministic backward: every (record, tile) instance
+// gets a slot of its own, so no two tiles add into the same memory and the
+// per-record sums are formed afterwards in a fixed order (det_reduce_kernel).
+// Record r's slots are base[r] .. base[r] + n_tiles[r] - 1 (base is the
+// exclusive scan of n_tiles in record order); the tile (tx, ty) of its
+// rectangle (x0, y0, x1, y1) has slot base[r] + (ty - y0) (x1 - x0 + 1) +
+// (tx - x0).  Slots at or past cap (the instance buffers overflowed, which
+// the sort has flagged) are neither written nor read.
+struct DetOut {
+  const uint32_t* base;
+  const ushort4* rect;
+  float4* p8;          // [cap][2]: the moments 0..7 of the slot
+  float* p1;           // [cap]: moment 8
+  size_t cap;
+  double* tile_loss;   // [tiles]: each tile's L1 sum (fused L1 only)
+};
+
+__device__ inline uint32_t det_slot(const DetOut& det, uint32_t r, int tx, int ty) {
+  const ushort4 rc = det.rect[r];
+  return det.base[r] + (uint32_t)(ty - (int)rc.y) * (uint32_t)(rc.z - rc.x + 1) + (uint32_t)(tx - (int)rc.x);
+}
+
+__device__ inline void det_store(const DetOut& det, uint32_t slot, const float* g) {
+  if (slot >= det.cap) return;
+  det.p8[2 * (size_t)slot] = make_float4(g[0], g[1], g[2], g[3]);
+  det.p8[2 * (size_t)slot + 1] = make_float4(g[4], g[5], g[6], g[7]);
+  det.p1[slot] = g[8];
+}
+
 template <typename T>
 __device__ inline void load_pixel(PixBwd<T>& P, bool inside, size_t p, const TileInfo<T>& ti, const T* bg,
                                   const T* __restrict__ image, const T* __restrict__ T_final,
@@ -537,12 +566,16 @@ __device__ inline void load_pixel(PixBwd<T>& P, bool inside, size_t p, const Til
   if (P.v0 == T(0) && P.v1 == T(0) && P.v2 == T(0)) P.nc = 0;
 }
 
-template <typename T, int kTile, int kBatch>
+// kDet (FP32 only): each (record, tile) sum goes to its own slot of `det`
+// instead of being added into the record, and every instance of the tile's
+// list gets its slot written (zeros where nothing was composited).
+template <typename T, int kTile, int kBatch, bool kDet>
 __global__ void __launch_bounds__(Shape<kTile>::kThreads, (bwd_min_blocks<T, kTile>())) render_bwd_kernel(
     gs_batch batch, Sizes cams, const T* __restrict__ splat, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ ranges, const T* __restrict__ bg, const T* __restrict__ image,
     const T* __restrict__ T_final, const uint32_t* __restrict__ n_contrib, const T* __restrict__ v_image,
-    const T* __restrict__ target, T l1_weight, double* loss, T* __restrict__ v2d) {
+    const T* __restrict__ target, T l1_weight, double* loss, T* __restrict__ v2d, DetOut det) {
+  static_assert(!kDet || sizeof(T) == 4, "the deterministic backward is FP32");
   constexpr int kThreads = Shape<kTile>::kThreads;
   __shared__ TileInfo<T> ti;
   __shared__ v2_t<T> s_m[kBatch];
@@ -551,6 +584,7 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (bwd_min_blocks<T, kTi
   __shared__ uint32_t s_mask[kBatch];
   __shared__ uint8_t s_list[kThreads / 32][kBatch];
   __shared__ uint32_t s_rec[kBatch];
+  __shared__ uint32_t s_slot[kDet ? kBatch : 1];
   // per-warp gradient slots where they fit in shared memory, else one set
   // shared by the warps through shared atomics
   constexpr int kW = Shape<kTile>::kWarps;
@@ -564,7 +598,11 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (bwd_min_blocks<T, kTi
   if (threadIdx.x == 0) s_max = 0;
   find_tile<kTile>(batch, cams, gt, &ti);
   __syncthreads();
-  if (!ti.ok) return;  // block-uniform
+  if (!ti.ok) {  // block-uniform; such a slot has no instances
+    if constexpr (kDet)
+      if (threadIdx.x == 0 && det.tile_loss) det.tile_loss[gt] = 0.0;
+    return;
+  }
   const int lane = threadIdx.x & 31;
   int lx, ly;
   tile_pixels<kTile>(threadIdx.x, lx, ly);
@@ -591,7 +629,11 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (bwd_min_blocks<T, kTi
   if (loss != nullptr && v_image == nullptr && threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < kThreads / 32; ++w) t += (double)s_loss[w];
-    if (t != 0.0) atomicAdd(loss, t);
+    if constexpr (kDet) {
+      if (det.tile_loss) det.tile_loss[gt] = t;
+    } else {
+      if (t != 0.0) atomicAdd(loss, t);
+    }
   }
   const uint32_t n_end = s_max;  // positions [0, n_end) of the tile list
   const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, nc_max);
@@ -604,6 +646,7 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (bwd_min_blocks<T, kTi
         const uint32_t r = vals[start + bstart + s];
         s_rec[s] = r;
         stage_splat<kTile>(s, r, splat, x0, y0, s_m, s_q, s_c, s_mask);
+        if constexpr (kDet) s_slot[s] = det_slot(det, r, ti.tx, ti.ty);
       }
 #pragma unroll
       for (int w = 0; w < kSlots; ++w)
@@ -672,13 +715,26 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (bwd_min_blocks<T, kTi
       }
       const bool nz = sg[0] != T(0) || sg[1] != T(0) || sg[2] != T(0) || sg[3] != T(0) || sg[4] != T(0) ||
                       sg[5] != T(0) || sg[6] != T(0) || sg[7] != T(0) || sg[8] != T(0);
-      if (nz) {
-        T rec[9];
+      T rec[9];
+      if constexpr (kDet) {
+        if (nz) moments_to_grad(sg, s_q[s], s_c[s].w, rec);
+        else
+#pragma unroll
+          for (int i = 0; i < 9; ++i) rec[i] = T(0);
+        det_store(det, s_slot[s], rec);
+      } else if (nz) {
         moments_to_grad(sg, s_q[s], s_c[s].w, rec);
         add_record(v2d, s_rec[s], rec);
       }
     }
     __syncthreads();
+  }
+  if constexpr (kDet) {
+    // instances behind every pixel's last contributor: zero slots
+    const uint32_t n_list = ranges[2 * gt + 1] - start;
+    const float zero[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (uint32_t pos = n_end + threadIdx.x; pos < n_list; pos += kThreads)
+      det_store(det, det_slot(det, vals[start + pos], ti.tx, ti.ty), zero);
   }
 }
 
@@ -712,29 +768,161 @@ void render_fwd_tile(int rb, const gs_batch& batch, const Sizes& cams, const flo
     render_fwd_launch<float, kTile, 256>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, n_added, st);
 }
 
-template <typename T, int kTile, int kBatch>
+template <typename T, int kTile, int kBatch, bool kDet = false>
 void render_bwd_launch(const gs_batch& batch, const Sizes& cams, const T* sp, const uint32_t* vals,
                        const uint32_t* ranges, const T* bg, const T* image, const T* T_final,
                        const uint32_t* n_contrib, const T* v_image, const T* target, T l1_weight, double* loss,
-                       T* v2d, cudaStream_t st) {
-  render_bwd_kernel<T, kTile, kBatch><<<batch.n_tiles, Shape<kTile>::kThreads, 0, st>>>(
-      batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image, target, l1_weight, loss, v2d);
+                       T* v2d, cudaStream_t st, const DetOut& det = DetOut{}) {
+  render_bwd_kernel<T, kTile, kBatch, kDet><<<batch.n_tiles, Shape<kTile>::kThreads, 0, st>>>(
+      batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image, target, l1_weight, loss, v2d, det);
 }
 
-template <int kTile>
+template <int kTile, bool kDet = false>
 void render_bwd_tile(int rb, const gs_batch& batch, const Sizes& cams, const float* sp, const uint32_t* vals,
                      const uint32_t* ranges, const float* bg, const float* image, const float* T_final,
                      const uint32_t* n_contrib, const float* v_image, const float* target, float l1_weight,
-                     double* loss, float* v2d, cudaStream_t st) {
+                     double* loss, float* v2d, cudaStream_t st, const DetOut& det = DetOut{}) {
   if (rb == 64)
-    render_bwd_launch<float, kTile, 64>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image,
-                                        target, l1_weight, loss, v2d, st);
+    render_bwd_launch<float, kTile, 64, kDet>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib,
+                                              v_image, target, l1_weight, loss, v2d, st, det);
   else if (rb == 128)
-    render_bwd_launch<float, kTile, 128>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image,
-                                         target, l1_weight, loss, v2d, st);
+    render_bwd_launch<float, kTile, 128, kDet>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib,
+                                               v_image, target, l1_weight, loss, v2d, st, det);
   else
-    render_bwd_launch<float, kTile, 256>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib, v_image,
-                                         target, l1_weight, loss, v2d, st);
+    render_bwd_launch<float, kTile, 256, kDet>(batch, cams, sp, vals, ranges, bg, image, T_final, n_contrib,
+                                               v_image, target, l1_weight, loss, v2d, st, det);
+}
+
+// ---- the deterministic backward's fixed-order reductions -----------------
+
+constexpr int kDetThreads = 1024;
+constexpr int kDetItems = 4;
+constexpr int kDetTile = kDetThreads * kDetItems;
+
+// Block-wide inclusive scan of one u64 per thread (kDetThreads threads).
+__device__ inline unsigned long long det_block_scan(unsigned long long x, unsigned long long* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) sm[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long w = sm[lane];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, w, off);
+      if (lane >= off) w += y;
+    }
+    sm[lane] = w;
+  }
+  __syncthreads();
+  const unsigned long long r = x + (warp > 0 ? sm[warp - 1] : 0ull);
+  __syncthreads();
+  return r;
+}
+
+// Sum of n_tiles over each kDetTile records.
+__global__ void __launch_bounds__(kDetThreads) det_scan_reduce_kernel(const uint32_t* __restrict__ n_tiles, size_t M,
+                                                                      unsigned long long* __restrict__ bsum) {
+  __shared__ unsigned long long sm[32];
+  const size_t r0 = (size_t)blockIdx.x * kDetTile + (size_t)threadIdx.x * kDetItems;
+  unsigned long long x = 0;
+#pragma unroll
+  for (int i = 0; i < kDetItems; ++i)
+    if (r0 + i < M) x += n_tiles[r0 + i];
+  x = det_block_scan(x, sm);
+  if (threadIdx.x == kDetThreads - 1) bsum[blockIdx.x] = x;
+}
+
+// Exclusive scan of the block sums, in place, in one block.
+__global__ void __launch_bounds__(kDetThreads) det_scan_top_kernel(unsigned long long* bsum, int n_blocks) {
+  __shared__ unsigned long long sm[32];
+  __shared__ unsigned long long s_last;
+  unsigned long long carry = 0;
+  for (int b0 = 0; b0 < n_blocks; b0 += kDetThreads) {
+    const int i = b0 + threadIdx.x;
+    const unsigned long long x = i < n_blocks ? bsum[i] : 0ull;
+    const unsigned long long inc = det_block_scan(x, sm);
+    if (i < n_blocks) bsum[i] = carry + inc - x;
+    if (threadIdx.x == kDetThreads - 1) s_last = inc;
+    __syncthreads();
+    carry += s_last;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[n_blocks] = carry;  // all instances of the records
+}
+
+// base[r] = sum of n_tiles over the records before r (0xffffffff past 32
+// bits: such records have no slot).
+__global__ void __launch_bounds__(kDetThreads) det_scan_down_kernel(const uint32_t* __restrict__ n_tiles, size_t M,
+                                                                    const unsigned long long* __restrict__ bsum,
+                                                                    uint32_t* __restrict__ base) {
+  __shared__ unsigned long long sm[32];
+  const size_t r0 = (size_t)blockIdx.x * kDetTile + (size_t)threadIdx.x * kDetItems;
+  uint32_t v[kDetItems];
+  unsigned long long x = 0;
+#pragma unroll
+  for (int i = 0; i < kDetItems; ++i) {
+    v[i] = r0 + i < M ? n_tiles[r0 + i] : 0u;
+    x += v[i];
+  }
+  unsigned long long e = det_block_scan(x, sm) - x + bsum[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < kDetItems; ++i) {
+    if (r0 + i < M) base[r0 + i] = e > 0xffffffffull ? 0xffffffffu : (uint32_t)e;
+    e += v[i];
+  }
+}
+
+// v2d[r] = sum over record r's slots in slot order; culled records get
+// zeros, and so does every record when the tile lists do not hold all the
+// records' instances (the sort overflowed its capacity or stopped: it has
+// flagged that, and some slots were never written).
+__global__ void __launch_bounds__(256) det_reduce_kernel(const uint32_t* __restrict__ n_tiles,
+                                                         const uint32_t* __restrict__ base,
+                                                         const unsigned long long* __restrict__ total,
+                                                         const uint32_t* __restrict__ n_instances,
+                                                         const float4* __restrict__ p8,
+                                                         const float* __restrict__ p1, size_t cap, size_t M,
+                                                         float* __restrict__ v2d) {
+  const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= M) return;
+  const bool complete = *total <= cap && *total == (unsigned long long)*n_instances;
+  const uint32_t n = complete ? n_tiles[r] : 0u;
+  const size_t b = base[r];
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f), c = a;
+  float d = 0.f;
+  for (uint32_t k = 0; k < n; ++k) {
+    const size_t sl = b + k;
+    if (sl >= cap) break;
+    const float4 x = p8[2 * sl], y = p8[2 * sl + 1];
+    a.x += x.x; a.y += x.y; a.z += x.z; a.w += x.w;
+    c.x += y.x; c.y += y.y; c.z += y.z; c.w += y.w;
+    d += p1[sl];
+  }
+  float4* dst = reinterpret_cast<float4*>(v2d) + 3 * r;
+  dst[0] = a;
+  dst[1] = c;
+  dst[2] = make_float4(d, 0.f, 0.f, 0.f);
+}
+
+// loss += the tiles' L1 sums, in a fixed order.
+__global__ void __launch_bounds__(kDetThreads) det_loss_kernel(const double* __restrict__ tile_loss,
+                                                               const gs_batch batch, double* loss) {
+  __shared__ double sm[kDetThreads];
+  const int n = batch.tile_offset[batch.B];
+  double x = 0.0;
+  for (int i = threadIdx.x; i < n; i += kDetThreads) x += tile_loss[i];
+  sm[threadIdx.x] = x;
+  __syncthreads();
+  for (int w = kDetThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && sm[0] != 0.0) atomicAdd(loss, sm[0]);
 }
 
 }  // namespace
@@ -767,6 +955,67 @@ cudaError_t launch_render_bwd(const gs_batch& batch, const gs_cameras& cams, con
   else
     render_bwd_tile<16>(rb, batch, sz, proj.splat, vals, ranges, bg, image, T_final, n_contrib, v_image, target,
                         l1_weight, loss, v2d, st);
+  return cudaGetLastError();
+}
+
+namespace {
+struct DetLayout {
+  size_t base, bsum, p8, p1, tile_loss, bytes;
+};
+inline size_t det_align(size_t x) { return (x + 255) & ~(size_t)255; }
+DetLayout det_layout(size_t M, int n_tiles, size_t cap) {
+  DetLayout L;
+  const size_t nblk = (M + kDetTile - 1) / kDetTile;
+  L.base = 0;
+  L.bsum = det_align(L.base + M * sizeof(uint32_t));
+  L.p8 = det_align(L.bsum + (nblk + 1) * sizeof(unsigned long long));
+  L.p1 = det_align(L.p8 + cap * 2 * sizeof(float4));
+  L.tile_loss = det_align(L.p1 + cap * sizeof(float));
+  L.bytes = det_align(L.tile_loss + (size_t)n_tiles * sizeof(double));
+  return L;
+}
+}  // namespace
+
+size_t render_bwd_det_bytes(size_t M, int n_tiles, size_t capacity) {
+  return det_layout(M, n_tiles, capacity).bytes;
+}
+
+cudaError_t launch_render_bwd_det(const gs_batch& batch, const gs_cameras& cams, const gs_projected& proj,
+                                  size_t M, const uint32_t* vals, const uint32_t* ranges,
+                                  const uint32_t* n_instances, const float* bg, const float* image,
+                                  const float* T_final, const uint32_t* n_contrib, const float* v_image,
+                                  const float* target, float l1_weight, double* loss, float* v2d, void* det_ws,
+                                  size_t capacity, cudaStream_t st) {
+  if (M == 0) return cudaSuccess;
+  const DetLayout L = det_layout(M, batch.n_tiles, capacity);
+  char* w = static_cast<char*>(det_ws);
+  uint32_t* base = reinterpret_cast<uint32_t*>(w + L.base);
+  unsigned long long* bsum = reinterpret_cast<unsigned long long*>(w + L.bsum);
+  DetOut det;
+  det.base = base;
+  det.rect = reinterpret_cast<const ushort4*>(proj.rect);
+  det.p8 = reinterpret_cast<float4*>(w + L.p8);
+  det.p1 = reinterpret_cast<float*>(w + L.p1);
+  det.cap = capacity;
+  const bool fused_loss = loss != nullptr && v_image == nullptr;
+  det.tile_loss = fused_loss ? reinterpret_cast<double*>(w + L.tile_loss) : nullptr;
+  const int nblk = (int)((M + kDetTile - 1) / kDetTile);
+  det_scan_reduce_kernel<<<nblk, kDetThreads, 0, st>>>(proj.n_tiles, M, bsum);
+  det_scan_top_kernel<<<1, kDetThreads, 0, st>>>(bsum, nblk);
+  det_scan_down_kernel<<<nblk, kDetThreads, 0, st>>>(proj.n_tiles, M, bsum, base);
+  if (batch.n_tiles > 0) {
+    const Sizes sz{cams.n_cams, cams.wh};
+    const int rb = tuning().render_bwd_batch;
+    if (batch.tile == 32)
+      render_bwd_tile<32, true>(rb, batch, sz, proj.splat, vals, ranges, bg, image, T_final, n_contrib, v_image,
+                                target, l1_weight, loss, v2d, st, det);
+    else
+      render_bwd_tile<16, true>(rb, batch, sz, proj.splat, vals, ranges, bg, image, T_final, n_contrib, v_image,
+                                target, l1_weight, loss, v2d, st, det);
+  }
+  det_reduce_kernel<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(proj.n_tiles, base, bsum + nblk, n_instances,
+                                                                 det.p8, det.p1, capacity, M, v2d);
+  if (fused_loss && batch.n_tiles > 0) det_loss_kernel<<<1, kDetThreads, 0, st>>>(det.tile_loss, batch, loss);
   return cudaGetLastError();
 }
 

@@ -13,8 +13,9 @@ import torch
 from . import _lib
 from .core import (Batch, Cameras, Gaussians, Projected, TileLists, adam_c, gs_adam_update, gs_adam_update_groups,
                    gs_gather_view_pixels, gs_photo_loss, gs_project, photo_loss_workspace_bytes,
-                   gs_project_bwd, gs_raster_bwd, gs_render_fwd, gs_sort_tiles, gs_step_advance, gs_zero,
-                   new_status, pose_se3_update, render_bwd_workspace_bytes, track_reproj_fwd_bwd,
+                   gs_project_bwd, gs_raster_bwd, gs_raster_bwd_det, gs_render_fwd, gs_sort_tiles,
+                   gs_step_advance, gs_zero, new_status, pose_se3_update, render_bwd_det_workspace_bytes,
+                   render_bwd_workspace_bytes, track_reproj_fwd_bwd,
                    track_workspace_bytes)
 
 
@@ -29,10 +30,15 @@ class Renderer:
     instance buffers when the sort reported an overflow."""
 
     def __init__(self, n: int, cams: Cameras, batch: Batch, capacity: int = 0, bg=(0.0, 0.0, 0.0),
-                 device="cuda", dtype=torch.float32):
+                 device="cuda", dtype=torch.float32, deterministic: bool = False):
         # dtype float64: the FP64 instantiation of projection and compositing
-        # (the Gaussians passed to forward/backward must be float64 too)
+        # (the Gaussians passed to forward/backward must be float64 too).
+        # deterministic: the backward whose gradients and loss do not depend
+        # on the order in which tiles run (gs_raster_bwd_det; FP32 only)
+        if deterministic and dtype != torch.float32:
+            raise ValueError("the deterministic backward is FP32 only")
         self.n, self.cams, self.batch, self.dtype = n, cams, batch, dtype
+        self.deterministic = deterministic
         self.proj = Projected(n, batch.B, device, dtype)
         cap = capacity if capacity > 0 else max(1 << 16, 4 * n * batch.B)
         self.tl = TileLists(n, batch, cap, device)
@@ -41,9 +47,13 @@ class Renderer:
         self.T_final = torch.zeros(P, dtype=dtype, device=device)
         self.n_contrib = torch.zeros(P, dtype=torch.int32, device=device)
         self.bg = torch.tensor(bg, dtype=dtype, device=device)
-        self.ws_bwd = torch.empty(max(render_bwd_workspace_bytes(n, batch, dtype == torch.float64), 256),
-                                  dtype=torch.uint8, device=device)
+        self.ws_bwd = torch.empty(max(self._bwd_bytes(), 256), dtype=torch.uint8, device=device)
         self.status = new_status(device)
+
+    def _bwd_bytes(self) -> int:
+        if self.deterministic:
+            return render_bwd_det_workspace_bytes(self.n, self.batch, self.tl.capacity)
+        return render_bwd_workspace_bytes(self.n, self.batch, self.dtype == torch.float64)
 
     def _layout(self):
         # a batch laid out on the device: its offsets follow the device copy
@@ -71,8 +81,9 @@ class Renderer:
                  l1_weight: float = 1.0, loss=None, Rt: torch.Tensor = None, mark=_nomark):
         # gs_render_bwd is exactly these two calls; issuing them separately
         # lets a caller time each half
-        gs_raster_bwd(g, self.cams, self.batch, self.proj, self.tl, self.bg, self.image, self.T_final,
-                      self.n_contrib, v_image, target, l1_weight, loss, self.ws_bwd, Rt)
+        raster = gs_raster_bwd_det if self.deterministic else gs_raster_bwd
+        raster(g, self.cams, self.batch, self.proj, self.tl, self.bg, self.image, self.T_final,
+               self.n_contrib, v_image, target, l1_weight, loss, self.ws_bwd, Rt)
         mark("raster_bwd")
         gs_project_bwd(g, self.cams, self.batch, self.proj, dg, g_tangent, self.ws_bwd, Rt)
         mark("project_bwd")
@@ -101,6 +112,8 @@ class Renderer:
         need = self.n_instances()
         if need > self.tl.capacity:
             self.tl = TileLists(self.n, self.batch, int(need * headroom) + 1024, self.image.device)
+            if self.deterministic:   # its slots grow with the capacity
+                self.ws_bwd = torch.empty(self._bwd_bytes(), dtype=torch.uint8, device=self.image.device)
             self.status.zero_()
             return True
         self.status.zero_()
@@ -153,7 +166,7 @@ class JointStep:
                  obs_xy: torch.Tensor, view_obs_offset: torch.Tensor, targets: torch.Tensor,
                  target_px_offset: np.ndarray, views, hyper: Hyper = None, mode: str = "batched",
                  capacity: int = 0, device="cuda", tile: int = 16, merged_tracks: bool = False,
-                 dynamic_batch: bool = False):
+                 dynamic_batch: bool = False, deterministic: bool = False):
         # merged_tracks: the "merged tracks" ablation variant, X_k = mu of a
         # Gaussian (obs_point then indexes Gaussians; X is ignored): the track
         # term reads the Gaussian means and adds its gradient into theirs.
@@ -161,7 +174,10 @@ class JointStep:
         # scene and its layout is recomputed on the device at the start of
         # every step, so next_batch() takes views of any sizes without
         # dropping a captured graph (batches of uneven views).
+        # deterministic: the compositing backward whose gradients do not
+        # depend on the order in which tiles run (gs_raster_bwd_det).
         self.dynamic_batch = bool(dynamic_batch)
+        self.deterministic = bool(deterministic)
         self.h = hyper or Hyper()
         self.merged_tracks = bool(merged_tracks)
         self.tile = int(tile)
@@ -208,12 +224,14 @@ class JointStep:
         self.batch = self._new_batch(views)
         n = self.g.n
         if self.mode == "batched":
-            self.renderers = [Renderer(n, self.cams, self.batch, self._capacity, device=self.device)]
+            self.renderers = [Renderer(n, self.cams, self.batch, self._capacity, device=self.device,
+                                       deterministic=self.deterministic)]
             self.slot_batches = [self.batch]
         else:
             self.slot_batches = [self._new_batch([v]) for v in views]
             cap = self._capacity // max(len(views), 1)
-            self.renderers = [Renderer(n, self.cams, b, cap, device=self.device) for b in self.slot_batches]
+            self.renderers = [Renderer(n, self.cams, b, cap, device=self.device, deterministic=self.deterministic)
+                              for b in self.slot_batches]
         self.track_ws = torch.empty(max(track_workspace_bytes(self.batch), 256), dtype=torch.uint8,
                                     device=self.device)
         self.ssim_on = self.h.lambda_ssim > 0.0
@@ -372,6 +390,10 @@ class JointStep:
             # depth passes 4, scan 2, expand 1, one per tile pass, ranges 1;
             # render fwd 1; raster bwd 1; project bwd + finalize 2
             per_render += 1 + (1 + 1 + 1 + 4 + 2 + 1 + tile_passes + 1) + 1 + 1 + 2
+            if self.deterministic:
+                # slot bases (3-kernel scan), the fixed-order record sums,
+                # and the tiles' loss sum with the fused L1
+                per_render += 3 + 1 + (0 if self.ssim_on else 1)
             if self.ssim_on:
                 per_render += 3  # photometric loss: block list, forward, backward
         # target gather 1 per renderer, layout 1 per renderer (dynamic

@@ -23,12 +23,12 @@ def oracle_cam(wh, K, Rt, v, near=0.01, far=1e10):
     return oracle.camera_from_rt(int(wh[v][0]), int(wh[v][1]), f32(K[v]), f32(Rt[v]), near, far)
 
 
-def gpu_forward(scene, wh, K, Rt, views, capacity=0, bg=(0.0, 0.0, 0.0), tile=16):
+def gpu_forward(scene, wh, K, Rt, views, capacity=0, bg=(0.0, 0.0, 0.0), tile=16, deterministic=False):
     from paper_2603_04847_gb300 import Batch, Cameras, Gaussians, Renderer
     g = Gaussians.from_numpy(scene)
     cams = Cameras.from_numpy(wh, K, Rt)
     batch = Batch(cams, views, tile=tile)
-    r = Renderer(g.n, cams, batch, capacity, bg=bg)
+    r = Renderer(g.n, cams, batch, capacity, bg=bg, deterministic=deterministic)
     r.ensure_capacity(g)
     r.forward(g)
     torch.cuda.synchronize()

@@ -68,8 +68,10 @@ def _f64_backward(r, g, Rt64, v_image):
 def test_f64_kernels_match_the_oracle_to_rounding(thin, tile):
     w = synth.make_workload("tiny")
     sc = {k: f32(v) for k, v in w["scene"].items()}
-    if thin:   # every Gaussian a long thin streak (axes x e^2, e^-1.5, e^-1.5)
-        sc["log_scale"] = sc["log_scale"] + np.array([2.0, -1.5, -1.5])
+    if thin:   # every Gaussian a long thin streak (axes x e^2, e^-1.5, e^-1.5);
+        # rounded to float like every input of the oracle (oracle_scene), so
+        # that both sides see the same values
+        sc["log_scale"] = f32(sc["log_scale"] + np.array([2.0, -1.5, -1.5]))
     wh, K, Rt = w["wh"], f32(w["K"]), f32(w["Rt"])
     r, g, Rt64 = _f64_render(sc, wh, K, Rt, [0], tile)
     cam = oracle_cam(wh, K, Rt, 0)
