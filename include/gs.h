@@ -516,14 +516,38 @@ gs_status sfm_ba_assemble(const float* X, int32_t n_points,
  * the caller builds (offsets non-decreasing, [P+1]); entries outside
  * [0, n_obs) and cameras outside [0, V) are skipped.  No camera is singled
  * out: a caller holds camera 0 fixed by solving without its six rows and
- * columns.  Double precision; device arrays owned by the caller.
+ * columns.  lambda_dev (device double, may be NULL): when given, the
+ * damping is read from it on the device and lambda is ignored (the LM loop
+ * of sfm_ba_lm_accept).  Double precision; device arrays owned by the
+ * caller.
  */
 gs_status sfm_ba_schur(int32_t n_cams, int32_t n_points, int64_t n_obs,
                        const double* U, const double* Vp, const double* gc,
                        const double* gp, const double* Wo,
                        const int32_t* obs_cam, const int64_t* point_obs_offset,
-                       const int32_t* point_obs, double lambda, double* S,
-                       double* rhs, double* Vinv, gs_stream stream);
+                       const int32_t* point_obs, double lambda,
+                       const double* lambda_dev, double* S, double* rhs,
+                       double* Vinv, gs_stream stream);
+
+/*
+ * sfm_ba_lm_accept — the accept / reject decision of one LM iteration of
+ * Eq. 4, on the device (so that a whole iteration can be captured in a
+ * CUDA graph and replayed without reading anything back).  objective [2]
+ * (device double): the robust objective at the current parameters and at
+ * the trial ones (sfm_ba_apply_step, then sfm_ba_objective into
+ * objective + 1).  If the trial one is lower: Rt [V,12] <- Rt_trial,
+ * X [P,3] <- X_trial, objective[0] <- objective[1], *lambda (device double,
+ * the damping read by sfm_ba_schur through lambda_dev) /= 10 and
+ * *n_accepted += 1 (device int32, may be NULL); else *lambda *= 10.  With
+ * n_iter (device int32, may be NULL): history[*n_iter] <- objective[0]
+ * while *n_iter < history_len (history may be NULL), then *n_iter += 1.
+ */
+gs_status sfm_ba_lm_accept(int32_t n_cams, int32_t n_points, double* objective,
+                           double* lambda, float* Rt, float* X,
+                           const float* Rt_trial, const float* X_trial,
+                           int32_t* n_accepted, double* history,
+                           int32_t history_len, int32_t* n_iter,
+                           gs_stream stream);
 
 /*
  * sfm_ba_back_substitute — the points' step once the cameras' step
@@ -535,11 +559,14 @@ gs_status sfm_ba_schur(int32_t n_cams, int32_t n_points, int64_t n_obs,
  * sfm_ba_solve_cameras — solves the reduced camera system of sfm_ba_schur
  * with camera 0 held fixed: S' dc' = rhs' over cameras 1..V-1, S' being S
  * without camera 0's six rows and columns.  S is overwritten (its lower
- * triangle below camera 0 holds the Cholesky factor of S'); dc [V,6] is
- * written, row 0 zero.  One thread block factors the whole system
- * (O(n^3 / 6) flops for n = 6 (V - 1)): meant for up to a few hundred
- * cameras.  A pivot <= 0 leaves dc zero and ORs GS_FLAG_NOT_SPD into the
- * device word *status (may be NULL).
+ * triangle below camera 0 holds the Cholesky factor of S', and camera 0's
+ * block is scratch); dc [V,6] is written, row 0 zero.  The factorization
+ * is tiled (32 x 32 tiles): per tile column one launch factors the
+ * diagonal tile, one solves the tiles below it and one updates the
+ * trailing tiles, a block per tile, so the O(n^3 / 6) flops (n = 6 (V - 1))
+ * spread over the SMs; 3 ceil(n / 32) + 2 launches in all, none of which
+ * synchronises with the host.  A pivot <= 0 leaves dc zero and ORs
+ * GS_FLAG_NOT_SPD into the device word *status (may be NULL).
  */
 gs_status sfm_ba_solve_cameras(int32_t n_cams, double* S, const double* rhs,
                                double* dc, int32_t* status, gs_stream stream);
@@ -726,7 +753,7 @@ gs_status gs_mcmc_reset_moments(int32_t n_rows, const int32_t* src,
  * gs_mcmc_noise — the cited method's noise on the means (the MCMC
  * exploration term): mean += noise_lr * sigmoid(-100 (o - 0.005)) *
  * Sigma eta, Sigma = R diag(exp(log_scale))^2 R^T, eta [N,3] given
- * (standard normal draws).  Computed in double, stored as float.
+ * (standard normal draws).  Computed in float; quat 16-byte aligned.
  */
 gs_status gs_mcmc_noise(int32_t n, float* mean, const float* log_scale,
                         const float* quat, const float* opacity_logit,

@@ -17,6 +17,7 @@ GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_NONFINITE, GS_ERR_UNSUPP
 GS_FLAG_CAPACITY = 1
 GS_FLAG_NONFINITE = 2
 GS_FLAG_SORT_STALL = 4
+GS_FLAG_NOT_SPD = 8
 GS_MAX_BATCH = 64
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_ARG", 2: "GS_ERR_CAPACITY", 3: "GS_ERR_CUDA",
                 4: "GS_ERR_NONFINITE", 5: "GS_ERR_UNSUPPORTED"}
@@ -138,7 +139,9 @@ PROTOTYPES = {
     "gs_mcmc_reset_moments": (ctypes.c_int, [c_int32, c_void_p, c_int32, c_int32, c_void_p, c_int32, c_void_p]),
     "sfm_ba_schur": (ctypes.c_int, [c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_void_p, c_void_p, ctypes.c_double, c_void_p, c_void_p, c_void_p,
-                                    c_void_p]),
+                                    c_void_p, c_void_p]),
+    "sfm_ba_lm_accept": (ctypes.c_int, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                        c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "sfm_ba_objective": (ctypes.c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,
                                         c_float, c_void_p, c_void_p]),
     "sfm_ba_apply_step": (ctypes.c_int, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,

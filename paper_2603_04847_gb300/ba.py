@@ -15,8 +15,8 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from .core import (Cameras, gs_zero, sfm_ba_apply_step, sfm_ba_assemble, sfm_ba_back_substitute, sfm_ba_objective,
-                   sfm_ba_schur, sfm_ba_solve_cameras)
+from .core import (Cameras, gs_zero, sfm_ba_apply_step, sfm_ba_assemble, sfm_ba_back_substitute, sfm_ba_lm_accept,
+                   sfm_ba_objective, sfm_ba_schur, sfm_ba_solve_cameras)
 
 
 class BundleAdjuster:
@@ -99,6 +99,53 @@ class BundleAdjuster:
             self.step()
             hist.append(self.objective)
         return hist
+
+    # -- the iteration on the device -----------------------------------------
+    def _device_iteration(self):
+        """One LM iteration whose accept / reject runs on the device
+        (sfm_ba_lm_accept): no host synchronisation, capturable."""
+        for a in (self.U, self.Vp, self.gc, self.gp, self.obj[1:2]):
+            gs_zero(a)
+        sfm_ba_assemble(self.X, self.cams, self.obs_point, self.obs_cam, self.obs_xy, self.delta, self.U, self.Vp,
+                        self.gc, self.gp, self.Wo, None, Rt=self.Rt)
+        sfm_ba_schur(self.U, self.Vp, self.gc, self.gp, self.Wo, self.obs_cam, self.off, self.ids, self.lam_dev,
+                     self.S, self.rhs, self.Vinv)
+        sfm_ba_solve_cameras(self.S, self.rhs, self.dc, self.status)
+        sfm_ba_back_substitute(self.Vinv, self.Vp, self.gp, self.Wo, self.obs_cam, self.off, self.ids, self.dc,
+                               self.dp)
+        sfm_ba_apply_step(self.Rt, self.X, self.dc, self.dp, self.Rt_trial, self.X_trial)
+        sfm_ba_objective(self.X_trial, self.cams, self.obs_point, self.obs_cam, self.obs_xy, self.delta,
+                         self.obj[1:2], Rt=self.Rt_trial)
+        sfm_ba_lm_accept(self.obj, self.lam_dev, self.Rt, self.X, self.Rt_trial, self.X_trial, self.n_acc_dev,
+                         self.hist_dev, self.n_iter_dev)
+
+    def run_graph(self, iters: int, max_iters: int = 4096):
+        """iters LM iterations as replays of one CUDA graph of the device
+        iteration (captured on first use); reads the results back once.
+        Returns the objective after each iteration, like run()."""
+        dev = self.X.device
+        if getattr(self, "graph", None) is None:
+            self.lam_dev = torch.tensor([self.lam], dtype=torch.float64, device=dev)
+            self.n_acc_dev = torch.zeros(1, dtype=torch.int32, device=dev)
+            self.n_iter_dev = torch.zeros(1, dtype=torch.int32, device=dev)
+            self.hist_dev = torch.zeros(max_iters, dtype=torch.float64, device=dev)
+            # the trial buffers are fixed in the graph: the current
+            # parameters stay in self.Rt / self.X from here on
+            torch.cuda.synchronize()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph):
+                self._device_iteration()
+        self.n_iter_dev.zero_()
+        for _ in range(iters):
+            self.graph.replay()
+        hist = [self.objective] + self.hist_dev[:min(iters, self.hist_dev.numel())].cpu().tolist()
+        self.objective = hist[-1]
+        self.lam = float(self.lam_dev.item())
+        return hist
+
+    def accepted(self) -> int:
+        """Steps accepted by run_graph so far."""
+        return int(self.n_acc_dev.item()) if getattr(self, "n_acc_dev", None) is not None else 0
 
     def status_flags(self) -> int:
         return int(self.status.item())

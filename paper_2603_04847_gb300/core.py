@@ -424,14 +424,30 @@ def sfm_ba_assemble(X: torch.Tensor, cams: Cameras, obs_point: torch.Tensor, obs
                               _p(objective), _stream(stream)), "sfm_ba_assemble")
 
 
-def sfm_ba_schur(U, Vp, gc, gp, Wo, obs_cam, point_obs_offset, point_obs, lam: float, S, rhs, Vinv, stream=None):
+def sfm_ba_schur(U, Vp, gc, gp, Wo, obs_cam, point_obs_offset, point_obs, lam, S, rhs, Vinv, stream=None):
     """Points eliminated from the damped LM system of Eq. 4: S [6V,6V], rhs
-    [6V], Vinv [P,9] written (float64 device tensors)."""
+    [6V], Vinv [P,9] written (float64 device tensors).  lam: the damping, a
+    float or a device double tensor [1] read on the device."""
     lib = _lib.load()
     _need_cuda(U, Vp, gc, gp, Wo, obs_cam, point_obs_offset, point_obs, S, rhs, Vinv)
+    lam_dev = lam if isinstance(lam, torch.Tensor) else None
+    _need_cuda(lam_dev)
     check(lib.sfm_ba_schur(U.shape[0], Vp.shape[0], obs_cam.shape[0], _p(U), _p(Vp), _p(gc), _p(gp), _p(Wo),
-                           _p(obs_cam), _p(point_obs_offset), _p(point_obs), float(lam), _p(S), _p(rhs), _p(Vinv),
-                           _stream(stream)), "sfm_ba_schur")
+                           _p(obs_cam), _p(point_obs_offset), _p(point_obs), 0.0 if lam_dev is not None else float(lam),
+                           _p(lam_dev), _p(S), _p(rhs), _p(Vinv), _stream(stream)), "sfm_ba_schur")
+
+
+def sfm_ba_lm_accept(objective, lam, Rt, X, Rt_trial, X_trial, n_accepted=None, history=None, n_iter=None,
+                     stream=None):
+    """The LM accept / reject on the device (sfm_ba_lm_accept): objective
+    [2] (current, trial) and lam [1] device doubles; Rt, X take the trial
+    values when the trial objective is lower."""
+    lib = _lib.load()
+    _need_cuda(objective, lam, Rt, X, Rt_trial, X_trial, n_accepted, history, n_iter)
+    check(lib.sfm_ba_lm_accept(Rt.shape[0], X.shape[0], _p(objective), _p(lam), _p(Rt), _p(X), _p(Rt_trial),
+                               _p(X_trial), _p(n_accepted), _p(history),
+                               0 if history is None else history.numel(), _p(n_iter), _stream(stream)),
+          "sfm_ba_lm_accept")
 
 
 def sfm_ba_objective(X, cams: Cameras, obs_point, obs_cam, obs_xy, delta: float, objective, Rt=None, stream=None):

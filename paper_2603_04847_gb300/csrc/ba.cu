@@ -12,6 +12,8 @@
 // camera (view-CSR), so a warp whose valid lanes share one camera sums the
 // camera's 42 values with shuffles and adds them once; otherwise each lane
 // adds its own.  Double precision throughout: the sums feed a linear solve.
+#include <algorithm>
+
 #include "gs_internal.h"
 
 namespace gs {
@@ -235,10 +237,12 @@ __device__ inline bool block_empty(const double* A, int n) {
 }
 
 __global__ void __launch_bounds__(64) ba_camera_init_kernel(int V, const double* __restrict__ U,
-                                                            const double* __restrict__ gc, double lambda,
+                                                            const double* __restrict__ gc, double lambda_h,
+                                                            const double* __restrict__ lambda_d,
                                                             double* __restrict__ S, double* __restrict__ rhs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V) return;
+  const double lambda = lambda_d ? *lambda_d : lambda_h;
   const double* Ui = U + 36 * (size_t)i;
   const bool empty = block_empty(Ui, 36);
   const size_t n = 6 * (size_t)V;
@@ -276,10 +280,11 @@ __device__ inline void point_block(const double* __restrict__ Vp, const double* 
 __global__ void __launch_bounds__(128) ba_point_schur_kernel(
     int V, int P, int64_t M, const double* __restrict__ Vp, const double* __restrict__ gp,
     const double* __restrict__ Wo, const int32_t* __restrict__ obs_cam, const int64_t* __restrict__ off,
-    const int32_t* __restrict__ point_obs, double lambda, double* __restrict__ Vinv, double* __restrict__ S,
-    double* __restrict__ rhs) {
+    const int32_t* __restrict__ point_obs, double lambda_h, const double* __restrict__ lambda_d,
+    double* __restrict__ Vinv, double* __restrict__ S, double* __restrict__ rhs) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= P) return;
+  const double lambda = lambda_d ? *lambda_d : lambda_h;
   double Vi[9], g[3];
   point_block(Vp, gp, k, lambda, Vi, g);
   for (int a = 0; a < 9; ++a) Vinv[9 * (size_t)k + a] = Vi[a];
@@ -334,72 +339,179 @@ __global__ void __launch_bounds__(128) ba_back_substitute_kernel(
 }
 
 // The reduced camera system with camera 0 held fixed, S' dc' = rhs' (S' =
-// S without camera 0's six rows and columns), solved by an in-place
-// Cholesky factorization S' = L L^T (L over the lower triangle of S') and
-// two triangular solves, in one thread block.  A first version for up to a
-// few hundred cameras: O(n^3 / 6) flops for n = 6 (V - 1).  A pivot that is
-// not positive (S' not positive definite) leaves dc zero and sets a flag.
-__device__ inline double block_sum_d(double v, double* red) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  __syncthreads();  // red is reused by consecutive calls
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double t = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-  return t;  // in every thread
-}
+// S without camera 0's six rows and columns, n = 6 (V - 1) unknowns), by a
+// tiled right-looking Cholesky factorization S' = L L^T in place over the
+// lower triangle of S', then two triangular solves.  Tiles are kChT x kChT
+// (the last row and column of tiles ragged).  For each tile column k:
+//   diag   factors tile (k, k) in shared memory (one block);
+//   panel  L_ik = A_ik L_kk^-T for the tiles below it (one block per tile);
+//   update A_ij -= L_ik L_jk^T for k < j <= i (one block per tile),
+// so the O(n^3 / 6) flops of the updates are spread over the SMs.  A pivot
+// that is not positive (S' not positive definite) sets a marker in S[0]
+// (camera 0's block, not part of S' and free to use as scratch) that the
+// later kernels read: they then do nothing, and the solve writes dc = 0
+// and raises GS_FLAG_NOT_SPD.
+constexpr int kChT = 32;
 
-__global__ void __launch_bounds__(1024) ba_cholesky_solve_kernel(int V, double* __restrict__ S,
-                                                                 const double* __restrict__ rhs,
-                                                                 double* __restrict__ dc, int32_t* status) {
-  __shared__ double red[32];
+__device__ inline bool chol_failed(const double* S) { return *(volatile const double*)S != 0.0; }
+
+__global__ void ba_chol_init_kernel(double* S) { S[0] = 0.0; }
+
+__global__ void __launch_bounds__(256) ba_chol_diag_kernel(int n, size_t ld, double* __restrict__ S, int k) {
+  __shared__ double a[kChT][kChT + 1];
   __shared__ int bad;
-  const int n = 6 * (V - 1);
-  const size_t ld = 6 * (size_t)V;
+  if (chol_failed(S)) return;  // block-uniform
   double* A = S + 6 * ld + 6;
-  const double* b = rhs + 6;
-  double* x = dc + 6;
-  for (int a = threadIdx.x; a < 6; a += blockDim.x) dc[a] = 0.0;
+  const int r0 = k * kChT, m = min(kChT, n - r0);
+  for (int e = threadIdx.x; e < kChT * kChT; e += blockDim.x) {
+    const int r = e / kChT, c = e % kChT;
+    a[r][c] = (r < m && c <= r) ? A[(size_t)(r0 + r) * ld + r0 + c] : 0.0;
+  }
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
-  for (int j = 0; j < n; ++j) {
+  for (int c = 0; c < m; ++c) {
     if (threadIdx.x == 0) {
-      const double d = A[j * ld + j];
-      if (d > 0.0 && isfinite(d)) A[j * ld + j] = sqrt(d);
+      const double d = a[c][c];
+      if (d > 0.0 && isfinite(d)) a[c][c] = sqrt(d);
       else bad = 1;
     }
     __syncthreads();
     if (bad) break;  // block-uniform
-    const double djj = A[j * ld + j];
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * ld + j] /= djj;
+    const double dcc = a[c][c];
+    for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) a[r][c] /= dcc;
     __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
-      const double aij = A[i * ld + j];
-      for (int k = j + 1; k <= i; ++k) A[i * ld + k] -= aij * A[k * ld + j];
+    const int t = m - c - 1;  // trailing rows; lower triangle of t x t
+    for (int e = threadIdx.x; e < t * t; e += blockDim.x) {
+      const int r = c + 1 + e / t, q = c + 1 + e % t;
+      if (q <= r) a[r][q] -= a[r][c] * a[q][c];
     }
     __syncthreads();
   }
   if (bad) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = 0.0;
+    if (threadIdx.x == 0) S[0] = 1.0;
+    return;
+  }
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int r = e / m, c = e % m;
+    if (c <= r) A[(size_t)(r0 + r) * ld + r0 + c] = a[r][c];
+  }
+}
+
+// Tile (k + 1 + blockIdx.x, k): X L_kk^T = A_ik, one thread per row.
+__global__ void __launch_bounds__(kChT) ba_chol_panel_kernel(int n, size_t ld, double* __restrict__ S, int k) {
+  __shared__ double L[kChT][kChT + 1];
+  __shared__ double x[kChT][kChT + 1];
+  if (chol_failed(S)) return;
+  double* A = S + 6 * ld + 6;
+  const int c0 = k * kChT, m = min(kChT, n - c0);
+  const int r0 = (k + 1 + (int)blockIdx.x) * kChT, mi = min(kChT, n - r0);
+  for (int r = 0; r < m; ++r)
+    for (int c = threadIdx.x; c < m; c += blockDim.x) L[r][c] = c <= r ? A[(size_t)(c0 + r) * ld + c0 + c] : 0.0;
+  for (int r = 0; r < mi; ++r)
+    for (int c = threadIdx.x; c < m; c += blockDim.x) x[r][c] = A[(size_t)(r0 + r) * ld + c0 + c];
+  __syncthreads();
+  const int r = threadIdx.x;
+  if (r < mi) {
+    for (int c = 0; c < m; ++c) {
+      double v = x[r][c];
+      for (int q = 0; q < c; ++q) v -= x[r][q] * L[c][q];
+      x[r][c] = v / L[c][c];
+    }
+  }
+  __syncthreads();
+  for (int rr = 0; rr < mi; ++rr)
+    for (int c = threadIdx.x; c < m; c += blockDim.x) A[(size_t)(r0 + rr) * ld + c0 + c] = x[rr][c];
+}
+
+// Tile (i, j) = (k + 1 + blockIdx.y, k + 1 + blockIdx.x), j <= i:
+// A_ij -= L_ik L_jk^T.
+__global__ void __launch_bounds__(256) ba_chol_update_kernel(int n, size_t ld, double* __restrict__ S, int k) {
+  __shared__ double Li[kChT][kChT + 1];
+  __shared__ double Lj[kChT][kChT + 1];
+  if (blockIdx.x > blockIdx.y) return;  // upper triangle of tiles
+  if (chol_failed(S)) return;
+  double* A = S + 6 * ld + 6;
+  const int c0 = k * kChT, m = min(kChT, n - c0);
+  const int i0 = (k + 1 + (int)blockIdx.y) * kChT, mi = min(kChT, n - i0);
+  const int j0 = (k + 1 + (int)blockIdx.x) * kChT, mj = min(kChT, n - j0);
+  for (int e = threadIdx.x; e < kChT * kChT; e += blockDim.x) {
+    const int r = e / kChT, c = e % kChT;
+    Li[r][c] = (r < mi && c < m) ? A[(size_t)(i0 + r) * ld + c0 + c] : 0.0;
+    Lj[r][c] = (r < mj && c < m) ? A[(size_t)(j0 + r) * ld + c0 + c] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < mi * mj; e += blockDim.x) {
+    const int r = e / mj, c = e % mj;
+    if (i0 == j0 && c > r) continue;  // diagonal tile: lower triangle only
+    double v = 0.0;
+#pragma unroll 8
+    for (int q = 0; q < kChT; ++q) v += Li[r][q] * Lj[c][q];
+    A[(size_t)(i0 + r) * ld + j0 + c] -= v;
+  }
+}
+
+// L y = b, then L^T x = y, tile by tile in one block; dc = (0, x).  The
+// off-diagonal products are summed by all threads, the triangle of each
+// diagonal tile by one thread from shared memory.
+__global__ void __launch_bounds__(1024) ba_chol_solve_kernel(int V, double* __restrict__ S,
+                                                             const double* __restrict__ rhs,
+                                                             double* __restrict__ dc, int32_t* status) {
+  __shared__ double part[kChT][33];
+  __shared__ double Ld[kChT][kChT + 1];
+  const int n = 6 * (V - 1);
+  const size_t ld = 6 * (size_t)V;
+  const double* A = S + 6 * ld + 6;
+  const double* b = rhs + 6;
+  double* y = dc + 6;  // y, then x in place (written and read by this block only)
+  for (int a = threadIdx.x; a < 6; a += blockDim.x) dc[a] = 0.0;
+  if (chol_failed(S)) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = 0.0;
     if (threadIdx.x == 0 && status) atomicOr(status, GS_FLAG_NOT_SPD);
     return;
   }
-  // L y = b (y kept in x)
-  for (int i = 0; i < n; ++i) {
-    double part = 0.0;
-    for (int k = threadIdx.x; k < i; k += blockDim.x) part += A[i * ld + k] * x[k];
-    const double sum = block_sum_d(part, red);
-    if (threadIdx.x == 0) x[i] = (b[i] - sum) / A[i * ld + i];
-    __syncthreads();
-  }
-  // L^T x = y
-  for (int i = n - 1; i >= 0; --i) {
-    double part = 0.0;
-    for (int k = i + 1 + threadIdx.x; k < n; k += blockDim.x) part += A[k * ld + i] * x[k];
-    const double sum = block_sum_d(part, red);
-    if (threadIdx.x == 0) x[i] = (x[i] - sum) / A[i * ld + i];
-    __syncthreads();
+  const int T = (n + kChT - 1) / kChT;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;  // 32 warps
+  for (int pass = 0; pass < 2; ++pass) {  // 0: L y = b; 1: L^T x = y
+    for (int tt = 0; tt < T; ++tt) {
+      const int t = pass == 0 ? tt : T - 1 - tt;
+      const int r0 = t * kChT, m = min(kChT, n - r0);
+      for (int e = threadIdx.x; e < kChT * kChT; e += blockDim.x) {
+        const int r = e / kChT, c = e % kChT;
+        Ld[r][c] = (r < m && c <= r) ? A[(size_t)(r0 + r) * ld + r0 + c] : 0.0;
+      }
+      // part[r][warp]: this warp's share of the products with the other
+      // tiles' solved unknowns (q < r0 forward, q >= r0 + m backward)
+      for (int r = 0; r < m; ++r) {
+        double v = 0.0;
+        if (pass == 0) {
+          for (int q = threadIdx.x; q < r0; q += blockDim.x) v += A[(size_t)(r0 + r) * ld + q] * y[q];
+        } else {
+          for (int q = r0 + m + threadIdx.x; q < n; q += blockDim.x) v += A[(size_t)q * ld + r0 + r] * y[q];
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) part[r][warp] = v;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        if (pass == 0) {
+          for (int r = 0; r < m; ++r) {
+            double v = b[r0 + r];
+            for (int w = 0; w < 32; ++w) v -= part[r][w];
+            for (int q = 0; q < r; ++q) v -= Ld[r][q] * y[r0 + q];
+            y[r0 + r] = v / Ld[r][r];
+          }
+        } else {
+          for (int r = m - 1; r >= 0; --r) {
+            double v = y[r0 + r];
+            for (int w = 0; w < 32; ++w) v -= part[r][w];
+            for (int q = r + 1; q < m; ++q) v -= Ld[q][r] * y[r0 + q];
+            y[r0 + r] = v / Ld[r][r];
+          }
+        }
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -407,22 +519,77 @@ __global__ void __launch_bounds__(1024) ba_cholesky_solve_kernel(int V, double* 
 
 cudaError_t launch_ba_schur(int V, int P, int64_t M, const double* U, const double* Vp, const double* gc,
                             const double* gp, const double* Wo, const int32_t* obs_cam, const int64_t* point_obs_offset,
-                            const int32_t* point_obs, double lambda, double* S, double* rhs, double* Vinv,
+                            const int32_t* point_obs, double lambda, const double* lambda_dev, double* S,
+                            double* rhs, double* Vinv,
                             cudaStream_t st) {
   if (V == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(S, 0, sizeof(double) * 36 * (size_t)V * (size_t)V, st);
   if (e != cudaSuccess) return e;
-  ba_camera_init_kernel<<<(V + 63) / 64, 64, 0, st>>>(V, U, gc, lambda, S, rhs);
+  ba_camera_init_kernel<<<(V + 63) / 64, 64, 0, st>>>(V, U, gc, lambda, lambda_dev, S, rhs);
   if (P > 0)
     ba_point_schur_kernel<<<(P + 127) / 128, 128, 0, st>>>(V, P, M, Vp, gp, Wo, obs_cam, point_obs_offset, point_obs,
-                                                            lambda, Vinv, S, rhs);
+                                                            lambda, lambda_dev, Vinv, S, rhs);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ba_solve_cameras(int V, double* S, const double* rhs, double* dc, int32_t* status,
                                    cudaStream_t st) {
   if (V <= 0) return cudaSuccess;
-  ba_cholesky_solve_kernel<<<1, 1024, 0, st>>>(V, S, rhs, dc, status);
+  const int n = 6 * (V - 1);
+  const size_t ld = 6 * (size_t)V;
+  const int T = (n + kChT - 1) / kChT;
+  ba_chol_init_kernel<<<1, 1, 0, st>>>(S);
+  for (int k = 0; k < T; ++k) {
+    ba_chol_diag_kernel<<<1, 256, 0, st>>>(n, ld, S, k);
+    if (k + 1 < T) {
+      ba_chol_panel_kernel<<<T - k - 1, kChT, 0, st>>>(n, ld, S, k);
+      ba_chol_update_kernel<<<dim3(T - k - 1, T - k - 1), 256, 0, st>>>(n, ld, S, k);
+    }
+  }
+  ba_chol_solve_kernel<<<1, 1024, 0, st>>>(V, S, rhs, dc, status);
+  return cudaGetLastError();
+}
+
+namespace {
+// Accept or reject the trial parameters of one LM iteration (Marquardt):
+// both kernels read the objectives before the second one writes them.
+__global__ void ba_lm_copy_kernel(int V, int P, const double* __restrict__ obj, float* __restrict__ Rt,
+                                  float* __restrict__ X, const float* __restrict__ Rt_trial,
+                                  const float* __restrict__ X_trial) {
+  if (!(obj[1] < obj[0])) return;  // grid-uniform
+  const size_t nR = 12 * (size_t)V, n = nR + 3 * (size_t)P;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    if (e < nR) Rt[e] = Rt_trial[e];
+    else X[e - nR] = X_trial[e - nR];
+  }
+}
+
+__global__ void ba_lm_decide_kernel(double* obj, double* lambda, int32_t* n_accepted, double* history,
+                                    int32_t history_len, int32_t* n_iter) {
+  const bool accept = obj[1] < obj[0];
+  if (accept) {
+    obj[0] = obj[1];
+    *lambda /= 10.0;
+    if (n_accepted) ++*n_accepted;
+  } else {
+    *lambda *= 10.0;
+  }
+  if (n_iter) {
+    const int it = *n_iter;
+    if (history && it < history_len) history[it] = obj[0];
+    *n_iter = it + 1;
+  }
+}
+}  // namespace
+
+cudaError_t launch_ba_lm_accept(int V, int P, double* obj, double* lambda, float* Rt, float* X, const float* Rt_trial,
+                                const float* X_trial, int32_t* n_accepted, double* history, int32_t history_len,
+                                int32_t* n_iter, cudaStream_t st) {
+  const size_t n = 12 * (size_t)V + 3 * (size_t)P;
+  if (n > 0)
+    ba_lm_copy_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(V, P, obj, Rt, X, Rt_trial,
+                                                                                         X_trial);
+  ba_lm_decide_kernel<<<1, 1, 0, st>>>(obj, lambda, n_accepted, history, history_len, n_iter);
   return cudaGetLastError();
 }
 

@@ -637,16 +637,31 @@ gs_status sfm_ba_assemble(const float* X, int32_t n_points, const gs_cameras* ca
 
 gs_status sfm_ba_schur(int32_t n_cams, int32_t n_points, int64_t n_obs, const double* U, const double* Vp,
                        const double* gc, const double* gp, const double* Wo, const int32_t* obs_cam,
-                       const int64_t* point_obs_offset, const int32_t* point_obs, double lambda, double* S,
-                       double* rhs, double* Vinv, gs_stream stream) {
+                       const int64_t* point_obs_offset, const int32_t* point_obs, double lambda,
+                       const double* lambda_dev, double* S, double* rhs, double* Vinv, gs_stream stream) {
   if (n_cams < 0 || n_points < 0 || n_obs < 0) return fail(GS_ERR_ARG, "sfm_ba_schur: negative sizes");
   if (n_cams > 0 && (!U || !gc || !S || !rhs)) return fail(GS_ERR_ARG, "sfm_ba_schur: null camera arrays");
   if (n_points > 0 && (!Vp || !gp || !Vinv || !point_obs_offset || (n_obs > 0 && (!Wo || !obs_cam || !point_obs))))
     return fail(GS_ERR_ARG, "sfm_ba_schur: null point or observation arrays");
-  if (!std::isfinite(lambda) || lambda < 0.0) return fail(GS_ERR_ARG, "sfm_ba_schur: lambda must be >= 0");
+  if (!lambda_dev && (!std::isfinite(lambda) || lambda < 0.0))
+    return fail(GS_ERR_ARG, "sfm_ba_schur: lambda must be >= 0");
   cudaError_t e = launch_ba_schur(n_cams, n_points, n_obs, U, Vp, gc, gp, Wo, obs_cam, point_obs_offset, point_obs,
-                                  lambda, S, rhs, Vinv, (cudaStream_t)stream);
+                                  lambda, lambda_dev, S, rhs, Vinv, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "sfm_ba_schur");
+  return GS_OK;
+}
+
+gs_status sfm_ba_lm_accept(int32_t n_cams, int32_t n_points, double* objective, double* lambda, float* Rt, float* X,
+                           const float* Rt_trial, const float* X_trial, int32_t* n_accepted, double* history,
+                           int32_t history_len, int32_t* n_iter, gs_stream stream) {
+  if (n_cams < 0 || n_points < 0 || history_len < 0) return fail(GS_ERR_ARG, "sfm_ba_lm_accept: negative sizes");
+  if (!objective || !lambda) return fail(GS_ERR_ARG, "sfm_ba_lm_accept: null objective or lambda");
+  if ((n_cams > 0 && (!Rt || !Rt_trial)) || (n_points > 0 && (!X || !X_trial)))
+    return fail(GS_ERR_ARG, "sfm_ba_lm_accept: null parameter arrays");
+  if (history && !n_iter) return fail(GS_ERR_ARG, "sfm_ba_lm_accept: history needs n_iter");
+  cudaError_t e = launch_ba_lm_accept(n_cams, n_points, objective, lambda, Rt, X, Rt_trial, X_trial, n_accepted,
+                                      history, history_len, n_iter, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sfm_ba_lm_accept");
   return GS_OK;
 }
 
@@ -762,6 +777,7 @@ gs_status gs_mcmc_noise(int32_t n, float* mean, const float* log_scale, const fl
   if (n > 0 && (!mean || !log_scale || !quat || !opacity_logit || !eta))
     return fail(GS_ERR_ARG, "gs_mcmc_noise: null argument");
   if (!std::isfinite(noise_lr)) return fail(GS_ERR_ARG, "gs_mcmc_noise: noise_lr");
+  if (n > 0 && !aligned(quat, 16)) return fail(GS_ERR_ARG, "gs_mcmc_noise: quat must be 16-byte aligned");
   cudaError_t e = launch_mcmc_noise(n, mean, log_scale, quat, opacity_logit, eta, noise_lr, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "gs_mcmc_noise");
   return GS_OK;

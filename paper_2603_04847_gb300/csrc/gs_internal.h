@@ -91,8 +91,11 @@ cudaError_t launch_ba_assemble(const float* X, int n_points, const gs_cameras& c
                                cudaStream_t st);
 cudaError_t launch_ba_schur(int V, int P, int64_t M, const double* U, const double* Vp, const double* gc,
                             const double* gp, const double* Wo, const int32_t* obs_cam, const int64_t* point_obs_offset,
-                            const int32_t* point_obs, double lambda, double* S, double* rhs, double* Vinv,
-                            cudaStream_t st);
+                            const int32_t* point_obs, double lambda, const double* lambda_dev, double* S,
+                            double* rhs, double* Vinv, cudaStream_t st);
+cudaError_t launch_ba_lm_accept(int V, int P, double* obj, double* lambda, float* Rt, float* X, const float* Rt_trial,
+                                const float* X_trial, int32_t* n_accepted, double* history, int32_t history_len,
+                                int32_t* n_iter, cudaStream_t st);
 cudaError_t launch_ba_apply(int V, int P, const float* Rt, const float* X, const double* dc, const double* dp,
                             float* Rt_out, float* X_out, cudaStream_t st);
 cudaError_t launch_ba_solve_cameras(int V, double* S, const double* rhs, double* dc, int32_t* status,

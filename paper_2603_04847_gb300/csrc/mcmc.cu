@@ -309,36 +309,38 @@ __global__ void __launch_bounds__(kThr) mcmc_reset_moments_kernel(int n_src, con
       }
 }
 
+// FP32 throughout (the means are float; the FP64 pipe of this part is a
+// small fraction of the FP32 rate, and the noise is a perturbation whose
+// float rounding, ~1e-7 relative, is far below its own size).
 __global__ void __launch_bounds__(kThr) mcmc_noise_kernel(int n, float* __restrict__ mean,
                                                           const float* __restrict__ log_scale,
                                                           const float* __restrict__ quat,
                                                           const float* __restrict__ logit,
-                                                          const float* __restrict__ eta, double lr) {
+                                                          const float* __restrict__ eta, float lr) {
   const int i = blockIdx.x * kThr + threadIdx.x;
   if (i >= n) return;
-  const double o = opacity_of(logit[i]);
-  const double gate = 1.0 / (1.0 + exp(100.0 * (o - kDead)));
-  double q[4];
-  double qq = 0.0;
-  for (int a = 0; a < 4; ++a) {
-    q[a] = quat[4 * (size_t)i + a];
-    qq += q[a] * q[a];
-  }
-  const double iq = 1.0 / sqrt(qq);
-  const double w = q[0] * iq, x = q[1] * iq, y = q[2] * iq, z = q[3] * iq;
-  const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
-                       2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
-                       2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
-  double s2[3], e[3], Rte[3];
+  const float o = 1.f / (1.f + expf(-logit[i]));
+  const float gate = 1.f / (1.f + expf(100.f * (o - (float)kDead)));
+  const float4 q = reinterpret_cast<const float4*>(quat)[i];
+  const float iq = 1.f / sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+  const float w = q.x * iq, x = q.y * iq, y = q.z * iq, z = q.w * iq;
+  const float R[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
+                      2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
+                      2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
+  float s2[3], e[3], Rte[3];
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double s = exp((double)log_scale[3 * (size_t)i + a]);
-    s2[a] = s * s;
+    const float sc = expf(log_scale[3 * (size_t)i + a]);
+    s2[a] = sc * sc;
     e[a] = eta[3 * (size_t)i + a];
   }
+#pragma unroll
   for (int a = 0; a < 3; ++a) Rte[a] = R[a] * e[0] + R[3 + a] * e[1] + R[6 + a] * e[2];   // R^T eta
+  const float k = lr * gate;
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double v = R[3 * a] * s2[0] * Rte[0] + R[3 * a + 1] * s2[1] * Rte[1] + R[3 * a + 2] * s2[2] * Rte[2];
-    mean[3 * (size_t)i + a] = (float)((double)mean[3 * (size_t)i + a] + lr * gate * v);
+    const float v = R[3 * a] * s2[0] * Rte[0] + R[3 * a + 1] * s2[1] * Rte[1] + R[3 * a + 2] * s2[2] * Rte[2];
+    mean[3 * (size_t)i + a] += k * v;
   }
 }
 
@@ -399,7 +401,7 @@ cudaError_t launch_mcmc_reset_moments(int n_rows, const int32_t* src, int n_src,
 cudaError_t launch_mcmc_noise(int n, float* mean, const float* log_scale, const float* quat, const float* logit,
                               const float* eta, float lr, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  mcmc_noise_kernel<<<(n + kThr - 1) / kThr, kThr, 0, st>>>(n, mean, log_scale, quat, logit, eta, (double)lr);
+  mcmc_noise_kernel<<<(n + kThr - 1) / kThr, kThr, 0, st>>>(n, mean, log_scale, quat, logit, eta, lr);
   return cudaGetLastError();
 }
 

@@ -235,3 +235,68 @@ def test_gpu_lm_converges_at_the_benchmark_size():
     assert hist[-1] <= float(truth.item()), (hist[0], hist[-1], float(truth.item()))
     np.testing.assert_array_equal(adj.Rt.cpu().numpy()[0], np.float32(Rt0[0]))
     assert adj.status_flags() == 0
+    # the same iterations with the accept / reject on the device, replayed
+    # from one CUDA graph: the same arithmetic, so the same objectives
+    g = BundleAdjuster(Cameras.from_numpy(wh, K, Rt0), dev(X0, torch.float32), op, oc, xy, delta=1.0, lam=1e-4)
+    hg = g.run_graph(20)
+    assert hg == hist
+    np.testing.assert_array_equal(g.X.cpu().numpy(), adj.X.cpu().numpy())
+    np.testing.assert_array_equal(g.Rt.cpu().numpy(), adj.Rt.cpu().numpy())
+    assert g.status_flags() == 0
+
+
+def test_gpu_lm_device_loop_matches_the_host_loop_and_recovers_a_noiseless_problem():
+    X0, Rt0, K, op, oc, xy = _perturbed(4, 5, 4, 20)
+    h = _adjuster(X0, Rt0, K, op, oc, xy).run(30)
+    adj = _adjuster(X0, Rt0, K, op, oc, xy)
+    g = adj.run_graph(10)
+    g += adj.run_graph(20)[1:]      # replays continue from the device state
+    assert g == h
+    assert g[-1] < 1e-6 * g[0]
+    assert adj.accepted() == sum(b < a for a, b in zip(h[:-1], h[1:]))
+
+
+def test_tiled_camera_solve_not_positive_definite_flags_and_zeroes():
+    """A reduced camera system that is not positive definite (a negative
+    diagonal entry in the third 32 x 32 tile): dc stays zero, the flag is
+    raised, and no later tile runs on the failed factor."""
+    from paper_2603_04847_gb300.core import sfm_ba_solve_cameras
+    V = 20                                   # n = 114 unknowns: 4 tiles, the last ragged
+    n = 6 * V
+    rng = np.random.default_rng(3)
+    B = rng.normal(size=(n, n))
+    S = B @ B.T + n * np.eye(n)
+    S[6 + 70, 6 + 70] = -1.0
+    St = torch.as_tensor(S, dtype=torch.float64, device="cuda").contiguous()
+    dc = torch.full((V, 6), np.nan, dtype=torch.float64, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sfm_ba_solve_cameras(St, torch.ones(n, dtype=torch.float64, device="cuda"), dc, status)
+    torch.cuda.synchronize()
+    from paper_2603_04847_gb300 import _lib
+    assert int(status.item()) & _lib.GS_FLAG_NOT_SPD
+    assert not dc.cpu().numpy().any()
+
+
+@pytest.mark.parametrize("V", [2, 7, 12, 50, 120])
+def test_tiled_camera_solve_equals_a_dense_solve(V):
+    """The tiled factorization and the two tiled triangular solves against
+    numpy's dense solve of S' x = rhs', for systems of 1 to 22 tiles (ragged
+    last tile at 6 (V - 1) = 6, 36, 66, 294, 714 unknowns)."""
+    from paper_2603_04847_gb300.core import sfm_ba_solve_cameras
+    n = 6 * V
+    rng = np.random.default_rng(V)
+    B = rng.normal(size=(n, n))
+    S = B @ B.T / n + np.diag(rng.uniform(0.5, 2.0, n))
+    rhs = rng.normal(size=n)
+    St = torch.as_tensor(S, dtype=torch.float64, device="cuda").contiguous()
+    dc = torch.full((V, 6), np.nan, dtype=torch.float64, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sfm_ba_solve_cameras(St, torch.as_tensor(rhs, device="cuda"), dc, status)
+    torch.cuda.synchronize()
+    exp = np.linalg.solve(S[6:, 6:], rhs[6:])
+    got = dc.cpu().numpy().reshape(-1)
+    assert int(status.item()) == 0
+    assert not got[:6].any()
+    assert np.abs(got[6:] - exp).max() <= 1e-10 * np.abs(exp).max()
+    L = np.tril(St.cpu().numpy()[6:, 6:])
+    np.testing.assert_allclose(L, np.linalg.cholesky(S[6:, 6:]), rtol=0, atol=1e-12 * np.abs(L).max())
