@@ -564,11 +564,14 @@ def stage_times(js, reps, flush):
 NCU_SUMMARY = {"raster_bwd": "render_bwd_mid_8x1237x822_200k.md"}
 
 
-def ncu_traffic(stage, workload, js):
+def ncu_traffic(stage, workload, js, model_bytes=None):
     """dram__bytes_read.sum + dram__bytes_write.sum per launch of the stage's
-    kernel, from its committed ncu summary -- only while the kernel source,
-    the workload and the staging batch are those the capture was taken on
-    (else None: the counters no longer describe this kernel)."""
+    kernel, from its committed ncu summary -- only while the kernel source
+    and the staging batch are those the capture was taken on (else None:
+    the counters no longer describe this kernel).  A capture of a smaller
+    workload of the same kernel is scaled to this launch by the ratio of
+    the algorithmic bytes (model_bytes, this launch) to those of the
+    captured launch; the result says so."""
     import hashlib
     from paper_2603_04847_gb300.core import gs_get_tuning
     name = NCU_SUMMARY.get(stage)
@@ -581,11 +584,18 @@ def ncu_traffic(stage, workload, js):
             sha = hashlib.sha256(f.read()).hexdigest()
     except (OSError, KeyError, ValueError):
         return None
-    if sha != kv.get("source_sha256") or workload != kv.get("workload"):
+    if sha != kv.get("source_sha256"):
         return None
     if str(gs_get_tuning()["render_bwd_batch"]) != kv.get("render_bwd_batch") or str(js.tile) != kv.get("tile"):
         return None
-    return int(kv["traffic_bytes_per_launch"])
+    t = int(kv["traffic_bytes_per_launch"])
+    if workload == kv.get("workload"):
+        return t
+    if model_bytes is None or "algorithmic_bytes_per_launch" not in kv:
+        return None
+    return dict(bytes=int(t * model_bytes / int(kv["algorithmic_bytes_per_launch"])),
+                scaled_from="%s capture (%d bytes per launch, algorithmic %s), x algorithmic bytes ratio" % (
+                    kv.get("workload"), t, kv["algorithmic_bytes_per_launch"]))
 
 
 def algorithmic_model(js):
@@ -768,7 +778,32 @@ def run_ours(args):
         if k in model and t > 0:
             stages[k]["GBps"] = model[k] / (t * 1e-3) / 1e9
             stages[k]["hbm_frac"] = stages[k]["GBps"] / hbm_peak
-    dominant = max(("project", "sort", "render_fwd", "raster_bwd", "project_bwd"), key=lambda k: st_ms.get(k, 0))
+    # the dominant kernel: the longest single-kernel stage (the sort stage
+    # is a dozen kernels, none of them near the top of the launch list; its
+    # HBM fraction is in `stages`).  The raster_bwd stage also clears the
+    # screen-space records (a memset of B N 48 bytes; not in the
+    # deterministic form), timed here on the same bytes and taken off
+    if not js.deterministic:
+        r0 = js.renderers[0]
+        nb = js.batch.B * js.g.n * 48
+        z = r0.ws_bwd[:nb]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        mz = []
+        for _ in range(5):
+            flush.zero_()
+            ev[0].record()
+            z.zero_()
+            ev[1].record()
+            torch.cuda.synchronize()
+            mz.append(ev[0].elapsed_time(ev[1]))
+        st_ms["raster_bwd_memset"] = sum(mz) / len(mz)
+        st_ms["raster_bwd_kernel"] = max(st_ms["raster_bwd"] - st_ms["raster_bwd_memset"], 1e-6)
+    kern_ms = dict(st_ms)
+    if "raster_bwd_kernel" in st_ms:
+        kern_ms["raster_bwd"] = st_ms["raster_bwd_kernel"]
+        stages["raster_bwd"]["records_clear_ms"] = st_ms["raster_bwd_memset"]
+        stages["raster_bwd"]["kernel_ms"] = st_ms["raster_bwd_kernel"]
+    dominant = max(("project", "render_fwd", "raster_bwd", "project_bwd"), key=lambda k: kern_ms.get(k, 0))
     # the compositing kernels are bound by FP32/SFU issue, not HBM: report
     # their pair throughput against the FP32 lane peak
     sms = torch.cuda.get_device_properties(local).multi_processor_count
@@ -781,20 +816,31 @@ def run_ours(args):
     # alpha gradient 15, colour-behind update 6, conic/mean/opacity
     # gradients 30).
     ALU = {"render_fwd": (10.0, 9.0), "raster_bwd": (10.0, 60.0)}
-    traffic = ncu_traffic(dominant, args.workload, js)
+    traffic = ncu_traffic(dominant, args.workload, js, model.get(dominant))
+    traffic_note = None
+    if isinstance(traffic, dict):
+        traffic, traffic_note = traffic["bytes"], traffic["scaled_from"]
+    kname = {"raster_bwd": "render_bwd_kernel", "render_fwd": "render_fwd_kernel", "project": "project_fwd_kernel",
+             "project_bwd": "project_bwd_kernel"}[dominant]
     if dominant in ALU:
         per_pos, per_add = ALU[dominant]
         fl = counts["pairs_bwd"] * per_pos + counts["added"] * per_add
-        ach = fl / (st_ms[dominant] * 1e-3) / 1e12
-        roof = dict(kernel=dominant, bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
-                    traffic=traffic, peak_source="derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (
+        ach = fl / (kern_ms[dominant] * 1e-3) / 1e12
+        roof = dict(kernel=kname, stage=dominant, bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s",
+                    frac=ach / fp32_peak, traffic=traffic, launch_ms=kern_ms[dominant],
+                    peak_source="derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (
                         sms, peaks.get("sm_max_mhz", 2070.0)),
                     work="%d examined positions x %.0f + %d composited splats x %.0f flop" % (
                         counts["pairs_bwd"], per_pos, counts["added"], per_add))
     else:
-        ach = model[dominant] / (st_ms[dominant] * 1e-3) / 1e9
-        roof = dict(kernel=dominant, bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak,
-                    traffic=traffic, peak_source=peak_src)
+        ach = model[dominant] / (kern_ms[dominant] * 1e-3) / 1e9
+        roof = dict(kernel=kname, stage=dominant, bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s",
+                    frac=ach / hbm_peak, traffic=traffic, launch_ms=kern_ms[dominant], peak_source=peak_src)
+    if traffic_note:
+        roof["traffic_note"] = traffic_note
+    if dominant == "raster_bwd" and "raster_bwd_memset" in st_ms:
+        roof["launch_note"] = "raster_bwd stage %.3f ms minus the clearing of its records (%.3f ms, same bytes)" % (
+            st_ms["raster_bwd"], st_ms["raster_bwd_memset"])
     step_bytes = sum(model.values())
     step_ms_now = sum(v for k, v in st_ms.items())
     hbm_step = dict(algorithmic_bytes=step_bytes, GBps=step_bytes / (ms * 1e-3) / 1e9,

@@ -85,6 +85,7 @@ enum {
 
 #define GS_ABI_VERSION 4
 #define GS_MAX_BATCH 64   /* views per call */
+#define GS_MAX_BA_CAMERAS 4096 /* cameras of one sfm_ba_solve_cameras call */
 
 typedef struct CUstream_st* gs_stream; /* = cudaStream_t */
 
@@ -565,7 +566,9 @@ gs_status sfm_ba_lm_accept(int32_t n_cams, int32_t n_points, double* objective,
  * diagonal tile, one solves the tiles below it and one updates the
  * trailing tiles, a block per tile, so the O(n^3 / 6) flops (n = 6 (V - 1))
  * spread over the SMs; 3 ceil(n / 32) + 2 launches in all, none of which
- * synchronises with the host.  A pivot <= 0 leaves dc zero and ORs
+ * synchronises with the host (the triangular solves keep the n unknowns in
+ * one block's shared memory: up to GS_MAX_BA_CAMERAS cameras, else
+ * GS_ERR_UNSUPPORTED).  A pivot <= 0 leaves dc zero and ORs
  * GS_FLAG_NOT_SPD into the device word *status (may be NULL).
  */
 gs_status sfm_ba_solve_cameras(int32_t n_cams, double* S, const double* rhs,

@@ -397,30 +397,27 @@ __global__ void __launch_bounds__(256) ba_chol_diag_kernel(int n, size_t ld, dou
   }
 }
 
-// Tile (k + 1 + blockIdx.x, k): X L_kk^T = A_ik, one thread per row.
-__global__ void __launch_bounds__(kChT) ba_chol_panel_kernel(int n, size_t ld, double* __restrict__ S, int k) {
+// Tile (k + 1 + blockIdx.x, k): X L_kk^T = A_ik, column by column (column c
+// of X is final once divided by L_cc; its products then leave the later
+// columns), a thread per element.
+__global__ void __launch_bounds__(kChT * kChT) ba_chol_panel_kernel(int n, size_t ld, double* __restrict__ S, int k) {
   __shared__ double L[kChT][kChT + 1];
   __shared__ double x[kChT][kChT + 1];
   if (chol_failed(S)) return;
   double* A = S + 6 * ld + 6;
   const int c0 = k * kChT, m = min(kChT, n - c0);
   const int r0 = (k + 1 + (int)blockIdx.x) * kChT, mi = min(kChT, n - r0);
-  for (int r = 0; r < m; ++r)
-    for (int c = threadIdx.x; c < m; c += blockDim.x) L[r][c] = c <= r ? A[(size_t)(c0 + r) * ld + c0 + c] : 0.0;
-  for (int r = 0; r < mi; ++r)
-    for (int c = threadIdx.x; c < m; c += blockDim.x) x[r][c] = A[(size_t)(r0 + r) * ld + c0 + c];
+  const int r = threadIdx.x / kChT, q = threadIdx.x % kChT;
+  L[r][q] = (r < m && q <= r) ? A[(size_t)(c0 + r) * ld + c0 + q] : 0.0;
+  x[r][q] = (r < mi && q < m) ? A[(size_t)(r0 + r) * ld + c0 + q] : 0.0;
   __syncthreads();
-  const int r = threadIdx.x;
-  if (r < mi) {
-    for (int c = 0; c < m; ++c) {
-      double v = x[r][c];
-      for (int q = 0; q < c; ++q) v -= x[r][q] * L[c][q];
-      x[r][c] = v / L[c][c];
-    }
+  for (int c = 0; c < m; ++c) {
+    if (q == c) x[r][c] /= L[c][c];
+    __syncthreads();
+    if (q > c && q < m) x[r][q] -= x[r][c] * L[q][c];
+    __syncthreads();
   }
-  __syncthreads();
-  for (int rr = 0; rr < mi; ++rr)
-    for (int c = threadIdx.x; c < m; c += blockDim.x) A[(size_t)(r0 + rr) * ld + c0 + c] = x[rr][c];
+  if (r < mi && q < m) A[(size_t)(r0 + r) * ld + c0 + q] = x[r][q];
 }
 
 // Tile (i, j) = (k + 1 + blockIdx.y, k + 1 + blockIdx.x), j <= i:
@@ -458,14 +455,14 @@ __global__ void __launch_bounds__(1024) ba_chol_solve_kernel(int V, double* __re
                                                              double* __restrict__ dc, int32_t* status) {
   __shared__ double part[kChT][33];
   __shared__ double Ld[kChT][kChT + 1];
+  extern __shared__ double y[];  // [n]: y, then x in place
   const int n = 6 * (V - 1);
   const size_t ld = 6 * (size_t)V;
   const double* A = S + 6 * ld + 6;
   const double* b = rhs + 6;
-  double* y = dc + 6;  // y, then x in place (written and read by this block only)
   for (int a = threadIdx.x; a < 6; a += blockDim.x) dc[a] = 0.0;
   if (chol_failed(S)) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dc[6 + i] = 0.0;
     if (threadIdx.x == 0 && status) atomicOr(status, GS_FLAG_NOT_SPD);
     return;
   }
@@ -513,6 +510,7 @@ __global__ void __launch_bounds__(1024) ba_chol_solve_kernel(int V, double* __re
       __syncthreads();
     }
   }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dc[6 + i] = y[i];
 }
 
 }  // namespace
@@ -542,11 +540,17 @@ cudaError_t launch_ba_solve_cameras(int V, double* S, const double* rhs, double*
   for (int k = 0; k < T; ++k) {
     ba_chol_diag_kernel<<<1, 256, 0, st>>>(n, ld, S, k);
     if (k + 1 < T) {
-      ba_chol_panel_kernel<<<T - k - 1, kChT, 0, st>>>(n, ld, S, k);
+      ba_chol_panel_kernel<<<T - k - 1, kChT * kChT, 0, st>>>(n, ld, S, k);
       ba_chol_update_kernel<<<dim3(T - k - 1, T - k - 1), 256, 0, st>>>(n, ld, S, k);
     }
   }
-  ba_chol_solve_kernel<<<1, 1024, 0, st>>>(V, S, rhs, dc, status);
+  const size_t ysm = (size_t)n * sizeof(double);
+  if (ysm > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(ba_chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)ysm);
+    if (e != cudaSuccess) return e;
+  }
+  ba_chol_solve_kernel<<<1, 1024, ysm, st>>>(V, S, rhs, dc, status);
   return cudaGetLastError();
 }
 

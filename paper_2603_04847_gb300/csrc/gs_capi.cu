@@ -698,6 +698,8 @@ gs_status sfm_ba_solve_cameras(int32_t n_cams, double* S, const double* rhs, dou
                                gs_stream stream) {
   if (n_cams < 0) return fail(GS_ERR_ARG, "sfm_ba_solve_cameras: negative n_cams");
   if (n_cams > 0 && (!S || !rhs || !dc)) return fail(GS_ERR_ARG, "sfm_ba_solve_cameras: null argument");
+  if (n_cams > GS_MAX_BA_CAMERAS)
+    return fail(GS_ERR_UNSUPPORTED, "sfm_ba_solve_cameras: more than %d cameras", GS_MAX_BA_CAMERAS);
   cudaError_t e = launch_ba_solve_cameras(n_cams, S, rhs, dc, status, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "sfm_ba_solve_cameras");
   return GS_OK;

@@ -24,6 +24,8 @@
 // always lands on a live Gaussian: its target is below cdf[n-1] itself, and
 // a search that ends on a dead one (possible only where the two scan levels
 // round differently) moves on to the nearest live one.
+#include <algorithm>
+
 #include "gs_internal.h"
 
 namespace gs {
@@ -43,6 +45,8 @@ struct McmcWs {
   double* bsum;    // [nb] per block, then exclusive over blocks
   int32_t* bcnt;   // [nb]
   double* total;   // [1]
+  int32_t* list;   // [n] the distinct drawn sources, in no particular order
+  uint32_t* list_n;  // [1]
 };
 
 inline size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -58,6 +62,8 @@ McmcWs mcmc_layout(void* base, int n, size_t* bytes) {
   w.bsum = (double*)(p + o); o += al(8 * (size_t)nb);
   w.bcnt = (int32_t*)(p + o); o += al(4 * (size_t)nb);
   w.total = (double*)(p + o); o += al(8);
+  w.list = (int32_t*)(p + o); o += al(4 * (size_t)n);
+  w.list_n = (uint32_t*)(p + o); o += al(4);
   if (bytes) *bytes = o;
   return w;
 }
@@ -158,10 +164,12 @@ __global__ void __launch_bounds__(kThr) mcmc_blocks_kernel(int nb, double* __res
 __global__ void __launch_bounds__(kThr) mcmc_apply_kernel(int n, const float* __restrict__ logit,
                                                           const double* __restrict__ bsum,
                                                           const int32_t* __restrict__ bcnt, double* __restrict__ cdf,
-                                                          int32_t* __restrict__ rank, int32_t* __restrict__ count) {
+                                                          int32_t* __restrict__ rank, int32_t* __restrict__ count,
+                                                          uint32_t* __restrict__ list_n) {
   __shared__ double s_d[kThr / 32];
   __shared__ int s_i[kThr / 32];
   const int i = blockIdx.x * kThr + threadIdx.x;
+  if (i == 0) *list_n = 0u;
   double v = 0.0;
   int c = 0;
   if (i < n) {
@@ -205,14 +213,15 @@ __device__ inline int draw_live(int n, double u, const double* __restrict__ cdf,
 __global__ void __launch_bounds__(kThr) mcmc_draw_kernel(int n, const int32_t* __restrict__ rank,
                                                          const double* __restrict__ cdf, const double* __restrict__ u,
                                                          int n_u, int32_t* __restrict__ src,
-                                                         int32_t* __restrict__ count) {
+                                                         int32_t* __restrict__ count, int32_t* __restrict__ list,
+                                                         uint32_t* __restrict__ list_n) {
   const int i = blockIdx.x * kThr + threadIdx.x;
   if (i >= n) return;
   const int r = rank[i];
   int s = -1;
   if (r >= 0 && r < n_u) {
     s = draw_live(n, u[r], cdf, rank);
-    if (s >= 0) atomicAdd(&count[s], 1);
+    if (s >= 0 && atomicAdd(&count[s], 1) == 0) list[atomicAdd(list_n, 1u)] = s;
   }
   src[i] = s;
 }
@@ -221,19 +230,25 @@ __global__ void __launch_bounds__(kThr) mcmc_draw_kernel(int n, const int32_t* _
 __global__ void __launch_bounds__(kThr) mcmc_grow_draw_kernel(int n, int n_add, const int32_t* __restrict__ rank,
                                                               const double* __restrict__ cdf,
                                                               const double* __restrict__ u, int32_t* __restrict__ src,
-                                                              int32_t* __restrict__ count) {
+                                                              int32_t* __restrict__ count, int32_t* __restrict__ list,
+                                                              uint32_t* __restrict__ list_n) {
   const int k = blockIdx.x * kThr + threadIdx.x;
   if (k >= n_add) return;
   const int s = draw_live(n, u[k], cdf, rank);
-  if (s >= 0) atomicAdd(&count[s], 1);
+  if (s >= 0 && atomicAdd(&count[s], 1) == 0) list[atomicAdd(list_n, 1u)] = s;
   src[k] = s;
 }
 
-__global__ void __launch_bounds__(kThr) mcmc_reset_kernel(int n, float* __restrict__ logit,
-                                                          float* __restrict__ log_scale,
+// Over the list of distinct drawn sources (dense warps: the FP64 reset runs
+// only where it is needed; each source is reset once, whatever the order of
+// the list).
+__global__ void __launch_bounds__(kThr) mcmc_reset_kernel(const int32_t* __restrict__ list,
+                                                          const uint32_t* __restrict__ list_n,
+                                                          float* __restrict__ logit, float* __restrict__ log_scale,
                                                           const int32_t* __restrict__ count) {
-  const int j = blockIdx.x * kThr + threadIdx.x;
-  if (j >= n || count[j] == 0) return;
+  const uint32_t k = blockIdx.x * kThr + threadIdx.x;
+  if (k >= *list_n) return;
+  const int j = list[k];
   const int N = count[j] + 1;
   const double o = opacity_of(logit[j]);
   const double oN = 1.0 - pow(1.0 - o, 1.0 / N);
@@ -296,17 +311,20 @@ struct MomentGroups {
 
 __global__ void __launch_bounds__(kThr) mcmc_reset_moments_kernel(int n_src, const int32_t* __restrict__ src,
                                                                   int row0, MomentGroups G) {
-  const int k = blockIdx.x * kThr + threadIdx.x;
+  // a warp per (k, row): the new row row0 + k, then the source src[k]
+  const int item = (int)((blockIdx.x * (size_t)kThr + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  const int k = item >> 1;
   if (k >= n_src) return;
   const int s = src[k];
   if (s < 0) return;
-  const size_t rows[2] = {(size_t)row0 + k, (size_t)s};
-  for (int g = 0; g < G.n; ++g)
-    for (int r = 0; r < 2; ++r)
-      for (int a = 0; a < G.width[g]; ++a) {
-        G.m[g][rows[r] * G.width[g] + a] = 0.f;
-        G.v[g][rows[r] * G.width[g] + a] = 0.f;
-      }
+  const size_t row = (item & 1) ? (size_t)s : (size_t)row0 + k;
+  for (int g = 0; g < G.n; ++g) {
+    const size_t w = (size_t)G.width[g];
+    for (int a = lane; a < G.width[g]; a += 32) {
+      G.m[g][row * w + a] = 0.f;
+      G.v[g][row * w + a] = 0.f;
+    }
+  }
 }
 
 // FP32 throughout (the means are float; the FP64 pipe of this part is a
@@ -361,9 +379,11 @@ cudaError_t launch_mcmc_relocate(int n, int sh_degree, float* mean, float* log_s
   const int K3 = 3 * (sh_degree + 1) * (sh_degree + 1);
   mcmc_reduce_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt);
   mcmc_blocks_kernel<<<1, kThr, 0, st>>>(nb, w.bsum, w.bcnt, w.total, n_dead);
-  mcmc_apply_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt, w.cdf, w.rank, w.count);
-  mcmc_draw_kernel<<<nb, kThr, 0, st>>>(n, w.rank, w.cdf, u, n_u, src, w.count);
-  mcmc_reset_kernel<<<nb, kThr, 0, st>>>(n, logit, log_scale, w.count);
+  mcmc_apply_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt, w.cdf, w.rank, w.count, w.list_n);
+  mcmc_draw_kernel<<<nb, kThr, 0, st>>>(n, w.rank, w.cdf, u, n_u, src, w.count, w.list, w.list_n);
+  const int n_sources = std::min(n, std::max(n_u, 0));  // bound on the distinct sources
+  if (n_sources > 0)
+    mcmc_reset_kernel<<<(n_sources + kThr - 1) / kThr, kThr, 0, st>>>(w.list, w.list_n, logit, log_scale, w.count);
   mcmc_copy_kernel<<<nb, kThr, 0, st>>>(n, K3, src, mean, log_scale, quat, logit, sh);
   return cudaGetLastError();
 }
@@ -377,9 +397,10 @@ cudaError_t launch_mcmc_grow(int n, int n_add, int sh_degree, float* mean, float
   const int K3 = 3 * (sh_degree + 1) * (sh_degree + 1);
   mcmc_reduce_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt);
   mcmc_blocks_kernel<<<1, kThr, 0, st>>>(nb, w.bsum, w.bcnt, w.total, nullptr);
-  mcmc_apply_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt, w.cdf, w.rank, w.count);
-  mcmc_grow_draw_kernel<<<nba, kThr, 0, st>>>(n, n_add, w.rank, w.cdf, u, src, w.count);
-  mcmc_reset_kernel<<<nb, kThr, 0, st>>>(n, logit, log_scale, w.count);
+  mcmc_apply_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt, w.cdf, w.rank, w.count, w.list_n);
+  mcmc_grow_draw_kernel<<<nba, kThr, 0, st>>>(n, n_add, w.rank, w.cdf, u, src, w.count, w.list, w.list_n);
+  const int n_sources = std::min(n, n_add);
+  mcmc_reset_kernel<<<(n_sources + kThr - 1) / kThr, kThr, 0, st>>>(w.list, w.list_n, logit, log_scale, w.count);
   mcmc_grow_copy_kernel<<<nba, kThr, 0, st>>>(n, n_add, K3, src, mean, log_scale, quat, logit, sh);
   return cudaGetLastError();
 }
@@ -394,7 +415,8 @@ cudaError_t launch_mcmc_reset_moments(int n_rows, const int32_t* src, int n_src,
     G.v[g] = groups[g].v;
     G.width[g] = (int)(groups[g].n / n_rows);
   }
-  mcmc_reset_moments_kernel<<<(n_src + kThr - 1) / kThr, kThr, 0, st>>>(n_src, src, row0, G);
+  const size_t warps = 2 * (size_t)n_src;
+  mcmc_reset_moments_kernel<<<(unsigned)((warps * 32 + kThr - 1) / kThr), kThr, 0, st>>>(n_src, src, row0, G);
   return cudaGetLastError();
 }
 
