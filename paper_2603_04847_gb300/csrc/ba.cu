@@ -397,27 +397,34 @@ __global__ void __launch_bounds__(256) ba_chol_diag_kernel(int n, size_t ld, dou
   }
 }
 
-// Tile (k + 1 + blockIdx.x, k): X L_kk^T = A_ik, column by column (column c
-// of X is final once divided by L_cc; its products then leave the later
-// columns), a thread per element.
-__global__ void __launch_bounds__(kChT * kChT) ba_chol_panel_kernel(int n, size_t ld, double* __restrict__ S, int k) {
+// Tile (k + 1 + blockIdx.x, k): X L_kk^T = A_ik, a thread per row (forward
+// substitution along the row, with the diagonal's reciprocals formed once).
+__global__ void __launch_bounds__(kChT) ba_chol_panel_kernel(int n, size_t ld, double* __restrict__ S, int k) {
   __shared__ double L[kChT][kChT + 1];
   __shared__ double x[kChT][kChT + 1];
+  __shared__ double inv[kChT];
   if (chol_failed(S)) return;
   double* A = S + 6 * ld + 6;
   const int c0 = k * kChT, m = min(kChT, n - c0);
   const int r0 = (k + 1 + (int)blockIdx.x) * kChT, mi = min(kChT, n - r0);
-  const int r = threadIdx.x / kChT, q = threadIdx.x % kChT;
-  L[r][q] = (r < m && q <= r) ? A[(size_t)(c0 + r) * ld + c0 + q] : 0.0;
-  x[r][q] = (r < mi && q < m) ? A[(size_t)(r0 + r) * ld + c0 + q] : 0.0;
+  for (int r = 0; r < m; ++r)
+    for (int c = threadIdx.x; c < m; c += blockDim.x) L[r][c] = c <= r ? A[(size_t)(c0 + r) * ld + c0 + c] : 0.0;
+  for (int r = 0; r < mi; ++r)
+    for (int c = threadIdx.x; c < m; c += blockDim.x) x[r][c] = A[(size_t)(r0 + r) * ld + c0 + c];
   __syncthreads();
-  for (int c = 0; c < m; ++c) {
-    if (q == c) x[r][c] /= L[c][c];
-    __syncthreads();
-    if (q > c && q < m) x[r][q] -= x[r][c] * L[q][c];
-    __syncthreads();
+  if ((int)threadIdx.x < m) inv[threadIdx.x] = 1.0 / L[threadIdx.x][threadIdx.x];
+  __syncthreads();
+  const int r = threadIdx.x;
+  if (r < mi) {
+    for (int c = 0; c < m; ++c) {
+      double v = x[r][c];
+      for (int q = 0; q < c; ++q) v -= x[r][q] * L[c][q];
+      x[r][c] = v * inv[c];
+    }
   }
-  if (r < mi && q < m) A[(size_t)(r0 + r) * ld + c0 + q] = x[r][q];
+  __syncthreads();
+  for (int rr = 0; rr < mi; ++rr)
+    for (int c = threadIdx.x; c < m; c += blockDim.x) A[(size_t)(r0 + rr) * ld + c0 + c] = x[rr][c];
 }
 
 // Tile (i, j) = (k + 1 + blockIdx.y, k + 1 + blockIdx.x), j <= i:
@@ -447,14 +454,17 @@ __global__ void __launch_bounds__(256) ba_chol_update_kernel(int n, size_t ld, d
   }
 }
 
-// L y = b, then L^T x = y, tile by tile in one block; dc = (0, x).  The
-// off-diagonal products are summed by all threads, the triangle of each
-// diagonal tile by one thread from shared memory.
+// L y = b, then L^T x = y, tile by tile in one block; dc = (0, x).  Per
+// tile: warp r sums row r's products with the other tiles' solved unknowns,
+// then warp 0 solves the tile's triangle with a lane per row (the solved
+// unknown of each column broadcast by a shuffle).  The unknowns stay in
+// shared memory.
 __global__ void __launch_bounds__(1024) ba_chol_solve_kernel(int V, double* __restrict__ S,
                                                              const double* __restrict__ rhs,
                                                              double* __restrict__ dc, int32_t* status) {
-  __shared__ double part[kChT][33];
   __shared__ double Ld[kChT][kChT + 1];
+  __shared__ double inv[kChT];
+  __shared__ double part[kChT];
   extern __shared__ double y[];  // [n]: y, then x in place
   const int n = 6 * (V - 1);
   const size_t ld = 6 * (size_t)V;
@@ -476,36 +486,37 @@ __global__ void __launch_bounds__(1024) ba_chol_solve_kernel(int V, double* __re
         const int r = e / kChT, c = e % kChT;
         Ld[r][c] = (r < m && c <= r) ? A[(size_t)(r0 + r) * ld + r0 + c] : 0.0;
       }
-      // part[r][warp]: this warp's share of the products with the other
-      // tiles' solved unknowns (q < r0 forward, q >= r0 + m backward)
-      for (int r = 0; r < m; ++r) {
+      if (warp < m) {
+        const int r = warp;
         double v = 0.0;
         if (pass == 0) {
-          for (int q = threadIdx.x; q < r0; q += blockDim.x) v += A[(size_t)(r0 + r) * ld + q] * y[q];
+          for (int q = lane; q < r0; q += 32) v += A[(size_t)(r0 + r) * ld + q] * y[q];
         } else {
-          for (int q = r0 + m + threadIdx.x; q < n; q += blockDim.x) v += A[(size_t)q * ld + r0 + r] * y[q];
+          for (int q = r0 + m + lane; q < n; q += 32) v += A[(size_t)q * ld + r0 + r] * y[q];
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) part[r][warp] = v;
+        if (lane == 0) part[r] = (pass == 0 ? b[r0 + r] : y[r0 + r]) - v;
       }
       __syncthreads();
-      if (threadIdx.x == 0) {
+      if (warp == 0) {
+        if (lane < m) inv[lane] = 1.0 / Ld[lane][lane];
+        __syncwarp();
+        double v = lane < m ? part[lane] : 0.0;
         if (pass == 0) {
-          for (int r = 0; r < m; ++r) {
-            double v = b[r0 + r];
-            for (int w = 0; w < 32; ++w) v -= part[r][w];
-            for (int q = 0; q < r; ++q) v -= Ld[r][q] * y[r0 + q];
-            y[r0 + r] = v / Ld[r][r];
+          for (int c = 0; c < m; ++c) {
+            const double yc = __shfl_sync(0xffffffffu, v, c) * inv[c];
+            if (lane == c) v = yc;
+            else if (lane > c && lane < m) v -= Ld[lane][c] * yc;
           }
         } else {
-          for (int r = m - 1; r >= 0; --r) {
-            double v = y[r0 + r];
-            for (int w = 0; w < 32; ++w) v -= part[r][w];
-            for (int q = r + 1; q < m; ++q) v -= Ld[q][r] * y[r0 + q];
-            y[r0 + r] = v / Ld[r][r];
+          for (int c = m - 1; c >= 0; --c) {
+            const double xc = __shfl_sync(0xffffffffu, v, c) * inv[c];
+            if (lane == c) v = xc;
+            else if (lane < c) v -= Ld[c][lane] * xc;
           }
         }
+        if (lane < m) y[r0 + lane] = v;
       }
       __syncthreads();
     }
@@ -540,7 +551,7 @@ cudaError_t launch_ba_solve_cameras(int V, double* S, const double* rhs, double*
   for (int k = 0; k < T; ++k) {
     ba_chol_diag_kernel<<<1, 256, 0, st>>>(n, ld, S, k);
     if (k + 1 < T) {
-      ba_chol_panel_kernel<<<T - k - 1, kChT * kChT, 0, st>>>(n, ld, S, k);
+      ba_chol_panel_kernel<<<T - k - 1, kChT, 0, st>>>(n, ld, S, k);
       ba_chol_update_kernel<<<dim3(T - k - 1, T - k - 1), 256, 0, st>>>(n, ld, S, k);
     }
   }

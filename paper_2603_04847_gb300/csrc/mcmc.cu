@@ -102,8 +102,11 @@ __device__ inline void block_scan(double v, int c, double* incl, int* excl, doub
   if (excl_d) *excl_d = lane > 0 ? dbase + xprev : dbase;
 }
 
+// The opacity is evaluated once (FP64 exp) and left in cdf[i] for
+// mcmc_apply_kernel, which overwrites it with the cumulative sum.
 __global__ void __launch_bounds__(kThr) mcmc_reduce_kernel(int n, const float* __restrict__ logit,
-                                                           double* __restrict__ bsum, int32_t* __restrict__ bcnt) {
+                                                           double* __restrict__ bsum, int32_t* __restrict__ bcnt,
+                                                           double* __restrict__ o_out) {
   __shared__ double s_d[kThr / 32];
   __shared__ int s_i[kThr / 32];
   const int i = blockIdx.x * kThr + threadIdx.x;
@@ -111,6 +114,7 @@ __global__ void __launch_bounds__(kThr) mcmc_reduce_kernel(int n, const float* _
   int c = 0;
   if (i < n) {
     const double o = opacity_of(logit[i]);
+    o_out[i] = o;
     if (o <= kDead) c = 1;
     else v = o;
   }
@@ -173,7 +177,7 @@ __global__ void __launch_bounds__(kThr) mcmc_apply_kernel(int n, const float* __
   double v = 0.0;
   int c = 0;
   if (i < n) {
-    const double o = opacity_of(logit[i]);
+    const double o = cdf[i];  // the opacity, left there by mcmc_reduce_kernel
     if (o <= kDead) c = 1;
     else v = o;
   }
@@ -311,18 +315,24 @@ struct MomentGroups {
 
 __global__ void __launch_bounds__(kThr) mcmc_reset_moments_kernel(int n_src, const int32_t* __restrict__ src,
                                                                   int row0, MomentGroups G) {
-  // a warp per (k, row): the new row row0 + k, then the source src[k]
-  const int item = (int)((blockIdx.x * (size_t)kThr + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  const int k = item >> 1;
-  if (k >= n_src) return;
-  const int s = src[k];
-  if (s < 0) return;
-  const size_t row = (item & 1) ? (size_t)s : (size_t)row0 + k;
-  for (int g = 0; g < G.n; ++g) {
-    const size_t w = (size_t)G.width[g];
-    for (int a = lane; a < G.width[g]; a += 32) {
-      G.m[g][row * w + a] = 0.f;
-      G.v[g][row * w + a] = 0.f;
+  // a thread per k reads src[k]; the warp then zeroes the two rows of each
+  // of its lanes with src[k] >= 0 in turn, lanes over the row (coalesced)
+  const int k = blockIdx.x * kThr + threadIdx.x, lane = threadIdx.x & 31;
+  const int s = k < n_src ? src[k] : -1;
+  unsigned todo = __ballot_sync(0xffffffffu, s >= 0);
+  while (todo) {
+    const int l = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const int kl = __shfl_sync(0xffffffffu, k, l), sl = __shfl_sync(0xffffffffu, s, l);
+    for (int r = 0; r < 2; ++r) {
+      const size_t row = r ? (size_t)sl : (size_t)row0 + kl;
+      for (int g = 0; g < G.n; ++g) {
+        const size_t w = (size_t)G.width[g];
+        for (int a = lane; a < G.width[g]; a += 32) {
+          G.m[g][row * w + a] = 0.f;
+          G.v[g][row * w + a] = 0.f;
+        }
+      }
     }
   }
 }
@@ -377,7 +387,7 @@ cudaError_t launch_mcmc_relocate(int n, int sh_degree, float* mean, float* log_s
   McmcWs w = mcmc_layout(ws, n, nullptr);
   const int nb = (n + kThr - 1) / kThr;
   const int K3 = 3 * (sh_degree + 1) * (sh_degree + 1);
-  mcmc_reduce_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt);
+  mcmc_reduce_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt, w.cdf);
   mcmc_blocks_kernel<<<1, kThr, 0, st>>>(nb, w.bsum, w.bcnt, w.total, n_dead);
   mcmc_apply_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt, w.cdf, w.rank, w.count, w.list_n);
   mcmc_draw_kernel<<<nb, kThr, 0, st>>>(n, w.rank, w.cdf, u, n_u, src, w.count, w.list, w.list_n);
@@ -395,7 +405,7 @@ cudaError_t launch_mcmc_grow(int n, int n_add, int sh_degree, float* mean, float
   const int nb = (n + kThr - 1) / kThr;
   const int nba = (n_add + kThr - 1) / kThr;
   const int K3 = 3 * (sh_degree + 1) * (sh_degree + 1);
-  mcmc_reduce_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt);
+  mcmc_reduce_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt, w.cdf);
   mcmc_blocks_kernel<<<1, kThr, 0, st>>>(nb, w.bsum, w.bcnt, w.total, nullptr);
   mcmc_apply_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt, w.cdf, w.rank, w.count, w.list_n);
   mcmc_grow_draw_kernel<<<nba, kThr, 0, st>>>(n, n_add, w.rank, w.cdf, u, src, w.count, w.list, w.list_n);
@@ -415,8 +425,7 @@ cudaError_t launch_mcmc_reset_moments(int n_rows, const int32_t* src, int n_src,
     G.v[g] = groups[g].v;
     G.width[g] = (int)(groups[g].n / n_rows);
   }
-  const size_t warps = 2 * (size_t)n_src;
-  mcmc_reset_moments_kernel<<<(unsigned)((warps * 32 + kThr - 1) / kThr), kThr, 0, st>>>(n_src, src, row0, G);
+  mcmc_reset_moments_kernel<<<(n_src + kThr - 1) / kThr, kThr, 0, st>>>(n_src, src, row0, G);
   return cudaGetLastError();
 }
 
