@@ -780,29 +780,10 @@ def run_ours(args):
             stages[k]["hbm_frac"] = stages[k]["GBps"] / hbm_peak
     # the dominant kernel: the longest single-kernel stage (the sort stage
     # is a dozen kernels, none of them near the top of the launch list; its
-    # HBM fraction is in `stages`).  The raster_bwd stage also clears the
-    # screen-space records (a memset of B N 48 bytes; not in the
-    # deterministic form), timed here on the same bytes and taken off
-    if not js.deterministic:
-        r0 = js.renderers[0]
-        nb = js.batch.B * js.g.n * 48
-        z = r0.ws_bwd[:nb]
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        mz = []
-        for _ in range(5):
-            flush.zero_()
-            ev[0].record()
-            z.zero_()
-            ev[1].record()
-            torch.cuda.synchronize()
-            mz.append(ev[0].elapsed_time(ev[1]))
-        st_ms["raster_bwd_memset"] = sum(mz) / len(mz)
-        st_ms["raster_bwd_kernel"] = max(st_ms["raster_bwd"] - st_ms["raster_bwd_memset"], 1e-6)
+    # HBM fraction is in `stages`).  The step clears the backward's
+    # screen-space records on the side stream, so the raster_bwd stage is
+    # the compositing backward's launch alone
     kern_ms = dict(st_ms)
-    if "raster_bwd_kernel" in st_ms:
-        kern_ms["raster_bwd"] = st_ms["raster_bwd_kernel"]
-        stages["raster_bwd"]["records_clear_ms"] = st_ms["raster_bwd_memset"]
-        stages["raster_bwd"]["kernel_ms"] = st_ms["raster_bwd_kernel"]
     dominant = max(("project", "render_fwd", "raster_bwd", "project_bwd"), key=lambda k: kern_ms.get(k, 0))
     # the compositing kernels are bound by FP32/SFU issue, not HBM: report
     # their pair throughput against the FP32 lane peak
@@ -838,9 +819,7 @@ def run_ours(args):
                     frac=ach / hbm_peak, traffic=traffic, launch_ms=kern_ms[dominant], peak_source=peak_src)
     if traffic_note:
         roof["traffic_note"] = traffic_note
-    if dominant == "raster_bwd" and "raster_bwd_memset" in st_ms:
-        roof["launch_note"] = "raster_bwd stage %.3f ms minus the clearing of its records (%.3f ms, same bytes)" % (
-            st_ms["raster_bwd"], st_ms["raster_bwd_memset"])
+
     step_bytes = sum(model.values())
     step_ms_now = sum(v for k, v in st_ms.items())
     hbm_step = dict(algorithmic_bytes=step_bytes, GBps=step_bytes / (ms * 1e-3) / 1e9,

@@ -419,6 +419,20 @@ gs_status gs_raster_bwd(const gs_gaussians* g, const gs_cameras* cams,
                         const float* v_image, const float* target,
                         float l1_weight, double* loss, void* ws,
                         size_t ws_bytes, gs_stream stream);
+/*
+ * gs_raster_bwd_zeroed — gs_raster_bwd without its first step: the caller
+ * has already zeroed the screen-space records, the first
+ * B * n_gaussians * 12 floats of ws (for instance with gs_zero on another
+ * stream, overlapping earlier work, and ordered before this call).
+ */
+gs_status gs_raster_bwd_zeroed(const gs_gaussians* g, const gs_cameras* cams,
+                               const gs_batch* batch, const gs_projected* proj,
+                               const uint32_t* vals, const uint32_t* ranges,
+                               const float* bg, const float* image,
+                               const float* T_final, const uint32_t* n_contrib,
+                               const float* v_image, const float* target,
+                               float l1_weight, double* loss, void* ws,
+                               size_t ws_bytes, gs_stream stream);
 gs_status gs_project_bwd(const gs_gaussians* g, const gs_cameras* cams,
                          const gs_batch* batch, const gs_projected* proj,
                          const gs_gaussian_grads* dg, double* g_pose_tangent,
@@ -445,6 +459,26 @@ gs_status track_reproj_fwd_bwd(const float* X, int32_t n_points,
                                float* grad_X, double* g_pose_tangent,
                                uint32_t* n_masked, void* ws, size_t ws_bytes,
                                gs_stream stream);
+
+/*
+ * track_reproj_fwd_bwd_det — the same term (arguments, workspace and rules
+ * of track_reproj_fwd_bwd) with results that do not depend on the order in
+ * which threads run, given that no track point has two observations in one
+ * camera (a track sees each image once): the slots are processed one
+ * launch after another in slot order, each block and warp keeps its own
+ * sums, and the loss and pose sums are formed in block order.  Two calls
+ * on the same inputs give bit-identical loss, grad_X and g_pose_tangent.
+ * 3 B launches instead of 2 (per slot: the kernel, the pose sums and the
+ * loss sum).
+ */
+gs_status track_reproj_fwd_bwd_det(const float* X, int32_t n_points,
+                                   const int32_t* obs_point, const float* obs_xy,
+                                   const int64_t* view_obs_offset,
+                                   const gs_cameras* cams, const gs_batch* batch,
+                                   float delta, float weight, double* loss,
+                                   float* grad_X, double* g_pose_tangent,
+                                   uint32_t* n_masked, void* ws, size_t ws_bytes,
+                                   gs_stream stream);
 
 /*
  * track_reproj_fwd_bwd_static — the same computation as track_reproj_fwd_bwd
@@ -507,7 +541,9 @@ gs_status sfm_ba_assemble(const float* X, int32_t n_points,
 /*
  * sfm_ba_schur — eliminates the points from the damped normal equations of
  * one LM iteration of Eq. 4 (the blocks of sfm_ba_assemble):
- *   S [6V,6V] = U_d - sum_k W_ik V_k^-1 W_jk^T   (row-major, written),
+ *   S [6V,6V] = U_d - sum_k W_ik V_k^-1 W_jk^T   (row-major; S is
+ *               symmetric and only its lower triangle is formed, which is
+ *               all sfm_ba_solve_cameras reads; the rest is not meaningful),
  *   rhs [6V]  = -gc + sum_k W_ik V_k^-1 gp_k      (written),
  *   Vinv [P,9] = V_k^-1 of the damped point blocks (written),
  * with the Marquardt damping A_d = A + lambda diag(A) of every camera block

@@ -105,6 +105,9 @@ PROTOTYPES = {
     "gs_raster_bwd": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                      c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_void_p,
                                      c_void_p, c_size_t, c_void_p]),
+    "gs_raster_bwd_zeroed": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_void_p,
+                                            c_void_p, c_size_t, c_void_p]),
     "gs_project_bwd": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                       c_size_t, c_void_p]),
     "gs_render_bwd_det_workspace": (ctypes.c_int, [c_int32, c_void_p, c_size_t, ctypes.POINTER(c_size_t)]),
@@ -118,6 +121,9 @@ PROTOTYPES = {
     "track_reproj_fwd_bwd": (ctypes.c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                             c_void_p, c_float, c_float, c_void_p, c_void_p, c_void_p,
                                             c_void_p, c_void_p, c_size_t, c_void_p]),
+    "track_reproj_fwd_bwd_det": (ctypes.c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                                c_void_p, c_float, c_float, c_void_p, c_void_p, c_void_p,
+                                                c_void_p, c_void_p, c_size_t, c_void_p]),
     "track_reproj_fwd_bwd_static": (ctypes.c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p,
                                                    c_void_p, c_void_p, c_float, c_float, c_void_p, c_void_p,
                                                    c_void_p, c_void_p, c_void_p]),

@@ -370,14 +370,19 @@ def gs_render_bwd(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, tl
 
 def gs_raster_bwd(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, tl: TileLists, bg, image,
                   T_final, n_contrib, v_image, target, l1_weight: float, loss, ws: torch.Tensor, Rt=None,
-                  stream=None):
+                  stream=None, records_zeroed: bool = False):
+    """records_zeroed: the caller has zeroed the screen-space records at the
+    start of ws (gs_raster_bwd_zeroed; FP32 only)."""
     lib = _lib.load()
     _need_cuda(bg, T_final, n_contrib, ws, image, v_image, target, loss)
     gc, cc, bc, pc = g.c(), cams.c(Rt, f64=g.f64), batch.c(), proj.c()
-    check(_fn(lib, "gs_raster_bwd", g.f64)(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc),
-                                           _p(tl.vals), _p(tl.ranges), _p(bg), _p(image), _p(T_final),
-                                           _p(n_contrib), _p(v_image), _p(target), float(l1_weight), _p(loss),
-                                           _p(ws), ws.numel(), _stream(stream)), "gs_raster_bwd")
+    if records_zeroed and g.f64:
+        raise _lib.GsError("gs_raster_bwd_zeroed is FP32 only")
+    fn = lib.gs_raster_bwd_zeroed if records_zeroed else _fn(lib, "gs_raster_bwd", g.f64)
+    check(fn(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc),
+             _p(tl.vals), _p(tl.ranges), _p(bg), _p(image), _p(T_final),
+             _p(n_contrib), _p(v_image), _p(target), float(l1_weight), _p(loss),
+             _p(ws), ws.numel(), _stream(stream)), "gs_raster_bwd")
 
 
 def gs_project_bwd(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, dg: Gaussians,
@@ -543,14 +548,18 @@ def track_workspace_bytes(batch: Batch) -> int:
 
 
 def track_reproj_fwd_bwd(X, obs_point, obs_xy, view_obs_offset, cams: Cameras, batch: Batch, delta: float,
-                         weight: float, loss, grad_X, g_pose_tangent, n_masked, ws, Rt=None, stream=None):
+                         weight: float, loss, grad_X, g_pose_tangent, n_masked, ws, Rt=None, stream=None,
+                         deterministic: bool = False):
+    """The track term of Eq. 6; deterministic: track_reproj_fwd_bwd_det
+    (bit-identical results from run to run)."""
     lib = _lib.load()
     _need_cuda(X, obs_point, obs_xy, view_obs_offset, loss, grad_X, g_pose_tangent, n_masked, ws)
     cc, bc = cams.c(Rt), batch.c()
-    check(lib.track_reproj_fwd_bwd(_p(X), X.shape[0], _p(obs_point), _p(obs_xy), _p(view_obs_offset),
-                                   ctypes.byref(cc), ctypes.byref(bc), float(delta), float(weight), _p(loss),
-                                   _p(grad_X), _p(g_pose_tangent), _p(n_masked), _p(ws), ws.numel(),
-                                   _stream(stream)), "track_reproj_fwd_bwd")
+    fn = lib.track_reproj_fwd_bwd_det if deterministic else lib.track_reproj_fwd_bwd
+    check(fn(_p(X), X.shape[0], _p(obs_point), _p(obs_xy), _p(view_obs_offset),
+             ctypes.byref(cc), ctypes.byref(bc), float(delta), float(weight), _p(loss),
+             _p(grad_X), _p(g_pose_tangent), _p(n_masked), _p(ws), ws.numel(),
+             _stream(stream)), "track_reproj_fwd_bwd")
 
 
 def track_reproj_fwd_bwd_static(X, obs_point, obs_xy, view_obs_offset, cams: Cameras, batch: Batch,

@@ -277,43 +277,79 @@ __device__ inline void point_block(const double* __restrict__ Vp, const double* 
   for (int a = 0; a < 3; ++a) g[a] = empty ? 0.0 : gp[3 * (size_t)k + a];
 }
 
-__global__ void __launch_bounds__(128) ba_point_schur_kernel(
-    int V, int P, int64_t M, const double* __restrict__ Vp, const double* __restrict__ gp,
-    const double* __restrict__ Wo, const int32_t* __restrict__ obs_cam, const int64_t* __restrict__ off,
-    const int32_t* __restrict__ point_obs, double lambda_h, const double* __restrict__ lambda_d,
-    double* __restrict__ Vinv, double* __restrict__ S, double* __restrict__ rhs) {
+// The damped point blocks' inverses, one thread per point.
+__global__ void __launch_bounds__(128) ba_point_vinv_kernel(int P, const double* __restrict__ Vp,
+                                                            const double* __restrict__ gp, double lambda_h,
+                                                            const double* __restrict__ lambda_d,
+                                                            double* __restrict__ Vinv) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= P) return;
   const double lambda = lambda_d ? *lambda_d : lambda_h;
   double Vi[9], g[3];
   point_block(Vp, gp, k, lambda, Vi, g);
   for (int a = 0; a < 9; ++a) Vinv[9 * (size_t)k + a] = Vi[a];
+}
+
+__device__ inline void point_schur_entry(int V, int P, int64_t M, int64_t p, const double* __restrict__ gp,
+                                         const double* __restrict__ Vp, const double* __restrict__ Wo,
+                                         const int32_t* __restrict__ obs_cam, const int64_t* __restrict__ off,
+                                         const int32_t* __restrict__ point_obs, const double* __restrict__ Vinv,
+                                         double* __restrict__ S, double* __restrict__ rhs) {
+  // the point whose list holds p: the last k with off[k] <= p
+  int lo = 0, hi = P - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= p) lo = mid;
+    else hi = mid - 1;
+  }
+  const int k = lo;
+  const int64_t oa = point_obs[p];
+  if (oa < 0 || oa >= M) return;
+  const int ca = obs_cam[oa];
+  if ((unsigned)ca >= (unsigned)V) return;
+  const bool empty = block_empty(Vp + 9 * (size_t)k, 9);
+  double Vi[9], g[3];
+  for (int e = 0; e < 9; ++e) Vi[e] = Vinv[9 * (size_t)k + e];
+  for (int e = 0; e < 3; ++e) g[e] = empty ? 0.0 : gp[3 * (size_t)k + e];
   const size_t n = 6 * (size_t)V;
-  for (int64_t p = off[k]; p < off[k + 1]; ++p) {
-    const int64_t oa = point_obs[p];
-    if (oa < 0 || oa >= M) continue;
-    const int ca = obs_cam[oa];
-    if ((unsigned)ca >= (unsigned)V) continue;
-    const double* Wa = Wo + 18 * oa;
-    double Y[18];  // W_a V^-1, 6x3
+  const double* Wa = Wo + 18 * oa;
+  double Y[18];  // W_a V^-1, 6x3
+  for (int r = 0; r < 6; ++r)
+    for (int c = 0; c < 3; ++c)
+      Y[3 * r + c] = Wa[3 * r] * Vi[c] + Wa[3 * r + 1] * Vi[3 + c] + Wa[3 * r + 2] * Vi[6 + c];
+  for (int r = 0; r < 6; ++r)
+    atomicAdd(&rhs[6 * (size_t)ca + r], Y[3 * r] * g[0] + Y[3 * r + 1] * g[1] + Y[3 * r + 2] * g[2]);
+  for (int64_t q = off[k]; q < off[k + 1]; ++q) {
+    const int64_t ob = point_obs[q];
+    if (ob < 0 || ob >= M) continue;
+    const int cb = obs_cam[ob];
+    if ((unsigned)cb >= (unsigned)V || cb > ca) continue;
+    const double* Wb = Wo + 18 * ob;
     for (int r = 0; r < 6; ++r)
-      for (int c = 0; c < 3; ++c)
-        Y[3 * r + c] = Wa[3 * r] * Vi[c] + Wa[3 * r + 1] * Vi[3 + c] + Wa[3 * r + 2] * Vi[6 + c];
-    for (int r = 0; r < 6; ++r)
-      atomicAdd(&rhs[6 * (size_t)ca + r], Y[3 * r] * g[0] + Y[3 * r + 1] * g[1] + Y[3 * r + 2] * g[2]);
-    for (int64_t q = off[k]; q < off[k + 1]; ++q) {
-      const int64_t ob = point_obs[q];
-      if (ob < 0 || ob >= M) continue;
-      const int cb = obs_cam[ob];
-      if ((unsigned)cb >= (unsigned)V) continue;
-      const double* Wb = Wo + 18 * ob;
-      for (int r = 0; r < 6; ++r)
-        for (int c = 0; c < 6; ++c)
-          atomicAdd(&S[(6 * (size_t)ca + r) * n + 6 * (size_t)cb + c],
-                    -(Y[3 * r] * Wb[3 * c] + Y[3 * r + 1] * Wb[3 * c + 1] + Y[3 * r + 2] * Wb[3 * c + 2]));
-    }
+      for (int c = 0; c < 6; ++c) {
+        if (cb == ca && c > r) continue;
+        atomicAdd(&S[(6 * (size_t)ca + r) * n + 6 * (size_t)cb + c],
+                  -(Y[3 * r] * Wb[3 * c] + Y[3 * r + 1] * Wb[3 * c + 1] + Y[3 * r + 2] * Wb[3 * c + 2]));
+      }
   }
 }
+
+// One thread per entry p of the points' observation lists (observation a
+// of point k): its share of rhs, and of S for every observation b of the
+// same point whose camera is not after a's.  S is symmetric and the camera
+// solve reads its lower triangle only, so the blocks above the diagonal are
+// left out (and, within a diagonal block, the entries above its diagonal).
+__global__ void __launch_bounds__(128) ba_point_schur_kernel(
+    int V, int P, int64_t M, const double* __restrict__ gp, const double* __restrict__ Vp,
+    const double* __restrict__ Wo, const int32_t* __restrict__ obs_cam, const int64_t* __restrict__ off,
+    const int32_t* __restrict__ point_obs, const double* __restrict__ Vinv, double* __restrict__ S,
+    double* __restrict__ rhs) {
+  const int64_t total = off[P];
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+       p += (int64_t)gridDim.x * blockDim.x)
+    point_schur_entry(V, P, M, p, gp, Vp, Wo, obs_cam, off, point_obs, Vinv, S, rhs);
+}
+
 
 __global__ void __launch_bounds__(128) ba_back_substitute_kernel(
     int V, int P, int64_t M, const double* __restrict__ Vinv, const double* __restrict__ Vp,
@@ -535,9 +571,14 @@ cudaError_t launch_ba_schur(int V, int P, int64_t M, const double* U, const doub
   cudaError_t e = cudaMemsetAsync(S, 0, sizeof(double) * 36 * (size_t)V * (size_t)V, st);
   if (e != cudaSuccess) return e;
   ba_camera_init_kernel<<<(V + 63) / 64, 64, 0, st>>>(V, U, gc, lambda, lambda_dev, S, rhs);
-  if (P > 0)
-    ba_point_schur_kernel<<<(P + 127) / 128, 128, 0, st>>>(V, P, M, Vp, gp, Wo, obs_cam, point_obs_offset, point_obs,
-                                                            lambda, lambda_dev, Vinv, S, rhs);
+  if (P > 0) {
+    ba_point_vinv_kernel<<<(P + 127) / 128, 128, 0, st>>>(P, Vp, gp, lambda, lambda_dev, Vinv);
+    // a thread per list entry (grid-stride: the host sizes the grid from
+    // the observation count, the kernel reads the lists' true length)
+    if (M > 0)
+      ba_point_schur_kernel<<<(unsigned)std::min<int64_t>((M + 127) / 128, 65535), 128, 0, st>>>(V, P, M, gp, Vp, Wo, obs_cam,
+                                                                          point_obs_offset, point_obs, Vinv, S, rhs);
+  }
   return cudaGetLastError();
 }
 

@@ -250,26 +250,48 @@ gs_status check_bwd_common(const gs_gaussians* g, const gs_cameras* cams, const 
 }
 }  // namespace
 
+namespace {
+gs_status raster_bwd(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
+                     const gs_projected* proj, const uint32_t* vals, const uint32_t* ranges, const float* bg,
+                     const float* image, const float* T_final, const uint32_t* n_contrib, const float* v_image,
+                     const float* target, float l1_weight, double* loss, void* ws, size_t ws_bytes,
+                     gs_stream stream, bool zero, const char* who) {
+  gs_status s;
+  if ((s = check_bwd_common(g, cams, batch, proj, ws, ws_bytes, who))) return s;
+  if (!vals || !ranges || !bg || !T_final || !n_contrib) return fail(GS_ERR_ARG, "%s: null argument", who);
+  if (!v_image && (!target || !image))
+    return fail(GS_ERR_ARG, "%s: need v_image, or image and target for the fused L1", who);
+  if (!v_image && !std::isfinite(l1_weight)) return fail(GS_ERR_NONFINITE, "%s: l1_weight", who);
+  cudaStream_t st = (cudaStream_t)stream;
+  float* v2d = reinterpret_cast<float*>(ws);
+  cudaError_t e;
+  if (zero) {
+    e = cudaMemsetAsync(v2d, 0, (size_t)batch->B * g->n * 12 * sizeof(float), st);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+  }
+  e = launch_render_bwd(*batch, *cams, *proj, vals, ranges, bg, image, T_final, n_contrib, v_image,
+                        target, l1_weight, loss, v2d, st);
+  if (e != cudaSuccess) return cuda_fail(e, who);
+  return GS_OK;
+}
+}  // namespace
+
 gs_status gs_raster_bwd(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
                         const gs_projected* proj, const uint32_t* vals, const uint32_t* ranges,
                         const float* bg, const float* image, const float* T_final,
                         const uint32_t* n_contrib, const float* v_image, const float* target,
                         float l1_weight, double* loss, void* ws, size_t ws_bytes, gs_stream stream) {
-  gs_status s;
-  if ((s = check_bwd_common(g, cams, batch, proj, ws, ws_bytes, "gs_raster_bwd"))) return s;
-  if (!vals || !ranges || !bg || !T_final || !n_contrib)
-    return fail(GS_ERR_ARG, "gs_raster_bwd: null argument");
-  if (!v_image && (!target || !image))
-    return fail(GS_ERR_ARG, "gs_raster_bwd: need v_image, or image and target for the fused L1");
-  if (!v_image && !std::isfinite(l1_weight)) return fail(GS_ERR_NONFINITE, "gs_raster_bwd: l1_weight");
-  cudaStream_t st = (cudaStream_t)stream;
-  float* v2d = reinterpret_cast<float*>(ws);
-  cudaError_t e = cudaMemsetAsync(v2d, 0, (size_t)batch->B * g->n * 12 * sizeof(float), st);
-  if (e != cudaSuccess) return cuda_fail(e, "gs_raster_bwd memset");
-  e = launch_render_bwd(*batch, *cams, *proj, vals, ranges, bg, image, T_final, n_contrib, v_image,
-                        target, l1_weight, loss, v2d, st);
-  if (e != cudaSuccess) return cuda_fail(e, "gs_raster_bwd");
-  return GS_OK;
+  return raster_bwd(g, cams, batch, proj, vals, ranges, bg, image, T_final, n_contrib, v_image, target, l1_weight,
+                    loss, ws, ws_bytes, stream, true, "gs_raster_bwd");
+}
+
+gs_status gs_raster_bwd_zeroed(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
+                               const gs_projected* proj, const uint32_t* vals, const uint32_t* ranges,
+                               const float* bg, const float* image, const float* T_final,
+                               const uint32_t* n_contrib, const float* v_image, const float* target,
+                               float l1_weight, double* loss, void* ws, size_t ws_bytes, gs_stream stream) {
+  return raster_bwd(g, cams, batch, proj, vals, ranges, bg, image, T_final, n_contrib, v_image, target, l1_weight,
+                    loss, ws, ws_bytes, stream, false, "gs_raster_bwd_zeroed");
 }
 
 gs_status gs_project_bwd(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
@@ -501,27 +523,45 @@ gs_status track_reproj_workspace(const gs_batch* batch, size_t* ws_bytes) {
   return GS_OK;
 }
 
+namespace {
+gs_status track_call(const float* X, int32_t n_points, const int32_t* obs_point, const float* obs_xy,
+                     const int64_t* view_obs_offset, const gs_cameras* cams, const gs_batch* batch, float delta,
+                     float weight, double* loss, float* grad_X, double* g_pose_tangent, uint32_t* n_masked,
+                     void* ws, size_t ws_bytes, gs_stream stream, bool det, const char* who) {
+  gs_status s;
+  if ((s = check_cameras(cams)) || (s = check_batch(batch))) return s;
+  if (n_points < 0 || !view_obs_offset || !grad_X || !g_pose_tangent || !ws)
+    return fail(GS_ERR_ARG, "%s: null argument", who);
+  if (n_points > 0 && (!X || !obs_point || !obs_xy)) return fail(GS_ERR_ARG, "%s: null array", who);
+  if (obs_xy && !aligned(obs_xy, 8)) return fail(GS_ERR_ARG, "%s: obs_xy must be 8-byte aligned", who);
+  if (!std::isfinite(delta) || !std::isfinite(weight))
+    return fail(GS_ERR_NONFINITE, "%s: non-finite delta/weight", who);
+  if (!(delta > 0.f)) return fail(GS_ERR_ARG, "%s: delta must be > 0", who);
+  if (ws_bytes < track_workspace_bytes(*batch)) return fail(GS_ERR_ARG, "%s: workspace too small", who);
+  cudaError_t e = (det ? launch_track_det : launch_track)(X, n_points, obs_point, obs_xy, view_obs_offset, *cams,
+                                                           *batch, delta, weight, loss, grad_X, g_pose_tangent,
+                                                           n_masked, ws, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, who);
+  return GS_OK;
+}
+}  // namespace
+
 gs_status track_reproj_fwd_bwd(const float* X, int32_t n_points, const int32_t* obs_point,
                                const float* obs_xy, const int64_t* view_obs_offset,
                                const gs_cameras* cams, const gs_batch* batch, float delta,
                                float weight, double* loss, float* grad_X, double* g_pose_tangent,
                                uint32_t* n_masked, void* ws, size_t ws_bytes, gs_stream stream) {
-  gs_status s;
-  if ((s = check_cameras(cams)) || (s = check_batch(batch))) return s;
-  if (n_points < 0 || !view_obs_offset || !grad_X || !g_pose_tangent || !ws)
-    return fail(GS_ERR_ARG, "track_reproj_fwd_bwd: null argument");
-  if (n_points > 0 && (!X || !obs_point || !obs_xy))
-    return fail(GS_ERR_ARG, "track_reproj_fwd_bwd: null array");
-  if (obs_xy && !aligned(obs_xy, 8)) return fail(GS_ERR_ARG, "track_reproj_fwd_bwd: obs_xy must be 8-byte aligned");
-  if (!std::isfinite(delta) || !std::isfinite(weight))
-    return fail(GS_ERR_NONFINITE, "track_reproj_fwd_bwd: non-finite delta/weight");
-  if (!(delta > 0.f)) return fail(GS_ERR_ARG, "track_reproj_fwd_bwd: delta must be > 0");
-  if (ws_bytes < track_workspace_bytes(*batch))
-    return fail(GS_ERR_ARG, "track_reproj_fwd_bwd: workspace too small");
-  cudaError_t e = launch_track(X, n_points, obs_point, obs_xy, view_obs_offset, *cams, *batch, delta,
-                               weight, loss, grad_X, g_pose_tangent, n_masked, ws, (cudaStream_t)stream);
-  if (e != cudaSuccess) return cuda_fail(e, "track_reproj_fwd_bwd");
-  return GS_OK;
+  return track_call(X, n_points, obs_point, obs_xy, view_obs_offset, cams, batch, delta, weight, loss, grad_X,
+                    g_pose_tangent, n_masked, ws, ws_bytes, stream, false, "track_reproj_fwd_bwd");
+}
+
+gs_status track_reproj_fwd_bwd_det(const float* X, int32_t n_points, const int32_t* obs_point,
+                                   const float* obs_xy, const int64_t* view_obs_offset,
+                                   const gs_cameras* cams, const gs_batch* batch, float delta,
+                                   float weight, double* loss, float* grad_X, double* g_pose_tangent,
+                                   uint32_t* n_masked, void* ws, size_t ws_bytes, gs_stream stream) {
+  return track_call(X, n_points, obs_point, obs_xy, view_obs_offset, cams, batch, delta, weight, loss, grad_X,
+                    g_pose_tangent, n_masked, ws, ws_bytes, stream, true, "track_reproj_fwd_bwd_det");
 }
 
 gs_status pose_se3_update(int32_t n_cams, const float* T0, float* xi, const double* g_tangent,

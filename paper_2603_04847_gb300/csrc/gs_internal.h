@@ -72,6 +72,10 @@ cudaError_t launch_track(const float* X, int n_points, const int32_t* obs_point,
                          const int64_t* view_obs_offset, const gs_cameras& cams, const gs_batch& batch,
                          float delta, float weight, double* loss, float* grad_X,
                          double* g_pose_tangent, uint32_t* n_masked, void* ws, cudaStream_t st);
+cudaError_t launch_track_det(const float* X, int n_points, const int32_t* obs_point, const float* obs_xy,
+                         const int64_t* view_obs_offset, const gs_cameras& cams, const gs_batch& batch,
+                         float delta, float weight, double* loss, float* grad_X,
+                         double* g_pose_tangent, uint32_t* n_masked, void* ws, cudaStream_t st);
 
 cudaError_t launch_pose_partials_finalize(const double* partial, int n_blocks, const gs_batch& batch,
                                           int n_cams, double* g_pose_tangent, cudaStream_t st);

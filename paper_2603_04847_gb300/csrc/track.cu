@@ -8,6 +8,7 @@
 // scalar atomics; a track has few observations, so they rarely collide),
 // and its pose-tangent share is reduced warp -> block (shared double) ->
 // per-block partial, summed in block order by a second kernel.
+#include <algorithm>
 #include <mutex>
 
 #include "gs_internal.h"
@@ -24,13 +25,24 @@ struct TrackSlot {
   long long pref;   // observations of slots before this one
 };
 
+// kDet: a launch over one slot (B == 1), whose sums do not depend on the
+// order in which warps and blocks run: each warp keeps its own pose and loss
+// sums (lane 0 adds its warp's reduced values in the warp's own order), the
+// block adds its warps in warp order, and the block's loss goes to
+// loss_partial[block] for a fixed-order sum (track_loss_finalize_kernel).
+// The point gradients are still added atomically: within one view a track
+// point has one observation, so no two adds of one launch meet.
+template <bool kDet>
 __global__ void __launch_bounds__(256) track_kernel(const float* __restrict__ X, int n_points,
                                                     const int32_t* __restrict__ obs_point,
                                                     const float2* __restrict__ obs_xy,
                                                     const int64_t* __restrict__ view_obs_offset,
                                                     gs_cameras cams, gs_batch batch, float delta,
                                                     float weight, double* loss, float* grad_X,
-                                                    uint32_t* n_masked, double* partial) {
+                                                    uint32_t* n_masked, double* partial, double* loss_partial) {
+  constexpr int kWarps = 256 / 32;
+  __shared__ double s_tan_w[kDet ? kWarps : 1][6];
+  __shared__ double s_loss_w[kDet ? kWarps : 1];
   __shared__ TrackSlot ts[GS_MAX_BATCH];
   __shared__ long long s_total;
   __shared__ double s_tan[GS_MAX_BATCH * 6];
@@ -60,6 +72,8 @@ __global__ void __launch_bounds__(256) track_kernel(const float* __restrict__ X,
     ts[b].cy = cams.K[4 * v + 3];
   }
   for (int i = threadIdx.x; i < batch.B * 6; i += blockDim.x) s_tan[i] = 0.0;
+  if constexpr (kDet)
+    for (int i = threadIdx.x; i < kWarps * 6; i += blockDim.x) (&s_tan_w[0][0])[i] = 0.0;
   __syncthreads();
   const long long total = s_total;
   const int lane = threadIdx.x & 31;
@@ -145,7 +159,10 @@ __global__ void __launch_bounds__(256) track_kernel(const float* __restrict__ X,
         float x = tan[a];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-        if (lane == 0) atomicAdd(&s_tan[6 * b0 + a], (double)x);
+        if (lane == 0) {
+          if constexpr (kDet) s_tan_w[threadIdx.x >> 5][a] += (double)x;
+          else atomicAdd(&s_tan[6 * b0 + a], (double)x);
+        }
       }
     } else if (valid) {
 #pragma unroll
@@ -158,16 +175,46 @@ __global__ void __launch_bounds__(256) track_kernel(const float* __restrict__ X,
     masked += __shfl_xor_sync(0xffffffffu, masked, off);
   }
   if (lane == 0) {
-    atomicAdd(&s_loss, (double)lsum);
+    if constexpr (kDet) s_loss_w[threadIdx.x >> 5] = (double)lsum;
+    else atomicAdd(&s_loss, (double)lsum);
     atomicAdd(&s_masked, masked);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (loss && s_loss != 0.0) atomicAdd(loss, s_loss);
+    if constexpr (kDet) {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += s_loss_w[w];
+      loss_partial[blockIdx.x] = t;
+    } else {
+      if (loss && s_loss != 0.0) atomicAdd(loss, s_loss);
+    }
     if (n_masked && s_masked) atomicAdd(n_masked, s_masked);
   }
-  for (int i = threadIdx.x; i < batch.B * 6; i += blockDim.x)
-    partial[(size_t)blockIdx.x * batch.B * 6 + i] = s_tan[i];
+  if constexpr (kDet) {
+    if (threadIdx.x < 6) {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += s_tan_w[w][threadIdx.x];
+      partial[(size_t)blockIdx.x * 6 + threadIdx.x] = t;
+    }
+  } else {
+    for (int i = threadIdx.x; i < batch.B * 6; i += blockDim.x)
+      partial[(size_t)blockIdx.x * batch.B * 6 + i] = s_tan[i];
+  }
+}
+
+// loss += the blocks' loss sums, in block order.
+__global__ void __launch_bounds__(256) track_loss_finalize_kernel(const double* __restrict__ loss_partial,
+                                                                  int n_blocks, double* loss) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < n_blocks; k += blockDim.x) s += loss_partial[k];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && red[0] != 0.0) atomicAdd(loss, red[0]);
 }
 
 }  // namespace
@@ -175,7 +222,9 @@ __global__ void __launch_bounds__(256) track_kernel(const float* __restrict__ X,
 int track_blocks() { return 2 * device_sm_count(); }
 
 size_t track_workspace_bytes(const gs_batch& batch) {
-  return (size_t)track_blocks() * batch.B * 6 * sizeof(double);
+  // the pose partials of all slots, or (deterministic form, one slot at a
+  // time) one slot's and the blocks' loss sums
+  return (size_t)track_blocks() * (size_t)std::max(batch.B * 6, 7) * sizeof(double);
 }
 
 cudaError_t launch_track(const float* X, int n_points, const int32_t* obs_point, const float* obs_xy,
@@ -184,12 +233,37 @@ cudaError_t launch_track(const float* X, int n_points, const int32_t* obs_point,
                          double* g_pose_tangent, uint32_t* n_masked, void* ws, cudaStream_t st) {
   const int nb = track_blocks();
   double* partial = reinterpret_cast<double*>(ws);
-  track_kernel<<<nb, 256, 0, st>>>(X, n_points, obs_point, reinterpret_cast<const float2*>(obs_xy),
-                                   view_obs_offset, cams, batch, delta, weight, loss, grad_X,
-                                   n_masked, partial);
+  track_kernel<false><<<nb, 256, 0, st>>>(X, n_points, obs_point, reinterpret_cast<const float2*>(obs_xy),
+                                          view_obs_offset, cams, batch, delta, weight, loss, grad_X, n_masked,
+                                          partial, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_pose_partials_finalize(partial, nb, batch, cams.n_cams, g_pose_tangent, st);
+}
+
+cudaError_t launch_track_det(const float* X, int n_points, const int32_t* obs_point, const float* obs_xy,
+                             const int64_t* view_obs_offset, const gs_cameras& cams, const gs_batch& batch,
+                             float delta, float weight, double* loss, float* grad_X, double* g_pose_tangent,
+                             uint32_t* n_masked, void* ws, cudaStream_t st) {
+  const int nb = track_blocks();
+  double* partial = reinterpret_cast<double*>(ws);
+  double* loss_partial = partial + (size_t)nb * 6;
+  // one slot per launch, in slot order: the additions into a point's
+  // gradient, the pose tangent and the loss then come in a fixed order
+  for (int b = 0; b < batch.B; ++b) {
+    gs_batch one = batch;
+    one.B = 1;
+    one.views = batch.views + b;
+    track_kernel<true><<<nb, 256, 0, st>>>(X, n_points, obs_point, reinterpret_cast<const float2*>(obs_xy),
+                                           view_obs_offset, cams, one, delta, weight, loss, grad_X, n_masked,
+                                           partial, loss_partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_pose_partials_finalize(partial, nb, one, cams.n_cams, g_pose_tangent, st);
+    if (e != cudaSuccess) return e;
+    if (loss) track_loss_finalize_kernel<<<1, 256, 0, st>>>(loss_partial, nb, loss);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace gs

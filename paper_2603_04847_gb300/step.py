@@ -77,13 +77,27 @@ class Renderer:
                       self.n_contrib, Rt)
         mark("render_fwd")
 
+    def zero_records(self):
+        """Zeroes the screen-space records of the (atomic) backward on the
+        current stream, so that a later backward(records_zeroed=True) skips
+        it; nothing to do for the deterministic backward, which writes every
+        record."""
+        if not self.deterministic and self.dtype == torch.float32:
+            gs_zero(self.ws_bwd[:self.batch.B * self.n * 48])
+
     def backward(self, g: Gaussians, dg: Gaussians, g_tangent: torch.Tensor, v_image=None, target=None,
-                 l1_weight: float = 1.0, loss=None, Rt: torch.Tensor = None, mark=_nomark):
+                 l1_weight: float = 1.0, loss=None, Rt: torch.Tensor = None, mark=_nomark,
+                 records_zeroed: bool = False):
         # gs_render_bwd is exactly these two calls; issuing them separately
-        # lets a caller time each half
-        raster = gs_raster_bwd_det if self.deterministic else gs_raster_bwd
-        raster(g, self.cams, self.batch, self.proj, self.tl, self.bg, self.image, self.T_final,
-               self.n_contrib, v_image, target, l1_weight, loss, self.ws_bwd, Rt)
+        # lets a caller time each half.  records_zeroed: zero_records() was
+        # issued before (on any stream ordered before this one)
+        if self.deterministic:
+            gs_raster_bwd_det(g, self.cams, self.batch, self.proj, self.tl, self.bg, self.image, self.T_final,
+                              self.n_contrib, v_image, target, l1_weight, loss, self.ws_bwd, Rt)
+        else:
+            gs_raster_bwd(g, self.cams, self.batch, self.proj, self.tl, self.bg, self.image, self.T_final,
+                          self.n_contrib, v_image, target, l1_weight, loss, self.ws_bwd, Rt,
+                          records_zeroed=records_zeroed and self.dtype == torch.float32)
         mark("raster_bwd")
         gs_project_bwd(g, self.cams, self.batch, self.proj, dg, g_tangent, self.ws_bwd, Rt)
         mark("project_bwd")
@@ -174,8 +188,9 @@ class JointStep:
         # scene and its layout is recomputed on the device at the start of
         # every step, so next_batch() takes views of any sizes without
         # dropping a captured graph (batches of uneven views).
-        # deterministic: the compositing backward whose gradients do not
-        # depend on the order in which tiles run (gs_raster_bwd_det).
+        # deterministic: the step whose results do not depend on the order
+        # in which threads run (gs_raster_bwd_det, track_reproj_fwd_bwd_det):
+        # two runs from the same state give bit-identical parameters.
         self.dynamic_batch = bool(dynamic_batch)
         self.deterministic = bool(deterministic)
         self.h = hyper or Hyper()
@@ -322,6 +337,11 @@ class JointStep:
                 extra = [] if self.merged_tracks else [self.gX]   # merged: gX is dg.mean
                 for t in self.dg.tensors() + extra + [self.g_tan, self.loss, self.n_masked]:
                     gs_zero(t)
+                # the backward's screen-space records too: a memset of B N 48
+                # bytes, here beside the compute-bound compositing instead of
+                # in front of the backward
+                for r in self.renderers:
+                    r.zero_records()
                 self._gather_targets()
                 # the track term: done before the join, so its += into the
                 # pose tangent (and, merged, into dg.mean) precedes the
@@ -329,7 +349,8 @@ class JointStep:
                 if h.lambda_ba != 0.0:
                     track_reproj_fwd_bwd(self.X, self.obs_point, self.obs_xy, self.view_obs_offset, self.cams,
                                          self.batch, h.huber_delta, h.lambda_ba, self.loss[1:2], self.gX,
-                                         self.g_tan, self.n_masked, self.track_ws, self.Rt)
+                                         self.g_tan, self.n_masked, self.track_ws, self.Rt,
+                                         deterministic=self.deterministic)
 
         # every slot's offsets first: the side stream gathers all slots'
         # targets once the first slot is sorted
@@ -348,10 +369,10 @@ class JointStep:
                               self.loss[0:1], r.v_image, r.ws_photo, self.Rt)
                 mark("photo")
                 r.backward(self.g, self.dg, self.g_tan, v_image=r.v_image, loss=self.loss[0:1], Rt=self.Rt,
-                           mark=mark)
+                           mark=mark, records_zeroed=True)
             else:
                 r.backward(self.g, self.dg, self.g_tan, target=tgt, l1_weight=h.l1_weight, loss=self.loss[0:1],
-                           Rt=self.Rt, mark=mark)
+                           Rt=self.Rt, mark=mark, records_zeroed=True)
         if not joined:
             fork()
             main.wait_stream(side)
@@ -400,7 +421,8 @@ class JointStep:
         # batches), track + finalize 2 (unless lambda_BA = 0), step advance
         # 1, Adam (all groups) 1, pose 1 (unless frozen)
         nr = len(self.renderers)
-        return (per_render + nr + (nr if self.dynamic_batch else 0) + (2 if self.h.lambda_ba != 0.0 else 0) + 1 +
+        track = (3 * self.batch.B if self.deterministic else 2) if self.h.lambda_ba != 0.0 else 0
+        return (per_render + nr + (nr if self.dynamic_batch else 0) + track + 1 +
                 1 + (0 if self.h.freeze_poses else 1))
 
     # -- CUDA graph ----------------------------------------------------------

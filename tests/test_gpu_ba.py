@@ -119,7 +119,9 @@ def test_schur_elimination_and_back_substitution_match_the_oracle(lam):
     dp = torch.full((P, 3), np.nan, dtype=torch.float64, device="cuda")
     sfm_ba_back_substitute(Vinv, Vp, gp, Wo, oc_d, off_d, ids_d, dev(dc, torch.float64), dp)
     torch.cuda.synchronize()
-    assert _close(S.cpu().numpy(), S_e) and _close(rhs.cpu().numpy(), rhs_e)
+    # S is symmetric and only its lower triangle is formed (all the camera
+    # solve reads)
+    assert _close(np.tril(S.cpu().numpy()), np.tril(S_e)) and _close(rhs.cpu().numpy(), rhs_e)
     assert _close(Vinv.cpu().numpy().reshape(-1, 3, 3), Vinv_e)
     assert _close(dp.cpu().numpy(), dp_e)
     assert not np.any(dp.cpu().numpy()[-1])         # the unobserved point stays put

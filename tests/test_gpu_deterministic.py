@@ -12,7 +12,11 @@ order, so its results do not depend on the order in which tiles run.
   runs and equals the atomic backward to FP32 summation rounding.
 - When the tile lists do not hold every instance (capacity overflow) the
   gradients are zero and the overflow is flagged, like the atomic path's
-  empty-gradient behaviour for missing instances."""
+  empty-gradient behaviour for missing instances.
+- The deterministic track term (track_reproj_fwd_bwd_det, a launch per
+  slot) is bit-identical across runs and equals the default term to FP32
+  summation rounding.  The whole deterministic joint step is checked in
+  test_gpu_joint_step.py."""
 import numpy as np
 import pytest
 
@@ -113,3 +117,38 @@ def test_overflow_gives_zero_gradients_and_a_flag():
     b = gpu_backward(ref, g2, v_image=f32(np.ones((ref.batch.n_pixels, 3))))
     for k in KEYS + ("tangent",):
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+def test_track_term_bit_identical_and_equal_to_the_atomic_term():
+    from paper_2603_04847_gb300 import Batch, Cameras
+    from paper_2603_04847_gb300.core import track_reproj_fwd_bwd, track_workspace_bytes
+    w = synth.make_workload("mid", n_tracks=20000)
+    tr = w["tracks"]
+    cams = Cameras.from_numpy(w["wh"], w["K"], w["Rt"])
+    batch = Batch(cams, [3, 0, 5, 7, 1, 3])          # a repeated view too
+    dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    rng = np.random.default_rng(0)
+    X = dev(tr["X"] + rng.normal(0, 0.01, tr["X"].shape), torch.float32)
+    op = dev(tr["obs_point"], torch.int32)
+    xy = dev(rng.uniform(0, 800, (len(tr["obs_point"]), 2)), torch.float32)
+    voff = dev(tr["view_obs_offset"], torch.int64)
+    ws = torch.empty(track_workspace_bytes(batch), dtype=torch.uint8, device="cuda")
+    res = []
+    for det in (True, True, False):
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        gX = torch.zeros_like(X)
+        gt = torch.zeros((cams.V, 6), dtype=torch.float64, device="cuda")
+        nm = torch.zeros(1, dtype=torch.int32, device="cuda")
+        track_reproj_fwd_bwd(X, op, xy, voff, cams, batch, 1.0, 0.5, loss, gX, gt, nm, ws, deterministic=det)
+        torch.cuda.synchronize()
+        res.append((loss.item(), gX.cpu().numpy(), gt.cpu().numpy(), int(nm.item())))
+    (l0, g0, t0, m0), (l1, g1, t1, m1), (la, ga, ta, ma) = res
+    assert l0 == l1 and m0 == m1 == ma
+    np.testing.assert_array_equal(g0, g1)
+    np.testing.assert_array_equal(t0, t1)
+    # the default term runs all slots in one launch, so its per-thread
+    # float sums group the observations differently
+    assert abs(l0 - la) <= 1e-6 * abs(la)
+    assert rel_linf(g0, ga) <= 1e-6
+    assert rel_linf(t0, ta) <= 1e-5
+    assert np.abs(g0).max() > 0 and np.abs(t0).max() > 0

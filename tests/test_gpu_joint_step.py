@@ -70,7 +70,7 @@ def _inputs(w, merged):
     return params, X, wh, K, Rt, targets, obs_point, obs_view, xy, tr["view_obs_offset"]
 
 
-def _gpu_step(w, views, inputs, hyper, merged):
+def _gpu_step(w, views, inputs, hyper, merged, deterministic=False, replays=1):
     from paper_2603_04847_gb300 import Cameras, Gaussians, Hyper, JointStep
     params, X, wh, K, Rt, targets, obs_point, obs_view, xy, voff = inputs
     cams = Cameras.from_numpy(wh, K, Rt)
@@ -82,24 +82,27 @@ def _gpu_step(w, views, inputs, hyper, merged):
     h = Hyper(**hyper)
     js = JointStep(g, cams, dev(X, torch.float32), dev(obs_point, torch.int32), dev(xy, torch.float32),
                    dev(voff, torch.int64), dev(tg, torch.float32), off, views, h, merged_tracks=merged,
-                   dynamic_batch=len(views) > 1)
+                   dynamic_batch=len(views) > 1, deterministic=deterministic)
     js.ensure_capacity()
     js.capture(warmup=0)     # capturing does not run the step
-    js.run()
+    for _ in range(replays):
+        js.run()
     torch.cuda.synchronize()
     assert js.status_flags() == 0
     return js
 
 
-@pytest.mark.parametrize("variant", list(VARIANTS))
+@pytest.mark.parametrize("variant", list(VARIANTS) + ["full_deterministic", "merged_tracks_deterministic"])
 @pytest.mark.parametrize("kind", ["tiny", "uneven_batch"])
 def test_graph_replayed_step_equals_the_oracle_iteration(kind, variant):
     w, views = _workload(kind)
+    det = variant.endswith("_deterministic")
+    variant = variant.replace("_deterministic", "")
     merged = variant == "merged_tracks"
     hyper = dict(HYPER, **VARIANTS[variant])
     inputs = _inputs(w, merged)
     params, X, wh, K, Rt, targets, obs_point, obs_view, xy, _ = inputs
-    js = _gpu_step(w, views, inputs, hyper, merged)
+    js = _gpu_step(w, views, inputs, hyper, merged, deterministic=det)
     V = len(wh)
     exp = oracle.joint_step(params, X, Rt, np.zeros((V, 6)), wh, K, views, targets, obs_point, obs_view, xy, hyper,
                             {}, 1, merged_tracks=merged)
@@ -138,3 +141,19 @@ def test_graph_replayed_step_equals_the_oracle_iteration(kind, variant):
         # the FP32 Adam step (bias corrections in float) is exact to ~3e-5
         np.testing.assert_allclose(xi, exp["xi"], rtol=1e-4, atol=1e-9)
         np.testing.assert_allclose(js.Rt.cpu().numpy(), exp["Rt"], rtol=0, atol=2e-6)
+
+
+@pytest.mark.parametrize("merged", [False, True])
+def test_deterministic_step_is_bit_identical_across_runs(merged):
+    """Two JointSteps from the same state, each replaying its graph three
+    times on the uneven batch: with the deterministic backward and track
+    term, every parameter, pose and both losses agree bit for bit."""
+    w, views = _workload("uneven_batch")
+    inputs = _inputs(w, merged)
+    outs = []
+    for _ in range(2):
+        js = _gpu_step(w, views, inputs, HYPER, merged, deterministic=True, replays=3)
+        outs.append([t.cpu().numpy().copy() for t in list(js.g.tensors()) + [js.X, js.xi, js.Rt, js.loss,
+                                                                             js.g_tan]])
+    for a, b in zip(*outs):
+        np.testing.assert_array_equal(a, b)
