@@ -575,8 +575,8 @@ def ncu_traffic(stage, workload, js, model_bytes=None):
     import hashlib
     from paper_2603_04847_gb300.core import gs_get_tuning
     name = NCU_SUMMARY.get(stage)
-    if name is None:
-        return None
+    if name is None or getattr(js, "deterministic", False):
+        return None   # no capture of this stage, or another instantiation of its kernel
     try:
         with open(os.path.join(ROOT, "profiles", name)) as f:
             kv = dict(line.strip().split(": ", 1) for line in f if ": " in line and line.startswith("    "))
