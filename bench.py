@@ -629,13 +629,6 @@ def algorithmic_model(js):
         "track": M_b * 24 + min(M_b, js.X.shape[0]) * 24,
         "adam": (N * (7 + 4 + 3 * K) + js.X.shape[0] * 3) * 4 * 7,
     }
-    if getattr(js, "fused_adam", False):
-        # the projection backward applies the Gaussians' Adam step: it reads
-        # the parameters and the two moments and writes parameters, moments
-        # and gradient (no earlier gradient read); Adam's launch is left with
-        # the track points
-        model["project_bwd"] = pbytes + vis * 36 + B * N * 4 + 2 * pbytes + 4 * pbytes
-        model["adam"] = js.X.shape[0] * 3 * 4 * 7
     return model, dict(instances=I, visible_records=vis, pairs_bwd=pairs_bwd, added=added, pixels=P,
                        obs_in_batch=M_b, pairs_brute=pairs_brute)
 

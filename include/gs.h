@@ -439,29 +439,6 @@ gs_status gs_project_bwd(const gs_gaussians* g, const gs_cameras* cams,
                          void* ws, size_t ws_bytes, gs_stream stream);
 
 /*
- * gs_project_bwd_adam — gs_project_bwd fused with the Adam step of the
- * Gaussians (Algorithm 1, "Backpropagate" then "Update Gaussians"; Adam as
- * Sec. 3.3 trains with), for a step whose Gaussian gradient is this
- * batch's projection backward alone: each thread, having summed its
- * Gaussian's gradient over the batch's views, applies Adam to its
- * parameters at once instead of writing the gradient for a separate pass.
- * groups [5]: mean, log_scale, quat, opacity_logit, sh, in that order; each
- * group's p must be the matching array of g (updated in place), n its
- * length, m and v its moments (quat's 16-byte aligned), lr its rate (the
- * group's g field is ignored); beta1, beta2, eps and the device step t as
- * gs_adam (bias corrections 1 - beta^t).  Every Gaussian gets its step,
- * those no view sees with a zero gradient.  dg (may be NULL): when given,
- * receives this batch's gradient (written, not added).  g_pose_tangent:
- * += as gs_project_bwd.  ws: the workspace of gs_raster_bwd.
- */
-gs_status gs_project_bwd_adam(const gs_gaussians* g, const gs_cameras* cams,
-                              const gs_batch* batch, const gs_projected* proj,
-                              const gs_gaussian_grads* dg, double* g_pose_tangent,
-                              const gs_adam_group* groups, float beta1,
-                              float beta2, float eps, const int32_t* step,
-                              void* ws, size_t ws_bytes, gs_stream stream);
-
-/*
  * track_reproj_fwd_bwd — Eq. 6 for the observations of the batch's views
  * (Algorithm 1, "Joint BA loss on track points").  Observations are
  * bucketed by camera: those of camera i are obs [view_obs_offset[i],

@@ -396,28 +396,6 @@ def gs_project_bwd(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, d
           "gs_project_bwd")
 
 
-def gs_project_bwd_adam(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, dg, g_pose_tangent,
-                        moments, lrs, beta1: float, beta2: float, eps: float, step: torch.Tensor, ws: torch.Tensor,
-                        Rt=None, stream=None):
-    """The projection backward fused with the Adam step of the Gaussians
-    (gs_project_bwd_adam): moments = [(m, v)] and lrs for mean, log_scale,
-    quat, opacity_logit, sh; dg (or None) receives this batch's gradient."""
-    lib = _lib.load()
-    if g.f64:
-        raise _lib.GsError("gs_project_bwd_adam is FP32 only")
-    _need_cuda(g_pose_tangent, ws, step)
-    arr = (_lib.gs_adam_group * 5)()
-    for i, (p, (m, v), lr) in enumerate(zip(g.tensors(), moments, lrs)):
-        _need_cuda(p, m, v)
-        arr[i] = _lib.gs_adam_group(p.data_ptr(), 0, m.data_ptr(), v.data_ptr(), p.numel(), float(lr), 0)
-    gc, cc, bc, pc = g.c(), cams.c(Rt), batch.c(), proj.c()
-    dgc = dg.grads_c() if dg is not None else None
-    check(lib.gs_project_bwd_adam(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc),
-                                  ctypes.byref(dgc) if dgc is not None else None, _p(g_pose_tangent), arr,
-                                  float(beta1), float(beta2), float(eps), _p(step), _p(ws), ws.numel(),
-                                  _stream(stream)), "gs_project_bwd_adam")
-
-
 def photo_loss_workspace_bytes(batch: Batch) -> int:
     lib = _lib.load()
     bc = batch.c()

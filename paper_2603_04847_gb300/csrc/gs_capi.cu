@@ -312,37 +312,6 @@ gs_status gs_project_bwd(const gs_gaussians* g, const gs_cameras* cams, const gs
   return GS_OK;
 }
 
-gs_status gs_project_bwd_adam(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
-                              const gs_projected* proj, const gs_gaussian_grads* dg, double* g_pose_tangent,
-                              const gs_adam_group* groups, float beta1, float beta2, float eps,
-                              const int32_t* step, void* ws, size_t ws_bytes, gs_stream stream) {
-  gs_status s;
-  const char* who = "gs_project_bwd_adam";
-  if ((s = check_bwd_common(g, cams, batch, proj, ws, ws_bytes, who))) return s;
-  if (!g_pose_tangent || !groups || !step) return fail(GS_ERR_ARG, "%s: null argument", who);
-  if (dg && (!dg->mean || !dg->log_scale || !dg->quat || !dg->opacity_logit || !dg->sh))
-    return fail(GS_ERR_ARG, "%s: null gradient array", who);
-  if (dg && !aligned(dg->quat, 16)) return fail(GS_ERR_ARG, "%s: grad quat must be 16-byte aligned", who);
-  const int K3 = 3 * (g->sh_degree + 1) * (g->sh_degree + 1);
-  const float* params[5] = {g->mean, g->log_scale, g->quat, g->opacity_logit, g->sh};
-  const int64_t widths[5] = {3, 3, 4, 1, K3};
-  for (int i = 0; i < 5; ++i) {
-    const gs_adam_group& G = groups[i];
-    if (G.p != params[i] || !G.m || !G.v || G.n != widths[i] * (int64_t)g->n)
-      return fail(GS_ERR_ARG, "%s: group %d must be the Gaussians' parameter array %d (p, m, v, n)", who, i, i);
-    if (!std::isfinite(G.lr)) return fail(GS_ERR_NONFINITE, "%s: learning rate of group %d", who, i);
-  }
-  if (!aligned(groups[2].m, 16) || !aligned(groups[2].v, 16))
-    return fail(GS_ERR_ARG, "%s: the quat moments must be 16-byte aligned", who);
-  const size_t vb = v2d_bytes(g->n, *batch);
-  const float* v2d = reinterpret_cast<const float*>(ws);
-  double* partial = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + vb);
-  const cudaError_t e = launch_project_bwd_adam(*g, *cams, *batch, *proj, v2d, dg, partial, g_pose_tangent, groups,
-                                                beta1, beta2, eps, step, (cudaStream_t)stream);
-  if (e != cudaSuccess) return cuda_fail(e, who);
-  return GS_OK;
-}
-
 gs_status gs_render_bwd(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
                         const gs_projected* proj, const uint32_t* vals, const uint32_t* ranges,
                         const float* bg, const float* image, const float* T_final,

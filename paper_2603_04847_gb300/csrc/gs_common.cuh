@@ -180,17 +180,6 @@ __device__ inline void load_slot_cams(const CamsT<T>& cams, const gs_batch& batc
   }
 }
 
-// One Adam step of one parameter (Algorithm 1, "Update Gaussians"; Adam as
-// Sec. 3.3 trains with): a = lr / (1 - beta1^t), rb2 = 1 / (1 - beta2^t).
-// Shared by the Adam kernels and the projection backward's fused update, so
-// that both give the same bits.
-__device__ inline void adam_elem(float& p, float g, float& m, float& v, float a, float beta1, float beta2,
-                                 float rb2, float eps) {
-  m = beta1 * m + (1.f - beta1) * g;
-  v = beta2 * v + (1.f - beta2) * g * g;
-  p -= a * m / (sqrtf(v * rb2) + eps);
-}
-
 __device__ inline void set_flag(int32_t* status, int32_t flag) {
   if (status) atomicOr(status, flag);
 }

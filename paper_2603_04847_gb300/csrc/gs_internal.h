@@ -28,10 +28,6 @@ cudaError_t launch_project_bwd_f64(const gs_gaussians_f64& g, const gs_cameras_f
 cudaError_t launch_project_bwd(const gs_gaussians& g, const gs_cameras& cams, const gs_batch& batch,
                                const gs_projected& proj, const float* v2d, const gs_gaussian_grads& dg,
                                double* partial, double* g_pose_tangent, cudaStream_t st);
-cudaError_t launch_project_bwd_adam(const gs_gaussians& g, const gs_cameras& cams, const gs_batch& batch,
-                                    const gs_projected& proj, const float* v2d, const gs_gaussian_grads* dg,
-                                    double* partial, double* g_pose_tangent, const gs_adam_group* groups,
-                                    float beta1, float beta2, float eps, const int32_t* step, cudaStream_t st);
 
 int sort_tile_bits(int n_tiles_total);
 size_t sort_workspace_bytes(int N, const gs_batch& batch, size_t capacity);

@@ -193,6 +193,13 @@ struct AdamGroups {
   int n;
 };
 
+__device__ inline void adam_elem(float& p, float g, float& m, float& v, float a, float beta1, float beta2,
+                                 float rb2, float eps) {
+  m = beta1 * m + (1.f - beta1) * g;
+  v = beta2 * v + (1.f - beta2) * g * g;
+  p -= a * m / (sqrtf(v * rb2) + eps);
+}
+
 __global__ void __launch_bounds__(256) adam_groups_kernel(AdamGroups G, float beta1, float beta2, float eps,
                                                           const int32_t* __restrict__ step) {
   const int t = *step;

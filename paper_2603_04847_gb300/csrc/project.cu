@@ -392,47 +392,10 @@ constexpr size_t project_bwd_smem() {
 
 // 3 blocks of 128 per SM for FP32 (168 registers); the FP64 instantiation
 // is a checking path and takes what it needs
-// The projection backward fused with Adam (gs_project_bwd_adam): the
-// parameter groups mean, log_scale, quat, opacity_logit, sh in that order.
-struct FusedAdam {
-  float* p[5];
-  float* m[5];
-  float* v[5];
-  float lr[5];
-  float beta1, beta2, eps;
-  const int32_t* step;
-};
-
-// Adam on the block's contiguous slice of the SH coefficients, the
-// gradients taken from shared memory (one padded column per thread);
-// dg_sh (may be null) receives the gradients.
-template <int KK>
-__device__ inline void adam_sh_block(const FusedAdam& fa, size_t j0, int n_local,
-                                     float (*s_v)[kProjThreads + 1], float* __restrict__ dg_sh, float a,
-                                     float rb2) {
-  const size_t base = j0 * KK;
-  for (int f = threadIdx.x; f < n_local * KK; f += kProjThreads) {
-    const int jl = f / KK;
-    const float gv = s_v[f - jl * KK][jl];
-    const size_t i = base + f;
-    float pv = fa.p[4][i], mv = fa.m[4][i], vv = fa.v[4][i];
-    adam_elem(pv, gv, mv, vv, a, fa.beta1, fa.beta2, rb2, fa.eps);
-    fa.p[4][i] = pv;
-    fa.m[4][i] = mv;
-    fa.v[4][i] = vv;
-    if (dg_sh) dg_sh[i] = gv;
-  }
-}
-
-template <typename T, int DEG, bool kAdam = false>
+template <typename T, int DEG>
 __global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? 3 : 1) project_bwd_kernel(
     GaussT<T> g, CamsT<T> cams, gs_batch batch, ProjT<T> proj, const T* __restrict__ v2d, GradsT<T> dg,
-    double* __restrict__ partial, FusedAdam fa) {
-  // kAdam (FP32): this batch's gradient is not added to dg's earlier
-  // contents; it goes into an Adam step of every parameter (also of the
-  // Gaussians no view sees, whose gradient is zero) and into dg only when
-  // dg.mean is not null
-  static_assert(!kAdam || sizeof(T) == 4, "the fused Adam update is FP32");
+    double* __restrict__ partial) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   __shared__ SlotCamT<T> sc[GS_MAX_BATCH];
   // per warp and view: the warp's six pose-tangent sums (FP32 in the FP32
@@ -671,22 +634,20 @@ __global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? 3 : 1) project_
     }
   }
 
-  const bool write_grad = !kAdam || dg.mean != nullptr;
-  if (active && (any || kAdam)) {
+  if (active && any) {
     // the accumulators are read before any of them is written, so the
     // thread waits one memory latency for all of them
-    T acc_ls[3] = {T(0), T(0), T(0)}, acc_mu[3] = {T(0), T(0), T(0)};
-    Quat4<T> cq{T(0), T(0), T(0), T(0)};
-    T acc_o = T(0);
-    if constexpr (!kAdam) {
+    T* gls = dg.log_scale + 3 * (size_t)j;
+    T* gqp = dg.quat + 4 * (size_t)j;
+    T* gm = dg.mean + 3 * (size_t)j;
+    T acc_ls[3], acc_mu[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        acc_ls[k] = dg.log_scale[3 * (size_t)j + k];
-        acc_mu[k] = dg.mean[3 * (size_t)j + k];
-      }
-      cq = load_quat(dg.quat, j);
-      acc_o = dg.opacity_logit[j];
+    for (int k = 0; k < 3; ++k) {
+      acc_ls[k] = gls[k];
+      acc_mu[k] = gm[k];
     }
+    Quat4<T> cq = load_quat(dg.quat, j);
+    T acc_o = dg.opacity_logit[j];
     // --- M = R diag(s): G_R = G_M diag(s); the scale gradient was summed in
     // each view's eigenframe
     T GR[9];
@@ -694,9 +655,8 @@ __global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? 3 : 1) project_
     for (int r = 0; r < 3; ++r)
 #pragma unroll
       for (int k = 0; k < 3; ++k) GR[3 * r + k] = GM[3 * r + k] * G.s[k];
-    T out_ls[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) out_ls[k] = acc_ls[k] + gls_eig[k];
+    for (int k = 0; k < 3; ++k) gls[k] = acc_ls[k] + gls_eig[k];
     const T w = G.qn[0], x = G.qn[1], y = G.qn[2], zq = G.qn[3];
     T vq[4];
     vq[0] = -T(2) * zq * GR[1] + T(2) * y * GR[2] + T(2) * zq * GR[3] - T(2) * x * GR[5] -
@@ -712,60 +672,15 @@ __global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? 3 : 1) project_
     cq.y += (vq[1] - dq * x) * G.qinv;
     cq.z += (vq[2] - dq * y) * G.qinv;
     cq.w += (vq[3] - dq * zq) * G.qinv;
-    T out_mu[3];
+    store_quat(gqp, cq);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) out_mu[i] = acc_mu[i] + vmu[i];
-    const T out_o = acc_o + vol * G.o * (T(1) - G.o);
-    if (write_grad) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        dg.log_scale[3 * (size_t)j + k] = out_ls[k];
-        dg.mean[3 * (size_t)j + k] = out_mu[k];
-      }
-      store_quat(dg.quat + 4 * (size_t)j, cq);
-      dg.opacity_logit[j] = out_o;
-    }
-    if constexpr (kAdam) {
-      const int t = *fa.step;
-      const float bc1 = 1.f - powf(fa.beta1, (float)t);
-      const float rb2 = 1.f / (1.f - powf(fa.beta2, (float)t));
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const size_t i = 3 * (size_t)j + k;
-        float pv = fa.p[0][i], mv = fa.m[0][i], vv = fa.v[0][i];
-        adam_elem(pv, out_mu[k], mv, vv, fa.lr[0] / bc1, fa.beta1, fa.beta2, rb2, fa.eps);
-        fa.p[0][i] = pv; fa.m[0][i] = mv; fa.v[0][i] = vv;
-        float ps = fa.p[1][i], ms = fa.m[1][i], vs = fa.v[1][i];
-        adam_elem(ps, out_ls[k], ms, vs, fa.lr[1] / bc1, fa.beta1, fa.beta2, rb2, fa.eps);
-        fa.p[1][i] = ps; fa.m[1][i] = ms; fa.v[1][i] = vs;
-      }
-      float4 pq = reinterpret_cast<float4*>(fa.p[2])[j], mq = reinterpret_cast<float4*>(fa.m[2])[j],
-             vq4 = reinterpret_cast<float4*>(fa.v[2])[j];
-      const float aq = fa.lr[2] / bc1;
-      adam_elem(pq.x, cq.x, mq.x, vq4.x, aq, fa.beta1, fa.beta2, rb2, fa.eps);
-      adam_elem(pq.y, cq.y, mq.y, vq4.y, aq, fa.beta1, fa.beta2, rb2, fa.eps);
-      adam_elem(pq.z, cq.z, mq.z, vq4.z, aq, fa.beta1, fa.beta2, rb2, fa.eps);
-      adam_elem(pq.w, cq.w, mq.w, vq4.w, aq, fa.beta1, fa.beta2, rb2, fa.eps);
-      reinterpret_cast<float4*>(fa.p[2])[j] = pq;
-      reinterpret_cast<float4*>(fa.m[2])[j] = mq;
-      reinterpret_cast<float4*>(fa.v[2])[j] = vq4;
-      float po = fa.p[3][j], mo = fa.m[3][j], vo = fa.v[3][j];
-      adam_elem(po, out_o, mo, vo, fa.lr[3] / bc1, fa.beta1, fa.beta2, rb2, fa.eps);
-      fa.p[3][j] = po; fa.m[3][j] = mo; fa.v[3][j] = vo;
-    }
+    for (int i = 0; i < 3; ++i) gm[i] = acc_mu[i] + vmu[i];
+    dg.opacity_logit[j] = acc_o + vol * G.o * (T(1) - G.o);
   }
   // SH gradients: through shared memory, then one coalesced read-modify-write
-  // of the block's contiguous slice of dg.sh (or, fused, the Adam step of
-  // the slice)
+  // of the block's contiguous slice of dg.sh
   __syncthreads();
-  if constexpr (kAdam) {
-    const int t = *fa.step;
-    const float bc1 = 1.f - powf(fa.beta1, (float)t);
-    const float rb2 = 1.f / (1.f - powf(fa.beta2, (float)t));
-    adam_sh_block<K * 3>(fa, (size_t)j0, n_local, s_vsh, write_grad ? dg.sh : nullptr, fa.lr[4] / bc1, rb2);
-  } else {
-    add_sh_block<T, K * 3>(dg.sh + (size_t)j0 * K * 3, n_local, s_vsh);
-  }
+  add_sh_block<T, K * 3>(dg.sh + (size_t)j0 * K * 3, n_local, s_vsh);
   __syncthreads();
   for (int i = threadIdx.x; i < batch.B * 6; i += blockDim.x) {
     T t = T(0);
@@ -794,10 +709,9 @@ cudaError_t project_fwd_t(const GaussT<T>& g, const CamsT<T>& cams, const gs_bat
   return cudaGetLastError();
 }
 
-template <typename T, int DEG, bool kAdam>
+template <typename T, int DEG>
 cudaError_t project_bwd_deg(const GaussT<T>& g, const CamsT<T>& cams, const gs_batch& batch, const ProjT<T>& proj,
-                            const T* v2d, const GradsT<T>& dg, double* partial, int blocks, const FusedAdam& fa,
-                            cudaStream_t st) {
+                            const T* v2d, const GradsT<T>& dg, double* partial, int blocks, cudaStream_t st) {
   constexpr size_t smem = project_bwd_smem<T, DEG>();
   // the opt-in for more than 48 KB of shared memory, once per device
   static bool configured[64] = {false};
@@ -805,27 +719,26 @@ cudaError_t project_bwd_deg(const GaussT<T>& g, const CamsT<T>& cams, const gs_b
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || !configured[dev]) {
-    e = cudaFuncSetAttribute(project_bwd_kernel<T, DEG, kAdam>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+    e = cudaFuncSetAttribute(project_bwd_kernel<T, DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
-  project_bwd_kernel<T, DEG, kAdam><<<blocks, kProjThreads, smem, st>>>(g, cams, batch, proj, v2d, dg, partial, fa);
+  project_bwd_kernel<T, DEG><<<blocks, kProjThreads, smem, st>>>(g, cams, batch, proj, v2d, dg, partial);
   return cudaGetLastError();
 }
 
-template <typename T, bool kAdam = false>
+template <typename T>
 cudaError_t project_bwd_t(const GaussT<T>& g, const CamsT<T>& cams, const gs_batch& batch, const ProjT<T>& proj,
                           const T* v2d, const GradsT<T>& dg, double* partial, double* g_pose_tangent,
-                          cudaStream_t st, const FusedAdam& fa = FusedAdam{}) {
+                          cudaStream_t st) {
   const int blocks = project_bwd_blocks(g.n);
   if (blocks == 0) return cudaSuccess;
   cudaError_t e;
   switch (g.sh_degree) {
-    case 0: e = project_bwd_deg<T, 0, kAdam>(g, cams, batch, proj, v2d, dg, partial, blocks, fa, st); break;
-    case 1: e = project_bwd_deg<T, 1, kAdam>(g, cams, batch, proj, v2d, dg, partial, blocks, fa, st); break;
-    case 2: e = project_bwd_deg<T, 2, kAdam>(g, cams, batch, proj, v2d, dg, partial, blocks, fa, st); break;
-    default: e = project_bwd_deg<T, 3, kAdam>(g, cams, batch, proj, v2d, dg, partial, blocks, fa, st); break;
+    case 0: e = project_bwd_deg<T, 0>(g, cams, batch, proj, v2d, dg, partial, blocks, st); break;
+    case 1: e = project_bwd_deg<T, 1>(g, cams, batch, proj, v2d, dg, partial, blocks, st); break;
+    case 2: e = project_bwd_deg<T, 2>(g, cams, batch, proj, v2d, dg, partial, blocks, st); break;
+    default: e = project_bwd_deg<T, 3>(g, cams, batch, proj, v2d, dg, partial, blocks, st); break;
   }
   if (e != cudaSuccess) return e;
   return launch_pose_partials_finalize(partial, blocks, batch, cams.n_cams, g_pose_tangent, st);
@@ -850,26 +763,6 @@ cudaError_t launch_project_bwd(const gs_gaussians& g, const gs_cameras& cams, co
                                double* partial, double* g_pose_tangent, cudaStream_t st) {
   return project_bwd_t<float>(view_of(g), view_of(cams), batch, view_of(proj), v2d, view_of(dg), partial,
                               g_pose_tangent, st);
-}
-
-cudaError_t launch_project_bwd_adam(const gs_gaussians& g, const gs_cameras& cams, const gs_batch& batch,
-                                    const gs_projected& proj, const float* v2d, const gs_gaussian_grads* dg,
-                                    double* partial, double* g_pose_tangent, const gs_adam_group* groups,
-                                    float beta1, float beta2, float eps, const int32_t* step, cudaStream_t st) {
-  FusedAdam fa;
-  for (int i = 0; i < 5; ++i) {
-    fa.p[i] = groups[i].p;
-    fa.m[i] = groups[i].m;
-    fa.v[i] = groups[i].v;
-    fa.lr[i] = groups[i].lr;
-  }
-  fa.beta1 = beta1;
-  fa.beta2 = beta2;
-  fa.eps = eps;
-  fa.step = step;
-  gs_gaussian_grads none{};
-  return project_bwd_t<float, true>(view_of(g), view_of(cams), batch, view_of(proj), v2d, view_of(dg ? *dg : none),
-                                    partial, g_pose_tangent, st, fa);
 }
 
 cudaError_t launch_project_bwd_f64(const gs_gaussians_f64& g, const gs_cameras_f64& cams, const gs_batch& batch,

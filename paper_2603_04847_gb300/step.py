@@ -13,7 +13,7 @@ import torch
 from . import _lib
 from .core import (Batch, Cameras, Gaussians, Projected, TileLists, adam_c, gs_adam_update, gs_adam_update_groups,
                    gs_gather_view_pixels, gs_photo_loss, gs_project, photo_loss_workspace_bytes,
-                   gs_project_bwd, gs_project_bwd_adam, gs_raster_bwd, gs_raster_bwd_det, gs_render_fwd, gs_sort_tiles,
+                   gs_project_bwd, gs_raster_bwd, gs_raster_bwd_det, gs_render_fwd, gs_sort_tiles,
                    gs_step_advance, gs_zero, new_status, pose_se3_update, render_bwd_det_workspace_bytes,
                    render_bwd_workspace_bytes, track_reproj_fwd_bwd,
                    track_workspace_bytes)
@@ -87,7 +87,7 @@ class Renderer:
 
     def backward(self, g: Gaussians, dg: Gaussians, g_tangent: torch.Tensor, v_image=None, target=None,
                  l1_weight: float = 1.0, loss=None, Rt: torch.Tensor = None, mark=_nomark,
-                 records_zeroed: bool = False, adam=None):
+                 records_zeroed: bool = False):
         # gs_render_bwd is exactly these two calls; issuing them separately
         # lets a caller time each half.  records_zeroed: zero_records() was
         # issued before (on any stream ordered before this one)
@@ -99,13 +99,7 @@ class Renderer:
                           self.n_contrib, v_image, target, l1_weight, loss, self.ws_bwd, Rt,
                           records_zeroed=records_zeroed and self.dtype == torch.float32)
         mark("raster_bwd")
-        if adam is not None:
-            # the projection backward fused with the Gaussians' Adam step: dg
-            # receives this batch's gradient (written, not added)
-            gs_project_bwd_adam(g, self.cams, self.batch, self.proj, dg, g_tangent, adam["moments"], adam["lrs"],
-                                adam["beta1"], adam["beta2"], adam["eps"], adam["step"], self.ws_bwd, Rt)
-        else:
-            gs_project_bwd(g, self.cams, self.batch, self.proj, dg, g_tangent, self.ws_bwd, Rt)
+        gs_project_bwd(g, self.cams, self.batch, self.proj, dg, g_tangent, self.ws_bwd, Rt)
         mark("project_bwd")
 
     def count_added(self, g: Gaussians, Rt: torch.Tensor = None) -> int:
@@ -186,7 +180,7 @@ class JointStep:
                  obs_xy: torch.Tensor, view_obs_offset: torch.Tensor, targets: torch.Tensor,
                  target_px_offset: np.ndarray, views, hyper: Hyper = None, mode: str = "batched",
                  capacity: int = 0, device="cuda", tile: int = 16, merged_tracks: bool = False,
-                 dynamic_batch: bool = False, deterministic: bool = False, fuse_adam: bool = True):
+                 dynamic_batch: bool = False, deterministic: bool = False):
         # merged_tracks: the "merged tracks" ablation variant, X_k = mu of a
         # Gaussian (obs_point then indexes Gaussians; X is ignored): the track
         # term reads the Gaussian means and adds its gradient into theirs.
@@ -199,10 +193,6 @@ class JointStep:
         # two runs from the same state give bit-identical parameters.
         self.dynamic_batch = bool(dynamic_batch)
         self.deterministic = bool(deterministic)
-        # fuse the Gaussians' Adam step into the projection backward when it
-        # alone forms their gradient (one renderer, track points apart);
-        # fuse_adam=False keeps the separate Adam launch
-        self.fused_adam = bool(fuse_adam) and mode == "batched" and not merged_tracks
         self.h = hyper or Hyper()
         self.merged_tracks = bool(merged_tracks)
         self.tile = int(tile)
@@ -340,25 +330,12 @@ class JointStep:
         h = self.h
         main = torch.cuda.current_stream()
         side = self._side_stream()
-        # batched, separate track points: the projection backward applies
-        # the Gaussians' Adam step itself (gs_project_bwd_adam), reading the
-        # step counter, which therefore advances first
-        fused = self.fused_adam
-        gs_step_advance(self.step_no)
-        ext = h.scene_extent
-        adam = None
-        if fused:
-            adam = dict(moments=[(a, b) for a, b in zip(self.m.tensors(), self.v.tensors())],
-                        lrs=[h.lr_mean * ext, h.lr_log_scale, h.lr_quat, h.lr_opacity, h.lr_sh],
-                        beta1=h.beta1, beta2=h.beta2, eps=h.eps, step=self.step_no)
 
         def fork():
             side.wait_stream(main)
             with torch.cuda.stream(side):
                 extra = [] if self.merged_tracks else [self.gX]   # merged: gX is dg.mean
-                # the fused backward writes dg (not adds into it)
-                grads = [] if fused else self.dg.tensors()
-                for t in grads + extra + [self.g_tan, self.loss, self.n_masked]:
+                for t in self.dg.tensors() + extra + [self.g_tan, self.loss, self.n_masked]:
                     gs_zero(t)
                 # the backward's screen-space records too: a memset of B N 48
                 # bytes, here beside the compute-bound compositing instead of
@@ -392,15 +369,16 @@ class JointStep:
                               self.loss[0:1], r.v_image, r.ws_photo, self.Rt)
                 mark("photo")
                 r.backward(self.g, self.dg, self.g_tan, v_image=r.v_image, loss=self.loss[0:1], Rt=self.Rt,
-                           mark=mark, records_zeroed=True, adam=adam)
+                           mark=mark, records_zeroed=True)
             else:
                 r.backward(self.g, self.dg, self.g_tan, target=tgt, l1_weight=h.l1_weight, loss=self.loss[0:1],
-                           Rt=self.Rt, mark=mark, records_zeroed=True, adam=adam)
+                           Rt=self.Rt, mark=mark, records_zeroed=True)
         if not joined:
             fork()
             main.wait_stream(side)
         mark("zero")
         mark("track")
+        gs_step_advance(self.step_no)
         # the pose update (one small kernel, independent of the parameter
         # update) runs on the side stream beside Adam
         side.wait_stream(main)
@@ -408,7 +386,8 @@ class JointStep:
             with torch.cuda.stream(side):
                 hp = adam_c(h.lr_pose, h.beta1, h.beta2, h.eps, self.step_no)
                 pose_se3_update(self.T0, self.xi, self.g_tan, self.g_xi, self.m_xi, self.v_xi, hp, self.Rt)
-        groups = [] if fused else [
+        ext = h.scene_extent
+        groups = [
             (self.g.mean, self.dg.mean, self.m.mean, self.v.mean, h.lr_mean * ext),
             (self.g.log_scale, self.dg.log_scale, self.m.log_scale, self.v.log_scale, h.lr_log_scale),
             (self.g.quat, self.dg.quat, self.m.quat, self.v.quat, h.lr_quat),

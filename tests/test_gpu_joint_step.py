@@ -70,7 +70,7 @@ def _inputs(w, merged):
     return params, X, wh, K, Rt, targets, obs_point, obs_view, xy, tr["view_obs_offset"]
 
 
-def _gpu_step(w, views, inputs, hyper, merged, deterministic=False, replays=1, fuse_adam=True):
+def _gpu_step(w, views, inputs, hyper, merged, deterministic=False, replays=1):
     from paper_2603_04847_gb300 import Cameras, Gaussians, Hyper, JointStep
     params, X, wh, K, Rt, targets, obs_point, obs_view, xy, voff = inputs
     cams = Cameras.from_numpy(wh, K, Rt)
@@ -82,7 +82,7 @@ def _gpu_step(w, views, inputs, hyper, merged, deterministic=False, replays=1, f
     h = Hyper(**hyper)
     js = JointStep(g, cams, dev(X, torch.float32), dev(obs_point, torch.int32), dev(xy, torch.float32),
                    dev(voff, torch.int64), dev(tg, torch.float32), off, views, h, merged_tracks=merged,
-                   dynamic_batch=len(views) > 1, deterministic=deterministic, fuse_adam=fuse_adam)
+                   dynamic_batch=len(views) > 1, deterministic=deterministic)
     js.ensure_capacity()
     js.capture(warmup=0)     # capturing does not run the step
     for _ in range(replays):
@@ -157,23 +157,3 @@ def test_deterministic_step_is_bit_identical_across_runs(merged):
                                                                              js.g_tan]])
     for a, b in zip(*outs):
         np.testing.assert_array_equal(a, b)
-
-
-def test_adam_fused_into_the_projection_backward_equals_the_separate_update():
-    """The batched step applies the Gaussians' Adam step inside the
-    projection backward (gs_project_bwd_adam).  Against the separate Adam
-    launch, over three replayed steps (both deterministic, so that the
-    fusion is the only difference): the same gradients and the same
-    parameters and moments up to the last bits of the update arithmetic."""
-    w, views = _workload("uneven_batch")
-    inputs = _inputs(w, False)
-    a = _gpu_step(w, views, inputs, HYPER, False, deterministic=True, replays=3, fuse_adam=True)
-    b = _gpu_step(w, views, inputs, HYPER, False, deterministic=True, replays=3, fuse_adam=False)
-    assert a.fused_adam and not b.fused_adam
-    for ta, tb in zip(a.dg.tensors(), b.dg.tensors()):
-        np.testing.assert_array_equal(ta.cpu().numpy(), tb.cpu().numpy())
-    for ga, gb in ((a.g, b.g), (a.m, b.m), (a.v, b.v)):
-        for ta, tb in zip(ga.tensors(), gb.tensors()):
-            x, y = ta.cpu().numpy(), tb.cpu().numpy()
-            np.testing.assert_allclose(x, y, rtol=1e-6, atol=1e-7 * (1.0 + np.abs(y).max()))
-    np.testing.assert_array_equal(a.X.cpu().numpy(), b.X.cpu().numpy())
