@@ -858,7 +858,11 @@ def run_ours(args):
     ts = TargetStream(js, host_tgt, inp["off"])
     if use_graph:
         js.capture()
-    loss_host = torch.zeros(2, dtype=torch.float64).pin_memory()
+    # each step's loss is read back one step later (two pinned buffers and
+    # events), so the host enqueues step i + 1 before it waits for step i
+    loss_host = [torch.zeros(2, dtype=torch.float64).pin_memory() for _ in range(2)]
+    loss_ready = [torch.cuda.Event(), torch.cuda.Event()]
+    losses = []
     n_e2e = max(10, args.steps)
     plan = []
     for i in range(n_e2e + 1):
@@ -889,17 +893,26 @@ def run_ours(args):
             set_views_async(js, plan[i])
         js.run() if use_graph else js.step()
         ts.end()
+        loss_host[i % 2].copy_(js.loss, non_blocking=True)
+        loss_ready[i % 2].record()
+        if i >= 1:   # the previous step's loss, read on the host
+            loss_ready[(i - 1) % 2].synchronize()
+            losses.append(float(loss_host[(i - 1) % 2][0]))
         if i + 1 < n_e2e:
             h2d_total += ts.put(js.views if plan[i + 1] is None else plan[i + 1].numpy())
-        loss_host.copy_(js.loss, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+    loss_ready[(n_e2e - 1) % 2].synchronize()
+    losses.append(float(loss_host[(n_e2e - 1) % 2][0]))
+    torch.cuda.current_stream().synchronize()
     e2e_s = slowest_rank_time(time.perf_counter() - t0, dev)
+    if len(losses) != n_e2e or not all(np.isfinite(losses)):
+        raise RuntimeError("end-to-end loop: losses not read back for every step")
     if js.status_flags():
         raise RuntimeError("device status flags %d during the end-to-end steps" % js.status_flags())
     h2d_step = h2d_total / n_e2e + 8 * len(inp["off"]) + (4 * W.batch if batch_list is not None else 0)
     e2e = dict(value=ws * e2e_px / 1e6 / e2e_s, unit=UNIT, h2d_bytes_per_step=int(h2d_step),
                d2h_bytes_per_step=16, ms_per_step=e2e_s * 1e3 / n_e2e,
-               pipeline="targets uploaded one step ahead on a copy stream (pinned host -> HBM)",
+               pipeline="targets uploaded one step ahead on a copy stream (pinned host -> HBM); each step's "
+                        "loss read back by the host one step later",
                l2="no flush inside the pipelined loop; the step's working set is larger than L2")
 
     cpu = None
