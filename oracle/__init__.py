@@ -48,6 +48,7 @@ _lib = None
 ALPHA_MIN = 1.0 / 255.0
 ALPHA_MAX = 0.99
 T_MIN = 1e-4
+RECT_MARGIN = 1.0 / 64.0   # px around a splat's support box (gs_oracle.c RECT_MARGIN)
 
 PROJ_FIELDS = [
     "visible", "depth", "mx", "my", "cov_xx", "cov_xy", "cov_yy",

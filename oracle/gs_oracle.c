@@ -20,6 +20,7 @@
 #define T_MIN 1e-4              /* stop before T' would fall below 1e-4   */
 #define DILATION 0.3            /* screen-space covariance dilation (px^2) */
 #define GUARD 1.3               /* guard band of the EWA Jacobian           */
+#define RECT_MARGIN (1.0 / 64.0) /* px around the support's bounding box      */
 
 /* ------------------------------------------------------------------------ */
 /* small dense linear algebra                                               */
@@ -246,8 +247,9 @@ static void project_one(const orc_scene* sc, int j, const orc_camera* cam,
   if (P->o < ALPHA_MIN) return;
   /* alpha >= 1/255 <=> q <= Q; the ellipse q <= Q has half-widths
    * sqrt(Q S2_xx), sqrt(Q S2_yy).  Pixel u is covered iff its centre u+0.5
-   * lies within; one pixel of margin on each side keeps the rectangle
-   * conservative under rounding. */
+   * lies within; RECT_MARGIN (1/64 px, about a hundred times the float
+   * rounding of the bounds at these image sizes) on each side keeps a float
+   * evaluation of the rectangle conservative. */
   const double Q = 2.0 * log(255.0 * P->o);
   const double rx = sqrt(Q * P->S2[0]);
   const double ry = sqrt(Q * P->S2[3]);
@@ -255,8 +257,8 @@ static void project_one(const orc_scene* sc, int j, const orc_camera* cam,
   P->bound[1] = P->m2[1] - ry - 0.5;
   P->bound[2] = P->m2[0] + rx - 0.5;
   P->bound[3] = P->m2[1] + ry - 0.5;
-  double x0 = ceil(P->bound[0]) - 1.0, y0 = ceil(P->bound[1]) - 1.0;
-  double x1 = floor(P->bound[2]) + 1.0, y1 = floor(P->bound[3]) + 1.0;
+  double x0 = ceil(P->bound[0] - RECT_MARGIN), y0 = ceil(P->bound[1] - RECT_MARGIN);
+  double x1 = floor(P->bound[2] + RECT_MARGIN), y1 = floor(P->bound[3] + RECT_MARGIN);
   if (x0 < 0.0) x0 = 0.0;
   if (y0 < 0.0) y0 = 0.0;
   if (x1 > cam->width - 1.0) x1 = cam->width - 1.0;

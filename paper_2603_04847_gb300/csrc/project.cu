@@ -343,10 +343,13 @@ __global__ void __launch_bounds__(kProjThreads) project_fwd_kernel(GaussT<T> g, 
       if (V.visible) {
         const T rx = gsqrt(Qcut * V.S2[0]);
         const T ry = gsqrt(Qcut * V.S2[2]);
-        T x0 = gceil(V.m2[0] - rx - T(0.5)) - T(1);
-        T y0 = gceil(V.m2[1] - ry - T(0.5)) - T(1);
-        T x1 = gfloor(V.m2[0] + rx - T(0.5)) + T(1);
-        T y1 = gfloor(V.m2[1] + ry - T(0.5)) + T(1);
+        // the pixels whose centre lies in the support's bounding box, with
+        // 1/64 px of margin (~100 times the float rounding of the bounds)
+        const T mg = T(1) / T(64);
+        T x0 = gceil(V.m2[0] - rx - T(0.5) - mg);
+        T y0 = gceil(V.m2[1] - ry - T(0.5) - mg);
+        T x1 = gfloor(V.m2[0] + rx - T(0.5) + mg);
+        T y1 = gfloor(V.m2[1] + ry - T(0.5) + mg);
         x0 = gmax(x0, T(0));
         y0 = gmax(y0, T(0));
         x1 = gmin(x1, (T)(c.W - 1));

@@ -35,6 +35,7 @@ def oracle_rect_knife(proj, W, H, tile, eps=2e-4):
     vis = proj[:, P["visible"]] > 0
     px = proj[:, [P["px_x0"], P["px_y0"], P["px_x1"], P["px_y1"]]].astype(np.int64)
     b = proj[:, [P["bound_x0"], P["bound_y0"], P["bound_x1"], P["bound_y1"]]]
+    b = b + np.array([-1.0, -1.0, 1.0, 1.0]) * oracle.RECT_MARGIN   # where ceil / floor decide
     near_int = np.abs(b - np.round(b)) < eps
     knife = near_int.any(1) | (np.abs(proj[:, P["opacity"]] - 1 / 255) < 1e-6)
     return vis, px // tile, knife

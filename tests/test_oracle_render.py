@@ -91,7 +91,7 @@ def test_tiled_equals_untiled(tile):
 def test_rect_is_conservative_brute_force():
     """Brute force over every pixel: each pixel where a Gaussian's alpha is
     >= 1/255 lies inside its rectangle, and the rectangle exceeds the exact
-    support's bounding box by at most the one-pixel margin (+1 rounding)."""
+    support's bounding box by at most the 1/64-px margin (+1 rounding)."""
     rng = np.random.default_rng(5)
     n = 40
     cam = oracle.make_camera(64, 48, 60, 60, 32, 24, np.eye(3), [0, 0, 0])
