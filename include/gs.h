@@ -258,7 +258,7 @@ int gs_device_sm_count(void);
  * outside [near, far]; 2-D covariance J R Sigma R^T J^T + 0.3 I with the
  * Jacobian J of pi at x_c (x/z, y/z clamped to 1.3 half-fields of view);
  * conic = its inverse; colour from SH; tile rectangle of the pixels whose
- * alpha can reach 1/255 (one pixel of margin).  Writes out->splat, ->rect
+ * alpha can reach 1/255 (1/64 px of margin).  Writes out->splat, ->rect
  * and ->n_tiles for all B*N records (n_tiles = 0 when culled).
  * Non-finite parameters set GS_FLAG_NONFINITE and cull the Gaussian.
  */
