@@ -128,14 +128,10 @@ __global__ void __launch_bounds__(kThr) mcmc_reduce_kernel(int n, const float* _
 }
 
 // Exclusive scan of the per-block sums in place, by one block with a carry.
-constexpr int kBlocksThr = 1024;  // one block over all the block sums
-
-__global__ void __launch_bounds__(kBlocksThr) mcmc_blocks_kernel(int nb, double* __restrict__ bsum,
-                                                                 int32_t* __restrict__ bcnt,
-                                                                 double* __restrict__ total,
-                                                                 uint32_t* __restrict__ n_dead) {
-  __shared__ double s_d[kBlocksThr / 32];
-  __shared__ int s_i[kBlocksThr / 32];
+__global__ void __launch_bounds__(kThr) mcmc_blocks_kernel(int nb, double* __restrict__ bsum, int32_t* __restrict__ bcnt,
+                                                           double* __restrict__ total, uint32_t* __restrict__ n_dead) {
+  __shared__ double s_d[kThr / 32];
+  __shared__ int s_i[kThr / 32];
   __shared__ double carry_d;
   __shared__ int carry_i;
   if (threadIdx.x == 0) {
@@ -143,7 +139,7 @@ __global__ void __launch_bounds__(kBlocksThr) mcmc_blocks_kernel(int nb, double*
     carry_i = 0;
   }
   __syncthreads();
-  for (int base = 0; base < nb; base += kBlocksThr) {
+  for (int base = 0; base < nb; base += kThr) {
     const int i = base + threadIdx.x;
     const double v = i < nb ? bsum[i] : 0.0;
     const int c = i < nb ? bcnt[i] : 0;
@@ -157,7 +153,7 @@ __global__ void __launch_bounds__(kBlocksThr) mcmc_blocks_kernel(int nb, double*
       bcnt[i] = ci + excl;
     }
     __syncthreads();
-    if (threadIdx.x == kBlocksThr - 1) {
+    if (threadIdx.x == kThr - 1) {
       carry_d = cd + incl;
       carry_i = ci + excl + c;
     }
@@ -392,7 +388,7 @@ cudaError_t launch_mcmc_relocate(int n, int sh_degree, float* mean, float* log_s
   const int nb = (n + kThr - 1) / kThr;
   const int K3 = 3 * (sh_degree + 1) * (sh_degree + 1);
   mcmc_reduce_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt, w.cdf);
-  mcmc_blocks_kernel<<<1, kBlocksThr, 0, st>>>(nb, w.bsum, w.bcnt, w.total, n_dead);
+  mcmc_blocks_kernel<<<1, kThr, 0, st>>>(nb, w.bsum, w.bcnt, w.total, n_dead);
   mcmc_apply_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt, w.cdf, w.rank, w.count, w.list_n);
   mcmc_draw_kernel<<<nb, kThr, 0, st>>>(n, w.rank, w.cdf, u, n_u, src, w.count, w.list, w.list_n);
   const int n_sources = std::min(n, std::max(n_u, 0));  // bound on the distinct sources
@@ -410,7 +406,7 @@ cudaError_t launch_mcmc_grow(int n, int n_add, int sh_degree, float* mean, float
   const int nba = (n_add + kThr - 1) / kThr;
   const int K3 = 3 * (sh_degree + 1) * (sh_degree + 1);
   mcmc_reduce_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt, w.cdf);
-  mcmc_blocks_kernel<<<1, kBlocksThr, 0, st>>>(nb, w.bsum, w.bcnt, w.total, nullptr);
+  mcmc_blocks_kernel<<<1, kThr, 0, st>>>(nb, w.bsum, w.bcnt, w.total, nullptr);
   mcmc_apply_kernel<<<nb, kThr, 0, st>>>(n, logit, w.bsum, w.bcnt, w.cdf, w.rank, w.count, w.list_n);
   mcmc_grow_draw_kernel<<<nba, kThr, 0, st>>>(n, n_add, w.rank, w.cdf, u, src, w.count, w.list, w.list_n);
   const int n_sources = std::min(n, n_add);
