@@ -395,8 +395,13 @@ constexpr size_t project_bwd_smem() {
 
 // 3 blocks of 128 per SM for FP32 (168 registers); the FP64 instantiation
 // is a checking path and takes what it needs
+// Blocks per SM the FP32 projection backward is compiled for (its register
+// budget): 3 (163 registers, no spills).  At 4 the SH3 kernel spills 88
+// bytes and measured 4.01 against 3.33 ms on the 16-view, 5M-Gaussian step.
+constexpr int kProjBwdMinBlocks = 3;
+
 template <typename T, int DEG>
-__global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? 3 : 1) project_bwd_kernel(
+__global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? kProjBwdMinBlocks : 1) project_bwd_kernel(
     GaussT<T> g, CamsT<T> cams, gs_batch batch, ProjT<T> proj, const T* __restrict__ v2d, GradsT<T> dg,
     double* __restrict__ partial) {
   constexpr int K = (DEG + 1) * (DEG + 1);
@@ -460,12 +465,20 @@ __global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? 3 : 1) project_
     if (live) {
       any = true;
       const SlotCamT<T>& c = sc[b];
-      ViewGeo<T> V;
-      view_geo(G, c, cams.near_plane, cams.far_plane, V);
-      const T v_mx = cur[0], v_my = cur[1], v_a = cur[2], v_b = cur[3];
-      const T v_c = cur[4], v_o = cur[5];
       T vcol[3] = {cur[6], cur[7], cur[8]};
-      // --- colour: SH and view direction --------------------------------
+      // --- colour: SH and view direction, before the projection's
+      // geometry, so that their registers are free again by then -------
+      struct {
+        T dir[3], dnorm;
+      } V;
+      {
+        const T d0 = G.mu[0] - c.campos[0], d1 = G.mu[1] - c.campos[1], d2 = G.mu[2] - c.campos[2];
+        V.dnorm = gsqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        const T idn0 = T(1) / V.dnorm;
+        V.dir[0] = d0 * idn0;
+        V.dir[1] = d1 * idn0;
+        V.dir[2] = d2 * idn0;
+      }
       T Y[K];
       sh_basis<T>(DEG, V.dir[0], V.dir[1], V.dir[2], Y);
       T wk[K];
@@ -496,10 +509,16 @@ __global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? 3 : 1) project_
         vmu[i] += vdv[i];
       }
       // v_campos = -vdv; its pose effect: g_rho += -R v_campos = R vdv
+      // --- the projection's geometry --------------------------------------
+      ViewGeo<T> VG;
+      view_geo(G, c, cams.near_plane, cams.far_plane, VG);
+      const ViewGeo<T>& V2 = VG;
+      const T v_mx = cur[0], v_my = cur[1], v_a = cur[2], v_b = cur[3];
+      const T v_c = cur[4], v_o = cur[5];
       // --- opacity -------------------------------------------------------
       vol += v_o;
       // --- conic -> 2-D covariance: G_S2 = -Q G_Q Q -----------------------
-      const T a = V.conic[0], bq = V.conic[1], cq = V.conic[2];
+      const T a = V2.conic[0], bq = V2.conic[1], cq = V2.conic[2];
       const T hb = T(0.5) * v_b;
       const T X00 = v_a * a + hb * bq, X01 = v_a * bq + hb * cq;
       const T X10 = hb * a + v_c * bq, X11 = hb * bq + v_c * cq;
@@ -518,11 +537,11 @@ __global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? 3 : 1) project_
       // with lambda_1 a sum of non-negative terms, 1 / lambda_2 =
       // lambda_1 / det and e_1 from the branch without cancellation.
       {
-        const T xx = V.S2[0], xy = V.S2[1], yy = V.S2[2];
+        const T xx = V2.S2[0], xy = V2.S2[1], yy = V2.S2[2];
         const T h = T(0.5) * (xx - yy);
         const T rr = gsqrt(h * h + xy * xy);
         const T l1 = T(0.5) * (xx + yy) + rr;
-        const T il1 = T(1) / l1, il2 = l1 * V.idet;   // 1/lambda_2 = lambda_1 / det
+        const T il1 = T(1) / l1, il2 = l1 * V2.idet;   // 1/lambda_2 = lambda_1 / det
         T e1x = h >= T(0) ? h + rr : xy, e1y = h >= T(0) ? xy : rr - h;
         const T n2 = e1x * e1x + e1y * e1y;
         if (n2 > T(0)) {
@@ -540,21 +559,21 @@ __global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? 3 : 1) project_
         const T S11 = -G11 * il1 * il1, S22 = -G22 * il2 * il2, S12 = -G12 * il1 * il2;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          const T Bx = V.j00 * V.Mc[k] + V.j02 * V.Mc[6 + k];
-          const T By = V.j11 * V.Mc[3 + k] + V.j12 * V.Mc[6 + k];
+          const T Bx = V2.j00 * V2.Mc[k] + V2.j02 * V2.Mc[6 + k];
+          const T By = V2.j11 * V2.Mc[3 + k] + V2.j12 * V2.Mc[6 + k];
           const T b1 = e1x * Bx + e1y * By, b2 = e2x * Bx + e2y * By;
           gls_eig[k] += T(2) * (S11 * b1 * b1 + T(2) * S12 * b1 * b2 + S22 * b2 * b2);
         }
       }
       // --- S2 = J Sc J^T: H = G_S2 J, G_Sc = J^T H, G_J = 2 H Sc ----------
-      const T H00 = gxx * V.j00, H01 = gxy * V.j11, H02 = gxx * V.j02 + gxy * V.j12;
-      const T H10 = gxy * V.j00, H11 = gyy * V.j11, H12 = gxy * V.j02 + gyy * V.j12;
+      const T H00 = gxx * V2.j00, H01 = gxy * V2.j11, H02 = gxx * V2.j02 + gxy * V2.j12;
+      const T H10 = gxy * V2.j00, H11 = gyy * V2.j11, H12 = gxy * V2.j02 + gyy * V2.j12;
       T GSc[9];
-      GSc[0] = V.j00 * H00; GSc[1] = V.j00 * H01; GSc[2] = V.j00 * H02;
-      GSc[3] = V.j11 * H10; GSc[4] = V.j11 * H11; GSc[5] = V.j11 * H12;
-      GSc[6] = V.j02 * H00 + V.j12 * H10;
-      GSc[7] = V.j02 * H01 + V.j12 * H11;
-      GSc[8] = V.j02 * H02 + V.j12 * H12;
+      GSc[0] = V2.j00 * H00; GSc[1] = V2.j00 * H01; GSc[2] = V2.j00 * H02;
+      GSc[3] = V2.j11 * H10; GSc[4] = V2.j11 * H11; GSc[5] = V2.j11 * H12;
+      GSc[6] = V2.j02 * H00 + V2.j12 * H10;
+      GSc[7] = V2.j02 * H01 + V2.j12 * H11;
+      GSc[8] = V2.j02 * H02 + V2.j12 * H12;
       // symmetrise (exact symmetry is lost only to rounding)
       {
         const T s01 = T(0.5) * (GSc[1] + GSc[3]);
@@ -564,7 +583,7 @@ __global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? 3 : 1) project_
         GSc[2] = GSc[6] = s02;
         GSc[5] = GSc[7] = s12;
       }
-      const T* S = V.Sc;
+      const T* S = V2.Sc;
       // full symmetric Sc
       const T Sf[9] = {S[0], S[1], S[2], S[1], S[3], S[4], S[2], S[4], S[5]};
       // G_J entries used: (0,0), (0,2), (1,1), (1,2)
@@ -578,8 +597,8 @@ __global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? 3 : 1) project_
       for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int k = 0; k < 3; ++k)
-          GMc[3 * r + k] = T(2) * (GSc[3 * r] * V.Mc[k] + GSc[3 * r + 1] * V.Mc[3 + k] +
-                                  GSc[3 * r + 2] * V.Mc[6 + k]);
+          GMc[3 * r + k] = T(2) * (GSc[3 * r] * V2.Mc[k] + GSc[3 * r + 1] * V2.Mc[3 + k] +
+                                  GSc[3 * r + 2] * V2.Mc[6 + k]);
       const T* W = c.R;
 #pragma unroll
       for (int r = 0; r < 3; ++r)
@@ -599,17 +618,17 @@ __global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? 3 : 1) project_
         tan[5] += T(2) * (B[3] - B[1]);
       }
       // --- J(x_c) and mean2d -> v_xc ------------------------------------
-      const T z = V.xc[2];
+      const T z = V2.xc[2];
       const T iz = T(1) / z, iz2 = iz * iz;
       T vxc[3];
-      const T dJ02dx = V.clx ? T(0) : -c.fx * iz2;
-      const T dJ12dy = V.cly ? T(0) : -c.fy * iz2;
-      const T dJ02dz = c.fx * V.tx * iz2 + (V.clx ? T(0) : c.fx * V.xc[0] * iz2 * iz);
-      const T dJ12dz = c.fy * V.ty * iz2 + (V.cly ? T(0) : c.fy * V.xc[1] * iz2 * iz);
+      const T dJ02dx = V2.clx ? T(0) : -c.fx * iz2;
+      const T dJ12dy = V2.cly ? T(0) : -c.fy * iz2;
+      const T dJ02dz = c.fx * V2.tx * iz2 + (V2.clx ? T(0) : c.fx * V2.xc[0] * iz2 * iz);
+      const T dJ12dz = c.fy * V2.ty * iz2 + (V2.cly ? T(0) : c.fy * V2.xc[1] * iz2 * iz);
       vxc[0] = GJ02 * dJ02dx + v_mx * c.fx * iz;
       vxc[1] = GJ12 * dJ12dy + v_my * c.fy * iz;
       vxc[2] = -GJ00 * c.fx * iz2 - GJ11 * c.fy * iz2 + GJ02 * dJ02dz + GJ12 * dJ12dz -
-               (v_mx * c.fx * V.xc[0] + v_my * c.fy * V.xc[1]) * iz2;
+               (v_mx * c.fx * V2.xc[0] + v_my * c.fy * V2.xc[1]) * iz2;
       // --- x_c = W mu + t ------------------------------------------------
 #pragma unroll
       for (int i = 0; i < 3; ++i) vmu[i] += W[i] * vxc[0] + W[3 + i] * vxc[1] + W[6 + i] * vxc[2];
@@ -617,9 +636,9 @@ __global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? 3 : 1) project_
       tan[0] = vxc[0] + W[0] * vdv[0] + W[1] * vdv[1] + W[2] * vdv[2];
       tan[1] = vxc[1] + W[3] * vdv[0] + W[4] * vdv[1] + W[5] * vdv[2];
       tan[2] = vxc[2] + W[6] * vdv[0] + W[7] * vdv[1] + W[8] * vdv[2];
-      tan[3] += V.xc[1] * vxc[2] - V.xc[2] * vxc[1];
-      tan[4] += V.xc[2] * vxc[0] - V.xc[0] * vxc[2];
-      tan[5] += V.xc[0] * vxc[1] - V.xc[1] * vxc[0];
+      tan[3] += V2.xc[1] * vxc[2] - V2.xc[2] * vxc[1];
+      tan[4] += V2.xc[2] * vxc[0] - V2.xc[0] * vxc[2];
+      tan[5] += V2.xc[0] * vxc[1] - V2.xc[1] * vxc[0];
     }
     // warp reduce the 6 tangent values into the warp's own slots
     const unsigned any_live = __ballot_sync(0xffffffffu, live);
