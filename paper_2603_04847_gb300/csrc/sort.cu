@@ -12,7 +12,7 @@
 //               depth order; each block owns one contiguous output range
 //   tile sort   stable LSD radix sort of the instances by tile id, over the
 //               bits the largest tile id uses only (8-bit digits, or 9-bit
-//               ones where that saves a pass: 17-18 bits in two)
+//               ones where that saves a pass: 17 bits as 9 + 8, 18 as 9 + 9)
 //   ranges      [start, end) per global tile
 //
 // Sorting 8-byte records by depth once and then 8-byte instances by tile
@@ -792,8 +792,14 @@ cudaError_t launch_sort_tiles(int N, const gs_cameras& cams, const gs_batch& bat
                                                          capacity, n_instances, passes, tp.rb, ghist_tile, w.lb_tile,
                                                          lbt_stride, w.stall);
   const int tile_grid = (int)radix_tiles(capacity);
+  const int tbits = sort_tile_bits(batch.n_tiles);
   for (int pass = 0; pass < passes; ++pass) {
-    auto* kern = tp.rb == 9 ? onesweep_kernel<9> : onesweep_kernel<8>;
+    // a last pass with 8 bits or fewer left (17-bit tile ids in 9 + 8) ranks
+    // 8: the digit's ninth bit is zero for every item, its counts sit in the
+    // first 256 bins of the pass's histogram and its look-back words in the
+    // first half of the pass's (zeroed) region
+    const int bits = std::min(tp.rb, tbits - tp.rb * pass);
+    auto* kern = bits > 8 ? onesweep_kernel<9> : onesweep_kernel<8>;
     kern<<<tile_grid, kSortThreads, 0, st>>>(kA, vA, kB, vB, n_instances, 0, capacity, tp.rb * pass,
                                              ghist_tile + tbins * pass, w.lb_tile + lbt_stride * pass,
                                              w.counters + kMaxDigits + pass, nullptr, nullptr, 0u, status, w.stall,

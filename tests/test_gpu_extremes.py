@@ -4,7 +4,10 @@
   span more than 2^24, so the depth sort runs its fourth 8-bit pass):
   tile lists in (tile, depth, index) order, image and gradients.
 - A batch of GS_MAX_BATCH (64) uneven views in one launch per stage, one
-  view repeated: every view's image and the summed gradients."""
+  view repeated: every view's image and the summed gradients.
+- Tile ids of 17 and 18 bits (tile passes of 9 + 8 and 9 + 9 bits): the
+  tile lists equal a lexicographic sort of the projection's own (tile,
+  depth key, record) triples, and the ranges their counts."""
 import numpy as np
 import pytest
 
@@ -141,3 +144,43 @@ def test_a_batch_of_the_maximum_number_of_views():
         assert rel_linf(got[k], exp[k]) <= GRAD_TOL, k
     for v in range(len(wh)):
         assert pose_rel_err(got["tangent"][v], tan[v], tab[v]) <= GRAD_TOL, v
+
+
+def _expected_lists(r, batch, N):
+    """(tile, record) of every instance, sorted by (global tile, depth key,
+    record), from the projection's rectangles and depth keys (numpy)."""
+    rect = r.proj.rect.cpu().numpy()[:batch.B * N].astype(np.int64) & 0xFFFF
+    ntl = r.proj.n_tiles.cpu().numpy()[:batch.B * N].astype(np.int64)
+    key = r.proj.depth_key.cpu().numpy()[:batch.B * N].view(np.uint32).astype(np.int64)
+    rec = np.nonzero(ntl > 0)[0]
+    x0, y0, x1 = rect[rec, 0], rect[rec, 1], rect[rec, 2]
+    w = x1 - x0 + 1
+    cnt = ntl[rec]
+    np.testing.assert_array_equal(cnt, w * (rect[rec, 3] - y0 + 1))
+    rep = np.repeat(np.arange(len(rec)), cnt)
+    local = np.arange(cnt.sum()) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+    b = rec[rep] // N
+    tiles_x = (batch.W.astype(np.int64) + batch.tile - 1) // batch.tile
+    tile = (batch.tile_offset_host[b] + (y0[rep] + local // w[rep]) * tiles_x[b]
+            + x0[rep] + local % w[rep])
+    order = np.lexsort((rec[rep], key[rec[rep]], tile))
+    return tile[order], rec[rep][order]
+
+
+@pytest.mark.parametrize("n_views,bits", [(9, 17), (17, 18)])
+def test_tile_ids_of_17_and_18_bits(n_views, bits):
+    w = synth.make_workload("batched", n_gaussians=30000, n_views=n_views, width=(1900, 1920),
+                            height=(1060, 1080), n_tracks=10, seed=4)
+    sc, wh, K, Rt = w["scene"], w["wh"], w["K"], w["Rt"]
+    r, g, cams, batch = gpu_forward(sc, wh, K, Rt, list(range(n_views)))
+    assert int(np.ceil(np.log2(batch.n_tiles))) == bits
+    t_exp, v_exp = _expected_lists(r, batch, g.n)
+    n_inst = r.n_instances()
+    assert n_inst == len(t_exp) and n_inst > 20 * 4096
+    np.testing.assert_array_equal(r.tl.tiles.cpu().numpy()[:n_inst].astype(np.int64), t_exp)
+    np.testing.assert_array_equal(r.tl.vals.cpu().numpy()[:n_inst].astype(np.int64), v_exp)
+    ranges = r.tl.ranges.cpu().numpy()[:2 * batch.n_tiles].reshape(-1, 2).astype(np.int64)
+    counts = np.bincount(t_exp, minlength=batch.n_tiles)
+    np.testing.assert_array_equal(ranges[:, 1] - ranges[:, 0], counts)
+    nz = counts > 0
+    np.testing.assert_array_equal(ranges[nz, 0], (np.cumsum(counts) - counts)[nz])

