@@ -578,18 +578,20 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (bwd_min_blocks<T, kTi
   static_assert(!kDet || sizeof(T) == 4, "the deterministic backward is FP32");
   constexpr int kThreads = Shape<kTile>::kThreads;
   __shared__ TileInfo<T> ti;
-  __shared__ v2_t<T> s_m[kBatch];
-  __shared__ v4_t<T> s_q[kBatch];
-  __shared__ v4_t<T> s_c[kBatch];
-  __shared__ uint32_t s_mask[kBatch];
+  // staged splats, two buffers: a batch is staged while the previous one's
+  // sums are written out
+  __shared__ v2_t<T> s_m[2][kBatch];
+  __shared__ v4_t<T> s_q[2][kBatch];
+  __shared__ v4_t<T> s_c[2][kBatch];
+  __shared__ uint32_t s_mask[2][kBatch];
   __shared__ uint8_t s_list[kThreads / 32][kBatch];
-  __shared__ uint32_t s_rec[kBatch];
-  __shared__ uint32_t s_slot[kDet ? kBatch : 1];
+  __shared__ uint32_t s_rec[2][kBatch];
+  __shared__ uint32_t s_slot[2][kDet ? kBatch : 1];
   // per-warp gradient slots where they fit in shared memory, else one set
   // shared by the warps through shared atomics
   constexpr int kW = Shape<kTile>::kWarps;
   constexpr int kSlots =
-      kBatch * ((int)(10 * sizeof(T)) + 8 + kW + (int)(9 * sizeof(T)) * kW) <= 45000 ? kW : 1;
+      kBatch * (2 * ((int)(10 * sizeof(T)) + 12) + kW + (int)(9 * sizeof(T)) * kW) <= 45000 ? kW : 1;
   __shared__ T s_g[kSlots][kBatch][9];
   __shared__ uint32_t s_max;
   __shared__ T s_loss[kThreads / 32];
@@ -638,31 +640,66 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (bwd_min_blocks<T, kTi
   const uint32_t n_end = s_max;  // positions [0, n_end) of the tile list
   const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, nc_max);
   const T amin = Consts<T>::alpha_min, amax = Consts<T>::alpha_max;
-  for (int bend = (int)n_end; bend > 0; bend -= kBatch) {
+  // Batches back to front.  The first phase of a round writes out the
+  // previous batch's sums (zeroing their slots) and stages this batch into
+  // the other buffer, on different threads where the block has enough of
+  // them; the second composites.  Two barriers a round.
+#pragma unroll 1
+  for (int i = threadIdx.x; i < kSlots * kBatch * 9; i += kThreads) (&s_g[0][0][0])[i] = T(0);
+  int prev_cnt = 0, buf = 0;
+  for (int bend = (int)n_end;; bend -= kBatch) {
     const int bstart = max(0, bend - kBatch);
-    const int cnt = bend - bstart;
-    for (int s = threadIdx.x; s < kBatch; s += kThreads) {
-      if (s < cnt) {
-        const uint32_t r = vals[start + bstart + s];
-        s_rec[s] = r;
-        stage_splat<kTile>(s, r, splat, x0, y0, s_m, s_q, s_c, s_mask);
-        if constexpr (kDet) s_slot[s] = det_slot(det, r, ti.tx, ti.ty);
+    const int cnt = bend > 0 ? bend - bstart : 0;
+    for (int u = threadIdx.x; u < 2 * kBatch; u += kThreads) {
+      if (u < kBatch) {
+        const int s = u, pb = buf ^ 1;
+        if (s < prev_cnt) {
+          T sg[9];
+#pragma unroll
+          for (int i = 0; i < 9; ++i) {
+            T acc = T(0);
+#pragma unroll
+            for (int w = 0; w < kSlots; ++w) {
+              acc += s_g[w][s][i];
+              s_g[w][s][i] = T(0);
+            }
+            sg[i] = acc;
+          }
+          const bool nz = sg[0] != T(0) || sg[1] != T(0) || sg[2] != T(0) || sg[3] != T(0) || sg[4] != T(0) ||
+                          sg[5] != T(0) || sg[6] != T(0) || sg[7] != T(0) || sg[8] != T(0);
+          T rec[9];
+          if constexpr (kDet) {
+            if (nz) moments_to_grad(sg, s_q[pb][s], s_c[pb][s].w, rec);
+            else
+#pragma unroll
+              for (int i = 0; i < 9; ++i) rec[i] = T(0);
+            det_store(det, s_slot[pb][s], rec);
+          } else if (nz) {
+            moments_to_grad(sg, s_q[pb][s], s_c[pb][s].w, rec);
+            add_record(v2d, s_rec[pb][s], rec);
+          }
+        }
+      } else {
+        const int s = u - kBatch;
+        if (s < cnt) {
+          const uint32_t r = vals[start + bstart + s];
+          s_rec[buf][s] = r;
+          stage_splat<kTile>(s, r, splat, x0, y0, s_m[buf], s_q[buf], s_c[buf], s_mask[buf]);
+          if constexpr (kDet) s_slot[buf][s] = det_slot(det, r, ti.tx, ti.ty);
+        }
       }
-#pragma unroll
-      for (int w = 0; w < kSlots; ++w)
-#pragma unroll
-        for (int i = 0; i < 9; ++i) s_g[w][s][i] = T(0);
     }
+    if (cnt == 0) break;  // block-uniform
     __syncthreads();
     // this warp's splats: before all its pixels' last contributor and able
     // to reach its 8x8 block; walked back to front
     const int n_mine =
-        warp_list<kBatch>(s_mask, wbit, cnt, (int)warp_nc - bstart, s_list[threadIdx.x >> 5], lane);
+        warp_list<kBatch>(s_mask[buf], wbit, cnt, (int)warp_nc - bstart, s_list[threadIdx.x >> 5], lane);
     for (int i = n_mine - 1; i >= 0; --i) {
       const int k = s_list[threadIdx.x >> 5][i];
       const uint32_t pos = (uint32_t)(bstart + k);
-      const v2_t<T> m = s_m[k];
-      const v4_t<T> q = s_q[k];
+      const v2_t<T> m = s_m[buf][k];
+      const v4_t<T> q = s_q[buf][k];
       const T dy = py - m.y;
       T Bdy, sy;
       row_terms(q, dy, Bdy, sy);
@@ -676,7 +713,7 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (bwd_min_blocks<T, kTi
         const T alpha = gmin(amax, araw);
         if (alpha >= amin) {
           contrib = true;
-          bwd_pixel(P0, s_c[k], dx, dy, araw, alpha, g);
+          bwd_pixel(P0, s_c[buf][k], dx, dy, araw, alpha, g);
         }
       }
       if (pos < P1.nc) {
@@ -685,7 +722,7 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (bwd_min_blocks<T, kTi
         const T alpha = gmin(amax, araw);
         if (alpha >= amin) {
           contrib = true;
-          bwd_pixel(P1, s_c[k], dx, dy, araw, alpha, g);
+          bwd_pixel(P1, s_c[buf][k], dx, dy, araw, alpha, g);
         }
       }
       if (__ballot_sync(0xffffffffu, contrib)) {
@@ -704,30 +741,8 @@ __global__ void __launch_bounds__(Shape<kTile>::kThreads, (bwd_min_blocks<T, kTi
       }
     }
     __syncthreads();
-    for (int s = threadIdx.x; s < cnt; s += kThreads) {
-      T sg[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        T acc = T(0);
-#pragma unroll
-        for (int w = 0; w < kSlots; ++w) acc += s_g[w][s][i];
-        sg[i] = acc;
-      }
-      const bool nz = sg[0] != T(0) || sg[1] != T(0) || sg[2] != T(0) || sg[3] != T(0) || sg[4] != T(0) ||
-                      sg[5] != T(0) || sg[6] != T(0) || sg[7] != T(0) || sg[8] != T(0);
-      T rec[9];
-      if constexpr (kDet) {
-        if (nz) moments_to_grad(sg, s_q[s], s_c[s].w, rec);
-        else
-#pragma unroll
-          for (int i = 0; i < 9; ++i) rec[i] = T(0);
-        det_store(det, s_slot[s], rec);
-      } else if (nz) {
-        moments_to_grad(sg, s_q[s], s_c[s].w, rec);
-        add_record(v2d, s_rec[s], rec);
-      }
-    }
-    __syncthreads();
+    prev_cnt = cnt;
+    buf ^= 1;
   }
   if constexpr (kDet) {
     // instances behind every pixel's last contributor: zero slots
