@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(128) ba_back_substitute_kernel(
 // (the last row and column of tiles ragged).  For each tile column k:
 //   diag   factors tile (k, k) in shared memory (one block);
 //   panel  L_ik = A_ik L_kk^-T for the tiles below it (one block per tile);
-//   update A_ij -= L_ik L_jk^T for k < j <= i (one block per tile),
+//   update A_ij -= L_ik L_jk^T for k < j <= i (four blocks per tile),
 // so the O(n^3 / 6) flops of the updates are spread over the SMs.  A pivot
 // that is not positive (S' not positive definite) sets a marker in S[0]
 // (camera 0's block, not part of S' and free to use as scratch) that the
@@ -393,101 +393,175 @@ __device__ inline bool chol_failed(const double* S) { return *(volatile const do
 
 __global__ void ba_chol_init_kernel(double* S) { S[0] = 0.0; }
 
-__global__ void __launch_bounds__(256) ba_chol_diag_kernel(int n, size_t ld, double* __restrict__ S, int k) {
+// Tile (k, k) in shared memory by 128 threads, each owning up to four
+// fixed entries of the strict lower triangle (columns >= 1).  One barrier a
+// column: in step c every thread updates its entries (r, q), c < q <= r,
+// with l_rc l_qc (l = a * 1/sqrt(pivot)), and the owner of entry (c + 1,
+// c + 1), which has then had its last update, forms the next pivot's
+// reciprocal square root at once.  Column c is scaled when the tile is
+// written back.  Four warps keep all four of the SM's FP64 pipes busy.
+constexpr int kDiagThreads = 128;
+
+// 1 / sqrt(d) for a pivot d > 0: an FP32 estimate refined by two Newton
+// steps for the reciprocal square root, y <- y + y (1 - d y^2) / 2, each
+// roughly squaring the relative error (~2^-22 -> ~2^-44 -> the FP64
+// rounding level).  Eight dependent FP64 operations instead of a square
+// root and a division: the pivot is on the factorization's serial path.
+// Outside the range where the FP32 estimate is normal, the plain form.
+__device__ inline double pivot_rsqrt(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf((float)d);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double e = fma(-d * y, y, 1.0);
+    y = fma(0.5 * y, e, y);
+  }
+  return y;
+}
+constexpr int kDiagEntries = (kChT * (kChT - 1) / 2 + kDiagThreads - 1) / kDiagThreads;  // 4
+__global__ void __launch_bounds__(kDiagThreads) ba_chol_diag_kernel(int n, size_t ld, double* __restrict__ S,
+                                                                     int k) {
   __shared__ double a[kChT][kChT + 1];
-  __shared__ int bad;
-  if (chol_failed(S)) return;  // block-uniform
+  __shared__ double s_piv[kChT], s_inv[kChT];
+  __shared__ int s_bad;
+  if (chol_failed(S)) return;
   double* A = S + 6 * ld + 6;
   const int r0 = k * kChT, m = min(kChT, n - r0);
-  for (int e = threadIdx.x; e < kChT * kChT; e += blockDim.x) {
+  const int t = threadIdx.x;
+  for (int e = t; e < kChT * kChT; e += kDiagThreads) {
     const int r = e / kChT, c = e % kChT;
     a[r][c] = (r < m && c <= r) ? A[(size_t)(r0 + r) * ld + r0 + c] : 0.0;
   }
-  if (threadIdx.x == 0) bad = 0;
+  // this thread's entries: numbers t, t + 128, ... of the strict lower
+  // triangle without column 0, taken row by row: (1,1), (2,1), (2,2), ...
+  int er[kDiagEntries], eq[kDiagEntries];
+#pragma unroll
+  for (int i = 0; i < kDiagEntries; ++i) {
+    int idx = t + i * kDiagThreads, r = 1;
+    while (idx >= r) {
+      idx -= r;
+      ++r;
+    }
+    er[i] = r;          // r in 1..32 (32: no entry)
+    eq[i] = idx + 1;    // q in 1..r
+  }
+  if (t == 0) {
+    s_bad = 0;
+  }
+  __syncthreads();
+  if (t == 0) {
+    const double d = a[0][0];
+    if (d > 0.0 && isfinite(d)) {
+      s_piv[0] = d;
+      s_inv[0] = pivot_rsqrt(d);
+    } else {
+      s_bad = 1;
+    }
+  }
   __syncthreads();
   for (int c = 0; c < m; ++c) {
-    if (threadIdx.x == 0) {
-      const double d = a[c][c];
-      if (d > 0.0 && isfinite(d)) a[c][c] = sqrt(d);
-      else bad = 1;
-    }
-    __syncthreads();
-    if (bad) break;  // block-uniform
-    const double dcc = a[c][c];
-    for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) a[r][c] /= dcc;
-    __syncthreads();
-    const int t = m - c - 1;  // trailing rows; lower triangle of t x t
-    for (int e = threadIdx.x; e < t * t; e += blockDim.x) {
-      const int r = c + 1 + e / t, q = c + 1 + e % t;
-      if (q <= r) a[r][q] -= a[r][c] * a[q][c];
+    if (s_bad) break;  // block-uniform
+    const double inv = s_inv[c];
+#pragma unroll
+    for (int i = 0; i < kDiagEntries; ++i) {
+      const int r = er[i], q = eq[i];
+      if (r < m && q > c) {
+        a[r][q] -= (a[r][c] * inv) * (a[q][c] * inv);
+        if (r == c + 1 && q == c + 1) {  // its last update: the next pivot
+          const double d = a[r][r];
+          if (d > 0.0 && isfinite(d)) {
+            s_piv[r] = d;
+            s_inv[r] = pivot_rsqrt(d);
+          } else {
+            s_bad = 1;
+          }
+        }
+      }
     }
     __syncthreads();
   }
-  if (bad) {
-    if (threadIdx.x == 0) S[0] = 1.0;
+  if (s_bad) {
+    if (t == 0) S[0] = 1.0;
     return;
   }
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+  for (int e = t; e < m * m; e += kDiagThreads) {
     const int r = e / m, c = e % m;
-    if (c <= r) A[(size_t)(r0 + r) * ld + r0 + c] = a[r][c];
+    if (c <= r) A[(size_t)(r0 + r) * ld + r0 + c] = (r == c ? s_piv[c] : a[r][c]) * s_inv[c];  // sqrt(d) = d / sqrt(d)
   }
 }
 
-// Tile (k + 1 + blockIdx.x, k): X L_kk^T = A_ik, a thread per row (forward
-// substitution along the row, with the diagonal's reciprocals formed once).
-__global__ void __launch_bounds__(kChT) ba_chol_panel_kernel(int n, size_t ld, double* __restrict__ S, int k) {
+// Tile (k + 1 + blockIdx.x, k): X L_kk^T = A_ik.  Four threads per row, each
+// owning every fourth column of it in registers (forward substitution,
+// right-looking: once x_c is final the owners of the later columns subtract
+// its products at once).  Each x_j takes its products in the order q = 0, 1,
+// ..., j - 1.  A panel lies below a full diagonal tile: only the last tile
+// column is ragged, and it has none.
+__global__ void __launch_bounds__(4 * kChT) ba_chol_panel_kernel(int n, size_t ld, double* __restrict__ S, int k) {
   __shared__ double L[kChT][kChT + 1];
-  __shared__ double x[kChT][kChT + 1];
   __shared__ double inv[kChT];
   if (chol_failed(S)) return;
   double* A = S + 6 * ld + 6;
-  const int c0 = k * kChT, m = min(kChT, n - c0);
+  const int c0 = k * kChT;
   const int r0 = (k + 1 + (int)blockIdx.x) * kChT, mi = min(kChT, n - r0);
-  for (int r = 0; r < m; ++r)
-    for (int c = threadIdx.x; c < m; c += blockDim.x) L[r][c] = c <= r ? A[(size_t)(c0 + r) * ld + c0 + c] : 0.0;
-  for (int r = 0; r < mi; ++r)
-    for (int c = threadIdx.x; c < m; c += blockDim.x) x[r][c] = A[(size_t)(r0 + r) * ld + c0 + c];
-  __syncthreads();
-  if ((int)threadIdx.x < m) inv[threadIdx.x] = 1.0 / L[threadIdx.x][threadIdx.x];
-  __syncthreads();
-  const int r = threadIdx.x;
-  if (r < mi) {
-    for (int c = 0; c < m; ++c) {
-      double v = x[r][c];
-      for (int q = 0; q < c; ++q) v -= x[r][q] * L[c][q];
-      x[r][c] = v * inv[c];
-    }
+  for (int e = threadIdx.x; e < kChT * kChT; e += blockDim.x) {
+    const int r = e / kChT, c = e % kChT;
+    L[r][c] = c <= r ? A[(size_t)(c0 + r) * ld + c0 + c] : 0.0;
   }
   __syncthreads();
-  for (int rr = 0; rr < mi; ++rr)
-    for (int c = threadIdx.x; c < m; c += blockDim.x) A[(size_t)(r0 + rr) * ld + c0 + c] = x[rr][c];
+  if ((int)threadIdx.x < kChT) inv[threadIdx.x] = 1.0 / L[threadIdx.x][threadIdx.x];
+  __syncthreads();
+  const int r = threadIdx.x / 4, p = threadIdx.x % 4;  // row r, columns p, p + 4, ...
+  const int lane = threadIdx.x % 32;
+  constexpr int kOwn = kChT / 4;
+  double x[kOwn];
+#pragma unroll
+  for (int i = 0; i < kOwn; ++i) x[i] = r < mi ? A[(size_t)(r0 + r) * ld + c0 + p + 4 * i] : 0.0;
+#pragma unroll
+  for (int c = 0; c < kChT; ++c) {
+    double xc = 0.0;
+    if (p == (c & 3)) {
+      x[c >> 2] *= inv[c];
+      xc = x[c >> 2];
+    }
+    xc = __shfl_sync(0xffffffffu, xc, (lane & ~3) | (c & 3));
+#pragma unroll
+    for (int i = 0; i < kOwn; ++i)
+      if (p + 4 * i > c) x[i] -= xc * L[p + 4 * i][c];
+  }
+  if (r < mi) {
+#pragma unroll
+    for (int i = 0; i < kOwn; ++i) A[(size_t)(r0 + r) * ld + c0 + p + 4 * i] = x[i];
+  }
 }
 
-// Tile (i, j) = (k + 1 + blockIdx.y, k + 1 + blockIdx.x), j <= i:
-// A_ij -= L_ik L_jk^T.
-__global__ void __launch_bounds__(256) ba_chol_update_kernel(int n, size_t ld, double* __restrict__ S, int k) {
-  __shared__ double Li[kChT][kChT + 1];
+// Rows [8 z, 8 z + 8) of tile (i, j) = (k + 1 + blockIdx.y, k + 1 +
+// blockIdx.x), j <= i: A_ij -= L_ik L_jk^T, a thread per entry (four
+// blocks per tile spread the FP64 work over more SMs).
+constexpr int kUpdRows = 8;
+__global__ void __launch_bounds__(kUpdRows * kChT) ba_chol_update_kernel(int n, size_t ld, double* __restrict__ S,
+                                                                          int k) {
+  __shared__ double Li[kUpdRows][kChT + 1];
   __shared__ double Lj[kChT][kChT + 1];
   if (blockIdx.x > blockIdx.y) return;  // upper triangle of tiles
   if (chol_failed(S)) return;
   double* A = S + 6 * ld + 6;
-  const int c0 = k * kChT, m = min(kChT, n - c0);
-  const int i0 = (k + 1 + (int)blockIdx.y) * kChT, mi = min(kChT, n - i0);
+  const int c0 = k * kChT;  // a full tile column (see the panel)
+  const int i0 = (k + 1 + (int)blockIdx.y) * kChT + kUpdRows * (int)blockIdx.z;
+  const int mi = max(0, min(kUpdRows, n - i0));
   const int j0 = (k + 1 + (int)blockIdx.x) * kChT, mj = min(kChT, n - j0);
-  for (int e = threadIdx.x; e < kChT * kChT; e += blockDim.x) {
-    const int r = e / kChT, c = e % kChT;
-    Li[r][c] = (r < mi && c < m) ? A[(size_t)(i0 + r) * ld + c0 + c] : 0.0;
-    Lj[r][c] = (r < mj && c < m) ? A[(size_t)(j0 + r) * ld + c0 + c] : 0.0;
-  }
+  const bool diag_tile = blockIdx.x == blockIdx.y;
+  if (mi == 0) return;  // block-uniform: rows past the ragged last tile
+  const int tx = threadIdx.x % kChT, ty = threadIdx.x / kChT;
+  Li[ty][tx] = ty < mi ? A[(size_t)(i0 + ty) * ld + c0 + tx] : 0.0;
+  for (int r = ty; r < kChT; r += kUpdRows) Lj[r][tx] = r < mj ? A[(size_t)(j0 + r) * ld + c0 + tx] : 0.0;
   __syncthreads();
-  for (int e = threadIdx.x; e < mi * mj; e += blockDim.x) {
-    const int r = e / mj, c = e % mj;
-    if (i0 == j0 && c > r) continue;  // diagonal tile: lower triangle only
-    double v = 0.0;
-#pragma unroll 8
-    for (int q = 0; q < kChT; ++q) v += Li[r][q] * Lj[c][q];
-    A[(size_t)(i0 + r) * ld + j0 + c] -= v;
-  }
+  const int r = ty, c = tx;  // row i0 + r, column j0 + c
+  const int rt = kUpdRows * (int)blockIdx.z + r;  // the row within its tile
+  if (r >= mi || c >= mj || (diag_tile && c > rt)) return;  // diagonal tile: lower triangle only
+  double v = 0.0;
+#pragma unroll
+  for (int q = 0; q < kChT; ++q) v += Li[r][q] * Lj[c][q];
+  A[(size_t)(i0 + r) * ld + j0 + c] -= v;
 }
 
 // L y = b, then L^T x = y, tile by tile in one block; dc = (0, x).  Per
@@ -590,10 +664,10 @@ cudaError_t launch_ba_solve_cameras(int V, double* S, const double* rhs, double*
   const int T = (n + kChT - 1) / kChT;
   ba_chol_init_kernel<<<1, 1, 0, st>>>(S);
   for (int k = 0; k < T; ++k) {
-    ba_chol_diag_kernel<<<1, 256, 0, st>>>(n, ld, S, k);
+    ba_chol_diag_kernel<<<1, kDiagThreads, 0, st>>>(n, ld, S, k);
     if (k + 1 < T) {
-      ba_chol_panel_kernel<<<T - k - 1, kChT, 0, st>>>(n, ld, S, k);
-      ba_chol_update_kernel<<<dim3(T - k - 1, T - k - 1), 256, 0, st>>>(n, ld, S, k);
+      ba_chol_panel_kernel<<<T - k - 1, 4 * kChT, 0, st>>>(n, ld, S, k);
+      ba_chol_update_kernel<<<dim3(T - k - 1, T - k - 1, kChT / kUpdRows), kUpdRows * kChT, 0, st>>>(n, ld, S, k);
     }
   }
   const size_t ysm = (size_t)n * sizeof(double);
