@@ -83,7 +83,7 @@ enum {
                              <= 0: its step was set to zero              */
 };
 
-#define GS_ABI_VERSION 4
+#define GS_ABI_VERSION 5
 #define GS_MAX_BATCH 64   /* views per call */
 #define GS_MAX_BA_CAMERAS 4096 /* cameras of one sfm_ba_solve_cameras call */
 
@@ -565,6 +565,66 @@ gs_status sfm_ba_schur(int32_t n_cams, int32_t n_points, int64_t n_obs,
                        const int32_t* point_obs, double lambda,
                        const double* lambda_dev, double* S, double* rhs,
                        double* Vinv, gs_stream stream);
+
+/*
+ * sfm_ba_pair_lists — HOST-side plan of the elimination by camera pairs
+ * (sfm_ba_schur_pairs), built once per problem: the observation structure
+ * does not change between LM iterations.  All pointers are host memory.
+ * Inputs as for sfm_ba_schur (obs_cam [n_obs], the CSR point lists
+ * point_obs_offset [n_points+1], point_obs).  An incidence (k, a, b) is an
+ * ordered pair of observations a, b of point k whose cameras satisfy
+ * obs_cam[b] <= obs_cam[a] (entries outside [0, n_obs) and cameras outside
+ * [0, n_cams) are skipped); incidences are grouped by camera pair (ca, cb)
+ * in order of (ca, cb), within a pair in order of k, then of a's and b's
+ * positions in the point's list, and each pair's list is cut into chunks of
+ * at most `chunk` (> 0) incidences.  Outputs:
+ *   n_inc, n_pairs, n_chunks   the sizes (always written);
+ *   inc [n_inc,3] (k, a, b), pair_cams [n_pairs,2] (ca, cb),
+ *   pair_chunks [n_pairs+1] (the chunks of pair p are
+ *   [pair_chunks[p], pair_chunks[p+1])), chunk_start [n_chunks+1] (the
+ *   incidences of chunk j are [chunk_start[j], chunk_start[j+1])): written
+ *   only when all four are non-NULL, so a first call with them NULL sizes
+ *   the arrays.  GS_ERR_ARG for null inputs, negative sizes or chunk <= 0.
+ */
+gs_status sfm_ba_pair_lists(int32_t n_cams, int32_t n_points, int64_t n_obs,
+                            const int32_t* obs_cam,
+                            const int64_t* point_obs_offset,
+                            const int32_t* point_obs, int32_t chunk,
+                            int64_t* n_inc, int32_t* n_pairs,
+                            int32_t* n_chunks, int32_t* inc,
+                            int32_t* pair_cams, int32_t* pair_chunks,
+                            int64_t* chunk_start);
+
+/*
+ * sfm_ba_schur_pairs_workspace — bytes of device workspace that
+ * sfm_ba_schur_pairs needs for n_obs observations and n_chunks chunks
+ * (per observation W V^-1 and W V^-1 g; per chunk its 42 partial sums).
+ */
+gs_status sfm_ba_schur_pairs_workspace(int64_t n_obs, int32_t n_chunks,
+                                       size_t* bytes);
+
+/*
+ * sfm_ba_schur_pairs — the elimination of sfm_ba_schur (same S lower
+ * triangle, rhs and Vinv, same damping and same conventions), summed by
+ * camera pairs from the plan of sfm_ba_pair_lists (its arrays copied to the
+ * device as they are) instead of with atomics: every entry of S and rhs is
+ * formed in one fixed order, so the result is bit-reproducible; it equals
+ * sfm_ba_schur's up to the order of the FP64 sums.  ws: device workspace
+ * of sfm_ba_schur_pairs_workspace(n_obs, n_chunks) bytes.  GS_ERR_ARG for
+ * null arrays, negative sizes or a small workspace.
+ */
+gs_status sfm_ba_schur_pairs(int32_t n_cams, int32_t n_points, int64_t n_obs,
+                             const double* U, const double* Vp,
+                             const double* gc, const double* gp,
+                             const double* Wo, const int32_t* obs_cam,
+                             const int64_t* point_obs_offset,
+                             const int32_t* point_obs, const int32_t* inc,
+                             const int32_t* pair_cams, int32_t n_pairs,
+                             const int32_t* pair_chunks,
+                             const int64_t* chunk_start, int32_t n_chunks,
+                             double lambda, const double* lambda_dev,
+                             double* S, double* rhs, double* Vinv, void* ws,
+                             size_t ws_bytes, gs_stream stream);
 
 /*
  * sfm_ba_lm_accept — the accept / reject decision of one LM iteration of

@@ -146,6 +146,13 @@ PROTOTYPES = {
     "sfm_ba_schur": (ctypes.c_int, [c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_void_p, c_void_p, ctypes.c_double, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_void_p]),
+    "sfm_ba_pair_lists": (ctypes.c_int, [c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p, c_int32, c_void_p,
+                                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sfm_ba_schur_pairs_workspace": (ctypes.c_int, [c_int64, c_int32, c_void_p]),
+    "sfm_ba_schur_pairs": (ctypes.c_int, [c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                          c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_void_p,
+                                          c_void_p, c_int32, ctypes.c_double, c_void_p, c_void_p, c_void_p, c_void_p,
+                                          c_void_p, c_size_t, c_void_p]),
     "sfm_ba_lm_accept": (ctypes.c_int, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                         c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "sfm_ba_objective": (ctypes.c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,
@@ -202,7 +209,7 @@ def load(path: str = LIB_PATH):
         if lib.gs_struct_size(i) != ctypes.sizeof(s):
             raise GsError("ABI mismatch for %s: C %d vs ctypes %d" % (s.__name__, lib.gs_struct_size(i),
                                                                       ctypes.sizeof(s)))
-    if lib.gs_abi_version() != 4:
+    if lib.gs_abi_version() != 5:
         raise GsError("unexpected libgs ABI version")
     _lib = lib
     return lib

@@ -2,7 +2,8 @@
 Adjustment") on the GPU.
 
 Each iteration runs in libgs kernels: the IRLS normal-equation blocks
-(sfm_ba_assemble), the elimination of the points (sfm_ba_schur), the
+(sfm_ba_assemble), the elimination of the points (sfm_ba_schur_pairs, or
+sfm_ba_schur with pairs=False), the
 reduced camera system with camera 0 fixed (sfm_ba_solve_cameras), the
 points' back-substitution, the trial parameters (sfm_ba_apply_step) and
 their objective (sfm_ba_objective).  The host reads the two objectives to
@@ -16,7 +17,8 @@ import numpy as np
 import torch
 
 from .core import (Cameras, gs_zero, sfm_ba_apply_step, sfm_ba_assemble, sfm_ba_back_substitute, sfm_ba_lm_accept,
-                   sfm_ba_objective, sfm_ba_schur, sfm_ba_solve_cameras)
+                   sfm_ba_objective, sfm_ba_pair_lists, sfm_ba_schur, sfm_ba_schur_pairs, sfm_ba_schur_pairs_workspace,
+                   sfm_ba_solve_cameras)
 
 
 class BundleAdjuster:
@@ -25,7 +27,7 @@ class BundleAdjuster:
     (obs_point, obs_cam [M] int, obs_xy [M,2] pixels)."""
 
     def __init__(self, cams: Cameras, X: torch.Tensor, obs_point, obs_cam, obs_xy, delta: float = 1.0,
-                 lam: float = 1e-4):
+                 lam: float = 1e-4, pairs: bool = True):
         dev = X.device
         self.cams, self.delta, self.lam = cams, float(delta), float(lam)
         self.Rt = cams.Rt.clone()
@@ -47,6 +49,14 @@ class BundleAdjuster:
         self.obs_point, self.obs_cam = t(op, torch.int32), t(oc, torch.int32)
         self.obs_xy = t(np.asarray(obs_xy, np.float32).reshape(-1, 2), torch.float32)
         self.off, self.ids = t(off, torch.int64), t(ids, torch.int32)
+        # the elimination by camera pairs: its plan is built once (the
+        # observation structure does not change between iterations)
+        self.plan = None
+        if pairs:
+            hplan = sfm_ba_pair_lists(V, P, oc, off, ids)
+            self.plan = {k: t(a, torch.int64 if a.dtype == np.int64 else torch.int32) for k, a in hplan.items()}
+            nb = sfm_ba_schur_pairs_workspace(M, hplan["chunk_start"].shape[0] - 1)
+            self.pair_ws = torch.empty(max(nb, 8), dtype=torch.uint8, device=dev)
 
         def z(*s):
             return torch.zeros(s, dtype=torch.float64, device=dev)
@@ -61,6 +71,14 @@ class BundleAdjuster:
                          Rt=self.Rt)
         self.objective = float(self.obj[0].item())
 
+    def _schur(self, lam):
+        if self.plan is not None:
+            sfm_ba_schur_pairs(self.U, self.Vp, self.gc, self.gp, self.Wo, self.obs_cam, self.off, self.ids, self.plan,
+                               lam, self.S, self.rhs, self.Vinv, self.pair_ws)
+        else:
+            sfm_ba_schur(self.U, self.Vp, self.gc, self.gp, self.Wo, self.obs_cam, self.off, self.ids, lam, self.S,
+                         self.rhs, self.Vinv)
+
     def step(self, mark=None) -> bool:
         """One LM iteration; returns whether the step was accepted.
         mark(name), if given, is called after each stage's launches."""
@@ -70,8 +88,7 @@ class BundleAdjuster:
         sfm_ba_assemble(self.X, self.cams, self.obs_point, self.obs_cam, self.obs_xy, self.delta, self.U, self.Vp,
                         self.gc, self.gp, self.Wo, None, Rt=self.Rt)
         mark("assemble")
-        sfm_ba_schur(self.U, self.Vp, self.gc, self.gp, self.Wo, self.obs_cam, self.off, self.ids, self.lam, self.S,
-                     self.rhs, self.Vinv)
+        self._schur(self.lam)
         mark("schur")
         sfm_ba_solve_cameras(self.S, self.rhs, self.dc, self.status)
         mark("solve_cameras")
@@ -108,8 +125,7 @@ class BundleAdjuster:
             gs_zero(a)
         sfm_ba_assemble(self.X, self.cams, self.obs_point, self.obs_cam, self.obs_xy, self.delta, self.U, self.Vp,
                         self.gc, self.gp, self.Wo, None, Rt=self.Rt)
-        sfm_ba_schur(self.U, self.Vp, self.gc, self.gp, self.Wo, self.obs_cam, self.off, self.ids, self.lam_dev,
-                     self.S, self.rhs, self.Vinv)
+        self._schur(self.lam_dev)
         sfm_ba_solve_cameras(self.S, self.rhs, self.dc, self.status)
         sfm_ba_back_substitute(self.Vinv, self.Vp, self.gp, self.Wo, self.obs_cam, self.off, self.ids, self.dc,
                                self.dp)

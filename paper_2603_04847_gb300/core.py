@@ -442,6 +442,54 @@ def sfm_ba_schur(U, Vp, gc, gp, Wo, obs_cam, point_obs_offset, point_obs, lam, S
                            _p(lam_dev), _p(S), _p(rhs), _p(Vinv), _stream(stream)), "sfm_ba_schur")
 
 
+PAIR_CHUNK = 128
+
+
+def sfm_ba_pair_lists(n_cams, n_points, obs_cam, point_obs_offset, point_obs, chunk=PAIR_CHUNK):
+    """The host-side plan of the elimination by camera pairs
+    (sfm_ba_pair_lists) from host arrays: dict of numpy arrays inc [n_inc,3],
+    pair_cams [n_pairs,2], pair_chunks [n_pairs+1], chunk_start
+    [n_chunks+1]."""
+    lib = _lib.load()
+    oc = np.ascontiguousarray(obs_cam, dtype=np.int32)
+    off = np.ascontiguousarray(point_obs_offset, dtype=np.int64)
+    ids = np.ascontiguousarray(point_obs, dtype=np.int32)
+    hp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    n_inc, n_pairs, n_chunks = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+    args = (int(n_cams), int(n_points), oc.shape[0], hp(oc), hp(off), hp(ids), int(chunk), ctypes.byref(n_inc),
+            ctypes.byref(n_pairs), ctypes.byref(n_chunks))
+    check(lib.sfm_ba_pair_lists(*args, None, None, None, None), "sfm_ba_pair_lists")
+    out = dict(inc=np.zeros((n_inc.value, 3), np.int32), pair_cams=np.zeros((n_pairs.value, 2), np.int32),
+               pair_chunks=np.zeros(n_pairs.value + 1, np.int32), chunk_start=np.zeros(n_chunks.value + 1, np.int64))
+    check(lib.sfm_ba_pair_lists(*args, hp(out["inc"]), hp(out["pair_cams"]), hp(out["pair_chunks"]),
+                                hp(out["chunk_start"])), "sfm_ba_pair_lists")
+    return out
+
+
+def sfm_ba_schur_pairs_workspace(n_obs, n_chunks):
+    lib = _lib.load()
+    b = ctypes.c_size_t()
+    check(lib.sfm_ba_schur_pairs_workspace(int(n_obs), int(n_chunks), ctypes.byref(b)), "sfm_ba_schur_pairs_workspace")
+    return b.value
+
+
+def sfm_ba_schur_pairs(U, Vp, gc, gp, Wo, obs_cam, point_obs_offset, point_obs, plan, lam, S, rhs, Vinv, ws,
+                       stream=None):
+    """sfm_ba_schur's outputs summed by camera pairs (sfm_ba_schur_pairs):
+    plan = the device copies (int32 / int64 tensors) of sfm_ba_pair_lists'
+    arrays; ws a device workspace of sfm_ba_schur_pairs_workspace bytes."""
+    lib = _lib.load()
+    _need_cuda(U, Vp, gc, gp, Wo, obs_cam, point_obs_offset, point_obs, S, rhs, Vinv, ws, *plan.values())
+    lam_dev = lam if isinstance(lam, torch.Tensor) else None
+    _need_cuda(lam_dev)
+    check(lib.sfm_ba_schur_pairs(U.shape[0], Vp.shape[0], obs_cam.shape[0], _p(U), _p(Vp), _p(gc), _p(gp), _p(Wo),
+                                 _p(obs_cam), _p(point_obs_offset), _p(point_obs), _p(plan["inc"]),
+                                 _p(plan["pair_cams"]), plan["pair_cams"].shape[0], _p(plan["pair_chunks"]),
+                                 _p(plan["chunk_start"]), plan["chunk_start"].shape[0] - 1,
+                                 0.0 if lam_dev is not None else float(lam), _p(lam_dev), _p(S), _p(rhs), _p(Vinv),
+                                 _p(ws), ws.numel(), _stream(stream)), "sfm_ba_schur_pairs")
+
+
 def sfm_ba_lm_accept(objective, lam, Rt, X, Rt_trial, X_trial, n_accepted=None, history=None, n_iter=None,
                      stream=None):
     """The LM accept / reject on the device (sfm_ba_lm_accept): objective

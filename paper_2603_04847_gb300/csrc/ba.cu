@@ -13,6 +13,7 @@
 // camera's 42 values with shuffles and adds them once; otherwise each lane
 // adds its own.  Double precision throughout: the sums feed a linear solve.
 #include <algorithm>
+#include <vector>
 
 #include "gs_internal.h"
 
@@ -351,6 +352,121 @@ __global__ void __launch_bounds__(128) ba_point_schur_kernel(
 }
 
 
+// --- the elimination by camera pairs ---------------------------------------
+// The same sums as ba_point_schur_kernel without atomics.  A host-built plan
+// lists, per camera pair (ca, cb), cb <= ca, every incidence (k, a, b): an
+// ordered pair of observations a, b of point k with cameras ca, cb.  Per
+// LM iteration:
+//   obs_y     Y_a = W_a V_k^-1 (6x3) and Y_a g_k (6) per observation;
+//   chunk     a warp per chunk of at most kPairChunk incidences of one pair:
+//             sum Y_a W_b^T (6x6) and, where a = b, sum Y_a g_k, summed per
+//             lane, then over the lanes in a fixed order, into 42 partials;
+//   finalize  per pair and entry, the chunks' partials in chunk order,
+//             subtracted from S (rhs: added, diagonal pairs only).
+// Each entry of S is then formed in one fixed order: the result does not
+// depend on scheduling.
+constexpr int kPairValues = 42;  // 36 entries of the 6x6 block, 6 of the rhs
+constexpr int kObsY = 24;        // per observation: Y (18), Y g (6)
+
+__global__ void __launch_bounds__(128) ba_obs_y_kernel(int V, int P, int64_t M, const double* __restrict__ gp,
+                                                       const double* __restrict__ Vp, const double* __restrict__ Wo,
+                                                       const int32_t* __restrict__ obs_cam,
+                                                       const int64_t* __restrict__ off,
+                                                       const int32_t* __restrict__ point_obs,
+                                                       const double* __restrict__ Vinv, double* __restrict__ Y) {
+  const int64_t total = off[P];
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = P - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= p) lo = mid;
+      else hi = mid - 1;
+    }
+    const int k = lo;
+    const int64_t a = point_obs[p];
+    if (a < 0 || a >= M || (unsigned)obs_cam[a] >= (unsigned)V) continue;
+    const bool empty = block_empty(Vp + 9 * (size_t)k, 9);
+    double Vi[9], g[3];
+    for (int e = 0; e < 9; ++e) Vi[e] = Vinv[9 * (size_t)k + e];
+    for (int e = 0; e < 3; ++e) g[e] = empty ? 0.0 : gp[3 * (size_t)k + e];
+    const double* Wa = Wo + 18 * a;
+    double* y = Y + kObsY * a;
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      double yr[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        yr[c] = Wa[3 * r] * Vi[c] + Wa[3 * r + 1] * Vi[3 + c] + Wa[3 * r + 2] * Vi[6 + c];
+        y[3 * r + c] = yr[c];
+      }
+      y[18 + r] = yr[0] * g[0] + yr[1] * g[1] + yr[2] * g[2];
+    }
+  }
+}
+
+constexpr int kPairWarps = 4;
+__global__ void __launch_bounds__(32 * kPairWarps) ba_pair_chunk_kernel(
+    int n_chunks, const int32_t* __restrict__ inc, const int64_t* __restrict__ chunk_start,
+    const double* __restrict__ Y, const double* __restrict__ Wo, double* __restrict__ partial) {
+  __shared__ double sh[kPairWarps][kPairValues][33];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int chunk = blockIdx.x * kPairWarps + warp;
+  if (chunk >= n_chunks) return;  // warp-uniform; no block-wide barrier below
+  double acc[kPairValues];
+#pragma unroll
+  for (int e = 0; e < kPairValues; ++e) acc[e] = 0.0;
+  for (int64_t i = chunk_start[chunk] + lane; i < chunk_start[chunk + 1]; i += 32) {
+    const int a = inc[3 * i + 1], b = inc[3 * i + 2];
+    const double* ya = Y + kObsY * (size_t)a;
+    const double* wb = Wo + 18 * (size_t)b;
+    double yv[18], wv[18];
+#pragma unroll
+    for (int e = 0; e < 18; ++e) {
+      yv[e] = ya[e];
+      wv[e] = wb[e];
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+        acc[6 * r + c] += yv[3 * r] * wv[3 * c] + yv[3 * r + 1] * wv[3 * c + 1] + yv[3 * r + 2] * wv[3 * c + 2];
+    if (a == b) {
+#pragma unroll
+      for (int r = 0; r < 6; ++r) acc[36 + r] += ya[18 + r];
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < kPairValues; ++e) sh[warp][e][lane] = acc[e];
+  __syncwarp();
+  for (int e = lane; e < kPairValues; e += 32) {
+    double t = 0.0;
+    for (int l = 0; l < 32; ++l) t += sh[warp][e][l];
+    partial[(size_t)chunk * kPairValues + e] = t;
+  }
+}
+
+__global__ void __launch_bounds__(128) ba_pair_finalize_kernel(int V, int n_pairs, const int32_t* __restrict__ pair_cams,
+                                                               const int32_t* __restrict__ pair_chunks,
+                                                               const double* __restrict__ partial,
+                                                               double* __restrict__ S, double* __restrict__ rhs) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n_pairs * kPairValues) return;
+  const int p = (int)(t / kPairValues), e = (int)(t % kPairValues);
+  const int ca = pair_cams[2 * p], cb = pair_cams[2 * p + 1];
+  if ((unsigned)ca >= (unsigned)V || (unsigned)cb >= (unsigned)V || cb > ca) return;
+  double sum = 0.0;
+  for (int j = pair_chunks[p]; j < pair_chunks[p + 1]; ++j) sum += partial[(size_t)j * kPairValues + e];
+  const size_t n = 6 * (size_t)V;
+  if (e < 36) {
+    const int r = e / 6, c = e % 6;
+    if (ca == cb && c > r) return;  // the diagonal block's lower triangle
+    S[(6 * (size_t)ca + r) * n + 6 * (size_t)cb + c] -= sum;
+  } else if (ca == cb) {
+    rhs[6 * (size_t)ca + (e - 36)] += sum;
+  }
+}
+
 __global__ void __launch_bounds__(128) ba_back_substitute_kernel(
     int V, int P, int64_t M, const double* __restrict__ Vinv, const double* __restrict__ Vp,
     const double* __restrict__ gp, const double* __restrict__ Wo, const int32_t* __restrict__ obs_cam,
@@ -652,6 +768,95 @@ cudaError_t launch_ba_schur(int V, int P, int64_t M, const double* U, const doub
     if (M > 0)
       ba_point_schur_kernel<<<(unsigned)std::min<int64_t>((M + 127) / 128, 65535), 128, 0, st>>>(V, P, M, gp, Vp, Wo, obs_cam,
                                                                           point_obs_offset, point_obs, Vinv, S, rhs);
+  }
+  return cudaGetLastError();
+}
+
+// Host side of the elimination by camera pairs: the incidences (k, a, b)
+// of every point's ordered observation pairs with cam(b) <= cam(a) (entries
+// outside [0, M) or with a camera outside [0, V) skipped), grouped by
+// camera pair in order of (ca, cb), within a pair in order of k, then a's and
+// b's positions in the point's list; each pair's list cut into chunks of at
+// most `chunk`.  With null outputs only the sizes are returned.
+int64_t ba_pair_plan(int V, int P, int64_t M, const int32_t* obs_cam, const int64_t* off, const int32_t* point_obs,
+                     int chunk, int32_t* n_pairs_out, int32_t* n_chunks_out, int32_t* inc, int32_t* pair_cams,
+                     int32_t* pair_chunks, int64_t* chunk_start) {
+  struct Inc {
+    int64_t pair;
+    int32_t k, a, b;
+  };
+  std::vector<Inc> all;
+  std::vector<int32_t> valid;
+  for (int k = 0; k < P; ++k) {
+    valid.clear();
+    for (int64_t q = off[k]; q < off[k + 1]; ++q) {
+      const int64_t o = point_obs[q];
+      if (o < 0 || o >= M || (unsigned)obs_cam[o] >= (unsigned)V) continue;
+      valid.push_back((int32_t)o);
+    }
+    for (const int32_t a : valid)
+      for (const int32_t b : valid) {
+        const int ca = obs_cam[a], cb = obs_cam[b];
+        if (cb <= ca) all.push_back({(int64_t)ca * V + cb, k, a, b});
+      }
+  }
+  std::stable_sort(all.begin(), all.end(), [](const Inc& x, const Inc& y) { return x.pair < y.pair; });
+  int32_t n_pairs = 0, n_chunks = 0;
+  for (size_t i = 0; i < all.size();) {
+    size_t j = i;
+    while (j < all.size() && all[j].pair == all[i].pair) ++j;
+    const int64_t cnt = (int64_t)(j - i);
+    if (pair_cams) {
+      pair_cams[2 * n_pairs] = (int32_t)(all[i].pair / V);
+      pair_cams[2 * n_pairs + 1] = (int32_t)(all[i].pair % V);
+      pair_chunks[n_pairs] = n_chunks;
+      for (int64_t c = 0; c < cnt; c += chunk) chunk_start[n_chunks + c / chunk] = (int64_t)i + c;
+    }
+    n_chunks += (int32_t)((cnt + chunk - 1) / chunk);
+    ++n_pairs;
+    i = j;
+  }
+  if (pair_cams) {
+    pair_chunks[n_pairs] = n_chunks;
+    chunk_start[n_chunks] = (int64_t)all.size();
+    for (size_t i = 0; i < all.size(); ++i) {
+      inc[3 * i] = all[i].k;
+      inc[3 * i + 1] = all[i].a;
+      inc[3 * i + 2] = all[i].b;
+    }
+  }
+  *n_pairs_out = n_pairs;
+  *n_chunks_out = n_chunks;
+  return (int64_t)all.size();
+}
+
+size_t ba_schur_pairs_workspace_bytes(int64_t M, int n_chunks) {
+  return sizeof(double) * ((size_t)kObsY * (size_t)std::max<int64_t>(M, 1) + (size_t)kPairValues * (size_t)n_chunks);
+}
+
+cudaError_t launch_ba_schur_pairs(int V, int P, int64_t M, const double* U, const double* Vp, const double* gc,
+                                  const double* gp, const double* Wo, const int32_t* obs_cam,
+                                  const int64_t* point_obs_offset, const int32_t* point_obs, const int32_t* inc,
+                                  const int32_t* pair_cams, int n_pairs, const int32_t* pair_chunks,
+                                  const int64_t* chunk_start, int n_chunks, double lambda, const double* lambda_dev,
+                                  double* S, double* rhs, double* Vinv, void* ws, cudaStream_t st) {
+  if (V == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(S, 0, sizeof(double) * 36 * (size_t)V * (size_t)V, st);
+  if (e != cudaSuccess) return e;
+  ba_camera_init_kernel<<<(V + 63) / 64, 64, 0, st>>>(V, U, gc, lambda, lambda_dev, S, rhs);
+  if (P == 0 || M == 0) return cudaGetLastError();
+  double* Y = (double*)ws;
+  double* partial = Y + (size_t)kObsY * (size_t)M;
+  ba_point_vinv_kernel<<<(P + 127) / 128, 128, 0, st>>>(P, Vp, gp, lambda, lambda_dev, Vinv);
+  ba_obs_y_kernel<<<(unsigned)std::min<int64_t>((M + 127) / 128, 65535), 128, 0, st>>>(
+      V, P, M, gp, Vp, Wo, obs_cam, point_obs_offset, point_obs, Vinv, Y);
+  if (n_chunks > 0) {
+    ba_pair_chunk_kernel<<<(n_chunks + kPairWarps - 1) / kPairWarps, 32 * kPairWarps, 0, st>>>(n_chunks, inc,
+                                                                                                chunk_start, Y, Wo,
+                                                                                                partial);
+    const int64_t nt = (int64_t)n_pairs * kPairValues;
+    ba_pair_finalize_kernel<<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(V, n_pairs, pair_cams, pair_chunks, partial,
+                                                                         S, rhs);
   }
   return cudaGetLastError();
 }

@@ -691,6 +691,52 @@ gs_status sfm_ba_schur(int32_t n_cams, int32_t n_points, int64_t n_obs, const do
   return GS_OK;
 }
 
+gs_status sfm_ba_pair_lists(int32_t n_cams, int32_t n_points, int64_t n_obs, const int32_t* obs_cam,
+                            const int64_t* point_obs_offset, const int32_t* point_obs, int32_t chunk, int64_t* n_inc,
+                            int32_t* n_pairs, int32_t* n_chunks, int32_t* inc, int32_t* pair_cams,
+                            int32_t* pair_chunks, int64_t* chunk_start) {
+  if (n_cams < 0 || n_points < 0 || n_obs < 0) return fail(GS_ERR_ARG, "sfm_ba_pair_lists: negative sizes");
+  if (chunk <= 0) return fail(GS_ERR_ARG, "sfm_ba_pair_lists: chunk must be > 0");
+  if (!n_inc || !n_pairs || !n_chunks) return fail(GS_ERR_ARG, "sfm_ba_pair_lists: null size outputs");
+  if (n_points > 0 && (!point_obs_offset || (n_obs > 0 && (!obs_cam || !point_obs))))
+    return fail(GS_ERR_ARG, "sfm_ba_pair_lists: null inputs");
+  const bool fill = inc && pair_cams && pair_chunks && chunk_start;
+  *n_inc = gs::ba_pair_plan(n_cams, n_points, n_obs, obs_cam, point_obs_offset, point_obs, chunk, n_pairs, n_chunks,
+                            fill ? inc : nullptr, fill ? pair_cams : nullptr, fill ? pair_chunks : nullptr,
+                            fill ? chunk_start : nullptr);
+  return GS_OK;
+}
+
+gs_status sfm_ba_schur_pairs_workspace(int64_t n_obs, int32_t n_chunks, size_t* bytes) {
+  if (n_obs < 0 || n_chunks < 0 || !bytes) return fail(GS_ERR_ARG, "sfm_ba_schur_pairs_workspace: bad arguments");
+  *bytes = gs::ba_schur_pairs_workspace_bytes(n_obs, n_chunks);
+  return GS_OK;
+}
+
+gs_status sfm_ba_schur_pairs(int32_t n_cams, int32_t n_points, int64_t n_obs, const double* U, const double* Vp,
+                             const double* gc, const double* gp, const double* Wo, const int32_t* obs_cam,
+                             const int64_t* point_obs_offset, const int32_t* point_obs, const int32_t* inc,
+                             const int32_t* pair_cams, int32_t n_pairs, const int32_t* pair_chunks,
+                             const int64_t* chunk_start, int32_t n_chunks, double lambda, const double* lambda_dev,
+                             double* S, double* rhs, double* Vinv, void* ws, size_t ws_bytes, gs_stream stream) {
+  if (n_cams < 0 || n_points < 0 || n_obs < 0 || n_pairs < 0 || n_chunks < 0)
+    return fail(GS_ERR_ARG, "sfm_ba_schur_pairs: negative sizes");
+  if (n_cams > 0 && (!U || !gc || !S || !rhs)) return fail(GS_ERR_ARG, "sfm_ba_schur_pairs: null camera arrays");
+  if (n_points > 0 && (!Vp || !gp || !Vinv || !point_obs_offset || (n_obs > 0 && (!Wo || !obs_cam || !point_obs))))
+    return fail(GS_ERR_ARG, "sfm_ba_schur_pairs: null point or observation arrays");
+  if (n_chunks > 0 && (!inc || !pair_cams || !pair_chunks || !chunk_start))
+    return fail(GS_ERR_ARG, "sfm_ba_schur_pairs: null plan arrays");
+  if (!lambda_dev && (!std::isfinite(lambda) || lambda < 0.0))
+    return fail(GS_ERR_ARG, "sfm_ba_schur_pairs: lambda must be >= 0");
+  if (n_points > 0 && n_obs > 0 && (!ws || ws_bytes < gs::ba_schur_pairs_workspace_bytes(n_obs, n_chunks)))
+    return fail(GS_ERR_ARG, "sfm_ba_schur_pairs: workspace too small");
+  cudaError_t e = gs::launch_ba_schur_pairs(n_cams, n_points, n_obs, U, Vp, gc, gp, Wo, obs_cam, point_obs_offset,
+                                            point_obs, inc, pair_cams, n_pairs, pair_chunks, chunk_start, n_chunks,
+                                            lambda, lambda_dev, S, rhs, Vinv, ws, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sfm_ba_schur_pairs");
+  return GS_OK;
+}
+
 gs_status sfm_ba_lm_accept(int32_t n_cams, int32_t n_points, double* objective, double* lambda, float* Rt, float* X,
                            const float* Rt_trial, const float* X_trial, int32_t* n_accepted, double* history,
                            int32_t history_len, int32_t* n_iter, gs_stream stream) {

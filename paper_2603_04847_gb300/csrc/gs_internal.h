@@ -89,6 +89,16 @@ cudaError_t launch_adam_groups(const gs_adam_group* groups, int n_groups, const 
 cudaError_t launch_step_advance(int32_t* step, cudaStream_t st);
 cudaError_t launch_batch_layout(const gs_cameras& cams, const gs_batch& batch, int64_t* px_offset,
                                 int32_t* tile_offset, int32_t* status, cudaStream_t st);
+int64_t ba_pair_plan(int V, int P, int64_t M, const int32_t* obs_cam, const int64_t* off, const int32_t* point_obs,
+                     int chunk, int32_t* n_pairs, int32_t* n_chunks, int32_t* inc, int32_t* pair_cams,
+                     int32_t* pair_chunks, int64_t* chunk_start);
+size_t ba_schur_pairs_workspace_bytes(int64_t M, int n_chunks);
+cudaError_t launch_ba_schur_pairs(int V, int P, int64_t M, const double* U, const double* Vp, const double* gc,
+                                  const double* gp, const double* Wo, const int32_t* obs_cam,
+                                  const int64_t* point_obs_offset, const int32_t* point_obs, const int32_t* inc,
+                                  const int32_t* pair_cams, int n_pairs, const int32_t* pair_chunks,
+                                  const int64_t* chunk_start, int n_chunks, double lambda, const double* lambda_dev,
+                                  double* S, double* rhs, double* Vinv, void* ws, cudaStream_t st);
 cudaError_t launch_ba_assemble(const float* X, int n_points, const gs_cameras& cams, const int32_t* obs_point,
                                const int32_t* obs_cam, const float* obs_xy, int64_t n_obs, float delta, double* U,
                                double* Vp, double* gc, double* gp, double* Wo, double* objective,

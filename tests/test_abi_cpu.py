@@ -48,7 +48,7 @@ def test_struct_layouts_match(lib):
     for i, s in enumerate(_lib.STRUCTS):
         assert lib.gs_struct_size(i) == ctypes.sizeof(s), s.__name__
     assert lib.gs_struct_size(99) == 0
-    assert lib.gs_abi_version() == 4
+    assert lib.gs_abi_version() == 5
 
 
 def test_argument_errors_without_gpu(lib):

@@ -97,9 +97,28 @@ def _by_point(op, P):
     return off, ids.astype(np.int32)
 
 
+def _schur(pairs, U, Vp, gc, gp, Wo, oc, oc_d, off, ids, lam, S, rhs, Vinv):
+    """sfm_ba_schur (atomics) or sfm_ba_schur_pairs (camera pairs, plan
+    from sfm_ba_pair_lists with small chunks so that pairs span several)."""
+    from paper_2603_04847_gb300.core import (sfm_ba_pair_lists, sfm_ba_schur, sfm_ba_schur_pairs,
+                                             sfm_ba_schur_pairs_workspace)
+    dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    off_d, ids_d = dev(off, torch.int64), dev(ids, torch.int32)
+    if not pairs:
+        sfm_ba_schur(U, Vp, gc, gp, Wo, oc_d, off_d, ids_d, lam, S, rhs, Vinv)
+        return
+    V, P = U.shape[0], Vp.shape[0]
+    plan = sfm_ba_pair_lists(V, P, oc, off, ids, chunk=7)
+    plan_d = {k: dev(a, torch.int64 if a.dtype == np.int64 else torch.int32) for k, a in plan.items()}
+    ws = torch.empty(sfm_ba_schur_pairs_workspace(len(oc), plan["chunk_start"].shape[0] - 1), dtype=torch.uint8,
+                     device="cuda")
+    sfm_ba_schur_pairs(U, Vp, gc, gp, Wo, oc_d, off_d, ids_d, plan_d, lam, S, rhs, Vinv, ws)
+
+
+@pytest.mark.parametrize("pairs", [False, True])
 @pytest.mark.parametrize("lam", [1e-6, 1e-3, 1.0])
-def test_schur_elimination_and_back_substitution_match_the_oracle(lam):
-    from paper_2603_04847_gb300.core import sfm_ba_back_substitute, sfm_ba_schur
+def test_schur_elimination_and_back_substitution_match_the_oracle(lam, pairs):
+    from paper_2603_04847_gb300.core import sfm_ba_back_substitute
     X, Rt, K, op, oc, xy = _problem(3, n_cams=5, n_pts=40, pix_noise=1.0, outliers=6)
     X = np.vstack([X, [[0.3, 0.2, 0.1]]])          # a point nobody observes
     V, P = Rt.shape[0], X.shape[0]
@@ -110,7 +129,7 @@ def test_schur_elimination_and_back_substitution_match_the_oracle(lam):
     S = torch.full((6 * V, 6 * V), np.nan, dtype=torch.float64, device="cuda")
     rhs = torch.full((6 * V,), np.nan, dtype=torch.float64, device="cuda")
     Vinv = torch.full((P, 9), np.nan, dtype=torch.float64, device="cuda")
-    sfm_ba_schur(U, Vp, gc, gp, Wo, oc_d, off_d, ids_d, lam, S, rhs, Vinv)
+    _schur(pairs, U, Vp, gc, gp, Wo, oc, oc_d, off, ids, lam, S, rhs, Vinv)
     blocks = ba.normal_equations(_r32(X), _r32(Rt), _r32(K), op, oc, _r32(xy), 1.0)
     S_e, rhs_e, Vinv_e, by_point, gp_reg = ba.schur_system(*blocks, op, oc, lam)
     dc = np.zeros((V, 6))
@@ -128,6 +147,36 @@ def test_schur_elimination_and_back_substitution_match_the_oracle(lam):
     # the whole step equals the oracle's dense solve of the undivided system
     dc_d, dp_d = ba.solve_dense(*blocks, op, oc, lam)
     assert _close(dc, dc_d, 1e-7) and _close(dp.cpu().numpy(), dp_d, 1e-7)
+
+
+def test_schur_by_camera_pairs_equals_the_atomic_form_and_is_reproducible():
+    """Shuffled observations, a point seen twice by one camera, an
+    observation of an out-of-range point: the pair form equals the atomic
+    one to rounding (lower triangle of S, rhs, Vinv), and two runs of it are
+    bit-identical."""
+    X, Rt, K, op, oc, xy = _problem(5, n_cams=6, n_pts=60, pix_noise=1.0, outliers=5)
+    P = X.shape[0]
+    op = np.concatenate([op, [3, P + 2]]).astype(np.int32)
+    oc = np.concatenate([oc, [oc[np.nonzero(op == 3)[0][0]], 2]]).astype(np.int32)   # point 3 twice in one camera
+    xy = np.vstack([xy, xy[np.nonzero(op == 3)[0][0]] + 0.5, [[5.0, 5.0]]])
+    perm = np.random.default_rng(2).permutation(len(op))
+    op, oc, xy = op[perm], oc[perm], xy[perm]
+    V = Rt.shape[0]
+    U, Vp, gc, gp, Wo, _, oc_d = _assemble(X, Rt, K, op, oc, xy, 1.0)
+    off, ids = _by_point(op, P)
+    outs = []
+    for pairs in (False, True, True):
+        S = torch.full((6 * V, 6 * V), np.nan, dtype=torch.float64, device="cuda")
+        rhs = torch.full((6 * V,), np.nan, dtype=torch.float64, device="cuda")
+        Vinv = torch.full((P, 9), np.nan, dtype=torch.float64, device="cuda")
+        _schur(pairs, U, Vp, gc, gp, Wo, oc, oc_d, off, ids, 1e-3, S, rhs, Vinv)
+        torch.cuda.synchronize()
+        outs.append((np.tril(S.cpu().numpy()), rhs.cpu().numpy(), Vinv.cpu().numpy()))
+    (Sa, ra, va), (Sp, rp, vp), (Sq, rq, vq) = outs
+    assert _close(Sp, Sa, 1e-12) and _close(rp, ra, 1e-12)
+    np.testing.assert_array_equal(vp, va)
+    np.testing.assert_array_equal(Sp, Sq)
+    np.testing.assert_array_equal(rp, rq)
 
 
 @pytest.mark.parametrize("lam", [1e-6, 1e-3, 1.0])
