@@ -16,9 +16,9 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from .core import (Cameras, gs_zero, sfm_ba_apply_step, sfm_ba_assemble, sfm_ba_back_substitute, sfm_ba_lm_accept,
-                   sfm_ba_objective, sfm_ba_pair_lists, sfm_ba_schur, sfm_ba_schur_pairs, sfm_ba_schur_pairs_workspace,
-                   sfm_ba_solve_cameras)
+from .core import (PAIR_CHUNK, Cameras, gs_zero, sfm_ba_apply_step, sfm_ba_assemble, sfm_ba_back_substitute,
+                   sfm_ba_lm_accept, sfm_ba_objective, sfm_ba_pair_lists, sfm_ba_schur, sfm_ba_schur_pairs,
+                   sfm_ba_schur_pairs_workspace, sfm_ba_solve_cameras)
 
 
 class BundleAdjuster:
@@ -27,7 +27,7 @@ class BundleAdjuster:
     (obs_point, obs_cam [M] int, obs_xy [M,2] pixels)."""
 
     def __init__(self, cams: Cameras, X: torch.Tensor, obs_point, obs_cam, obs_xy, delta: float = 1.0,
-                 lam: float = 1e-4, pairs: bool = True):
+                 lam: float = 1e-4, pairs: bool = True, pair_chunk: int = PAIR_CHUNK):
         dev = X.device
         self.cams, self.delta, self.lam = cams, float(delta), float(lam)
         self.Rt = cams.Rt.clone()
@@ -53,7 +53,7 @@ class BundleAdjuster:
         # observation structure does not change between iterations)
         self.plan = None
         if pairs:
-            hplan = sfm_ba_pair_lists(V, P, oc, off, ids)
+            hplan = sfm_ba_pair_lists(V, P, oc, off, ids, chunk=pair_chunk)
             self.plan = {k: t(a, torch.int64 if a.dtype == np.int64 else torch.int32) for k, a in hplan.items()}
             nb = sfm_ba_schur_pairs_workspace(M, hplan["chunk_start"].shape[0] - 1)
             self.pair_ws = torch.empty(max(nb, 8), dtype=torch.uint8, device=dev)

@@ -442,7 +442,7 @@ def sfm_ba_schur(U, Vp, gc, gp, Wo, obs_cam, point_obs_offset, point_obs, lam, S
                            _p(lam_dev), _p(S), _p(rhs), _p(Vinv), _stream(stream)), "sfm_ba_schur")
 
 
-PAIR_CHUNK = 128
+PAIR_CHUNK = 256
 
 
 def sfm_ba_pair_lists(n_cams, n_points, obs_cam, point_obs_offset, point_obs, chunk=PAIR_CHUNK):

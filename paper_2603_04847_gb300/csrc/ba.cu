@@ -439,10 +439,15 @@ __global__ void __launch_bounds__(32 * kPairWarps) ba_pair_chunk_kernel(
 #pragma unroll
   for (int e = 0; e < kPairValues; ++e) sh[warp][e][lane] = acc[e];
   __syncwarp();
+  // over the lanes: four interleaved running sums (lanes l, l + 8, l + 16,
+  // l + 24), then pairwise -- a fixed order with a short dependent chain
   for (int e = lane; e < kPairValues; e += 32) {
-    double t = 0.0;
-    for (int l = 0; l < 32; ++l) t += sh[warp][e][l];
-    partial[(size_t)chunk * kPairValues + e] = t;
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int l = 0; l < 8; ++l)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) t[j] += sh[warp][e][l + 8 * j];
+    partial[(size_t)chunk * kPairValues + e] = (t[0] + t[1]) + (t[2] + t[3]);
   }
 }
 
