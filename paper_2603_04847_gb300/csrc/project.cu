@@ -308,12 +308,12 @@ __device__ inline void load_rec9(const double* v2d, size_t rec, double (&o)[9]) 
   o[8] = p[4].x;
 }
 
-template <typename T, int DEG>
 // FP32: 5 blocks of 128 per SM (96 registers; the SH3 form spills 16 bytes):
 // 1.49 -> 1.47 ms on the 16-view, 5M-Gaussian step, where 6 blocks spill 88
 // bytes and lose
-__global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? 5 : 1) project_fwd_kernel(GaussT<T> g, CamsT<T> cams, gs_batch batch,
-                                                                   ProjT<T> out, int32_t* status) {
+template <typename T, int DEG>
+__global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? 5 : 1)
+    project_fwd_kernel(GaussT<T> g, CamsT<T> cams, gs_batch batch, ProjT<T> out, int32_t* status) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   __shared__ SlotCamT<T> sc[GS_MAX_BATCH];
   __shared__ T s_sh[K * 3][kProjThreads + 1];
