@@ -514,36 +514,40 @@ __device__ inline bool chol_failed(const double* S) { return *(volatile const do
 
 __global__ void ba_chol_init_kernel(double* S) { S[0] = 0.0; }
 
-// Tile (k, k) in shared memory by 128 threads, each owning up to four
-// fixed entries of the strict lower triangle (columns >= 1).  One barrier a
-// column: in step c every thread updates its entries (r, q), c < q <= r,
-// with l_rc l_qc (l = a * 1/sqrt(pivot)), and the owner of entry (c + 1,
-// c + 1), which has then had its last update, forms the next pivot's
-// reciprocal square root at once.  Column c is scaled when the tile is
-// written back.  Four warps keep all four of the SM's FP64 pipes busy.
+// Tile (k, k) in shared memory, one barrier per column.  FP64 issues at
+// ~2 lanes per clock per SM, one pipe per SM quarter, so a warp's FP64
+// instruction occupies its quarter's pipe for many cycles and the pivots'
+// serial chain must not queue behind the trailing update:
+//   warp 0     lane r - 1 owns the diagonal entry (r, r): in step c it
+//              subtracts l_rc^2, and lane c (owner of (c + 1, c + 1), which
+//              has then had its last update) forms the next pivot's
+//              reciprocal square root at once;
+//   warps 1-3  the strict lower trailing triangle of step c, spread evenly
+//              over their 96 threads through a shared table of the
+//              triangle's (row, column) offsets.
+// Column c is scaled when the tile is written back.
 constexpr int kDiagThreads = 128;
+constexpr int kDiagUpd = kDiagThreads - 32;
 
-// 1 / sqrt(d) for a pivot d > 0: an FP32 estimate refined by two Newton
-// steps for the reciprocal square root, y <- y + y (1 - d y^2) / 2, each
-// roughly squaring the relative error (~2^-22 -> ~2^-44 -> the FP64
-// rounding level).  Eight dependent FP64 operations instead of a square
-// root and a division: the pivot is on the factorization's serial path.
-// Outside the range where the FP32 estimate is normal, the plain form.
+// 1 / sqrt(d) for a pivot d > 0: an FP32 estimate (relative error ~2^-22)
+// refined by one step of Halley's iteration for the reciprocal square
+// root, y <- y (1 + e/2 + 3e^2/8) with e = 1 - d y^2, which cubes the
+// relative error (to the FP64 rounding level, ~1 ulp).  Five dependent FP64
+// operations instead of a square root and a division: the pivot is on the
+// factorization's serial path.  Outside the range where the FP32 estimate
+// is normal, the plain form.
 __device__ inline double pivot_rsqrt(double d) {
   if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-  double y = (double)rsqrtf((float)d);
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const double e = fma(-d * y, y, 1.0);
-    y = fma(0.5 * y, e, y);
-  }
-  return y;
+  const double y = (double)rsqrtf((float)d);
+  const double e = fma(-d * y, y, 1.0);
+  return fma(y, e * fma(0.375, e, 0.5), y);
 }
-constexpr int kDiagEntries = (kChT * (kChT - 1) / 2 + kDiagThreads - 1) / kDiagThreads;  // 4
+
 __global__ void __launch_bounds__(kDiagThreads) ba_chol_diag_kernel(int n, size_t ld, double* __restrict__ S,
                                                                      int k) {
   __shared__ double a[kChT][kChT + 1];
   __shared__ double s_piv[kChT], s_inv[kChT];
+  __shared__ uint8_t s_tri[kChT * (kChT - 1) / 2][2];  // (i, j), j < i, row by row
   __shared__ int s_bad;
   if (chol_failed(S)) return;
   double* A = S + 6 * ld + 6;
@@ -553,22 +557,13 @@ __global__ void __launch_bounds__(kDiagThreads) ba_chol_diag_kernel(int n, size_
     const int r = e / kChT, c = e % kChT;
     a[r][c] = (r < m && c <= r) ? A[(size_t)(r0 + r) * ld + r0 + c] : 0.0;
   }
-  // this thread's entries: numbers t, t + 128, ... of the strict lower
-  // triangle without column 0, taken row by row: (1,1), (2,1), (2,2), ...
-  int er[kDiagEntries], eq[kDiagEntries];
-#pragma unroll
-  for (int i = 0; i < kDiagEntries; ++i) {
-    int idx = t + i * kDiagThreads, r = 1;
-    while (idx >= r) {
-      idx -= r;
-      ++r;
+  if (t < kChT) {  // row i of the triangle table: entries i (i - 1) / 2 + j, j < i
+    for (int j = 0; j < t; ++j) {
+      s_tri[t * (t - 1) / 2 + j][0] = (uint8_t)t;
+      s_tri[t * (t - 1) / 2 + j][1] = (uint8_t)j;
     }
-    er[i] = r;          // r in 1..32 (32: no entry)
-    eq[i] = idx + 1;    // q in 1..r
   }
-  if (t == 0) {
-    s_bad = 0;
-  }
+  if (t == 0) s_bad = 0;
   __syncthreads();
   if (t == 0) {
     const double d = a[0][0];
@@ -583,12 +578,12 @@ __global__ void __launch_bounds__(kDiagThreads) ba_chol_diag_kernel(int n, size_
   for (int c = 0; c < m; ++c) {
     if (s_bad) break;  // block-uniform
     const double inv = s_inv[c];
-#pragma unroll
-    for (int i = 0; i < kDiagEntries; ++i) {
-      const int r = er[i], q = eq[i];
-      if (r < m && q > c) {
-        a[r][q] -= (a[r][c] * inv) * (a[q][c] * inv);
-        if (r == c + 1 && q == c + 1) {  // its last update: the next pivot
+    if (t < 32) {
+      const int r = t + 1;  // diagonal entry (r, r)
+      if (r > c && r < m) {
+        const double l = a[r][c] * inv;
+        a[r][r] -= l * l;
+        if (r == c + 1) {  // its last update: the next pivot
           const double d = a[r][r];
           if (d > 0.0 && isfinite(d)) {
             s_piv[r] = d;
@@ -597,6 +592,13 @@ __global__ void __launch_bounds__(kDiagThreads) ba_chol_diag_kernel(int n, size_
             s_bad = 1;
           }
         }
+      }
+    } else {
+      // trailing strict lower triangle: rows c + 1 + i, columns c + 1 + j, j < i
+      const int w = m - c - 1, cnt = w * (w - 1) / 2;
+      for (int e = t - 32; e < cnt; e += kDiagUpd) {
+        const int r = c + 1 + s_tri[e][0], q = c + 1 + s_tri[e][1];
+        a[r][q] -= (a[r][c] * inv) * (a[q][c] * inv);
       }
     }
     __syncthreads();
