@@ -737,6 +737,7 @@ def run_ours(args):
     if flags:
         raise RuntimeError("device status flags %d after warm-up" % flags)
 
+    t_start = bcur
     timed_batches = None if batch_list is None else batch_list[bcur:bcur + args.steps]
     px_steps = ([js.batch.pixels] * args.steps if timed_batches is None else
                 [batch_pixels(js.cams, timed_batches[i].numpy()) for i in range(args.steps)])
@@ -748,8 +749,6 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.mark_on()
     times = time_graph(js, args.steps, flush, use_graph, timed_batches)
-    if batch_list is not None:
-        bcur += args.steps
     torch.cuda.synchronize()
     clocks.mark_off()
     tot = slowest_rank_time(sum(times), dev)   # ms, as time_graph returns
@@ -877,13 +876,11 @@ def run_ours(args):
     loss_ready = [torch.cuda.Event(), torch.cuda.Event()]
     losses = []
     n_e2e = max(10, args.steps)
+    # the same batches as the device-timed steps (after one untimed step on
+    # the batch before them), so that the two numbers compare like for like
     plan = []
     for i in range(n_e2e + 1):
-        if batch_list is not None:
-            plan.append(batch_list[bcur % len(batch_list)])
-            bcur += 1
-        else:
-            plan.append(None)
+        plan.append(None if batch_list is None else batch_list[(t_start - 1 + i) % len(batch_list)])
     # one untimed pass first: the first replay of a freshly captured graph
     # also uploads it to the device
     ts.put(js.views if plan[0] is None else plan[0].numpy())

@@ -657,7 +657,8 @@ gs_status sfm_ba_lm_accept(int32_t n_cams, int32_t n_points, double* objective,
  * with camera 0 held fixed: S' dc' = rhs' over cameras 1..V-1, S' being S
  * without camera 0's six rows and columns.  S is overwritten (its lower
  * triangle below camera 0 holds the Cholesky factor of S', and camera 0's
- * block is scratch); dc [V,6] is written, row 0 zero.  The factorization
+ * rows are scratch: the reciprocals of the factor's diagonal among them);
+ * dc [V,6] is written, row 0 zero.  The factorization
  * is tiled (32 x 32 tiles): per tile column one launch factors the
  * diagonal tile, one solves the tiles below it and one updates the
  * trailing tiles, a block per tile, so the O(n^3 / 6) flops (n = 6 (V - 1))

@@ -505,9 +505,10 @@ __global__ void __launch_bounds__(128) ba_back_substitute_kernel(
 //   update A_ij -= L_ik L_jk^T for k < j <= i (four blocks per tile),
 // so the O(n^3 / 6) flops of the updates are spread over the SMs.  A pivot
 // that is not positive (S' not positive definite) sets a marker in S[0]
-// (camera 0's block, not part of S' and free to use as scratch) that the
+// (camera 0's rows are not part of S' and free to use as scratch) that the
 // later kernels read: they then do nothing, and the solve writes dc = 0
-// and raises GS_FLAG_NOT_SPD.
+// and raises GS_FLAG_NOT_SPD.  S[1 .. n] receive the reciprocals of L's
+// diagonal, which the solve uses.
 constexpr int kChT = 32;
 
 __device__ inline bool chol_failed(const double* S) { return *(volatile const double*)S != 0.0; }
@@ -611,6 +612,7 @@ __global__ void __launch_bounds__(kDiagThreads) ba_chol_diag_kernel(int n, size_
     const int r = e / m, c = e % m;
     if (c <= r) A[(size_t)(r0 + r) * ld + r0 + c] = (r == c ? s_piv[c] : a[r][c]) * s_inv[c];  // sqrt(d) = d / sqrt(d)
   }
+  if (t < m) S[1 + r0 + t] = s_inv[t];  // the reciprocal of L's diagonal, for the solve
 }
 
 // Tile (k + 1 + blockIdx.x, k): X L_kk^T = A_ik.  Four threads per row, each
@@ -715,10 +717,13 @@ __global__ void __launch_bounds__(1024) ba_chol_solve_kernel(int V, double* __re
     for (int tt = 0; tt < T; ++tt) {
       const int t = pass == 0 ? tt : T - 1 - tt;
       const int r0 = t * kChT, m = min(kChT, n - r0);
+      // the tile's triangle scaled so that each substitution step is one
+      // FMA: column c by 1 / L_cc (forward), row c by 1 / L_cc (backward)
       for (int e = threadIdx.x; e < kChT * kChT; e += blockDim.x) {
         const int r = e / kChT, c = e % kChT;
-        Ld[r][c] = (r < m && c <= r) ? A[(size_t)(r0 + r) * ld + r0 + c] : 0.0;
+        Ld[r][c] = (r < m && c <= r) ? A[(size_t)(r0 + r) * ld + r0 + c] * S[1 + r0 + (pass == 0 ? c : r)] : 0.0;
       }
+      if ((int)threadIdx.x < m) inv[threadIdx.x] = S[1 + r0 + threadIdx.x];
       if (warp < m) {
         const int r = warp;
         double v = 0.0;
@@ -733,23 +738,22 @@ __global__ void __launch_bounds__(1024) ba_chol_solve_kernel(int V, double* __re
       }
       __syncthreads();
       if (warp == 0) {
-        if (lane < m) inv[lane] = 1.0 / Ld[lane][lane];
-        __syncwarp();
+        // right-looking substitution on the unscaled unknowns: lane c's
+        // value is final once step c comes, then only the FMA of the later
+        // (earlier) lanes depends on it; each lane scales its own at the end
         double v = lane < m ? part[lane] : 0.0;
         if (pass == 0) {
           for (int c = 0; c < m; ++c) {
-            const double yc = __shfl_sync(0xffffffffu, v, c) * inv[c];
-            if (lane == c) v = yc;
-            else if (lane > c && lane < m) v -= Ld[lane][c] * yc;
+            const double vc = __shfl_sync(0xffffffffu, v, c);
+            if (lane > c && lane < m) v = fma(-Ld[lane][c], vc, v);
           }
         } else {
           for (int c = m - 1; c >= 0; --c) {
-            const double xc = __shfl_sync(0xffffffffu, v, c) * inv[c];
-            if (lane == c) v = xc;
-            else if (lane < c) v -= Ld[c][lane] * xc;
+            const double vc = __shfl_sync(0xffffffffu, v, c);
+            if (lane < c) v = fma(-Ld[c][lane], vc, v);
           }
         }
-        if (lane < m) y[r0 + lane] = v;
+        if (lane < m) y[r0 + lane] = v * inv[lane];
       }
       __syncthreads();
     }
