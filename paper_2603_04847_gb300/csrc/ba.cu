@@ -617,23 +617,25 @@ __global__ void __launch_bounds__(kDiagThreads) ba_chol_diag_kernel(int n, size_
 
 // Tile (k + 1 + blockIdx.x, k): X L_kk^T = A_ik.  Four threads per row, each
 // owning every fourth column of it in registers (forward substitution,
-// right-looking: once x_c is final the owners of the later columns subtract
-// its products at once).  Each x_j takes its products in the order q = 0, 1,
-// ..., j - 1.  A panel lies below a full diagonal tile: only the last tile
-// column is ragged, and it has none.
+// right-looking on the unscaled unknowns: once v_c is final, the owners of
+// the later columns subtract v_c M_jc at once, M = L_kk with column c
+// scaled by 1 / L_cc, so a step of the serial path is one shuffle and one
+// FMA; each unknown is scaled by its 1 / L_cc at the end).  The reciprocal
+// pivots come from the diagonal kernel (S[1 ..]).  A panel lies below a
+// full diagonal tile: only the last tile column is ragged, and it has none.
 __global__ void __launch_bounds__(4 * kChT) ba_chol_panel_kernel(int n, size_t ld, double* __restrict__ S, int k) {
-  __shared__ double L[kChT][kChT + 1];
+  __shared__ double M[kChT][kChT + 1];
   __shared__ double inv[kChT];
   if (chol_failed(S)) return;
   double* A = S + 6 * ld + 6;
   const int c0 = k * kChT;
   const int r0 = (k + 1 + (int)blockIdx.x) * kChT, mi = min(kChT, n - r0);
+  if ((int)threadIdx.x < kChT) inv[threadIdx.x] = S[1 + c0 + threadIdx.x];
+  __syncthreads();
   for (int e = threadIdx.x; e < kChT * kChT; e += blockDim.x) {
     const int r = e / kChT, c = e % kChT;
-    L[r][c] = c <= r ? A[(size_t)(c0 + r) * ld + c0 + c] : 0.0;
+    M[r][c] = c < r ? A[(size_t)(c0 + r) * ld + c0 + c] * inv[c] : 0.0;
   }
-  __syncthreads();
-  if ((int)threadIdx.x < kChT) inv[threadIdx.x] = 1.0 / L[threadIdx.x][threadIdx.x];
   __syncthreads();
   const int r = threadIdx.x / 4, p = threadIdx.x % 4;  // row r, columns p, p + 4, ...
   const int lane = threadIdx.x % 32;
@@ -643,19 +645,14 @@ __global__ void __launch_bounds__(4 * kChT) ba_chol_panel_kernel(int n, size_t l
   for (int i = 0; i < kOwn; ++i) x[i] = r < mi ? A[(size_t)(r0 + r) * ld + c0 + p + 4 * i] : 0.0;
 #pragma unroll
   for (int c = 0; c < kChT; ++c) {
-    double xc = 0.0;
-    if (p == (c & 3)) {
-      x[c >> 2] *= inv[c];
-      xc = x[c >> 2];
-    }
-    xc = __shfl_sync(0xffffffffu, xc, (lane & ~3) | (c & 3));
+    const double vc = __shfl_sync(0xffffffffu, x[c >> 2], (lane & ~3) | (c & 3));
 #pragma unroll
     for (int i = 0; i < kOwn; ++i)
-      if (p + 4 * i > c) x[i] -= xc * L[p + 4 * i][c];
+      if (p + 4 * i > c) x[i] = fma(-vc, M[p + 4 * i][c], x[i]);
   }
   if (r < mi) {
 #pragma unroll
-    for (int i = 0; i < kOwn; ++i) A[(size_t)(r0 + r) * ld + c0 + p + 4 * i] = x[i];
+    for (int i = 0; i < kOwn; ++i) A[(size_t)(r0 + r) * ld + c0 + p + 4 * i] = x[i] * inv[p + 4 * i];
   }
 }
 
