@@ -36,6 +36,13 @@ class BundleAdjuster:
         self.X_trial = torch.empty_like(self.X)
         op = np.asarray(obs_point, np.int32)
         oc = np.asarray(obs_cam, np.int32)
+        xy = np.asarray(obs_xy, np.float32).reshape(-1, 2)
+        # observations in camera order (stable; the benchmark's already
+        # are): the blocks' warps then share a camera and add its sums once
+        # (sfm_ba_assemble); the results do not depend on the order beyond
+        # the FP64 summation order
+        perm = np.argsort(oc, kind="stable")
+        op, oc, xy = op[perm], oc[perm], xy[perm]
         V, P, M = cams.V, self.X.shape[0], op.shape[0]
         # each point's observations as a CSR list (setup, from the host arrays)
         ok = (op >= 0) & (op < P)
@@ -47,7 +54,7 @@ class BundleAdjuster:
             return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
 
         self.obs_point, self.obs_cam = t(op, torch.int32), t(oc, torch.int32)
-        self.obs_xy = t(np.asarray(obs_xy, np.float32).reshape(-1, 2), torch.float32)
+        self.obs_xy = t(xy, torch.float32)
         self.off, self.ids = t(off, torch.int64), t(ids, torch.int32)
         # the elimination by camera pairs: its plan is built once (the
         # observation structure does not change between iterations)
