@@ -216,18 +216,40 @@ __global__ void __launch_bounds__(256) adam_groups_kernel(AdamGroups G, float be
     const bool vec = (((uintptr_t)A.p | (uintptr_t)A.g | (uintptr_t)A.m | (uintptr_t)A.v) & 15) == 0;
     if (vec) {
       const int64_t hi4 = lo + ((hi - lo) & ~(int64_t)3);
-      for (int64_t i = lo + 4 * threadIdx.x; i < hi4; i += 4 * blockDim.x) {
-        float4 p = *reinterpret_cast<float4*>(A.p + i);
-        const float4 g = *reinterpret_cast<const float4*>(A.g + i);
-        float4 m = *reinterpret_cast<float4*>(A.m + i);
-        float4 v = *reinterpret_cast<float4*>(A.v + i);
-        adam_elem(p.x, g.x, m.x, v.x, a, beta1, beta2, rb2, eps);
-        adam_elem(p.y, g.y, m.y, v.y, a, beta1, beta2, rb2, eps);
-        adam_elem(p.z, g.z, m.z, v.z, a, beta1, beta2, rb2, eps);
-        adam_elem(p.w, g.w, m.w, v.w, a, beta1, beta2, rb2, eps);
-        *reinterpret_cast<float4*>(A.p + i) = p;
-        *reinterpret_cast<float4*>(A.m + i) = m;
-        *reinterpret_cast<float4*>(A.v + i) = v;
+      // two float4 of each stream per thread in flight: all eight loads
+      // are issued before the first store (the streams may not alias one
+      // another, which the compiler cannot know)
+      const int64_t step4 = 4 * (int64_t)blockDim.x;
+      for (int64_t i = lo + 4 * threadIdx.x; i < hi4; i += 2 * step4) {
+        const int64_t j = i + step4;
+        const bool two = j < hi4;
+        float4 p0 = *reinterpret_cast<float4*>(A.p + i), p1;
+        const float4 g0 = *reinterpret_cast<const float4*>(A.g + i);
+        float4 m0 = *reinterpret_cast<float4*>(A.m + i), m1;
+        float4 v0 = *reinterpret_cast<float4*>(A.v + i), v1;
+        float4 g1;
+        if (two) {
+          p1 = *reinterpret_cast<float4*>(A.p + j);
+          g1 = *reinterpret_cast<const float4*>(A.g + j);
+          m1 = *reinterpret_cast<float4*>(A.m + j);
+          v1 = *reinterpret_cast<float4*>(A.v + j);
+        }
+        adam_elem(p0.x, g0.x, m0.x, v0.x, a, beta1, beta2, rb2, eps);
+        adam_elem(p0.y, g0.y, m0.y, v0.y, a, beta1, beta2, rb2, eps);
+        adam_elem(p0.z, g0.z, m0.z, v0.z, a, beta1, beta2, rb2, eps);
+        adam_elem(p0.w, g0.w, m0.w, v0.w, a, beta1, beta2, rb2, eps);
+        *reinterpret_cast<float4*>(A.p + i) = p0;
+        *reinterpret_cast<float4*>(A.m + i) = m0;
+        *reinterpret_cast<float4*>(A.v + i) = v0;
+        if (two) {
+          adam_elem(p1.x, g1.x, m1.x, v1.x, a, beta1, beta2, rb2, eps);
+          adam_elem(p1.y, g1.y, m1.y, v1.y, a, beta1, beta2, rb2, eps);
+          adam_elem(p1.z, g1.z, m1.z, v1.z, a, beta1, beta2, rb2, eps);
+          adam_elem(p1.w, g1.w, m1.w, v1.w, a, beta1, beta2, rb2, eps);
+          *reinterpret_cast<float4*>(A.p + j) = p1;
+          *reinterpret_cast<float4*>(A.m + j) = m1;
+          *reinterpret_cast<float4*>(A.v + j) = v1;
+        }
       }
       for (int64_t i = hi4 + threadIdx.x; i < hi; i += blockDim.x)
         adam_elem(A.p[i], A.g[i], A.m[i], A.v[i], a, beta1, beta2, rb2, eps);
