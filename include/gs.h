@@ -437,6 +437,19 @@ gs_status gs_project_bwd(const gs_gaussians* g, const gs_cameras* cams,
                          const gs_batch* batch, const gs_projected* proj,
                          const gs_gaussian_grads* dg, double* g_pose_tangent,
                          void* ws, size_t ws_bytes, gs_stream stream);
+/*
+ * gs_project_bwd_clearing — gs_project_bwd (same arguments and results)
+ * that also leaves the screen-space records zero behind it: each record is
+ * zeroed right after it is read, all B * n_gaussians of them.  A following
+ * gs_raster_bwd_zeroed on the same workspace then needs no clearing pass
+ * (the first one after allocation still does).  FP32.
+ */
+gs_status gs_project_bwd_clearing(const gs_gaussians* g, const gs_cameras* cams,
+                                  const gs_batch* batch,
+                                  const gs_projected* proj,
+                                  const gs_gaussian_grads* dg,
+                                  double* g_pose_tangent, void* ws,
+                                  size_t ws_bytes, gs_stream stream);
 
 /*
  * track_reproj_fwd_bwd — Eq. 6 for the observations of the batch's views

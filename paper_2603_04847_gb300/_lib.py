@@ -110,6 +110,8 @@ PROTOTYPES = {
                                             c_void_p, c_size_t, c_void_p]),
     "gs_project_bwd": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                       c_size_t, c_void_p]),
+    "gs_project_bwd_clearing": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                               c_void_p, c_size_t, c_void_p]),
     "gs_render_bwd_det_workspace": (ctypes.c_int, [c_int32, c_void_p, c_size_t, ctypes.POINTER(c_size_t)]),
     "gs_raster_bwd_det": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                          c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_float,

@@ -386,14 +386,17 @@ def gs_raster_bwd(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, tl
 
 
 def gs_project_bwd(g: Gaussians, cams: Cameras, batch: Batch, proj: Projected, dg: Gaussians,
-                   g_pose_tangent: torch.Tensor, ws: torch.Tensor, Rt=None, stream=None):
+                   g_pose_tangent: torch.Tensor, ws: torch.Tensor, Rt=None, stream=None, clear_records: bool = False):
+    """clear_records: gs_project_bwd_clearing, which leaves the screen-space
+    records of ws zero behind it (FP32 only)."""
     lib = _lib.load()
     _need_cuda(g_pose_tangent, ws)
+    if clear_records and g.f64:
+        raise _lib.GsError("gs_project_bwd_clearing is FP32 only")
     gc, cc, bc, pc, dgc = g.c(), cams.c(Rt, f64=g.f64), batch.c(), proj.c(), dg.grads_c()
-    check(_fn(lib, "gs_project_bwd", g.f64)(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc),
-                                            ctypes.byref(pc), ctypes.byref(dgc), _p(g_pose_tangent), _p(ws),
-                                            ws.numel(), _stream(stream)),
-          "gs_project_bwd")
+    fn = lib.gs_project_bwd_clearing if clear_records else _fn(lib, "gs_project_bwd", g.f64)
+    check(fn(ctypes.byref(gc), ctypes.byref(cc), ctypes.byref(bc), ctypes.byref(pc), ctypes.byref(dgc),
+             _p(g_pose_tangent), _p(ws), ws.numel(), _stream(stream)), "gs_project_bwd")
 
 
 def photo_loss_workspace_bytes(batch: Batch) -> int:

@@ -294,11 +294,11 @@ gs_status gs_raster_bwd_zeroed(const gs_gaussians* g, const gs_cameras* cams, co
                     loss, ws, ws_bytes, stream, false, "gs_raster_bwd_zeroed");
 }
 
-gs_status gs_project_bwd(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
-                         const gs_projected* proj, const gs_gaussian_grads* dg, double* g_pose_tangent,
-                         void* ws, size_t ws_bytes, gs_stream stream) {
+static gs_status project_bwd_call(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
+                                  const gs_projected* proj, const gs_gaussian_grads* dg, double* g_pose_tangent,
+                                  void* ws, size_t ws_bytes, gs_stream stream, bool clear, const char* who) {
   gs_status s;
-  if ((s = check_bwd_common(g, cams, batch, proj, ws, ws_bytes, "gs_project_bwd"))) return s;
+  if ((s = check_bwd_common(g, cams, batch, proj, ws, ws_bytes, who))) return s;
   if (!dg || !g_pose_tangent) return fail(GS_ERR_ARG, "gs_project_bwd: null argument");
   if (!dg->mean || !dg->log_scale || !dg->quat || !dg->opacity_logit || !dg->sh)
     return fail(GS_ERR_ARG, "gs_project_bwd: null gradient array");
@@ -306,10 +306,23 @@ gs_status gs_project_bwd(const gs_gaussians* g, const gs_cameras* cams, const gs
   const size_t vb = v2d_bytes(g->n, *batch);
   float* v2d = reinterpret_cast<float*>(ws);
   double* partial = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + vb);
-  cudaError_t e = launch_project_bwd(*g, *cams, *batch, *proj, v2d, *dg, partial, g_pose_tangent,
+  cudaError_t e = launch_project_bwd(*g, *cams, *batch, *proj, v2d, *dg, partial, g_pose_tangent, clear,
                                      (cudaStream_t)stream);
-  if (e != cudaSuccess) return cuda_fail(e, "gs_project_bwd");
+  if (e != cudaSuccess) return cuda_fail(e, who);
   return GS_OK;
+}
+
+gs_status gs_project_bwd(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
+                         const gs_projected* proj, const gs_gaussian_grads* dg, double* g_pose_tangent,
+                         void* ws, size_t ws_bytes, gs_stream stream) {
+  return project_bwd_call(g, cams, batch, proj, dg, g_pose_tangent, ws, ws_bytes, stream, false, "gs_project_bwd");
+}
+
+gs_status gs_project_bwd_clearing(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,
+                                  const gs_projected* proj, const gs_gaussian_grads* dg, double* g_pose_tangent,
+                                  void* ws, size_t ws_bytes, gs_stream stream) {
+  return project_bwd_call(g, cams, batch, proj, dg, g_pose_tangent, ws, ws_bytes, stream, true,
+                          "gs_project_bwd_clearing");
 }
 
 gs_status gs_render_bwd(const gs_gaussians* g, const gs_cameras* cams, const gs_batch* batch,

@@ -26,8 +26,8 @@ cudaError_t launch_project_bwd_f64(const gs_gaussians_f64& g, const gs_cameras_f
                                    const gs_projected_f64& proj, const double* v2d, const gs_gaussian_grads_f64& dg,
                                    double* partial, double* g_pose_tangent, cudaStream_t st);
 cudaError_t launch_project_bwd(const gs_gaussians& g, const gs_cameras& cams, const gs_batch& batch,
-                               const gs_projected& proj, const float* v2d, const gs_gaussian_grads& dg,
-                               double* partial, double* g_pose_tangent, cudaStream_t st);
+                               const gs_projected& proj, float* v2d, const gs_gaussian_grads& dg,
+                               double* partial, double* g_pose_tangent, bool clear_records, cudaStream_t st);
 
 int sort_tile_bits(int n_tiles_total);
 size_t sort_workspace_bytes(int N, const gs_batch& batch, size_t capacity);

@@ -297,6 +297,19 @@ __device__ inline void load_rec9(const float* v2d, size_t rec, float (&o)[9]) {
   o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
   o[8] = p[2].x;
 }
+// Zeroes record rec (all 12 scalars) after it has been read.
+__device__ inline void clear_rec(float* v2d, size_t rec) {
+  float4* p = reinterpret_cast<float4*>(v2d) + 3 * rec;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  p[0] = z;
+  p[1] = z;
+  p[2] = z;
+}
+__device__ inline void clear_rec(double* v2d, size_t rec) {
+  double2* p = reinterpret_cast<double2*>(v2d) + 6 * rec;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) p[i] = make_double2(0.0, 0.0);
+}
 __device__ inline void load_rec9(const double* v2d, size_t rec, double (&o)[9]) {
   const double2* p = reinterpret_cast<const double2*>(v2d) + 6 * rec;
 #pragma unroll
@@ -405,8 +418,8 @@ constexpr int kProjBwdMinBlocks = 3;
 
 template <typename T, int DEG>
 __global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? kProjBwdMinBlocks : 1) project_bwd_kernel(
-    GaussT<T> g, CamsT<T> cams, gs_batch batch, ProjT<T> proj, const T* __restrict__ v2d, GradsT<T> dg,
-    double* __restrict__ partial) {
+    GaussT<T> g, CamsT<T> cams, gs_batch batch, ProjT<T> proj, T* __restrict__ v2d, GradsT<T> dg,
+    double* __restrict__ partial, bool clear) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   __shared__ SlotCamT<T> sc[GS_MAX_BATCH];
   // per warp and view: the warp's six pose-tangent sums (FP32 in the FP32
@@ -461,6 +474,10 @@ __global__ void __launch_bounds__(kProjThreads, sizeof(T) == 4 ? kProjBwdMinBloc
 #pragma unroll
     for (int i = 0; i < 9; ++i) cur[i] = nrec[i];
     if (active && b + 1 < batch.B) load_rec9(v2d, (size_t)(b + 1) * N + j, nrec);
+    // record b has been read (its load was issued a view earlier), so the
+    // store does not wait on it; a store right behind the load of the same
+    // address would hold up the prefetch
+    if (clear && active) clear_rec(v2d, (size_t)b * N + j);
     bool nz = false;
 #pragma unroll
     for (int i = 0; i < 9; ++i) nz = nz || (cur[i] != T(0));
@@ -736,7 +753,7 @@ cudaError_t project_fwd_t(const GaussT<T>& g, const CamsT<T>& cams, const gs_bat
 
 template <typename T, int DEG>
 cudaError_t project_bwd_deg(const GaussT<T>& g, const CamsT<T>& cams, const gs_batch& batch, const ProjT<T>& proj,
-                            const T* v2d, const GradsT<T>& dg, double* partial, int blocks, cudaStream_t st) {
+                            T* v2d, const GradsT<T>& dg, double* partial, int blocks, bool clear, cudaStream_t st) {
   constexpr size_t smem = project_bwd_smem<T, DEG>();
   // the opt-in for more than 48 KB of shared memory, once per device
   static bool configured[64] = {false};
@@ -748,22 +765,22 @@ cudaError_t project_bwd_deg(const GaussT<T>& g, const CamsT<T>& cams, const gs_b
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
-  project_bwd_kernel<T, DEG><<<blocks, kProjThreads, smem, st>>>(g, cams, batch, proj, v2d, dg, partial);
+  project_bwd_kernel<T, DEG><<<blocks, kProjThreads, smem, st>>>(g, cams, batch, proj, v2d, dg, partial, clear);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t project_bwd_t(const GaussT<T>& g, const CamsT<T>& cams, const gs_batch& batch, const ProjT<T>& proj,
-                          const T* v2d, const GradsT<T>& dg, double* partial, double* g_pose_tangent,
+                          T* v2d, const GradsT<T>& dg, double* partial, double* g_pose_tangent, bool clear,
                           cudaStream_t st) {
   const int blocks = project_bwd_blocks(g.n);
   if (blocks == 0) return cudaSuccess;
   cudaError_t e;
   switch (g.sh_degree) {
-    case 0: e = project_bwd_deg<T, 0>(g, cams, batch, proj, v2d, dg, partial, blocks, st); break;
-    case 1: e = project_bwd_deg<T, 1>(g, cams, batch, proj, v2d, dg, partial, blocks, st); break;
-    case 2: e = project_bwd_deg<T, 2>(g, cams, batch, proj, v2d, dg, partial, blocks, st); break;
-    default: e = project_bwd_deg<T, 3>(g, cams, batch, proj, v2d, dg, partial, blocks, st); break;
+    case 0: e = project_bwd_deg<T, 0>(g, cams, batch, proj, v2d, dg, partial, blocks, clear, st); break;
+    case 1: e = project_bwd_deg<T, 1>(g, cams, batch, proj, v2d, dg, partial, blocks, clear, st); break;
+    case 2: e = project_bwd_deg<T, 2>(g, cams, batch, proj, v2d, dg, partial, blocks, clear, st); break;
+    default: e = project_bwd_deg<T, 3>(g, cams, batch, proj, v2d, dg, partial, blocks, clear, st); break;
   }
   if (e != cudaSuccess) return e;
   return launch_pose_partials_finalize(partial, blocks, batch, cams.n_cams, g_pose_tangent, st);
@@ -784,17 +801,17 @@ cudaError_t launch_project_fwd_f64(const gs_gaussians_f64& g, const gs_cameras_f
 }
 
 cudaError_t launch_project_bwd(const gs_gaussians& g, const gs_cameras& cams, const gs_batch& batch,
-                               const gs_projected& proj, const float* v2d, const gs_gaussian_grads& dg,
-                               double* partial, double* g_pose_tangent, cudaStream_t st) {
+                               const gs_projected& proj, float* v2d, const gs_gaussian_grads& dg,
+                               double* partial, double* g_pose_tangent, bool clear_records, cudaStream_t st) {
   return project_bwd_t<float>(view_of(g), view_of(cams), batch, view_of(proj), v2d, view_of(dg), partial,
-                              g_pose_tangent, st);
+                              g_pose_tangent, clear_records, st);
 }
 
 cudaError_t launch_project_bwd_f64(const gs_gaussians_f64& g, const gs_cameras_f64& cams, const gs_batch& batch,
                                    const gs_projected_f64& proj, const double* v2d, const gs_gaussian_grads_f64& dg,
                                    double* partial, double* g_pose_tangent, cudaStream_t st) {
-  return project_bwd_t<double>(view_of(g), view_of(cams), batch, view_of(proj), v2d, view_of(dg), partial,
-                               g_pose_tangent, st);
+  return project_bwd_t<double>(view_of(g), view_of(cams), batch, view_of(proj), const_cast<double*>(v2d),
+                               view_of(dg), partial, g_pose_tangent, false, st);
 }
 
 }  // namespace gs

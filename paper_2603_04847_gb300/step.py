@@ -49,6 +49,7 @@ class Renderer:
         self.bg = torch.tensor(bg, dtype=dtype, device=device)
         self.ws_bwd = torch.empty(max(self._bwd_bytes(), 256), dtype=torch.uint8, device=device)
         self.status = new_status(device)
+        self.zero_records()   # so that a first backward may already pass records_zeroed
 
     def _bwd_bytes(self) -> int:
         if self.deterministic:
@@ -87,10 +88,13 @@ class Renderer:
 
     def backward(self, g: Gaussians, dg: Gaussians, g_tangent: torch.Tensor, v_image=None, target=None,
                  l1_weight: float = 1.0, loss=None, Rt: torch.Tensor = None, mark=_nomark,
-                 records_zeroed: bool = False):
+                 records_zeroed: bool = False, clear_records: bool = False):
         # gs_render_bwd is exactly these two calls; issuing them separately
-        # lets a caller time each half.  records_zeroed: zero_records() was
-        # issued before (on any stream ordered before this one)
+        # lets a caller time each half.  records_zeroed: the records are
+        # zero (zero_records() was issued before, on any stream ordered
+        # before this one, or the last backward cleared them).
+        # clear_records: the projection backward zeroes each record after
+        # reading it, so that the next backward can pass records_zeroed
         if self.deterministic:
             gs_raster_bwd_det(g, self.cams, self.batch, self.proj, self.tl, self.bg, self.image, self.T_final,
                               self.n_contrib, v_image, target, l1_weight, loss, self.ws_bwd, Rt)
@@ -99,8 +103,15 @@ class Renderer:
                           self.n_contrib, v_image, target, l1_weight, loss, self.ws_bwd, Rt,
                           records_zeroed=records_zeroed and self.dtype == torch.float32)
         mark("raster_bwd")
-        gs_project_bwd(g, self.cams, self.batch, self.proj, dg, g_tangent, self.ws_bwd, Rt)
+        gs_project_bwd(g, self.cams, self.batch, self.proj, dg, g_tangent, self.ws_bwd, Rt,
+                       clear_records=clear_records and self.atomic_records)
         mark("project_bwd")
+
+    @property
+    def atomic_records(self) -> bool:
+        """The backward accumulates into screen-space records that must be
+        zero before it (FP32, not the deterministic form)."""
+        return not self.deterministic and self.dtype == torch.float32
 
     def count_added(self, g: Gaussians, Rt: torch.Tensor = None) -> int:
         """Re-runs the forward with the per-pixel added-splat counter and
@@ -337,11 +348,9 @@ class JointStep:
                 extra = [] if self.merged_tracks else [self.gX]   # merged: gX is dg.mean
                 for t in self.dg.tensors() + extra + [self.g_tan, self.loss, self.n_masked]:
                     gs_zero(t)
-                # the backward's screen-space records too: a memset of B N 48
-                # bytes, here beside the compute-bound compositing instead of
-                # in front of the backward
-                for r in self.renderers:
-                    r.zero_records()
+                # the backward's screen-space records need no clearing: the
+                # last step's projection backward zeroed each after reading
+                # it (clear_records), the renderer's construction before that
                 self._gather_targets()
                 # the track term: done before the join, so its += into the
                 # pose tangent (and, merged, into dg.mean) precedes the
@@ -369,10 +378,10 @@ class JointStep:
                               self.loss[0:1], r.v_image, r.ws_photo, self.Rt)
                 mark("photo")
                 r.backward(self.g, self.dg, self.g_tan, v_image=r.v_image, loss=self.loss[0:1], Rt=self.Rt,
-                           mark=mark, records_zeroed=True)
+                           mark=mark, records_zeroed=True, clear_records=True)
             else:
                 r.backward(self.g, self.dg, self.g_tan, target=tgt, l1_weight=h.l1_weight, loss=self.loss[0:1],
-                           Rt=self.Rt, mark=mark, records_zeroed=True)
+                           Rt=self.Rt, mark=mark, records_zeroed=True, clear_records=True)
         if not joined:
             fork()
             main.wait_stream(side)

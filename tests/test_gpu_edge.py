@@ -166,6 +166,57 @@ def test_graph_replay_matches_eager_and_plain():
     assert int(eager.step_no.item()) == 3 and int(graphed.step_no.item()) == 3
 
 
+def test_records_cleared_by_the_projection_backward():
+    """The joint step leaves the backward's screen-space records zero
+    behind its projection backward (gs_project_bwd_clearing), so it skips
+    the clearing pass: three graph replays equal three steps that zero the
+    records explicitly before each backward, and the records are zero
+    after every step."""
+    cleared = _joint("batched")
+    cleared.capture(warmup=0)
+    for _ in range(3):
+        cleared.run()
+        torch.cuda.synchronize()
+        for r in cleared.renderers:
+            assert not r.ws_bwd[:r.batch.B * r.n * 48].any()
+    zeroed = _joint("batched")
+    for _ in range(3):
+        for r in zeroed.renderers:
+            r.zero_records()
+        zeroed.step()
+    torch.cuda.synchronize()
+    for x, y in zip(_state(cleared), _state(zeroed)):
+        np.testing.assert_allclose(x, y, rtol=1e-4, atol=1e-6)
+    assert cleared.status_flags() == 0
+
+
+def test_project_bwd_clearing_equals_project_bwd():
+    from paper_2603_04847_gb300 import Gaussians
+    from paper_2603_04847_gb300.core import gs_project_bwd
+    w = synth.make_workload("batched", n_gaussians=2000, n_views=3, width=(60, 90), height=(40, 70), n_tracks=10)
+    r, g, cams, batch = gpu_forward(w["scene"], w["wh"], w["K"], w["Rt"], [0, 1, 2])
+    rng = np.random.default_rng(4)
+    vimg = torch.as_tensor(rng.normal(size=(batch.pixels, 3)), dtype=torch.float32, device="cuda")
+    from paper_2603_04847_gb300.core import gs_raster_bwd
+    gs_raster_bwd(g, cams, batch, r.proj, r.tl, r.bg, r.image, r.T_final, r.n_contrib, vimg, None, 1.0, None,
+                  r.ws_bwd)
+    rec = r.ws_bwd[:batch.B * g.n * 48].clone()
+    outs = []
+    for clear in (False, True):
+        r.ws_bwd[:batch.B * g.n * 48].copy_(rec)
+        dg = Gaussians.zeros_like(g)
+        tan = torch.zeros((cams.V, 6), dtype=torch.float64, device="cuda")
+        gs_project_bwd(g, cams, batch, r.proj, dg, tan, r.ws_bwd, clear_records=clear)
+        torch.cuda.synchronize()
+        outs.append([t.cpu().numpy() for t in dg.tensors()] + [tan.cpu().numpy()])
+        if clear:
+            assert not r.ws_bwd[:batch.B * g.n * 48].any()
+        else:
+            assert torch.equal(r.ws_bwd[:batch.B * g.n * 48], rec)
+    for a, b in zip(*outs):
+        np.testing.assert_array_equal(a, b)
+
+
 def test_target_stream_matches_device_resident_targets():
     """Streaming each step's targets from pinned host memory one step ahead
     (TargetStream: two alternating device copies filled on a copy stream)
