@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain one-view-per-launch timing")
     ap.add_argument("--lambda-ssim", type=float, default=0.0,
                     help="SSIM weight of Eq. 5 (the paper: 0.2); 0 = the L1 photometric term alone")
+    ap.add_argument("--variant", default="full", choices=["full", "frozen-poses", "photometric-only", "merged-tracks"],
+                    help="the paper's ablation variants of the joint step (full: the method)")
     ap.add_argument("--deterministic", action="store_true",
                     help="the compositing backward with run-to-run bit-identical gradients")
     ap.add_argument("--profile-steps", type=int, default=0,
@@ -493,11 +495,18 @@ def tune_child(workload, mode, local, cache_path, lambda_ssim=0.0, w_path=None, 
         json.dump(cache, f)
 
 
-def make_step(inp, views, mode, lambda_ba, tile=16, lambda_ssim=0.0, dynamic=False, deterministic=False):
+def make_step(inp, views, mode, lambda_ba, tile=16, lambda_ssim=0.0, dynamic=False, deterministic=False,
+              variant="full"):
+    """variant: the paper's ablation variants -- frozen-poses (no pose
+    update), photometric-only (lambda_BA = 0: no track term), merged-tracks
+    (the track points are Gaussian means: the tracks' point ids index the
+    Gaussians)."""
     from paper_2603_04847_gb300 import Hyper, JointStep
+    h = Hyper(lambda_ba=0.0 if variant == "photometric-only" else lambda_ba, lambda_ssim=lambda_ssim,
+              freeze_poses=variant == "frozen-poses")
     js = JointStep(inp["g"], inp["cams"], inp["X"], inp["obs_point"], inp["obs_xy"], inp["view_obs_offset"],
-                   inp["targets"], inp["off"], views, Hyper(lambda_ba=lambda_ba, lambda_ssim=lambda_ssim), mode=mode,
-                   tile=tile, dynamic_batch=dynamic, deterministic=deterministic)
+                   inp["targets"], inp["off"], views, h, mode=mode, tile=tile, dynamic_batch=dynamic,
+                   deterministic=deterministic, merged_tracks=variant == "merged-tracks")
     js.ensure_capacity()
     return js
 
@@ -690,7 +699,7 @@ def run_ours(args):
     dyn = uneven(w)
     views = list(range(min(W.batch, W.n_views)))
     js = make_step(inp, views, args.mode, W.lambda_ba, lambda_ssim=args.lambda_ssim, dynamic=dyn,
-                   deterministic=args.deterministic)
+                   deterministic=args.deterministic, variant=args.variant)
     # random batches (Algorithm 1, "Sample image indices") when the workload
     # has more views than one batch
     n_batches = args.warmup + args.steps + max(10, args.steps) + 8
@@ -842,7 +851,7 @@ def run_ours(args):
     plain = None
     if not args.no_plain and args.mode == "batched":
         jp = make_step(inp, views, "plain", W.lambda_ba, tile=js.tile, lambda_ssim=args.lambda_ssim, dynamic=dyn,
-                       deterministic=args.deterministic)
+                       deterministic=args.deterministic, variant=args.variant)
         npl = max(3, min(args.steps, 10))
         pb = None if batch_list is None else batch_list[:npl]
         if pb is not None:
@@ -940,6 +949,7 @@ def run_ours(args):
                                     W.batch, W.n_views, ", uneven sizes, laid out on the device" if dyn else "")
                                 if batch_list is not None else "all views every step",
                                 mean_pixels_per_step=P_mean,
+                                variant=args.variant,
                                 lambda_ssim=args.lambda_ssim,
                                 backward="deterministic (per-instance slots, fixed-order sums)"
                                 if args.deterministic else "atomic (per-tile sums added by FP32 atomics)",
