@@ -67,3 +67,11 @@ def test_empty_problem(plan_fn):
     assert got["inc"].shape == (0, 3) and got["pair_cams"].shape == (0, 2)
     np.testing.assert_array_equal(got["pair_chunks"], [0])
     np.testing.assert_array_equal(got["chunk_start"], [0])
+
+
+def test_bad_arguments_are_reported(plan_fn):
+    from paper_2603_04847_gb300._lib import GsError
+    with pytest.raises(GsError):
+        plan_fn(3, 1, np.zeros(2, np.int32), np.array([0, 2], np.int64), np.array([0, 1], np.int32), chunk=0)
+    with pytest.raises(GsError):
+        plan_fn(-1, 1, np.zeros(2, np.int32), np.array([0, 2], np.int64), np.array([0, 1], np.int32))
