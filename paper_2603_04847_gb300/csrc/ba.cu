@@ -408,15 +408,20 @@ __global__ void __launch_bounds__(128) ba_obs_y_kernel(int V, int P, int64_t M, 
 constexpr int kPairWarps = 4;
 __global__ void __launch_bounds__(32 * kPairWarps) ba_pair_chunk_kernel(
     int n_chunks, const int32_t* __restrict__ inc, const int64_t* __restrict__ chunk_start,
-    const double* __restrict__ Y, const double* __restrict__ Wo, double* __restrict__ partial) {
+    const int32_t* __restrict__ obs_cam, const double* __restrict__ Y, const double* __restrict__ Wo,
+    double* __restrict__ partial) {
   __shared__ double sh[kPairWarps][kPairValues][33];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int chunk = blockIdx.x * kPairWarps + warp;
   if (chunk >= n_chunks) return;  // warp-uniform; no block-wide barrier below
+  // a chunk's incidences share one camera pair: on the diagonal only the
+  // block's lower triangle is needed (the finalize reads no more)
+  const int64_t i0 = chunk_start[chunk];
+  const bool diag = obs_cam[inc[3 * i0 + 1]] == obs_cam[inc[3 * i0 + 2]];
   double acc[kPairValues];
 #pragma unroll
   for (int e = 0; e < kPairValues; ++e) acc[e] = 0.0;
-  for (int64_t i = chunk_start[chunk] + lane; i < chunk_start[chunk + 1]; i += 32) {
+  for (int64_t i = i0 + lane; i < chunk_start[chunk + 1]; i += 32) {
     const int a = inc[3 * i + 1], b = inc[3 * i + 2];
     const double* ya = Y + kObsY * (size_t)a;
     const double* wb = Wo + 18 * (size_t)b;
@@ -426,11 +431,19 @@ __global__ void __launch_bounds__(32 * kPairWarps) ba_pair_chunk_kernel(
       yv[e] = ya[e];
       wv[e] = wb[e];
     }
+    if (diag) {
 #pragma unroll
-    for (int r = 0; r < 6; ++r)
+      for (int r = 0; r < 6; ++r)
 #pragma unroll
-      for (int c = 0; c < 6; ++c)
-        acc[6 * r + c] += yv[3 * r] * wv[3 * c] + yv[3 * r + 1] * wv[3 * c + 1] + yv[3 * r + 2] * wv[3 * c + 2];
+        for (int c = 0; c <= r; ++c)
+          acc[6 * r + c] += yv[3 * r] * wv[3 * c] + yv[3 * r + 1] * wv[3 * c + 1] + yv[3 * r + 2] * wv[3 * c + 2];
+    } else {
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+          acc[6 * r + c] += yv[3 * r] * wv[3 * c] + yv[3 * r + 1] * wv[3 * c + 1] + yv[3 * r + 2] * wv[3 * c + 2];
+    }
     if (a == b) {
 #pragma unroll
       for (int r = 0; r < 6; ++r) acc[36 + r] += ya[18 + r];
@@ -859,9 +872,8 @@ cudaError_t launch_ba_schur_pairs(int V, int P, int64_t M, const double* U, cons
   ba_obs_y_kernel<<<(unsigned)std::min<int64_t>((M + 127) / 128, 65535), 128, 0, st>>>(
       V, P, M, gp, Vp, Wo, obs_cam, point_obs_offset, point_obs, Vinv, Y);
   if (n_chunks > 0) {
-    ba_pair_chunk_kernel<<<(n_chunks + kPairWarps - 1) / kPairWarps, 32 * kPairWarps, 0, st>>>(n_chunks, inc,
-                                                                                                chunk_start, Y, Wo,
-                                                                                                partial);
+    ba_pair_chunk_kernel<<<(n_chunks + kPairWarps - 1) / kPairWarps, 32 * kPairWarps, 0, st>>>(
+        n_chunks, inc, chunk_start, obs_cam, Y, Wo, partial);
     const int64_t nt = (int64_t)n_pairs * kPairValues;
     ba_pair_finalize_kernel<<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(V, n_pairs, pair_cams, pair_chunks, partial,
                                                                          S, rhs);
