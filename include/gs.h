@@ -13,10 +13,13 @@
  *   sfm_ba_assemble   Eq. 4: the normal-equation blocks of one LM iteration
  *   sfm_ba_schur, sfm_ba_solve_cameras, sfm_ba_back_substitute   Eq. 4:
  *                     point elimination, camera solve, back-substitution
+ *                     (sfm_ba_pair_lists + sfm_ba_schur_pairs: the
+ *                     elimination summed by camera pairs, no atomics)
  *   gs_mcmc_relocate, gs_mcmc_grow, gs_mcmc_noise, gs_mcmc_reset_moments
  *                     the MCMC densification (Sec. 3.3)
  *   gs_render_bwd     L1 gradient of Eq. 5 (fused) + compositing backward
- *                     + projection backward with pose gradient
+ *                     + projection backward with pose gradient (its halves
+ *                     gs_raster_bwd[_zeroed] and gs_project_bwd[_clearing])
  *                     (Algorithm 1 "Backpropagate"; Sec. 3.3: poses are
  *                     optimised by both losses)
  *   track_reproj_fwd_bwd   Eq. 6: Huber reprojection of the separate track
