@@ -312,19 +312,30 @@ __global__ void batch_layout_kernel(gs_cameras cams, gs_batch batch, int64_t* __
 // fixed order.  A camera may fill several slots of a batch: the block of its
 // first slot sums them all (slot order, then block order) and the blocks of
 // its other slots do nothing, so no two blocks write one camera's entries.
-__global__ void pose_partial_finalize_kernel(const double* __restrict__ partial, int n_blocks,
-                                             gs_batch batch, int n_cams, double* g_pose_tangent) {
+constexpr int kFinThreads = 1024;
+__global__ void __launch_bounds__(kFinThreads)
+    pose_partial_finalize_kernel(const double* __restrict__ partial, int n_blocks, gs_batch batch, int n_cams,
+                                 double* g_pose_tangent) {
   const int b = blockIdx.x / 6, i = blockIdx.x % 6;
   const int v = batch.views[b];
   for (int b2 = 0; b2 < b; ++b2)
     if (batch.views[b2] == v) return;  // block-uniform: an earlier slot owns camera v
-  __shared__ double red[256];
-  double s = 0.0;
+  __shared__ double red[kFinThreads];
+  // four interleaved running sums per thread (rows k, k + T, k + 2T, k + 3T
+  // of each group of 4T), then pairwise: a fixed order with short
+  // dependent chains (FP64 adds are slow to retire on this part)
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int b2 = b; b2 < batch.B; ++b2) {
     if (batch.views[b2] != v) continue;
-    for (int k = threadIdx.x; k < n_blocks; k += blockDim.x)
-      s += partial[(size_t)k * batch.B * 6 + 6 * b2 + i];
+    for (int k0 = 0; k0 < n_blocks; k0 += 4 * kFinThreads) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = k0 + q * kFinThreads + (int)threadIdx.x;
+        if (k < n_blocks) acc[q] += partial[(size_t)k * batch.B * 6 + 6 * b2 + i];
+      }
+    }
   }
+  const double s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
   red[threadIdx.x] = s;
   __syncthreads();
   for (int off = blockDim.x / 2; off > 0; off >>= 1) {
@@ -338,8 +349,8 @@ __global__ void pose_partial_finalize_kernel(const double* __restrict__ partial,
 
 cudaError_t launch_pose_partials_finalize(const double* partial, int n_blocks, const gs_batch& batch,
                                           int n_cams, double* g_pose_tangent, cudaStream_t st) {
-  pose_partial_finalize_kernel<<<batch.B * 6, 256, 0, st>>>(partial, n_blocks, batch, n_cams,
-                                                            g_pose_tangent);
+  pose_partial_finalize_kernel<<<batch.B * 6, kFinThreads, 0, st>>>(partial, n_blocks, batch, n_cams,
+                                                                    g_pose_tangent);
   return cudaGetLastError();
 }
 
